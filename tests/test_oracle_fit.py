@@ -1,0 +1,43 @@
+"""Pins for the oracle's Fisher scoring (Eq. 4) on log-parameters.
+
+The optimum is checked against scipy.optimize (a different optimiser on the same
+objective) and against the first-order condition g ~ 0."""
+import numpy as np
+import pytest
+import scipy.optimize as so
+
+import oracle
+import workloads
+
+EXP, MAT = oracle.EXP_ISO, oracle.MATERN_ISO
+
+
+@pytest.mark.parametrize("covfun,theta,start", [
+    (EXP, [1.0, 0.1, 0.05], [0.5, 0.3, 0.2]),
+    (MAT, [1.5, 0.08, 1.2, 0.05], [1.0, 0.15, 1.0, 0.1]),
+])
+def test_fisher_scoring_reaches_the_optimum(covfun, theta, start):
+    w = workloads.make_field(500, covfun, theta, 10, p=2, seed=17, sim="dense",
+                             beta=[1.0, -0.5])
+    fit = oracle.fisher_fit(w.locs, w.y, w.X, w.NN, covfun, np.array(start), tol=1e-8)
+    assert fit["status"] == 0
+    assert 1 <= fit["iters"] <= 40
+    # first-order condition on the log scale
+    gt = fit["theta"] * fit["grad"]
+    It = fit["theta"][:, None] * fit["info"] * fit["theta"][None, :]
+    assert gt @ np.linalg.solve(It, gt) < 1e-8
+
+    def negll(lt):
+        try:
+            return -oracle.loglik_grad_info(w.locs, w.y, w.X, w.NN, np.exp(lt), covfun)["loglik"]
+        except oracle.OracleError:
+            return np.inf
+
+    def neggrad(lt):
+        r = oracle.loglik_grad_info(w.locs, w.y, w.X, w.NN, np.exp(lt), covfun)
+        return -r["grad"] * np.exp(lt)
+
+    res = so.minimize(negll, np.log(start), jac=neggrad, method="BFGS",
+                      options={"gtol": 1e-9, "maxiter": 500})
+    assert abs(-res.fun - fit["loglik"]) <= 1e-9 * abs(fit["loglik"])
+    assert fit["loglik"] >= -res.fun - 1e-9 * abs(fit["loglik"])
