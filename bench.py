@@ -1,0 +1,330 @@
+#!/usr/bin/env python
+"""Benchmark: Vecchia loglik + gradient + Fisher information throughput (points/s).
+
+One step = one full ``vecchia_loglik_grad_info`` pass (status reset, Matern table, the
+per-observation kernel, the reduction + profile kernel) over the n = 100000, m = 30
+isotropic Matern workload (p = 3, four parameters, evaluated at the generating
+parameters), with the inputs resident in device memory when the timed region starts.
+The inputs (~17 MB) fit in L2, so L2 is flushed (a 256 MB write) before every timed step,
+outside the timed region.
+
+Reported beside the device-timed value:
+  * e2e        -- the same metric through the host-memory entry point
+                  (vecchia_loglik_grad_info_host) from pinned host buffers, with the H2D
+                  copies of the inputs and the D2H copy of the result inside the timed region;
+  * roofline   -- the per-observation kernel against the FP64 ALU peak (its algorithmic
+                  FMA count per observation x observations / its CUDA-event duration);
+  * cpu_baseline -- the FP64 CPU oracle on the host cores, on a bounded prefix sample.
+``--impl reference`` times the CPU oracle itself as the reference arm.
+Multi-GPU runs (torchrun) are independent replicas: each rank evaluates its own copy.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "Vecchia lik+grad+info points/s at m=30 (FP64 pass)"
+UNIT = "points/s"
+WORKLOAD = ("isotropic Matern n=100000 in [0,1]^2, m=30 maxmin-ordered nearest earlier "
+            "neighbours, p=3 (1, x1, x2), theta=(2.0, 0.05, 1.5, 0.05), y from a sequential "
+            "Vecchia draw with m=60")
+# FP64 peak of the GB300 derived from unit counts and clocks: each SM sub-partition
+# retires one 32-lane FP64 FMA warp-instruction per 64 cycles (2 FMA/clk/SM, measured by
+# a microbenchmark: 596 GFMA/s at ~1.96 GHz), 152 SMs, 2070 MHz maximum SM clock.
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
+
+
+def algorithmic_fma_per_point(K: int, p: int, q: int) -> float:
+    """Cholesky + forward solves of y, X + last-row derivative terms, covariance
+    evaluations excluded: (K^3-K)/6 + (2+p)K(K-1)/2 + q(K^2 + K(K-1)/2) + q(1+p)K + q(q+1)K/2."""
+    return ((K ** 3 - K) / 6 + (2 + p) * K * (K - 1) / 2 + q * (K * K + K * (K - 1) / 2)
+            + q * (1 + p) * K + q * (q + 1) * K / 2)
+
+
+def covariance_fma_per_point(K: int, covfun: int, d: int) -> float:
+    """FP64 work of the covariance and derivative entries as implemented: per off-diagonal
+    pair, the squared distance (2d + 1 ops) twice, plus three degree-12 Horner chains
+    (Matern value, rho- and nu-derivatives) and the table lookup subtraction."""
+    pairs = K * (K - 1) / 2
+    if covfun == 1:
+        return pairs * (2 * (2 * d + 1) + 3 * 13 + 2 + 6)
+    return pairs * (2 * d + 1 + 35)
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thr = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thr = threading.Thread(target=self._read, daemon=True)
+        self.thr.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thr:
+            self.thr.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_workload():
+    import workloads
+    return workloads.cfg_matern_100k()
+
+
+def cpu_oracle_rate(w, target_s: float = 12.0, nthreads: int = 0):
+    """Times the oracle on a prefix of the workload (all host cores unless nthreads > 0);
+    the prefix is sized from a short calibration run to take about target_s seconds."""
+    import oracle
+    oracle.build()
+    th = w.theta_true
+    n0 = min(w.n, 3000)
+    t0 = time.perf_counter()
+    oracle.loglik_grad_info(w.locs[:n0], w.y[:n0], w.X[:n0], w.NN[:n0], th, w.covfun,
+                            nthreads=nthreads)
+    rate0 = n0 / (time.perf_counter() - t0)
+    ns = int(min(w.n, max(n0, rate0 * target_s)))
+    t0 = time.perf_counter()
+    oracle.loglik_grad_info(w.locs[:ns], w.y[:ns], w.X[:ns], w.NN[:ns], th, w.covfun,
+                            nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    cores = nthreads if nthreads > 0 else (os.cpu_count() or 1)
+    return ns / dt, ns, dt, cores
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    w = make_workload()
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    # each step: the oracle on a bounded prefix sized so the whole run stays short
+    rate, ns, dt, _ = cpu_oracle_rate(w, target_s=4.0)
+    times = []
+    for _ in range(args.warmup):
+        oracle.loglik_grad_info(w.locs[:ns], w.y[:ns], w.X[:ns], w.NN[:ns], w.theta_true, w.covfun)
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.loglik_grad_info(w.locs[:ns], w.y[:ns], w.X[:ns], w.NN[:ns], w.theta_true, w.covfun)
+        times.append(time.perf_counter() - t0)
+    step_s = statistics.mean(times)
+    value = ns / step_s
+    sample = "first %d of %d observations (maxmin order) per step, OpenMP over observations" % (ns, w.n)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "n": w.n, "m": w.m, "p": w.p,
+                       "covfun": "matern_iso", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import paper_2407_02740_gb300 as vg
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if not os.path.exists(vg.LIB_PATH):
+        vg.build()
+    w = make_workload()
+    q = 4
+    K = w.m + 1
+    t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)  # noqa
+    locs, y, X = t(w.locs, torch.float64), t(w.y, torch.float64), t(w.X, torch.float64)
+    NN, th = t(w.NN, torch.int32), t(w.theta_true, torch.float64)
+    h = vg.Handle(local)
+    h.set_timing(True)
+    stream = torch.cuda.current_stream(dev)
+    out = torch.empty(1 + q + q * q + w.p, dtype=torch.float64, device=dev)
+    st = torch.empty(2, dtype=torch.int64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        vg.vecchia_loglik_grad_info(locs, y, X, NN, th, w.covfun, stream=stream, out=out,
+                                    status=st, handle=h)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if int(st[0].item()) != 0:
+        raise RuntimeError("pass failed with status %s" % st.cpu().numpy())
+
+    sampler = ClockSampler(local)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    step_ms, pass_ms = [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        pass_ms.append(h.last_timing()["pass"])
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    total_ms = float(sum(step_ms))
+    if ws > 1:
+        tt = torch.tensor([total_ms], dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms_per_step = total_ms / args.steps
+    value = ws * w.n * args.steps / (total_ms / 1e3)
+
+    # end to end through the host-memory entry point, pinned host buffers
+    pin = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt).pin_memory().numpy()  # noqa
+    hl, hy, hX = pin(w.locs, torch.float64), pin(w.y, torch.float64), pin(w.X, torch.float64)
+    hNN, hth = pin(w.NN, torch.int32), pin(w.theta_true, torch.float64)
+    he = vg.Handle(local)
+    for _ in range(2):
+        vg.vecchia_loglik_grad_info_host(hl, hy, hX, hNN, hth, w.covfun, handle=he)
+    e2e_s = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = vg.vecchia_loglik_grad_info_host(hl, hy, hX, hNN, hth, w.covfun, handle=he)
+        e2e_s.append(time.perf_counter() - t0)
+    e2e_total = sum(e2e_s)
+    if ws > 1:
+        tt = torch.tensor([e2e_total], dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        e2e_total = float(tt.item())
+    h2d = hl.nbytes + hy.nbytes + hX.nbytes + hNN.nbytes + hth.nbytes
+    d2h = 8 * (1 + q + q * q + w.p) + 16
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.barrier()
+        return 0
+
+    res = vg.unpack(out, q, w.p)
+    fma_pt = algorithmic_fma_per_point(K, w.p, q)
+    cov_pt = covariance_fma_per_point(K, w.covfun, w.d)
+    kern_ms = statistics.mean(pass_ms)
+    achieved = 2 * fma_pt * w.n / (kern_ms * 1e-3) / 1e9
+    achieved_cov = 2 * (fma_pt + cov_pt) * w.n / (kern_ms * 1e-3) / 1e9
+    bytes_pt = 4 * K + 8 * (w.d + 1 + w.p)
+    cpu_rate, cpu_n, cpu_s, cpu_cores = cpu_oracle_rate(w)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": w.n, "m": w.m, "p": w.p, "covfun": "matern_iso",
+                   "point": "generating parameters", "l2": "flushed (256 MB write) before each step",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "roofline": {"bound": "alu", "unit": "GFLOP/s", "achieved": achieved,
+                     "peak": FP64_PEAK_GFLOPS, "frac": achieved / FP64_PEAK_GFLOPS,
+                     "traffic": None, "kernel": "k_pass_fp64 (per-observation pass)",
+                     "kernel_ms": kern_ms, "flop_per_point": 2 * fma_pt,
+                     "achieved_incl_covariance": achieved_cov,
+                     "frac_incl_covariance": achieved_cov / FP64_PEAK_GFLOPS,
+                     "peak_note": "FP64 FMA units: 152 SMs x 2 FMA/clk x 2070 MHz",
+                     "hbm_gbs": bytes_pt * w.n / (kern_ms * 1e-3) / 1e9,
+                     "hbm_frac_of_measured": bytes_pt * w.n / (kern_ms * 1e-3) / 1e9 / 6785.9},
+        "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": cpu_cores, "kind": "oracle",
+                         "sample": "first %d of %d observations, %.1f s" % (cpu_n, w.n, cpu_s)},
+        "e2e": {"value": ws * w.n * args.steps / e2e_total, "unit": UNIT,
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": args.steps * int(vg.lib().vecchia_kernels_per_pass(w.covfun)),
+        "clocks": clocks,
+        "result": {"loglik": res["loglik"], "grad": [float(v) for v in res["grad"]]},
+    }
+    print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.barrier()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

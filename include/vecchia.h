@@ -1,0 +1,171 @@
+/*
+ * vecchia.h -- C ABI of the GB300 (sm_103a) Vecchia likelihood library.
+ *
+ * The library evaluates, on one GPU, the Vecchia-approximate Gaussian-process
+ * loglikelihood with the regression coefficients beta profiled out, its gradient and
+ * its Fisher information with respect to the covariance parameters (James & Guinness,
+ * "Implementation and Analysis of GPU Algorithms for Vecchia Approximation":
+ * Sec. 2.1 Eq. 3 for the approximation, Algorithm 1 for the per-observation sums,
+ * Sec. 3 for the profile step that turns the sums into loglik / gradient / information),
+ * and runs Fisher scoring (Eq. 4) on top of it.
+ *
+ * Conventions shared by every entry point
+ *   - Arrays are contiguous, row-major, 0-based.  Floating point arrays are FP64.
+ *   - locs    n x d   observation locations (the order defines the Vecchia ordering).
+ *   - y       n       responses.
+ *   - X       n x p   design matrix (p >= 1; a column of ones for an intercept).
+ *   - NNarray n x (m+1), int32.  Row i = [i, j_1, ..., j_k, -1, ..., -1]: column 0 is i
+ *             itself, then the k = min(i, m) (or fewer) neighbours, all < i, then -1
+ *             padding (Sec. 3: "row i containing the indices of the min(i, m+1)
+ *             observations that are closest to observation i, including i itself").
+ *             The neighbour order within a row does not change the result beyond rounding.
+ *   - covparms, in this order (all > 0; the nugget variance is sigma2 * tau2, added on the
+ *     diagonal only, as in Sec. 4.3 Eq. 5):
+ *       VEC_EXP_ISO        (sigma2, rho, tau2)       C = sigma2 exp(-|h| / rho)         Eq. 6
+ *       VEC_MATERN_ISO     (sigma2, rho, nu, tau2)   C = sigma2 2^(1-nu)/Gamma(nu) x^nu K_nu(x),
+ *                                                    x = |h| / rho, 0.05 <= nu <= 20
+ *       VEC_EXP_SPACETIME  (sigma2, rho_s, rho_t, tau2), d = 3 (lon, lat, time):
+ *                          C = sigma2 exp(-sqrt((dlon^2 + dlat^2)/rho_s^2 + dt^2/rho_t^2))
+ *   - Results: loglik (scalar), grad (q), info (q x q, row-major, symmetric), betahat (p),
+ *     where q = vecchia_nparms(covfun).  The loglikelihood includes -n/2 log(2 pi).
+ *   - Errors are returned as vec_status codes; nothing is printed, no exception crosses
+ *     the ABI, and the library never aborts the process.  vecchia_last_error() returns a
+ *     thread-local message for the last failing call on the calling thread.
+ */
+#ifndef VECCHIA_GB300_H
+#define VECCHIA_GB300_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define VECCHIA_API __attribute__((visibility("default")))
+#else
+#define VECCHIA_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    VEC_OK = 0,
+    VEC_ERR_ARG = 1,         /* invalid argument or NNarray row                          */
+    VEC_ERR_NOT_PD = 2,      /* a conditioning block is not positive definite            */
+    VEC_ERR_NONFINITE = 3,   /* a non-finite value reached the sums                      */
+    VEC_ERR_NOMEM = 4,       /* device allocation failed                                 */
+    VEC_ERR_CUDA = 5,        /* a CUDA runtime call failed                               */
+    VEC_ERR_TIMEOUT = 6,     /* a bounded device wait gave up                            */
+    VEC_ERR_UNSUPPORTED = 7  /* size or option outside what this build supports          */
+} vec_status;
+
+typedef enum { VEC_EXP_ISO = 0, VEC_MATERN_ISO = 1, VEC_EXP_SPACETIME = 2 } vec_covfun;
+
+/* VEC_FP64: every step in FP64.  VEC_MIXED: covariance assembly, Cholesky trailing
+ * updates and solves in FP32; pivots, per-observation last-row terms, the sums over
+ * observations, the profile step and the Fisher step in FP64. */
+typedef enum { VEC_FP64 = 0, VEC_MIXED = 1 } vec_precision;
+
+/* Opaque context bound to one CUDA device.  It owns the library's device scratch
+ * (per-block partial sums, the Matern coefficient table, fit state) and a CUDA stream
+ * used by the synchronous entry points.  A handle may be used by one host thread at a
+ * time; calls on one handle must not overlap on the GPU. */
+typedef struct vec_handle_s* vec_handle;
+
+/* Creates a handle on `device` (a CUDA ordinal).  Returns VEC_ERR_CUDA if the device
+ * cannot be used.  *out is set to NULL on failure. */
+VECCHIA_API vec_status vecchia_create(vec_handle* out, int device);
+
+/* Frees the handle and its device scratch after synchronising its work. NULL is a no-op. */
+VECCHIA_API vec_status vecchia_destroy(vec_handle h);
+
+/* Message for the last error raised on the calling thread ("" if none). */
+VECCHIA_API const char* vecchia_last_error(void);
+
+/* Number of covariance parameters q of a covariance function, or -1 if unknown. */
+VECCHIA_API int vecchia_nparms(vec_covfun covfun);
+
+/* Largest m supported by this build (the conditioning block is (m+1) x (m+1)). */
+VECCHIA_API int vecchia_max_m(void);
+
+/* Lanes of a warp that work on one observation in the pass kernel: 1, 2, 4, 8, 16 or 32,
+ * or 0 to let the library choose from the block size (the default).  A choice whose
+ * shared-memory footprint does not fit makes later passes return VEC_ERR_UNSUPPORTED. */
+VECCHIA_API vec_status vecchia_set_lanes(vec_handle h, int lanes);
+
+/* Tracing.  With timing enabled, every pass records CUDA events (on the pass's stream)
+ * around its three phases: setup (status reset, Matern table), the per-observation kernel,
+ * and the reduction + profile kernel.  vecchia_last_timing waits for the last traced pass
+ * and returns the three durations in milliseconds (any pointer may be NULL); it returns
+ * VEC_ERR_ARG if no traced pass has run.  Timing adds two event records per phase. */
+VECCHIA_API vec_status vecchia_set_timing(vec_handle h, int enable);
+VECCHIA_API vec_status vecchia_last_timing(vec_handle h, float* ms_setup, float* ms_pass,
+                                           float* ms_profile);
+
+/* Number of kernels one vecchia_loglik_grad_info call launches for this covariance
+ * function (used to count launches in benchmarks). */
+VECCHIA_API int vecchia_kernels_per_pass(vec_covfun covfun);
+
+/*
+ * vecchia_loglik_grad_info -- one Vecchia likelihood pass on device-resident data.
+ *
+ * Algorithm 1 (all n observations, including the first m, which condition on fewer
+ * neighbours) followed by the profile step of Sec. 3:
+ *   betahat = XSX^-1 ySX,
+ *   loglik  = -n/2 log(2 pi) - 1/2 logdet - 1/2 (ySy - ySX' betahat),
+ *   grad_j  = -1/2 (dlogdet_j + dySy_j - 2 betahat' dySX_j + betahat' dXSX_j betahat),
+ *   info    = sum over observations of I(block) - I(neighbours).
+ *
+ * Pointers locs, y, X, NNarray, covparms: DEVICE memory on the handle's device, caller
+ * owned, read only.  out: DEVICE memory, caller owned, length 1 + q + q*q + p doubles,
+ * written as [loglik, grad[q], info[q*q], betahat[p]].  dev_status: DEVICE memory,
+ * caller owned, 2 int64 values written as [vec_status, first failing observation or -1].
+ * The call is asynchronous on `stream` (a cudaStream_t; NULL = legacy default stream):
+ * it returns after enqueuing.  The return value reports argument errors (VEC_ERR_ARG,
+ * VEC_ERR_UNSUPPORTED) and launch failures (VEC_ERR_CUDA); errors found by the kernels
+ * (bad NNarray row, covariance parameter out of range, block not positive definite,
+ * non-finite sums) are reported in dev_status once the stream reaches that point, and
+ * then out holds NaNs.  Requires 1 <= n < 2^31, 1 <= d <= 3 (d = 3 for the space-time
+ * covariance), 1 <= p <= 8, 0 <= m <= vecchia_max_m().
+ */
+VECCHIA_API vec_status vecchia_loglik_grad_info(vec_handle h, const double* locs, const double* y,
+                                    const double* X, const int32_t* NNarray, int64_t n,
+                                    int d, int p, int m, const double* covparms,
+                                    vec_covfun covfun, vec_precision prec, void* stream,
+                                    double* out, int64_t* dev_status);
+
+/*
+ * vecchia_loglik_grad_info_host -- the same pass end to end from HOST memory.
+ *
+ * All pointers are HOST memory, caller owned.  Inputs are copied to device buffers owned
+ * by the handle (grown on demand, kept between calls), the pass runs on the handle's
+ * stream, and the results are copied back before the call returns.  Outputs: *loglik,
+ * grad[q], info[q*q], betahat[p]; *bad_index = first observation whose block is not
+ * positive definite, or -1 (may be NULL).  Returns the kernel-side status as well
+ * (VEC_ERR_NOT_PD, VEC_ERR_ARG for a bad NNarray row, ...).
+ */
+VECCHIA_API vec_status vecchia_loglik_grad_info_host(vec_handle h, const double* locs, const double* y,
+                                         const double* X, const int32_t* NNarray, int64_t n,
+                                         int d, int p, int m, const double* covparms,
+                                         vec_covfun covfun, vec_precision prec,
+                                         double* loglik, double* grad, double* info,
+                                         double* betahat, int64_t* bad_index);
+
+/*
+ * vecchia_covariance_pairs -- the library's device covariance functions on explicit pairs.
+ *
+ * For each pair k: C[k] = C(la[k], lb[k]; covparms) including the nugget sigma2 tau2 when
+ * same[k] != 0 (the two entries are the same observation), and dC[k*q + j] = dC/dtheta_j.
+ * These are the functions assembled in Algorithm 1 (Sec. 4.3 Eq. 6 and the Matern family);
+ * for the Matern family the call first rebuilds the handle's coefficient table for nu.
+ * Pointers are DEVICE memory, caller owned: covparms (q), la and lb (npairs x d), same
+ * (npairs int32), C (npairs), dC (npairs x q).  Asynchronous on `stream`.
+ */
+VECCHIA_API vec_status vecchia_covariance_pairs(vec_handle h, vec_covfun covfun, const double* covparms,
+                                    int d, int64_t npairs, const double* la, const double* lb,
+                                    const int32_t* same, double* C, double* dC, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VECCHIA_GB300_H */

@@ -1,0 +1,245 @@
+"""GB300 (sm_103a) Vecchia likelihood library -- Python binding.
+
+A thin ctypes layer over the C ABI in ``include/vecchia.h`` (library
+``libvecchia_gb300.so``, built by ``builder.py``).  It only marshals arguments: every
+step of the likelihood pass runs in the library's CUDA kernels.  PyTorch supplies
+device memory and streams.  There is no CPU fallback: if the library is missing, every
+call raises.
+
+Entry points (same names as the C ABI):
+  * ``vecchia_loglik_grad_info``       -- device-resident pass, asynchronous on a stream
+  * ``vecchia_loglik_grad_info_host``  -- end-to-end pass from host (numpy) arrays
+  * ``vecchia_covariance_pairs``       -- the device covariance functions on explicit pairs
+Covariance functions (parameter order): EXP_ISO (sigma2, rho, tau2), MATERN_ISO (sigma2,
+rho, nu, tau2), EXP_SPACETIME (sigma2, rho_s, rho_t, tau2); nugget = sigma2 * tau2.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvecchia_gb300.so")
+
+EXP_ISO, MATERN_ISO, EXP_SPACETIME = 0, 1, 2
+FP64, MIXED = 0, 1
+NPARMS = {EXP_ISO: 3, MATERN_ISO: 4, EXP_SPACETIME: 4}
+STATUS = {0: "VEC_OK", 1: "VEC_ERR_ARG", 2: "VEC_ERR_NOT_PD", 3: "VEC_ERR_NONFINITE",
+          4: "VEC_ERR_NOMEM", 5: "VEC_ERR_CUDA", 6: "VEC_ERR_TIMEOUT", 7: "VEC_ERR_UNSUPPORTED"}
+_PREC = {"fp64": FP64, "mixed": MIXED, FP64: FP64, MIXED: MIXED}
+
+
+class VecchiaError(RuntimeError):
+    def __init__(self, code: int, msg: str, bad_index: int = -1):
+        super().__init__("%s: %s" % (STATUS.get(code, "?"), msg))
+        self.code = code
+        self.bad_index = bad_index
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def build(force: bool = False) -> str:
+    """Compiles the CUDA library in-tree (nvcc, sm_103a) and returns its path."""
+    from . import builder
+    return builder.build(force=force)
+
+
+def lib():
+    """Loads the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("the CUDA library %s is not built; run "
+                               "paper_2407_02740_gb300.build() (no CPU fallback exists)" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        P, i64, ci = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+        L.vecchia_create.argtypes = [ctypes.POINTER(P), ci]
+        L.vecchia_destroy.argtypes = [P]
+        L.vecchia_last_error.restype = ctypes.c_char_p
+        L.vecchia_nparms.argtypes = [ci]
+        L.vecchia_set_lanes.argtypes = [P, ci]
+        L.vecchia_set_timing.argtypes = [P, ci]
+        L.vecchia_last_timing.argtypes = [P, P, P, P]
+        L.vecchia_kernels_per_pass.argtypes = [ci]
+        L.vecchia_loglik_grad_info.argtypes = [P, P, P, P, P, i64, ci, ci, ci, P, ci, ci, P, P, P]
+        L.vecchia_loglik_grad_info_host.argtypes = [P, P, P, P, P, i64, ci, ci, ci, P, ci, ci,
+                                                    P, P, P, P, P]
+        L.vecchia_covariance_pairs.argtypes = [P, ci, P, ci, i64, P, P, P, P, P, P]
+        for f in (L.vecchia_create, L.vecchia_destroy, L.vecchia_set_lanes,
+                  L.vecchia_loglik_grad_info, L.vecchia_loglik_grad_info_host,
+                  L.vecchia_covariance_pairs, L.vecchia_nparms, L.vecchia_max_m,
+                  L.vecchia_set_timing, L.vecchia_last_timing, L.vecchia_kernels_per_pass):
+            f.restype = ci
+        _lib = L
+    return _lib
+
+
+def _check(code: int, bad_index: int = -1):
+    if code != 0:
+        raise VecchiaError(code, lib().vecchia_last_error().decode(), bad_index)
+
+
+class Handle:
+    """Owns a vec_handle (device scratch + stream) on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self._h = ctypes.c_void_p()
+        _check(lib().vecchia_create(ctypes.byref(self._h), device))
+        self.device = device
+
+    @property
+    def ptr(self):
+        return self._h
+
+    def set_lanes(self, lanes: int):
+        _check(lib().vecchia_set_lanes(self._h, lanes))
+
+    def set_timing(self, enable: bool = True):
+        _check(lib().vecchia_set_timing(self._h, 1 if enable else 0))
+
+    def last_timing(self) -> dict:
+        """Durations (ms) of the last traced pass: setup, pass kernel, profile kernel."""
+        a, b, c = ctypes.c_float(), ctypes.c_float(), ctypes.c_float()
+        _check(lib().vecchia_last_timing(self._h, ctypes.byref(a), ctypes.byref(b),
+                                         ctypes.byref(c)))
+        return {"setup": a.value, "pass": b.value, "profile": c.value}
+
+    def close(self):
+        if self._h:
+            lib().vecchia_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_handles: dict = {}
+
+
+def default_handle(device: int = 0) -> Handle:
+    h = _handles.get(device)
+    if h is None:
+        h = _handles[device] = Handle(device)
+    return h
+
+
+def _dptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _dev_tensor_check(t, dtype, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype or not t.is_contiguous():
+        raise TypeError("%s must be contiguous %s" % (name, dtype))
+
+
+def vecchia_loglik_grad_info(locs, y, X, NNarray, covparms, covfun: int, prec="fp64",
+                             stream=None, out=None, status=None, handle: Handle | None = None):
+    """Device-resident pass (asynchronous).  Tensors must be CUDA, contiguous: locs (n, d)
+    float64, y (n,) float64, X (n, p) float64, NNarray (n, m+1) int32, covparms (q,) float64.
+    Returns (out, status): out = [loglik, grad(q), info(q*q), betahat(p)] float64 and
+    status = [code, first failing observation] int64, both on the device."""
+    import torch
+    for t, dt, nm in ((locs, torch.float64, "locs"), (y, torch.float64, "y"),
+                      (X, torch.float64, "X"), (NNarray, torch.int32, "NNarray"),
+                      (covparms, torch.float64, "covparms")):
+        _dev_tensor_check(t, dt, nm)
+    n, d = locs.shape
+    p = X.shape[1]
+    m = NNarray.shape[1] - 1
+    q = NPARMS[covfun]
+    dev = locs.device
+    if handle is None:
+        handle = default_handle(dev.index if dev.index is not None else 0)
+    if out is None:
+        out = torch.empty(1 + q + q * q + p, dtype=torch.float64, device=dev)
+    if status is None:
+        status = torch.empty(2, dtype=torch.int64, device=dev)
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    sptr = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check(lib().vecchia_loglik_grad_info(handle.ptr, _dptr(locs), _dptr(y), _dptr(X),
+                                          _dptr(NNarray), n, d, p, m, _dptr(covparms), covfun,
+                                          _PREC[prec], sptr, _dptr(out), _dptr(status)))
+    return out, status
+
+
+def unpack(out, q: int, p: int) -> dict:
+    """Splits a result vector into loglik, grad, info, betahat (numpy)."""
+    o = out.detach().cpu().numpy() if hasattr(out, "detach") else np.asarray(out)
+    return {"loglik": float(o[0]), "grad": o[1:1 + q].copy(),
+            "info": o[1 + q:1 + q + q * q].reshape(q, q).copy(),
+            "betahat": o[1 + q + q * q:1 + q + q * q + p].copy()}
+
+
+def _host(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def vecchia_loglik_grad_info_host(locs, y, X, NNarray, covparms, covfun: int, prec="fp64",
+                                  handle: Handle | None = None, device: int = 0) -> dict:
+    """End-to-end pass from host arrays (copies in, runs, copies out, synchronises)."""
+    locs = _host(locs, np.float64)
+    if locs.ndim == 1:
+        locs = locs[:, None]
+    y = _host(y, np.float64)
+    X = _host(X, np.float64)
+    if X.ndim == 1:
+        X = X[:, None]
+    NN = _host(NNarray, np.int32)
+    cp = _host(covparms, np.float64)
+    n, d = locs.shape
+    p = X.shape[1]
+    m = NN.shape[1] - 1
+    q = NPARMS[covfun]
+    if handle is None:
+        handle = default_handle(device)
+    ll = ctypes.c_double()
+    grad = np.empty(q)
+    info = np.empty((q, q))
+    beta = np.empty(p)
+    bad = ctypes.c_int64(-1)
+    P = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    code = lib().vecchia_loglik_grad_info_host(handle.ptr, P(locs), P(y), P(X), P(NN), n, d, p,
+                                               m, P(cp), covfun, _PREC[prec], ctypes.byref(ll),
+                                               P(grad), P(info), P(beta), ctypes.byref(bad))
+    _check(code, bad.value)
+    return {"loglik": ll.value, "grad": grad, "info": info, "betahat": beta,
+            "bad_index": bad.value}
+
+
+def vecchia_covariance_pairs(covfun: int, covparms, la, lb, same, stream=None,
+                             handle: Handle | None = None):
+    """Device covariance C (npairs,) and dC (npairs, q) for CUDA tensors la, lb (npairs, d)."""
+    import torch
+    _dev_tensor_check(covparms, torch.float64, "covparms")
+    _dev_tensor_check(la, torch.float64, "la")
+    _dev_tensor_check(lb, torch.float64, "lb")
+    _dev_tensor_check(same, torch.int32, "same")
+    npairs, d = la.shape
+    q = NPARMS[covfun]
+    dev = la.device
+    if handle is None:
+        handle = default_handle(dev.index if dev.index is not None else 0)
+    C = torch.empty(npairs, dtype=torch.float64, device=dev)
+    dC = torch.empty(npairs, q, dtype=torch.float64, device=dev)
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    _check(lib().vecchia_covariance_pairs(handle.ptr, covfun, _dptr(covparms), d, npairs,
+                                          _dptr(la), _dptr(lb), _dptr(same), _dptr(C), _dptr(dC),
+                                          ctypes.c_void_p(stream.cuda_stream)))
+    return C, dC

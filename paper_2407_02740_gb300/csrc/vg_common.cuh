@@ -1,0 +1,94 @@
+// vg_common.cuh -- device helpers shared by the Vecchia kernels (CUDA library side).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace vg {
+
+// status codes written by kernels (same numbering as vec_status in include/vecchia.h)
+enum : int { ST_OK = 0, ST_ARG = 1, ST_NOT_PD = 2, ST_NONFINITE = 3 };
+
+enum : int { COV_EXP = 0, COV_MATERN = 1, COV_ST = 2 };
+
+constexpr int KMAX = 81;   // largest conditioning block (m <= 80)
+constexpr int PMAX = 8;    // largest number of regression columns
+constexpr int DMAX = 3;    // largest location dimension
+
+__host__ __device__ constexpr int nparms(int cov) { return cov == COV_EXP ? 3 : 4; }
+// number of covariance parameters whose derivative matrix needs a per-pair evaluation
+// (sigma2 and tau2 are handled in closed form)
+__host__ __device__ constexpr int npair_derivs(int cov) { return cov == COV_EXP ? 1 : 2; }
+
+// Per-observation record (the Algorithm 1 sums) in packed symmetric storage.
+//   [logdet, ySy, XSX (p(p+1)/2), ySX (p),
+//    for each derivative parameter j in 0..Q-1 (theta index j+1):
+//       dlogdet_j, dySy_j, dySX_j (p), dXSX_j (p(p+1)/2),
+//    info_jl for 0 <= j <= l < Q]
+// The sigma2 entries are not accumulated: with the relative nugget, dSigma/dsigma2 =
+// Sigma/sigma2, so every sigma2 term follows from the totals (see the profile kernel).
+struct RecLayout {
+    int p, Q, P2, per_j, base_j, base_info, nstat;
+    __host__ __device__ void init(int p_, int Q_) {
+        p = p_; Q = Q_; P2 = p * (p + 1) / 2;
+        per_j = 2 + p + P2;
+        base_j = 2 + P2 + p;
+        base_info = base_j + Q * per_j;
+        nstat = base_info + Q * (Q + 1) / 2;
+    }
+};
+
+// 1/sqrt(v) from an FP32 seed and two Newton steps.  Each step forms the residual
+// r = 1 - v y^2 in FP64 and applies the small correction y r / 2 in FP32; the result
+// carries FP64 accuracy (the seed error ~1e-7 is squared twice).  Values outside the
+// FP32 normal range fall back to the FP64 library routine.
+__device__ __forceinline__ double rsqrt_newton(double v) {
+    float vf = (float)v;
+    if (!(vf > 1e-36f && vf < 1e36f)) return rsqrt(v);
+    double y = (double)rsqrtf(vf);
+    double t = v * y;
+    double r = fma(-t, y, 1.0);
+    y = y + (double)(0.5f * (float)y * (float)r);
+    t = v * y;
+    r = fma(-t, y, 1.0);
+    y = y + (double)(0.5f * (float)y * (float)r);
+    return y;
+}
+
+// digamma(x), x > 0: shift upward with psi(x) = psi(x+1) - 1/x until x >= 12, then the
+// asymptotic expansion psi(z) = ln z - 1/(2z) - sum_k B_2k / (2k z^2k).
+__device__ inline double dev_digamma(double x) {
+    double acc = 0.0;
+    while (x < 12.0) { acc -= 1.0 / x; x += 1.0; }
+    double iz = 1.0 / x, z2 = iz * iz;
+    double s = z2 * (1.0 / 12.0 - z2 * (1.0 / 120.0 - z2 * (1.0 / 252.0 - z2 * (1.0 / 240.0
+               - z2 * (1.0 / 132.0 - z2 * (691.0 / 32760.0))))));
+    return acc + log(x) - 0.5 * iz - s;
+}
+
+// Arguments of the pass kernel (K1).
+struct PassArgs {
+    const double* __restrict__ locs;
+    const double* __restrict__ y;
+    const double* __restrict__ X;
+    const int32_t* __restrict__ NN;
+    const double* __restrict__ covparms;
+    const double* __restrict__ mtab;   // Matern table (global), or nullptr
+    double* __restrict__ partials;     // [gridDim.x][nstat]
+    int* status;                       // [0] status code
+    long long* bad;                    // first failing observation
+    long long n;
+    int d, p, m;
+    int nstat, nv;
+    int slot_stride;                   // doubles per slot
+    int acc_per_lane;                  // ceil(nstat / L)
+    int tab_in_smem;                   // copy the Matern table into shared memory
+};
+
+// Device-side error reporting: the first error code wins; the smallest failing
+// observation index is kept.
+__device__ __forceinline__ void report(int* status, long long* bad, int code, long long i) {
+    atomicCAS(status, 0, code);
+    if (i >= 0) atomicMin(bad, i);
+}
+
+}  // namespace vg

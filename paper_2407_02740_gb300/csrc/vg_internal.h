@@ -1,0 +1,41 @@
+// vg_internal.h -- host-side interface between the C ABI layer and the kernel launchers.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "vg_common.cuh"
+
+namespace vg {
+
+
+struct PassPlan {
+    int L;             // lanes per observation
+    int threads;       // threads per block
+    int grid;          // persistent grid (blocks)
+    size_t smem;       // dynamic shared memory per block
+    int tab_smem;      // Matern table staged in shared memory
+    int nstat;         // doubles per partial record
+    int nv;            // per-observation value count
+    int slot_stride;   // doubles per shared-memory slot
+    int acc_per_lane;  // accumulator doubles per thread
+};
+
+// Chooses the lanes-per-observation mapping that fits shared memory (or the forced one).
+// Returns 0 on success, -1 if no mapping fits, -2 on a CUDA error.
+int plan_pass(int cov, int m, int d, int p, int nsm, int force_L, PassPlan* plan);
+size_t pass_smem_bytes(int cov, int m, int d, int p, int L, int threads, bool tab_smem);
+
+cudaError_t launch_pass(int cov, const PassPlan& plan, const PassArgs& args, cudaStream_t st);
+cudaError_t launch_init_status(int* status, long long* bad, cudaStream_t st);
+cudaError_t launch_mtab_build(const double* covparms, double* tab, cudaStream_t st);
+cudaError_t launch_profile(const double* partials, int nblk, int nstat, int p, int cov,
+                           long long n, const double* covparms, const int* status,
+                           const long long* bad, double* out, long long* dev_status,
+                           cudaStream_t st);
+cudaError_t launch_cov_pairs(int cov, const double* covparms, const double* tab, int d,
+                             long long npairs, const double* la, const double* lb,
+                             const int32_t* same, double* C, double* dC, cudaStream_t st);
+int mtab_doubles();
+
+}  // namespace vg

@@ -1,0 +1,322 @@
+// vg_kernels.cu -- kernel instantiations and launch planning for the Vecchia pass.
+//
+//   k_init_status   resets the device status word and failing-index slot
+//   k_mtab_build    per-pass Matern coefficient table (vg_matern.cuh)
+//   k_pass_fp64     K1, the fused per-observation pass (vg_pass.cuh)
+//   k_profile       K2: fixed-order sum of the per-block partial records, then the profile
+//                   step of Sec. 3 (betahat, loglik, gradient, Fisher information)
+//   k_cov_pairs     covariance and derivatives for explicit location pairs (the same
+//                   device covariance code, exposed for testing)
+#include <climits>
+#include <cstdio>
+
+#include "vg_internal.h"
+#include "vg_pass.cuh"
+
+namespace vg {
+
+__global__ void k_init_status(int* status, long long* bad) {
+    status[0] = 0;
+    bad[0] = LLONG_MAX;
+}
+
+// Profile step.  tot = sum over blocks of the partial records; the sigma2 entries are
+// formed here from the totals (dSigma/dsigma2 = Sigma/sigma2 with the relative nugget):
+//   dlogdet_0 = n/sigma2, dySy_0 = -ySy/sigma2, dySX_0 = -ySX/sigma2, dXSX_0 = -XSX/sigma2,
+//   info_00 = n/(2 sigma2^2), info_0l = dlogdet_l/(2 sigma2).
+__global__ void k_profile(const double* __restrict__ partials, int nblk, int nstat, int p,
+                          int cov, long long n, const double* __restrict__ covparms,
+                          const int* status, const long long* bad, double* out,
+                          long long* dev_status) {
+    __shared__ double tot[256];
+    const int tid = threadIdx.x;
+    for (int t = tid; t < nstat; t += blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < nblk; ++b) s += partials[(size_t)b * nstat + t];
+        tot[t] = s;
+    }
+    __syncthreads();
+    if (tid != 0) return;
+    const int q = nparms(cov), Q = q - 1;
+    RecLayout RL;
+    RL.init(p, Q);
+    int st = status[0];
+    const int nout = 1 + q + q * q + p;
+    double XSX[PMAX * PMAX], ySX[PMAX], dySX[4][PMAX], dXSX[4][PMAX * PMAX];
+    double dlogdet[4], dySy[4], info[16];
+    const double logdet = tot[0], ySy = tot[1];
+    {
+        int u = 2;
+        for (int a = 0; a < p; ++a)
+            for (int b = a; b < p; ++b) { XSX[a * p + b] = XSX[b * p + a] = tot[u]; ++u; }
+        for (int a = 0; a < p; ++a) ySX[a] = tot[u++];
+    }
+    for (int j = 0; j < Q; ++j) {
+        int u = RL.base_j + j * RL.per_j;
+        dlogdet[j + 1] = tot[u++];
+        dySy[j + 1] = tot[u++];
+        for (int a = 0; a < p; ++a) dySX[j + 1][a] = tot[u++];
+        for (int a = 0; a < p; ++a)
+            for (int b = a; b < p; ++b) {
+                dXSX[j + 1][a * p + b] = dXSX[j + 1][b * p + a] = tot[u];
+                ++u;
+            }
+    }
+    {
+        int u = RL.base_info;
+        for (int j = 0; j < Q; ++j)
+            for (int l = j; l < Q; ++l) {
+                info[(j + 1) * q + (l + 1)] = info[(l + 1) * q + (j + 1)] = tot[u];
+                ++u;
+            }
+    }
+    const double s2 = covparms[0];
+    const double nd = (double)n;
+    dlogdet[0] = nd / s2;
+    dySy[0] = -ySy / s2;
+    for (int a = 0; a < p; ++a) dySX[0][a] = -ySX[a] / s2;
+    for (int a = 0; a < p * p; ++a) dXSX[0][a] = -XSX[a] / s2;
+    info[0] = nd / (2.0 * s2 * s2);
+    for (int l = 1; l < q; ++l) info[l] = info[l * q] = dlogdet[l] / (2.0 * s2);
+
+    // betahat = XSX^-1 ySX by Cholesky
+    double Lc[PMAX * PMAX], z[PMAX], beta[PMAX];
+    bool pd = true;
+    for (int c = 0; c < p && pd; ++c) {
+        double v = XSX[c * p + c];
+        for (int s = 0; s < c; ++s) v -= Lc[c * p + s] * Lc[c * p + s];
+        if (!(v > 0.0)) { pd = false; break; }
+        Lc[c * p + c] = sqrt(v);
+        for (int r = c + 1; r < p; ++r) {
+            double w = XSX[r * p + c];
+            for (int s = 0; s < c; ++s) w -= Lc[r * p + s] * Lc[c * p + s];
+            Lc[r * p + c] = w / Lc[c * p + c];
+        }
+    }
+    if (pd) {
+        for (int a = 0; a < p; ++a) {
+            double w = ySX[a];
+            for (int s = 0; s < a; ++s) w -= Lc[a * p + s] * z[s];
+            z[a] = w / Lc[a * p + a];
+        }
+        for (int a = p - 1; a >= 0; --a) {
+            double w = z[a];
+            for (int r = a + 1; r < p; ++r) w -= Lc[r * p + a] * beta[r];
+            beta[a] = w / Lc[a * p + a];
+        }
+    }
+    double quad = ySy;
+    for (int a = 0; a < p; ++a) quad -= ySX[a] * beta[a];
+    const double LOG2PI = 1.8378770664093454836;
+    out[0] = -0.5 * nd * LOG2PI - 0.5 * logdet - 0.5 * quad;
+    for (int J = 0; J < q; ++J) {
+        double t = dlogdet[J] + dySy[J];
+        for (int a = 0; a < p; ++a) t -= 2.0 * beta[a] * dySX[J][a];
+        for (int a = 0; a < p; ++a)
+            for (int b = 0; b < p; ++b) t += beta[a] * dXSX[J][a * p + b] * beta[b];
+        out[1 + J] = -0.5 * t;
+    }
+    for (int t = 0; t < q * q; ++t) out[1 + q + t] = info[t];
+    for (int a = 0; a < p; ++a) out[1 + q + q * q + a] = beta[a];
+    if (st == 0) {
+        if (!pd) st = ST_NONFINITE;
+        for (int t = 0; t < nout; ++t)
+            if (!isfinite(out[t])) st = ST_NONFINITE;
+    }
+    if (st != 0)
+        for (int t = 0; t < nout; ++t) out[t] = __longlong_as_double(0x7ff8000000000000ll);
+    dev_status[0] = st;
+    dev_status[1] = (bad[0] == LLONG_MAX) ? -1 : bad[0];
+}
+
+// Covariance C and its q theta-derivatives for npairs location pairs (AoS, d each).
+template <int COV>
+__global__ void k_cov_pairs(const double* __restrict__ covparms, const double* __restrict__ tab,
+                            int d, long long npairs, const double* __restrict__ la,
+                            const double* __restrict__ lb, const int32_t* __restrict__ same,
+                            double* __restrict__ C, double* __restrict__ dC) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= npairs) return;
+    const int q = nparms(COV);
+    const double* th = covparms;
+    const double s2 = th[0], tau2 = th[q - 1];
+    const double* a = la + i * d;
+    const double* b = lb + i * d;
+    double out[4] = {0.0, 0.0, 0.0, 0.0};
+    double c = 0.0;
+    if (COV == COV_EXP) {
+        double s = 0.0;
+        for (int k = 0; k < d; ++k) { double t = a[k] - b[k]; s = fma(t, t, s); }
+        double x = sqrt(s) / th[1];
+        double e = exp(-x);
+        c = s2 * e;
+        out[0] = e;
+        out[1] = s2 * e * x / th[1];
+    } else if (COV == COV_MATERN) {
+        double s = 0.0;
+        for (int k = 0; k < d; ++k) { double t = a[k] - b[k]; s = fma(t, t, s); }
+        s /= th[1] * th[1];
+        const double nu = th[2], psi = dev_digamma(nu), lg = lgamma(nu);
+        double F0 = matern_F0(tab, s, nu, psi, lg), F1, F2;
+        matern_F12(tab, s, nu, psi, lg, F1, F2);
+        c = s2 * F0;
+        out[0] = F0;
+        out[1] = s2 * F1 / th[1];
+        out[2] = s2 * F2;
+    } else {
+        double t0 = a[0] - b[0], t1 = a[1] - b[1], t2 = a[2] - b[2];
+        double us = fma(t0, t0, t1 * t1), ut = t2 * t2;
+        double D = sqrt(us / (th[1] * th[1]) + ut / (th[2] * th[2]));
+        double e = exp(-D);
+        c = s2 * e;
+        out[0] = e;
+        if (D > 0.0) {
+            out[1] = s2 * e / D * us / (th[1] * th[1] * th[1]);
+            out[2] = s2 * e / D * ut / (th[2] * th[2] * th[2]);
+        }
+    }
+    if (same[i]) {
+        c += s2 * tau2;
+        out[0] += tau2;
+        out[q - 1] = s2;
+    }
+    C[i] = c;
+    for (int j = 0; j < q; ++j) dC[i * q + j] = out[j];
+}
+
+// ----------------------------------------------------------------------------------------
+// Launch planning
+// ----------------------------------------------------------------------------------------
+static int nv_of(int p, int Q) { return 4 + p + Q * (3 + p) + Q * (Q + 1) / 2; }
+
+template <int COV, int L>
+static const void* pass_kernel_ptr() {
+    return reinterpret_cast<const void*>(&k_pass_fp64<COV, L>);
+}
+
+template <int COV>
+static const void* pass_kernel_for(int L) {
+    switch (L) {
+    case 1: return pass_kernel_ptr<COV, 1>();
+    case 2: return pass_kernel_ptr<COV, 2>();
+    case 4: return pass_kernel_ptr<COV, 4>();
+    case 8: return pass_kernel_ptr<COV, 8>();
+    case 16: return pass_kernel_ptr<COV, 16>();
+    case 32: return pass_kernel_ptr<COV, 32>();
+    default: return nullptr;
+    }
+}
+
+static const void* pass_kernel(int cov, int L) {
+    switch (cov) {
+    case COV_EXP: return pass_kernel_for<COV_EXP>(L);
+    case COV_MATERN: return pass_kernel_for<COV_MATERN>(L);
+    case COV_ST: return pass_kernel_for<COV_ST>(L);
+    default: return nullptr;
+    }
+}
+
+size_t pass_smem_bytes(int cov, int m, int d, int p, int L, int threads, bool tab_smem) {
+    const int Q = npair_derivs(cov) + 1;
+    RecLayout RL;
+    RL.init(p, Q);
+    const int nv = nv_of(p, Q);
+    SlotLayout SL;
+    SL.init(m, d, p, cov, nv);
+    const int ngrp = threads / L;
+    const int acc_per_lane = (RL.nstat + L - 1) / L;
+    size_t dbl = (size_t)(tab_smem ? MT_DOUBLES : 0) + (RL.nstat + 1) / 2 +
+                 (size_t)threads * acc_per_lane + (size_t)ngrp * SL.total;
+    size_t ints = (size_t)ngrp * (m + 1);
+    return dbl * sizeof(double) + ints * sizeof(int);
+}
+
+int plan_pass(int cov, int m, int d, int p, int nsm, int force_L, PassPlan* plan) {
+    const int threads = 128;
+    const size_t budget = 220 * 1024;
+    int chosen = -1;
+    bool tab = false;
+    for (int L = 1; L <= 32; L *= 2) {
+        if (force_L > 0 && L != force_L) continue;
+        bool t = (cov == COV_MATERN);
+        size_t b = pass_smem_bytes(cov, m, d, p, L, threads, t);
+        if (b > budget && t) { t = false; b = pass_smem_bytes(cov, m, d, p, L, threads, t); }
+        if (b <= budget) { chosen = L; tab = t; break; }
+    }
+    if (chosen < 0) return -1;
+    const int Q = npair_derivs(cov) + 1;
+    RecLayout RL;
+    RL.init(p, Q);
+    plan->L = chosen;
+    plan->threads = threads;
+    plan->tab_smem = tab ? 1 : 0;
+    plan->nstat = RL.nstat;
+    plan->nv = nv_of(p, Q);
+    SlotLayout SL;
+    SL.init(m, d, p, cov, plan->nv);
+    plan->slot_stride = SL.total;
+    plan->acc_per_lane = (RL.nstat + chosen - 1) / chosen;
+    plan->smem = pass_smem_bytes(cov, m, d, p, chosen, threads, tab);
+    const void* fn = pass_kernel(cov, chosen);
+    if (!fn) return -1;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan->smem) !=
+        cudaSuccess)
+        return -2;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, plan->smem) !=
+            cudaSuccess || per_sm < 1)
+        return -2;
+    plan->grid = nsm * per_sm;
+    return 0;
+}
+
+cudaError_t launch_pass(int cov, const PassPlan& plan, const PassArgs& args, cudaStream_t st) {
+    const void* fn = pass_kernel(cov, plan.L);
+    if (!fn) return cudaErrorInvalidValue;
+    PassArgs a = args;
+    void* params[] = {&a};
+    return cudaLaunchKernel(fn, dim3(plan.grid), dim3(plan.threads), params, plan.smem, st);
+}
+
+cudaError_t launch_init_status(int* status, long long* bad, cudaStream_t st) {
+    k_init_status<<<1, 1, 0, st>>>(status, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mtab_build(const double* covparms, double* tab, cudaStream_t st) {
+    k_mtab_build<<<MT_NINT, 32, 0, st>>>(covparms, tab);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_profile(const double* partials, int nblk, int nstat, int p, int cov,
+                           long long n, const double* covparms, const int* status,
+                           const long long* bad, double* out, long long* dev_status,
+                           cudaStream_t st) {
+    k_profile<<<1, 256, 0, st>>>(partials, nblk, nstat, p, cov, n, covparms, status, bad, out,
+                                 dev_status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cov_pairs(int cov, const double* covparms, const double* tab, int d,
+                             long long npairs, const double* la, const double* lb,
+                             const int32_t* same, double* C, double* dC, cudaStream_t st) {
+    if (npairs <= 0) return cudaSuccess;
+    const int tpb = 128;
+    const unsigned blocks = (unsigned)((npairs + tpb - 1) / tpb);
+    switch (cov) {
+    case COV_EXP:
+        k_cov_pairs<COV_EXP><<<blocks, tpb, 0, st>>>(covparms, tab, d, npairs, la, lb, same, C, dC);
+        break;
+    case COV_MATERN:
+        k_cov_pairs<COV_MATERN><<<blocks, tpb, 0, st>>>(covparms, tab, d, npairs, la, lb, same, C, dC);
+        break;
+    default:
+        k_cov_pairs<COV_ST><<<blocks, tpb, 0, st>>>(covparms, tab, d, npairs, la, lb, same, C, dC);
+        break;
+    }
+    return cudaGetLastError();
+}
+
+int mtab_doubles() { return MT_DOUBLES; }
+
+}  // namespace vg

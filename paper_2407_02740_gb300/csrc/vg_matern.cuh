@@ -1,0 +1,175 @@
+// vg_matern.cuh -- Matern correlation with general smoothness on the device.
+//
+// CUDA has no modified Bessel function of the second kind (the paper's Sec. 5 names this
+// as the reason its software cannot offer the Matern family with arbitrary smoothness).
+// Here M_nu(x) = 2^(1-nu)/Gamma(nu) x^nu K_nu(x) and the two derivatives the likelihood
+// needs are evaluated in two layers:
+//
+//  1. matern_direct: K_nu, K_(nu-1) and dK_nu/dnu from the integral
+//        K_nu(x) = int_0^inf exp(-x cosh t) cosh(nu t) dt
+//     (and its nu-derivative int exp(-x cosh t) t sinh(nu t) dt), trapezoid rule in t.
+//     The integrands are even and entire in t and decay double-exponentially, so the
+//     trapezoid sum converges geometrically in 1/h.  Scales are kept in log space.
+//  2. A per-pass coefficient table.  Within one pass nu is fixed, so the three functions
+//        F0(s) = M_nu(sqrt s),
+//        F1(s) = -x dM/dx = 2^(1-nu)/Gamma(nu) x^(nu+1) K_(nu-1)(x),  (rho dM/drho)
+//        F2(s) = dM/dnu,
+//     of s = x^2 = |h|^2 / rho^2 are tabulated once per pass as polynomials of degree D on
+//     dyadic sub-intervals: octave [2^e, 2^(e+1)) split into J equal parts.  The octave and
+//     part come from the exponent and leading mantissa bits of s (integer work), the local
+//     variable w = mantissa - centre is exact, and each function is a D-step Horner chain.
+//     Working in s avoids a square root per entry.  The only singularity of F(s) is at
+//     s = 0 (terms s^nu and s^nu log s), so on a part [a, a (1 + 1/J)] the Chebyshev
+//     interpolant converges like (4J + 2)^-D; with J = 4 and D = 12 that is < 1e-16
+//     relative to M(0) = 1.  Below 2^E0 the direct formula is used; at and above 2^E1 the
+//     functions are below 1e-20 for every nu <= 20 and are returned as 0.
+#pragma once
+#include "vg_common.cuh"
+
+namespace vg {
+
+constexpr int MT_E0 = -30;   // table covers s in [2^-30, 2^13)
+constexpr int MT_E1 = 13;
+constexpr int MT_LOGJ = 2;
+constexpr int MT_J = 1 << MT_LOGJ;
+constexpr int MT_D = 12;     // polynomial degree
+constexpr int MT_NC = MT_D + 1;
+constexpr int MT_NINT = (MT_E1 - MT_E0) * MT_J;
+constexpr int MT_PER_INT = 3 * MT_NC;          // F0, F1, F2 coefficients per interval
+constexpr int MT_DOUBLES = MT_NINT * MT_PER_INT;
+
+// F0, F1, F2 at x > 0 by the trapezoid rule (see header).  psi = digamma(nu),
+// lgnu = lgamma(nu).
+__device__ inline void matern_direct(double nu, double x, double psi, double lgnu,
+                                     double& F0, double& F1, double& F2) {
+    const double h = 0.1;
+    // envelope exponent mu t - x cosh t with mu = max(nu, |nu-1|) bounds all three
+    // integrands; factor out its maximum Phi
+    double mu = fmax(nu, fabs(nu - 1.0));
+    double ts = asinh(mu / x);
+    double Phi = mu * ts - x * cosh(ts);
+    double S0 = 0.0, S1 = 0.0, S2 = 0.0;
+    for (int k = 0; k < 20000; ++k) {
+        double t = k * h;
+        double ph = mu * t - x * cosh(t) - Phi;
+        double E = exp(ph) * (k == 0 ? 0.5 : 1.0);
+        // cosh(nu t) e^{-mu t}, cosh((nu-1) t) e^{-mu t}, t sinh(nu t) e^{-mu t}
+        double a = exp((nu - mu) * t), b = exp(-(nu + mu) * t);
+        double nu1 = fabs(nu - 1.0);
+        double c = exp((nu1 - mu) * t), dd = exp(-(nu1 + mu) * t);
+        S0 += E * 0.5 * (a + b);
+        S1 += E * 0.5 * (c + dd);
+        S2 += E * 0.5 * t * (a - b);
+        if (t > ts && ph < -50.0) break;
+    }
+    const double LN2 = 0.6931471805599453;
+    double lx = log(x);
+    double logA = (1.0 - nu) * LN2 - lgnu + nu * lx + Phi + log(h);
+    double A = exp(logA);
+    F0 = A * S0;
+    F1 = A * x * S1;
+    F2 = F0 * (-LN2 - psi + lx) + A * S2;
+}
+
+// Locates s in the table.  Returns the interval index and the local variable w, or
+// -1 when s < 2^E0 (direct formula, includes s == 0), or -2 when s >= 2^E1 (zero).
+__device__ __forceinline__ int mtab_locate(double s, double& w) {
+    unsigned long long bits = (unsigned long long)__double_as_longlong(s);
+    int e = (int)((bits >> 52) & 0x7ffull) - 1023;
+    if (e < MT_E0) return -1;
+    if (e >= MT_E1) return -2;
+    int j = (int)((bits >> (52 - MT_LOGJ)) & (unsigned long long)(MT_J - 1));
+    double mant = __longlong_as_double((long long)((bits & 0x000fffffffffffffull) |
+                                                   0x3ff0000000000000ull));
+    // centre 1 + (2j+1)/(2J) is dyadic, so w is exact (Sterbenz)
+    w = mant - (1.0 + (double)(2 * j + 1) / (double)(2 * MT_J));
+    return (e - MT_E0) * MT_J + j;
+}
+
+__device__ __forceinline__ double horner13(const double* c, double w) {
+    double p = c[12];
+#pragma unroll
+    for (int k = 11; k >= 0; --k) p = fma(p, w, c[k]);
+    return p;
+}
+
+// F0 (and optionally F1, F2) at s = x^2 from the table, with the direct formula below the
+// table and zero above it.
+__device__ __forceinline__ double matern_F0(const double* tab, double s, double nu, double psi,
+                                            double lg) {
+    double w;
+    int it = mtab_locate(s, w);
+    if (it >= 0) return horner13(tab + it * MT_PER_INT, w);
+    if (it == -2) return 0.0;
+    if (!(s > 0.0)) return 1.0;
+    double f0, f1, f2;
+    matern_direct(nu, sqrt(s), psi, lg, f0, f1, f2);
+    return f0;
+}
+__device__ __forceinline__ void matern_F12(const double* tab, double s, double nu, double psi,
+                                           double lg, double& F1, double& F2) {
+    double w;
+    int it = mtab_locate(s, w);
+    if (it >= 0) {
+        const double* cf = tab + it * MT_PER_INT;
+        F1 = horner13(cf + MT_NC, w);
+        F2 = horner13(cf + 2 * MT_NC, w);
+    } else if (it == -2 || !(s > 0.0)) {
+        F1 = 0.0;
+        F2 = 0.0;
+    } else {
+        double f0;
+        matern_direct(nu, sqrt(s), psi, lg, f0, F1, F2);
+    }
+}
+
+// Table builder: one block per interval, MT_NC threads evaluate the interpolation nodes,
+// then three threads turn node values into monomial coefficients in w.
+// nu is read from covparms[2]; invalid nu leaves the table untouched (the pass reports
+// the parameter error).
+__global__ void k_mtab_build(const double* __restrict__ covparms, double* __restrict__ tab) {
+    __shared__ double vals[3][MT_NC];
+    const double nu = covparms[2];
+    if (!(nu >= 0.05 && nu <= 20.0)) return;
+    const int it = blockIdx.x;
+    const int e = MT_E0 + it / MT_J, j = it % MT_J;
+    const double hw = 1.0 / (2.0 * MT_J);
+    const double cen = 1.0 + (double)(2 * j + 1) / (double)(2 * MT_J);
+    const double PI = 3.14159265358979323846;
+    const int i = threadIdx.x;
+    if (i < MT_NC) {
+        double u = cos(PI * (i + 0.5) / MT_NC);
+        double s = ldexp(cen + hw * u, e);
+        double psi = dev_digamma(nu), lg = lgamma(nu);
+        double f0, f1, f2;
+        matern_direct(nu, sqrt(s), psi, lg, f0, f1, f2);
+        vals[0][i] = f0; vals[1][i] = f1; vals[2][i] = f2;
+    }
+    __syncthreads();
+    if (i < 3) {
+        double a[MT_NC];
+        for (int k = 0; k < MT_NC; ++k) {
+            double acc = 0.0;
+            for (int q = 0; q < MT_NC; ++q) acc += vals[i][q] * cos(PI * k * (q + 0.5) / MT_NC);
+            a[k] = acc * (2.0 / MT_NC);
+        }
+        a[0] *= 0.5;
+        // sum_k a_k T_k(u) -> monomials in u, via T_{k+1} = 2u T_k - T_{k-1}
+        double mono[MT_NC], Tm[MT_NC], Tc[MT_NC], Tn[MT_NC];
+        for (int k = 0; k < MT_NC; ++k) { mono[k] = 0.0; Tm[k] = 0.0; Tc[k] = 0.0; }
+        Tm[0] = 1.0;            // T_0
+        Tc[1] = 1.0;            // T_1
+        mono[0] = a[0];
+        for (int k = 0; k < MT_NC; ++k) mono[k] += a[1] * Tc[k];
+        for (int deg = 2; deg < MT_NC; ++deg) {
+            for (int k = 0; k < MT_NC; ++k) Tn[k] = -Tm[k] + (k > 0 ? 2.0 * Tc[k - 1] : 0.0);
+            for (int k = 0; k < MT_NC; ++k) { mono[k] += a[deg] * Tn[k]; Tm[k] = Tc[k]; Tc[k] = Tn[k]; }
+        }
+        // u = w / hw: coefficient of w^k is mono_k / hw^k (exact power-of-two scaling)
+        double* out = tab + (size_t)it * MT_PER_INT + i * MT_NC;
+        double sc = 1.0;
+        for (int k = 0; k < MT_NC; ++k) { out[k] = mono[k] * sc; sc *= (2.0 * MT_J); }
+    }
+}
+
+}  // namespace vg
