@@ -59,6 +59,8 @@ cudaError_t grow(T** p, size_t* cap, size_t need) {
 
 }  // namespace
 
+void vg::set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
+
 struct vec_handle_s {
     int device = 0;
     int nsm = 0;

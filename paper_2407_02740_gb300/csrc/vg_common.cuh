@@ -14,6 +14,17 @@ constexpr int KMAX = 81;   // largest conditioning block (m <= 80)
 constexpr int PMAX = 8;    // largest number of regression columns
 constexpr int DMAX = 3;    // largest location dimension
 
+// Geometry of the per-pass Matern coefficient table (see vg_matern.cuh).
+constexpr int MT_E0 = -30;   // table covers s in [2^-30, 2^13)
+constexpr int MT_E1 = 13;
+constexpr int MT_LOGJ = 2;
+constexpr int MT_J = 1 << MT_LOGJ;
+constexpr int MT_D = 12;     // polynomial degree
+constexpr int MT_NC = MT_D + 1;
+constexpr int MT_NINT = (MT_E1 - MT_E0) * MT_J;
+constexpr int MT_PER_INT = 3 * MT_NC;          // F0, F1, F2 coefficients per interval
+constexpr int MT_DOUBLES = MT_NINT * MT_PER_INT;
+
 __host__ __device__ constexpr int nparms(int cov) { return cov == COV_EXP ? 3 : 4; }
 // number of covariance parameters whose derivative matrix needs a per-pair evaluation
 // (sigma2 and tau2 are handled in closed form)

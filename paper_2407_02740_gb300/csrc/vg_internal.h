@@ -38,4 +38,7 @@ cudaError_t launch_cov_pairs(int cov, const double* covparms, const double* tab,
                              const int32_t* same, double* C, double* dC, cudaStream_t st);
 int mtab_doubles();
 
+// Records the thread-local message returned by vecchia_last_error().
+void set_last_error(const char* msg);
+
 }  // namespace vg

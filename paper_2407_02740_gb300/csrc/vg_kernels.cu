@@ -232,16 +232,20 @@ size_t pass_smem_bytes(int cov, int m, int d, int p, int L, int threads, bool ta
 }
 
 int plan_pass(int cov, int m, int d, int p, int nsm, int force_L, PassPlan* plan) {
-    const int threads = 128;
+    // 128 threads (one warp per SM sub-partition, which the FP64 units need) unless the
+    // largest blocks only fit with fewer slots per block
     const size_t budget = 220 * 1024;
-    int chosen = -1;
+    int chosen = -1, threads = 128;
     bool tab = false;
-    for (int L = 1; L <= 32; L *= 2) {
-        if (force_L > 0 && L != force_L) continue;
-        bool t = (cov == COV_MATERN);
-        size_t b = pass_smem_bytes(cov, m, d, p, L, threads, t);
-        if (b > budget && t) { t = false; b = pass_smem_bytes(cov, m, d, p, L, threads, t); }
-        if (b <= budget) { chosen = L; tab = t; break; }
+    for (int thr = 128; thr >= 32 && chosen < 0; thr /= 2) {
+        for (int L = 1; L <= 32; L *= 2) {
+            if (force_L > 0 && L != force_L) continue;
+            if (L > thr) continue;
+            bool t = (cov == COV_MATERN);
+            size_t b = pass_smem_bytes(cov, m, d, p, L, thr, t);
+            if (b > budget && t) { t = false; b = pass_smem_bytes(cov, m, d, p, L, thr, t); }
+            if (b <= budget) { chosen = L; tab = t; threads = thr; break; }
+        }
     }
     if (chosen < 0) return -1;
     const int Q = npair_derivs(cov) + 1;

@@ -28,15 +28,7 @@
 
 namespace vg {
 
-constexpr int MT_E0 = -30;   // table covers s in [2^-30, 2^13)
-constexpr int MT_E1 = 13;
-constexpr int MT_LOGJ = 2;
-constexpr int MT_J = 1 << MT_LOGJ;
-constexpr int MT_D = 12;     // polynomial degree
-constexpr int MT_NC = MT_D + 1;
-constexpr int MT_NINT = (MT_E1 - MT_E0) * MT_J;
-constexpr int MT_PER_INT = 3 * MT_NC;          // F0, F1, F2 coefficients per interval
-constexpr int MT_DOUBLES = MT_NINT * MT_PER_INT;
+// table geometry (MT_*) is defined in vg_common.cuh
 
 // F0, F1, F2 at x > 0 by the trapezoid rule (see header).  psi = digamma(nu),
 // lgnu = lgamma(nu).

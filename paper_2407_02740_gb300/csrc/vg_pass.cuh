@@ -49,9 +49,11 @@ struct SlotLayout {
     }
 };
 
+// Synchronises the lanes of a group and orders their shared-memory accesses.  Also
+// issued for one-lane groups: it is then a memory barrier between the phases.
 template <int L>
 __device__ __forceinline__ void gsync(unsigned mask) {
-    if (L > 1) __syncwarp(mask);
+    __syncwarp(mask);
 }
 
 // sums over the L lanes of a group (xor partners stay inside the group)
@@ -346,32 +348,23 @@ __global__ void __launch_bounds__(128) k_pass_fp64(PassArgs args) {
         }
 
         // ---------------- m_j = L^-1 g_j (in place, column sweep) ----------------
-        {
-            double prev[Q];
-            for (int c = 0; c < Kp; ++c) {
-                const double ic = invd[c];
-                double mc[Q];
+        // Column c: every lane reads the finished residual g_j[c] and scales it; after a
+        // group barrier the owner of c stores m_j[c] and each lane updates its rows a > c.
+        for (int c = 0; c < Kp; ++c) {
+            const double ic = invd[c];
+            double mc[Q];
 #pragma unroll
-                for (int j = 0; j < Q; ++j) mc[j] = G[j * Kmax + c] * ic;
-                // the owner of column c-1 stores its final values now (nobody reads them
-                // in this sweep any more)
-                if (c > 0 && (((c - 1 - gl) & (L - 1)) == 0)) {
+            for (int j = 0; j < Q; ++j) mc[j] = G[j * Kmax + c] * ic;
+            gsync<L>(gmask);
+            if (((c - gl) & (L - 1)) == 0) {
 #pragma unroll
-                    for (int j = 0; j < Q; ++j) G[j * Kmax + c - 1] = prev[j];
-                }
-                const int a0 = c + 1 + ((gl - c - 1) & (L - 1));
-                for (int a = a0; a < Kp; a += L) {
-                    const double lac = A[a * (a + 1) / 2 + c];
-#pragma unroll
-                    for (int j = 0; j < Q; ++j) G[j * Kmax + a] = fma(-lac, mc[j], G[j * Kmax + a]);
-                }
-#pragma unroll
-                for (int j = 0; j < Q; ++j) prev[j] = mc[j];
-                gsync<L>(gmask);
+                for (int j = 0; j < Q; ++j) G[j * Kmax + c] = mc[j];
             }
-            if (((last - gl) & (L - 1)) == 0) {
+            const int a0 = c + 1 + ((gl - c - 1) & (L - 1));
+            for (int a = a0; a < Kp; a += L) {
+                const double lac = A[a * (a + 1) / 2 + c];
 #pragma unroll
-                for (int j = 0; j < Q; ++j) G[j * Kmax + last] = prev[j];
+                for (int j = 0; j < Q; ++j) G[j * Kmax + a] = fma(-lac, mc[j], G[j * Kmax + a]);
             }
             gsync<L>(gmask);
         }

@@ -105,14 +105,20 @@ def test_pass_matches_oracle(covfun, theta, p, m):
 
 
 @pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16, 32])
-def test_every_lane_mapping(lanes):
-    th = np.array([1.5, 0.07, 1.2, 0.05])
-    w = field(MAT, 900, 15, 2, th, seed=5)
-    o = oracle.loglik_grad_info(w.locs, w.y, w.X, w.NN, th, MAT)
+@pytest.mark.parametrize("covfun,theta,m,p", [
+    (MAT, [1.5, 0.07, 1.2, 0.05], 15, 2),
+    (MAT, [1.5, 0.07, 1.2, 0.05], 5, 1),   # small enough for one lane per observation
+    (EXP, [1.1, 0.2, 0.05], 8, 1),
+])
+def test_every_lane_mapping(lanes, covfun, theta, m, p):
+    th = np.array(theta)
+    w = field(covfun, 900, m, p, th, seed=5)
+    o = oracle.loglik_grad_info(w.locs, w.y, w.X, w.NN, th, covfun)
     try:
         g = gpu_pass(w, th, lanes=lanes)
     except vg.VecchiaError as e:
         assert e.code == 7  # that mapping does not fit shared memory
+        assert not (lanes >= 8 and m <= 8)
         return
     compare(g, o)
 
@@ -153,9 +159,14 @@ def test_edge_cases_single_point_m0_and_short_rows():
 
 def test_largest_m_and_p():
     th = np.array([1.0, 0.15, 0.05])
-    w = field(EXP, 700, 80, 8, th, seed=2, sim="dense")
-    o = oracle.loglik_grad_info(w.locs, w.y, w.X, w.NN, th, EXP)
-    compare(gpu_pass(w, th), o)
+    w = field(EXP, 700, 80, 1, th, seed=2, sim="dense")
+    x1, x2 = w.locs[:, 0], w.locs[:, 1]
+    # eight linearly independent regressors: a cubic surface without the x1^2 x2, x1 x2^2 terms
+    X = np.column_stack([np.ones(w.n), x1, x2, x1 * x1, x1 * x2, x2 * x2, x1 ** 3, x2 ** 3])
+    w8 = workloads.Workload("p8", EXP, w.locs, w.y + X @ np.linspace(0.5, -0.5, 8), X, w.NN,
+                            th, th, 80)
+    o = oracle.loglik_grad_info(w8.locs, w8.y, w8.X, w8.NN, th, EXP)
+    compare(gpu_pass(w8, th), o)
 
 
 def test_errors_are_reported_not_faulted():
