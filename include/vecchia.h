@@ -164,6 +164,38 @@ VECCHIA_API vec_status vecchia_covariance_pairs(vec_handle h, vec_covfun covfun,
                                     int d, int64_t npairs, const double* la, const double* lb,
                                     const int32_t* same, double* C, double* dC, void* stream);
 
+/*
+ * vecchia_loglik_grad_info_noalloc -- the device-resident pass without any allocation.
+ *
+ * The paper has no counterpart to this entry point; it exists for callers that cannot
+ * allocate device memory at the moment they need a likelihood value: code that runs
+ * while its stream is being captured into a CUDA graph (an allocation cannot be part of
+ * a capture), programs whose GPU memory is owned entirely by another allocator or held
+ * to a fixed budget, and latency-sensitive loops that cannot afford the device-wide
+ * synchronisation an allocation may cause.
+ *
+ * Same arguments, layouts, results and error reporting as vecchia_loglik_grad_info, but
+ * no handle: it runs on the calling thread's current CUDA device, all pointers must be
+ * device memory on that device, and the caller still provides `out` and `dev_status`.
+ * It calls no cudaMalloc, cudaFree or other allocating routine.  Its scratch (per-block
+ * partial sums, status word, Matern table) is one file-scope device array of
+ * 1,102,592 bytes that every GPU loading this library holds until the process exits;
+ * the partial-sum region holds 131072 doubles, and a pass whose launch plan needs more
+ * (blocks x record length) is rejected with VEC_ERR_UNSUPPORTED before anything runs.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress,
+ * with that device current); make that first call before any stream capture.
+ * Every call shares the one array and leaves its contents behind: the kernels reset the
+ * status word and rewrite the rest in full on each call, but calls whose work overlaps on
+ * the GPU (other streams, other host threads) race on it and must be serialised.
+ */
+VECCHIA_API vec_status vecchia_loglik_grad_info_noalloc(const double* locs, const double* y,
+                                                        const double* X, const int32_t* NNarray,
+                                                        int64_t n, int d, int p, int m,
+                                                        const double* covparms,
+                                                        vec_covfun covfun, vec_precision prec,
+                                                        void* stream, double* out,
+                                                        int64_t* dev_status);
+
 #ifdef __cplusplus
 }
 #endif

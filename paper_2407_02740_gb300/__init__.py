@@ -74,10 +74,13 @@ def lib():
         L.vecchia_loglik_grad_info_host.argtypes = [P, P, P, P, P, i64, ci, ci, ci, P, ci, ci,
                                                     P, P, P, P, P]
         L.vecchia_covariance_pairs.argtypes = [P, ci, P, ci, i64, P, P, P, P, P, P]
+        L.vecchia_loglik_grad_info_noalloc.argtypes = [P, P, P, P, i64, ci, ci, ci, P, ci, ci,
+                                                       P, P, P]
         for f in (L.vecchia_create, L.vecchia_destroy, L.vecchia_set_lanes,
                   L.vecchia_loglik_grad_info, L.vecchia_loglik_grad_info_host,
                   L.vecchia_covariance_pairs, L.vecchia_nparms, L.vecchia_max_m,
-                  L.vecchia_set_timing, L.vecchia_last_timing, L.vecchia_kernels_per_pass):
+                  L.vecchia_set_timing, L.vecchia_last_timing, L.vecchia_kernels_per_pass,
+                  L.vecchia_loglik_grad_info_noalloc):
             f.restype = ci
         _lib = L
     return _lib
@@ -175,6 +178,37 @@ def vecchia_loglik_grad_info(locs, y, X, NNarray, covparms, covfun: int, prec="f
     _check(lib().vecchia_loglik_grad_info(handle.ptr, _dptr(locs), _dptr(y), _dptr(X),
                                           _dptr(NNarray), n, d, p, m, _dptr(covparms), covfun,
                                           _PREC[prec], sptr, _dptr(out), _dptr(status)))
+    return out, status
+
+
+def vecchia_loglik_grad_info_noalloc(locs, y, X, NNarray, covparms, covfun: int,
+                                     prec="fp64", stream=None, out=None, status=None):
+    """The device-resident pass without any device allocation by the library: for callers
+    that cannot allocate (inside a stream capture, under another allocator's budget).  It
+    runs on the current CUDA device with the library's static scratch; `out` and `status`
+    are still supplied by the caller (allocated here only when not given).  Calls that
+    overlap on the GPU share that scratch and must be serialised."""
+    import torch
+    for t, dt, nm in ((locs, torch.float64, "locs"), (y, torch.float64, "y"),
+                      (X, torch.float64, "X"), (NNarray, torch.int32, "NNarray"),
+                      (covparms, torch.float64, "covparms")):
+        _dev_tensor_check(t, dt, nm)
+    n, d = locs.shape
+    p = X.shape[1]
+    m = NNarray.shape[1] - 1
+    q = NPARMS[covfun]
+    dev = locs.device
+    if out is None:
+        out = torch.empty(1 + q + q * q + p, dtype=torch.float64, device=dev)
+    if status is None:
+        status = torch.empty(2, dtype=torch.int64, device=dev)
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    with torch.cuda.device(dev):
+        _check(lib().vecchia_loglik_grad_info_noalloc(
+            _dptr(locs), _dptr(y), _dptr(X), _dptr(NNarray), n, d, p, m, _dptr(covparms),
+            covfun, _PREC[prec], ctypes.c_void_p(stream.cuda_stream), _dptr(out),
+            _dptr(status)))
     return out, status
 
 
