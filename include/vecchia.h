@@ -92,6 +92,10 @@ VECCHIA_API int vecchia_max_m(void);
  * shared-memory footprint does not fit makes later passes return VEC_ERR_UNSUPPORTED. */
 VECCHIA_API vec_status vecchia_set_lanes(vec_handle h, int lanes);
 
+/* Threads per block of the pass kernel: 32, 64, 128 or 256, or 0 to let the library
+ * choose (the default).  Same rules as vecchia_set_lanes. */
+VECCHIA_API vec_status vecchia_set_block_threads(vec_handle h, int threads);
+
 /* Tracing.  With timing enabled, every pass records CUDA events (on the pass's stream)
  * around its three phases: setup (status reset, Matern table), the per-observation kernel,
  * and the reduction + profile kernel.  vecchia_last_timing waits for the last traced pass

@@ -67,6 +67,7 @@ def lib():
         L.vecchia_last_error.restype = ctypes.c_char_p
         L.vecchia_nparms.argtypes = [ci]
         L.vecchia_set_lanes.argtypes = [P, ci]
+        L.vecchia_set_block_threads.argtypes = [P, ci]
         L.vecchia_set_timing.argtypes = [P, ci]
         L.vecchia_last_timing.argtypes = [P, P, P, P]
         L.vecchia_kernels_per_pass.argtypes = [ci]
@@ -76,7 +77,7 @@ def lib():
         L.vecchia_covariance_pairs.argtypes = [P, ci, P, ci, i64, P, P, P, P, P, P]
         L.vecchia_loglik_grad_info_noalloc.argtypes = [P, P, P, P, i64, ci, ci, ci, P, ci, ci,
                                                        P, P, P]
-        for f in (L.vecchia_create, L.vecchia_destroy, L.vecchia_set_lanes,
+        for f in (L.vecchia_create, L.vecchia_destroy, L.vecchia_set_lanes, L.vecchia_set_block_threads,
                   L.vecchia_loglik_grad_info, L.vecchia_loglik_grad_info_host,
                   L.vecchia_covariance_pairs, L.vecchia_nparms, L.vecchia_max_m,
                   L.vecchia_set_timing, L.vecchia_last_timing, L.vecchia_kernels_per_pass,
@@ -105,6 +106,9 @@ class Handle:
 
     def set_lanes(self, lanes: int):
         _check(lib().vecchia_set_lanes(self._h, lanes))
+
+    def set_block_threads(self, threads: int):
+        _check(lib().vecchia_set_block_threads(self._h, threads))
 
     def set_timing(self, enable: bool = True):
         _check(lib().vecchia_set_timing(self._h, 1 if enable else 0))

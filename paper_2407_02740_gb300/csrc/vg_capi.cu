@@ -64,7 +64,8 @@ void vg::set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
 struct vec_handle_s {
     int device = 0;
     int nsm = 0;
-    int lanes = 0;  // 0 = automatic
+    int lanes = 0;    // 0 = automatic
+    int threads = 0;  // 0 = automatic
     cudaStream_t stream = nullptr;
     // tracing
     int timing = 0;
@@ -139,6 +140,14 @@ vec_status vecchia_set_lanes(vec_handle h, int lanes) {
           lanes == 32))
         return fail(VEC_ERR_ARG, "lanes must be 0, 1, 2, 4, 8, 16 or 32 (got %d)", lanes);
     h->lanes = lanes;
+    return VEC_OK;
+}
+
+vec_status vecchia_set_block_threads(vec_handle h, int threads) {
+    if (!h) return fail(VEC_ERR_ARG, "vecchia_set_block_threads: NULL handle");
+    if (!(threads == 0 || threads == 32 || threads == 64 || threads == 128 || threads == 256))
+        return fail(VEC_ERR_ARG, "threads must be 0, 32, 64, 128 or 256 (got %d)", threads);
+    h->threads = threads;
     return VEC_OK;
 }
 
@@ -220,7 +229,7 @@ vec_status enqueue_pass(vec_handle h, const double* locs, const double* y, const
                         double* out, long long* dev_status) {
     const int cov = (int)covfun;
     vg::PassPlan plan;
-    int pr = vg::plan_pass(cov, m, d, p, h->nsm, h->lanes, &plan);
+    int pr = vg::plan_pass(cov, m, d, p, h->nsm, h->lanes, h->threads, &plan);
     if (pr == -1) return fail(VEC_ERR_UNSUPPORTED, "no kernel mapping fits m = %d, p = %d", m, p);
     if (pr != 0) return cuda_fail(cudaGetLastError(), "planning the pass kernel");
     cudaError_t e = grow(&h->partials, &h->partials_cap, (size_t)plan.grid * plan.nstat);

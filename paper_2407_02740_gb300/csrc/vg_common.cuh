@@ -14,15 +14,19 @@ constexpr int KMAX = 81;   // largest conditioning block (m <= 80)
 constexpr int PMAX = 8;    // largest number of regression columns
 constexpr int DMAX = 3;    // largest location dimension
 
-// Geometry of the per-pass Matern coefficient table (see vg_matern.cuh).
+// Geometry of the per-pass Matern coefficient table (see vg_matern.cuh).  Each function
+// on each interval is a degree-12 polynomial in w stored as 8 FP64 coefficients (w^0..w^7)
+// followed by 5 FP32 coefficients (w^8..w^12, padded to 6 floats): 11 double slots.
 constexpr int MT_E0 = -30;   // table covers s in [2^-30, 2^13)
 constexpr int MT_E1 = 13;
 constexpr int MT_LOGJ = 2;
 constexpr int MT_J = 1 << MT_LOGJ;
 constexpr int MT_D = 12;     // polynomial degree
 constexpr int MT_NC = MT_D + 1;
+constexpr int MT_NHEAD = 8;  // FP64 coefficients per function
+constexpr int MT_FSTRIDE = MT_NHEAD + 3;       // double slots per function
 constexpr int MT_NINT = (MT_E1 - MT_E0) * MT_J;
-constexpr int MT_PER_INT = 3 * MT_NC;          // F0, F1, F2 coefficients per interval
+constexpr int MT_PER_INT = 3 * MT_FSTRIDE;     // F0, F1, F2 per interval
 constexpr int MT_DOUBLES = MT_NINT * MT_PER_INT;
 
 __host__ __device__ constexpr int nparms(int cov) { return cov == COV_EXP ? 3 : 4; }

@@ -23,7 +23,8 @@ struct PassPlan {
 
 // Chooses the lanes-per-observation mapping that fits shared memory (or the forced one).
 // Returns 0 on success, -1 if no mapping fits, -2 on a CUDA error.
-int plan_pass(int cov, int m, int d, int p, int nsm, int force_L, PassPlan* plan);
+int plan_pass(int cov, int m, int d, int p, int nsm, int force_L, int force_threads,
+              PassPlan* plan);
 size_t pass_smem_bytes(int cov, int m, int d, int p, int L, int threads, bool tab_smem);
 
 cudaError_t launch_pass(int cov, const PassPlan& plan, const PassArgs& args, cudaStream_t st);

@@ -231,16 +231,21 @@ size_t pass_smem_bytes(int cov, int m, int d, int p, int L, int threads, bool ta
     return dbl * sizeof(double) + ints * sizeof(int);
 }
 
-int plan_pass(int cov, int m, int d, int p, int nsm, int force_L, PassPlan* plan) {
-    // 128 threads (one warp per SM sub-partition, which the FP64 units need) unless the
-    // largest blocks only fit with fewer slots per block
+int plan_pass(int cov, int m, int d, int p, int nsm, int force_L, int force_threads,
+              PassPlan* plan) {
+    // Preference: 256 threads (two warps per SM sub-partition, so that one warp's FP64
+    // dependency waits are covered by the other), then 128 (one warp per sub-partition,
+    // the minimum that occupies all FP64 units), then fewer when the largest blocks do
+    // not fit; within a block size, the fewest lanes per observation that fit.
     const size_t budget = 220 * 1024;
     int chosen = -1, threads = 128;
     bool tab = false;
-    for (int thr = 128; thr >= 32 && chosen < 0; thr /= 2) {
+    for (int thr = 256; thr >= 32 && chosen < 0; thr /= 2) {
+        if (force_threads > 0 && thr != force_threads) continue;
         for (int L = 1; L <= 32; L *= 2) {
             if (force_L > 0 && L != force_L) continue;
             if (L > thr) continue;
+            if (thr == 256 && force_L <= 0 && L > 16) continue;
             bool t = (cov == COV_MATERN);
             size_t b = pass_smem_bytes(cov, m, d, p, L, thr, t);
             if (b > budget && t) { t = false; b = pass_smem_bytes(cov, m, d, p, L, thr, t); }
@@ -288,7 +293,7 @@ cudaError_t launch_init_status(int* status, long long* bad, cudaStream_t st) {
 }
 
 cudaError_t launch_mtab_build(const double* covparms, double* tab, cudaStream_t st) {
-    k_mtab_build<<<MT_NINT, 32, 0, st>>>(covparms, tab);
+    k_mtab_build<<<MT_NINT, MT_NC * 32, 0, st>>>(covparms, tab);
     return cudaGetLastError();
 }
 

@@ -65,23 +65,35 @@ __device__ inline void matern_direct(double nu, double x, double psi, double lgn
 
 // Locates s in the table.  Returns the interval index and the local variable w, or
 // -1 when s < 2^E0 (direct formula, includes s == 0), or -2 when s >= 2^E1 (zero).
+// The interval centre 1 + (2j+1)/(2J) is built from bits, so w = mantissa - centre is
+// one exact FP64 subtraction (Sterbenz).
 __device__ __forceinline__ int mtab_locate(double s, double& w) {
-    unsigned long long bits = (unsigned long long)__double_as_longlong(s);
-    int e = (int)((bits >> 52) & 0x7ffull) - 1023;
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(s);
+    const int e = (int)((bits >> 52) & 0x7ffull) - 1023;
     if (e < MT_E0) return -1;
     if (e >= MT_E1) return -2;
-    int j = (int)((bits >> (52 - MT_LOGJ)) & (unsigned long long)(MT_J - 1));
-    double mant = __longlong_as_double((long long)((bits & 0x000fffffffffffffull) |
-                                                   0x3ff0000000000000ull));
-    // centre 1 + (2j+1)/(2J) is dyadic, so w is exact (Sterbenz)
-    w = mant - (1.0 + (double)(2 * j + 1) / (double)(2 * MT_J));
-    return (e - MT_E0) * MT_J + j;
+    const unsigned long long j = (bits >> (52 - MT_LOGJ)) & (unsigned long long)(MT_J - 1);
+    const double mant = __longlong_as_double((long long)((bits & 0x000fffffffffffffull) |
+                                                         0x3ff0000000000000ull));
+    const double cen = __longlong_as_double(
+        (long long)(0x3ff0000000000000ull | ((2ull * j + 1ull) << (52 - MT_LOGJ - 1))));
+    w = mant - cen;
+    return (e - MT_E0) * MT_J + (int)j;
 }
 
-__device__ __forceinline__ double horner13(const double* c, double w) {
-    double p = c[12];
+// Degree-12 polynomial in w: the tail w^8..w^12 (coefficients <= 1e-8 in size on every
+// interval, so FP32 rounding there is below 1e-15 absolute) in FP32, the head in FP64.
+__device__ __forceinline__ double horner_split(const double* c, double w) {
+    const float* t = reinterpret_cast<const float*>(c + MT_NHEAD);
+    const float wf = (float)w;
+    float pt = t[4];
+    pt = fmaf(pt, wf, t[3]);
+    pt = fmaf(pt, wf, t[2]);
+    pt = fmaf(pt, wf, t[1]);
+    pt = fmaf(pt, wf, t[0]);
+    double p = (double)pt;
 #pragma unroll
-    for (int k = 11; k >= 0; --k) p = fma(p, w, c[k]);
+    for (int k = MT_NHEAD - 1; k >= 0; --k) p = fma(p, w, c[k]);
     return p;
 }
 
@@ -91,7 +103,7 @@ __device__ __forceinline__ double matern_F0(const double* tab, double s, double 
                                             double lg) {
     double w;
     int it = mtab_locate(s, w);
-    if (it >= 0) return horner13(tab + it * MT_PER_INT, w);
+    if (it >= 0) return horner_split(tab + it * MT_PER_INT, w);
     if (it == -2) return 0.0;
     if (!(s > 0.0)) return 1.0;
     double f0, f1, f2;
@@ -104,8 +116,8 @@ __device__ __forceinline__ void matern_F12(const double* tab, double s, double n
     int it = mtab_locate(s, w);
     if (it >= 0) {
         const double* cf = tab + it * MT_PER_INT;
-        F1 = horner13(cf + MT_NC, w);
-        F2 = horner13(cf + 2 * MT_NC, w);
+        F1 = horner_split(cf + MT_FSTRIDE, w);
+        F2 = horner_split(cf + 2 * MT_FSTRIDE, w);
     } else if (it == -2 || !(s > 0.0)) {
         F1 = 0.0;
         F2 = 0.0;
@@ -115,11 +127,49 @@ __device__ __forceinline__ void matern_F12(const double* tab, double s, double n
     }
 }
 
-// Table builder: one block per interval, MT_NC threads evaluate the interpolation nodes,
-// then three threads turn node values into monomial coefficients in w.
+// Warp-cooperative version of matern_direct for the table builder: lane l sums the
+// trapezoid nodes k = l, l+32, ..., then the partial sums are combined in a fixed order.
+__device__ inline void matern_direct_warp(double nu, double x, double psi, double lgnu,
+                                          double& F0, double& F1, double& F2) {
+    const double h = 0.1;
+    const int lane = threadIdx.x & 31;
+    double mu = fmax(nu, fabs(nu - 1.0));
+    double ts = asinh(mu / x);
+    double Phi = mu * ts - x * cosh(ts);
+    double S0 = 0.0, S1 = 0.0, S2 = 0.0;
+    const double nu1 = fabs(nu - 1.0);
+    for (int k = lane; k < 20000; k += 32) {
+        double t = k * h;
+        double ph = mu * t - x * cosh(t) - Phi;
+        double E = exp(ph) * (k == 0 ? 0.5 : 1.0);
+        double a = exp((nu - mu) * t), b = exp(-(nu + mu) * t);
+        double c = exp((nu1 - mu) * t), dd = exp(-(nu1 + mu) * t);
+        S0 += E * 0.5 * (a + b);
+        S1 += E * 0.5 * (c + dd);
+        S2 += E * 0.5 * t * (a - b);
+        if (t > ts && ph < -50.0) break;  // the integrand decreases from here on
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        S0 += __shfl_xor_sync(0xffffffffu, S0, o);
+        S1 += __shfl_xor_sync(0xffffffffu, S1, o);
+        S2 += __shfl_xor_sync(0xffffffffu, S2, o);
+    }
+    const double LN2 = 0.6931471805599453;
+    double lx = log(x);
+    double logA = (1.0 - nu) * LN2 - lgnu + nu * lx + Phi + log(h);
+    double A = exp(logA);
+    F0 = A * S0;
+    F1 = A * x * S1;
+    F2 = F0 * (-LN2 - psi + lx) + A * S2;
+}
+
+// Table builder: one block of MT_NC warps per interval; warp i evaluates interpolation
+// node i, then three threads turn node values into monomial coefficients in w.
 // nu is read from covparms[2]; invalid nu leaves the table untouched (the pass reports
 // the parameter error).
-__global__ void k_mtab_build(const double* __restrict__ covparms, double* __restrict__ tab) {
+__global__ void __launch_bounds__(MT_NC * 32) k_mtab_build(const double* __restrict__ covparms,
+                                                           double* __restrict__ tab) {
     __shared__ double vals[3][MT_NC];
     const double nu = covparms[2];
     if (!(nu >= 0.05 && nu <= 20.0)) return;
@@ -128,16 +178,17 @@ __global__ void k_mtab_build(const double* __restrict__ covparms, double* __rest
     const double hw = 1.0 / (2.0 * MT_J);
     const double cen = 1.0 + (double)(2 * j + 1) / (double)(2 * MT_J);
     const double PI = 3.14159265358979323846;
-    const int i = threadIdx.x;
-    if (i < MT_NC) {
-        double u = cos(PI * (i + 0.5) / MT_NC);
+    const int node = threadIdx.x >> 5;
+    {
+        double u = cos(PI * (node + 0.5) / MT_NC);
         double s = ldexp(cen + hw * u, e);
         double psi = dev_digamma(nu), lg = lgamma(nu);
         double f0, f1, f2;
-        matern_direct(nu, sqrt(s), psi, lg, f0, f1, f2);
-        vals[0][i] = f0; vals[1][i] = f1; vals[2][i] = f2;
+        matern_direct_warp(nu, sqrt(s), psi, lg, f0, f1, f2);
+        if ((threadIdx.x & 31) == 0) { vals[0][node] = f0; vals[1][node] = f1; vals[2][node] = f2; }
     }
     __syncthreads();
+    const int i = threadIdx.x;
     if (i < 3) {
         double a[MT_NC];
         for (int k = 0; k < MT_NC; ++k) {
@@ -157,10 +208,17 @@ __global__ void k_mtab_build(const double* __restrict__ covparms, double* __rest
             for (int k = 0; k < MT_NC; ++k) Tn[k] = -Tm[k] + (k > 0 ? 2.0 * Tc[k - 1] : 0.0);
             for (int k = 0; k < MT_NC; ++k) { mono[k] += a[deg] * Tn[k]; Tm[k] = Tc[k]; Tc[k] = Tn[k]; }
         }
-        // u = w / hw: coefficient of w^k is mono_k / hw^k (exact power-of-two scaling)
-        double* out = tab + (size_t)it * MT_PER_INT + i * MT_NC;
+        // u = w / hw: coefficient of w^k is mono_k / hw^k (exact power-of-two scaling);
+        // w^0..w^7 stored in FP64, w^8..w^12 in FP32 (see horner_split)
+        double* out = tab + (size_t)it * MT_PER_INT + i * MT_FSTRIDE;
+        float* tail = reinterpret_cast<float*>(out + MT_NHEAD);
         double sc = 1.0;
-        for (int k = 0; k < MT_NC; ++k) { out[k] = mono[k] * sc; sc *= (2.0 * MT_J); }
+        for (int k = 0; k < MT_NC; ++k) {
+            if (k < MT_NHEAD) out[k] = mono[k] * sc;
+            else tail[k - MT_NHEAD] = (float)(mono[k] * sc);
+            sc *= (2.0 * MT_J);
+        }
+        tail[MT_NC - MT_NHEAD] = 0.0f;
     }
 }
 

@@ -26,7 +26,8 @@ namespace {
 
 // Layout of the scratch array, in doubles; each region starts on a 256-byte boundary.
 constexpr int kTabOff = 0;
-constexpr int kTabLen = ((vg::MT_DOUBLES + 31) / 32) * 32;
+constexpr int kTabLen = 6720;                     // reserved for the Matern table
+static_assert(vg::MT_DOUBLES <= kTabLen, "the Matern table must fit its reserved region");
 constexpr int kStatusOff = kTabOff + kTabLen;      // int status, then long long bad index
 constexpr int kStatusLen = 32;
 constexpr int kPartOff = kStatusOff + kStatusLen;
@@ -101,7 +102,7 @@ VECCHIA_API vec_status vecchia_loglik_grad_info_noalloc(
 
     const int cov = (int)covfun;
     vg::PassPlan plan;
-    int pr = vg::plan_pass(cov, m, d, p, nsm, 0, &plan);
+    int pr = vg::plan_pass(cov, m, d, p, nsm, 0, 0, &plan);
     if (pr == -1) return nfail(VEC_ERR_UNSUPPORTED, "no kernel mapping fits m = %d, p = %d", m, p);
     if (pr != 0) return nfail(VEC_ERR_CUDA, "planning the pass kernel failed");
     const long long need = (long long)plan.grid * plan.nstat;

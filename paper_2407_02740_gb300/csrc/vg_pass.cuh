@@ -87,7 +87,7 @@ __device__ __forceinline__ bool circle_pair(int Kp, int Nv, int r, int k, int& a
 }
 
 template <int COV, int L>
-__global__ void __launch_bounds__(128) k_pass_fp64(PassArgs args) {
+__global__ void __launch_bounds__(256) k_pass_fp64(PassArgs args) {
     extern __shared__ __align__(16) double smem[];
     constexpr int NG = npair_derivs(COV);
     constexpr int Q = NG + 1;
@@ -175,9 +175,7 @@ __global__ void __launch_bounds__(128) k_pass_fp64(PassArgs args) {
     const double diagC = sig2 * (1.0 + tau2);
     // EXP: rho = th[1]; MATERN: rho = th[1], nu = th[2]; ST: rho_s = th[1], rho_t = th[2]
     const double inv_r1 = 1.0 / th[1];
-    const double inv_r1sq = inv_r1 * inv_r1;
-    const double inv_r2 = (COV == COV_ST) ? 1.0 / th[2] : 0.0;
-    const double inv_r2sq = inv_r2 * inv_r2;
+    const double inv_r2 = (COV == COV_ST) ? 1.0 / th[2] : 1.0;
     double m_psi = 0.0, m_lg = 0.0;
     if (COV == COV_MATERN && ok) { m_psi = dev_digamma(th[2]); m_lg = lgamma(th[2]); }
     __syncthreads();
@@ -206,7 +204,10 @@ __global__ void __launch_bounds__(128) k_pass_fp64(PassArgs args) {
         for (int a = gl; a < Kp; a += L) {
             int j = row[Kp - 1 - a];
             idx[a] = j;
-            for (int k = 0; k < d; ++k) loc[k * Kmax + a] = args.locs[(long long)j * d + k];
+            // coordinates are stored divided by their range parameter, so that squared
+            // distances come out already scaled
+            for (int k = 0; k < d; ++k)
+                loc[k * Kmax + a] = args.locs[(long long)j * d + k] * ((COV == COV_ST && k == 2) ? inv_r2 : inv_r1);
             Yg[a] = args.y[j];
             for (int t = 0; t < p; ++t) Yg[(1 + t) * Kmax + a] = args.X[(long long)j * p + t];
         }
@@ -228,7 +229,7 @@ __global__ void __launch_bounds__(128) k_pass_fp64(PassArgs args) {
                     double t = loc[k * Kmax + a] - loc[k * Kmax + c];
                     s = fma(t, t, s);
                 }
-                double x = sqrt(s) * inv_r1;
+                double x = sqrt(s);
                 double ex = sig2 * exp(-x);
                 C = ex;
                 D1[a * (a - 1) / 2 + c] = ex * x;          // rho dC/drho
@@ -236,7 +237,7 @@ __global__ void __launch_bounds__(128) k_pass_fp64(PassArgs args) {
                 double t0 = loc[a] - loc[c];
                 double t1 = loc[Kmax + a] - loc[Kmax + c];
                 double t2 = loc[2 * Kmax + a] - loc[2 * Kmax + c];
-                double u = fma(t0, t0, t1 * t1) * inv_r1sq + t2 * t2 * inv_r2sq;
+                double u = fma(t0, t0, fma(t1, t1, t2 * t2));
                 double D = sqrt(u);
                 double ex = sig2 * exp(-D);
                 C = ex;
@@ -247,7 +248,7 @@ __global__ void __launch_bounds__(128) k_pass_fp64(PassArgs args) {
                     double t = loc[k * Kmax + a] - loc[k * Kmax + c];
                     s = fma(t, t, s);
                 }
-                C = sig2 * matern_F0(tab, s * inv_r1sq, th[2], m_psi, m_lg);
+                C = sig2 * matern_F0(tab, s, th[2], m_psi, m_lg);
             }
             A[e] = C;
         }
@@ -323,8 +324,8 @@ __global__ void __launch_bounds__(128) k_pass_fp64(PassArgs args) {
                         double t1 = loc[Kmax + a] - loc[Kmax + c];
                         double t2 = loc[2 * Kmax + a] - loc[2 * Kmax + c];
                         double w = D1[a * (a - 1) / 2 + c];
-                        dv[0] = w * fma(t0, t0, t1 * t1) * inv_r1sq * inv_r1;
-                        if (NG > 1) dv[NG - 1] = w * t2 * t2 * inv_r2sq * inv_r2;
+                        dv[0] = w * fma(t0, t0, t1 * t1) * inv_r1;
+                        if (NG > 1) dv[NG - 1] = w * t2 * t2 * inv_r2;
                     } else {
                         double s = 0.0;
                         for (int kk = 0; kk < d; ++kk) {
@@ -332,7 +333,7 @@ __global__ void __launch_bounds__(128) k_pass_fp64(PassArgs args) {
                             s = fma(t, t, s);
                         }
                         double F1, F2;
-                        matern_F12(tab, s * inv_r1sq, th[2], m_psi, m_lg, F1, F2);
+                        matern_F12(tab, s, th[2], m_psi, m_lg, F1, F2);
                         dv[0] = sig2 * F1 * inv_r1;
                         if (NG > 1) dv[NG - 1] = sig2 * F2;
                     }
