@@ -217,6 +217,9 @@ def run_ours(args):
         vg.vecchia_loglik_grad_info(locs, y, X, NN, th, w.covfun, stream=stream, out=out,
                                     status=st, handle=h)
 
+    # untimed: pick the kernel mapping for this problem (recorded in the handle)
+    tune = vg.vecchia_autotune(locs, y, X, NN, th, w.covfun, stream=stream, handle=h)
+
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -271,6 +274,16 @@ def run_ours(args):
     h2d = hl.nbytes + hy.nbytes + hX.nbytes + hNN.nbytes + hth.nbytes
     d2h = 8 * (1 + q + q * q + w.p) + 16
 
+    # Fisher-scoring fit from the workload's starting point (tol 1e-4): the first call
+    # builds the iteration graph, the second reuses it; both are wall time around the call
+    fit_times, fit = [], None
+    for _ in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fit = vg.vecchia_fit(locs, y, X, NN, w.covfun, w.theta_start, tol=1e-4, stream=stream,
+                             handle=h)
+        fit_times.append(time.perf_counter() - t0)
+
     if rank != 0:
         if ws > 1:
             torch.distributed.barrier()
@@ -306,6 +319,12 @@ def run_ours(args):
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": args.steps * int(vg.lib().vecchia_kernels_per_pass(w.covfun)),
         "clocks": clocks,
+        "mapping": {"lanes_per_observation": tune["lanes"], "threads_per_block": tune["threads"],
+                    "source": "vecchia_autotune"},
+        "fit": {"precision": "f64", "tol": 1e-4, "start": [float(v) for v in w.theta_start],
+                "seconds_first_call": fit_times[0], "seconds": fit_times[1],
+                "iters": fit["iters"], "passes": fit["evals"], "status": fit["status"],
+                "theta": [float(v) for v in fit["theta"]], "loglik": fit["loglik"]},
         "result": {"loglik": res["loglik"], "grad": [float(v) for v in res["grad"]]},
     }
     print(json.dumps(line))

@@ -96,6 +96,29 @@ VECCHIA_API vec_status vecchia_set_lanes(vec_handle h, int lanes);
  * choose (the default).  Same rules as vecchia_set_lanes. */
 VECCHIA_API vec_status vecchia_set_block_threads(vec_handle h, int threads);
 
+/*
+ * Autotuning of the kernel mapping.  vecchia_autotune runs the pass on the given inputs
+ * (DEVICE pointers, as for vecchia_loglik_grad_info) once per candidate mapping -- lanes
+ * per observation 1..32 x threads per block 64..256, every pair whose shared memory fits --
+ * times each with CUDA events (one warm-up, best of `reps`), and records the fastest in
+ * the handle under the key (covfun, m, d, p, precision, floor(log2 n)).  Later passes and
+ * fits on the handle whose key matches use that mapping unless vecchia_set_lanes /
+ * vecchia_set_block_threads force one.  Outputs (HOST, may be NULL): the chosen lanes,
+ * threads and its pass time in ms.  Synchronises `stream`.  Must not be called during a
+ * stream capture.
+ */
+VECCHIA_API vec_status vecchia_autotune(vec_handle h, const double* locs, const double* y,
+                                        const double* X, const int32_t* NNarray, int64_t n,
+                                        int d, int p, int m, const double* covparms,
+                                        vec_covfun covfun, vec_precision prec, void* stream,
+                                        int reps, int* lanes_out, int* threads_out,
+                                        float* ms_out);
+
+/* Writes / reads the handle's autotuning records as JSON (an array of objects with keys
+ * covfun, m, d, p, prec, log2n, lanes, threads, ms).  Loading adds to the records. */
+VECCHIA_API vec_status vecchia_autotune_save(vec_handle h, const char* path);
+VECCHIA_API vec_status vecchia_autotune_load(vec_handle h, const char* path);
+
 /* Tracing.  With timing enabled, every pass records CUDA events (on the pass's stream)
  * around its three phases: setup (status reset, Matern table), the per-observation kernel,
  * and the reduction + profile kernel.  vecchia_last_timing waits for the last traced pass
@@ -153,6 +176,48 @@ VECCHIA_API vec_status vecchia_loglik_grad_info_host(vec_handle h, const double*
                                          vec_covfun covfun, vec_precision prec,
                                          double* loglik, double* grad, double* info,
                                          double* betahat, int64_t* bad_index);
+
+/* Options of vecchia_fit.  A NULL pointer means the defaults shown. */
+typedef struct {
+    double tol;         /* stop when g~' I~^-1 g~ < tol on the log scale (1e-4)            */
+    int maxit;          /* largest number of accepted Fisher steps (40, Table 2 of the paper)*/
+    int max_halvings;   /* step halvings tried before giving up (10)                        */
+    int use_graph;      /* 1: all iterations inside one CUDA graph with a WHILE node (1);
+                           0: one host round trip per iteration                             */
+    int prec;           /* vec_precision of the passes (VEC_FP64)                           */
+} vec_fit_opts;
+
+/* Outcome of vecchia_fit. */
+typedef struct {
+    int status;         /* 0 converged, 1 iteration limit, 2 no ascent step, 3 start failed */
+    int iters;          /* accepted Fisher steps                                            */
+    int evals;          /* likelihood passes run (accepted steps + halvings + 1)            */
+    int pass_status;    /* vec_status of the last pass                                      */
+} vec_fit_info;
+
+/*
+ * vecchia_fit -- Fisher scoring (Eq. 4) for the covariance parameters, beta profiled.
+ *
+ * Iterates on log theta: g~ = theta (.) grad, I~ = diag(theta) info diag(theta),
+ * Delta = I~^-1 g~ (a ridge r * 1e-4 * max diag(I~), r = 1..8, is added if I~ is not PD);
+ * stops when g~' Delta < tol (checked before stepping) or after maxit accepted steps;
+ * a trial theta (.) exp(Delta / 2^h) is accepted at the first h = 0..max_halvings whose
+ * loglik is finite and larger; a failed pass counts as -inf; the Matern smoothness is
+ * clamped to [0.05, 20].  Every iteration runs on the device (pass + step kernel); with
+ * use_graph = 1 the whole loop is one CUDA graph launch.
+ *
+ * locs, y, X, NNarray: DEVICE memory (as in vecchia_loglik_grad_info).  start: HOST, q
+ * values (must be valid parameters).  Outputs are HOST memory: theta_out (q), betahat (p),
+ * *loglik, grad (q), info (q*q) at the final accepted parameters, and fit_info (may be
+ * NULL).  Runs on `stream` and returns after the fit has finished.  Returns VEC_OK when
+ * the loop ran (inspect fit_info->status), or an argument / CUDA error.
+ */
+VECCHIA_API vec_status vecchia_fit(vec_handle h, const double* locs, const double* y,
+                                   const double* X, const int32_t* NNarray, int64_t n, int d,
+                                   int p, int m, vec_covfun covfun, const double* start,
+                                   const vec_fit_opts* opts, void* stream, double* theta_out,
+                                   double* betahat, double* loglik, double* grad, double* info,
+                                   vec_fit_info* fit_info);
 
 /*
  * vecchia_covariance_pairs -- the library's device covariance functions on explicit pairs.

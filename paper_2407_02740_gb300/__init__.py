@@ -32,6 +32,22 @@ STATUS = {0: "VEC_OK", 1: "VEC_ERR_ARG", 2: "VEC_ERR_NOT_PD", 3: "VEC_ERR_NONFIN
 _PREC = {"fp64": FP64, "mixed": MIXED, FP64: FP64, MIXED: MIXED}
 
 
+class FitOpts(ctypes.Structure):
+    """vec_fit_opts (include/vecchia.h)."""
+    _fields_ = [("tol", ctypes.c_double), ("maxit", ctypes.c_int),
+                ("max_halvings", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("prec", ctypes.c_int)]
+
+
+class FitInfo(ctypes.Structure):
+    """vec_fit_info (include/vecchia.h)."""
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("evals", ctypes.c_int),
+                ("pass_status", ctypes.c_int)]
+
+
+FIT_STATUS = {0: "converged", 1: "iteration limit", 2: "no ascent step", 3: "start failed"}
+
+
 class VecchiaError(RuntimeError):
     def __init__(self, code: int, msg: str, bad_index: int = -1):
         super().__init__("%s: %s" % (STATUS.get(code, "?"), msg))
@@ -68,6 +84,9 @@ def lib():
         L.vecchia_nparms.argtypes = [ci]
         L.vecchia_set_lanes.argtypes = [P, ci]
         L.vecchia_set_block_threads.argtypes = [P, ci]
+        L.vecchia_autotune.argtypes = [P, P, P, P, P, i64, ci, ci, ci, P, ci, ci, P, ci, P, P, P]
+        L.vecchia_autotune_save.argtypes = [P, ctypes.c_char_p]
+        L.vecchia_autotune_load.argtypes = [P, ctypes.c_char_p]
         L.vecchia_set_timing.argtypes = [P, ci]
         L.vecchia_last_timing.argtypes = [P, P, P, P]
         L.vecchia_kernels_per_pass.argtypes = [ci]
@@ -75,13 +94,16 @@ def lib():
         L.vecchia_loglik_grad_info_host.argtypes = [P, P, P, P, P, i64, ci, ci, ci, P, ci, ci,
                                                     P, P, P, P, P]
         L.vecchia_covariance_pairs.argtypes = [P, ci, P, ci, i64, P, P, P, P, P, P]
+        L.vecchia_fit.argtypes = [P, P, P, P, P, i64, ci, ci, ci, ci, P, ctypes.POINTER(FitOpts),
+                                  P, P, P, P, P, P, ctypes.POINTER(FitInfo)]
         L.vecchia_loglik_grad_info_noalloc.argtypes = [P, P, P, P, i64, ci, ci, ci, P, ci, ci,
                                                        P, P, P]
         for f in (L.vecchia_create, L.vecchia_destroy, L.vecchia_set_lanes, L.vecchia_set_block_threads,
                   L.vecchia_loglik_grad_info, L.vecchia_loglik_grad_info_host,
                   L.vecchia_covariance_pairs, L.vecchia_nparms, L.vecchia_max_m,
                   L.vecchia_set_timing, L.vecchia_last_timing, L.vecchia_kernels_per_pass,
-                  L.vecchia_loglik_grad_info_noalloc):
+                  L.vecchia_loglik_grad_info_noalloc, L.vecchia_fit, L.vecchia_autotune,
+                  L.vecchia_autotune_save, L.vecchia_autotune_load):
             f.restype = ci
         _lib = L
     return _lib
@@ -119,6 +141,12 @@ class Handle:
         _check(lib().vecchia_last_timing(self._h, ctypes.byref(a), ctypes.byref(b),
                                          ctypes.byref(c)))
         return {"setup": a.value, "pass": b.value, "profile": c.value}
+
+    def autotune_save(self, path: str):
+        _check(lib().vecchia_autotune_save(self._h, path.encode()))
+
+    def autotune_load(self, path: str):
+        _check(lib().vecchia_autotune_load(self._h, path.encode()))
 
     def close(self):
         if self._h:
@@ -183,6 +211,68 @@ def vecchia_loglik_grad_info(locs, y, X, NNarray, covparms, covfun: int, prec="f
                                           _dptr(NNarray), n, d, p, m, _dptr(covparms), covfun,
                                           _PREC[prec], sptr, _dptr(out), _dptr(status)))
     return out, status
+
+
+def vecchia_autotune(locs, y, X, NNarray, covparms, covfun: int, prec="fp64", reps: int = 3,
+                     stream=None, handle: Handle | None = None) -> dict:
+    """Times every kernel mapping on these inputs and records the fastest in the handle
+    (see vecchia_autotune in include/vecchia.h).  Returns lanes, threads and ms."""
+    import torch
+    for t, dt, nm in ((locs, torch.float64, "locs"), (y, torch.float64, "y"),
+                      (X, torch.float64, "X"), (NNarray, torch.int32, "NNarray"),
+                      (covparms, torch.float64, "covparms")):
+        _dev_tensor_check(t, dt, nm)
+    n, d = locs.shape
+    p = X.shape[1]
+    m = NNarray.shape[1] - 1
+    dev = locs.device
+    if handle is None:
+        handle = default_handle(dev.index if dev.index is not None else 0)
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    lanes, threads, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+    _check(lib().vecchia_autotune(handle.ptr, _dptr(locs), _dptr(y), _dptr(X), _dptr(NNarray), n,
+                                  d, p, m, _dptr(covparms), covfun, _PREC[prec],
+                                  ctypes.c_void_p(stream.cuda_stream), reps, ctypes.byref(lanes),
+                                  ctypes.byref(threads), ctypes.byref(ms)))
+    return {"lanes": lanes.value, "threads": threads.value, "ms": ms.value}
+
+
+def vecchia_fit(locs, y, X, NNarray, covfun: int, start, tol: float = 1e-4, maxit: int = 40,
+                max_halvings: int = 10, use_graph: bool = True, prec="fp64", stream=None,
+                handle: Handle | None = None) -> dict:
+    """Fisher scoring on the device (see vecchia_fit in include/vecchia.h).  Data tensors
+    are CUDA tensors as for vecchia_loglik_grad_info; start is a host sequence of q values.
+    Returns theta, betahat, loglik, grad, info (numpy) and status / iters / evals."""
+    import torch
+    for t, dt, nm in ((locs, torch.float64, "locs"), (y, torch.float64, "y"),
+                      (X, torch.float64, "X"), (NNarray, torch.int32, "NNarray")):
+        _dev_tensor_check(t, dt, nm)
+    n, d = locs.shape
+    p = X.shape[1]
+    m = NNarray.shape[1] - 1
+    q = NPARMS[covfun]
+    dev = locs.device
+    if handle is None:
+        handle = default_handle(dev.index if dev.index is not None else 0)
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    st = np.ascontiguousarray(start, dtype=np.float64)
+    opts = FitOpts(tol, maxit, max_halvings, 1 if use_graph else 0, _PREC[prec])
+    info_ = FitInfo()
+    theta = np.empty(q)
+    beta = np.empty(p)
+    ll = ctypes.c_double()
+    grad = np.empty(q)
+    info = np.empty((q, q))
+    P = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    _check(lib().vecchia_fit(handle.ptr, _dptr(locs), _dptr(y), _dptr(X), _dptr(NNarray), n, d,
+                             p, m, covfun, P(st), ctypes.byref(opts),
+                             ctypes.c_void_p(stream.cuda_stream), P(theta), P(beta),
+                             ctypes.byref(ll), P(grad), P(info), ctypes.byref(info_)))
+    return {"theta": theta, "betahat": beta, "loglik": ll.value, "grad": grad, "info": info,
+            "status": info_.status, "iters": info_.iters, "evals": info_.evals,
+            "pass_status": info_.pass_status}
 
 
 def vecchia_loglik_grad_info_noalloc(locs, y, X, NNarray, covparms, covfun: int,

@@ -1,15 +1,18 @@
 // vg_capi.cu -- the extern "C" boundary of the Vecchia library (declared in
 // include/vecchia.h): handles, argument validation, scratch management and launch order.
 #include <climits>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "../../include/vecchia.h"
 #include "vg_internal.h"
 #include "vg_common.cuh"
+#include "vg_fit.h"
 
 namespace {
 
@@ -61,6 +64,11 @@ cudaError_t grow(T** p, size_t* cap, size_t need) {
 
 void vg::set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
 
+struct TuneEntry {
+    int cov, m, d, p, prec, log2n, lanes, threads;
+    float ms;
+};
+
 struct vec_handle_s {
     int device = 0;
     int nsm = 0;
@@ -71,6 +79,16 @@ struct vec_handle_s {
     int timing = 0;
     int traced = 0;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    // Fisher-scoring driver
+    vg::FitState* fs = nullptr;
+    double* fit_out = nullptr;
+    long long* fit_st = nullptr;
+    double* fit_start = nullptr;
+    cudaGraph_t fit_graph = nullptr;
+    cudaGraphExec_t fit_exec = nullptr;
+    unsigned long long fit_key[16] = {0};
+    // autotuned mappings
+    std::vector<TuneEntry> tune;
     // pass scratch
     double* partials = nullptr;
     size_t partials_cap = 0;
@@ -195,6 +213,12 @@ vec_status vecchia_destroy(vec_handle h) {
     cudaFree(h->h_st);
     for (int k = 0; k < 4; ++k)
         if (h->ev[k]) cudaEventDestroy(h->ev[k]);
+    if (h->fit_exec) cudaGraphExecDestroy(h->fit_exec);
+    if (h->fit_graph) cudaGraphDestroy(h->fit_graph);
+    cudaFree(h->fs);
+    cudaFree(h->fit_out);
+    cudaFree(h->fit_st);
+    cudaFree(h->fit_start);
     if (h->stream) cudaStreamDestroy(h->stream);
     delete h;
     return VEC_OK;
@@ -222,6 +246,35 @@ vec_status check_args(const void* locs, const void* y, const void* X, const void
     return VEC_OK;
 }
 
+// Chooses the kernel mapping and makes sure the partial-sum scratch is large enough
+// (the only allocation a pass may need; done before any graph capture).
+int ilog2(int64_t n) {
+    int k = 0;
+    while ((1ll << (k + 1)) <= n) ++k;
+    return k;
+}
+
+vec_status prepare_pass(vec_handle h, int cov, int m, int d, int p, vg::PassPlan* plan,
+                        int64_t n = 0, int prec = 0) {
+    int L = h->lanes, thr = h->threads;
+    if (L == 0 && thr == 0 && n > 0) {
+        const int lg = ilog2(n);
+        for (const TuneEntry& t : h->tune)
+            if (t.cov == cov && t.m == m && t.d == d && t.p == p && t.prec == prec && t.log2n == lg) {
+                L = t.lanes;
+                thr = t.threads;
+            }
+    }
+    int pr = vg::plan_pass(cov, m, d, p, h->nsm, L, thr, plan);
+    if (pr == -1 && (L != h->lanes || thr != h->threads))  // a stale record: plan afresh
+        pr = vg::plan_pass(cov, m, d, p, h->nsm, h->lanes, h->threads, plan);
+    if (pr == -1) return fail(VEC_ERR_UNSUPPORTED, "no kernel mapping fits m = %d, p = %d", m, p);
+    if (pr != 0) return cuda_fail(cudaGetLastError(), "planning the pass kernel");
+    cudaError_t e = grow(&h->partials, &h->partials_cap, (size_t)plan->grid * plan->nstat);
+    if (e != cudaSuccess) return cuda_fail(e, "allocating partial sums");
+    return VEC_OK;
+}
+
 // Enqueues the full pass on `st`.  Device pointers only.
 vec_status enqueue_pass(vec_handle h, const double* locs, const double* y, const double* X,
                         const int32_t* NN, int64_t n, int d, int p, int m,
@@ -229,11 +282,9 @@ vec_status enqueue_pass(vec_handle h, const double* locs, const double* y, const
                         double* out, long long* dev_status) {
     const int cov = (int)covfun;
     vg::PassPlan plan;
-    int pr = vg::plan_pass(cov, m, d, p, h->nsm, h->lanes, h->threads, &plan);
-    if (pr == -1) return fail(VEC_ERR_UNSUPPORTED, "no kernel mapping fits m = %d, p = %d", m, p);
-    if (pr != 0) return cuda_fail(cudaGetLastError(), "planning the pass kernel");
-    cudaError_t e = grow(&h->partials, &h->partials_cap, (size_t)plan.grid * plan.nstat);
-    if (e != cudaSuccess) return cuda_fail(e, "allocating partial sums");
+    vec_status ps = prepare_pass(h, cov, m, d, p, &plan, n, 0);
+    if (ps != VEC_OK) return ps;
+    cudaError_t e;
     const bool tr = h->timing != 0;
     if (tr) cudaEventRecord(h->ev[0], st);
     e = vg::launch_init_status(h->status, h->bad, st);
@@ -330,6 +381,272 @@ vec_status vecchia_loglik_grad_info_host(vec_handle h, const double* locs, const
         return fail((vec_status)code, "pass failed: %s (first observation %lld)",
                     (code >= 0 && code < 4) ? names[code] : "?", (long long)dst[1]);
     }
+    return VEC_OK;
+}
+
+vec_status vecchia_fit(vec_handle h, const double* locs, const double* y, const double* X,
+                       const int32_t* NNarray, int64_t n, int d, int p, int m, vec_covfun covfun,
+                       const double* start, const vec_fit_opts* opts, void* stream,
+                       double* theta_out, double* betahat, double* loglik, double* grad,
+                       double* info, vec_fit_info* fit_info) {
+    if (!h) return fail(VEC_ERR_ARG, "vecchia_fit: NULL handle");
+    vec_fit_opts o = {1e-4, 40, 10, 1, (int)VEC_FP64};
+    if (opts) o = *opts;
+    vec_status s = check_args(locs, y, X, NNarray, n, d, p, m, start, covfun, (vec_precision)o.prec);
+    if (s != VEC_OK) return s;
+    if (!theta_out || !betahat || !loglik || !grad || !info)
+        return fail(VEC_ERR_ARG, "vecchia_fit: an output pointer is NULL");
+    if (!(o.tol >= 0.0) || o.maxit < 0 || o.maxit > 100000 || o.max_halvings < 0 || o.max_halvings > 60)
+        return fail(VEC_ERR_ARG, "vecchia_fit: bad options (tol %g, maxit %d, max_halvings %d)", o.tol,
+                    o.maxit, o.max_halvings);
+    const int q = vecchia_nparms(covfun);
+    for (int j = 0; j < q; ++j)
+        if (!(start[j] > 0.0) || !std::isfinite(start[j]))
+            return fail(VEC_ERR_ARG, "vecchia_fit: start[%d] = %g is not a positive number", j, start[j]);
+    if (covfun == VEC_MATERN_ISO && !(start[2] >= 0.05 && start[2] <= 20.0))
+        return fail(VEC_ERR_ARG, "vecchia_fit: start smoothness %g outside [0.05, 20]", start[2]);
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(VEC_ERR_CUDA, "cannot select device %d", h->device);
+    const int cov = (int)covfun;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSuccess;
+    if (!h->fs) e = cudaMalloc(reinterpret_cast<void**>(&h->fs), sizeof(vg::FitState));
+    if (e == cudaSuccess && !h->fit_out) e = cudaMalloc(reinterpret_cast<void**>(&h->fit_out), sizeof(double) * 32);
+    if (e == cudaSuccess && !h->fit_st) e = cudaMalloc(reinterpret_cast<void**>(&h->fit_st), sizeof(long long) * 2);
+    if (e == cudaSuccess && !h->fit_start) e = cudaMalloc(reinterpret_cast<void**>(&h->fit_start), sizeof(double) * 4);
+    if (e != cudaSuccess) return cuda_fail(e, "vecchia_fit: allocating the fit state");
+    vg::PassPlan plan;
+    s = prepare_pass(h, cov, m, d, p, &plan, n, o.prec);
+    if (s != VEC_OK) return s;
+    const double* theta_trial = h->fs->theta_trial;  // device address of the member
+    // a hard bound on the number of passes, so the device loop always ends
+    const int max_evals = (o.maxit + 2) * (o.max_halvings + 2);
+    e = cudaMemcpyAsync(h->fit_start, start, sizeof(double) * q, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = vg::launch_fit_init(h->fs, h->fit_start, q, st);
+    if (e != cudaSuccess) return cuda_fail(e, "vecchia_fit: initialising");
+    const int saved_timing = h->timing;
+    h->timing = 0;
+    if (o.use_graph) {
+        unsigned long long key[16] = {(unsigned long long)(uintptr_t)locs, (unsigned long long)(uintptr_t)y,
+                                      (unsigned long long)(uintptr_t)X, (unsigned long long)(uintptr_t)NNarray,
+                                      (unsigned long long)n, (unsigned long long)d, (unsigned long long)p,
+                                      (unsigned long long)m, (unsigned long long)cov,
+                                      (unsigned long long)o.prec, (unsigned long long)o.maxit,
+                                      (unsigned long long)o.max_halvings, 0ull,
+                                      (unsigned long long)plan.L, (unsigned long long)plan.threads, 1ull};
+        std::memcpy(&key[12], &o.tol, sizeof(double));
+        if (!h->fit_exec || std::memcmp(key, h->fit_key, sizeof(key)) != 0) {
+            if (h->fit_exec) { cudaGraphExecDestroy(h->fit_exec); h->fit_exec = nullptr; }
+            if (h->fit_graph) { cudaGraphDestroy(h->fit_graph); h->fit_graph = nullptr; }
+            cudaGraph_t graph = nullptr;
+            cudaGraphConditionalHandle cond;
+            cudaGraphNode_t node;
+            e = cudaGraphCreate(&graph, 0);
+            if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault);
+            cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+            cp.conditional.handle = cond;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            if (e == cudaSuccess) e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+            if (e != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                h->timing = saved_timing;
+                return cuda_fail(e, "vecchia_fit: building the iteration graph");
+            }
+            cudaGraph_t body = cp.conditional.phGraph_out[0];
+            e = cudaStreamBeginCaptureToGraph(h->stream, body, nullptr, nullptr, 0,
+                                              cudaStreamCaptureModeRelaxed);
+            vec_status ps = VEC_OK;
+            if (e == cudaSuccess) {
+                ps = enqueue_pass(h, locs, y, X, NNarray, n, d, p, m, theta_trial, covfun, h->stream,
+                                  h->fit_out, h->fit_st);
+                cudaError_t e2 = vg::launch_fit_step(h->fs, h->fit_out, h->fit_st, q, p, cov, o.tol,
+                                                     o.maxit, o.max_halvings, cond, 1, h->stream);
+                cudaGraph_t captured = nullptr;
+                e = cudaStreamEndCapture(h->stream, &captured);
+                if (e == cudaSuccess) e = e2;
+            }
+            if (e == cudaSuccess && ps == VEC_OK) e = cudaGraphInstantiate(&h->fit_exec, graph, 0);
+            if (e != cudaSuccess || ps != VEC_OK) {
+                cudaGraphDestroy(graph);
+                h->fit_exec = nullptr;
+                h->timing = saved_timing;
+                if (ps != VEC_OK) return ps;
+                return cuda_fail(e, "vecchia_fit: capturing the iteration graph");
+            }
+            h->fit_graph = graph;
+            std::memcpy(h->fit_key, key, sizeof(key));
+        }
+        e = cudaGraphLaunch(h->fit_exec, st);
+        if (e != cudaSuccess) {
+            h->timing = saved_timing;
+            return cuda_fail(e, "vecchia_fit: launching the iteration graph");
+        }
+    } else {
+        for (int ev = 0; ev < max_evals; ++ev) {
+            s = enqueue_pass(h, locs, y, X, NNarray, n, d, p, m, theta_trial, covfun, st,
+                             h->fit_out, h->fit_st);
+            if (s != VEC_OK) { h->timing = saved_timing; return s; }
+            cudaGraphConditionalHandle none = 0;
+            e = vg::launch_fit_step(h->fs, h->fit_out, h->fit_st, q, p, cov, o.tol, o.maxit,
+                                    o.max_halvings, none, 0, st);
+            int done = 0;
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(&done, &h->fs->done, sizeof(int), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) { h->timing = saved_timing; return cuda_fail(e, "vecchia_fit: iterating"); }
+            if (done) break;
+        }
+    }
+    h->timing = saved_timing;
+    vg::FitState fs;
+    e = cudaMemcpyAsync(&fs, h->fs, sizeof(fs), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "vecchia_fit: reading the result");
+    for (int j = 0; j < q; ++j) { theta_out[j] = fs.theta_cur[j]; grad[j] = fs.grad[j]; }
+    for (int t = 0; t < q * q; ++t) info[t] = fs.info[t];
+    for (int a = 0; a < p; ++a) betahat[a] = fs.beta[a];
+    *loglik = fs.loglik;
+    if (fit_info) {
+        fit_info->status = fs.done ? fs.status : vg::FIT_MAXIT;
+        fit_info->iters = fs.iters;
+        fit_info->evals = fs.evals;
+        fit_info->pass_status = fs.pass_status;
+    }
+    return VEC_OK;
+}
+
+vec_status vecchia_autotune(vec_handle h, const double* locs, const double* y, const double* X,
+                            const int32_t* NNarray, int64_t n, int d, int p, int m,
+                            const double* covparms, vec_covfun covfun, vec_precision prec,
+                            void* stream, int reps, int* lanes_out, int* threads_out,
+                            float* ms_out) {
+    if (!h) return fail(VEC_ERR_ARG, "vecchia_autotune: NULL handle");
+    vec_status s = check_args(locs, y, X, NNarray, n, d, p, m, covparms, covfun, prec);
+    if (s != VEC_OK) return s;
+    if (reps < 1) reps = 1;
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(VEC_ERR_CUDA, "cannot select device %d", h->device);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int cov = (int)covfun;
+    const int q = vecchia_nparms(covfun);
+    double* out = nullptr;
+    long long* dst = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&out), sizeof(double) * (1 + q + q * q + p));
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&dst), sizeof(long long) * 2);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    const int saved_L = h->lanes, saved_T = h->threads, saved_timing = h->timing;
+    h->timing = 0;
+    int bestL = 0, bestT = 0;
+    float best = 1e30f;
+    static const int thr_list[] = {256, 128, 64};
+    for (int ti = 0; ti < 3 && e == cudaSuccess; ++ti) {
+        for (int L = 1; L <= 32 && e == cudaSuccess; L *= 2) {
+            if (L > thr_list[ti]) continue;
+            vg::PassPlan plan;
+            if (vg::plan_pass(cov, m, d, p, h->nsm, L, thr_list[ti], &plan) != 0) continue;
+            if (plan.L != L || plan.threads != thr_list[ti]) continue;
+            h->lanes = L;
+            h->threads = thr_list[ti];
+            s = enqueue_pass(h, locs, y, X, NNarray, n, d, p, m, covparms, covfun, st, out, dst);
+            if (s != VEC_OK) break;
+            float tmin = 1e30f;
+            for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+                e = cudaEventRecord(e0, st);
+                s = enqueue_pass(h, locs, y, X, NNarray, n, d, p, m, covparms, covfun, st, out, dst);
+                if (s != VEC_OK) break;
+                if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < tmin) tmin = ms;
+            }
+            if (s != VEC_OK) break;
+            if (tmin < best) { best = tmin; bestL = L; bestT = thr_list[ti]; }
+        }
+        if (s != VEC_OK) break;
+    }
+    h->lanes = saved_L;
+    h->threads = saved_T;
+    h->timing = saved_timing;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(out);
+    cudaFree(dst);
+    if (s != VEC_OK) return s;
+    if (e != cudaSuccess) return cuda_fail(e, "vecchia_autotune");
+    if (bestL == 0) return fail(VEC_ERR_UNSUPPORTED, "vecchia_autotune: no mapping fits");
+    TuneEntry t = {cov, m, d, p, (int)prec, ilog2(n), bestL, bestT, best};
+    bool replaced = false;
+    for (TuneEntry& u : h->tune)
+        if (u.cov == t.cov && u.m == t.m && u.d == t.d && u.p == t.p && u.prec == t.prec &&
+            u.log2n == t.log2n) { u = t; replaced = true; }
+    if (!replaced) h->tune.push_back(t);
+    if (lanes_out) *lanes_out = bestL;
+    if (threads_out) *threads_out = bestT;
+    if (ms_out) *ms_out = best;
+    return VEC_OK;
+}
+
+vec_status vecchia_autotune_save(vec_handle h, const char* path) {
+    if (!h || !path) return fail(VEC_ERR_ARG, "vecchia_autotune_save: NULL argument");
+    FILE* f = std::fopen(path, "w");
+    if (!f) return fail(VEC_ERR_ARG, "vecchia_autotune_save: cannot open %s", path);
+    std::fprintf(f, "[\n");
+    for (size_t i = 0; i < h->tune.size(); ++i) {
+        const TuneEntry& t = h->tune[i];
+        std::fprintf(f, "  {\"covfun\": %d, \"m\": %d, \"d\": %d, \"p\": %d, \"prec\": %d, "
+                        "\"log2n\": %d, \"lanes\": %d, \"threads\": %d, \"ms\": %.6f}%s\n",
+                     t.cov, t.m, t.d, t.p, t.prec, t.log2n, t.lanes, t.threads, t.ms,
+                     i + 1 < h->tune.size() ? "," : "");
+    }
+    std::fprintf(f, "]\n");
+    std::fclose(f);
+    return VEC_OK;
+}
+
+vec_status vecchia_autotune_load(vec_handle h, const char* path) {
+    if (!h || !path) return fail(VEC_ERR_ARG, "vecchia_autotune_load: NULL argument");
+    FILE* f = std::fopen(path, "r");
+    if (!f) return fail(VEC_ERR_ARG, "vecchia_autotune_load: cannot open %s", path);
+    std::string txt;
+    char buf[4096];
+    size_t k;
+    while ((k = std::fread(buf, 1, sizeof(buf), f)) > 0) txt.append(buf, k);
+    std::fclose(f);
+    // one record per {...}; every key must be present
+    size_t pos = 0;
+    int loaded = 0;
+    while ((pos = txt.find('{', pos)) != std::string::npos) {
+        size_t end = txt.find('}', pos);
+        if (end == std::string::npos) break;
+        std::string rec = txt.substr(pos, end - pos);
+        auto get = [&](const char* key, double* v) {
+            std::string pat = std::string("\"") + key + "\"";
+            size_t at = rec.find(pat);
+            if (at == std::string::npos) return false;
+            at = rec.find(':', at);
+            if (at == std::string::npos) return false;
+            return std::sscanf(rec.c_str() + at + 1, "%lf", v) == 1;
+        };
+        double v[9];
+        const char* keys[9] = {"covfun", "m", "d", "p", "prec", "log2n", "lanes", "threads", "ms"};
+        bool ok = true;
+        for (int i = 0; i < 9 && ok; ++i) ok = get(keys[i], &v[i]);
+        if (!ok) return fail(VEC_ERR_ARG, "vecchia_autotune_load: malformed record in %s", path);
+        TuneEntry t = {(int)v[0], (int)v[1], (int)v[2], (int)v[3], (int)v[4], (int)v[5], (int)v[6],
+                       (int)v[7], (float)v[8]};
+        bool replaced = false;
+        for (TuneEntry& u : h->tune)
+            if (u.cov == t.cov && u.m == t.m && u.d == t.d && u.p == t.p && u.prec == t.prec &&
+                u.log2n == t.log2n) { u = t; replaced = true; }
+        if (!replaced) h->tune.push_back(t);
+        ++loaded;
+        pos = end + 1;
+    }
+    (void)loaded;
     return VEC_OK;
 }
 
