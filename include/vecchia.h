@@ -184,14 +184,16 @@ typedef struct {
     int max_halvings;   /* step halvings tried before giving up (10)                        */
     int use_graph;      /* 1: all iterations inside one CUDA graph with a WHILE node (1);
                            0: one host round trip per iteration                             */
-    int prec;           /* vec_precision of the passes (VEC_FP64)                           */
+    int prec;           /* VEC_FP64 (default): FP64 passes throughout.  VEC_MIXED: mixed-
+                           precision passes until convergence, then FP64 passes from that
+                           point until convergence again (the results are FP64 results)    */
 } vec_fit_opts;
 
 /* Outcome of vecchia_fit. */
 typedef struct {
     int status;         /* 0 converged, 1 iteration limit, 2 no ascent step, 3 start failed */
-    int iters;          /* accepted Fisher steps                                            */
-    int evals;          /* likelihood passes run (accepted steps + halvings + 1)            */
+    int iters;          /* accepted Fisher steps (both phases for VEC_MIXED)                */
+    int evals;          /* likelihood passes run (accepted steps + halvings + 1 per phase)  */
     int pass_status;    /* vec_status of the last pass                                      */
 } vec_fit_info;
 

@@ -84,15 +84,17 @@ struct vec_handle_s {
     double* fit_out = nullptr;
     long long* fit_st = nullptr;
     double* fit_start = nullptr;
-    cudaGraph_t fit_graph = nullptr;
-    cudaGraphExec_t fit_exec = nullptr;
-    unsigned long long fit_key[16] = {0};
+    cudaGraph_t fit_graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t fit_exec[2] = {nullptr, nullptr};
+    unsigned long long fit_key[2][16] = {{0}, {0}};
+    int fit_lru = 0;
     // autotuned mappings
     std::vector<TuneEntry> tune;
     // pass scratch
     double* partials = nullptr;
     size_t partials_cap = 0;
     double* mtab = nullptr;
+    float* mtabf = nullptr;
     int* status = nullptr;
     long long* bad = nullptr;
     // staging for the host-memory entry point
@@ -186,6 +188,8 @@ vec_status vecchia_create(vec_handle* out, int device) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&h->mtab),
                                          sizeof(double) * vg::mtab_doubles());
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&h->mtabf),
+                                         sizeof(float) * vg::mtab_floats());
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&h->status), sizeof(int) * 4);
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&h->bad), sizeof(long long) * 2);
     if (e != cudaSuccess) {
@@ -202,6 +206,7 @@ vec_status vecchia_destroy(vec_handle h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     cudaFree(h->partials);
     cudaFree(h->mtab);
+    cudaFree(h->mtabf);
     cudaFree(h->status);
     cudaFree(h->bad);
     cudaFree(h->h_locs);
@@ -213,8 +218,10 @@ vec_status vecchia_destroy(vec_handle h) {
     cudaFree(h->h_st);
     for (int k = 0; k < 4; ++k)
         if (h->ev[k]) cudaEventDestroy(h->ev[k]);
-    if (h->fit_exec) cudaGraphExecDestroy(h->fit_exec);
-    if (h->fit_graph) cudaGraphDestroy(h->fit_graph);
+    for (int k = 0; k < 2; ++k) {
+        if (h->fit_exec[k]) cudaGraphExecDestroy(h->fit_exec[k]);
+        if (h->fit_graph[k]) cudaGraphDestroy(h->fit_graph[k]);
+    }
     cudaFree(h->fs);
     cudaFree(h->fit_out);
     cudaFree(h->fit_st);
@@ -242,7 +249,6 @@ vec_status check_args(const void* locs, const void* y, const void* X, const void
     if (m < 0 || m > vg::KMAX - 1)
         return fail(VEC_ERR_UNSUPPORTED, "m = %d out of range [0, %d]", m, vg::KMAX - 1);
     if (prec != VEC_FP64 && prec != VEC_MIXED) return fail(VEC_ERR_ARG, "unknown precision %d", (int)prec);
-    if (prec == VEC_MIXED) return fail(VEC_ERR_UNSUPPORTED, "mixed precision is not available in this build");
     return VEC_OK;
 }
 
@@ -265,9 +271,9 @@ vec_status prepare_pass(vec_handle h, int cov, int m, int d, int p, vg::PassPlan
                 thr = t.threads;
             }
     }
-    int pr = vg::plan_pass(cov, m, d, p, h->nsm, L, thr, plan);
+    int pr = vg::plan_pass(cov, m, d, p, h->nsm, L, thr, plan, prec);
     if (pr == -1 && (L != h->lanes || thr != h->threads))  // a stale record: plan afresh
-        pr = vg::plan_pass(cov, m, d, p, h->nsm, h->lanes, h->threads, plan);
+        pr = vg::plan_pass(cov, m, d, p, h->nsm, h->lanes, h->threads, plan, prec);
     if (pr == -1) return fail(VEC_ERR_UNSUPPORTED, "no kernel mapping fits m = %d, p = %d", m, p);
     if (pr != 0) return cuda_fail(cudaGetLastError(), "planning the pass kernel");
     cudaError_t e = grow(&h->partials, &h->partials_cap, (size_t)plan->grid * plan->nstat);
@@ -279,20 +285,22 @@ vec_status prepare_pass(vec_handle h, int cov, int m, int d, int p, vg::PassPlan
 vec_status enqueue_pass(vec_handle h, const double* locs, const double* y, const double* X,
                         const int32_t* NN, int64_t n, int d, int p, int m,
                         const double* covparms, vec_covfun covfun, cudaStream_t st,
-                        double* out, long long* dev_status) {
+                        double* out, long long* dev_status, int prec) {
     const int cov = (int)covfun;
     vg::PassPlan plan;
-    vec_status ps = prepare_pass(h, cov, m, d, p, &plan, n, 0);
+    vec_status ps = prepare_pass(h, cov, m, d, p, &plan, n, prec);
     if (ps != VEC_OK) return ps;
     cudaError_t e;
     const bool tr = h->timing != 0;
     if (tr) cudaEventRecord(h->ev[0], st);
     e = vg::launch_init_status(h->status, h->bad, st);
-    if (e == cudaSuccess && cov == vg::COV_MATERN) e = vg::launch_mtab_build(covparms, h->mtab, st);
+    if (e == cudaSuccess && cov == vg::COV_MATERN)
+        e = vg::launch_mtab_build(covparms, h->mtab, prec ? h->mtabf : nullptr, st);
     if (e != cudaSuccess) return cuda_fail(e, "launching the setup kernels");
     vg::PassArgs a;
     a.locs = locs; a.y = y; a.X = X; a.NN = NN; a.covparms = covparms;
-    a.mtab = h->mtab; a.partials = h->partials; a.status = h->status; a.bad = h->bad;
+    a.mtab = h->mtab; a.mtabf = h->mtabf; a.partials = h->partials; a.status = h->status;
+    a.bad = h->bad;
     a.n = n; a.d = d; a.p = p; a.m = m;
     a.nstat = plan.nstat; a.nv = plan.nv; a.slot_stride = plan.slot_stride;
     a.acc_per_lane = plan.acc_per_lane; a.tab_in_smem = plan.tab_smem;
@@ -327,7 +335,7 @@ vec_status vecchia_loglik_grad_info(vec_handle h, const double* locs, const doub
     if (!g.ok) return fail(VEC_ERR_CUDA, "cannot select device %d", h->device);
     return enqueue_pass(h, locs, y, X, NNarray, n, d, p, m, covparms, covfun,
                         reinterpret_cast<cudaStream_t>(stream), out,
-                        reinterpret_cast<long long*>(dev_status));
+                        reinterpret_cast<long long*>(dev_status), (int)prec);
 }
 
 vec_status vecchia_loglik_grad_info_host(vec_handle h, const double* locs, const double* y,
@@ -361,7 +369,7 @@ vec_status vecchia_loglik_grad_info_host(vec_handle h, const double* locs, const
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->h_cov, covparms, sizeof(double) * q, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(e, "copying inputs to the device");
     s = enqueue_pass(h, h->h_locs, h->h_y, h->h_X, h->h_NN, n, d, p, m, h->h_cov, covfun, st,
-                     h->h_out, h->h_st);
+                     h->h_out, h->h_st, (int)prec);
     if (s != VEC_OK) return s;
     double res[1 + 4 + 16 + vg::PMAX];
     long long dst[2];
@@ -415,87 +423,109 @@ vec_status vecchia_fit(vec_handle h, const double* locs, const double* y, const 
     if (e == cudaSuccess && !h->fit_st) e = cudaMalloc(reinterpret_cast<void**>(&h->fit_st), sizeof(long long) * 2);
     if (e == cudaSuccess && !h->fit_start) e = cudaMalloc(reinterpret_cast<void**>(&h->fit_start), sizeof(double) * 4);
     if (e != cudaSuccess) return cuda_fail(e, "vecchia_fit: allocating the fit state");
-    vg::PassPlan plan;
-    s = prepare_pass(h, cov, m, d, p, &plan, n, o.prec);
-    if (s != VEC_OK) return s;
     const double* theta_trial = h->fs->theta_trial;  // device address of the member
     // a hard bound on the number of passes, so the device loop always ends
     const int max_evals = (o.maxit + 2) * (o.max_halvings + 2);
     e = cudaMemcpyAsync(h->fit_start, start, sizeof(double) * q, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = vg::launch_fit_init(h->fs, h->fit_start, q, st);
     if (e != cudaSuccess) return cuda_fail(e, "vecchia_fit: initialising");
     const int saved_timing = h->timing;
     h->timing = 0;
-    if (o.use_graph) {
-        unsigned long long key[16] = {(unsigned long long)(uintptr_t)locs, (unsigned long long)(uintptr_t)y,
-                                      (unsigned long long)(uintptr_t)X, (unsigned long long)(uintptr_t)NNarray,
-                                      (unsigned long long)n, (unsigned long long)d, (unsigned long long)p,
-                                      (unsigned long long)m, (unsigned long long)cov,
-                                      (unsigned long long)o.prec, (unsigned long long)o.maxit,
-                                      (unsigned long long)o.max_halvings, 0ull,
-                                      (unsigned long long)plan.L, (unsigned long long)plan.threads, 1ull};
-        std::memcpy(&key[12], &o.tol, sizeof(double));
-        if (!h->fit_exec || std::memcmp(key, h->fit_key, sizeof(key)) != 0) {
-            if (h->fit_exec) { cudaGraphExecDestroy(h->fit_exec); h->fit_exec = nullptr; }
-            if (h->fit_graph) { cudaGraphDestroy(h->fit_graph); h->fit_graph = nullptr; }
-            cudaGraph_t graph = nullptr;
-            cudaGraphConditionalHandle cond;
-            cudaGraphNode_t node;
-            e = cudaGraphCreate(&graph, 0);
-            if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault);
-            cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
-            cp.conditional.handle = cond;
-            cp.conditional.type = cudaGraphCondTypeWhile;
-            cp.conditional.size = 1;
-            if (e == cudaSuccess) e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+    // phases: a mixed-precision fit first (when asked), then FP64 from where it stopped
+    const int nphase = (o.prec == (int)VEC_MIXED) ? 2 : 1;
+    int total_iters = 0, total_evals = 0;
+    for (int phase = 0; phase < nphase; ++phase) {
+        const int prec = (nphase == 2 && phase == 0) ? 1 : 0;
+        const double* phase_start = (phase == 0) ? h->fit_start : h->fs->theta_cur;
+        vg::PassPlan pplan;
+        s = prepare_pass(h, cov, m, d, p, &pplan, n, prec);
+        if (s != VEC_OK) { h->timing = saved_timing; return s; }
+        e = vg::launch_fit_init(h->fs, phase_start, q, st);
+        if (e != cudaSuccess) { h->timing = saved_timing; return cuda_fail(e, "vecchia_fit: initialising"); }
+        if (o.use_graph) {
+            unsigned long long key[16] = {(unsigned long long)(uintptr_t)locs, (unsigned long long)(uintptr_t)y,
+                                          (unsigned long long)(uintptr_t)X, (unsigned long long)(uintptr_t)NNarray,
+                                          (unsigned long long)n, (unsigned long long)d, (unsigned long long)p,
+                                          (unsigned long long)m, (unsigned long long)cov,
+                                          (unsigned long long)prec, (unsigned long long)o.maxit,
+                                          (unsigned long long)o.max_halvings, 0ull,
+                                          (unsigned long long)pplan.L, (unsigned long long)pplan.threads, 1ull};
+            std::memcpy(&key[12], &o.tol, sizeof(double));
+            int slot = -1;
+            for (int k = 0; k < 2; ++k)
+                if (h->fit_exec[k] && std::memcmp(key, h->fit_key[k], sizeof(key)) == 0) slot = k;
+            if (slot < 0) {
+                slot = h->fit_lru;
+                h->fit_lru ^= 1;
+                if (h->fit_exec[slot]) { cudaGraphExecDestroy(h->fit_exec[slot]); h->fit_exec[slot] = nullptr; }
+                if (h->fit_graph[slot]) { cudaGraphDestroy(h->fit_graph[slot]); h->fit_graph[slot] = nullptr; }
+                cudaGraph_t graph = nullptr;
+                cudaGraphConditionalHandle cond;
+                cudaGraphNode_t node;
+                e = cudaGraphCreate(&graph, 0);
+                if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault);
+                cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+                cp.conditional.handle = cond;
+                cp.conditional.type = cudaGraphCondTypeWhile;
+                cp.conditional.size = 1;
+                if (e == cudaSuccess) e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+                if (e != cudaSuccess) {
+                    if (graph) cudaGraphDestroy(graph);
+                    h->timing = saved_timing;
+                    return cuda_fail(e, "vecchia_fit: building the iteration graph");
+                }
+                cudaGraph_t body = cp.conditional.phGraph_out[0];
+                e = cudaStreamBeginCaptureToGraph(h->stream, body, nullptr, nullptr, 0,
+                                                  cudaStreamCaptureModeRelaxed);
+                vec_status ps = VEC_OK;
+                if (e == cudaSuccess) {
+                    ps = enqueue_pass(h, locs, y, X, NNarray, n, d, p, m, theta_trial, covfun, h->stream,
+                                      h->fit_out, h->fit_st, prec);
+                    cudaError_t e2 = vg::launch_fit_step(h->fs, h->fit_out, h->fit_st, q, p, cov, o.tol,
+                                                         o.maxit, o.max_halvings, cond, 1, h->stream);
+                    cudaGraph_t captured = nullptr;
+                    e = cudaStreamEndCapture(h->stream, &captured);
+                    if (e == cudaSuccess) e = e2;
+                }
+                if (e == cudaSuccess && ps == VEC_OK) e = cudaGraphInstantiate(&h->fit_exec[slot], graph, 0);
+                if (e != cudaSuccess || ps != VEC_OK) {
+                    cudaGraphDestroy(graph);
+                    h->fit_exec[slot] = nullptr;
+                    h->timing = saved_timing;
+                    if (ps != VEC_OK) return ps;
+                    return cuda_fail(e, "vecchia_fit: capturing the iteration graph");
+                }
+                h->fit_graph[slot] = graph;
+                std::memcpy(h->fit_key[slot], key, sizeof(key));
+            }
+            e = cudaGraphLaunch(h->fit_exec[slot], st);
             if (e != cudaSuccess) {
-                if (graph) cudaGraphDestroy(graph);
                 h->timing = saved_timing;
-                return cuda_fail(e, "vecchia_fit: building the iteration graph");
+                return cuda_fail(e, "vecchia_fit: launching the iteration graph");
             }
-            cudaGraph_t body = cp.conditional.phGraph_out[0];
-            e = cudaStreamBeginCaptureToGraph(h->stream, body, nullptr, nullptr, 0,
-                                              cudaStreamCaptureModeRelaxed);
-            vec_status ps = VEC_OK;
-            if (e == cudaSuccess) {
-                ps = enqueue_pass(h, locs, y, X, NNarray, n, d, p, m, theta_trial, covfun, h->stream,
-                                  h->fit_out, h->fit_st);
-                cudaError_t e2 = vg::launch_fit_step(h->fs, h->fit_out, h->fit_st, q, p, cov, o.tol,
-                                                     o.maxit, o.max_halvings, cond, 1, h->stream);
-                cudaGraph_t captured = nullptr;
-                e = cudaStreamEndCapture(h->stream, &captured);
-                if (e == cudaSuccess) e = e2;
+        } else {
+            for (int ev = 0; ev < max_evals; ++ev) {
+                s = enqueue_pass(h, locs, y, X, NNarray, n, d, p, m, theta_trial, covfun, st,
+                                 h->fit_out, h->fit_st, prec);
+                if (s != VEC_OK) { h->timing = saved_timing; return s; }
+                cudaGraphConditionalHandle none = 0;
+                e = vg::launch_fit_step(h->fs, h->fit_out, h->fit_st, q, p, cov, o.tol, o.maxit,
+                                        o.max_halvings, none, 0, st);
+                int done = 0;
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(&done, &h->fs->done, sizeof(int), cudaMemcpyDeviceToHost, st);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+                if (e != cudaSuccess) { h->timing = saved_timing; return cuda_fail(e, "vecchia_fit: iterating"); }
+                if (done) break;
             }
-            if (e == cudaSuccess && ps == VEC_OK) e = cudaGraphInstantiate(&h->fit_exec, graph, 0);
-            if (e != cudaSuccess || ps != VEC_OK) {
-                cudaGraphDestroy(graph);
-                h->fit_exec = nullptr;
-                h->timing = saved_timing;
-                if (ps != VEC_OK) return ps;
-                return cuda_fail(e, "vecchia_fit: capturing the iteration graph");
-            }
-            h->fit_graph = graph;
-            std::memcpy(h->fit_key, key, sizeof(key));
         }
-        e = cudaGraphLaunch(h->fit_exec, st);
-        if (e != cudaSuccess) {
-            h->timing = saved_timing;
-            return cuda_fail(e, "vecchia_fit: launching the iteration graph");
-        }
-    } else {
-        for (int ev = 0; ev < max_evals; ++ev) {
-            s = enqueue_pass(h, locs, y, X, NNarray, n, d, p, m, theta_trial, covfun, st,
-                             h->fit_out, h->fit_st);
-            if (s != VEC_OK) { h->timing = saved_timing; return s; }
-            cudaGraphConditionalHandle none = 0;
-            e = vg::launch_fit_step(h->fs, h->fit_out, h->fit_st, q, p, cov, o.tol, o.maxit,
-                                    o.max_halvings, none, 0, st);
-            int done = 0;
-            if (e == cudaSuccess)
-                e = cudaMemcpyAsync(&done, &h->fs->done, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (nphase == 2 && phase == 0) {
+            vg::FitState f0;
+            e = cudaMemcpyAsync(&f0, h->fs, sizeof(f0), cudaMemcpyDeviceToHost, st);
             if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-            if (e != cudaSuccess) { h->timing = saved_timing; return cuda_fail(e, "vecchia_fit: iterating"); }
-            if (done) break;
+            if (e != cudaSuccess) { h->timing = saved_timing; return cuda_fail(e, "vecchia_fit: reading phase 1"); }
+            total_iters += f0.iters;
+            total_evals += f0.evals;
+            if (f0.status == vg::FIT_START_FAILED) break;  // the FP64 phase starts from the same point
         }
     }
     h->timing = saved_timing;
@@ -509,8 +539,8 @@ vec_status vecchia_fit(vec_handle h, const double* locs, const double* y, const 
     *loglik = fs.loglik;
     if (fit_info) {
         fit_info->status = fs.done ? fs.status : vg::FIT_MAXIT;
-        fit_info->iters = fs.iters;
-        fit_info->evals = fs.evals;
+        fit_info->iters = total_iters + fs.iters;
+        fit_info->evals = total_evals + fs.evals;
         fit_info->pass_status = fs.pass_status;
     }
     return VEC_OK;
@@ -546,16 +576,18 @@ vec_status vecchia_autotune(vec_handle h, const double* locs, const double* y, c
         for (int L = 1; L <= 32 && e == cudaSuccess; L *= 2) {
             if (L > thr_list[ti]) continue;
             vg::PassPlan plan;
-            if (vg::plan_pass(cov, m, d, p, h->nsm, L, thr_list[ti], &plan) != 0) continue;
+            if (vg::plan_pass(cov, m, d, p, h->nsm, L, thr_list[ti], &plan, (int)prec) != 0) continue;
             if (plan.L != L || plan.threads != thr_list[ti]) continue;
             h->lanes = L;
             h->threads = thr_list[ti];
-            s = enqueue_pass(h, locs, y, X, NNarray, n, d, p, m, covparms, covfun, st, out, dst);
+            s = enqueue_pass(h, locs, y, X, NNarray, n, d, p, m, covparms, covfun, st, out, dst,
+                             (int)prec);
             if (s != VEC_OK) break;
             float tmin = 1e30f;
             for (int r = 0; r < reps && e == cudaSuccess; ++r) {
                 e = cudaEventRecord(e0, st);
-                s = enqueue_pass(h, locs, y, X, NNarray, n, d, p, m, covparms, covfun, st, out, dst);
+                s = enqueue_pass(h, locs, y, X, NNarray, n, d, p, m, covparms, covfun, st, out, dst,
+                                 (int)prec);
                 if (s != VEC_OK) break;
                 if (e == cudaSuccess) e = cudaEventRecord(e1, st);
                 if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -664,7 +696,7 @@ vec_status vecchia_covariance_pairs(vec_handle h, vec_covfun covfun, const doubl
     if (!g.ok) return fail(VEC_ERR_CUDA, "cannot select device %d", h->device);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = cudaSuccess;
-    if (covfun == VEC_MATERN_ISO) e = vg::launch_mtab_build(covparms, h->mtab, st);
+    if (covfun == VEC_MATERN_ISO) e = vg::launch_mtab_build(covparms, h->mtab, nullptr, st);
     if (e == cudaSuccess)
         e = vg::launch_cov_pairs((int)covfun, covparms, h->mtab, d, npairs, la, lb, same, C, dC, st);
     if (e != cudaSuccess) return cuda_fail(e, "vecchia_covariance_pairs");

@@ -28,6 +28,9 @@ constexpr int MT_FSTRIDE = MT_NHEAD + 3;       // double slots per function
 constexpr int MT_NINT = (MT_E1 - MT_E0) * MT_J;
 constexpr int MT_PER_INT = 3 * MT_FSTRIDE;     // F0, F1, F2 per interval
 constexpr int MT_DOUBLES = MT_NINT * MT_PER_INT;
+// FP32 copy for the mixed path: 13 FP32 coefficients per function and interval
+constexpr int MT_PER_INT_F = 3 * MT_NC;
+constexpr int MT_FLOATS = MT_NINT * MT_PER_INT_F;
 
 __host__ __device__ constexpr int nparms(int cov) { return cov == COV_EXP ? 3 : 4; }
 // number of covariance parameters whose derivative matrix needs a per-pair evaluation
@@ -88,6 +91,7 @@ struct PassArgs {
     const int32_t* __restrict__ NN;
     const double* __restrict__ covparms;
     const double* __restrict__ mtab;   // Matern table (global), or nullptr
+    const float* __restrict__ mtabf;   // FP32 Matern table for the mixed path, or nullptr
     double* __restrict__ partials;     // [gridDim.x][nstat]
     int* status;                       // [0] status code
     long long* bad;                    // first failing observation

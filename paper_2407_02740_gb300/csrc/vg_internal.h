@@ -17,19 +17,23 @@ struct PassPlan {
     int tab_smem;      // Matern table staged in shared memory
     int nstat;         // doubles per partial record
     int nv;            // per-observation value count
-    int slot_stride;   // doubles per shared-memory slot
+    int slot_stride;   // bytes per shared-memory slot
     int acc_per_lane;  // accumulator doubles per thread
+    int prec;          // 0 = FP64 kernel, 1 = mixed (FP32 block) kernel
 };
 
 // Chooses the lanes-per-observation mapping that fits shared memory (or the forced one).
 // Returns 0 on success, -1 if no mapping fits, -2 on a CUDA error.
 int plan_pass(int cov, int m, int d, int p, int nsm, int force_L, int force_threads,
-              PassPlan* plan);
-size_t pass_smem_bytes(int cov, int m, int d, int p, int L, int threads, bool tab_smem);
+              PassPlan* plan, int prec = 0);
+size_t pass_smem_bytes(int cov, int m, int d, int p, int L, int threads, bool tab_smem,
+                       int prec = 0);
+const void* pass_kernel_f64(int cov, int L);
+const void* pass_kernel_f32(int cov, int L);
 
 cudaError_t launch_pass(int cov, const PassPlan& plan, const PassArgs& args, cudaStream_t st);
 cudaError_t launch_init_status(int* status, long long* bad, cudaStream_t st);
-cudaError_t launch_mtab_build(const double* covparms, double* tab, cudaStream_t st);
+cudaError_t launch_mtab_build(const double* covparms, double* tab, float* tabf, cudaStream_t st);
 cudaError_t launch_profile(const double* partials, int nblk, int nstat, int p, int cov,
                            long long n, const double* covparms, const int* status,
                            const long long* bad, double* out, long long* dev_status,
@@ -38,6 +42,7 @@ cudaError_t launch_cov_pairs(int cov, const double* covparms, const double* tab,
                              long long npairs, const double* la, const double* lb,
                              const int32_t* same, double* C, double* dC, cudaStream_t st);
 int mtab_doubles();
+int mtab_floats();
 
 // Records the thread-local message returned by vecchia_last_error().
 void set_last_error(const char* msg);

@@ -11,9 +11,75 @@
 #include <cstdio>
 
 #include "vg_internal.h"
+#include "vg_matern.cuh"
 #include "vg_pass.cuh"
 
 namespace vg {
+
+// Table builder: one block of MT_NC warps per interval; warp i evaluates interpolation
+// node i, then three threads turn node values into monomial coefficients in w.
+// nu is read from covparms[2]; invalid nu leaves the table untouched (the pass reports
+// the parameter error).
+__global__ void __launch_bounds__(MT_NC * 32) k_mtab_build(const double* __restrict__ covparms,
+                                                           double* __restrict__ tab,
+                                                           float* __restrict__ tabf) {
+    __shared__ double vals[3][MT_NC];
+    const double nu = covparms[2];
+    if (!(nu >= 0.05 && nu <= 20.0)) return;
+    const int it = blockIdx.x;
+    const int e = MT_E0 + it / MT_J, j = it % MT_J;
+    const double hw = 1.0 / (2.0 * MT_J);
+    const double cen = 1.0 + (double)(2 * j + 1) / (double)(2 * MT_J);
+    const double PI = 3.14159265358979323846;
+    const int node = threadIdx.x >> 5;
+    {
+        double u = cos(PI * (node + 0.5) / MT_NC);
+        double s = ldexp(cen + hw * u, e);
+        double psi = dev_digamma(nu), lg = lgamma(nu);
+        double f0, f1, f2;
+        matern_direct_warp(nu, sqrt(s), psi, lg, f0, f1, f2);
+        if ((threadIdx.x & 31) == 0) { vals[0][node] = f0; vals[1][node] = f1; vals[2][node] = f2; }
+    }
+    __syncthreads();
+    const int i = threadIdx.x;
+    if (i < 3) {
+        double a[MT_NC];
+        for (int k = 0; k < MT_NC; ++k) {
+            double acc = 0.0;
+            for (int q = 0; q < MT_NC; ++q) acc += vals[i][q] * cos(PI * k * (q + 0.5) / MT_NC);
+            a[k] = acc * (2.0 / MT_NC);
+        }
+        a[0] *= 0.5;
+        // sum_k a_k T_k(u) -> monomials in u, via T_{k+1} = 2u T_k - T_{k-1}
+        double mono[MT_NC], Tm[MT_NC], Tc[MT_NC], Tn[MT_NC];
+        for (int k = 0; k < MT_NC; ++k) { mono[k] = 0.0; Tm[k] = 0.0; Tc[k] = 0.0; }
+        Tm[0] = 1.0;            // T_0
+        Tc[1] = 1.0;            // T_1
+        mono[0] = a[0];
+        for (int k = 0; k < MT_NC; ++k) mono[k] += a[1] * Tc[k];
+        for (int deg = 2; deg < MT_NC; ++deg) {
+            for (int k = 0; k < MT_NC; ++k) Tn[k] = -Tm[k] + (k > 0 ? 2.0 * Tc[k - 1] : 0.0);
+            for (int k = 0; k < MT_NC; ++k) { mono[k] += a[deg] * Tn[k]; Tm[k] = Tc[k]; Tc[k] = Tn[k]; }
+        }
+        // u = w / hw: coefficient of w^k is mono_k / hw^k (exact power-of-two scaling);
+        // w^0..w^7 stored in FP64, w^8..w^12 in FP32 (see horner_split)
+        double* out = tab + (size_t)it * MT_PER_INT + i * MT_FSTRIDE;
+        float* tail = reinterpret_cast<float*>(out + MT_NHEAD);
+        double sc = 1.0;
+        for (int k = 0; k < MT_NC; ++k) {
+            if (k < MT_NHEAD) out[k] = mono[k] * sc;
+            else tail[k - MT_NHEAD] = (float)(mono[k] * sc);
+            sc *= (2.0 * MT_J);
+        }
+        tail[MT_NC - MT_NHEAD] = 0.0f;
+        if (tabf) {  // FP32 copy for the mixed path
+            float* of = tabf + (size_t)it * MT_PER_INT_F + i * MT_NC;
+            double sc2 = 1.0;
+            for (int k = 0; k < MT_NC; ++k) { of[k] = (float)(mono[k] * sc2); sc2 *= (2.0 * MT_J); }
+        }
+    }
+}
+
 
 __global__ void k_init_status(int* status, long long* bad) {
     status[0] = 0;
@@ -157,7 +223,7 @@ __global__ void k_cov_pairs(const double* __restrict__ covparms, const double* _
         for (int k = 0; k < d; ++k) { double t = a[k] - b[k]; s = fma(t, t, s); }
         s /= th[1] * th[1];
         const double nu = th[2], psi = dev_digamma(nu), lg = lgamma(nu);
-        double F0 = matern_F0(tab, s, nu, psi, lg), F1, F2;
+        double F0 = matern_F0(tab, s, nu, psi, lg), F1, F2;  // FP64 table
         matern_F12(tab, s, nu, psi, lg, F1, F2);
         c = s2 * F0;
         out[0] = F0;
@@ -189,50 +255,29 @@ __global__ void k_cov_pairs(const double* __restrict__ covparms, const double* _
 // ----------------------------------------------------------------------------------------
 static int nv_of(int p, int Q) { return 4 + p + Q * (3 + p) + Q * (Q + 1) / 2; }
 
-template <int COV, int L>
-static const void* pass_kernel_ptr() {
-    return reinterpret_cast<const void*>(&k_pass_fp64<COV, L>);
+static const void* pass_kernel(int cov, int L, int prec) {
+    return prec == 0 ? pass_kernel_f64(cov, L) : pass_kernel_f32(cov, L);
 }
 
-template <int COV>
-static const void* pass_kernel_for(int L) {
-    switch (L) {
-    case 1: return pass_kernel_ptr<COV, 1>();
-    case 2: return pass_kernel_ptr<COV, 2>();
-    case 4: return pass_kernel_ptr<COV, 4>();
-    case 8: return pass_kernel_ptr<COV, 8>();
-    case 16: return pass_kernel_ptr<COV, 16>();
-    case 32: return pass_kernel_ptr<COV, 32>();
-    default: return nullptr;
-    }
-}
-
-static const void* pass_kernel(int cov, int L) {
-    switch (cov) {
-    case COV_EXP: return pass_kernel_for<COV_EXP>(L);
-    case COV_MATERN: return pass_kernel_for<COV_MATERN>(L);
-    case COV_ST: return pass_kernel_for<COV_ST>(L);
-    default: return nullptr;
-    }
-}
-
-size_t pass_smem_bytes(int cov, int m, int d, int p, int L, int threads, bool tab_smem) {
+size_t pass_smem_bytes(int cov, int m, int d, int p, int L, int threads, bool tab_smem,
+                       int prec) {
     const int Q = npair_derivs(cov) + 1;
     RecLayout RL;
     RL.init(p, Q);
     const int nv = nv_of(p, Q);
     SlotLayout SL;
-    SL.init(m, d, p, cov, nv);
+    SL.init(m, d, p, cov, nv, prec == 0 ? 8 : 4);
     const int ngrp = threads / L;
     const int acc_per_lane = (RL.nstat + L - 1) / L;
-    size_t dbl = (size_t)(tab_smem ? MT_DOUBLES : 0) + (RL.nstat + 1) / 2 +
-                 (size_t)threads * acc_per_lane + (size_t)ngrp * SL.total;
+    const size_t tab_words = tab_smem ? (prec == 0 ? MT_DOUBLES : (MT_FLOATS + 1) / 2) : 0;
+    size_t bytes = (tab_words + (RL.nstat + 1) / 2 + (size_t)threads * acc_per_lane) * sizeof(double) +
+                   (size_t)ngrp * SL.bytes;
     size_t ints = (size_t)ngrp * (m + 1);
-    return dbl * sizeof(double) + ints * sizeof(int);
+    return bytes + ints * sizeof(int);
 }
 
 int plan_pass(int cov, int m, int d, int p, int nsm, int force_L, int force_threads,
-              PassPlan* plan) {
+              PassPlan* plan, int prec) {
     // Preference: 256 threads (two warps per SM sub-partition, so that one warp's FP64
     // dependency waits are covered by the other), then 128 (one warp per sub-partition,
     // the minimum that occupies all FP64 units), then fewer when the largest blocks do
@@ -247,8 +292,8 @@ int plan_pass(int cov, int m, int d, int p, int nsm, int force_L, int force_thre
             if (L > thr) continue;
             if (thr == 256 && force_L <= 0 && L > 16) continue;
             bool t = (cov == COV_MATERN);
-            size_t b = pass_smem_bytes(cov, m, d, p, L, thr, t);
-            if (b > budget && t) { t = false; b = pass_smem_bytes(cov, m, d, p, L, thr, t); }
+            size_t b = pass_smem_bytes(cov, m, d, p, L, thr, t, prec);
+            if (b > budget && t) { t = false; b = pass_smem_bytes(cov, m, d, p, L, thr, t, prec); }
             if (b <= budget) { chosen = L; tab = t; threads = thr; break; }
         }
     }
@@ -262,11 +307,12 @@ int plan_pass(int cov, int m, int d, int p, int nsm, int force_L, int force_thre
     plan->nstat = RL.nstat;
     plan->nv = nv_of(p, Q);
     SlotLayout SL;
-    SL.init(m, d, p, cov, plan->nv);
-    plan->slot_stride = SL.total;
+    SL.init(m, d, p, cov, plan->nv, prec == 0 ? 8 : 4);
+    plan->slot_stride = SL.bytes;
+    plan->prec = prec;
     plan->acc_per_lane = (RL.nstat + chosen - 1) / chosen;
-    plan->smem = pass_smem_bytes(cov, m, d, p, chosen, threads, tab);
-    const void* fn = pass_kernel(cov, chosen);
+    plan->smem = pass_smem_bytes(cov, m, d, p, chosen, threads, tab, prec);
+    const void* fn = pass_kernel(cov, chosen, prec);
     if (!fn) return -1;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan->smem) !=
         cudaSuccess)
@@ -280,7 +326,7 @@ int plan_pass(int cov, int m, int d, int p, int nsm, int force_L, int force_thre
 }
 
 cudaError_t launch_pass(int cov, const PassPlan& plan, const PassArgs& args, cudaStream_t st) {
-    const void* fn = pass_kernel(cov, plan.L);
+    const void* fn = pass_kernel(cov, plan.L, plan.prec);
     if (!fn) return cudaErrorInvalidValue;
     PassArgs a = args;
     void* params[] = {&a};
@@ -292,8 +338,8 @@ cudaError_t launch_init_status(int* status, long long* bad, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_mtab_build(const double* covparms, double* tab, cudaStream_t st) {
-    k_mtab_build<<<MT_NINT, MT_NC * 32, 0, st>>>(covparms, tab);
+cudaError_t launch_mtab_build(const double* covparms, double* tab, float* tabf, cudaStream_t st) {
+    k_mtab_build<<<MT_NINT, MT_NC * 32, 0, st>>>(covparms, tab, tabf);
     return cudaGetLastError();
 }
 
@@ -327,5 +373,6 @@ cudaError_t launch_cov_pairs(int cov, const double* covparms, const double* tab,
 }
 
 int mtab_doubles() { return MT_DOUBLES; }
+int mtab_floats() { return MT_FLOATS; }
 
 }  // namespace vg

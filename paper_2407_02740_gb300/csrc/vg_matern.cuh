@@ -164,61 +164,52 @@ __device__ inline void matern_direct_warp(double nu, double x, double psi, doubl
     F2 = F0 * (-LN2 - psi + lx) + A * S2;
 }
 
-// Table builder: one block of MT_NC warps per interval; warp i evaluates interpolation
-// node i, then three threads turn node values into monomial coefficients in w.
-// nu is read from covparms[2]; invalid nu leaves the table untouched (the pass reports
-// the parameter error).
-__global__ void __launch_bounds__(MT_NC * 32) k_mtab_build(const double* __restrict__ covparms,
-                                                           double* __restrict__ tab) {
-    __shared__ double vals[3][MT_NC];
-    const double nu = covparms[2];
-    if (!(nu >= 0.05 && nu <= 20.0)) return;
-    const int it = blockIdx.x;
-    const int e = MT_E0 + it / MT_J, j = it % MT_J;
-    const double hw = 1.0 / (2.0 * MT_J);
-    const double cen = 1.0 + (double)(2 * j + 1) / (double)(2 * MT_J);
-    const double PI = 3.14159265358979323846;
-    const int node = threadIdx.x >> 5;
-    {
-        double u = cos(PI * (node + 0.5) / MT_NC);
-        double s = ldexp(cen + hw * u, e);
-        double psi = dev_digamma(nu), lg = lgamma(nu);
+// FP32 table (mixed path): same intervals, 13 FP32 coefficients per function, located
+// from the FP32 bits of s.
+__device__ __forceinline__ int mtab_locate_f(float s, float& w) {
+    const unsigned bits = __float_as_uint(s);
+    const int e = (int)((bits >> 23) & 0xffu) - 127;
+    if (e < MT_E0) return -1;
+    if (e >= MT_E1) return -2;
+    const unsigned j = (bits >> (23 - MT_LOGJ)) & (unsigned)(MT_J - 1);
+    const float mant = __uint_as_float((bits & 0x007fffffu) | 0x3f800000u);
+    const float cen = __uint_as_float(0x3f800000u | ((2u * j + 1u) << (23 - MT_LOGJ - 1)));
+    w = mant - cen;
+    return (e - MT_E0) * MT_J + (int)j;
+}
+__device__ __forceinline__ float horner13f(const float* c, float w) {
+    float p = c[12];
+#pragma unroll
+    for (int k = 11; k >= 0; --k) p = fmaf(p, w, c[k]);
+    return p;
+}
+__device__ __forceinline__ float matern_F0f(const float* tab, float s, double nu, double psi,
+                                            double lg) {
+    float w;
+    int it = mtab_locate_f(s, w);
+    if (it >= 0) return horner13f(tab + it * MT_PER_INT_F, w);
+    if (it == -2) return 0.0f;
+    if (!(s > 0.0f)) return 1.0f;
+    double f0, f1, f2;
+    matern_direct(nu, sqrt((double)s), psi, lg, f0, f1, f2);
+    return (float)f0;
+}
+__device__ __forceinline__ void matern_F12f(const float* tab, float s, double nu, double psi,
+                                            double lg, float& F1, float& F2) {
+    float w;
+    int it = mtab_locate_f(s, w);
+    if (it >= 0) {
+        const float* cf = tab + it * MT_PER_INT_F;
+        F1 = horner13f(cf + MT_NC, w);
+        F2 = horner13f(cf + 2 * MT_NC, w);
+    } else if (it == -2 || !(s > 0.0f)) {
+        F1 = 0.0f;
+        F2 = 0.0f;
+    } else {
         double f0, f1, f2;
-        matern_direct_warp(nu, sqrt(s), psi, lg, f0, f1, f2);
-        if ((threadIdx.x & 31) == 0) { vals[0][node] = f0; vals[1][node] = f1; vals[2][node] = f2; }
-    }
-    __syncthreads();
-    const int i = threadIdx.x;
-    if (i < 3) {
-        double a[MT_NC];
-        for (int k = 0; k < MT_NC; ++k) {
-            double acc = 0.0;
-            for (int q = 0; q < MT_NC; ++q) acc += vals[i][q] * cos(PI * k * (q + 0.5) / MT_NC);
-            a[k] = acc * (2.0 / MT_NC);
-        }
-        a[0] *= 0.5;
-        // sum_k a_k T_k(u) -> monomials in u, via T_{k+1} = 2u T_k - T_{k-1}
-        double mono[MT_NC], Tm[MT_NC], Tc[MT_NC], Tn[MT_NC];
-        for (int k = 0; k < MT_NC; ++k) { mono[k] = 0.0; Tm[k] = 0.0; Tc[k] = 0.0; }
-        Tm[0] = 1.0;            // T_0
-        Tc[1] = 1.0;            // T_1
-        mono[0] = a[0];
-        for (int k = 0; k < MT_NC; ++k) mono[k] += a[1] * Tc[k];
-        for (int deg = 2; deg < MT_NC; ++deg) {
-            for (int k = 0; k < MT_NC; ++k) Tn[k] = -Tm[k] + (k > 0 ? 2.0 * Tc[k - 1] : 0.0);
-            for (int k = 0; k < MT_NC; ++k) { mono[k] += a[deg] * Tn[k]; Tm[k] = Tc[k]; Tc[k] = Tn[k]; }
-        }
-        // u = w / hw: coefficient of w^k is mono_k / hw^k (exact power-of-two scaling);
-        // w^0..w^7 stored in FP64, w^8..w^12 in FP32 (see horner_split)
-        double* out = tab + (size_t)it * MT_PER_INT + i * MT_FSTRIDE;
-        float* tail = reinterpret_cast<float*>(out + MT_NHEAD);
-        double sc = 1.0;
-        for (int k = 0; k < MT_NC; ++k) {
-            if (k < MT_NHEAD) out[k] = mono[k] * sc;
-            else tail[k - MT_NHEAD] = (float)(mono[k] * sc);
-            sc *= (2.0 * MT_J);
-        }
-        tail[MT_NC - MT_NHEAD] = 0.0f;
+        matern_direct(nu, sqrt((double)s), psi, lg, f0, f1, f2);
+        F1 = (float)f1;
+        F2 = (float)f2;
     }
 }
 

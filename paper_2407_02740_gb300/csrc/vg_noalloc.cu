@@ -120,11 +120,11 @@ VECCHIA_API vec_status vecchia_loglik_grad_info_noalloc(
     // the status word and failing index restart from zero / "none" on every call; the
     // table and every partial record are rewritten in full by the kernels below
     e = vg::launch_init_status(status, bad, st);
-    if (e == cudaSuccess && cov == vg::COV_MATERN) e = vg::launch_mtab_build(covparms, tab, st);
+    if (e == cudaSuccess && cov == vg::COV_MATERN) e = vg::launch_mtab_build(covparms, tab, nullptr, st);
     if (e != cudaSuccess) return nfail(VEC_ERR_CUDA, "launching the setup kernels: %s", cudaGetErrorString(e));
     vg::PassArgs a;
     a.locs = locs; a.y = y; a.X = X; a.NN = NNarray; a.covparms = covparms;
-    a.mtab = tab; a.partials = partials; a.status = status; a.bad = bad;
+    a.mtab = tab; a.mtabf = nullptr; a.partials = partials; a.status = status; a.bad = bad;
     a.n = n; a.d = d; a.p = p; a.m = m;
     a.nstat = plan.nstat; a.nv = plan.nv; a.slot_stride = plan.slot_stride;
     a.acc_per_lane = plan.acc_per_lane; a.tab_in_smem = plan.tab_smem;

@@ -1,4 +1,4 @@
-// vg_pass.cuh -- K1: the fused per-observation Vecchia pass, FP64.
+// vg_pass.cuh -- K1: the fused per-observation Vecchia pass, FP64 or mixed precision.
 //
 // Algorithm 1 of the paper, one observation at a time per "group" of L lanes of a warp
 // (L = 1, 2, 4, 8, 16 or 32 lanes per observation, chosen per block size).  The
@@ -6,7 +6,8 @@
 // every step is done by the L lanes together:
 //
 //   gather      NNarray row -> block indices (neighbours reversed, observation last),
-//               locations, y and X rows                              (Algorithm 1, l. 4-5)
+//               coordinates relative to the observation and divided by their range,
+//               y and X rows                                         (Algorithm 1, l. 4-5)
 //   assembly    lower triangle of the covariance, nugget on the diagonal       (l. 6)
 //   factor      left-looking Cholesky; y and X ride along as extra rows, so the same
 //               column sweep produces Liy = L^-1 y and LiX = L^-1 X            (l. 7-9)
@@ -16,23 +17,81 @@
 //               the lanes scatter into g without atomics), m_j = L^-1 g_j, then the dot
 //               products that give dlogdet, dySy, dySX, dXSX and the information (l. 14-15,
 //               written out from dL = L Phi(L^-1 dSigma L^-T))
-//   accumulate  per-observation values into per-lane running sums (shared memory), then a
-//               fixed-order block reduction into one partial record per block.
+//   accumulate  per-observation values into per-lane FP64 running sums (shared memory),
+//               then a fixed-order block reduction into one partial record per block.
+//
+// T is the working type of the block.  T = double is the FP64 path.  T = float is the
+// mixed path: the block, the covariance entries, the factorisation, the solves and the
+// derivative work are FP32; the coordinate differences (taken in FP64 relative to the
+// observation before rounding), the per-observation values, every sum over observations,
+// the profile step and the Fisher step stay FP64.
 //
 // FP64 on this GPU issues one warp instruction per 64 cycles per SM sub-partition whatever
 // the number of active lanes, so the mapping keeps all 32 lanes busy: rows, pairs and
-// vector entries are spread round-robin over the L lanes of a group, and each pivot costs
-// an FP32 seed plus two short FP64 Newton steps instead of a square root and a division.
+// vector entries are spread round-robin over the L lanes of a group, and each FP64 pivot
+// costs an FP32 seed plus two short FP64 Newton steps instead of a square root and a
+// division.
 #pragma once
 #include "vg_common.cuh"
 #include "vg_matern.cuh"
 
 namespace vg {
 
-// sizes (in doubles) of the parts of one slot; K = m + 1
+// Per-type arithmetic used by the pass.
+template <typename T>
+struct Num;
+template <>
+struct Num<double> {
+    static __device__ __forceinline__ double fma_(double a, double b, double c) { return fma(a, b, c); }
+    static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+    static __device__ __forceinline__ double exp_(double x) { return exp(x); }
+    static __device__ __forceinline__ double rsqrt_pivot(double v) { return rsqrt_newton(v); }
+    static __device__ __forceinline__ bool finite_(double x) { return isfinite(x); }
+};
+template <>
+struct Num<float> {
+    static __device__ __forceinline__ float fma_(float a, float b, float c) { return fmaf(a, b, c); }
+    static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+    static __device__ __forceinline__ float exp_(float x) { return expf(x); }
+    // FP32 seed and one FP32 Newton step
+    static __device__ __forceinline__ float rsqrt_pivot(float v) {
+        float y = rsqrtf(v);
+        return y * fmaf(-0.5f * v * y, y, 1.5f);
+    }
+    static __device__ __forceinline__ bool finite_(float x) { return isfinite(x); }
+};
+
+// Matern lookups in the working type: FP64 table (split Horner) or FP32 table.
+template <typename T>
+struct MaternT;
+template <>
+struct MaternT<double> {
+    using Tab = double;
+    static __device__ __forceinline__ double F0(const double* tab, double s, double nu, double psi, double lg) {
+        return matern_F0(tab, s, nu, psi, lg);
+    }
+    static __device__ __forceinline__ void F12(const double* tab, double s, double nu, double psi,
+                                               double lg, double& F1, double& F2) {
+        matern_F12(tab, s, nu, psi, lg, F1, F2);
+    }
+};
+template <>
+struct MaternT<float> {
+    using Tab = float;
+    static __device__ __forceinline__ float F0(const float* tab, float s, double nu, double psi, double lg) {
+        return matern_F0f(tab, s, nu, psi, lg);
+    }
+    static __device__ __forceinline__ void F12(const float* tab, float s, double nu, double psi,
+                                               double lg, float& F1, float& F2) {
+        matern_F12f(tab, s, nu, psi, lg, F1, F2);
+    }
+};
+
+// Layout of one slot: the T arrays first (offsets in T elements), then the FP64 value
+// vector V.  K = m + 1.
 struct SlotLayout {
-    int K, A, Y, inv, loc, bacc, b, G, D1, V, total;
-    __host__ __device__ void init(int m, int d, int p, int cov, int nv) {
+    int K, A, Y, inv, loc, bacc, b, G, D1, nT, Vbyte, bytes;
+    __host__ __device__ void init(int m, int d, int p, int cov, int nv, int tsize) {
         K = m + 1;
         int Q = npair_derivs(cov) + 1;
         A = 0;
@@ -43,9 +102,10 @@ struct SlotLayout {
         b = bacc + K;
         G = b + K;
         D1 = G + Q * K;
-        V = D1 + (cov == COV_MATERN ? 0 : K * (K - 1) / 2);
-        total = V + nv;
-        total |= 1;  // odd stride spreads the slots of a warp over the shared-memory banks
+        nT = D1 + (cov == COV_MATERN ? 0 : K * (K - 1) / 2);
+        Vbyte = ((nT * tsize + 7) / 8) * 8;
+        bytes = Vbyte + nv * 8;
+        bytes = ((bytes / 8) | 1) * 8;  // odd number of 8-byte words: slots spread over banks
     }
 };
 
@@ -57,14 +117,8 @@ __device__ __forceinline__ void gsync(unsigned mask) {
 }
 
 // sums over the L lanes of a group (xor partners stay inside the group)
-template <int L>
-__device__ __forceinline__ double gsum(double v, unsigned mask) {
-#pragma unroll
-    for (int o = L / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
-    return v;
-}
-template <int L>
-__device__ __forceinline__ int gsum_i(int v, unsigned mask) {
+template <int L, typename U>
+__device__ __forceinline__ U gsum(U v, unsigned mask) {
 #pragma unroll
     for (int o = L / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
     return v;
@@ -86,9 +140,12 @@ __device__ __forceinline__ bool circle_pair(int Kp, int Nv, int r, int k, int& a
     return true;
 }
 
-template <int COV, int L>
-__global__ void __launch_bounds__(256) k_pass_fp64(PassArgs args) {
+template <int COV, int L, typename T>
+__global__ void __launch_bounds__(256) k_pass(PassArgs args) {
     extern __shared__ __align__(16) double smem[];
+    using N = Num<T>;
+    using MT = MaternT<T>;
+    using Tab = typename MT::Tab;
     constexpr int NG = npair_derivs(COV);
     constexpr int Q = NG + 1;
     const int tid = threadIdx.x;
@@ -102,29 +159,35 @@ __global__ void __launch_bounds__(256) k_pass_fp64(PassArgs args) {
 
     // ---- shared-memory carve-up: [Matern table][stat index table][acc][slots][int slots]
     double* sp = smem;
-    const double* tab = args.mtab;
+    const Tab* tab = sizeof(T) == 8 ? reinterpret_cast<const Tab*>(args.mtab)
+                                    : reinterpret_cast<const Tab*>(args.mtabf);
     if (COV == COV_MATERN && args.tab_in_smem) {
-        for (int t = tid; t < MT_DOUBLES; t += blockDim.x) sp[t] = args.mtab[t];
-        tab = sp;
-        sp += MT_DOUBLES;
+        const int nwords = sizeof(T) == 8 ? MT_DOUBLES : (MT_FLOATS + 1) / 2;
+        const double* src = sizeof(T) == 8 ? args.mtab : reinterpret_cast<const double*>(args.mtabf);
+        for (int t = tid; t < nwords; t += blockDim.x) sp[t] = src[t];
+        tab = reinterpret_cast<const Tab*>(sp);
+        sp += nwords;
     }
     uint32_t* sidx = reinterpret_cast<uint32_t*>(sp);
     sp += (args.nstat + 1) / 2;
     double* acc = sp + (size_t)tid * args.acc_per_lane;
+    double* accbase = sp;
     sp += (size_t)blockDim.x * args.acc_per_lane;
     SlotLayout SL;
-    SL.init(m, d, p, COV, args.nv);
-    double* slot = sp + (size_t)grp * args.slot_stride;
-    int* idx = reinterpret_cast<int*>(sp + (size_t)ngrp * args.slot_stride) + grp * Kmax;
-    double* A = slot + SL.A;
-    double* Yg = slot + SL.Y;
-    double* invd = slot + SL.inv;
-    double* loc = slot + SL.loc;
-    double* bacc = slot + SL.bacc;
-    double* bv = slot + SL.b;
-    double* G = slot + SL.G;
-    double* D1 = slot + SL.D1;
-    double* V = slot + SL.V;
+    SL.init(m, d, p, COV, args.nv, (int)sizeof(T));
+    char* slotc = reinterpret_cast<char*>(sp) + (size_t)grp * args.slot_stride;
+    int* idx = reinterpret_cast<int*>(reinterpret_cast<char*>(sp) + (size_t)ngrp * args.slot_stride) +
+               grp * Kmax;
+    T* slot = reinterpret_cast<T*>(slotc);
+    T* A = slot + SL.A;
+    T* Yg = slot + SL.Y;
+    T* invd = slot + SL.inv;
+    T* loc = slot + SL.loc;
+    T* bacc = slot + SL.bacc;
+    T* bv = slot + SL.b;
+    T* G = slot + SL.G;
+    T* D1 = slot + SL.D1;
+    double* V = reinterpret_cast<double*>(slotc + SL.Vbyte);
 
     // ---- per-observation value vector V and the record formulas (see RecLayout)
     //   V[0] = 1, V[1] = 0, V[2] = logdet_i, V[3] = ell, V[4..4+p) = x,
@@ -172,10 +235,12 @@ __global__ void __launch_bounds__(256) k_pass_fp64(PassArgs args) {
     if (!ok) {
         if (blockIdx.x == 0 && tid == 0) report(args.status, args.bad, ST_ARG, -1);
     }
-    const double diagC = sig2 * (1.0 + tau2);
+    const T sig2T = (T)sig2;
+    const T diagC = (T)(sig2 * (1.0 + tau2));
     // EXP: rho = th[1]; MATERN: rho = th[1], nu = th[2]; ST: rho_s = th[1], rho_t = th[2]
     const double inv_r1 = 1.0 / th[1];
     const double inv_r2 = (COV == COV_ST) ? 1.0 / th[2] : 1.0;
+    const T inv_r1T = (T)inv_r1, inv_r2T = (T)inv_r2;
     double m_psi = 0.0, m_lg = 0.0;
     if (COV == COV_MATERN && ok) { m_psi = dev_digamma(th[2]); m_lg = lgamma(th[2]); }
     __syncthreads();
@@ -194,22 +259,24 @@ __global__ void __launch_bounds__(256) k_pass_fp64(PassArgs args) {
                 badrow |= (v >= i) | (c >= 2 && row[c - 1] < 0);
             } else if (v != -1) badrow = 1;
         }
-        cnt = gsum_i<L>(cnt, gmask);
-        badrow = gsum_i<L>(badrow, gmask);
+        cnt = gsum<L>(cnt, gmask);
+        badrow = gsum<L>(badrow, gmask);
         if (badrow) {
             if (gl == 0) report(args.status, args.bad, ST_ARG, i);
             continue;
         }
         const int Kp = cnt + 1;
+        const double* li = args.locs + i * (long long)d;
         for (int a = gl; a < Kp; a += L) {
             int j = row[Kp - 1 - a];
             idx[a] = j;
-            // coordinates are stored divided by their range parameter, so that squared
-            // distances come out already scaled
+            // coordinates relative to the observation, divided by their range parameter
+            // (FP64 difference, then rounded to T): squared distances come out scaled
             for (int k = 0; k < d; ++k)
-                loc[k * Kmax + a] = args.locs[(long long)j * d + k] * ((COV == COV_ST && k == 2) ? inv_r2 : inv_r1);
-            Yg[a] = args.y[j];
-            for (int t = 0; t < p; ++t) Yg[(1 + t) * Kmax + a] = args.X[(long long)j * p + t];
+                loc[k * Kmax + a] = (T)((args.locs[(long long)j * d + k] - li[k]) *
+                                        ((COV == COV_ST && k == 2) ? inv_r2 : inv_r1));
+            Yg[a] = (T)args.y[j];
+            for (int t = 0; t < p; ++t) Yg[(1 + t) * Kmax + a] = (T)args.X[(long long)j * p + t];
         }
         gsync<L>(gmask);
 
@@ -220,35 +287,35 @@ __global__ void __launch_bounds__(256) k_pass_fp64(PassArgs args) {
             while (a * (a + 1) / 2 > e) --a;
             while ((a + 1) * (a + 2) / 2 <= e) ++a;
             int c = e - a * (a + 1) / 2;
-            double C;
+            T C;
             if (a == c) {
                 C = diagC;
             } else if (COV == COV_EXP) {
-                double s = 0.0;
+                T s = (T)0;
                 for (int k = 0; k < d; ++k) {
-                    double t = loc[k * Kmax + a] - loc[k * Kmax + c];
-                    s = fma(t, t, s);
+                    T t = loc[k * Kmax + a] - loc[k * Kmax + c];
+                    s = N::fma_(t, t, s);
                 }
-                double x = sqrt(s);
-                double ex = sig2 * exp(-x);
+                T x = N::sqrt_(s);
+                T ex = sig2T * N::exp_(-x);
                 C = ex;
                 D1[a * (a - 1) / 2 + c] = ex * x;          // rho dC/drho
             } else if (COV == COV_ST) {
-                double t0 = loc[a] - loc[c];
-                double t1 = loc[Kmax + a] - loc[Kmax + c];
-                double t2 = loc[2 * Kmax + a] - loc[2 * Kmax + c];
-                double u = fma(t0, t0, fma(t1, t1, t2 * t2));
-                double D = sqrt(u);
-                double ex = sig2 * exp(-D);
+                T t0 = loc[a] - loc[c];
+                T t1 = loc[Kmax + a] - loc[Kmax + c];
+                T t2 = loc[2 * Kmax + a] - loc[2 * Kmax + c];
+                T u = N::fma_(t0, t0, N::fma_(t1, t1, t2 * t2));
+                T D = N::sqrt_(u);
+                T ex = sig2T * N::exp_(-D);
                 C = ex;
-                D1[a * (a - 1) / 2 + c] = D > 0.0 ? ex / D : 0.0;
+                D1[a * (a - 1) / 2 + c] = D > (T)0 ? ex / D : (T)0;
             } else {  // Matern
-                double s = 0.0;
+                T s = (T)0;
                 for (int k = 0; k < d; ++k) {
-                    double t = loc[k * Kmax + a] - loc[k * Kmax + c];
-                    s = fma(t, t, s);
+                    T t = loc[k * Kmax + a] - loc[k * Kmax + c];
+                    s = N::fma_(t, t, s);
                 }
-                C = sig2 * matern_F0(tab, s, th[2], m_psi, m_lg);
+                C = sig2T * MT::F0(tab, s, th[2], m_psi, m_lg);
             }
             A[e] = C;
         }
@@ -259,26 +326,26 @@ __global__ void __launch_bounds__(256) k_pass_fp64(PassArgs args) {
         const int R = Kp + 1 + p;
         bool pd = true;
         for (int c = 0; c < Kp; ++c) {
-            const double* Lc = A + c * (c + 1) / 2;
+            const T* Lc = A + c * (c + 1) / 2;
             const int r0 = c + ((gl - c) & (L - 1));
             for (int r = r0; r < R; r += L) {
-                double* Rr = r < Kp ? A + r * (r + 1) / 2 : Yg + (r - Kp) * Kmax;
-                double v0 = Rr[c], v1 = 0.0;
+                T* Rr = r < Kp ? A + r * (r + 1) / 2 : Yg + (r - Kp) * Kmax;
+                T v0 = Rr[c], v1 = (T)0;
                 int s = 0;
                 for (; s + 1 < c; s += 2) {
-                    v0 = fma(-Rr[s], Lc[s], v0);
-                    v1 = fma(-Rr[s + 1], Lc[s + 1], v1);
+                    v0 = N::fma_(-Rr[s], Lc[s], v0);
+                    v1 = N::fma_(-Rr[s + 1], Lc[s + 1], v1);
                 }
-                if (s < c) v0 = fma(-Rr[s], Lc[s], v0);
+                if (s < c) v0 = N::fma_(-Rr[s], Lc[s], v0);
                 Rr[c] = v0 + v1;
             }
             gsync<L>(gmask);
-            const double vc = Lc[c];
-            if (!(vc > 0.0) || !isfinite(vc)) { pd = false; break; }
-            const double ic = rsqrt_newton(vc);
+            const T vc = Lc[c];
+            if (!(vc > (T)0) || !N::finite_(vc)) { pd = false; break; }
+            const T ic = N::rsqrt_pivot(vc);
             if (r0 == c) invd[c] = ic;
             for (int r = (r0 == c ? r0 + L : r0); r < R; r += L) {
-                double* Rr = r < Kp ? A + r * (r + 1) / 2 : Yg + (r - Kp) * Kmax;
+                T* Rr = r < Kp ? A + r * (r + 1) / 2 : Yg + (r - Kp) * Kmax;
                 Rr[c] *= ic;
             }
             gsync<L>(gmask);
@@ -291,13 +358,13 @@ __global__ void __launch_bounds__(256) k_pass_fp64(PassArgs args) {
         const int last = Kp - 1;
 
         // ---------------- b = last row of L^-1 (L^T b^T = e_last) ----------------
-        for (int a = gl; a < Kp; a += L) bacc[a] = (a == last) ? 1.0 : 0.0;
+        for (int a = gl; a < Kp; a += L) bacc[a] = (a == last) ? (T)1 : (T)0;
         gsync<L>(gmask);
         for (int c = last; c >= 0; --c) {
-            const double bc = bacc[c] * invd[c];
+            const T bc = bacc[c] * invd[c];
             if (((c - gl) & (L - 1)) == 0) bv[c] = bc;
-            const double* Lr = A + c * (c + 1) / 2;
-            for (int a = gl; a < c; a += L) bacc[a] = fma(-Lr[a], bc, bacc[a]);
+            const T* Lr = A + c * (c + 1) / 2;
+            for (int a = gl; a < c; a += L) bacc[a] = N::fma_(-Lr[a], bc, bacc[a]);
             gsync<L>(gmask);
         }
 
@@ -305,8 +372,8 @@ __global__ void __launch_bounds__(256) k_pass_fp64(PassArgs args) {
         // g for the pair-derivative parameters starts at 0; the nugget one is sigma2 b.
         for (int a = gl; a < Kp; a += L) {
 #pragma unroll
-            for (int j = 0; j < NG; ++j) G[j * Kmax + a] = 0.0;
-            G[NG * Kmax + a] = sig2 * bv[a];
+            for (int j = 0; j < NG; ++j) G[j * Kmax + a] = (T)0;
+            G[NG * Kmax + a] = sig2T * bv[a];
         }
         gsync<L>(gmask);
         {
@@ -316,32 +383,32 @@ __global__ void __launch_bounds__(256) k_pass_fp64(PassArgs args) {
                 for (int k = gl; k < npr; k += L) {
                     int a, c;
                     if (!circle_pair(Kp, Nv, r, k, a, c)) continue;
-                    double dv[NG];
+                    T dv[NG];
                     if (COV == COV_EXP) {
-                        dv[0] = D1[a * (a - 1) / 2 + c] * inv_r1;
+                        dv[0] = D1[a * (a - 1) / 2 + c] * inv_r1T;
                     } else if (COV == COV_ST) {
-                        double t0 = loc[a] - loc[c];
-                        double t1 = loc[Kmax + a] - loc[Kmax + c];
-                        double t2 = loc[2 * Kmax + a] - loc[2 * Kmax + c];
-                        double w = D1[a * (a - 1) / 2 + c];
-                        dv[0] = w * fma(t0, t0, t1 * t1) * inv_r1;
-                        if (NG > 1) dv[NG - 1] = w * t2 * t2 * inv_r2;
+                        T t0 = loc[a] - loc[c];
+                        T t1 = loc[Kmax + a] - loc[Kmax + c];
+                        T t2 = loc[2 * Kmax + a] - loc[2 * Kmax + c];
+                        T w = D1[a * (a - 1) / 2 + c];
+                        dv[0] = w * N::fma_(t0, t0, t1 * t1) * inv_r1T;
+                        if (NG > 1) dv[NG - 1] = w * t2 * t2 * inv_r2T;
                     } else {
-                        double s = 0.0;
+                        T s = (T)0;
                         for (int kk = 0; kk < d; ++kk) {
-                            double t = loc[kk * Kmax + a] - loc[kk * Kmax + c];
-                            s = fma(t, t, s);
+                            T t = loc[kk * Kmax + a] - loc[kk * Kmax + c];
+                            s = N::fma_(t, t, s);
                         }
-                        double F1, F2;
-                        matern_F12(tab, s, th[2], m_psi, m_lg, F1, F2);
-                        dv[0] = sig2 * F1 * inv_r1;
-                        if (NG > 1) dv[NG - 1] = sig2 * F2;
+                        T F1, F2;
+                        MT::F12(tab, s, th[2], m_psi, m_lg, F1, F2);
+                        dv[0] = sig2T * F1 * inv_r1T;
+                        if (NG > 1) dv[NG - 1] = sig2T * F2;
                     }
-                    const double ba = bv[a], bc = bv[c];
+                    const T ba = bv[a], bc = bv[c];
 #pragma unroll
                     for (int j = 0; j < NG; ++j) {
-                        G[j * Kmax + a] = fma(dv[j], bc, G[j * Kmax + a]);
-                        G[j * Kmax + c] = fma(dv[j], ba, G[j * Kmax + c]);
+                        G[j * Kmax + a] = N::fma_(dv[j], bc, G[j * Kmax + a]);
+                        G[j * Kmax + c] = N::fma_(dv[j], ba, G[j * Kmax + c]);
                     }
                 }
                 gsync<L>(gmask);
@@ -352,8 +419,8 @@ __global__ void __launch_bounds__(256) k_pass_fp64(PassArgs args) {
         // Column c: every lane reads the finished residual g_j[c] and scales it; after a
         // group barrier the owner of c stores m_j[c] and each lane updates its rows a > c.
         for (int c = 0; c < Kp; ++c) {
-            const double ic = invd[c];
-            double mc[Q];
+            const T ic = invd[c];
+            T mc[Q];
 #pragma unroll
             for (int j = 0; j < Q; ++j) mc[j] = G[j * Kmax + c] * ic;
             gsync<L>(gmask);
@@ -363,9 +430,9 @@ __global__ void __launch_bounds__(256) k_pass_fp64(PassArgs args) {
             }
             const int a0 = c + 1 + ((gl - c - 1) & (L - 1));
             for (int a = a0; a < Kp; a += L) {
-                const double lac = A[a * (a + 1) / 2 + c];
+                const T lac = A[a * (a + 1) / 2 + c];
 #pragma unroll
-                for (int j = 0; j < Q; ++j) G[j * Kmax + a] = fma(-lac, mc[j], G[j * Kmax + a]);
+                for (int j = 0; j < Q; ++j) G[j * Kmax + a] = N::fma_(-lac, mc[j], G[j * Kmax + a]);
             }
             gsync<L>(gmask);
         }
@@ -373,33 +440,33 @@ __global__ void __launch_bounds__(256) k_pass_fp64(PassArgs args) {
         // ---------------- per-observation values ----------------
         {
             // partial dot products over this lane's entries, last entry of hat() halved
-            double dl[Q], dx[Q][PMAX], mm[Q * (Q + 1) / 2];
+            T dl[Q], dx[Q][PMAX], mm[Q * (Q + 1) / 2];
 #pragma unroll
             for (int j = 0; j < Q; ++j) {
-                dl[j] = 0.0;
-                for (int t = 0; t < p; ++t) dx[j][t] = 0.0;
+                dl[j] = (T)0;
+                for (int t = 0; t < p; ++t) dx[j][t] = (T)0;
             }
 #pragma unroll
-            for (int t = 0; t < Q * (Q + 1) / 2; ++t) mm[t] = 0.0;
+            for (int t = 0; t < Q * (Q + 1) / 2; ++t) mm[t] = (T)0;
             for (int a = gl; a < Kp; a += L) {
-                const double hf = (a == last) ? 0.5 : 1.0;
-                const double ly = Yg[a] * hf;
-                double mj[Q];
+                const T hf = (a == last) ? (T)0.5 : (T)1;
+                const T ly = Yg[a] * hf;
+                T mj[Q];
 #pragma unroll
                 for (int j = 0; j < Q; ++j) {
                     mj[j] = G[j * Kmax + a];
-                    dl[j] = fma(mj[j], ly, dl[j]);
+                    dl[j] = N::fma_(mj[j], ly, dl[j]);
                 }
                 for (int t = 0; t < p; ++t) {
-                    const double lx = Yg[(1 + t) * Kmax + a] * hf;
+                    const T lx = Yg[(1 + t) * Kmax + a] * hf;
 #pragma unroll
-                    for (int j = 0; j < Q; ++j) dx[j][t] = fma(mj[j], lx, dx[j][t]);
+                    for (int j = 0; j < Q; ++j) dx[j][t] = N::fma_(mj[j], lx, dx[j][t]);
                 }
                 int u = 0;
 #pragma unroll
                 for (int j = 0; j < Q; ++j)
 #pragma unroll
-                    for (int l = j; l < Q; ++l) { mm[u] = fma(mj[j], mj[l], mm[u]); ++u; }
+                    for (int l = j; l < Q; ++l) { mm[u] = N::fma_(mj[j], mj[l], mm[u]); ++u; }
             }
 #pragma unroll
             for (int j = 0; j < Q; ++j) {
@@ -411,25 +478,25 @@ __global__ void __launch_bounds__(256) k_pass_fp64(PassArgs args) {
             if (gl == 0) {
                 V[0] = 1.0;
                 V[1] = 0.0;
-                V[2] = -2.0 * log(invd[last]);
-                V[3] = Yg[last];
-                for (int t = 0; t < p; ++t) V[4 + t] = Yg[(1 + t) * Kmax + last];
+                V[2] = -2.0 * log((double)invd[last]);
+                V[3] = (double)Yg[last];
+                for (int t = 0; t < p; ++t) V[4 + t] = (double)Yg[(1 + t) * Kmax + last];
 #pragma unroll
                 for (int j = 0; j < Q; ++j) {
                     const int vb = vb0 + j * vstep;
-                    const double md = G[j * Kmax + last];
+                    const double md = (double)G[j * Kmax + last];
                     V[vb] = md;
-                    V[vb + 1] = -dl[j];
-                    for (int t = 0; t < p; ++t) V[vb + 2 + t] = -dx[j][t];
+                    V[vb + 1] = -(double)dl[j];
+                    for (int t = 0; t < p; ++t) V[vb + 2 + t] = -(double)dx[j][t];
                     V[vb + 2 + p] = -0.5 * md;
                 }
 #pragma unroll
-                for (int t = 0; t < Q * (Q + 1) / 2; ++t) V[vmm + t] = mm[t];
+                for (int t = 0; t < Q * (Q + 1) / 2; ++t) V[vmm + t] = (double)mm[t];
             }
             gsync<L>(gmask);
         }
 
-        // ---------------- accumulate the record ----------------
+        // ---------------- accumulate the record (FP64) ----------------
         for (int t = gl, k = 0; t < args.nstat; t += L, ++k) {
             const uint32_t w = sidx[t];
             const double v1 = V[w & 255u] * V[(w >> 8) & 255u];
@@ -440,7 +507,6 @@ __global__ void __launch_bounds__(256) k_pass_fp64(PassArgs args) {
 
     // ---------------- block reduction (fixed order) ----------------
     __syncthreads();
-    double* accbase = sp - (size_t)blockDim.x * args.acc_per_lane;
     for (int t = tid; t < args.nstat; t += blockDim.x) {
         const int lr = t % L, k = t / L;
         double s = 0.0;
