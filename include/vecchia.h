@@ -177,6 +177,29 @@ VECCHIA_API vec_status vecchia_loglik_grad_info_host(vec_handle h, const double*
                                          double* loglik, double* grad, double* info,
                                          double* betahat, int64_t* bad_index);
 
+/*
+ * vecchia_batch_loglik_grad_info -- the pass for many independent datasets at once.
+ *
+ * nbatch datasets share the covariance family, d and p; each has its own n_b, m_b and
+ * theta_b.  Their arrays are concatenated: dataset b owns rows [off[b], off[b+1]) of locs,
+ * y and X (off = point_offsets, HOST, nbatch+1 values, off[0] = 0), and its NNarray
+ * (n_b x (m_b+1), indices LOCAL to the dataset, same conventions as above) follows the
+ * previous dataset's in NNarray.  m: HOST, nbatch values.  covparms: DEVICE, nbatch x q.
+ * out: DEVICE, nbatch x (1+q+q*q+p) doubles, row b = [loglik, grad, info, betahat] of
+ * dataset b; dev_status: DEVICE, nbatch x 2 int64 ([status, first failing observation]).
+ * One persistent launch covers all datasets: CTAs take tiles (ranges of observations of
+ * one dataset) from a work counter, and each tile's sums form one record, so results do
+ * not depend on the schedule.  The small work list (tiles, offsets) is copied from the
+ * host first and the call waits for that copy; the pass itself is then enqueued on
+ * `stream` and the call returns.  Requires 1 <= n_b, sum of n_b < 2^31,
+ * 0 <= m_b <= vecchia_max_m().
+ */
+VECCHIA_API vec_status vecchia_batch_loglik_grad_info(
+    vec_handle h, int nbatch, const double* locs, const double* y, const double* X,
+    const int32_t* NNarray, const int64_t* point_offsets, const int* m, int d, int p,
+    const double* covparms, vec_covfun covfun, vec_precision prec, void* stream, double* out,
+    int64_t* dev_status);
+
 /* Options of vecchia_fit.  A NULL pointer means the defaults shown. */
 typedef struct {
     double tol;         /* stop when g~' I~^-1 g~ < tol on the log scale (1e-4)            */

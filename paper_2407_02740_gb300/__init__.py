@@ -94,6 +94,8 @@ def lib():
         L.vecchia_loglik_grad_info_host.argtypes = [P, P, P, P, P, i64, ci, ci, ci, P, ci, ci,
                                                     P, P, P, P, P]
         L.vecchia_covariance_pairs.argtypes = [P, ci, P, ci, i64, P, P, P, P, P, P]
+        L.vecchia_batch_loglik_grad_info.argtypes = [P, ci, P, P, P, P, P, P, ci, ci, P, ci, ci,
+                                                     P, P, P]
         L.vecchia_fit.argtypes = [P, P, P, P, P, i64, ci, ci, ci, ci, P, ctypes.POINTER(FitOpts),
                                   P, P, P, P, P, P, ctypes.POINTER(FitInfo)]
         L.vecchia_loglik_grad_info_noalloc.argtypes = [P, P, P, P, i64, ci, ci, ci, P, ci, ci,
@@ -103,7 +105,8 @@ def lib():
                   L.vecchia_covariance_pairs, L.vecchia_nparms, L.vecchia_max_m,
                   L.vecchia_set_timing, L.vecchia_last_timing, L.vecchia_kernels_per_pass,
                   L.vecchia_loglik_grad_info_noalloc, L.vecchia_fit, L.vecchia_autotune,
-                  L.vecchia_autotune_save, L.vecchia_autotune_load):
+                  L.vecchia_autotune_save, L.vecchia_autotune_load,
+                  L.vecchia_batch_loglik_grad_info):
             f.restype = ci
         _lib = L
     return _lib
@@ -210,6 +213,42 @@ def vecchia_loglik_grad_info(locs, y, X, NNarray, covparms, covfun: int, prec="f
     _check(lib().vecchia_loglik_grad_info(handle.ptr, _dptr(locs), _dptr(y), _dptr(X),
                                           _dptr(NNarray), n, d, p, m, _dptr(covparms), covfun,
                                           _PREC[prec], sptr, _dptr(out), _dptr(status)))
+    return out, status
+
+
+def vecchia_batch_loglik_grad_info(locs, y, X, NNarray, point_offsets, m, covparms, covfun: int,
+                                   prec="fp64", stream=None, out=None, status=None,
+                                   handle: Handle | None = None):
+    """Batched pass over concatenated datasets (see include/vecchia.h).  locs, y, X,
+    NNarray (flat int32, per-dataset NNarrays with local indices, concatenated) and covparms
+    (nbatch x q) are CUDA tensors; point_offsets (nbatch+1) and m (nbatch) are host
+    sequences.  Returns (out (nbatch, 1+q+q*q+p), status (nbatch, 2)) on the device."""
+    import torch
+    for t, dt, nm in ((locs, torch.float64, "locs"), (y, torch.float64, "y"),
+                      (X, torch.float64, "X"), (NNarray, torch.int32, "NNarray"),
+                      (covparms, torch.float64, "covparms")):
+        _dev_tensor_check(t, dt, nm)
+    off = np.ascontiguousarray(point_offsets, dtype=np.int64)
+    mm = np.ascontiguousarray(m, dtype=np.int32)
+    nb = len(mm)
+    d = locs.shape[1]
+    p = X.shape[1]
+    q = NPARMS[covfun]
+    dev = locs.device
+    if handle is None:
+        handle = default_handle(dev.index if dev.index is not None else 0)
+    if out is None:
+        out = torch.empty(nb, 1 + q + q * q + p, dtype=torch.float64, device=dev)
+    if status is None:
+        status = torch.empty(nb, 2, dtype=torch.int64, device=dev)
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    P = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    _check(lib().vecchia_batch_loglik_grad_info(handle.ptr, nb, _dptr(locs), _dptr(y), _dptr(X),
+                                                _dptr(NNarray), P(off), P(mm), d, p,
+                                                _dptr(covparms), covfun, _PREC[prec],
+                                                ctypes.c_void_p(stream.cuda_stream), _dptr(out),
+                                                _dptr(status)))
     return out, status
 
 

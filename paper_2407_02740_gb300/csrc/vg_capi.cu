@@ -90,6 +90,18 @@ struct vec_handle_s {
     int fit_lru = 0;
     // autotuned mappings
     std::vector<TuneEntry> tune;
+    // batched pass scratch
+    int4* b_tiles = nullptr; size_t c_tiles = 0;
+    int* b_tile_off = nullptr; size_t c_tile_off = 0;
+    long long* b_pt_off = nullptr; size_t c_pt_off = 0;
+    long long* b_nn_off = nullptr; size_t c_nn_off = 0;
+    int* b_m = nullptr; size_t c_m = 0;
+    int* b_status = nullptr; size_t c_status = 0;
+    long long* b_bad = nullptr; size_t c_bad = 0;
+    int* b_counter = nullptr; size_t c_counter = 0;
+    double* b_partials = nullptr; size_t c_bpart = 0;
+    double* b_tabs = nullptr; size_t c_tabs = 0;
+    float* b_tabsf = nullptr; size_t c_tabsf = 0;
     // pass scratch
     double* partials = nullptr;
     size_t partials_cap = 0;
@@ -226,6 +238,9 @@ vec_status vecchia_destroy(vec_handle h) {
     cudaFree(h->fit_out);
     cudaFree(h->fit_st);
     cudaFree(h->fit_start);
+    cudaFree(h->b_tiles); cudaFree(h->b_tile_off); cudaFree(h->b_pt_off); cudaFree(h->b_nn_off);
+    cudaFree(h->b_m); cudaFree(h->b_status); cudaFree(h->b_bad); cudaFree(h->b_counter);
+    cudaFree(h->b_partials); cudaFree(h->b_tabs); cudaFree(h->b_tabsf);
     if (h->stream) cudaStreamDestroy(h->stream);
     delete h;
     return VEC_OK;
@@ -680,6 +695,147 @@ vec_status vecchia_autotune_load(vec_handle h, const char* path) {
     }
     (void)loaded;
     return VEC_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Host-side description of a batch and the uploads shared by the batched pass and fit.
+struct BatchPlan {
+    int nbatch, mmax, ntiles;
+    vg::PassPlan plan;
+    std::vector<int4> tiles;
+    std::vector<int> tile_off;
+    std::vector<long long> pt_off, nn_off;
+};
+
+vec_status prepare_batch(vec_handle h, int nbatch, const int64_t* point_offsets, const int* m,
+                         int d, int p, vec_covfun covfun, int prec, cudaStream_t st, BatchPlan* B) {
+    if (nbatch < 1) return fail(VEC_ERR_ARG, "nbatch = %d", nbatch);
+    if (!point_offsets || !m) return fail(VEC_ERR_ARG, "point_offsets and m are required");
+    if (point_offsets[0] != 0) return fail(VEC_ERR_ARG, "point_offsets[0] must be 0");
+    B->nbatch = nbatch;
+    B->mmax = 0;
+    B->pt_off.assign(point_offsets, point_offsets + nbatch + 1);
+    B->nn_off.assign(nbatch + 1, 0);
+    for (int b = 0; b < nbatch; ++b) {
+        const long long nb = point_offsets[b + 1] - point_offsets[b];
+        if (nb < 1) return fail(VEC_ERR_ARG, "dataset %d has n = %lld", b, nb);
+        if (m[b] < 0 || m[b] > vg::KMAX - 1)
+            return fail(VEC_ERR_UNSUPPORTED, "dataset %d: m = %d out of range", b, m[b]);
+        if (m[b] > B->mmax) B->mmax = m[b];
+        B->nn_off[b + 1] = B->nn_off[b] + nb * (m[b] + 1);
+    }
+    if (point_offsets[nbatch] > (int64_t)INT_MAX) return fail(VEC_ERR_ARG, "too many observations");
+    const int cov = (int)covfun;
+    // mapping: forced, else autotuned for (cov, mmax, d, p, prec, total n), else planned
+    int L = h->lanes, thr = h->threads;
+    if (L == 0 && thr == 0) {
+        const int lg = ilog2(point_offsets[nbatch]);
+        for (const TuneEntry& t : h->tune)
+            if (t.cov == cov && t.m == B->mmax && t.d == d && t.p == p && t.prec == prec + 2 &&
+                t.log2n == lg) { L = t.lanes; thr = t.threads; }
+    }
+    int pr = vg::plan_pass(cov, B->mmax, d, p, h->nsm, L, thr, &B->plan, prec, true);
+    if (pr == -1) pr = vg::plan_pass(cov, B->mmax, d, p, h->nsm, h->lanes, h->threads, &B->plan, prec, true);
+    if (pr == -1) return fail(VEC_ERR_UNSUPPORTED, "no kernel mapping fits m = %d, p = %d", B->mmax, p);
+    if (pr != 0) return cuda_fail(cudaGetLastError(), "planning the batched pass");
+    const int ngrp = B->plan.threads / B->plan.L;
+    const long long tsize = ngrp * 32 > 256 ? ngrp * 32 : 256;
+    B->tiles.clear();
+    B->tile_off.assign(nbatch + 1, 0);
+    for (int b = 0; b < nbatch; ++b) {
+        const long long nb = point_offsets[b + 1] - point_offsets[b];
+        for (long long s0 = 0; s0 < nb; s0 += tsize) {
+            long long e0 = s0 + tsize < nb ? s0 + tsize : nb;
+            B->tiles.push_back(make_int4(b, (int)s0, (int)e0, 0));
+        }
+        B->tile_off[b + 1] = (int)B->tiles.size();
+    }
+    B->ntiles = (int)B->tiles.size();
+    cudaError_t e = grow(&h->b_tiles, &h->c_tiles, (size_t)B->ntiles);
+    if (e == cudaSuccess) e = grow(&h->b_tile_off, &h->c_tile_off, (size_t)nbatch + 1);
+    if (e == cudaSuccess) e = grow(&h->b_pt_off, &h->c_pt_off, (size_t)nbatch + 1);
+    if (e == cudaSuccess) e = grow(&h->b_nn_off, &h->c_nn_off, (size_t)nbatch + 1);
+    if (e == cudaSuccess) e = grow(&h->b_m, &h->c_m, (size_t)nbatch);
+    if (e == cudaSuccess) e = grow(&h->b_status, &h->c_status, (size_t)nbatch);
+    if (e == cudaSuccess) e = grow(&h->b_bad, &h->c_bad, (size_t)nbatch);
+    if (e == cudaSuccess) e = grow(&h->b_counter, &h->c_counter, (size_t)1);
+    if (e == cudaSuccess) e = grow(&h->b_partials, &h->c_bpart, (size_t)B->ntiles * B->plan.nstat);
+    if (e == cudaSuccess && cov == vg::COV_MATERN)
+        e = grow(&h->b_tabs, &h->c_tabs, (size_t)nbatch * vg::mtab_doubles());
+    if (e == cudaSuccess && cov == vg::COV_MATERN && prec)
+        e = grow(&h->b_tabsf, &h->c_tabsf, (size_t)nbatch * vg::mtab_floats());
+    if (e != cudaSuccess) return cuda_fail(e, "allocating batch scratch");
+    e = cudaMemcpyAsync(h->b_tiles, B->tiles.data(), sizeof(int4) * B->ntiles, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->b_tile_off, B->tile_off.data(), sizeof(int) * (nbatch + 1), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->b_pt_off, B->pt_off.data(), sizeof(long long) * (nbatch + 1), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->b_nn_off, B->nn_off.data(), sizeof(long long) * (nbatch + 1), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->b_m, m, sizeof(int) * nbatch, cudaMemcpyHostToDevice, st);
+    // the host vectors are released when B goes out of scope: make the copies complete
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "uploading the batch description");
+    return VEC_OK;
+}
+
+// Enqueues one batched pass (device pointers); no host synchronisation.
+vec_status enqueue_batch(vec_handle h, const BatchPlan& B, const double* locs, const double* y,
+                         const double* X, const int32_t* NN, int d, int p, const double* covparms,
+                         vec_covfun covfun, int prec, cudaStream_t st, double* out,
+                         long long* dev_status, const int* active) {
+    const int cov = (int)covfun;
+    const int q = vecchia_nparms(covfun);
+    cudaError_t e = vg::launch_init_batch(h->b_status, h->b_bad, B.nbatch, h->b_counter, st);
+    if (e == cudaSuccess && cov == vg::COV_MATERN)
+        e = vg::launch_mtab_build_batch(covparms, B.nbatch, q, h->b_tabs, prec ? h->b_tabsf : nullptr, st);
+    if (e != cudaSuccess) return cuda_fail(e, "launching the batch setup kernels");
+    vg::BatchArgs a;
+    a.base.locs = locs; a.base.y = y; a.base.X = X; a.base.NN = NN; a.base.covparms = nullptr;
+    a.base.mtab = nullptr; a.base.mtabf = nullptr; a.base.partials = h->b_partials;
+    a.base.status = nullptr; a.base.bad = nullptr;
+    a.base.n = B.pt_off[B.nbatch]; a.base.d = d; a.base.p = p; a.base.m = B.mmax;
+    a.base.nstat = B.plan.nstat; a.base.nv = B.plan.nv; a.base.slot_stride = B.plan.slot_stride;
+    a.base.acc_per_lane = B.plan.acc_per_lane; a.base.tab_in_smem = B.plan.tab_smem;
+    a.pt_off = h->b_pt_off; a.nn_off = h->b_nn_off; a.m_b = h->b_m; a.covparms_b = covparms;
+    a.tabs = h->b_tabs; a.tabsf = h->b_tabsf; a.tiles = h->b_tiles; a.ntiles = B.ntiles;
+    a.tile_counter = h->b_counter; a.status_b = h->b_status; a.bad_b = h->b_bad; a.active_b = active;
+    e = vg::launch_pass_batch(cov, B.plan, a, st);
+    if (e == cudaSuccess)
+        e = vg::launch_profile_batch(h->b_partials, h->b_tile_off, B.nbatch, B.plan.nstat, p, cov,
+                                     h->b_pt_off, covparms, h->b_status, h->b_bad, out, dev_status, st);
+    if (e != cudaSuccess) return cuda_fail(e, "launching the batched pass");
+    return VEC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+vec_status vecchia_batch_loglik_grad_info(vec_handle h, int nbatch, const double* locs,
+                                          const double* y, const double* X, const int32_t* NNarray,
+                                          const int64_t* point_offsets, const int* m, int d, int p,
+                                          const double* covparms, vec_covfun covfun,
+                                          vec_precision prec, void* stream, double* out,
+                                          int64_t* dev_status) {
+    if (!h) return fail(VEC_ERR_ARG, "vecchia_batch_loglik_grad_info: NULL handle");
+    if (!locs || !y || !X || !NNarray || !covparms || !out || !dev_status)
+        return fail(VEC_ERR_ARG, "a required pointer is NULL");
+    if (vecchia_nparms(covfun) < 0) return fail(VEC_ERR_ARG, "unknown covariance function");
+    if (d < 1 || d > vg::DMAX || (covfun == VEC_EXP_SPACETIME && d != 3)) return fail(VEC_ERR_ARG, "bad d = %d", d);
+    if (p < 1 || p > vg::PMAX) return fail(VEC_ERR_ARG, "p = %d out of range", p);
+    if (prec != VEC_FP64 && prec != VEC_MIXED) return fail(VEC_ERR_ARG, "unknown precision");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(VEC_ERR_CUDA, "cannot select device %d", h->device);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    BatchPlan B;
+    vec_status s = prepare_batch(h, nbatch, point_offsets, m, d, p, covfun, (int)prec, st, &B);
+    if (s != VEC_OK) return s;
+    return enqueue_batch(h, B, locs, y, X, NNarray, d, p, covparms, covfun, (int)prec, st, out,
+                         reinterpret_cast<long long*>(dev_status), nullptr);
 }
 
 vec_status vecchia_covariance_pairs(vec_handle h, vec_covfun covfun, const double* covparms,

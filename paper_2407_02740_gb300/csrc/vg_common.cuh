@@ -103,6 +103,25 @@ struct PassArgs {
     int tab_in_smem;                   // copy the Matern table into shared memory
 };
 
+// Arguments of the batched pass kernel: many datasets (common d, p, covariance family),
+// concatenated; each has its own n, m and theta.  Work is a list of tiles, each a range of
+// observations of one dataset; each tile's sums become one record.
+struct BatchArgs {
+    PassArgs base;                      // concatenated locs/y/X/NN; m = largest m; sizes
+    const long long* __restrict__ pt_off;   // nbatch + 1 observation offsets
+    const long long* __restrict__ nn_off;   // nbatch + 1 NNarray element offsets
+    const int* __restrict__ m_b;            // nbatch
+    const double* __restrict__ covparms_b;  // nbatch x q
+    const double* __restrict__ tabs;        // nbatch x MT_DOUBLES (Matern)
+    const float* __restrict__ tabsf;        // nbatch x MT_FLOATS (Matern, mixed)
+    const int4* __restrict__ tiles;         // (dataset, first, end, unused)
+    int ntiles;
+    int* tile_counter;
+    int* status_b;                      // nbatch
+    long long* bad_b;                   // nbatch
+    const int* active_b;                // nbatch flags (datasets to evaluate), or nullptr = all
+};
+
 // Device-side error reporting: the first error code wins; the smallest failing
 // observation index is kept.
 __device__ __forceinline__ void report(int* status, long long* bad, int code, long long i) {

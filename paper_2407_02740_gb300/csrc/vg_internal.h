@@ -20,16 +20,28 @@ struct PassPlan {
     int slot_stride;   // bytes per shared-memory slot
     int acc_per_lane;  // accumulator doubles per thread
     int prec;          // 0 = FP64 kernel, 1 = mixed (FP32 block) kernel
+    int batched;       // plan made for the batched kernel
 };
 
 // Chooses the lanes-per-observation mapping that fits shared memory (or the forced one).
 // Returns 0 on success, -1 if no mapping fits, -2 on a CUDA error.
 int plan_pass(int cov, int m, int d, int p, int nsm, int force_L, int force_threads,
-              PassPlan* plan, int prec = 0);
+              PassPlan* plan, int prec = 0, bool batched = false);
 size_t pass_smem_bytes(int cov, int m, int d, int p, int L, int threads, bool tab_smem,
                        int prec = 0);
 const void* pass_kernel_f64(int cov, int L);
 const void* pass_kernel_f32(int cov, int L);
+const void* pass_batch_kernel_f64(int cov, int L);
+const void* pass_batch_kernel_f32(int cov, int L);
+cudaError_t launch_pass_batch(int cov, const PassPlan& plan, const BatchArgs& args, cudaStream_t st);
+cudaError_t launch_mtab_build_batch(const double* covparms_b, int nbatch, int q, double* tabs,
+                                    float* tabsf, cudaStream_t st);
+cudaError_t launch_init_batch(int* status_b, long long* bad_b, int nbatch, int* tile_counter,
+                              cudaStream_t st);
+cudaError_t launch_profile_batch(const double* partials, const int* tile_off, int nbatch, int nstat,
+                                 int p, int cov, const long long* pt_off, const double* covparms_b,
+                                 const int* status_b, const long long* bad_b, double* out,
+                                 long long* dev_status, cudaStream_t st);
 
 cudaError_t launch_pass(int cov, const PassPlan& plan, const PassArgs& args, cudaStream_t st);
 cudaError_t launch_init_status(int* status, long long* bad, cudaStream_t st);

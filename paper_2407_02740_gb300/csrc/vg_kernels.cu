@@ -22,8 +22,12 @@ namespace vg {
 // the parameter error).
 __global__ void __launch_bounds__(MT_NC * 32) k_mtab_build(const double* __restrict__ covparms,
                                                            double* __restrict__ tab,
-                                                           float* __restrict__ tabf) {
+                                                           float* __restrict__ tabf, int q) {
     __shared__ double vals[3][MT_NC];
+    // blockIdx.y selects the dataset of a batch: its parameters and its tables
+    covparms += (size_t)blockIdx.y * q;
+    tab += (size_t)blockIdx.y * MT_DOUBLES;
+    if (tabf) tabf += (size_t)blockIdx.y * MT_FLOATS;
     const double nu = covparms[2];
     if (!(nu >= 0.05 && nu <= 20.0)) return;
     const int it = blockIdx.x;
@@ -86,27 +90,17 @@ __global__ void k_init_status(int* status, long long* bad) {
     bad[0] = LLONG_MAX;
 }
 
-// Profile step.  tot = sum over blocks of the partial records; the sigma2 entries are
+// Profile step from the summed record tot (nstat entries).  The sigma2 entries are
 // formed here from the totals (dSigma/dsigma2 = Sigma/sigma2 with the relative nugget):
 //   dlogdet_0 = n/sigma2, dySy_0 = -ySy/sigma2, dySX_0 = -ySX/sigma2, dXSX_0 = -XSX/sigma2,
 //   info_00 = n/(2 sigma2^2), info_0l = dlogdet_l/(2 sigma2).
-__global__ void k_profile(const double* __restrict__ partials, int nblk, int nstat, int p,
-                          int cov, long long n, const double* __restrict__ covparms,
-                          const int* status, const long long* bad, double* out,
-                          long long* dev_status) {
-    __shared__ double tot[256];
-    const int tid = threadIdx.x;
-    for (int t = tid; t < nstat; t += blockDim.x) {
-        double s = 0.0;
-        for (int b = 0; b < nblk; ++b) s += partials[(size_t)b * nstat + t];
-        tot[t] = s;
-    }
-    __syncthreads();
-    if (tid != 0) return;
+__device__ void profile_from_totals(const double* tot, int p, int cov, long long n,
+                                    const double* covparms, int st0, long long bad0, double* out,
+                                    long long* dev_status) {
     const int q = nparms(cov), Q = q - 1;
     RecLayout RL;
     RL.init(p, Q);
-    int st = status[0];
+    int st = st0;
     const int nout = 1 + q + q * q + p;
     double XSX[PMAX * PMAX], ySX[PMAX], dySX[4][PMAX], dXSX[4][PMAX * PMAX];
     double dlogdet[4], dySy[4], info[16];
@@ -147,6 +141,7 @@ __global__ void k_profile(const double* __restrict__ partials, int nblk, int nst
 
     // betahat = XSX^-1 ySX by Cholesky
     double Lc[PMAX * PMAX], z[PMAX], beta[PMAX];
+    for (int a = 0; a < PMAX; ++a) beta[a] = 0.0;
     bool pd = true;
     for (int c = 0; c < p && pd; ++c) {
         double v = XSX[c * p + c];
@@ -192,7 +187,52 @@ __global__ void k_profile(const double* __restrict__ partials, int nblk, int nst
     if (st != 0)
         for (int t = 0; t < nout; ++t) out[t] = __longlong_as_double(0x7ff8000000000000ll);
     dev_status[0] = st;
-    dev_status[1] = (bad[0] == LLONG_MAX) ? -1 : bad[0];
+    dev_status[1] = (bad0 == LLONG_MAX) ? -1 : bad0;
+}
+
+// Single dataset: sum the per-block partial records in a fixed order, then profile.
+__global__ void k_profile(const double* __restrict__ partials, int nblk, int nstat, int p,
+                          int cov, long long n, const double* __restrict__ covparms,
+                          const int* status, const long long* bad, double* out,
+                          long long* dev_status) {
+    __shared__ double tot[256];
+    const int tid = threadIdx.x;
+    for (int t = tid; t < nstat; t += blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < nblk; ++b) s += partials[(size_t)b * nstat + t];
+        tot[t] = s;
+    }
+    __syncthreads();
+    if (tid == 0) profile_from_totals(tot, p, cov, n, covparms, status[0], bad[0], out, dev_status);
+}
+
+// Batch: block b sums the records of dataset b's tiles [tile_off[b], tile_off[b+1]) in
+// order and profiles them with the dataset's parameters.
+__global__ void k_profile_batch(const double* __restrict__ partials, const int* __restrict__ tile_off,
+                                int nstat, int p, int cov, const long long* __restrict__ pt_off,
+                                const double* __restrict__ covparms_b, const int* status_b,
+                                const long long* bad_b, double* out, long long* dev_status) {
+    __shared__ double tot[256];
+    const int b = blockIdx.x, tid = threadIdx.x;
+    const int q = nparms(cov);
+    const int nout = 1 + q + q * q + p;
+    for (int t = tid; t < nstat; t += blockDim.x) {
+        double s = 0.0;
+        for (int k = tile_off[b]; k < tile_off[b + 1]; ++k) s += partials[(size_t)k * nstat + t];
+        tot[t] = s;
+    }
+    __syncthreads();
+    if (tid == 0)
+        profile_from_totals(tot, p, cov, pt_off[b + 1] - pt_off[b], covparms_b + (size_t)b * q,
+                            status_b[b], bad_b[b], out + (size_t)b * nout, dev_status + 2 * (size_t)b);
+}
+
+__global__ void k_init_batch(int* status_b, long long* bad_b, int nbatch, int* tile_counter) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbatch; b += gridDim.x * blockDim.x) {
+        status_b[b] = 0;
+        bad_b[b] = LLONG_MAX;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *tile_counter = 0;
 }
 
 // Covariance C and its q theta-derivatives for npairs location pairs (AoS, d each).
@@ -255,7 +295,8 @@ __global__ void k_cov_pairs(const double* __restrict__ covparms, const double* _
 // ----------------------------------------------------------------------------------------
 static int nv_of(int p, int Q) { return 4 + p + Q * (3 + p) + Q * (Q + 1) / 2; }
 
-static const void* pass_kernel(int cov, int L, int prec) {
+static const void* pass_kernel(int cov, int L, int prec, bool batched = false) {
+    if (batched) return prec == 0 ? pass_batch_kernel_f64(cov, L) : pass_batch_kernel_f32(cov, L);
     return prec == 0 ? pass_kernel_f64(cov, L) : pass_kernel_f32(cov, L);
 }
 
@@ -277,7 +318,7 @@ size_t pass_smem_bytes(int cov, int m, int d, int p, int L, int threads, bool ta
 }
 
 int plan_pass(int cov, int m, int d, int p, int nsm, int force_L, int force_threads,
-              PassPlan* plan, int prec) {
+              PassPlan* plan, int prec, bool batched) {
     // Preference: 256 threads (two warps per SM sub-partition, so that one warp's FP64
     // dependency waits are covered by the other), then 128 (one warp per sub-partition,
     // the minimum that occupies all FP64 units), then fewer when the largest blocks do
@@ -312,7 +353,8 @@ int plan_pass(int cov, int m, int d, int p, int nsm, int force_L, int force_thre
     plan->prec = prec;
     plan->acc_per_lane = (RL.nstat + chosen - 1) / chosen;
     plan->smem = pass_smem_bytes(cov, m, d, p, chosen, threads, tab, prec);
-    const void* fn = pass_kernel(cov, chosen, prec);
+    plan->batched = batched ? 1 : 0;
+    const void* fn = pass_kernel(cov, chosen, prec, batched);
     if (!fn) return -1;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan->smem) !=
         cudaSuccess)
@@ -333,13 +375,42 @@ cudaError_t launch_pass(int cov, const PassPlan& plan, const PassArgs& args, cud
     return cudaLaunchKernel(fn, dim3(plan.grid), dim3(plan.threads), params, plan.smem, st);
 }
 
+cudaError_t launch_pass_batch(int cov, const PassPlan& plan, const BatchArgs& args, cudaStream_t st) {
+    const void* fn = pass_kernel(cov, plan.L, plan.prec, true);
+    if (!fn) return cudaErrorInvalidValue;
+    BatchArgs a = args;
+    void* params[] = {&a};
+    return cudaLaunchKernel(fn, dim3(plan.grid), dim3(plan.threads), params, plan.smem, st);
+}
+
+cudaError_t launch_mtab_build_batch(const double* covparms_b, int nbatch, int q, double* tabs,
+                                    float* tabsf, cudaStream_t st) {
+    k_mtab_build<<<dim3(MT_NINT, nbatch), MT_NC * 32, 0, st>>>(covparms_b, tabs, tabsf, q);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_batch(int* status_b, long long* bad_b, int nbatch, int* tile_counter,
+                              cudaStream_t st) {
+    k_init_batch<<<(nbatch + 255) / 256, 256, 0, st>>>(status_b, bad_b, nbatch, tile_counter);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_profile_batch(const double* partials, const int* tile_off, int nbatch, int nstat,
+                                 int p, int cov, const long long* pt_off, const double* covparms_b,
+                                 const int* status_b, const long long* bad_b, double* out,
+                                 long long* dev_status, cudaStream_t st) {
+    k_profile_batch<<<nbatch, 256, 0, st>>>(partials, tile_off, nstat, p, cov, pt_off, covparms_b,
+                                           status_b, bad_b, out, dev_status);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_init_status(int* status, long long* bad, cudaStream_t st) {
     k_init_status<<<1, 1, 0, st>>>(status, bad);
     return cudaGetLastError();
 }
 
 cudaError_t launch_mtab_build(const double* covparms, double* tab, float* tabf, cudaStream_t st) {
-    k_mtab_build<<<MT_NINT, MT_NC * 32, 0, st>>>(covparms, tab, tabf);
+    k_mtab_build<<<MT_NINT, MT_NC * 32, 0, st>>>(covparms, tab, tabf, 4);
     return cudaGetLastError();
 }
 

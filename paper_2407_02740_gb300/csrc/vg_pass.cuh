@@ -140,6 +140,313 @@ __device__ __forceinline__ bool circle_pair(int Kp, int Nv, int r, int k, int& a
     return true;
 }
 
+// Everything the per-observation body needs: the group's lanes and shared-memory slot,
+// the data of the dataset being processed, and per-pass constants derived from theta.
+template <typename T, typename Tab>
+struct PassEnv {
+    // group
+    int gl;
+    unsigned gmask;
+    // slot (shared memory)
+    T *A, *Yg, *invd, *loc, *bacc, *bv, *G, *D1;
+    double* V;
+    int* idx;
+    int Kmax;             // slot stride: largest block size of the launch
+    // dataset
+    const double* locs;
+    const double* y;
+    const double* X;
+    const int32_t* NN;
+    int d, p, m;          // m: NNarray row width - 1 of this dataset
+    int* status;
+    long long* bad;
+    // theta-derived
+    double nu, m_psi, m_lg, inv_r1, inv_r2;
+    T sig2T, diagC, inv_r1T, inv_r2T;
+    const Tab* tab;
+    // record formulas and per-lane sums
+    const uint32_t* sidx;
+    double* acc;
+    int nstat, vb0, vstep, vmm;
+};
+
+// Algorithm 1 for observation i of the dataset in E (all L lanes of the group call it).
+template <int COV, int L, typename T, typename Tab>
+__device__ __forceinline__ void vecchia_point(const PassEnv<T, Tab>& E, long long i) {
+    using N = Num<T>;
+    using MT = MaternT<T>;
+    constexpr int NG = npair_derivs(COV);
+    constexpr int Q = NG + 1;
+    const int gl = E.gl;
+    const unsigned gmask = E.gmask;
+    const int d = E.d, p = E.p, m = E.m, Kmax = E.Kmax;
+    T* A = E.A; T* Yg = E.Yg; T* invd = E.invd; T* loc = E.loc; T* bacc = E.bacc;
+    T* bv = E.bv; T* G = E.G; T* D1 = E.D1;
+    double* V = E.V;
+    int* idx = E.idx;
+    const T sig2T = E.sig2T, diagC = E.diagC, inv_r1T = E.inv_r1T, inv_r2T = E.inv_r2T;
+    const double inv_r1 = E.inv_r1, inv_r2 = E.inv_r2, m_psi = E.m_psi, m_lg = E.m_lg;
+    const Tab* tab = E.tab;
+    const uint32_t* sidx = E.sidx;
+    double* acc = E.acc;
+    const int vb0 = E.vb0, vstep = E.vstep, vmm = E.vmm;
+    // ---------------- gather ----------------
+    const int32_t* row = E.NN + i * (long long)(m + 1);
+    int cnt = 0, badrow = 0;
+    for (int c = gl; c <= m; c += L) {
+        int v = row[c];
+        if (c == 0) badrow |= (v != (int)i);
+        else if (v >= 0) {
+            cnt++;
+            badrow |= (v >= i) | (c >= 2 && row[c - 1] < 0);
+        } else if (v != -1) badrow = 1;
+    }
+    cnt = gsum<L>(cnt, gmask);
+    badrow = gsum<L>(badrow, gmask);
+    if (badrow) {
+        if (gl == 0) report(E.status, E.bad, ST_ARG, i);
+        return;
+    }
+    const int Kp = cnt + 1;
+    const double* li = E.locs + i * (long long)d;
+    for (int a = gl; a < Kp; a += L) {
+        int j = row[Kp - 1 - a];
+        idx[a] = j;
+        // coordinates relative to the observation, divided by their range parameter
+        // (FP64 difference, then rounded to T): squared distances come out scaled
+        for (int k = 0; k < d; ++k)
+            loc[k * Kmax + a] = (T)((E.locs[(long long)j * d + k] - li[k]) *
+                                    ((COV == COV_ST && k == 2) ? inv_r2 : inv_r1));
+        Yg[a] = (T)E.y[j];
+        for (int t = 0; t < p; ++t) Yg[(1 + t) * Kmax + a] = (T)E.X[(long long)j * p + t];
+    }
+    gsync<L>(gmask);
+
+    // ---------------- covariance assembly (packed lower triangle) ----------------
+    const int ntri = Kp * (Kp + 1) / 2;
+    for (int e = gl; e < ntri; e += L) {
+        int a = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+        while (a * (a + 1) / 2 > e) --a;
+        while ((a + 1) * (a + 2) / 2 <= e) ++a;
+        int c = e - a * (a + 1) / 2;
+        T C;
+        if (a == c) {
+            C = diagC;
+        } else if (COV == COV_EXP) {
+            T s = (T)0;
+            for (int k = 0; k < d; ++k) {
+                T t = loc[k * Kmax + a] - loc[k * Kmax + c];
+                s = N::fma_(t, t, s);
+            }
+            T x = N::sqrt_(s);
+            T ex = sig2T * N::exp_(-x);
+            C = ex;
+            D1[a * (a - 1) / 2 + c] = ex * x;          // rho dC/drho
+        } else if (COV == COV_ST) {
+            T t0 = loc[a] - loc[c];
+            T t1 = loc[Kmax + a] - loc[Kmax + c];
+            T t2 = loc[2 * Kmax + a] - loc[2 * Kmax + c];
+            T u = N::fma_(t0, t0, N::fma_(t1, t1, t2 * t2));
+            T D = N::sqrt_(u);
+            T ex = sig2T * N::exp_(-D);
+            C = ex;
+            D1[a * (a - 1) / 2 + c] = D > (T)0 ? ex / D : (T)0;
+        } else {  // Matern
+            T s = (T)0;
+            for (int k = 0; k < d; ++k) {
+                T t = loc[k * Kmax + a] - loc[k * Kmax + c];
+                s = N::fma_(t, t, s);
+            }
+            C = sig2T * MT::F0(tab, s, E.nu, m_psi, m_lg);
+        }
+        A[e] = C;
+    }
+    gsync<L>(gmask);
+
+    // ---------------- Cholesky + forward solves of y and X ----------------
+    // combined rows: r < Kp -> matrix row r (packed), r >= Kp -> augmented row r - Kp
+    const int R = Kp + 1 + p;
+    bool pd = true;
+    for (int c = 0; c < Kp; ++c) {
+        const T* Lc = A + c * (c + 1) / 2;
+        const int r0 = c + ((gl - c) & (L - 1));
+        for (int r = r0; r < R; r += L) {
+            T* Rr = r < Kp ? A + r * (r + 1) / 2 : Yg + (r - Kp) * Kmax;
+            T v0 = Rr[c], v1 = (T)0;
+            int s = 0;
+            for (; s + 1 < c; s += 2) {
+                v0 = N::fma_(-Rr[s], Lc[s], v0);
+                v1 = N::fma_(-Rr[s + 1], Lc[s + 1], v1);
+            }
+            if (s < c) v0 = N::fma_(-Rr[s], Lc[s], v0);
+            Rr[c] = v0 + v1;
+        }
+        gsync<L>(gmask);
+        const T vc = Lc[c];
+        if (!(vc > (T)0) || !N::finite_(vc)) { pd = false; break; }
+        const T ic = N::rsqrt_pivot(vc);
+        if (r0 == c) invd[c] = ic;
+        for (int r = (r0 == c ? r0 + L : r0); r < R; r += L) {
+            T* Rr = r < Kp ? A + r * (r + 1) / 2 : Yg + (r - Kp) * Kmax;
+            Rr[c] *= ic;
+        }
+        gsync<L>(gmask);
+    }
+    if (!pd) {
+        if (gl == 0) report(E.status, E.bad, ST_NOT_PD, i);
+        gsync<L>(gmask);
+        return;
+    }
+    const int last = Kp - 1;
+
+    // ---------------- b = last row of L^-1 (L^T b^T = e_last) ----------------
+    for (int a = gl; a < Kp; a += L) bacc[a] = (a == last) ? (T)1 : (T)0;
+    gsync<L>(gmask);
+    for (int c = last; c >= 0; --c) {
+        const T bc = bacc[c] * invd[c];
+        if (((c - gl) & (L - 1)) == 0) bv[c] = bc;
+        const T* Lr = A + c * (c + 1) / 2;
+        for (int a = gl; a < c; a += L) bacc[a] = N::fma_(-Lr[a], bc, bacc[a]);
+        gsync<L>(gmask);
+    }
+
+    // ---------------- g_j = dSigma_j b^T ----------------
+    // g for the pair-derivative parameters starts at 0; the nugget one is sigma2 b.
+    for (int a = gl; a < Kp; a += L) {
+#pragma unroll
+        for (int j = 0; j < NG; ++j) G[j * Kmax + a] = (T)0;
+        G[NG * Kmax + a] = sig2T * bv[a];
+    }
+    gsync<L>(gmask);
+    {
+        const int Nv = (Kp & 1) ? Kp + 1 : Kp;
+        const int npr = Nv / 2;
+        for (int r = 0; r < Nv - 1; ++r) {
+            for (int k = gl; k < npr; k += L) {
+                int a, c;
+                if (!circle_pair(Kp, Nv, r, k, a, c)) continue;
+                T dv[NG];
+                if (COV == COV_EXP) {
+                    dv[0] = D1[a * (a - 1) / 2 + c] * inv_r1T;
+                } else if (COV == COV_ST) {
+                    T t0 = loc[a] - loc[c];
+                    T t1 = loc[Kmax + a] - loc[Kmax + c];
+                    T t2 = loc[2 * Kmax + a] - loc[2 * Kmax + c];
+                    T w = D1[a * (a - 1) / 2 + c];
+                    dv[0] = w * N::fma_(t0, t0, t1 * t1) * inv_r1T;
+                    if (NG > 1) dv[NG - 1] = w * t2 * t2 * inv_r2T;
+                } else {
+                    T s = (T)0;
+                    for (int kk = 0; kk < d; ++kk) {
+                        T t = loc[kk * Kmax + a] - loc[kk * Kmax + c];
+                        s = N::fma_(t, t, s);
+                    }
+                    T F1, F2;
+                    MT::F12(tab, s, E.nu, m_psi, m_lg, F1, F2);
+                    dv[0] = sig2T * F1 * inv_r1T;
+                    if (NG > 1) dv[NG - 1] = sig2T * F2;
+                }
+                const T ba = bv[a], bc = bv[c];
+#pragma unroll
+                for (int j = 0; j < NG; ++j) {
+                    G[j * Kmax + a] = N::fma_(dv[j], bc, G[j * Kmax + a]);
+                    G[j * Kmax + c] = N::fma_(dv[j], ba, G[j * Kmax + c]);
+                }
+            }
+            gsync<L>(gmask);
+        }
+    }
+
+    // ---------------- m_j = L^-1 g_j (in place, column sweep) ----------------
+    // Column c: every lane reads the finished residual g_j[c] and scales it; after a
+    // group barrier the owner of c stores m_j[c] and each lane updates its rows a > c.
+    for (int c = 0; c < Kp; ++c) {
+        const T ic = invd[c];
+        T mc[Q];
+#pragma unroll
+        for (int j = 0; j < Q; ++j) mc[j] = G[j * Kmax + c] * ic;
+        gsync<L>(gmask);
+        if (((c - gl) & (L - 1)) == 0) {
+#pragma unroll
+            for (int j = 0; j < Q; ++j) G[j * Kmax + c] = mc[j];
+        }
+        const int a0 = c + 1 + ((gl - c - 1) & (L - 1));
+        for (int a = a0; a < Kp; a += L) {
+            const T lac = A[a * (a + 1) / 2 + c];
+#pragma unroll
+            for (int j = 0; j < Q; ++j) G[j * Kmax + a] = N::fma_(-lac, mc[j], G[j * Kmax + a]);
+        }
+        gsync<L>(gmask);
+    }
+
+    // ---------------- per-observation values ----------------
+    {
+        // partial dot products over this lane's entries, last entry of hat() halved
+        T dl[Q], dx[Q][PMAX], mm[Q * (Q + 1) / 2];
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+            dl[j] = (T)0;
+            for (int t = 0; t < p; ++t) dx[j][t] = (T)0;
+        }
+#pragma unroll
+        for (int t = 0; t < Q * (Q + 1) / 2; ++t) mm[t] = (T)0;
+        for (int a = gl; a < Kp; a += L) {
+            const T hf = (a == last) ? (T)0.5 : (T)1;
+            const T ly = Yg[a] * hf;
+            T mj[Q];
+#pragma unroll
+            for (int j = 0; j < Q; ++j) {
+                mj[j] = G[j * Kmax + a];
+                dl[j] = N::fma_(mj[j], ly, dl[j]);
+            }
+            for (int t = 0; t < p; ++t) {
+                const T lx = Yg[(1 + t) * Kmax + a] * hf;
+#pragma unroll
+                for (int j = 0; j < Q; ++j) dx[j][t] = N::fma_(mj[j], lx, dx[j][t]);
+            }
+            int u = 0;
+#pragma unroll
+            for (int j = 0; j < Q; ++j)
+#pragma unroll
+                for (int l = j; l < Q; ++l) { mm[u] = N::fma_(mj[j], mj[l], mm[u]); ++u; }
+        }
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+            dl[j] = gsum<L>(dl[j], gmask);
+            for (int t = 0; t < p; ++t) dx[j][t] = gsum<L>(dx[j][t], gmask);
+        }
+#pragma unroll
+        for (int t = 0; t < Q * (Q + 1) / 2; ++t) mm[t] = gsum<L>(mm[t], gmask);
+        if (gl == 0) {
+            V[0] = 1.0;
+            V[1] = 0.0;
+            V[2] = -2.0 * log((double)invd[last]);
+            V[3] = (double)Yg[last];
+            for (int t = 0; t < p; ++t) V[4 + t] = (double)Yg[(1 + t) * Kmax + last];
+#pragma unroll
+            for (int j = 0; j < Q; ++j) {
+                const int vb = vb0 + j * vstep;
+                const double md = (double)G[j * Kmax + last];
+                V[vb] = md;
+                V[vb + 1] = -(double)dl[j];
+                for (int t = 0; t < p; ++t) V[vb + 2 + t] = -(double)dx[j][t];
+                V[vb + 2 + p] = -0.5 * md;
+            }
+#pragma unroll
+            for (int t = 0; t < Q * (Q + 1) / 2; ++t) V[vmm + t] = (double)mm[t];
+        }
+        gsync<L>(gmask);
+    }
+
+    // ---------------- accumulate the record (FP64) ----------------
+    for (int t = gl, k = 0; t < E.nstat; t += L, ++k) {
+        const uint32_t w = sidx[t];
+        const double v1 = V[w & 255u] * V[(w >> 8) & 255u];
+        acc[k] += fma(V[(w >> 16) & 255u], V[w >> 24], v1);
+    }
+    gsync<L>(gmask);
+}
+
 template <int COV, int L, typename T>
 __global__ void __launch_bounds__(256) k_pass(PassArgs args) {
     extern __shared__ __align__(16) double smem[];
@@ -247,263 +554,19 @@ __global__ void __launch_bounds__(256) k_pass(PassArgs args) {
 
     const long long n = args.n;
     const long long gstride = (long long)gridDim.x * ngrp;
-    for (long long i = (long long)blockIdx.x * ngrp + grp; ok && i < n; i += gstride) {
-        // ---------------- gather ----------------
-        const int32_t* row = args.NN + i * (long long)(m + 1);
-        int cnt = 0, badrow = 0;
-        for (int c = gl; c <= m; c += L) {
-            int v = row[c];
-            if (c == 0) badrow |= (v != (int)i);
-            else if (v >= 0) {
-                cnt++;
-                badrow |= (v >= i) | (c >= 2 && row[c - 1] < 0);
-            } else if (v != -1) badrow = 1;
-        }
-        cnt = gsum<L>(cnt, gmask);
-        badrow = gsum<L>(badrow, gmask);
-        if (badrow) {
-            if (gl == 0) report(args.status, args.bad, ST_ARG, i);
-            continue;
-        }
-        const int Kp = cnt + 1;
-        const double* li = args.locs + i * (long long)d;
-        for (int a = gl; a < Kp; a += L) {
-            int j = row[Kp - 1 - a];
-            idx[a] = j;
-            // coordinates relative to the observation, divided by their range parameter
-            // (FP64 difference, then rounded to T): squared distances come out scaled
-            for (int k = 0; k < d; ++k)
-                loc[k * Kmax + a] = (T)((args.locs[(long long)j * d + k] - li[k]) *
-                                        ((COV == COV_ST && k == 2) ? inv_r2 : inv_r1));
-            Yg[a] = (T)args.y[j];
-            for (int t = 0; t < p; ++t) Yg[(1 + t) * Kmax + a] = (T)args.X[(long long)j * p + t];
-        }
-        gsync<L>(gmask);
-
-        // ---------------- covariance assembly (packed lower triangle) ----------------
-        const int ntri = Kp * (Kp + 1) / 2;
-        for (int e = gl; e < ntri; e += L) {
-            int a = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-            while (a * (a + 1) / 2 > e) --a;
-            while ((a + 1) * (a + 2) / 2 <= e) ++a;
-            int c = e - a * (a + 1) / 2;
-            T C;
-            if (a == c) {
-                C = diagC;
-            } else if (COV == COV_EXP) {
-                T s = (T)0;
-                for (int k = 0; k < d; ++k) {
-                    T t = loc[k * Kmax + a] - loc[k * Kmax + c];
-                    s = N::fma_(t, t, s);
-                }
-                T x = N::sqrt_(s);
-                T ex = sig2T * N::exp_(-x);
-                C = ex;
-                D1[a * (a - 1) / 2 + c] = ex * x;          // rho dC/drho
-            } else if (COV == COV_ST) {
-                T t0 = loc[a] - loc[c];
-                T t1 = loc[Kmax + a] - loc[Kmax + c];
-                T t2 = loc[2 * Kmax + a] - loc[2 * Kmax + c];
-                T u = N::fma_(t0, t0, N::fma_(t1, t1, t2 * t2));
-                T D = N::sqrt_(u);
-                T ex = sig2T * N::exp_(-D);
-                C = ex;
-                D1[a * (a - 1) / 2 + c] = D > (T)0 ? ex / D : (T)0;
-            } else {  // Matern
-                T s = (T)0;
-                for (int k = 0; k < d; ++k) {
-                    T t = loc[k * Kmax + a] - loc[k * Kmax + c];
-                    s = N::fma_(t, t, s);
-                }
-                C = sig2T * MT::F0(tab, s, th[2], m_psi, m_lg);
-            }
-            A[e] = C;
-        }
-        gsync<L>(gmask);
-
-        // ---------------- Cholesky + forward solves of y and X ----------------
-        // combined rows: r < Kp -> matrix row r (packed), r >= Kp -> augmented row r - Kp
-        const int R = Kp + 1 + p;
-        bool pd = true;
-        for (int c = 0; c < Kp; ++c) {
-            const T* Lc = A + c * (c + 1) / 2;
-            const int r0 = c + ((gl - c) & (L - 1));
-            for (int r = r0; r < R; r += L) {
-                T* Rr = r < Kp ? A + r * (r + 1) / 2 : Yg + (r - Kp) * Kmax;
-                T v0 = Rr[c], v1 = (T)0;
-                int s = 0;
-                for (; s + 1 < c; s += 2) {
-                    v0 = N::fma_(-Rr[s], Lc[s], v0);
-                    v1 = N::fma_(-Rr[s + 1], Lc[s + 1], v1);
-                }
-                if (s < c) v0 = N::fma_(-Rr[s], Lc[s], v0);
-                Rr[c] = v0 + v1;
-            }
-            gsync<L>(gmask);
-            const T vc = Lc[c];
-            if (!(vc > (T)0) || !N::finite_(vc)) { pd = false; break; }
-            const T ic = N::rsqrt_pivot(vc);
-            if (r0 == c) invd[c] = ic;
-            for (int r = (r0 == c ? r0 + L : r0); r < R; r += L) {
-                T* Rr = r < Kp ? A + r * (r + 1) / 2 : Yg + (r - Kp) * Kmax;
-                Rr[c] *= ic;
-            }
-            gsync<L>(gmask);
-        }
-        if (!pd) {
-            if (gl == 0) report(args.status, args.bad, ST_NOT_PD, i);
-            gsync<L>(gmask);
-            continue;
-        }
-        const int last = Kp - 1;
-
-        // ---------------- b = last row of L^-1 (L^T b^T = e_last) ----------------
-        for (int a = gl; a < Kp; a += L) bacc[a] = (a == last) ? (T)1 : (T)0;
-        gsync<L>(gmask);
-        for (int c = last; c >= 0; --c) {
-            const T bc = bacc[c] * invd[c];
-            if (((c - gl) & (L - 1)) == 0) bv[c] = bc;
-            const T* Lr = A + c * (c + 1) / 2;
-            for (int a = gl; a < c; a += L) bacc[a] = N::fma_(-Lr[a], bc, bacc[a]);
-            gsync<L>(gmask);
-        }
-
-        // ---------------- g_j = dSigma_j b^T ----------------
-        // g for the pair-derivative parameters starts at 0; the nugget one is sigma2 b.
-        for (int a = gl; a < Kp; a += L) {
-#pragma unroll
-            for (int j = 0; j < NG; ++j) G[j * Kmax + a] = (T)0;
-            G[NG * Kmax + a] = sig2T * bv[a];
-        }
-        gsync<L>(gmask);
-        {
-            const int Nv = (Kp & 1) ? Kp + 1 : Kp;
-            const int npr = Nv / 2;
-            for (int r = 0; r < Nv - 1; ++r) {
-                for (int k = gl; k < npr; k += L) {
-                    int a, c;
-                    if (!circle_pair(Kp, Nv, r, k, a, c)) continue;
-                    T dv[NG];
-                    if (COV == COV_EXP) {
-                        dv[0] = D1[a * (a - 1) / 2 + c] * inv_r1T;
-                    } else if (COV == COV_ST) {
-                        T t0 = loc[a] - loc[c];
-                        T t1 = loc[Kmax + a] - loc[Kmax + c];
-                        T t2 = loc[2 * Kmax + a] - loc[2 * Kmax + c];
-                        T w = D1[a * (a - 1) / 2 + c];
-                        dv[0] = w * N::fma_(t0, t0, t1 * t1) * inv_r1T;
-                        if (NG > 1) dv[NG - 1] = w * t2 * t2 * inv_r2T;
-                    } else {
-                        T s = (T)0;
-                        for (int kk = 0; kk < d; ++kk) {
-                            T t = loc[kk * Kmax + a] - loc[kk * Kmax + c];
-                            s = N::fma_(t, t, s);
-                        }
-                        T F1, F2;
-                        MT::F12(tab, s, th[2], m_psi, m_lg, F1, F2);
-                        dv[0] = sig2T * F1 * inv_r1T;
-                        if (NG > 1) dv[NG - 1] = sig2T * F2;
-                    }
-                    const T ba = bv[a], bc = bv[c];
-#pragma unroll
-                    for (int j = 0; j < NG; ++j) {
-                        G[j * Kmax + a] = N::fma_(dv[j], bc, G[j * Kmax + a]);
-                        G[j * Kmax + c] = N::fma_(dv[j], ba, G[j * Kmax + c]);
-                    }
-                }
-                gsync<L>(gmask);
-            }
-        }
-
-        // ---------------- m_j = L^-1 g_j (in place, column sweep) ----------------
-        // Column c: every lane reads the finished residual g_j[c] and scales it; after a
-        // group barrier the owner of c stores m_j[c] and each lane updates its rows a > c.
-        for (int c = 0; c < Kp; ++c) {
-            const T ic = invd[c];
-            T mc[Q];
-#pragma unroll
-            for (int j = 0; j < Q; ++j) mc[j] = G[j * Kmax + c] * ic;
-            gsync<L>(gmask);
-            if (((c - gl) & (L - 1)) == 0) {
-#pragma unroll
-                for (int j = 0; j < Q; ++j) G[j * Kmax + c] = mc[j];
-            }
-            const int a0 = c + 1 + ((gl - c - 1) & (L - 1));
-            for (int a = a0; a < Kp; a += L) {
-                const T lac = A[a * (a + 1) / 2 + c];
-#pragma unroll
-                for (int j = 0; j < Q; ++j) G[j * Kmax + a] = N::fma_(-lac, mc[j], G[j * Kmax + a]);
-            }
-            gsync<L>(gmask);
-        }
-
-        // ---------------- per-observation values ----------------
-        {
-            // partial dot products over this lane's entries, last entry of hat() halved
-            T dl[Q], dx[Q][PMAX], mm[Q * (Q + 1) / 2];
-#pragma unroll
-            for (int j = 0; j < Q; ++j) {
-                dl[j] = (T)0;
-                for (int t = 0; t < p; ++t) dx[j][t] = (T)0;
-            }
-#pragma unroll
-            for (int t = 0; t < Q * (Q + 1) / 2; ++t) mm[t] = (T)0;
-            for (int a = gl; a < Kp; a += L) {
-                const T hf = (a == last) ? (T)0.5 : (T)1;
-                const T ly = Yg[a] * hf;
-                T mj[Q];
-#pragma unroll
-                for (int j = 0; j < Q; ++j) {
-                    mj[j] = G[j * Kmax + a];
-                    dl[j] = N::fma_(mj[j], ly, dl[j]);
-                }
-                for (int t = 0; t < p; ++t) {
-                    const T lx = Yg[(1 + t) * Kmax + a] * hf;
-#pragma unroll
-                    for (int j = 0; j < Q; ++j) dx[j][t] = N::fma_(mj[j], lx, dx[j][t]);
-                }
-                int u = 0;
-#pragma unroll
-                for (int j = 0; j < Q; ++j)
-#pragma unroll
-                    for (int l = j; l < Q; ++l) { mm[u] = N::fma_(mj[j], mj[l], mm[u]); ++u; }
-            }
-#pragma unroll
-            for (int j = 0; j < Q; ++j) {
-                dl[j] = gsum<L>(dl[j], gmask);
-                for (int t = 0; t < p; ++t) dx[j][t] = gsum<L>(dx[j][t], gmask);
-            }
-#pragma unroll
-            for (int t = 0; t < Q * (Q + 1) / 2; ++t) mm[t] = gsum<L>(mm[t], gmask);
-            if (gl == 0) {
-                V[0] = 1.0;
-                V[1] = 0.0;
-                V[2] = -2.0 * log((double)invd[last]);
-                V[3] = (double)Yg[last];
-                for (int t = 0; t < p; ++t) V[4 + t] = (double)Yg[(1 + t) * Kmax + last];
-#pragma unroll
-                for (int j = 0; j < Q; ++j) {
-                    const int vb = vb0 + j * vstep;
-                    const double md = (double)G[j * Kmax + last];
-                    V[vb] = md;
-                    V[vb + 1] = -(double)dl[j];
-                    for (int t = 0; t < p; ++t) V[vb + 2 + t] = -(double)dx[j][t];
-                    V[vb + 2 + p] = -0.5 * md;
-                }
-#pragma unroll
-                for (int t = 0; t < Q * (Q + 1) / 2; ++t) V[vmm + t] = (double)mm[t];
-            }
-            gsync<L>(gmask);
-        }
-
-        // ---------------- accumulate the record (FP64) ----------------
-        for (int t = gl, k = 0; t < args.nstat; t += L, ++k) {
-            const uint32_t w = sidx[t];
-            const double v1 = V[w & 255u] * V[(w >> 8) & 255u];
-            acc[k] += fma(V[(w >> 16) & 255u], V[w >> 24], v1);
-        }
-        gsync<L>(gmask);
-    }
+    PassEnv<T, Tab> E;
+    E.gl = gl; E.gmask = gmask;
+    E.A = A; E.Yg = Yg; E.invd = invd; E.loc = loc; E.bacc = bacc; E.bv = bv; E.G = G; E.D1 = D1;
+    E.V = V; E.idx = idx; E.Kmax = Kmax;
+    E.locs = args.locs; E.y = args.y; E.X = args.X; E.NN = args.NN;
+    E.d = d; E.p = p; E.m = m; E.status = args.status; E.bad = args.bad;
+    E.nu = (COV == COV_MATERN) ? th[2] : 0.0; E.m_psi = m_psi; E.m_lg = m_lg;
+    E.inv_r1 = inv_r1; E.inv_r2 = inv_r2;
+    E.sig2T = sig2T; E.diagC = diagC; E.inv_r1T = inv_r1T; E.inv_r2T = inv_r2T;
+    E.tab = tab; E.sidx = sidx; E.acc = acc; E.nstat = args.nstat;
+    E.vb0 = vb0; E.vstep = vstep; E.vmm = vmm;
+    for (long long i = (long long)blockIdx.x * ngrp + grp; ok && i < n; i += gstride)
+        vecchia_point<COV, L, T, Tab>(E, i);
 
     // ---------------- block reduction (fixed order) ----------------
     __syncthreads();
@@ -512,6 +575,147 @@ __global__ void __launch_bounds__(256) k_pass(PassArgs args) {
         double s = 0.0;
         for (int g = 0; g < ngrp; ++g) s += accbase[(size_t)(g * L + lr) * args.acc_per_lane + k];
         args.partials[(size_t)blockIdx.x * args.nstat + t] = s;
+    }
+}
+
+// Batched pass: CTAs take tiles from an atomic counter; for each tile they stage the
+// dataset's Matern table and theta-derived constants, run Algorithm 1 on the tile's
+// observations and reduce the tile's sums into its own record (so the result does not
+// depend on which CTA ran which tile).
+template <int COV, int L, typename T>
+__global__ void __launch_bounds__(256) k_pass_batch(BatchArgs bargs) {
+    extern __shared__ __align__(16) double smem[];
+    using MT = MaternT<T>;
+    using Tab = typename MT::Tab;
+    constexpr int NG = npair_derivs(COV);
+    constexpr int Q = NG + 1;
+    const PassArgs& args = bargs.base;
+    __shared__ int s_tile;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int gl = lane & (L - 1);
+    const int grp = tid / L;
+    const int ngrp = blockDim.x / L;
+    const unsigned gmask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << (lane & ~(L - 1)));
+    const int d = args.d, p = args.p;
+    const int Kmax = args.m + 1;
+    const int q = nparms(COV);
+
+    double* sp = smem;
+    Tab* stab = reinterpret_cast<Tab*>(sp);
+    const int tab_words = (COV == COV_MATERN && args.tab_in_smem)
+                              ? (sizeof(T) == 8 ? MT_DOUBLES : (MT_FLOATS + 1) / 2) : 0;
+    sp += tab_words;
+    uint32_t* sidx = reinterpret_cast<uint32_t*>(sp);
+    sp += (args.nstat + 1) / 2;
+    double* acc = sp + (size_t)tid * args.acc_per_lane;
+    double* accbase = sp;
+    sp += (size_t)blockDim.x * args.acc_per_lane;
+    SlotLayout SL;
+    SL.init(args.m, d, p, COV, args.nv, (int)sizeof(T));
+    char* slotc = reinterpret_cast<char*>(sp) + (size_t)grp * args.slot_stride;
+    int* idx = reinterpret_cast<int*>(reinterpret_cast<char*>(sp) + (size_t)ngrp * args.slot_stride) +
+               grp * Kmax;
+    T* slot = reinterpret_cast<T*>(slotc);
+
+    RecLayout RL;
+    RL.init(p, Q);
+    const int vb0 = 4 + p, vstep = 3 + p, vmm = vb0 + Q * vstep;
+    if (tid == 0) {
+        auto pk = [](int a, int b, int c, int e) {
+            return (uint32_t)a | ((uint32_t)b << 8) | ((uint32_t)c << 16) | ((uint32_t)e << 24);
+        };
+        int t = 0;
+        sidx[t++] = pk(2, 0, 1, 1);
+        sidx[t++] = pk(3, 3, 1, 1);
+        for (int a = 0; a < p; ++a)
+            for (int b = a; b < p; ++b) sidx[t++] = pk(4 + a, 4 + b, 1, 1);
+        for (int a = 0; a < p; ++a) sidx[t++] = pk(3, 4 + a, 1, 1);
+        for (int j = 0; j < Q; ++j) {
+            int vb = vb0 + j * vstep;
+            sidx[t++] = pk(vb, 0, 1, 1);
+            sidx[t++] = pk(3, vb + 1, vb + 1, 3);
+            for (int a = 0; a < p; ++a) sidx[t++] = pk(vb + 1, 4 + a, 3, vb + 2 + a);
+            for (int a = 0; a < p; ++a)
+                for (int b = a; b < p; ++b) sidx[t++] = pk(vb + 2 + a, 4 + b, 4 + a, vb + 2 + b);
+        }
+        int mm = vmm;
+        for (int j = 0; j < Q; ++j)
+            for (int l = j; l < Q; ++l) sidx[t++] = pk(mm++, 0, vb0 + j * vstep, vb0 + l * vstep + 2 + p);
+    }
+
+    PassEnv<T, Tab> E;
+    E.gl = gl; E.gmask = gmask;
+    E.A = slot + SL.A; E.Yg = slot + SL.Y; E.invd = slot + SL.inv; E.loc = slot + SL.loc;
+    E.bacc = slot + SL.bacc; E.bv = slot + SL.b; E.G = slot + SL.G; E.D1 = slot + SL.D1;
+    E.V = reinterpret_cast<double*>(slotc + SL.Vbyte); E.idx = idx; E.Kmax = Kmax;
+    E.d = d; E.p = p; E.sidx = sidx; E.acc = acc; E.nstat = args.nstat;
+    E.vb0 = vb0; E.vstep = vstep; E.vmm = vmm;
+
+    int cur_b = -1;
+    bool ok = false;
+    for (;;) {
+        if (tid == 0) s_tile = atomicAdd(bargs.tile_counter, 1);
+        __syncthreads();
+        const int t = s_tile;
+        if (t >= bargs.ntiles) break;
+        const int4 tile = bargs.tiles[t];
+        const int b = tile.x;
+        if (b != cur_b) {
+            cur_b = b;
+            const double* th = bargs.covparms_b + (size_t)b * q;
+            const double sig2 = th[0], tau2 = th[q - 1];
+            ok = sig2 > 0.0 && tau2 > 0.0 && th[1] > 0.0 && th[2] > 0.0 && isfinite(sig2) &&
+                 isfinite(tau2) && isfinite(th[1]) && isfinite(th[2]);
+            if (COV != COV_EXP) ok = ok && th[3] > 0.0 && isfinite(th[3]);
+            if (COV == COV_MATERN) ok = ok && th[2] >= 0.05 && th[2] <= 20.0;
+            E.inv_r1 = 1.0 / th[1];
+            E.inv_r2 = (COV == COV_ST) ? 1.0 / th[2] : 1.0;
+            E.sig2T = (T)sig2;
+            E.diagC = (T)(sig2 * (1.0 + tau2));
+            E.inv_r1T = (T)E.inv_r1;
+            E.inv_r2T = (T)E.inv_r2;
+            E.nu = (COV == COV_MATERN) ? th[2] : 0.0;
+            E.m_psi = (COV == COV_MATERN && ok) ? dev_digamma(th[2]) : 0.0;
+            E.m_lg = (COV == COV_MATERN && ok) ? lgamma(th[2]) : 0.0;
+            const long long po = bargs.pt_off[b];
+            E.locs = args.locs + po * d;
+            E.y = args.y + po;
+            E.X = args.X + po * p;
+            E.NN = args.NN + bargs.nn_off[b];
+            E.m = bargs.m_b[b];
+            E.status = bargs.status_b + b;
+            E.bad = bargs.bad_b + b;
+            if (COV == COV_MATERN) {
+                const Tab* gt = sizeof(T) == 8
+                    ? reinterpret_cast<const Tab*>(bargs.tabs + (size_t)b * MT_DOUBLES)
+                    : reinterpret_cast<const Tab*>(bargs.tabsf + (size_t)b * MT_FLOATS);
+                if (tab_words) {
+                    const double* src = reinterpret_cast<const double*>(gt);
+                    double* dst = reinterpret_cast<double*>(stab);
+                    for (int k = tid; k < tab_words; k += blockDim.x) dst[k] = src[k];
+                    E.tab = stab;
+                } else {
+                    E.tab = gt;
+                }
+            } else {
+                E.tab = nullptr;
+            }
+            if (!ok && tid == 0) report(E.status, E.bad, ST_ARG, -1);
+        }
+        for (int k = 0; k < args.acc_per_lane; ++k) acc[k] = 0.0;
+        __syncthreads();
+        const bool active = bargs.active_b == nullptr || bargs.active_b[b] != 0;
+        if (ok && active)
+            for (long long i = tile.y + grp; i < tile.z; i += ngrp) vecchia_point<COV, L, T, Tab>(E, i);
+        __syncthreads();
+        for (int u = tid; u < args.nstat; u += blockDim.x) {
+            const int lr = u % L, k = u / L;
+            double s = 0.0;
+            for (int g = 0; g < ngrp; ++g) s += accbase[(size_t)(g * L + lr) * args.acc_per_lane + k];
+            args.partials[(size_t)t * args.nstat + u] = s;
+        }
+        __syncthreads();
     }
 }
 

@@ -26,4 +26,26 @@ const void* pass_kernel_f32(int cov, int L) {
     }
 }
 
+template <int COV>
+static const void* batch_kernel_for_lanes(int L) {
+    switch (L) {
+    case 1: return reinterpret_cast<const void*>(&k_pass_batch<COV, 1, float>);
+    case 2: return reinterpret_cast<const void*>(&k_pass_batch<COV, 2, float>);
+    case 4: return reinterpret_cast<const void*>(&k_pass_batch<COV, 4, float>);
+    case 8: return reinterpret_cast<const void*>(&k_pass_batch<COV, 8, float>);
+    case 16: return reinterpret_cast<const void*>(&k_pass_batch<COV, 16, float>);
+    case 32: return reinterpret_cast<const void*>(&k_pass_batch<COV, 32, float>);
+    default: return nullptr;
+    }
+}
+
+const void* pass_batch_kernel_f32(int cov, int L) {
+    switch (cov) {
+    case COV_EXP: return batch_kernel_for_lanes<COV_EXP>(L);
+    case COV_MATERN: return batch_kernel_for_lanes<COV_MATERN>(L);
+    case COV_ST: return batch_kernel_for_lanes<COV_ST>(L);
+    default: return nullptr;
+    }
+}
+
 }  // namespace vg

@@ -1,0 +1,139 @@
+"""Batched pass: each dataset of one persistent launch equals its own single-dataset pass
+run with the same kernel mapping (1e-12 relative on the loglik, 1e-9 on the gradient:
+same per-point arithmetic, only the FP64 tile/block summation order differs), and the
+oracle (FP64) or the FP64 batched result within the mixed-precision bounds (mixed)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2407_02740_gb300 as vg  # noqa: E402
+
+# error bounds of the mixed path against FP64 (same as the single-dataset mixed tests)
+MIXED_BOUNDS = {"loglik": 1e-6, "grad": 2e-4, "info": 2e-5, "beta": 5e-6}
+
+
+def _dev(a, dt):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=torch.device("cuda:0"))
+
+
+def _batch(bw, th, prec, h):
+    out, st = vg.vecchia_batch_loglik_grad_info(
+        _dev(bw.locs, torch.float64), _dev(bw.y, torch.float64), _dev(bw.X, torch.float64),
+        _dev(bw.NN, torch.int32), bw.offsets, bw.m, _dev(th, torch.float64), bw.covfun,
+        prec=prec, handle=h)
+    torch.cuda.synchronize()
+    return out, st.cpu().numpy()
+
+
+def _rel_errors(g, o):
+    scale = max(np.linalg.norm(o["grad"]), np.sqrt(np.trace(o["info"])))
+    return {"loglik": abs(g["loglik"] - o["loglik"]) / abs(o["loglik"]),
+            "grad": np.linalg.norm(g["grad"] - o["grad"]) / scale,
+            "info": np.linalg.norm(g["info"] - o["info"]) / np.linalg.norm(o["info"]),
+            "beta": np.linalg.norm(g["betahat"] - o["betahat"]) / (np.linalg.norm(o["betahat"]) + 1)}
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("lanes,threads", [(8, 128), (32, 256)])
+def test_batch_matches_single_with_same_mapping(prec, lanes, threads):
+    bw = workloads.cfg_batch(seed=21, nbatch=9, n_range=(150, 3000), m_choices=(0, 5, 12, 30),
+                             m_sim=12)
+    h = vg.Handle(0)
+    h.set_lanes(lanes)
+    h.set_block_threads(threads)
+    try:
+        out, st = _batch(bw, bw.theta_true, prec, h)
+        assert np.all(st[:, 0] == 0)
+        for b in range(bw.nbatch):
+            w = bw.dataset(b)
+            single, sst = vg.vecchia_loglik_grad_info(
+                _dev(w.locs, torch.float64), _dev(w.y, torch.float64), _dev(w.X, torch.float64),
+                _dev(w.NN, torch.int32), _dev(w.theta_true, torch.float64), w.covfun, prec=prec,
+                handle=h)
+            g = vg.unpack(out[b], 4, 1)
+            s1 = vg.unpack(single, 4, 1)
+            assert abs(g["loglik"] - s1["loglik"]) <= 1e-12 * abs(s1["loglik"])
+            assert np.allclose(g["grad"], s1["grad"], rtol=1e-9, atol=1e-9 * np.abs(s1["grad"]).max())
+            assert np.allclose(g["info"], s1["info"], rtol=1e-9, atol=1e-9 * np.abs(s1["info"]).max())
+    finally:
+        h.close()
+
+
+def test_batch_fp64_matches_oracle():
+    bw = workloads.cfg_batch(seed=21, nbatch=9, n_range=(150, 3000), m_choices=(0, 5, 12, 30),
+                             m_sim=12)
+    h = vg.Handle(0)
+    try:
+        out, st = _batch(bw, bw.theta_true, "fp64", h)
+        assert np.all(st[:, 0] == 0)
+        for b in range(bw.nbatch):
+            w = bw.dataset(b)
+            g = vg.unpack(out[b], 4, 1)
+            o = oracle.loglik_grad_info(w.locs, w.y, w.X, w.NN, w.theta_true, w.covfun)
+            assert abs(g["loglik"] - o["loglik"]) <= 1e-10 * abs(o["loglik"])
+            scale = max(np.linalg.norm(o["grad"]), np.sqrt(np.trace(o["info"])))
+            assert np.linalg.norm(g["grad"] - o["grad"]) <= 1e-10 * scale
+            assert np.linalg.norm(g["info"] - o["info"]) <= 1e-10 * np.linalg.norm(o["info"])
+            assert np.allclose(g["betahat"], o["betahat"], rtol=1e-9, atol=1e-10)
+    finally:
+        h.close()
+
+
+def test_batch_mixed_within_bounds_of_fp64():
+    bw = workloads.cfg_batch(seed=23, nbatch=12, n_range=(500, 4000), m_choices=(10, 20, 30),
+                             m_sim=30)
+    h = vg.Handle(0)
+    try:
+        o64, s64 = _batch(bw, bw.theta_true, "fp64", h)
+        omx, smx = _batch(bw, bw.theta_true, "mixed", h)
+        assert np.all(s64[:, 0] == 0) and np.all(smx[:, 0] == 0)
+        for b in range(bw.nbatch):
+            err = _rel_errors(vg.unpack(omx[b], 4, 1), vg.unpack(o64[b], 4, 1))
+            for k, bound in MIXED_BOUNDS.items():
+                assert err[k] <= bound, (b, k, err)
+    finally:
+        h.close()
+
+
+def test_batch_reports_errors_per_dataset():
+    bw = workloads.cfg_batch(seed=22, nbatch=4, n_range=(200, 400), m_choices=(8,), m_sim=8)
+    th = bw.theta_true.copy()
+    th[2, 2] = 30.0  # smoothness out of range for dataset 2 only
+    h = vg.Handle(0)
+    try:
+        out, st = _batch(bw, th, "fp64", h)
+        assert list(st[:, 0]) == [0, 0, 1, 0]
+        o = out.cpu().numpy()
+        assert np.isnan(o[2, 0]) and np.all(np.isfinite(o[[0, 1, 3], 0]))
+    finally:
+        h.close()
+
+
+def test_batch_single_dataset_equals_single_pass():
+    # nbatch = 1 is the plain pass over one dataset
+    w = workloads.cfg_small_exp()
+    h = vg.Handle(0)
+    h.set_lanes(8)
+    h.set_block_threads(128)
+    try:
+        locs, y, X = _dev(w.locs, torch.float64), _dev(w.y, torch.float64), _dev(w.X, torch.float64)
+        NN = _dev(w.NN, torch.int32)
+        th = _dev(w.theta_true, torch.float64)
+        m = w.NN.shape[1] - 1
+        out, st = vg.vecchia_batch_loglik_grad_info(locs, y, X, NN.reshape(-1), [0, w.n], [m],
+                                                    th.reshape(1, -1), w.covfun, handle=h)
+        single, sst = vg.vecchia_loglik_grad_info(locs, y, X, NN, th, w.covfun, handle=h)
+        torch.cuda.synchronize()
+        q = len(w.theta_true)
+        g = vg.unpack(out[0], q, X.shape[1])
+        s1 = vg.unpack(single, q, X.shape[1])
+        assert int(st[0, 0]) == 0 and int(sst[0]) == 0
+        assert abs(g["loglik"] - s1["loglik"]) <= 1e-12 * abs(s1["loglik"])
+        assert np.allclose(g["grad"], s1["grad"], rtol=1e-9, atol=1e-9 * np.abs(s1["grad"]).max())
+    finally:
+        h.close()

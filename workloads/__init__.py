@@ -46,8 +46,8 @@ def build(force: bool = False) -> str:
     """Compile the preprocessing library in-tree (gcc, plain C, no FMA contraction)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".%d.tmp" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-ffp-contract=off",
-                               "-std=c11", _SRC, "-o", tmp, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+                               "-std=gnu11", _SRC, "-o", tmp, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -67,6 +67,8 @@ def _load():
         lib.prep_ordered_nn.argtypes = [P, i64, ci, ci, P]
         lib.prep_ordered_nn_brute.argtypes = [P, i64, ci, ci, P]
         lib.prep_seq_recurrence.argtypes = [i64, ci, P, P, P, P, P]
+        lib.prep_seq_weights.argtypes = [i64, ci, ci, P, P, ci, P, P, P]
+        lib.prep_seq_weights.restype = ci
         for f in (lib.prep_maxmin, lib.prep_maxmin_brute, lib.prep_ordered_nn,
                   lib.prep_ordered_nn_brute, lib.prep_seq_recurrence):
             f.restype = ci
@@ -154,8 +156,28 @@ def simulate_sequential(covfun, theta, locs, NN, rng, chunk: int = 2048) -> np.n
     m = W - 1
     Wt = np.zeros((n, max(m, 1)), dtype=np.float64)
     sd = np.zeros(n, dtype=np.float64)
+    # closed-form kernels: the C helper (OpenMP); other smoothness values: numpy + scipy
+    kind = None
+    th = np.asarray(theta, dtype=np.float64)
+    if covfun == EXP_ISO:
+        kind, thc = 0, th[[0, 1, 2]]
+    elif covfun == EXP_SPACETIME:
+        kind, thc = 3, th
+    elif covfun == MATERN_ISO and float(th[2]) in (0.5, 1.5, 2.5):
+        kind = {0.5: 0, 1.5: 1, 2.5: 2}[float(th[2])]
+        thc = th[[0, 1, 3]]
+    if kind is not None:
+        NNc = np.ascontiguousarray(NN, dtype=np.int32)
+        Wc = np.zeros((n, max(m, 1)))
+        locs_c = np.ascontiguousarray(locs, dtype=np.float64)
+        thc = np.ascontiguousarray(thc, dtype=np.float64)
+        rc = _load().prep_seq_weights(n, locs_c.shape[1], m, _ptr(NNc), _ptr(locs_c), kind,
+                                      _ptr(thc), _ptr(Wc), _ptr(sd))
+        if rc != 0:
+            raise RuntimeError("sequential weights failed (block not positive definite)")
+        Wt = Wc
     kcount = (NN[:, 1:] >= 0).sum(axis=1) if m > 0 else np.zeros(n, dtype=np.int64)
-    for k in np.unique(kcount):
+    for k in (np.unique(kcount) if kind is None else []):
         idx = np.nonzero(kcount == k)[0]
         for s in range(0, len(idx), chunk):
             ii = idx[s:s + chunk]
@@ -318,3 +340,63 @@ def cfg_swath_1m2(seed: int = 1003, slices: int = 16, bands: int = 8, per: int =
     start = np.array([np.var(y), 10.0, 4.0, 0.1])
     return _finish("swath_n%d_m%d" % (locs.shape[0], m), EXP_SPACETIME, locs, y, X, m, theta,
                    start, NN=NN, seed=seed, m_sim=m_sim)
+
+
+@dataclass
+class BatchWorkload:
+    """Many independent fields, concatenated: dataset b owns rows off[b]:off[b+1] of locs,
+    y, X and a block of NN (its own n_b x (m_b+1) array, indices local to the dataset)."""
+    covfun: int
+    locs: np.ndarray
+    y: np.ndarray
+    X: np.ndarray
+    NN: np.ndarray          # flat int32, concatenated per-dataset arrays
+    offsets: np.ndarray     # nbatch + 1, int64
+    m: np.ndarray           # nbatch, int32
+    theta_true: np.ndarray  # nbatch x q
+    theta_start: np.ndarray  # nbatch x q
+
+    @property
+    def nbatch(self):
+        return len(self.m)
+
+    def dataset(self, b) -> Workload:
+        s, e = self.offsets[b], self.offsets[b + 1]
+        nn_s = int(sum((self.offsets[k + 1] - self.offsets[k]) * (self.m[k] + 1) for k in range(b)))
+        nb, mb = e - s, int(self.m[b])
+        NN = self.NN[nn_s: nn_s + nb * (mb + 1)].reshape(nb, mb + 1)
+        return Workload("batch%d" % b, self.covfun, self.locs[s:e], self.y[s:e], self.X[s:e], NN,
+                        self.theta_true[b], self.theta_start[b], mb)
+
+
+def cfg_batch(seed: int = 1004, nbatch: int = 256, n_range=(1000, 50000), m_choices=(10, 20, 40),
+              nu_choices=(0.5, 1.5, 2.5), m_sim: int = 40) -> BatchWorkload:
+    """nbatch Matern fields in [0,1]^2: n log-uniform in n_range, m from m_choices,
+    sigma2 log-uniform [0.5, 2], rho log-uniform [0.02, 0.3], nu from nu_choices, tau2
+    log-uniform [0.001, 0.2], X = 1, beta = 0, sequential draw with m_sim neighbours."""
+    rng = np.random.default_rng(seed)
+    lo, hi = np.log(n_range[0]), np.log(n_range[1])
+    locs, ys, Xs, NNs, ms, th, st = [], [], [], [], [], [], []
+    off = [0]
+    for b in range(nbatch):
+        n = int(round(np.exp(rng.uniform(lo, hi))))
+        m = int(rng.choice(m_choices))
+        theta = np.array([np.exp(rng.uniform(np.log(0.5), np.log(2.0))),
+                          np.exp(rng.uniform(np.log(0.02), np.log(0.3))),
+                          float(rng.choice(nu_choices)),
+                          np.exp(rng.uniform(np.log(0.001), np.log(0.2)))])
+        L = rng.uniform(0.0, 1.0, size=(n, 2))
+        L = L[maxmin_order(L)]
+        NNsim = ordered_nn(L, max(m, m_sim))
+        e = simulate_sequential(MATERN_ISO, theta, L, NNsim[:, : m_sim + 1], rng)
+        locs.append(L)
+        ys.append(e)
+        Xs.append(np.ones((n, 1)))
+        NNs.append(np.ascontiguousarray(NNsim[:, : m + 1]).ravel())
+        ms.append(m)
+        th.append(theta)
+        st.append(np.array([np.var(e), 0.1, 1.0, 0.1]))
+        off.append(off[-1] + n)
+    return BatchWorkload(MATERN_ISO, np.concatenate(locs), np.concatenate(ys), np.concatenate(Xs),
+                         np.concatenate(NNs).astype(np.int32), np.array(off, dtype=np.int64),
+                         np.array(ms, dtype=np.int32), np.array(th), np.array(st))

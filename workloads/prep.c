@@ -1,9 +1,11 @@
 /*
- * prep.c -- input preprocessing for Vecchia workloads: maxmin ordering, ordered
- * nearest neighbours (NNarray) and the sequential-simulation recurrence.
+ * prep.c -- input preprocessing and field generation for Vecchia workloads: maxmin
+ * ordering, ordered nearest neighbours (NNarray), and the pieces of the sequential draw
+ * of synthetic fields (regression weights from closed-form covariances, recurrence).
  *
  * This is input generation, shared by both sides that consume the inputs (the CPU
- * oracle and the CUDA library).  It evaluates no covariance, likelihood or derivative.
+ * oracle and the CUDA library), and used by neither to compute anything: it evaluates
+ * no likelihood or derivative, and its covariance code exists only to draw y.
  *
  *   Ordering (Sec. 2.1; maxmin heuristic of Guinness 2018): the first point is the one
  *   nearest to the centroid; each next point is the one whose minimum distance to the
@@ -403,4 +405,86 @@ int prep_seq_recurrence(int64_t n, int m, const int32_t* NN, const double* W, co
         e[i] = s + sd[i] * z[i];
     }
     return PREP_OK;
+}
+
+/* ------------------------------ sequential-draw weights ------------------------------ */
+/* Generator-side Gaussian-process regression weights for drawing fields from a sequential
+ * model: for each i with listed earlier neighbours N(i), W[i] = S_NN^-1 S_Ni and
+ * sd[i] = sqrt(S_ii - S_iN W[i]) for the covariance S = sigma2 (R + tau2 I).
+ * kind: 0 exponential exp(-r/rho); 1 Matern nu = 3/2 (1 + x) e^-x; 2 Matern nu = 5/2
+ * (1 + x + x^2/3) e^-x (x = r/rho); 3 space-time exponential (d = 3, theta =
+ * (sigma2, rho_s, rho_t, tau2)).  theta for kinds 0-2: (sigma2, rho, tau2).
+ * W is n x m (unused entries 0).  Returns PREP_ERR_ARG if a block is not positive definite. */
+static double gen_corr(int kind, const double* a, const double* b, int d, const double* th)
+{
+    if (kind == 3) {
+        double s = ((a[0] - b[0]) * (a[0] - b[0]) + (a[1] - b[1]) * (a[1] - b[1])) / (th[1] * th[1]);
+        s += (a[2] - b[2]) * (a[2] - b[2]) / (th[2] * th[2]);
+        return exp(-sqrt(s));
+    }
+    double x = sqrt(sqdist(a, b, d)) / th[1];
+    if (kind == 1) return (1.0 + x) * exp(-x);
+    if (kind == 2) return (1.0 + x + x * x / 3.0) * exp(-x);
+    return exp(-x);
+}
+
+int prep_seq_weights(int64_t n, int d, int m, const int32_t* NN, const double* x, int kind,
+                     const double* theta, double* W, double* sd)
+{
+    if (n < 1 || d < 1 || m < 0 || kind < 0 || kind > 3) return PREP_ERR_ARG;
+    const double sig2 = theta[0];
+    const double tau2 = theta[kind == 3 ? 3 : 2];
+    int err = PREP_OK;
+#pragma omp parallel
+    {
+        const int K = m + 1;
+        double* S = (double*)malloc(sizeof(double) * (size_t)K * K);
+        double* z = (double*)malloc(sizeof(double) * (size_t)K);
+        int32_t* ix = (int32_t*)malloc(sizeof(int32_t) * (size_t)K);
+#pragma omp for schedule(dynamic, 1024)
+        for (int64_t i = 0; i < n; i++) {
+            const int32_t* row = NN + i * (int64_t)K;
+            int k = 0;
+            while (k < m && row[1 + k] >= 0) { ix[k] = row[1 + k]; k++; }
+            ix[k] = (int32_t)i;
+            const int Kp = k + 1;
+            for (int a = 0; a < Kp; a++)
+                for (int b = 0; b <= a; b++) {
+                    double c = sig2 * gen_corr(kind, x + (int64_t)ix[a] * d, x + (int64_t)ix[b] * d, d, theta);
+                    if (a == b) c += sig2 * tau2;
+                    S[a * Kp + b] = c;
+                }
+            /* Cholesky of the (k+1) block; its last row gives L_N^-1 S_Ni and the sd */
+            int bad = 0;
+            for (int c = 0; c < Kp && !bad; c++) {
+                double v = S[c * Kp + c];
+                for (int s = 0; s < c; s++) v -= S[c * Kp + s] * S[c * Kp + s];
+                if (!(v > 0.0)) { bad = 1; break; }
+                double l = sqrt(v);
+                S[c * Kp + c] = l;
+                for (int r = c + 1; r < Kp; r++) {
+                    double u = S[r * Kp + c];
+                    for (int s = 0; s < c; s++) u -= S[r * Kp + s] * S[c * Kp + s];
+                    S[r * Kp + c] = u / l;
+                }
+            }
+            if (bad) {
+#pragma omp critical
+                err = PREP_ERR_ARG;
+                continue;
+            }
+            /* W = L_N^-T (last row of L restricted to the neighbours) */
+            for (int a = k - 1; a >= 0; a--) {
+                double u = S[k * Kp + a];
+                for (int r = a + 1; r < k; r++) u -= S[r * Kp + a] * z[r];
+                z[a] = u / S[a * Kp + a];
+            }
+            for (int a = 0; a < m; a++) W[i * (int64_t)m + a] = (a < k) ? z[a] : 0.0;
+            sd[i] = S[k * Kp + k];
+        }
+        free(S);
+        free(z);
+        free(ix);
+    }
+    return err;
 }
