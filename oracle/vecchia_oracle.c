@@ -641,7 +641,8 @@ int orc_loglik_grad_info(const double* locs, const double* y, const double* X,
  *   Delta = I~^-1 g~; stop (converged) when g~^T Delta < tol, before taking the step;
  *   trial theta' = theta (.) exp(Delta / 2^h), h = 0..10, accepted at the first h whose
  *   loglik is finite and larger than the current one; a trial that fails (not PD,
- *   non-finite) counts as -inf; nu is clamped to [0.05, 20];
+ *   non-finite, or outside the parameter domain because a parameter underflowed to 0 or
+ *   overflowed) counts as -inf; nu is clamped to [0.05, 20];
  *   at most maxit accepted steps.
  * Outputs the final theta, betahat, loglik, grad, info; *iters = accepted steps;
  * *status = 0 converged, 1 iteration limit, 2 no ascent step found, else an error code. */
@@ -693,9 +694,8 @@ int orc_fisher_fit(const double* locs, const double* y, const double* X, const i
                 for (int t = 0; t < q * q; t++) I[t] = In[t];
                 for (int a = 0; a < p; a++) bh[a] = bhn[a];
                 ll = lln;
-            } else if (s2 != ORC_OK && s2 != ORC_ERR_NOT_PD && s2 != ORC_ERR_NONFINITE) {
-                return s2;
             }
+            /* any other outcome is a failed trial: the step is halved */
         }
         if (!accepted) { *status = 2; break; }
         it++;

@@ -41,3 +41,17 @@ def test_fisher_scoring_reaches_the_optimum(covfun, theta, start):
                       options={"gtol": 1e-9, "maxiter": 500})
     assert abs(-res.fun - fit["loglik"]) <= 1e-9 * abs(fit["loglik"])
     assert fit["loglik"] >= -res.fun - 1e-9 * abs(fit["loglik"])
+
+
+def test_fit_trial_outside_domain_is_a_failed_trial():
+    # a field whose likelihood rises towards the boundary (smoothness at its lower clamp,
+    # nugget -> 0): late trials underflow the nugget to exactly 0, which must count as a
+    # failed trial (step halved), so the fit ends with "no ascent" instead of an error
+    bw = workloads.cfg_batch(seed=31, nbatch=6, n_range=(300, 1500), m_choices=(5, 10, 20),
+                             m_sim=20)
+    w = bw.dataset(5)
+    fit = oracle.fisher_fit(w.locs, w.y, w.X, w.NN, w.covfun, w.theta_start)
+    assert fit["status"] == 2
+    assert fit["theta"][2] == 0.05 and fit["theta"][3] < 0.01
+    start = oracle.loglik_grad_info(w.locs, w.y, w.X, w.NN, w.theta_start, w.covfun)
+    assert fit["loglik"] > start["loglik"]
