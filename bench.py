@@ -15,6 +15,9 @@ Reported beside the device-timed value:
   * roofline   -- the per-observation kernel against the FP64 ALU peak (its algorithmic
                   FMA count per observation x observations / its CUDA-event duration);
   * cpu_baseline -- the FP64 CPU oracle on the host cores, on a bounded prefix sample.
+  * batched    -- 256 independent fields (n from 1000 to 50000, m in {10, 20, 40}): the
+                  batched pass as one CUDA-graph replay vs 256 per-dataset calls, and
+                  batched Fisher-scoring fits vs 256 sequential device fits.
 ``--impl reference`` times the CPU oracle itself as the reference arm.
 Multi-GPU runs (torchrun) are independent replicas: each rank evaluates its own copy.
 """
@@ -151,6 +154,165 @@ def cpu_oracle_rate(w, target_s: float = 12.0, nthreads: int = 0):
     dt = time.perf_counter() - t0
     cores = nthreads if nthreads > 0 else (os.cpu_count() or 1)
     return ns / dt, ns, dt, cores
+
+
+def run_batched(vg, torch, dev, stream, steps: int, warmup: int, flush, local: int) -> dict:
+    """The 256-dataset batch (Matern fields, n log-uniform in [1000, 50000], m in
+    {10, 20, 40}, per-dataset parameters, X = 1): the batched pass as one CUDA-graph
+    replay of a batch plan (mapping from the batched autotuner) against 256 per-dataset
+    pass calls, the mixed-precision batched pass, and batched Fisher-scoring fits against
+    256 sequential single-dataset device fits.  L2 is flushed before every timed step."""
+    import workloads
+    t_gen = time.perf_counter()
+    bw = workloads.cfg_batch()
+    t_gen = time.perf_counter() - t_gen
+    t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)  # noqa
+    locs, y, X, NN = (t(bw.locs, torch.float64), t(bw.y, torch.float64), t(bw.X, torch.float64),
+                      t(bw.NN, torch.int32))
+    th, th0 = t(bw.theta_true, torch.float64), t(bw.theta_start, torch.float64)
+    nb, q, p = bw.nbatch, 4, 1
+    ntot = int(bw.offsets[-1])
+    nout = 1 + q + q * q + p
+    hb = vg.Handle(local)
+    tune = vg.vecchia_batch_autotune(locs, y, X, NN, bw.offsets, bw.m, th, bw.covfun, reps=2,
+                                     stream=stream, handle=hb)
+
+    def graph_of(plan, cp, out, st):
+        side = torch.cuda.Stream(dev)
+        side.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(side):
+            plan.run(locs, y, X, NN, cp, out, st)
+        torch.cuda.current_stream(dev).wait_stream(side)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            plan.run(locs, y, X, NN, cp, out, st)
+        return g
+
+    def time_steps(fn, k):
+        ms = []
+        for _ in range(k):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return ms
+
+    res = {}
+    for prec in ("fp64", "mixed"):
+        plan = vg.BatchPlan(bw.offsets, bw.m, 2, p, bw.covfun, prec=prec, handle=hb, device=local)
+        out = torch.empty(nb, nout, dtype=torch.float64, device=dev)
+        st = torch.empty(nb, 2, dtype=torch.int64, device=dev)
+        g = graph_of(plan, th, out, st)
+        for _ in range(warmup):
+            g.replay()
+        torch.cuda.synchronize()
+        ms = time_steps(g.replay, steps)
+        res[prec] = {"out": out.clone(), "status": st.cpu().numpy(), "ms": ms,
+                     "mapping": plan.mapping()}
+        plan.close()
+    if np.any(res["fp64"]["status"][:, 0] != 0):
+        raise RuntimeError("batched pass failed: %s" % res["fp64"]["status"][:, 0])
+
+    # the same work as 256 separate pass calls (planned mapping per dataset), one stream
+    hs = vg.Handle(local)
+    nn_off = np.concatenate([[0], np.cumsum(np.diff(bw.offsets) * (bw.m.astype(np.int64) + 1))])
+    views = []
+    for b in range(nb):
+        s0, e0 = int(bw.offsets[b]), int(bw.offsets[b + 1])
+        views.append((locs[s0:e0], y[s0:e0], X[s0:e0],
+                      NN[int(nn_off[b]):int(nn_off[b + 1])].view(e0 - s0, int(bw.m[b]) + 1)))
+    outs = torch.empty(nb, nout, dtype=torch.float64, device=dev)
+    sts = torch.empty(nb, 2, dtype=torch.int64, device=dev)
+
+    def per_dataset():
+        for b, (a0, a1, a2, a3) in enumerate(views):
+            vg.vecchia_loglik_grad_info(a0, a1, a2, a3, th[b], bw.covfun, stream=stream,
+                                        out=outs[b], status=sts[b], handle=hs)
+    per_dataset()
+    torch.cuda.synchronize()
+    ms_sep = time_steps(per_dataset, max(3, steps // 5))
+    o64 = res["fp64"]["out"].cpu().numpy()
+    osep = outs.cpu().numpy()
+    omx = res["mixed"]["out"].cpu().numpy()
+    nb_n = np.diff(bw.offsets).astype(np.float64)
+    ll_rel_sep = float(np.max(np.abs(o64[:, 0] - osep[:, 0]) / np.maximum(np.abs(osep[:, 0]), nb_n)))
+    ll_rel_mixed = float(np.max(np.abs(omx[:, 0] - o64[:, 0]) / np.maximum(np.abs(o64[:, 0]), nb_n)))
+
+    # fits: one batched fit (graph) vs the 256 datasets fitted one after another
+    bfit_s, bfit = [], None
+    for _ in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        bfit = vg.vecchia_batch_fit(locs, y, X, NN, bw.offsets, bw.m, bw.covfun, th0, tol=1e-4,
+                                    stream=stream, handle=hb)
+        bfit_s.append(time.perf_counter() - t0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    mfit = vg.vecchia_batch_fit(locs, y, X, NN, bw.offsets, bw.m, bw.covfun, th0, tol=1e-4,
+                                prec="mixed", stream=stream, handle=hb)
+    mfit_s = time.perf_counter() - t0
+    seq_ll = np.empty(nb)
+    seq_iters = np.empty(nb, dtype=np.int64)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for b, (a0, a1, a2, a3) in enumerate(views):
+        f = vg.vecchia_fit(a0, a1, a2, a3, bw.covfun, bw.theta_start[b], tol=1e-4, stream=stream,
+                           handle=hs)
+        seq_ll[b] = f["loglik"]
+        seq_iters[b] = f["iters"]
+    seq_s = time.perf_counter() - t0
+    bll = bfit["out"][:, 0].cpu().numpy()
+    mll = mfit["out"][:, 0].cpu().numpy()
+    conv = (bfit["status"] == 0)
+    both = conv & (mfit["status"] == 0)
+    norm = np.maximum(np.abs(bll), np.diff(bw.offsets).astype(np.float64))
+    hs.close()
+    hb.close()
+
+    flop = float(sum(2 * algorithmic_fma_per_point(int(mb) + 1, p, q) * (bw.offsets[b + 1] - bw.offsets[b])
+                     for b, mb in enumerate(bw.m)))
+    b_ms = statistics.median(res["fp64"]["ms"])
+    return {
+        "workload": "256 Matern fields in [0,1]^2, n log-uniform in [1000, 50000] (total %d), "
+                    "m in {10, 20, 40}, per-dataset (sigma2, rho, nu, tau2) drawn from the "
+                    "stated priors, X = 1, sequential Vecchia draws with m = 40" % ntot,
+        "datasets": nb, "points": ntot, "generation_s": t_gen,
+        "value": ntot / (b_ms * 1e-3), "unit": UNIT, "dtype": "f64",
+        "ms_per_step": b_ms, "launch": "one CUDA-graph replay of a batch plan (4 kernels)",
+        "gpu_launches_per_step": 4,
+        "mapping": {"lanes_per_observation": tune["lanes"], "threads_per_block": tune["threads"],
+                    "source": "vecchia_batch_autotune"},
+        "roofline": {"bound": "alu", "unit": "GFLOP/s", "peak": FP64_PEAK_GFLOPS,
+                     "achieved": flop / (b_ms * 1e-3) / 1e9,
+                     "frac": flop / (b_ms * 1e-3) / 1e9 / FP64_PEAK_GFLOPS,
+                     "note": "whole replay (tables, pass, profiles) timed"},
+        "per_dataset_launches": {"value": ntot / (statistics.median(ms_sep) * 1e-3), "unit": UNIT,
+                                 "ms_per_step": statistics.median(ms_sep),
+                                 "gpu_launches_per_step": nb * 4,
+                                 "max_loglik_rel_diff_vs_batched": ll_rel_sep},
+        "speedup_vs_per_dataset": statistics.median(ms_sep) / b_ms,
+        "mixed": {"value": ntot / (statistics.median(res["mixed"]["ms"]) * 1e-3), "unit": UNIT,
+                  "ms_per_step": statistics.median(res["mixed"]["ms"]),
+                  "mapping": res["mixed"]["mapping"],
+                  "max_loglik_rel_diff_vs_fp64": ll_rel_mixed},
+        "fit": {"tol": 1e-4, "start": "(var y, 0.1, 1.0, 0.1) per dataset",
+                "batched_f64_s": bfit_s[1], "batched_f64_first_call_s": bfit_s[0],
+                "batched_mixed_s": mfit_s, "sequential_f64_s": seq_s,
+                "speedup_batched_vs_sequential": seq_s / bfit_s[1],
+                "converged": int(conv.sum()),
+                "status_counts": {str(k): int((bfit["status"] == k).sum()) for k in range(4)},
+                "max_iters": int(bfit["iters"].max()), "max_passes": int(bfit["evals"].max()),
+                "max_loglik_rel_diff_vs_sequential": float(np.max(np.abs(bll - seq_ll) / np.abs(seq_ll))),
+                "max_loglik_diff_mixed_vs_f64": float(np.max(np.abs(mll - bll)[both] / norm[both]))
+                if np.any(both) else None,
+                "loglik_diff_note": "over datasets where both fits converged, |difference| / "
+                                    "max(|loglik|, n) (a field's loglik can be near 0)",
+                "sequential_iters_equal": bool(np.array_equal(seq_iters, bfit["iters"]))},
+    }
 
 
 def run_reference(args):
@@ -316,6 +478,8 @@ def run_ours(args):
                               stream=stream, handle=hm)
         mfit_times.append(time.perf_counter() - t0)
 
+    batched = run_batched(vg, torch, dev, stream, args.steps, args.warmup, flush, local)
+
     if rank != 0:
         if ws > 1:
             torch.distributed.barrier()
@@ -376,6 +540,7 @@ def run_ours(args):
                           "status": mfit["status"], "loglik": mfit["loglik"],
                           "loglik_rel_to_f64_fit": abs(mfit["loglik"] - fit["loglik"]) / abs(fit["loglik"]),
                           "theta": [float(v) for v in mfit["theta"]]}},
+        "batched": batched,
     }
     print(json.dumps(line))
     if ws > 1:

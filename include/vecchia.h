@@ -115,7 +115,8 @@ VECCHIA_API vec_status vecchia_autotune(vec_handle h, const double* locs, const 
                                         float* ms_out);
 
 /* Writes / reads the handle's autotuning records as JSON (an array of objects with keys
- * covfun, m, d, p, prec, log2n, lanes, threads, ms).  Loading adds to the records. */
+ * covfun, m, d, p, prec, log2n, lanes, threads, ms; prec is the vec_precision, plus 2 for
+ * records of the batched pass).  Loading adds to the records. */
 VECCHIA_API vec_status vecchia_autotune_save(vec_handle h, const char* path);
 VECCHIA_API vec_status vecchia_autotune_load(vec_handle h, const char* path);
 
@@ -243,6 +244,80 @@ VECCHIA_API vec_status vecchia_fit(vec_handle h, const double* locs, const doubl
                                    const vec_fit_opts* opts, void* stream, double* theta_out,
                                    double* betahat, double* loglik, double* grad, double* info,
                                    vec_fit_info* fit_info);
+
+/*
+ * Batch plans: the batched pass split into a host-side preparation and a device-only run.
+ *
+ * vecchia_batch_plan_create does everything of vecchia_batch_loglik_grad_info that needs
+ * the host: it checks the batch description (point_offsets and m, HOST, as there), picks
+ * the kernel mapping (forced on the handle, else the handle's batched autotuning record,
+ * else planned), builds the work list, allocates the plan's own device buffers and
+ * uploads the work list (waiting for the copy).  The plan is bound to the handle's
+ * device, independent of the handle afterwards, and must be released with
+ * vecchia_batch_plan_destroy.
+ *
+ * vecchia_batch_plan_run enqueues one batched pass for the planned batch on `stream`:
+ * the same arguments, layouts, results and per-dataset status as
+ * vecchia_batch_loglik_grad_info, but it only launches kernels (no allocation, no copy,
+ * no synchronisation), so it can be captured into a CUDA graph and replayed.  Runs of one
+ * plan share its buffers: two runs of the same plan must not overlap on the GPU.
+ *
+ * vecchia_batch_plan_mapping reports the plan's lanes per observation, threads per block
+ * and number of tiles (HOST pointers, each may be NULL).
+ */
+typedef struct vec_batch_plan_s* vec_batch_plan;
+VECCHIA_API vec_status vecchia_batch_plan_create(vec_handle h, int nbatch,
+                                                 const int64_t* point_offsets, const int* m,
+                                                 int d, int p, vec_covfun covfun,
+                                                 vec_precision prec, vec_batch_plan* plan_out);
+VECCHIA_API vec_status vecchia_batch_plan_run(vec_batch_plan plan, const double* locs,
+                                              const double* y, const double* X,
+                                              const int32_t* NNarray, const double* covparms,
+                                              void* stream, double* out, int64_t* dev_status);
+VECCHIA_API vec_status vecchia_batch_plan_mapping(vec_batch_plan plan, int* lanes, int* threads,
+                                                  int* ntiles);
+VECCHIA_API vec_status vecchia_batch_plan_destroy(vec_batch_plan plan);
+
+/*
+ * vecchia_batch_fit -- Fisher scoring (Eq. 4) for many independent datasets at once.
+ *
+ * Data as in vecchia_batch_loglik_grad_info (concatenated DEVICE arrays, HOST
+ * point_offsets and m).  start: DEVICE, nbatch x q starting parameters (a dataset whose
+ * start is not a valid parameter vector ends with status 3, start failed).  opts as in
+ * vecchia_fit; every dataset follows the rules of vecchia_fit on its own, with its own
+ * step, halvings and stopping test.  Each iteration is one batched pass (one persistent
+ * launch) over the datasets that are still iterating, then one step kernel for all of
+ * them; with use_graph = 1 the iterations run inside one CUDA graph whose WHILE node
+ * repeats while any dataset iterates.  VEC_MIXED runs a mixed-precision phase for all
+ * datasets, then an FP64 phase from each dataset's phase-1 result.
+ * Outputs: theta_out, DEVICE, nbatch x q; out, DEVICE, nbatch x (1+q+q*q+p) = [loglik,
+ * grad, info, betahat] at theta_out (FP64 pass values); fit_info, HOST, nbatch entries
+ * (may be NULL).  Runs on `stream` and returns after all fits have finished.
+ */
+VECCHIA_API vec_status vecchia_batch_fit(vec_handle h, int nbatch, const double* locs,
+                                         const double* y, const double* X,
+                                         const int32_t* NNarray, const int64_t* point_offsets,
+                                         const int* m, int d, int p, vec_covfun covfun,
+                                         const double* start, const vec_fit_opts* opts,
+                                         void* stream, double* theta_out, double* out,
+                                         vec_fit_info* fit_info);
+
+/*
+ * vecchia_batch_autotune -- vecchia_autotune for the batched pass.
+ *
+ * Times the batched pass (vecchia_batch_loglik_grad_info, same arguments) under every
+ * (lanes per observation, threads per block) mapping that fits the largest m of the batch
+ * and records the fastest in the handle, keyed by (covfun, largest m, d, p, prec,
+ * floor(log2(total n))) apart from the single-dataset records; later batched calls with
+ * a matching key use it unless a mapping is forced.  Synchronises `stream`.
+ */
+VECCHIA_API vec_status vecchia_batch_autotune(vec_handle h, int nbatch, const double* locs,
+                                              const double* y, const double* X,
+                                              const int32_t* NNarray,
+                                              const int64_t* point_offsets, const int* m, int d,
+                                              int p, const double* covparms, vec_covfun covfun,
+                                              vec_precision prec, void* stream, int reps,
+                                              int* lanes_out, int* threads_out, float* ms_out);
 
 /*
  * vecchia_covariance_pairs -- the library's device covariance functions on explicit pairs.

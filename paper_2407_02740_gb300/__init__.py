@@ -10,6 +10,10 @@ Entry points (same names as the C ABI):
   * ``vecchia_loglik_grad_info``       -- device-resident pass, asynchronous on a stream
   * ``vecchia_loglik_grad_info_host``  -- end-to-end pass from host (numpy) arrays
   * ``vecchia_covariance_pairs``       -- the device covariance functions on explicit pairs
+  * ``vecchia_fit``                    -- Fisher scoring on the device (CUDA graph)
+  * ``vecchia_batch_loglik_grad_info`` -- the pass for many datasets in one launch
+  * ``vecchia_batch_fit``              -- Fisher scoring for many datasets at once
+  * ``vecchia_autotune`` / ``vecchia_batch_autotune`` -- kernel-mapping autotuner
 Covariance functions (parameter order): EXP_ISO (sigma2, rho, tau2), MATERN_ISO (sigma2,
 rho, nu, tau2), EXP_SPACETIME (sigma2, rho_s, rho_t, tau2); nugget = sigma2 * tau2.
 """
@@ -100,13 +104,24 @@ def lib():
                                   P, P, P, P, P, P, ctypes.POINTER(FitInfo)]
         L.vecchia_loglik_grad_info_noalloc.argtypes = [P, P, P, P, i64, ci, ci, ci, P, ci, ci,
                                                        P, P, P]
+        L.vecchia_batch_fit.argtypes = [P, ci, P, P, P, P, P, P, ci, ci, ci, P,
+                                        ctypes.POINTER(FitOpts), P, P, P, P]
+        L.vecchia_batch_autotune.argtypes = [P, ci, P, P, P, P, P, P, ci, ci, P, ci, ci, P, ci,
+                                             P, P, P]
+        L.vecchia_batch_plan_create.argtypes = [P, ci, P, P, ci, ci, ci, ci, ctypes.POINTER(P)]
+        L.vecchia_batch_plan_run.argtypes = [P, P, P, P, P, P, P, P, P]
+        L.vecchia_batch_plan_mapping.argtypes = [P, P, P, P]
+        L.vecchia_batch_plan_destroy.argtypes = [P]
         for f in (L.vecchia_create, L.vecchia_destroy, L.vecchia_set_lanes, L.vecchia_set_block_threads,
                   L.vecchia_loglik_grad_info, L.vecchia_loglik_grad_info_host,
                   L.vecchia_covariance_pairs, L.vecchia_nparms, L.vecchia_max_m,
                   L.vecchia_set_timing, L.vecchia_last_timing, L.vecchia_kernels_per_pass,
                   L.vecchia_loglik_grad_info_noalloc, L.vecchia_fit, L.vecchia_autotune,
                   L.vecchia_autotune_save, L.vecchia_autotune_load,
-                  L.vecchia_batch_loglik_grad_info):
+                  L.vecchia_batch_loglik_grad_info, L.vecchia_batch_fit,
+                  L.vecchia_batch_autotune, L.vecchia_batch_plan_create,
+                  L.vecchia_batch_plan_run, L.vecchia_batch_plan_mapping,
+                  L.vecchia_batch_plan_destroy):
             f.restype = ci
         _lib = L
     return _lib
@@ -250,6 +265,127 @@ def vecchia_batch_loglik_grad_info(locs, y, X, NNarray, point_offsets, m, covpar
                                                 ctypes.c_void_p(stream.cuda_stream), _dptr(out),
                                                 _dptr(status)))
     return out, status
+
+
+def _batch_common(locs, y, X, NNarray, point_offsets, m, extra=()):
+    import torch
+    for t, dt, nm in ((locs, torch.float64, "locs"), (y, torch.float64, "y"),
+                      (X, torch.float64, "X"), (NNarray, torch.int32, "NNarray")) + tuple(extra):
+        _dev_tensor_check(t, dt, nm)
+    off = np.ascontiguousarray(point_offsets, dtype=np.int64)
+    mm = np.ascontiguousarray(m, dtype=np.int32)
+    if off.shape != (len(mm) + 1,):
+        raise ValueError("point_offsets needs nbatch + 1 entries")
+    return off, mm
+
+
+class BatchPlan:
+    """vec_batch_plan (include/vecchia.h): the batch description prepared once; ``run``
+    only launches kernels and may be captured into a CUDA graph (torch.cuda.graph)."""
+
+    def __init__(self, point_offsets, m, d: int, p: int, covfun: int, prec="fp64",
+                 handle: Handle | None = None, device: int = 0):
+        self._p = ctypes.c_void_p()
+        off = np.ascontiguousarray(point_offsets, dtype=np.int64)
+        mm = np.ascontiguousarray(m, dtype=np.int32)
+        if off.shape != (len(mm) + 1,):
+            raise ValueError("point_offsets needs nbatch + 1 entries")
+        if handle is None:
+            handle = default_handle(device)
+        P = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+        _check(lib().vecchia_batch_plan_create(handle.ptr, len(mm), P(off), P(mm), d, p, covfun,
+                                               _PREC[prec], ctypes.byref(self._p)))
+        self.nbatch, self.d, self.p, self.covfun = len(mm), d, p, covfun
+
+    def mapping(self) -> dict:
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().vecchia_batch_plan_mapping(self._p, ctypes.byref(a), ctypes.byref(b),
+                                                ctypes.byref(c)))
+        return {"lanes": a.value, "threads": b.value, "ntiles": c.value}
+
+    def run(self, locs, y, X, NNarray, covparms, out, status, stream=None):
+        """Enqueues the batched pass; out (nbatch, 1+q+q*q+p) and status (nbatch, 2) are
+        caller-provided CUDA tensors."""
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream(locs.device)
+        _check(lib().vecchia_batch_plan_run(self._p, _dptr(locs), _dptr(y), _dptr(X),
+                                            _dptr(NNarray), _dptr(covparms),
+                                            ctypes.c_void_p(stream.cuda_stream), _dptr(out),
+                                            _dptr(status)))
+
+    def close(self):
+        if self._p:
+            lib().vecchia_batch_plan_destroy(self._p)
+            self._p = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def vecchia_batch_fit(locs, y, X, NNarray, point_offsets, m, covfun: int, start,
+                      tol: float = 1e-4, maxit: int = 40, max_halvings: int = 10,
+                      use_graph: bool = True, prec="fp64", stream=None,
+                      handle: Handle | None = None) -> dict:
+    """Fisher scoring for many datasets at once (see vecchia_batch_fit in
+    include/vecchia.h).  Data as for vecchia_batch_loglik_grad_info; start is a CUDA
+    tensor (nbatch, q).  Returns theta (nbatch, q) and out (nbatch, 1+q+q*q+p) as CUDA
+    tensors and status / iters / evals / pass_status as numpy arrays."""
+    import torch
+    off, mm = _batch_common(locs, y, X, NNarray, point_offsets, m,
+                            ((start, torch.float64, "start"),))
+    nb = len(mm)
+    d = locs.shape[1]
+    p = X.shape[1]
+    q = NPARMS[covfun]
+    dev = locs.device
+    if tuple(start.shape) != (nb, q):
+        raise ValueError("start must be (nbatch, q)")
+    if handle is None:
+        handle = default_handle(dev.index if dev.index is not None else 0)
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    theta = torch.empty(nb, q, dtype=torch.float64, device=dev)
+    out = torch.empty(nb, 1 + q + q * q + p, dtype=torch.float64, device=dev)
+    infos = (FitInfo * nb)()
+    opts = FitOpts(tol, maxit, max_halvings, 1 if use_graph else 0, _PREC[prec])
+    P = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    _check(lib().vecchia_batch_fit(handle.ptr, nb, _dptr(locs), _dptr(y), _dptr(X), _dptr(NNarray),
+                                   P(off), P(mm), d, p, covfun, _dptr(start), ctypes.byref(opts),
+                                   ctypes.c_void_p(stream.cuda_stream), _dptr(theta), _dptr(out),
+                                   ctypes.cast(infos, ctypes.c_void_p)))
+    return {"theta": theta, "out": out,
+            "status": np.array([f.status for f in infos]),
+            "iters": np.array([f.iters for f in infos]),
+            "evals": np.array([f.evals for f in infos]),
+            "pass_status": np.array([f.pass_status for f in infos])}
+
+
+def vecchia_batch_autotune(locs, y, X, NNarray, point_offsets, m, covparms, covfun: int,
+                           prec="fp64", reps: int = 3, stream=None,
+                           handle: Handle | None = None) -> dict:
+    """Times every kernel mapping of the batched pass on these inputs and records the
+    fastest in the handle (see vecchia_batch_autotune in include/vecchia.h)."""
+    import torch
+    off, mm = _batch_common(locs, y, X, NNarray, point_offsets, m,
+                            ((covparms, torch.float64, "covparms"),))
+    dev = locs.device
+    if handle is None:
+        handle = default_handle(dev.index if dev.index is not None else 0)
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    lanes, threads, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+    P = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    _check(lib().vecchia_batch_autotune(handle.ptr, len(mm), _dptr(locs), _dptr(y), _dptr(X),
+                                        _dptr(NNarray), P(off), P(mm), locs.shape[1], X.shape[1],
+                                        _dptr(covparms), covfun, _PREC[prec],
+                                        ctypes.c_void_p(stream.cuda_stream), reps,
+                                        ctypes.byref(lanes), ctypes.byref(threads),
+                                        ctypes.byref(ms)))
+    return {"lanes": lanes.value, "threads": threads.value, "ms": ms.value}
 
 
 def vecchia_autotune(locs, y, X, NNarray, covparms, covfun: int, prec="fp64", reps: int = 3,

@@ -64,9 +64,33 @@ cudaError_t grow(T** p, size_t* cap, size_t need) {
 
 void vg::set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
 
+constexpr int kFitKey = 24;  // words of the single-fit graph cache key
+
 struct TuneEntry {
     int cov, m, d, p, prec, log2n, lanes, threads;
     float ms;
+};
+
+// Device buffers of a batched pass: the work list (tiles of observations), per-dataset
+// offsets and m, status words, per-tile partial records and per-dataset Matern tables.
+struct BatchScratch {
+    int4* tiles = nullptr; size_t c_tiles = 0;
+    int* tile_off = nullptr; size_t c_tile_off = 0;
+    long long* pt_off = nullptr; size_t c_pt_off = 0;
+    long long* nn_off = nullptr; size_t c_nn_off = 0;
+    int* m = nullptr; size_t c_m = 0;
+    int* status = nullptr; size_t c_status = 0;
+    long long* bad = nullptr; size_t c_bad = 0;
+    int* counter = nullptr; size_t c_counter = 0;
+    double* partials = nullptr; size_t c_part = 0;
+    double* tabs = nullptr; size_t c_tabs = 0;
+    float* tabsf = nullptr; size_t c_tabsf = 0;
+    void release() {
+        cudaFree(tiles); cudaFree(tile_off); cudaFree(pt_off); cudaFree(nn_off); cudaFree(m);
+        cudaFree(status); cudaFree(bad); cudaFree(counter); cudaFree(partials); cudaFree(tabs);
+        cudaFree(tabsf);
+        *this = BatchScratch();
+    }
 };
 
 struct vec_handle_s {
@@ -86,22 +110,19 @@ struct vec_handle_s {
     double* fit_start = nullptr;
     cudaGraph_t fit_graph[2] = {nullptr, nullptr};
     cudaGraphExec_t fit_exec[2] = {nullptr, nullptr};
-    unsigned long long fit_key[2][16] = {{0}, {0}};
+    unsigned long long fit_key[2][kFitKey] = {{0}, {0}};
     int fit_lru = 0;
     // autotuned mappings
     std::vector<TuneEntry> tune;
     // batched pass scratch
-    int4* b_tiles = nullptr; size_t c_tiles = 0;
-    int* b_tile_off = nullptr; size_t c_tile_off = 0;
-    long long* b_pt_off = nullptr; size_t c_pt_off = 0;
-    long long* b_nn_off = nullptr; size_t c_nn_off = 0;
-    int* b_m = nullptr; size_t c_m = 0;
-    int* b_status = nullptr; size_t c_status = 0;
-    long long* b_bad = nullptr; size_t c_bad = 0;
-    int* b_counter = nullptr; size_t c_counter = 0;
-    double* b_partials = nullptr; size_t c_bpart = 0;
-    double* b_tabs = nullptr; size_t c_tabs = 0;
-    float* b_tabsf = nullptr; size_t c_tabsf = 0;
+    BatchScratch bs;
+    // batched fit state
+    vg::FitState* bf_fs = nullptr; size_t c_bf_fs = 0;
+    double* bf_theta = nullptr; size_t c_bf_theta = 0;
+    int* bf_active = nullptr; size_t c_bf_active = 0;
+    int* bf_any = nullptr; size_t c_bf_any = 0;
+    double* bf_out = nullptr; size_t c_bf_out = 0;
+    long long* bf_st = nullptr; size_t c_bf_st = 0;
     // pass scratch
     double* partials = nullptr;
     size_t partials_cap = 0;
@@ -238,9 +259,9 @@ vec_status vecchia_destroy(vec_handle h) {
     cudaFree(h->fit_out);
     cudaFree(h->fit_st);
     cudaFree(h->fit_start);
-    cudaFree(h->b_tiles); cudaFree(h->b_tile_off); cudaFree(h->b_pt_off); cudaFree(h->b_nn_off);
-    cudaFree(h->b_m); cudaFree(h->b_status); cudaFree(h->b_bad); cudaFree(h->b_counter);
-    cudaFree(h->b_partials); cudaFree(h->b_tabs); cudaFree(h->b_tabsf);
+    h->bs.release();
+    cudaFree(h->bf_fs); cudaFree(h->bf_theta); cudaFree(h->bf_active); cudaFree(h->bf_any);
+    cudaFree(h->bf_out); cudaFree(h->bf_st);
     if (h->stream) cudaStreamDestroy(h->stream);
     delete h;
     return VEC_OK;
@@ -457,13 +478,20 @@ vec_status vecchia_fit(vec_handle h, const double* locs, const double* y, const 
         e = vg::launch_fit_init(h->fs, phase_start, q, st);
         if (e != cudaSuccess) { h->timing = saved_timing; return cuda_fail(e, "vecchia_fit: initialising"); }
         if (o.use_graph) {
-            unsigned long long key[16] = {(unsigned long long)(uintptr_t)locs, (unsigned long long)(uintptr_t)y,
-                                          (unsigned long long)(uintptr_t)X, (unsigned long long)(uintptr_t)NNarray,
-                                          (unsigned long long)n, (unsigned long long)d, (unsigned long long)p,
-                                          (unsigned long long)m, (unsigned long long)cov,
-                                          (unsigned long long)prec, (unsigned long long)o.maxit,
-                                          (unsigned long long)o.max_halvings, 0ull,
-                                          (unsigned long long)pplan.L, (unsigned long long)pplan.threads, 1ull};
+            // everything the captured kernels read: inputs, sizes, options, the mapping and
+            // the handle's scratch buffers (a later call may have reallocated them)
+            unsigned long long key[kFitKey] = {
+                (unsigned long long)(uintptr_t)locs, (unsigned long long)(uintptr_t)y,
+                (unsigned long long)(uintptr_t)X, (unsigned long long)(uintptr_t)NNarray,
+                (unsigned long long)n, (unsigned long long)d, (unsigned long long)p,
+                (unsigned long long)m, (unsigned long long)cov, (unsigned long long)prec,
+                (unsigned long long)o.maxit, (unsigned long long)o.max_halvings, 0ull,
+                (unsigned long long)pplan.L, (unsigned long long)pplan.threads,
+                (unsigned long long)pplan.grid, (unsigned long long)(uintptr_t)h->partials,
+                (unsigned long long)(uintptr_t)h->mtab, (unsigned long long)(uintptr_t)h->mtabf,
+                (unsigned long long)(uintptr_t)h->status, (unsigned long long)(uintptr_t)h->bad,
+                (unsigned long long)(uintptr_t)h->fs, (unsigned long long)(uintptr_t)h->fit_out,
+                (unsigned long long)(uintptr_t)h->fit_st};
             std::memcpy(&key[12], &o.tol, sizeof(double));
             int slot = -1;
             for (int k = 0; k < 2; ++k)
@@ -710,8 +738,9 @@ struct BatchPlan {
     std::vector<long long> pt_off, nn_off;
 };
 
-vec_status prepare_batch(vec_handle h, int nbatch, const int64_t* point_offsets, const int* m,
-                         int d, int p, vec_covfun covfun, int prec, cudaStream_t st, BatchPlan* B) {
+vec_status prepare_batch(vec_handle h, BatchScratch& S, int nbatch, const int64_t* point_offsets,
+                         const int* m, int d, int p, vec_covfun covfun, int prec, cudaStream_t st,
+                         BatchPlan* B) {
     if (nbatch < 1) return fail(VEC_ERR_ARG, "nbatch = %d", nbatch);
     if (!point_offsets || !m) return fail(VEC_ERR_ARG, "point_offsets and m are required");
     if (point_offsets[0] != 0) return fail(VEC_ERR_ARG, "point_offsets[0] must be 0");
@@ -754,59 +783,61 @@ vec_status prepare_batch(vec_handle h, int nbatch, const int64_t* point_offsets,
         B->tile_off[b + 1] = (int)B->tiles.size();
     }
     B->ntiles = (int)B->tiles.size();
-    cudaError_t e = grow(&h->b_tiles, &h->c_tiles, (size_t)B->ntiles);
-    if (e == cudaSuccess) e = grow(&h->b_tile_off, &h->c_tile_off, (size_t)nbatch + 1);
-    if (e == cudaSuccess) e = grow(&h->b_pt_off, &h->c_pt_off, (size_t)nbatch + 1);
-    if (e == cudaSuccess) e = grow(&h->b_nn_off, &h->c_nn_off, (size_t)nbatch + 1);
-    if (e == cudaSuccess) e = grow(&h->b_m, &h->c_m, (size_t)nbatch);
-    if (e == cudaSuccess) e = grow(&h->b_status, &h->c_status, (size_t)nbatch);
-    if (e == cudaSuccess) e = grow(&h->b_bad, &h->c_bad, (size_t)nbatch);
-    if (e == cudaSuccess) e = grow(&h->b_counter, &h->c_counter, (size_t)1);
-    if (e == cudaSuccess) e = grow(&h->b_partials, &h->c_bpart, (size_t)B->ntiles * B->plan.nstat);
+    cudaError_t e = grow(&S.tiles, &S.c_tiles, (size_t)B->ntiles);
+    if (e == cudaSuccess) e = grow(&S.tile_off, &S.c_tile_off, (size_t)nbatch + 1);
+    if (e == cudaSuccess) e = grow(&S.pt_off, &S.c_pt_off, (size_t)nbatch + 1);
+    if (e == cudaSuccess) e = grow(&S.nn_off, &S.c_nn_off, (size_t)nbatch + 1);
+    if (e == cudaSuccess) e = grow(&S.m, &S.c_m, (size_t)nbatch);
+    if (e == cudaSuccess) e = grow(&S.status, &S.c_status, (size_t)nbatch);
+    if (e == cudaSuccess) e = grow(&S.bad, &S.c_bad, (size_t)nbatch);
+    if (e == cudaSuccess) e = grow(&S.counter, &S.c_counter, (size_t)1);
+    if (e == cudaSuccess) e = grow(&S.partials, &S.c_part, (size_t)B->ntiles * B->plan.nstat);
     if (e == cudaSuccess && cov == vg::COV_MATERN)
-        e = grow(&h->b_tabs, &h->c_tabs, (size_t)nbatch * vg::mtab_doubles());
+        e = grow(&S.tabs, &S.c_tabs, (size_t)nbatch * vg::mtab_doubles());
     if (e == cudaSuccess && cov == vg::COV_MATERN && prec)
-        e = grow(&h->b_tabsf, &h->c_tabsf, (size_t)nbatch * vg::mtab_floats());
+        e = grow(&S.tabsf, &S.c_tabsf, (size_t)nbatch * vg::mtab_floats());
     if (e != cudaSuccess) return cuda_fail(e, "allocating batch scratch");
-    e = cudaMemcpyAsync(h->b_tiles, B->tiles.data(), sizeof(int4) * B->ntiles, cudaMemcpyHostToDevice, st);
+    e = cudaMemcpyAsync(S.tiles, B->tiles.data(), sizeof(int4) * B->ntiles, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(h->b_tile_off, B->tile_off.data(), sizeof(int) * (nbatch + 1), cudaMemcpyHostToDevice, st);
+        e = cudaMemcpyAsync(S.tile_off, B->tile_off.data(), sizeof(int) * (nbatch + 1), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(h->b_pt_off, B->pt_off.data(), sizeof(long long) * (nbatch + 1), cudaMemcpyHostToDevice, st);
+        e = cudaMemcpyAsync(S.pt_off, B->pt_off.data(), sizeof(long long) * (nbatch + 1), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(h->b_nn_off, B->nn_off.data(), sizeof(long long) * (nbatch + 1), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h->b_m, m, sizeof(int) * nbatch, cudaMemcpyHostToDevice, st);
+        e = cudaMemcpyAsync(S.nn_off, B->nn_off.data(), sizeof(long long) * (nbatch + 1), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(S.m, m, sizeof(int) * nbatch, cudaMemcpyHostToDevice, st);
     // the host vectors are released when B goes out of scope: make the copies complete
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "uploading the batch description");
     return VEC_OK;
 }
 
-// Enqueues one batched pass (device pointers); no host synchronisation.
-vec_status enqueue_batch(vec_handle h, const BatchPlan& B, const double* locs, const double* y,
-                         const double* X, const int32_t* NN, int d, int p, const double* covparms,
-                         vec_covfun covfun, int prec, cudaStream_t st, double* out,
-                         long long* dev_status, const int* active) {
+// Enqueues one batched pass (device pointers): kernel launches only, no allocation, copy
+// or host synchronisation, so it may be captured into a CUDA graph.
+vec_status enqueue_batch(const BatchScratch& S, const BatchPlan& B, const double* locs,
+                         const double* y, const double* X, const int32_t* NN, int d, int p,
+                         const double* covparms, vec_covfun covfun, int prec, cudaStream_t st,
+                         double* out, long long* dev_status, const int* active) {
     const int cov = (int)covfun;
     const int q = vecchia_nparms(covfun);
-    cudaError_t e = vg::launch_init_batch(h->b_status, h->b_bad, B.nbatch, h->b_counter, st);
+    cudaError_t e = vg::launch_init_batch(S.status, S.bad, B.nbatch, S.counter, st);
     if (e == cudaSuccess && cov == vg::COV_MATERN)
-        e = vg::launch_mtab_build_batch(covparms, B.nbatch, q, h->b_tabs, prec ? h->b_tabsf : nullptr, st);
+        e = vg::launch_mtab_build_batch(covparms, B.nbatch, q, S.tabs, prec ? S.tabsf : nullptr,
+                                        active, st);
     if (e != cudaSuccess) return cuda_fail(e, "launching the batch setup kernels");
     vg::BatchArgs a;
     a.base.locs = locs; a.base.y = y; a.base.X = X; a.base.NN = NN; a.base.covparms = nullptr;
-    a.base.mtab = nullptr; a.base.mtabf = nullptr; a.base.partials = h->b_partials;
+    a.base.mtab = nullptr; a.base.mtabf = nullptr; a.base.partials = S.partials;
     a.base.status = nullptr; a.base.bad = nullptr;
     a.base.n = B.pt_off[B.nbatch]; a.base.d = d; a.base.p = p; a.base.m = B.mmax;
     a.base.nstat = B.plan.nstat; a.base.nv = B.plan.nv; a.base.slot_stride = B.plan.slot_stride;
     a.base.acc_per_lane = B.plan.acc_per_lane; a.base.tab_in_smem = B.plan.tab_smem;
-    a.pt_off = h->b_pt_off; a.nn_off = h->b_nn_off; a.m_b = h->b_m; a.covparms_b = covparms;
-    a.tabs = h->b_tabs; a.tabsf = h->b_tabsf; a.tiles = h->b_tiles; a.ntiles = B.ntiles;
-    a.tile_counter = h->b_counter; a.status_b = h->b_status; a.bad_b = h->b_bad; a.active_b = active;
+    a.pt_off = S.pt_off; a.nn_off = S.nn_off; a.m_b = S.m; a.covparms_b = covparms;
+    a.tabs = S.tabs; a.tabsf = S.tabsf; a.tiles = S.tiles; a.ntiles = B.ntiles;
+    a.tile_counter = S.counter; a.status_b = S.status; a.bad_b = S.bad; a.active_b = active;
     e = vg::launch_pass_batch(cov, B.plan, a, st);
     if (e == cudaSuccess)
-        e = vg::launch_profile_batch(h->b_partials, h->b_tile_off, B.nbatch, B.plan.nstat, p, cov,
-                                     h->b_pt_off, covparms, h->b_status, h->b_bad, out, dev_status, st);
+        e = vg::launch_profile_batch(S.partials, S.tile_off, B.nbatch, B.plan.nstat, p, cov,
+                                     S.pt_off, covparms, S.status, S.bad, out, dev_status, st);
     if (e != cudaSuccess) return cuda_fail(e, "launching the batched pass");
     return VEC_OK;
 }
@@ -815,27 +846,311 @@ vec_status enqueue_batch(vec_handle h, const BatchPlan& B, const double* locs, c
 
 extern "C" {
 
+static vec_status check_batch_args(const char* who, vec_handle h, int nbatch, const double* locs,
+                                   const double* y, const double* X, const int32_t* NNarray,
+                                   const int64_t* point_offsets, const int* m, int d, int p,
+                                   vec_covfun covfun, int prec) {
+    if (!h) return fail(VEC_ERR_ARG, "%s: NULL handle", who);
+    if (!locs || !y || !X || !NNarray || !point_offsets || !m)
+        return fail(VEC_ERR_ARG, "%s: a required pointer is NULL", who);
+    if (nbatch < 1) return fail(VEC_ERR_ARG, "%s: nbatch = %d", who, nbatch);
+    if (vecchia_nparms(covfun) < 0) return fail(VEC_ERR_ARG, "%s: unknown covariance function", who);
+    if (d < 1 || d > vg::DMAX || (covfun == VEC_EXP_SPACETIME && d != 3))
+        return fail(VEC_ERR_ARG, "%s: bad d = %d", who, d);
+    if (p < 1 || p > vg::PMAX) return fail(VEC_ERR_ARG, "%s: p = %d out of range", who, p);
+    if (prec != VEC_FP64 && prec != VEC_MIXED) return fail(VEC_ERR_ARG, "%s: unknown precision", who);
+    return VEC_OK;
+}
+
 vec_status vecchia_batch_loglik_grad_info(vec_handle h, int nbatch, const double* locs,
                                           const double* y, const double* X, const int32_t* NNarray,
                                           const int64_t* point_offsets, const int* m, int d, int p,
                                           const double* covparms, vec_covfun covfun,
                                           vec_precision prec, void* stream, double* out,
                                           int64_t* dev_status) {
-    if (!h) return fail(VEC_ERR_ARG, "vecchia_batch_loglik_grad_info: NULL handle");
-    if (!locs || !y || !X || !NNarray || !covparms || !out || !dev_status)
-        return fail(VEC_ERR_ARG, "a required pointer is NULL");
+    vec_status s = check_batch_args("vecchia_batch_loglik_grad_info", h, nbatch, locs, y, X, NNarray,
+                                    point_offsets, m, d, p, covfun, (int)prec);
+    if (s != VEC_OK) return s;
+    if (!covparms || !out || !dev_status) return fail(VEC_ERR_ARG, "a required pointer is NULL");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(VEC_ERR_CUDA, "cannot select device %d", h->device);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    BatchPlan B;
+    s = prepare_batch(h, h->bs, nbatch, point_offsets, m, d, p, covfun, (int)prec, st, &B);
+    if (s != VEC_OK) return s;
+    return enqueue_batch(h->bs, B, locs, y, X, NNarray, d, p, covparms, covfun, (int)prec, st, out,
+                         reinterpret_cast<long long*>(dev_status), nullptr);
+}
+
+}  // extern "C"
+
+struct vec_batch_plan_s {
+    int device = 0;
+    int nbatch = 0, d = 0, p = 0, prec = 0;
+    vec_covfun covfun = VEC_EXP_ISO;
+    BatchPlan B;
+    BatchScratch S;
+};
+
+extern "C" {
+
+vec_status vecchia_batch_plan_create(vec_handle h, int nbatch, const int64_t* point_offsets,
+                                     const int* m, int d, int p, vec_covfun covfun,
+                                     vec_precision prec, vec_batch_plan* plan_out) {
+    if (!plan_out) return fail(VEC_ERR_ARG, "vecchia_batch_plan_create: plan_out is NULL");
+    *plan_out = nullptr;
+    if (!h) return fail(VEC_ERR_ARG, "vecchia_batch_plan_create: NULL handle");
+    if (!point_offsets || !m) return fail(VEC_ERR_ARG, "vecchia_batch_plan_create: point_offsets and m are required");
     if (vecchia_nparms(covfun) < 0) return fail(VEC_ERR_ARG, "unknown covariance function");
     if (d < 1 || d > vg::DMAX || (covfun == VEC_EXP_SPACETIME && d != 3)) return fail(VEC_ERR_ARG, "bad d = %d", d);
     if (p < 1 || p > vg::PMAX) return fail(VEC_ERR_ARG, "p = %d out of range", p);
     if (prec != VEC_FP64 && prec != VEC_MIXED) return fail(VEC_ERR_ARG, "unknown precision");
     DeviceGuard g(h->device);
     if (!g.ok) return fail(VEC_ERR_CUDA, "cannot select device %d", h->device);
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    BatchPlan B;
-    vec_status s = prepare_batch(h, nbatch, point_offsets, m, d, p, covfun, (int)prec, st, &B);
-    if (s != VEC_OK) return s;
-    return enqueue_batch(h, B, locs, y, X, NNarray, d, p, covparms, covfun, (int)prec, st, out,
+    vec_batch_plan_s* P = new (std::nothrow) vec_batch_plan_s;
+    if (!P) return fail(VEC_ERR_NOMEM, "vecchia_batch_plan_create: out of host memory");
+    P->device = h->device;
+    P->nbatch = nbatch;
+    P->d = d;
+    P->p = p;
+    P->prec = (int)prec;
+    P->covfun = covfun;
+    vec_status s = prepare_batch(h, P->S, nbatch, point_offsets, m, d, p, covfun, (int)prec,
+                                 h->stream, &P->B);
+    if (s != VEC_OK) {
+        P->S.release();
+        delete P;
+        return s;
+    }
+    *plan_out = P;
+    return VEC_OK;
+}
+
+vec_status vecchia_batch_plan_run(vec_batch_plan plan, const double* locs, const double* y,
+                                  const double* X, const int32_t* NNarray, const double* covparms,
+                                  void* stream, double* out, int64_t* dev_status) {
+    if (!plan) return fail(VEC_ERR_ARG, "vecchia_batch_plan_run: NULL plan");
+    if (!locs || !y || !X || !NNarray || !covparms || !out || !dev_status)
+        return fail(VEC_ERR_ARG, "vecchia_batch_plan_run: a required pointer is NULL");
+    DeviceGuard g(plan->device);
+    if (!g.ok) return fail(VEC_ERR_CUDA, "cannot select device %d", plan->device);
+    return enqueue_batch(plan->S, plan->B, locs, y, X, NNarray, plan->d, plan->p, covparms,
+                         plan->covfun, plan->prec, reinterpret_cast<cudaStream_t>(stream), out,
                          reinterpret_cast<long long*>(dev_status), nullptr);
+}
+
+vec_status vecchia_batch_plan_mapping(vec_batch_plan plan, int* lanes, int* threads, int* ntiles) {
+    if (!plan) return fail(VEC_ERR_ARG, "vecchia_batch_plan_mapping: NULL plan");
+    if (lanes) *lanes = plan->B.plan.L;
+    if (threads) *threads = plan->B.plan.threads;
+    if (ntiles) *ntiles = plan->B.ntiles;
+    return VEC_OK;
+}
+
+vec_status vecchia_batch_plan_destroy(vec_batch_plan plan) {
+    if (!plan) return VEC_OK;
+    DeviceGuard g(plan->device);
+    plan->S.release();
+    delete plan;
+    return VEC_OK;
+}
+
+vec_status vecchia_batch_fit(vec_handle h, int nbatch, const double* locs, const double* y,
+                             const double* X, const int32_t* NNarray, const int64_t* point_offsets,
+                             const int* m, int d, int p, vec_covfun covfun, const double* start,
+                             const vec_fit_opts* opts, void* stream, double* theta_out, double* out,
+                             vec_fit_info* fit_info) {
+    vec_fit_opts o = {1e-4, 40, 10, 1, (int)VEC_FP64};
+    if (opts) o = *opts;
+    vec_status s = check_batch_args("vecchia_batch_fit", h, nbatch, locs, y, X, NNarray,
+                                    point_offsets, m, d, p, covfun, o.prec);
+    if (s != VEC_OK) return s;
+    if (!start || !theta_out || !out) return fail(VEC_ERR_ARG, "vecchia_batch_fit: a required pointer is NULL");
+    if (!(o.tol >= 0.0) || o.maxit < 0 || o.maxit > 100000 || o.max_halvings < 0 || o.max_halvings > 60)
+        return fail(VEC_ERR_ARG, "vecchia_batch_fit: bad options (tol %g, maxit %d, max_halvings %d)",
+                    o.tol, o.maxit, o.max_halvings);
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(VEC_ERR_CUDA, "cannot select device %d", h->device);
+    const int cov = (int)covfun;
+    const int q = vecchia_nparms(covfun);
+    const int nout = 1 + q + q * q + p;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = grow(&h->bf_fs, &h->c_bf_fs, (size_t)nbatch);
+    if (e == cudaSuccess) e = grow(&h->bf_theta, &h->c_bf_theta, (size_t)nbatch * q);
+    if (e == cudaSuccess) e = grow(&h->bf_active, &h->c_bf_active, (size_t)nbatch);
+    if (e == cudaSuccess) e = grow(&h->bf_any, &h->c_bf_any, (size_t)1);
+    if (e == cudaSuccess) e = grow(&h->bf_out, &h->c_bf_out, (size_t)nbatch * nout);
+    if (e == cudaSuccess) e = grow(&h->bf_st, &h->c_bf_st, (size_t)nbatch * 2);
+    if (e != cudaSuccess) return cuda_fail(e, "vecchia_batch_fit: allocating the fit state");
+    const int max_evals = (o.maxit + 2) * (o.max_halvings + 2);
+    const int nphase = (o.prec == (int)VEC_MIXED) ? 2 : 1;
+    std::vector<vg::FitState> fsh((size_t)nbatch);
+    std::vector<int> iters0((size_t)nbatch, 0), evals0((size_t)nbatch, 0);
+    const int saved_timing = h->timing;
+    h->timing = 0;
+    for (int phase = 0; phase < nphase; ++phase) {
+        const int prec = (nphase == 2 && phase == 0) ? 1 : 0;
+        BatchPlan B;
+        s = prepare_batch(h, h->bs, nbatch, point_offsets, m, d, p, covfun, prec, st, &B);
+        if (s != VEC_OK) break;
+        e = vg::launch_fit_init_batch(h->bf_fs, start, phase > 0 ? 1 : 0, q, nbatch, h->bf_theta,
+                                      h->bf_active, st);
+        if (e != cudaSuccess) { s = cuda_fail(e, "vecchia_batch_fit: initialising"); break; }
+        if (o.use_graph) {
+            // WHILE node around (batched pass, batched step); built for this call only,
+            // since it captures the handle's batch buffers as they are now
+            cudaGraph_t graph = nullptr;
+            cudaGraphExec_t exec = nullptr;
+            cudaGraphConditionalHandle cond;
+            cudaGraphNode_t node;
+            e = cudaGraphCreate(&graph, 0);
+            if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault);
+            cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+            cp.conditional.handle = cond;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            if (e == cudaSuccess) e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+            vec_status ps = VEC_OK;
+            if (e == cudaSuccess) {
+                e = cudaStreamBeginCaptureToGraph(h->stream, cp.conditional.phGraph_out[0], nullptr,
+                                                  nullptr, 0, cudaStreamCaptureModeRelaxed);
+                if (e == cudaSuccess) {
+                    ps = enqueue_batch(h->bs, B, locs, y, X, NNarray, d, p, h->bf_theta, covfun, prec,
+                                       h->stream, h->bf_out, h->bf_st, h->bf_active);
+                    cudaError_t e2 = vg::launch_fit_step_batch(
+                        h->bf_fs, h->bf_out, h->bf_st, q, p, cov, o.tol, o.maxit, o.max_halvings,
+                        nbatch, h->bf_theta, h->bf_active, h->bf_any, cond, 1, h->stream);
+                    cudaGraph_t captured = nullptr;
+                    e = cudaStreamEndCapture(h->stream, &captured);
+                    if (e == cudaSuccess) e = e2;
+                }
+            }
+            if (e == cudaSuccess && ps == VEC_OK) e = cudaGraphInstantiate(&exec, graph, 0);
+            if (e == cudaSuccess && ps == VEC_OK) e = cudaGraphLaunch(exec, st);
+            if (e == cudaSuccess && ps == VEC_OK) e = cudaStreamSynchronize(st);
+            if (exec) cudaGraphExecDestroy(exec);
+            if (graph) cudaGraphDestroy(graph);
+            if (ps != VEC_OK) { s = ps; break; }
+            if (e != cudaSuccess) { s = cuda_fail(e, "vecchia_batch_fit: running the iteration graph"); break; }
+        } else {
+            for (int ev = 0; ev < max_evals; ++ev) {
+                s = enqueue_batch(h->bs, B, locs, y, X, NNarray, d, p, h->bf_theta, covfun, prec, st,
+                                  h->bf_out, h->bf_st, h->bf_active);
+                if (s != VEC_OK) break;
+                cudaGraphConditionalHandle none = 0;
+                e = vg::launch_fit_step_batch(h->bf_fs, h->bf_out, h->bf_st, q, p, cov, o.tol, o.maxit,
+                                              o.max_halvings, nbatch, h->bf_theta, h->bf_active,
+                                              h->bf_any, none, 0, st);
+                int any = 0;
+                if (e == cudaSuccess) e = cudaMemcpyAsync(&any, h->bf_any, sizeof(int), cudaMemcpyDeviceToHost, st);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+                if (e != cudaSuccess) { s = cuda_fail(e, "vecchia_batch_fit: iterating"); break; }
+                if (!any) break;
+            }
+            if (s != VEC_OK) break;
+        }
+        if (nphase == 2 && phase == 0) {
+            e = cudaMemcpyAsync(fsh.data(), h->bf_fs, sizeof(vg::FitState) * nbatch, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) { s = cuda_fail(e, "vecchia_batch_fit: reading phase 1"); break; }
+            for (int b = 0; b < nbatch; ++b) { iters0[b] = fsh[b].iters; evals0[b] = fsh[b].evals; }
+        }
+    }
+    h->timing = saved_timing;
+    if (s != VEC_OK) return s;
+    e = vg::launch_fit_export_batch(h->bf_fs, nbatch, q, p, theta_out, out, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(fsh.data(), h->bf_fs, sizeof(vg::FitState) * nbatch, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "vecchia_batch_fit: reading the result");
+    if (fit_info)
+        for (int b = 0; b < nbatch; ++b) {
+            fit_info[b].status = fsh[b].done ? fsh[b].status : vg::FIT_MAXIT;
+            fit_info[b].iters = iters0[b] + fsh[b].iters;
+            fit_info[b].evals = evals0[b] + fsh[b].evals;
+            fit_info[b].pass_status = fsh[b].pass_status;
+        }
+    return VEC_OK;
+}
+
+vec_status vecchia_batch_autotune(vec_handle h, int nbatch, const double* locs, const double* y,
+                                  const double* X, const int32_t* NNarray,
+                                  const int64_t* point_offsets, const int* m, int d, int p,
+                                  const double* covparms, vec_covfun covfun, vec_precision prec,
+                                  void* stream, int reps, int* lanes_out, int* threads_out,
+                                  float* ms_out) {
+    vec_status s = check_batch_args("vecchia_batch_autotune", h, nbatch, locs, y, X, NNarray,
+                                    point_offsets, m, d, p, covfun, (int)prec);
+    if (s != VEC_OK) return s;
+    if (!covparms) return fail(VEC_ERR_ARG, "vecchia_batch_autotune: covparms is NULL");
+    if (reps < 1) reps = 1;
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(VEC_ERR_CUDA, "cannot select device %d", h->device);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int cov = (int)covfun;
+    const int q = vecchia_nparms(covfun);
+    double* out = nullptr;
+    long long* dst = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&out), sizeof(double) * nbatch * (1 + q + q * q + p));
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&dst), sizeof(long long) * 2 * nbatch);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    const int saved_L = h->lanes, saved_T = h->threads;
+    int bestL = 0, bestT = 0, mmax = 0;
+    float best = 1e30f;
+    for (int b = 0; b < nbatch; ++b) mmax = m[b] > mmax ? m[b] : mmax;
+    static const int thr_list[] = {256, 128, 64};
+    for (int ti = 0; ti < 3 && e == cudaSuccess && s == VEC_OK; ++ti) {
+        for (int L = 1; L <= 32 && e == cudaSuccess; L *= 2) {
+            if (L > thr_list[ti]) continue;
+            vg::PassPlan plan;
+            if (vg::plan_pass(cov, mmax, d, p, h->nsm, L, thr_list[ti], &plan, (int)prec, true) != 0) continue;
+            if (plan.L != L || plan.threads != thr_list[ti]) continue;
+            h->lanes = L;
+            h->threads = thr_list[ti];
+            BatchPlan B;
+            s = prepare_batch(h, h->bs, nbatch, point_offsets, m, d, p, covfun, (int)prec, st, &B);
+            if (s != VEC_OK) break;
+            s = enqueue_batch(h->bs, B, locs, y, X, NNarray, d, p, covparms, covfun, (int)prec, st, out,
+                              dst, nullptr);
+            if (s != VEC_OK) break;
+            float tmin = 1e30f;
+            for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+                e = cudaEventRecord(e0, st);
+                s = enqueue_batch(h->bs, B, locs, y, X, NNarray, d, p, covparms, covfun, (int)prec, st,
+                                  out, dst, nullptr);
+                if (s != VEC_OK) break;
+                if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < tmin) tmin = ms;
+            }
+            if (s != VEC_OK) break;
+            if (tmin < best) { best = tmin; bestL = L; bestT = thr_list[ti]; }
+        }
+    }
+    h->lanes = saved_L;
+    h->threads = saved_T;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(out);
+    cudaFree(dst);
+    if (s != VEC_OK) return s;
+    if (e != cudaSuccess) return cuda_fail(e, "vecchia_batch_autotune");
+    if (bestL == 0) return fail(VEC_ERR_UNSUPPORTED, "vecchia_batch_autotune: no mapping fits");
+    // batched records are kept apart from single-dataset ones: prec + 2
+    TuneEntry t = {cov, mmax, d, p, (int)prec + 2, ilog2(point_offsets[nbatch]), bestL, bestT, best};
+    bool replaced = false;
+    for (TuneEntry& u : h->tune)
+        if (u.cov == t.cov && u.m == t.m && u.d == t.d && u.p == t.p && u.prec == t.prec &&
+            u.log2n == t.log2n) { u = t; replaced = true; }
+    if (!replaced) h->tune.push_back(t);
+    if (lanes_out) *lanes_out = bestL;
+    if (threads_out) *threads_out = bestT;
+    if (ms_out) *ms_out = best;
+    return VEC_OK;
 }
 
 vec_status vecchia_covariance_pairs(vec_handle h, vec_covfun covfun, const double* covparms,

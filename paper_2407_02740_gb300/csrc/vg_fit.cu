@@ -14,6 +14,9 @@
 //   * the Matern smoothness is clamped to [0.05, 20].
 // The iterations run inside a CUDA graph whose WHILE conditional node repeats the body
 // until k_fit_step clears the condition, so the host is not involved between iterations.
+// The batched form keeps one state per dataset: each iteration is one batched pass over
+// the datasets still iterating, then k_fit_step_batch applies the same rules to each of
+// them and keeps the loop going while any remains.
 #include <climits>
 #include <cmath>
 #include <cstdarg>
@@ -25,8 +28,7 @@
 
 namespace vg {
 
-__global__ void k_fit_init(FitState* fs, const double* start, int q) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__device__ static void fit_init_one(FitState* fs, const double* start, int q) {
     for (int j = 0; j < 4; ++j) {
         fs->theta_trial[j] = (j < q) ? start[j] : 0.0;
         fs->theta_cur[j] = fs->theta_trial[j];
@@ -43,6 +45,25 @@ __global__ void k_fit_init(FitState* fs, const double* start, int q) {
     fs->done = 0;
     fs->status = FIT_RUNNING;
     fs->pass_status = 0;
+}
+
+__global__ void k_fit_init(FitState* fs, const double* start, int q) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    fit_init_one(fs, start, q);
+}
+
+// Batch: dataset b starts from start[b*q..] or, when from_cur is set, from its own
+// theta_cur (the second phase of a mixed-precision fit).  theta_b (nbatch x q) holds the
+// parameters of the next batched pass and active[b] whether dataset b is still iterating.
+__global__ void k_fit_init_batch(FitState* fs, const double* start, int from_cur, int q, int nbatch,
+                                 double* theta_b, int* active) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbatch) return;
+    double s0[4];
+    for (int j = 0; j < q; ++j) s0[j] = from_cur ? fs[b].theta_cur[j] : start[(size_t)b * q + j];
+    fit_init_one(fs + b, s0, q);
+    for (int j = 0; j < q; ++j) theta_b[(size_t)b * q + j] = fs[b].theta_trial[j];
+    active[b] = 1;
 }
 
 // Solves A x = b for a small SPD matrix (n <= 4) by Cholesky; false if not PD.
@@ -78,16 +99,15 @@ __device__ static void set_trial(FitState* fs, int q, int cov, double scale) {
     if (cov == COV_MATERN) fs->theta_trial[2] = fmin(20.0, fmax(0.05, fs->theta_trial[2]));
 }
 
-// out = [loglik, grad(q), info(q*q), betahat(p)] of the pass at theta_trial;
-// dev_status = [code, first failing observation].
-__global__ void k_fit_step(FitState* fs, const double* out, const long long* dev_status, int q,
-                           int p, int cov, double tol, int maxit, int max_halvings,
-                           cudaGraphConditionalHandle cond, int use_cond) {
+// One scoring decision for one dataset.  out = [loglik, grad(q), info(q*q), betahat(p)] of
+// the pass at theta_trial; dev_status = [code, first failing observation].  On return
+// fs->done tells whether the fit has ended; otherwise theta_trial holds the next point.
+__device__ static void fit_step_one(FitState* fs, const double* out, const long long* dev_status,
+                                    int q, int p, int cov, double tol, int maxit,
+                                    int max_halvings) {
     const int max_evals = (maxit + 2) * (max_halvings + 2);
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
     if (fs->done || fs->evals >= max_evals) {
         if (!fs->done) { fs->done = 1; fs->status = FIT_MAXIT; }
-        if (use_cond) cudaGraphSetConditional(cond, 0);
         return;
     }
     fs->evals += 1;
@@ -100,7 +120,6 @@ __global__ void k_fit_step(FitState* fs, const double* out, const long long* dev
         if (!ok) {
             fs->done = 1;
             fs->status = FIT_START_FAILED;
-            if (use_cond) cudaGraphSetConditional(cond, 0);
             return;
         }
         accept = true;
@@ -112,11 +131,9 @@ __global__ void k_fit_step(FitState* fs, const double* out, const long long* dev
         if (fs->halvings > max_halvings) {
             fs->done = 1;
             fs->status = FIT_NO_ASCENT;
-            if (use_cond) cudaGraphSetConditional(cond, 0);
             return;
         }
         set_trial(fs, q, cov, ldexp(1.0, -fs->halvings));
-        if (use_cond) cudaGraphSetConditional(cond, 1);
         return;
     }
     // accept the trial point
@@ -146,7 +163,6 @@ __global__ void k_fit_step(FitState* fs, const double* out, const long long* dev
     if (!solved) {
         fs->done = 1;
         fs->status = FIT_NO_ASCENT;
-        if (use_cond) cudaGraphSetConditional(cond, 0);
         return;
     }
     double dec = 0.0;
@@ -160,7 +176,64 @@ __global__ void k_fit_step(FitState* fs, const double* out, const long long* dev
     } else {
         set_trial(fs, q, cov, 1.0);
     }
+}
+
+__global__ void k_fit_step(FitState* fs, const double* out, const long long* dev_status, int q,
+                           int p, int cov, double tol, int maxit, int max_halvings,
+                           cudaGraphConditionalHandle cond, int use_cond) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    fit_step_one(fs, out, dev_status, q, p, cov, tol, maxit, max_halvings);
     if (use_cond) cudaGraphSetConditional(cond, fs->done ? 0 : 1);
+}
+
+// Batch: one block; thread t steps datasets t, t + blockDim.x, ...  Datasets that have
+// ended are left alone.  The loop condition (and *any_active) is 1 while any dataset
+// still iterates.
+__global__ void k_fit_step_batch(FitState* fs, const double* out, const long long* dev_status,
+                                 int q, int p, int cov, double tol, int maxit, int max_halvings,
+                                 int nbatch, double* theta_b, int* active, int* any_active,
+                                 cudaGraphConditionalHandle cond, int use_cond) {
+    const int nout = 1 + q + q * q + p;
+    int mine = 0;
+    for (int b = threadIdx.x; b < nbatch; b += blockDim.x) {
+        if (!active[b]) continue;
+        FitState* f = fs + b;
+        fit_step_one(f, out + (size_t)b * nout, dev_status + 2 * (size_t)b, q, p, cov, tol, maxit,
+                     max_halvings);
+        if (f->done) {
+            active[b] = 0;
+        } else {
+            for (int j = 0; j < q; ++j) theta_b[(size_t)b * q + j] = f->theta_trial[j];
+            mine = 1;
+        }
+    }
+    const int any = __syncthreads_or(mine);
+    if (threadIdx.x == 0) {
+        *any_active = any;
+        if (use_cond) cudaGraphSetConditional(cond, any ? 1 : 0);
+    }
+}
+
+// Batch results: theta_out (nbatch x q) and out (nbatch x (1+q+q*q+p)) = [loglik, grad,
+// info, betahat] at each dataset's last accepted parameters.
+__global__ void k_fit_export_batch(const FitState* fs, int nbatch, int q, int p, double* theta_out,
+                                   double* out) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbatch) return;
+    const FitState& f = fs[b];
+    const int nout = 1 + q + q * q + p;
+    double* o = out + (size_t)b * nout;
+    for (int j = 0; j < q; ++j) theta_out[(size_t)b * q + j] = f.theta_cur[j];
+    o[0] = f.loglik;
+    for (int j = 0; j < q; ++j) o[1 + j] = f.grad[j];
+    for (int t = 0; t < q * q; ++t) o[1 + q + t] = f.info[t];
+    for (int a = 0; a < p; ++a) o[1 + q + q * q + a] = f.beta[a];
+}
+
+cudaError_t launch_fit_export_batch(const FitState* fs, int nbatch, int q, int p, double* theta_out,
+                                    double* out, cudaStream_t st) {
+    k_fit_export_batch<<<(nbatch + 127) / 128, 128, 0, st>>>(fs, nbatch, q, p, theta_out, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_fit_init(FitState* fs, const double* start, int q, cudaStream_t st) {
@@ -173,6 +246,22 @@ cudaError_t launch_fit_step(FitState* fs, const double* out, const long long* de
                             cudaGraphConditionalHandle cond, int use_cond, cudaStream_t st) {
     k_fit_step<<<1, 1, 0, st>>>(fs, out, dev_status, q, p, cov, tol, maxit, max_halvings, cond,
                                 use_cond);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fit_init_batch(FitState* fs, const double* start, int from_cur, int q,
+                                  int nbatch, double* theta_b, int* active, cudaStream_t st) {
+    k_fit_init_batch<<<(nbatch + 127) / 128, 128, 0, st>>>(fs, start, from_cur, q, nbatch, theta_b,
+                                                         active);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fit_step_batch(FitState* fs, const double* out, const long long* dev_status,
+                                  int q, int p, int cov, double tol, int maxit, int max_halvings,
+                                  int nbatch, double* theta_b, int* active, int* any_active,
+                                  cudaGraphConditionalHandle cond, int use_cond, cudaStream_t st) {
+    k_fit_step_batch<<<1, 256, 0, st>>>(fs, out, dev_status, q, p, cov, tol, maxit, max_halvings,
+                                        nbatch, theta_b, active, any_active, cond, use_cond);
     return cudaGetLastError();
 }
 

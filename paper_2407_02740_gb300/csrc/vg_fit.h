@@ -32,5 +32,13 @@ cudaError_t launch_fit_init(FitState* fs, const double* start, int q, cudaStream
 cudaError_t launch_fit_step(FitState* fs, const double* out, const long long* dev_status, int q,
                             int p, int cov, double tol, int maxit, int max_halvings,
                             cudaGraphConditionalHandle cond, int use_cond, cudaStream_t st);
+cudaError_t launch_fit_init_batch(FitState* fs, const double* start, int from_cur, int q,
+                                  int nbatch, double* theta_b, int* active, cudaStream_t st);
+cudaError_t launch_fit_step_batch(FitState* fs, const double* out, const long long* dev_status,
+                                  int q, int p, int cov, double tol, int maxit, int max_halvings,
+                                  int nbatch, double* theta_b, int* active, int* any_active,
+                                  cudaGraphConditionalHandle cond, int use_cond, cudaStream_t st);
+cudaError_t launch_fit_export_batch(const FitState* fs, int nbatch, int q, int p, double* theta_out,
+                                    double* out, cudaStream_t st);
 
 }  // namespace vg

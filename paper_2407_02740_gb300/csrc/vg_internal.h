@@ -35,7 +35,7 @@ const void* pass_batch_kernel_f64(int cov, int L);
 const void* pass_batch_kernel_f32(int cov, int L);
 cudaError_t launch_pass_batch(int cov, const PassPlan& plan, const BatchArgs& args, cudaStream_t st);
 cudaError_t launch_mtab_build_batch(const double* covparms_b, int nbatch, int q, double* tabs,
-                                    float* tabsf, cudaStream_t st);
+                                    float* tabsf, const int* active, cudaStream_t st);
 cudaError_t launch_init_batch(int* status_b, long long* bad_b, int nbatch, int* tile_counter,
                               cudaStream_t st);
 cudaError_t launch_profile_batch(const double* partials, const int* tile_off, int nbatch, int nstat,

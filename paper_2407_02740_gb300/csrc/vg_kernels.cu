@@ -22,9 +22,12 @@ namespace vg {
 // the parameter error).
 __global__ void __launch_bounds__(MT_NC * 32) k_mtab_build(const double* __restrict__ covparms,
                                                            double* __restrict__ tab,
-                                                           float* __restrict__ tabf, int q) {
+                                                           float* __restrict__ tabf, int q,
+                                                           const int* __restrict__ active) {
     __shared__ double vals[3][MT_NC];
-    // blockIdx.y selects the dataset of a batch: its parameters and its tables
+    // blockIdx.y selects the dataset of a batch: its parameters and its tables; datasets
+    // whose active flag is 0 are skipped
+    if (active && !active[blockIdx.y]) return;
     covparms += (size_t)blockIdx.y * q;
     tab += (size_t)blockIdx.y * MT_DOUBLES;
     if (tabf) tabf += (size_t)blockIdx.y * MT_FLOATS;
@@ -356,8 +359,18 @@ int plan_pass(int cov, int m, int d, int p, int nsm, int force_L, int force_thre
     plan->batched = batched ? 1 : 0;
     const void* fn = pass_kernel(cov, chosen, prec, batched);
     if (!fn) return -1;
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan->smem) !=
-        cudaSuccess)
+    // The attribute is raised to the device's opt-in limit rather than to this launch's
+    // size, so that plans and captured graphs made earlier for larger blocks stay
+    // launchable after later, smaller plans of the same kernel.
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, fn) != cudaSuccess)
+        return -2;
+    const int dyn_max = optin - (int)fa.sharedSizeBytes;
+    if (dyn_max < (int)plan->smem ||
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max) != cudaSuccess)
         return -2;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, plan->smem) !=
@@ -384,8 +397,8 @@ cudaError_t launch_pass_batch(int cov, const PassPlan& plan, const BatchArgs& ar
 }
 
 cudaError_t launch_mtab_build_batch(const double* covparms_b, int nbatch, int q, double* tabs,
-                                    float* tabsf, cudaStream_t st) {
-    k_mtab_build<<<dim3(MT_NINT, nbatch), MT_NC * 32, 0, st>>>(covparms_b, tabs, tabsf, q);
+                                    float* tabsf, const int* active, cudaStream_t st) {
+    k_mtab_build<<<dim3(MT_NINT, nbatch), MT_NC * 32, 0, st>>>(covparms_b, tabs, tabsf, q, active);
     return cudaGetLastError();
 }
 
@@ -410,7 +423,7 @@ cudaError_t launch_init_status(int* status, long long* bad, cudaStream_t st) {
 }
 
 cudaError_t launch_mtab_build(const double* covparms, double* tab, float* tabf, cudaStream_t st) {
-    k_mtab_build<<<MT_NINT, MT_NC * 32, 0, st>>>(covparms, tab, tabf, 4);
+    k_mtab_build<<<MT_NINT, MT_NC * 32, 0, st>>>(covparms, tab, tabf, 4, nullptr);
     return cudaGetLastError();
 }
 

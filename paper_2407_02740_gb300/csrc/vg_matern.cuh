@@ -5,11 +5,12 @@
 // Here M_nu(x) = 2^(1-nu)/Gamma(nu) x^nu K_nu(x) and the two derivatives the likelihood
 // needs are evaluated in two layers:
 //
-//  1. matern_direct: K_nu, K_(nu-1) and dK_nu/dnu from the integral
+//  1. matern_direct_warp (table builder): K_nu, K_(nu-1) and dK_nu/dnu from the integral
 //        K_nu(x) = int_0^inf exp(-x cosh t) cosh(nu t) dt
-//     (and its nu-derivative int exp(-x cosh t) t sinh(nu t) dt), trapezoid rule in t.
-//     The integrands are even and entire in t and decay double-exponentially, so the
-//     trapezoid sum converges geometrically in 1/h.  Scales are kept in log space.
+//     (and its nu-derivative int exp(-x cosh t) t sinh(nu t) dt), trapezoid rule in t,
+//     the nodes shared by the 32 lanes of a warp.  The integrands are even and entire in t
+//     and decay double-exponentially, so the trapezoid sum converges geometrically in 1/h.
+//     Scales are kept in log space.
 //  2. A per-pass coefficient table.  Within one pass nu is fixed, so the three functions
 //        F0(s) = M_nu(sqrt s),
 //        F1(s) = -x dM/dx = 2^(1-nu)/Gamma(nu) x^(nu+1) K_(nu-1)(x),  (rho dM/drho)
@@ -21,8 +22,9 @@
 //     Working in s avoids a square root per entry.  The only singularity of F(s) is at
 //     s = 0 (terms s^nu and s^nu log s), so on a part [a, a (1 + 1/J)] the Chebyshev
 //     interpolant converges like (4J + 2)^-D; with J = 4 and D = 12 that is < 1e-16
-//     relative to M(0) = 1.  Below 2^E0 the direct formula is used; at and above 2^E1 the
-//     functions are below 1e-20 for every nu <= 20 and are returned as 0.
+//     relative to M(0) = 1.  Below 2^E0 the small-argument expansion (matern_small) is
+//     used; at and above 2^E1 the functions are below 1e-20 for every nu <= 20 and are
+//     returned as 0.
 #pragma once
 #include "vg_common.cuh"
 
@@ -30,37 +32,69 @@ namespace vg {
 
 // table geometry (MT_*) is defined in vg_common.cuh
 
-// F0, F1, F2 at x > 0 by the trapezoid rule (see header).  psi = digamma(nu),
-// lgnu = lgamma(nu).
-__device__ inline void matern_direct(double nu, double x, double psi, double lgnu,
-                                     double& F0, double& F1, double& F2) {
-    const double h = 0.1;
-    // envelope exponent mu t - x cosh t with mu = max(nu, |nu-1|) bounds all three
-    // integrands; factor out its maximum Phi
-    double mu = fmax(nu, fabs(nu - 1.0));
-    double ts = asinh(mu / x);
-    double Phi = mu * ts - x * cosh(ts);
-    double S0 = 0.0, S1 = 0.0, S2 = 0.0;
-    for (int k = 0; k < 20000; ++k) {
-        double t = k * h;
-        double ph = mu * t - x * cosh(t) - Phi;
-        double E = exp(ph) * (k == 0 ? 0.5 : 1.0);
-        // cosh(nu t) e^{-mu t}, cosh((nu-1) t) e^{-mu t}, t sinh(nu t) e^{-mu t}
-        double a = exp((nu - mu) * t), b = exp(-(nu + mu) * t);
-        double nu1 = fabs(nu - 1.0);
-        double c = exp((nu1 - mu) * t), dd = exp(-(nu1 + mu) * t);
-        S0 += E * 0.5 * (a + b);
-        S1 += E * 0.5 * (c + dd);
-        S2 += E * 0.5 * t * (a - b);
-        if (t > ts && ph < -50.0) break;
+// F0, F1, F2 below the table (0 < s < 2^E0, so u = s/4 < 2^-32) from the small-argument
+// expansion.  For non-integer nu the series of I_(-nu) and I_nu give
+//   M_nu(x) = Gamma(1-nu) sum_k u^k / (k! Gamma(k+1-nu))
+//             - Gamma(1-nu) u^nu sum_k u^k / (k! Gamma(k+1+nu)),
+// and for u < 2^-32 every term other than 1, A1 u, C u^nu and, for nu < 1,
+// C u^(nu+1)/(1+nu) is below 3e-18, where A1 = 1/(1-nu) and C = -Gamma(1-nu)/Gamma(1+nu).
+// A1 and C have poles at nu = 1 whose sum stays finite, so for |nu - 1| < 0.01 the pair is
+// evaluated as
+//   A1 u + C u^nu = u [(g - 1)/delta + g expm1(delta l)/delta],
+//   delta = nu - 1, l = log u, g = Gamma(1-delta)/Gamma(2+delta),
+// which tends to u (log u + 2 gamma_E - 1) at nu = 1 (the expansion of x K_1(x)).  At
+// nu = 2 the u^nu term and the u^2 term have canceling poles too; both are O(u^2 log u)
+// together, and the u^nu term is dropped for nu >= 1.99 (it is below u^1.99 |C| there).
+// F1 = -2u dM/du and F2 = dM/dnu follow term by term.  psi = digamma(nu).
+static __device__ __noinline__ void matern_small(double nu, double s, double psi, double& F0, double& F1,
+                                    double& F2) {
+    const double u = 0.25 * s;
+    const double l = log(u);
+    const double EULER = 0.57721566490153286061;
+    const double PI = 3.14159265358979323846;
+    const double dl = nu - 1.0;
+    if (fabs(dl) < 0.01) {
+        const double lgg = lgamma(1.0 - dl) - lgamma(2.0 + dl);
+        const double g = exp(lgg);
+        const double gp = g * (-dev_digamma(1.0 - dl) - dev_digamma(2.0 + dl));  // dg/ddelta
+        const double c1 = 2.0 * EULER - 1.0;   // g'(0): limit of (g - 1)/delta
+        const double c2 = 0.5 * (c1 * c1 + 1.0);  // g''(0)/2: limit of d/ddelta (g - 1)/delta
+        const double G1 = fabs(dl) < 1e-6 ? c1 + c2 * dl : expm1(lgg) / dl;
+        const double G1p = fabs(dl) < 1e-3 ? c2 : (gp * dl - (g - 1.0)) / (dl * dl);
+        const double z = dl * l;
+        double E, Ep;  // expm1(delta l)/delta and its delta-derivative
+        if (fabs(z) < 1e-3) {
+            E = l * (1.0 + z * (0.5 + z * (1.0 / 6.0 + z * (1.0 / 24.0))));
+            Ep = l * l * (0.5 + z * (1.0 / 3.0 + z * 0.125));
+        } else {
+            const double em = expm1(z);
+            E = em / dl;
+            Ep = (z * (em + 1.0) - em) / (dl * dl);
+        }
+        F0 = 1.0 + u * (G1 + g * E);
+        F1 = -2.0 * u * (G1 + g * (E + exp(z)));
+        F2 = u * (G1p + gp * E + g * Ep);
+        return;
     }
-    const double LN2 = 0.6931471805599453;
-    double lx = log(x);
-    double logA = (1.0 - nu) * LN2 - lgnu + nu * lx + Phi + log(h);
-    double A = exp(logA);
-    F0 = A * S0;
-    F1 = A * x * S1;
-    F2 = F0 * (-LN2 - psi + lx) + A * S2;
+    const double A1 = 1.0 / (1.0 - nu);
+    F0 = 1.0 + A1 * u;
+    F1 = -2.0 * A1 * u;
+    F2 = A1 * A1 * u;
+    if (nu < 1.99) {
+        const double C = -tgamma(1.0 - nu) / tgamma(1.0 + nu);
+        // d log|C| / dnu = -psi(1-nu) - psi(1+nu), with psi(1-nu) = psi(nu) + pi cot(pi nu)
+        const double D = -2.0 * psi - 1.0 / nu - PI / tan(PI * nu);
+        const double t = C * exp(nu * l);  // C u^nu
+        F0 += t;
+        F1 -= 2.0 * nu * t;
+        F2 += t * (D + l);
+        if (nu < 1.0) {
+            const double t1 = t * u / (1.0 + nu);  // C u^(nu+1) / (1+nu)
+            F0 += t1;
+            F1 -= 2.0 * (1.0 + nu) * t1;
+            F2 += t1 * (D + l - 1.0 / (1.0 + nu));
+        }
+    }
 }
 
 // Locates s in the table.  Returns the interval index and the local variable w, or
@@ -107,7 +141,7 @@ __device__ __forceinline__ double matern_F0(const double* tab, double s, double 
     if (it == -2) return 0.0;
     if (!(s > 0.0)) return 1.0;
     double f0, f1, f2;
-    matern_direct(nu, sqrt(s), psi, lg, f0, f1, f2);
+    matern_small(nu, s, psi, f0, f1, f2);
     return f0;
 }
 __device__ __forceinline__ void matern_F12(const double* tab, double s, double nu, double psi,
@@ -123,12 +157,15 @@ __device__ __forceinline__ void matern_F12(const double* tab, double s, double n
         F2 = 0.0;
     } else {
         double f0;
-        matern_direct(nu, sqrt(s), psi, lg, f0, F1, F2);
+        matern_small(nu, s, psi, f0, F1, F2);
     }
 }
 
-// Warp-cooperative version of matern_direct for the table builder: lane l sums the
-// trapezoid nodes k = l, l+32, ..., then the partial sums are combined in a fixed order.
+// F0, F1, F2 at x > 0 by the trapezoid rule (h = 0.1; see the header), for the table
+// builder: the envelope exponent mu t - x cosh t with mu = max(nu, |nu-1|) bounds all three
+// integrands and its maximum Phi is factored out; lane l sums the nodes k = l, l+32, ...,
+// then the partial sums are combined in a fixed order.  psi = digamma(nu),
+// lgnu = lgamma(nu).
 __device__ inline void matern_direct_warp(double nu, double x, double psi, double lgnu,
                                           double& F0, double& F1, double& F2) {
     const double h = 0.1;
@@ -191,7 +228,7 @@ __device__ __forceinline__ float matern_F0f(const float* tab, float s, double nu
     if (it == -2) return 0.0f;
     if (!(s > 0.0f)) return 1.0f;
     double f0, f1, f2;
-    matern_direct(nu, sqrt((double)s), psi, lg, f0, f1, f2);
+    matern_small(nu, (double)s, psi, f0, f1, f2);
     return (float)f0;
 }
 __device__ __forceinline__ void matern_F12f(const float* tab, float s, double nu, double psi,
@@ -207,7 +244,7 @@ __device__ __forceinline__ void matern_F12f(const float* tab, float s, double nu
         F2 = 0.0f;
     } else {
         double f0, f1, f2;
-        matern_direct(nu, sqrt((double)s), psi, lg, f0, f1, f2);
+        matern_small(nu, (double)s, psi, f0, f1, f2);
         F1 = (float)f1;
         F2 = (float)f2;
     }

@@ -13,8 +13,15 @@ pytestmark = pytest.mark.gpu
 
 import paper_2407_02740_gb300 as vg  # noqa: E402
 
-# error bounds of the mixed path against FP64 (same as the single-dataset mixed tests)
+# error bounds of the mixed path against FP64 at nugget tau2 >= 0.05 (the single-dataset
+# mixed tests); the FP32 covariance entries carry relative errors of ~6e-8, which the
+# block's conditioning (~(1 + tau2) / tau2 for correlated neighbours) amplifies, so below
+# tau2 = 0.05 every bound is scaled by 0.05 / tau2
 MIXED_BOUNDS = {"loglik": 1e-6, "grad": 2e-4, "info": 2e-5, "beta": 5e-6}
+
+
+def mixed_scale(tau2):
+    return max(1.0, 0.05 / tau2)
 
 
 def _dev(a, dt):
@@ -30,9 +37,11 @@ def _batch(bw, th, prec, h):
     return out, st.cpu().numpy()
 
 
-def _rel_errors(g, o):
+def _rel_errors(g, o, n):
+    # loglik: relative, or per observation where |loglik| < n (a field's loglik can be
+    # close to 0, which makes a relative error meaningless)
     scale = max(np.linalg.norm(o["grad"]), np.sqrt(np.trace(o["info"])))
-    return {"loglik": abs(g["loglik"] - o["loglik"]) / abs(o["loglik"]),
+    return {"loglik": abs(g["loglik"] - o["loglik"]) / max(abs(o["loglik"]), n),
             "grad": np.linalg.norm(g["grad"] - o["grad"]) / scale,
             "info": np.linalg.norm(g["info"] - o["info"]) / np.linalg.norm(o["info"]),
             "beta": np.linalg.norm(g["betahat"] - o["betahat"]) / (np.linalg.norm(o["betahat"]) + 1)}
@@ -93,9 +102,11 @@ def test_batch_mixed_within_bounds_of_fp64():
         omx, smx = _batch(bw, bw.theta_true, "mixed", h)
         assert np.all(s64[:, 0] == 0) and np.all(smx[:, 0] == 0)
         for b in range(bw.nbatch):
-            err = _rel_errors(vg.unpack(omx[b], 4, 1), vg.unpack(o64[b], 4, 1))
+            err = _rel_errors(vg.unpack(omx[b], 4, 1), vg.unpack(o64[b], 4, 1),
+                              bw.offsets[b + 1] - bw.offsets[b])
+            f = mixed_scale(bw.theta_true[b, 3])
             for k, bound in MIXED_BOUNDS.items():
-                assert err[k] <= bound, (b, k, err)
+                assert err[k] <= bound * f, (b, k, f, err)
     finally:
         h.close()
 
@@ -136,4 +147,49 @@ def test_batch_single_dataset_equals_single_pass():
         assert abs(g["loglik"] - s1["loglik"]) <= 1e-12 * abs(s1["loglik"])
         assert np.allclose(g["grad"], s1["grad"], rtol=1e-9, atol=1e-9 * np.abs(s1["grad"]).max())
     finally:
+        h.close()
+
+
+def test_batch_plan_run_and_graph_replay():
+    bw = workloads.cfg_batch(seed=24, nbatch=7, n_range=(300, 2000), m_choices=(5, 10, 20),
+                             m_sim=20)
+    inp = (_dev(bw.locs, torch.float64), _dev(bw.y, torch.float64), _dev(bw.X, torch.float64),
+           _dev(bw.NN, torch.int32))
+    h = vg.Handle(0)
+    plan = vg.BatchPlan(bw.offsets, bw.m, 2, 1, bw.covfun, handle=h)
+    try:
+        mp = plan.mapping()
+        assert mp["ntiles"] >= bw.nbatch
+        th = _dev(bw.theta_true, torch.float64)
+        out = torch.empty(bw.nbatch, 22, dtype=torch.float64, device="cuda:0")
+        st = torch.empty(bw.nbatch, 2, dtype=torch.int64, device="cuda:0")
+        plan.run(*inp, th, out, st)
+        ref, rst = vg.vecchia_batch_loglik_grad_info(*inp, bw.offsets, bw.m, th, bw.covfun,
+                                                     handle=h)
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref) and torch.equal(st, rst)
+        # capture one run, then replay it on new parameters written into the same tensor
+        thg = th.clone()
+        outg = torch.empty_like(out)
+        stg = torch.empty_like(st)
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            plan.run(*inp, thg, outg, stg)
+        torch.cuda.current_stream().wait_stream(side)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            plan.run(*inp, thg, outg, stg)
+        th2 = th.clone()
+        th2[:, 1] *= 1.3
+        th2[:, 3] *= 0.7
+        thg.copy_(th2)
+        g.replay()
+        ref2, _ = vg.vecchia_batch_loglik_grad_info(*inp, bw.offsets, bw.m, th2, bw.covfun,
+                                                    handle=h)
+        torch.cuda.synchronize()
+        assert torch.equal(outg, ref2)
+        assert not torch.equal(ref2, ref)
+    finally:
+        plan.close()
         h.close()

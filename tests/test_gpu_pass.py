@@ -29,7 +29,7 @@ def compare(g, o, tol=TOL):
     return errs
 
 
-def gpu_pass(w, theta, lanes=0, covfun=None):
+def gpu_pass(w, theta, lanes=0, covfun=None, prec="fp64"):
     dev = torch.device("cuda:0")
     h = vg.Handle(0)
     h.set_lanes(lanes)
@@ -37,7 +37,8 @@ def gpu_pass(w, theta, lanes=0, covfun=None):
     out, st = vg.vecchia_loglik_grad_info(t(w.locs, torch.float64), t(w.y, torch.float64),
                                           t(w.X, torch.float64), t(w.NN, torch.int32),
                                           t(theta, torch.float64),
-                                          w.covfun if covfun is None else covfun, handle=h)
+                                          w.covfun if covfun is None else covfun, prec=prec,
+                                          handle=h)
     torch.cuda.synchronize()
     st = st.cpu().numpy()
     res = vg.unpack(out, len(theta), w.p)
@@ -55,14 +56,17 @@ def field(covfun, n, m, p, theta, seed=0, sim="sequential"):
 # ------------------------------------------------------------------ covariance functions
 def test_matern_device_covariance_matches_oracle():
     rng = np.random.default_rng(0)
-    x = np.concatenate([np.geomspace(1e-7, 95.0, 400), rng.uniform(0, 3, 300)])
+    # below x^2 = 2^-30 the device uses the small-argument expansion (down to 1e-150 here)
+    x = np.concatenate([np.geomspace(1e-150, 1e-7, 60, endpoint=False),
+                        np.geomspace(1e-7, 95.0, 400), rng.uniform(0, 3, 300)])
     la = np.zeros((len(x), 2))
     lb = np.column_stack([x * 0.7, np.zeros(len(x))])
     same = np.zeros(len(x), np.int32)
     same[:5] = 1
     lb[:5] = 0.0
     dev = torch.device("cuda:0")
-    for nu in [0.05, 0.3, 0.5, 0.999, 1.0, 1.001, 1.5, 2.5, 4.0, 10.0, 20.0]:
+    for nu in [0.05, 0.3, 0.5, 0.989, 0.999, 0.9999999, 1.0, 1.0000001, 1.001, 1.0101, 1.5,
+               1.9899, 1.999999, 2.0, 2.0000001, 2.5, 4.0, 10.0, 20.0]:
         th = np.array([1.3, 0.7, nu, 0.02])
         C, dC = vg.vecchia_covariance_pairs(
             MAT, torch.tensor(th, device=dev), torch.tensor(la, device=dev),
@@ -102,6 +106,20 @@ def test_pass_matches_oracle(covfun, theta, p, m):
     # away from the truth as well (start of a fit)
     th2 = th * np.array([1.5, 2.0] + [0.7] * (len(th) - 2))
     compare(gpu_pass(w, th2), oracle.loglik_grad_info(w.locs, w.y, w.X, w.NN, th2, covfun))
+
+
+@pytest.mark.parametrize("nu", [0.3, 1.0, 1.0004, 1.5, 2.0, 3.5])
+def test_pass_at_extreme_range_matches_oracle(nu):
+    # a trial point of a fit that runs off towards rho -> infinity: every scaled squared
+    # distance is far below the coefficient table, so each pair takes the small-argument
+    # expansion, in the FP64 pass and in the mixed one
+    w = field(MAT, 700, 12, 1, [1.0, 0.1, 1.5, 0.05], seed=5)
+    th = np.array([0.9, 3.0e4, nu, 0.08])
+    o = oracle.loglik_grad_info(w.locs, w.y, w.X, w.NN, th, MAT)
+    compare(gpu_pass(w, th), o)
+    gm = gpu_pass(w, th, prec="mixed")
+    assert gm["status"] == 0
+    assert abs(gm["loglik"] - o["loglik"]) <= 1e-4 * max(abs(o["loglik"]), w.n)
 
 
 @pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16, 32])

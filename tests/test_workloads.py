@@ -56,3 +56,20 @@ def test_small_exp_workload_shape():
     w = workloads.cfg_small_exp()
     assert w.n == 2000 and w.m == 10 and w.NN.shape == (2000, 11) and w.p == 1
     assert np.all(w.NN[:, 0] == np.arange(2000))
+
+
+def test_batch_workload_layout_and_determinism():
+    a = workloads.cfg_batch(seed=5, nbatch=7, n_range=(100, 600), m_choices=(0, 3, 8), m_sim=8)
+    b = workloads.cfg_batch(seed=5, nbatch=7, n_range=(100, 600), m_choices=(0, 3, 8), m_sim=8)
+    for k in ("locs", "y", "X", "NN", "offsets", "m", "theta_true", "theta_start"):
+        assert np.array_equal(getattr(a, k), getattr(b, k)), k
+    off = a.offsets
+    assert off[0] == 0 and np.all(np.diff(off) >= 1) and off[-1] == len(a.y) == len(a.locs)
+    assert a.NN.size == int(np.sum(np.diff(off) * (a.m.astype(np.int64) + 1)))
+    for k in range(a.nbatch):
+        w = a.dataset(k)
+        n = w.n
+        assert np.array_equal(w.NN[:, 0], np.arange(n))
+        nb = w.NN[:, 1:]
+        assert np.all((nb == -1) | ((nb >= 0) & (nb < np.arange(n)[:, None])))
+        assert np.isclose(w.theta_start[0], np.var(w.y))

@@ -373,12 +373,16 @@ def cfg_batch(seed: int = 1004, nbatch: int = 256, n_range=(1000, 50000), m_choi
               nu_choices=(0.5, 1.5, 2.5), m_sim: int = 40) -> BatchWorkload:
     """nbatch Matern fields in [0,1]^2: n log-uniform in n_range, m from m_choices,
     sigma2 log-uniform [0.5, 2], rho log-uniform [0.02, 0.3], nu from nu_choices, tau2
-    log-uniform [0.001, 0.2], X = 1, beta = 0, sequential draw with m_sim neighbours."""
-    rng = np.random.default_rng(seed)
+    log-uniform [0.001, 0.2], X = 1, beta = 0, sequential draw with m_sim neighbours.
+    Dataset b draws from its own generator (child b of SeedSequence(seed)), so the
+    datasets are built in parallel threads (the C helpers release the GIL) and do not
+    depend on the thread schedule."""
+    from concurrent.futures import ThreadPoolExecutor
     lo, hi = np.log(n_range[0]), np.log(n_range[1])
-    locs, ys, Xs, NNs, ms, th, st = [], [], [], [], [], [], []
-    off = [0]
-    for b in range(nbatch):
+    children = np.random.SeedSequence(seed).spawn(nbatch)
+
+    def one(b):
+        rng = np.random.default_rng(children[b])
         n = int(round(np.exp(rng.uniform(lo, hi))))
         m = int(rng.choice(m_choices))
         theta = np.array([np.exp(rng.uniform(np.log(0.5), np.log(2.0))),
@@ -389,14 +393,13 @@ def cfg_batch(seed: int = 1004, nbatch: int = 256, n_range=(1000, 50000), m_choi
         L = L[maxmin_order(L)]
         NNsim = ordered_nn(L, max(m, m_sim))
         e = simulate_sequential(MATERN_ISO, theta, L, NNsim[:, : m_sim + 1], rng)
-        locs.append(L)
-        ys.append(e)
-        Xs.append(np.ones((n, 1)))
-        NNs.append(np.ascontiguousarray(NNsim[:, : m + 1]).ravel())
-        ms.append(m)
-        th.append(theta)
-        st.append(np.array([np.var(e), 0.1, 1.0, 0.1]))
-        off.append(off[-1] + n)
+        return (L, e, np.ones((n, 1)), np.ascontiguousarray(NNsim[:, : m + 1]).ravel(), m, theta,
+                np.array([np.var(e), 0.1, 1.0, 0.1]))
+
+    with ThreadPoolExecutor(max_workers=max(1, min(16, os.cpu_count() or 1))) as ex:
+        parts = list(ex.map(one, range(nbatch)))
+    locs, ys, Xs, NNs, ms, th, st = (list(t) for t in zip(*parts))
+    off = np.concatenate([[0], np.cumsum([len(e) for e in ys])])
     return BatchWorkload(MATERN_ISO, np.concatenate(locs), np.concatenate(ys), np.concatenate(Xs),
                          np.concatenate(NNs).astype(np.int32), np.array(off, dtype=np.int64),
                          np.array(ms, dtype=np.int32), np.array(th), np.array(st))
