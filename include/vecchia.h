@@ -320,6 +320,73 @@ VECCHIA_API vec_status vecchia_batch_autotune(vec_handle h, int nbatch, const do
                                               int* lanes_out, int* threads_out, float* ms_out);
 
 /*
+ * Fields at shared locations.  nfields fields observed at the same n locations, with the
+ * same covariates and NNarray (replicated simulations, the training fields of a learned
+ * start): locs (n x d), X (n x p) and NNarray (n x (m+1)) are given once, Y is nfields x n
+ * (row b = field b), covparms / start / theta_out are nfields x q.  All DEVICE memory.
+ * Internally these are batches whose datasets share rows, so they run the same kernels
+ * as the batched calls and return the same per-field results:
+ *
+ * vecchia_fields_loglik_grad_info -- as vecchia_batch_loglik_grad_info (out: nfields x
+ *   (1+q+q*q+p), dev_status: nfields x 2).  Waits for the small work-list upload only.
+ * vecchia_fields_fit -- as vecchia_batch_fit (fit_info: HOST, nfields entries or NULL).
+ *   Returns after all fits have finished.
+ * vecchia_fields_simulate -- draws from the Vecchia joint density the NNarray defines
+ *   (Sec. 2.1, Eq. 3: each y_i given its listed earlier neighbours is Gaussian with the
+ *   regression weights and conditional variance of the covariance model, nugget
+ *   included): with b_i the last row of the inverse Cholesky factor of i's block
+ *   (neighbours, then i), b_i . (y_N(i), y_i) = z_i, so y_i = (z_i - sum_c b_ic
+ *   y_NN[i][c]) / b_i0 in the ordering.  z: nfields x n standard normal variates supplied
+ *   by the caller; y: nfields x n output (mean zero: add X beta separately).  The factor
+ *   rows are computed by the pass kernels in FP64 (a chunk of fields at a time, at most
+ *   ~1 GiB of handle scratch), then one warp per field runs the recurrence.
+ *   dev_status: nfields x 2 as for the pass (a block that is not positive definite, a bad
+ *   NNarray row or bad parameters; y of such a field is undefined).  Asynchronous.
+ */
+VECCHIA_API vec_status vecchia_fields_loglik_grad_info(vec_handle h, int nfields,
+                                                       const double* locs, const double* X,
+                                                       const int32_t* NNarray, int64_t n, int d,
+                                                       int p, int m, const double* Y,
+                                                       const double* covparms, vec_covfun covfun,
+                                                       vec_precision prec, void* stream,
+                                                       double* out, int64_t* dev_status);
+VECCHIA_API vec_status vecchia_fields_fit(vec_handle h, int nfields, const double* locs,
+                                          const double* X, const int32_t* NNarray, int64_t n,
+                                          int d, int p, int m, const double* Y, vec_covfun covfun,
+                                          const double* start, const vec_fit_opts* opts,
+                                          void* stream, double* theta_out, double* out,
+                                          vec_fit_info* fit_info);
+VECCHIA_API vec_status vecchia_fields_simulate(vec_handle h, int nfields, const double* locs,
+                                               const int32_t* NNarray, int64_t n, int d, int m,
+                                               const double* covparms, vec_covfun covfun,
+                                               const double* z, void* stream, double* y,
+                                               int64_t* dev_status);
+
+/*
+ * vecchia_fields_variogram -- binned empirical semivariogram features of fields at shared
+ * locations (the input of a learned starting point for vecchia_fit; the paper has no
+ * counterpart).
+ *
+ * For field f (row f of Y, nfields x n) the pairs are every (i, NNarray[i][c]), c >= 1,
+ * NNarray[i][c] >= 0, and npairs random pairs (floor(r1 n / 2^32), floor(r2 n / 2^32))
+ * from rand_pairs (DEVICE, 2 x npairs uint32, interleaved r1, r2; the same words for
+ * every field).  A pair's squared lag h^2 = sum_k (s_ik - s_jk)^2 (FP64, coordinates in
+ * order, no fused multiply-add) falls in bin k when edges2[k] <= h^2 < edges2[k+1]
+ * (edges2: DEVICE, nbins + 1 ascending squared lags, 1 <= nbins <= 64); others are
+ * ignored.  features (DEVICE, nfields x nbins, FP32): the mean of (y_i - y_j)^2 / 2 over
+ * the bin's pairs, divided by the population variance of the field; an empty bin copies
+ * the nearest non-empty bin (the lower one on a tie), all bins empty gives NaN.
+ * bin_sum (FP64) and bin_count (int64), DEVICE nfields x nbins, may be NULL: the raw sums
+ * and counts.  Sums are FP64 in a fixed order (deterministic).  Asynchronous on `stream`.
+ */
+VECCHIA_API vec_status vecchia_fields_variogram(vec_handle h, int nfields, const double* locs,
+                                                const int32_t* NNarray, int64_t n, int d, int m,
+                                                const double* Y, const uint32_t* rand_pairs,
+                                                int64_t npairs, const double* edges2, int nbins,
+                                                void* stream, float* features, double* bin_sum,
+                                                int64_t* bin_count);
+
+/*
  * vecchia_covariance_pairs -- the library's device covariance functions on explicit pairs.
  *
  * For each pair k: C[k] = C(la[k], lb[k]; covparms) including the nugget sigma2 tau2 when

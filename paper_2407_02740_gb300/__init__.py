@@ -14,6 +14,8 @@ Entry points (same names as the C ABI):
   * ``vecchia_batch_loglik_grad_info`` -- the pass for many datasets in one launch
   * ``vecchia_batch_fit``              -- Fisher scoring for many datasets at once
   * ``vecchia_autotune`` / ``vecchia_batch_autotune`` -- kernel-mapping autotuner
+  * ``vecchia_fields_*``               -- many fields at shared locations: pass, fit,
+                                          simulation
 Covariance functions (parameter order): EXP_ISO (sigma2, rho, tau2), MATERN_ISO (sigma2,
 rho, nu, tau2), EXP_SPACETIME (sigma2, rho_s, rho_t, tau2); nugget = sigma2 * tau2.
 """
@@ -112,6 +114,13 @@ def lib():
         L.vecchia_batch_plan_run.argtypes = [P, P, P, P, P, P, P, P, P]
         L.vecchia_batch_plan_mapping.argtypes = [P, P, P, P]
         L.vecchia_batch_plan_destroy.argtypes = [P]
+        L.vecchia_fields_loglik_grad_info.argtypes = [P, ci, P, P, P, i64, ci, ci, ci, P, P, ci,
+                                                      ci, P, P, P]
+        L.vecchia_fields_fit.argtypes = [P, ci, P, P, P, i64, ci, ci, ci, P, ci, P,
+                                         ctypes.POINTER(FitOpts), P, P, P, P]
+        L.vecchia_fields_simulate.argtypes = [P, ci, P, P, i64, ci, ci, P, ci, P, P, P, P]
+        L.vecchia_fields_variogram.argtypes = [P, ci, P, P, i64, ci, ci, P, P, i64, P, ci, P, P, P,
+                                               P]
         for f in (L.vecchia_create, L.vecchia_destroy, L.vecchia_set_lanes, L.vecchia_set_block_threads,
                   L.vecchia_loglik_grad_info, L.vecchia_loglik_grad_info_host,
                   L.vecchia_covariance_pairs, L.vecchia_nparms, L.vecchia_max_m,
@@ -121,7 +130,9 @@ def lib():
                   L.vecchia_batch_loglik_grad_info, L.vecchia_batch_fit,
                   L.vecchia_batch_autotune, L.vecchia_batch_plan_create,
                   L.vecchia_batch_plan_run, L.vecchia_batch_plan_mapping,
-                  L.vecchia_batch_plan_destroy):
+                  L.vecchia_batch_plan_destroy, L.vecchia_fields_loglik_grad_info,
+                  L.vecchia_fields_fit, L.vecchia_fields_simulate,
+                  L.vecchia_fields_variogram):
             f.restype = ci
         _lib = L
     return _lib
@@ -386,6 +397,133 @@ def vecchia_batch_autotune(locs, y, X, NNarray, point_offsets, m, covparms, covf
                                         ctypes.byref(lanes), ctypes.byref(threads),
                                         ctypes.byref(ms)))
     return {"lanes": lanes.value, "threads": threads.value, "ms": ms.value}
+
+
+def _fields_common(locs, X, NNarray, Y, extra=()):
+    import torch
+    for t, dt, nm in ((locs, torch.float64, "locs"), (X, torch.float64, "X"),
+                      (NNarray, torch.int32, "NNarray"), (Y, torch.float64, "Y")) + tuple(extra):
+        _dev_tensor_check(t, dt, nm)
+    n, d = locs.shape
+    if NNarray.shape[0] != n or X.shape[0] != n or Y.dim() != 2 or Y.shape[1] != n:
+        raise ValueError("shapes: locs (n, d), X (n, p), NNarray (n, m+1), Y (nfields, n)")
+    return n, d, X.shape[1], NNarray.shape[1] - 1, Y.shape[0]
+
+
+def vecchia_fields_loglik_grad_info(locs, X, NNarray, Y, covparms, covfun: int, prec="fp64",
+                                    stream=None, out=None, status=None,
+                                    handle: Handle | None = None):
+    """The pass for nfields fields at shared locations (see include/vecchia.h).  Y is
+    (nfields, n), covparms (nfields, q).  Returns (out, status) on the device."""
+    import torch
+    n, d, p, m, nf = _fields_common(locs, X, NNarray, Y, ((covparms, torch.float64, "covparms"),))
+    q = NPARMS[covfun]
+    dev = locs.device
+    if handle is None:
+        handle = default_handle(dev.index if dev.index is not None else 0)
+    if out is None:
+        out = torch.empty(nf, 1 + q + q * q + p, dtype=torch.float64, device=dev)
+    if status is None:
+        status = torch.empty(nf, 2, dtype=torch.int64, device=dev)
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    _check(lib().vecchia_fields_loglik_grad_info(handle.ptr, nf, _dptr(locs), _dptr(X),
+                                                 _dptr(NNarray), n, d, p, m, _dptr(Y),
+                                                 _dptr(covparms), covfun, _PREC[prec],
+                                                 ctypes.c_void_p(stream.cuda_stream), _dptr(out),
+                                                 _dptr(status)))
+    return out, status
+
+
+def vecchia_fields_fit(locs, X, NNarray, Y, covfun: int, start, tol: float = 1e-4,
+                       maxit: int = 40, max_halvings: int = 10, use_graph: bool = True,
+                       prec="fp64", stream=None, handle: Handle | None = None) -> dict:
+    """Fisher scoring for nfields fields at shared locations (see vecchia_fields_fit);
+    start is a CUDA tensor (nfields, q).  Same result dictionary as vecchia_batch_fit."""
+    import torch
+    n, d, p, m, nf = _fields_common(locs, X, NNarray, Y, ((start, torch.float64, "start"),))
+    q = NPARMS[covfun]
+    dev = locs.device
+    if tuple(start.shape) != (nf, q):
+        raise ValueError("start must be (nfields, q)")
+    if handle is None:
+        handle = default_handle(dev.index if dev.index is not None else 0)
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    theta = torch.empty(nf, q, dtype=torch.float64, device=dev)
+    out = torch.empty(nf, 1 + q + q * q + p, dtype=torch.float64, device=dev)
+    infos = (FitInfo * nf)()
+    opts = FitOpts(tol, maxit, max_halvings, 1 if use_graph else 0, _PREC[prec])
+    _check(lib().vecchia_fields_fit(handle.ptr, nf, _dptr(locs), _dptr(X), _dptr(NNarray), n, d,
+                                    p, m, _dptr(Y), covfun, _dptr(start), ctypes.byref(opts),
+                                    ctypes.c_void_p(stream.cuda_stream), _dptr(theta), _dptr(out),
+                                    ctypes.cast(infos, ctypes.c_void_p)))
+    return {"theta": theta, "out": out,
+            "status": np.array([f.status for f in infos]),
+            "iters": np.array([f.iters for f in infos]),
+            "evals": np.array([f.evals for f in infos]),
+            "pass_status": np.array([f.pass_status for f in infos])}
+
+
+def vecchia_fields_simulate(locs, NNarray, covparms, covfun: int, z, stream=None,
+                            handle: Handle | None = None):
+    """Sequential Vecchia draws (see vecchia_fields_simulate): z (nfields, n) standard
+    normal variates on the device, covparms (nfields, q).  Returns (y, status)."""
+    import torch
+    for t, dt, nm in ((locs, torch.float64, "locs"), (NNarray, torch.int32, "NNarray"),
+                      (covparms, torch.float64, "covparms"), (z, torch.float64, "z")):
+        _dev_tensor_check(t, dt, nm)
+    n, d = locs.shape
+    m = NNarray.shape[1] - 1
+    nf = z.shape[0]
+    if z.dim() != 2 or z.shape[1] != n or NNarray.shape[0] != n:
+        raise ValueError("shapes: locs (n, d), NNarray (n, m+1), z (nfields, n)")
+    dev = locs.device
+    if handle is None:
+        handle = default_handle(dev.index if dev.index is not None else 0)
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    y = torch.empty_like(z)
+    status = torch.empty(nf, 2, dtype=torch.int64, device=dev)
+    _check(lib().vecchia_fields_simulate(handle.ptr, nf, _dptr(locs), _dptr(NNarray), n, d, m,
+                                         _dptr(covparms), covfun, _dptr(z),
+                                         ctypes.c_void_p(stream.cuda_stream), _dptr(y),
+                                         _dptr(status)))
+    return y, status
+
+
+def vecchia_fields_variogram(locs, NNarray, Y, rand_pairs, edges2, stream=None, raw=False,
+                             handle: Handle | None = None):
+    """Binned semivariogram features (see vecchia_fields_variogram): Y (nfields, n),
+    rand_pairs (npairs, 2) uint32 as an int32 CUDA tensor (same bits), edges2 (nbins+1)
+    squared lag edges.  Returns features (nfields, nbins) float32, and with raw=True also
+    the bin sums and counts."""
+    import torch
+    for t, dt, nm in ((locs, torch.float64, "locs"), (NNarray, torch.int32, "NNarray"),
+                      (Y, torch.float64, "Y"), (edges2, torch.float64, "edges2"),
+                      (rand_pairs, torch.int32, "rand_pairs")):
+        _dev_tensor_check(t, dt, nm)
+    n, d = locs.shape
+    m = NNarray.shape[1] - 1
+    nf = Y.shape[0]
+    nb = edges2.shape[0] - 1
+    npairs = rand_pairs.shape[0]
+    if Y.dim() != 2 or Y.shape[1] != n or (npairs and rand_pairs.shape[1] != 2):
+        raise ValueError("shapes: locs (n, d), Y (nfields, n), rand_pairs (npairs, 2)")
+    dev = locs.device
+    if handle is None:
+        handle = default_handle(dev.index if dev.index is not None else 0)
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    feats = torch.empty(nf, nb, dtype=torch.float32, device=dev)
+    bs = torch.empty(nf, nb, dtype=torch.float64, device=dev) if raw else None
+    bc = torch.empty(nf, nb, dtype=torch.int64, device=dev) if raw else None
+    _check(lib().vecchia_fields_variogram(handle.ptr, nf, _dptr(locs), _dptr(NNarray), n, d, m,
+                                          _dptr(Y), _dptr(rand_pairs) if npairs else None, npairs,
+                                          _dptr(edges2), nb, ctypes.c_void_p(stream.cuda_stream),
+                                          _dptr(feats), _dptr(bs) if raw else None,
+                                          _dptr(bc) if raw else None))
+    return (feats, bs, bc) if raw else feats
 
 
 def vecchia_autotune(locs, y, X, NNarray, covparms, covfun: int, prec="fp64", reps: int = 3,

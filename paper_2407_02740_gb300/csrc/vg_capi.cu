@@ -1,10 +1,12 @@
 // vg_capi.cu -- the extern "C" boundary of the Vecchia library (declared in
 // include/vecchia.h): handles, argument validation, scratch management and launch order.
+#include <algorithm>
 #include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <new>
 #include <string>
 #include <vector>
@@ -76,9 +78,7 @@ struct TuneEntry {
 struct BatchScratch {
     int4* tiles = nullptr; size_t c_tiles = 0;
     int* tile_off = nullptr; size_t c_tile_off = 0;
-    long long* pt_off = nullptr; size_t c_pt_off = 0;
-    long long* nn_off = nullptr; size_t c_nn_off = 0;
-    int* m = nullptr; size_t c_m = 0;
+    vg::DatasetDesc* desc = nullptr; size_t c_desc = 0;
     int* status = nullptr; size_t c_status = 0;
     long long* bad = nullptr; size_t c_bad = 0;
     int* counter = nullptr; size_t c_counter = 0;
@@ -86,7 +86,7 @@ struct BatchScratch {
     double* tabs = nullptr; size_t c_tabs = 0;
     float* tabsf = nullptr; size_t c_tabsf = 0;
     void release() {
-        cudaFree(tiles); cudaFree(tile_off); cudaFree(pt_off); cudaFree(nn_off); cudaFree(m);
+        cudaFree(tiles); cudaFree(tile_off); cudaFree(desc);
         cudaFree(status); cudaFree(bad); cudaFree(counter); cudaFree(partials); cudaFree(tabs);
         cudaFree(tabsf);
         *this = BatchScratch();
@@ -123,6 +123,13 @@ struct vec_handle_s {
     int* bf_any = nullptr; size_t c_bf_any = 0;
     double* bf_out = nullptr; size_t c_bf_out = 0;
     long long* bf_st = nullptr; size_t c_bf_st = 0;
+    // simulation factor rows
+    double* sim_factor = nullptr; size_t c_sim_factor = 0;
+    // semivariogram scratch
+    double* vg_mean = nullptr; size_t c_vg_mean = 0;
+    double* vg_var = nullptr; size_t c_vg_var = 0;
+    double* vg_psum = nullptr; size_t c_vg_psum = 0;
+    long long* vg_pcnt = nullptr; size_t c_vg_pcnt = 0;
     // pass scratch
     double* partials = nullptr;
     size_t partials_cap = 0;
@@ -261,7 +268,8 @@ vec_status vecchia_destroy(vec_handle h) {
     cudaFree(h->fit_start);
     h->bs.release();
     cudaFree(h->bf_fs); cudaFree(h->bf_theta); cudaFree(h->bf_active); cudaFree(h->bf_any);
-    cudaFree(h->bf_out); cudaFree(h->bf_st);
+    cudaFree(h->bf_out); cudaFree(h->bf_st); cudaFree(h->sim_factor);
+    cudaFree(h->vg_mean); cudaFree(h->vg_var); cudaFree(h->vg_psum); cudaFree(h->vg_pcnt);
     if (h->stream) cudaStreamDestroy(h->stream);
     delete h;
     return VEC_OK;
@@ -732,36 +740,34 @@ namespace {
 // Host-side description of a batch and the uploads shared by the batched pass and fit.
 struct BatchPlan {
     int nbatch, mmax, ntiles;
+    long long ntot;
     vg::PassPlan plan;
     std::vector<int4> tiles;
     std::vector<int> tile_off;
-    std::vector<long long> pt_off, nn_off;
+    std::vector<vg::DatasetDesc> desc;
 };
 
-vec_status prepare_batch(vec_handle h, BatchScratch& S, int nbatch, const int64_t* point_offsets,
-                         const int* m, int d, int p, vec_covfun covfun, int prec, cudaStream_t st,
-                         BatchPlan* B) {
+// Plans and uploads a batch described dataset by dataset (B->desc filled by the caller).
+vec_status prepare_batch_desc(vec_handle h, BatchScratch& S, int d, int p, vec_covfun covfun,
+                              int prec, cudaStream_t st, BatchPlan* B) {
+    const int nbatch = (int)B->desc.size();
     if (nbatch < 1) return fail(VEC_ERR_ARG, "nbatch = %d", nbatch);
-    if (!point_offsets || !m) return fail(VEC_ERR_ARG, "point_offsets and m are required");
-    if (point_offsets[0] != 0) return fail(VEC_ERR_ARG, "point_offsets[0] must be 0");
     B->nbatch = nbatch;
     B->mmax = 0;
-    B->pt_off.assign(point_offsets, point_offsets + nbatch + 1);
-    B->nn_off.assign(nbatch + 1, 0);
+    B->ntot = 0;
     for (int b = 0; b < nbatch; ++b) {
-        const long long nb = point_offsets[b + 1] - point_offsets[b];
-        if (nb < 1) return fail(VEC_ERR_ARG, "dataset %d has n = %lld", b, nb);
-        if (m[b] < 0 || m[b] > vg::KMAX - 1)
-            return fail(VEC_ERR_UNSUPPORTED, "dataset %d: m = %d out of range", b, m[b]);
-        if (m[b] > B->mmax) B->mmax = m[b];
-        B->nn_off[b + 1] = B->nn_off[b] + nb * (m[b] + 1);
+        const vg::DatasetDesc& D = B->desc[b];
+        if (D.n < 1) return fail(VEC_ERR_ARG, "dataset %d has n = %d", b, D.n);
+        if (D.m < 0 || D.m > vg::KMAX - 1)
+            return fail(VEC_ERR_UNSUPPORTED, "dataset %d: m = %d out of range", b, D.m);
+        if (D.m > B->mmax) B->mmax = D.m;
+        B->ntot += D.n;
     }
-    if (point_offsets[nbatch] > (int64_t)INT_MAX) return fail(VEC_ERR_ARG, "too many observations");
     const int cov = (int)covfun;
     // mapping: forced, else autotuned for (cov, mmax, d, p, prec, total n), else planned
     int L = h->lanes, thr = h->threads;
     if (L == 0 && thr == 0) {
-        const int lg = ilog2(point_offsets[nbatch]);
+        const int lg = ilog2(B->ntot);
         for (const TuneEntry& t : h->tune)
             if (t.cov == cov && t.m == B->mmax && t.d == d && t.p == p && t.prec == prec + 2 &&
                 t.log2n == lg) { L = t.lanes; thr = t.threads; }
@@ -775,7 +781,7 @@ vec_status prepare_batch(vec_handle h, BatchScratch& S, int nbatch, const int64_
     B->tiles.clear();
     B->tile_off.assign(nbatch + 1, 0);
     for (int b = 0; b < nbatch; ++b) {
-        const long long nb = point_offsets[b + 1] - point_offsets[b];
+        const long long nb = B->desc[b].n;
         for (long long s0 = 0; s0 < nb; s0 += tsize) {
             long long e0 = s0 + tsize < nb ? s0 + tsize : nb;
             B->tiles.push_back(make_int4(b, (int)s0, (int)e0, 0));
@@ -785,9 +791,7 @@ vec_status prepare_batch(vec_handle h, BatchScratch& S, int nbatch, const int64_
     B->ntiles = (int)B->tiles.size();
     cudaError_t e = grow(&S.tiles, &S.c_tiles, (size_t)B->ntiles);
     if (e == cudaSuccess) e = grow(&S.tile_off, &S.c_tile_off, (size_t)nbatch + 1);
-    if (e == cudaSuccess) e = grow(&S.pt_off, &S.c_pt_off, (size_t)nbatch + 1);
-    if (e == cudaSuccess) e = grow(&S.nn_off, &S.c_nn_off, (size_t)nbatch + 1);
-    if (e == cudaSuccess) e = grow(&S.m, &S.c_m, (size_t)nbatch);
+    if (e == cudaSuccess) e = grow(&S.desc, &S.c_desc, (size_t)nbatch);
     if (e == cudaSuccess) e = grow(&S.status, &S.c_status, (size_t)nbatch);
     if (e == cudaSuccess) e = grow(&S.bad, &S.c_bad, (size_t)nbatch);
     if (e == cudaSuccess) e = grow(&S.counter, &S.c_counter, (size_t)1);
@@ -801,14 +805,54 @@ vec_status prepare_batch(vec_handle h, BatchScratch& S, int nbatch, const int64_
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(S.tile_off, B->tile_off.data(), sizeof(int) * (nbatch + 1), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(S.pt_off, B->pt_off.data(), sizeof(long long) * (nbatch + 1), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(S.nn_off, B->nn_off.data(), sizeof(long long) * (nbatch + 1), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(S.m, m, sizeof(int) * nbatch, cudaMemcpyHostToDevice, st);
+        e = cudaMemcpyAsync(S.desc, B->desc.data(), sizeof(vg::DatasetDesc) * nbatch, cudaMemcpyHostToDevice, st);
     // the host vectors are released when B goes out of scope: make the copies complete
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "uploading the batch description");
     return VEC_OK;
+}
+
+// Concatenated datasets: dataset b owns rows [off[b], off[b+1]) and the next n_b (m_b+1)
+// NNarray entries.
+vec_status prepare_batch(vec_handle h, BatchScratch& S, int nbatch, const int64_t* point_offsets,
+                         const int* m, int d, int p, vec_covfun covfun, int prec, cudaStream_t st,
+                         BatchPlan* B) {
+    if (nbatch < 1) return fail(VEC_ERR_ARG, "nbatch = %d", nbatch);
+    if (!point_offsets || !m) return fail(VEC_ERR_ARG, "point_offsets and m are required");
+    if (point_offsets[0] != 0) return fail(VEC_ERR_ARG, "point_offsets[0] must be 0");
+    if (point_offsets[nbatch] > (int64_t)INT_MAX) return fail(VEC_ERR_ARG, "too many observations");
+    B->desc.assign(nbatch, vg::DatasetDesc());
+    long long nn = 0;
+    for (int b = 0; b < nbatch; ++b) {
+        const long long nb = point_offsets[b + 1] - point_offsets[b];
+        if (nb < 1) return fail(VEC_ERR_ARG, "dataset %d has n = %lld", b, nb);
+        vg::DatasetDesc& D = B->desc[b];
+        D.loc = D.x = D.y = point_offsets[b];
+        D.nn = nn;
+        D.n = (int)nb;
+        D.m = m[b];
+        nn += nb * (long long)(m[b] + 1);
+    }
+    return prepare_batch_desc(h, S, d, p, covfun, prec, st, B);
+}
+
+// Fields at shared locations: every field uses locs, X and NNarray from row 0; field b's
+// observations are y[b n, (b+1) n).
+vec_status prepare_fields(vec_handle h, BatchScratch& S, int nfields, int64_t n, int m, int d,
+                          int p, vec_covfun covfun, int prec, cudaStream_t st, BatchPlan* B) {
+    if (nfields < 1) return fail(VEC_ERR_ARG, "nfields = %d", nfields);
+    if (n < 1 || n > (int64_t)INT_MAX) return fail(VEC_ERR_ARG, "n = %lld out of range", (long long)n);
+    if ((long long)nfields * n > (long long)INT_MAX * 64)
+        return fail(VEC_ERR_ARG, "nfields x n too large");
+    B->desc.assign(nfields, vg::DatasetDesc());
+    for (int b = 0; b < nfields; ++b) {
+        vg::DatasetDesc& D = B->desc[b];
+        D.loc = D.x = D.nn = 0;
+        D.y = (long long)b * n;
+        D.n = (int)n;
+        D.m = m;
+    }
+    return prepare_batch_desc(h, S, d, p, covfun, prec, st, B);
 }
 
 // Enqueues one batched pass (device pointers): kernel launches only, no allocation, copy
@@ -816,7 +860,8 @@ vec_status prepare_batch(vec_handle h, BatchScratch& S, int nbatch, const int64_
 vec_status enqueue_batch(const BatchScratch& S, const BatchPlan& B, const double* locs,
                          const double* y, const double* X, const int32_t* NN, int d, int p,
                          const double* covparms, vec_covfun covfun, int prec, cudaStream_t st,
-                         double* out, long long* dev_status, const int* active) {
+                         double* out, long long* dev_status, const int* active,
+                         double* factor = nullptr) {
     const int cov = (int)covfun;
     const int q = vecchia_nparms(covfun);
     cudaError_t e = vg::launch_init_batch(S.status, S.bad, B.nbatch, S.counter, st);
@@ -828,16 +873,18 @@ vec_status enqueue_batch(const BatchScratch& S, const BatchPlan& B, const double
     a.base.locs = locs; a.base.y = y; a.base.X = X; a.base.NN = NN; a.base.covparms = nullptr;
     a.base.mtab = nullptr; a.base.mtabf = nullptr; a.base.partials = S.partials;
     a.base.status = nullptr; a.base.bad = nullptr;
-    a.base.n = B.pt_off[B.nbatch]; a.base.d = d; a.base.p = p; a.base.m = B.mmax;
+    a.base.n = B.ntot; a.base.d = d; a.base.p = p; a.base.m = B.mmax;
     a.base.nstat = B.plan.nstat; a.base.nv = B.plan.nv; a.base.slot_stride = B.plan.slot_stride;
     a.base.acc_per_lane = B.plan.acc_per_lane; a.base.tab_in_smem = B.plan.tab_smem;
-    a.pt_off = S.pt_off; a.nn_off = S.nn_off; a.m_b = S.m; a.covparms_b = covparms;
+    a.desc = S.desc; a.covparms_b = covparms; a.factor = factor;
     a.tabs = S.tabs; a.tabsf = S.tabsf; a.tiles = S.tiles; a.ntiles = B.ntiles;
     a.tile_counter = S.counter; a.status_b = S.status; a.bad_b = S.bad; a.active_b = active;
     e = vg::launch_pass_batch(cov, B.plan, a, st);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && factor)  // factor rows only: report the per-dataset status
+        e = vg::launch_batch_status(S.status, S.bad, B.nbatch, dev_status, st);
+    else if (e == cudaSuccess)
         e = vg::launch_profile_batch(S.partials, S.tile_off, B.nbatch, B.plan.nstat, p, cov,
-                                     S.pt_off, covparms, S.status, S.bad, out, dev_status, st);
+                                     S.desc, covparms, S.status, S.bad, out, dev_status, st);
     if (e != cudaSuccess) return cuda_fail(e, "launching the batched pass");
     return VEC_OK;
 }
@@ -955,19 +1002,20 @@ vec_status vecchia_batch_plan_destroy(vec_batch_plan plan) {
     return VEC_OK;
 }
 
-vec_status vecchia_batch_fit(vec_handle h, int nbatch, const double* locs, const double* y,
-                             const double* X, const int32_t* NNarray, const int64_t* point_offsets,
-                             const int* m, int d, int p, vec_covfun covfun, const double* start,
-                             const vec_fit_opts* opts, void* stream, double* theta_out, double* out,
-                             vec_fit_info* fit_info) {
-    vec_fit_opts o = {1e-4, 40, 10, 1, (int)VEC_FP64};
-    if (opts) o = *opts;
-    vec_status s = check_batch_args("vecchia_batch_fit", h, nbatch, locs, y, X, NNarray,
-                                    point_offsets, m, d, p, covfun, o.prec);
-    if (s != VEC_OK) return s;
-    if (!start || !theta_out || !out) return fail(VEC_ERR_ARG, "vecchia_batch_fit: a required pointer is NULL");
+}  // extern "C"
+
+// Batched Fisher scoring over the batch that prep(prec, &plan) describes (see
+// vecchia_batch_fit).  Arguments are checked by the callers.
+static vec_status batch_fit_impl(vec_handle h, int nbatch,
+                                 const std::function<vec_status(int, BatchPlan*)>& prep,
+                                 const double* locs, const double* y, const double* X,
+                                 const int32_t* NNarray, int d, int p, vec_covfun covfun,
+                                 const double* start, const vec_fit_opts& o, void* stream,
+                                 double* theta_out, double* out, vec_fit_info* fit_info) {
+    vec_status s = VEC_OK;
+    if (!start || !theta_out || !out) return fail(VEC_ERR_ARG, "batched fit: a required pointer is NULL");
     if (!(o.tol >= 0.0) || o.maxit < 0 || o.maxit > 100000 || o.max_halvings < 0 || o.max_halvings > 60)
-        return fail(VEC_ERR_ARG, "vecchia_batch_fit: bad options (tol %g, maxit %d, max_halvings %d)",
+        return fail(VEC_ERR_ARG, "batched fit: bad options (tol %g, maxit %d, max_halvings %d)",
                     o.tol, o.maxit, o.max_halvings);
     DeviceGuard g(h->device);
     if (!g.ok) return fail(VEC_ERR_CUDA, "cannot select device %d", h->device);
@@ -991,7 +1039,7 @@ vec_status vecchia_batch_fit(vec_handle h, int nbatch, const double* locs, const
     for (int phase = 0; phase < nphase; ++phase) {
         const int prec = (nphase == 2 && phase == 0) ? 1 : 0;
         BatchPlan B;
-        s = prepare_batch(h, h->bs, nbatch, point_offsets, m, d, p, covfun, prec, st, &B);
+        s = prep(prec, &B);
         if (s != VEC_OK) break;
         e = vg::launch_fit_init_batch(h->bf_fs, start, phase > 0 ? 1 : 0, q, nbatch, h->bf_theta,
                                       h->bf_active, st);
@@ -1073,6 +1121,26 @@ vec_status vecchia_batch_fit(vec_handle h, int nbatch, const double* locs, const
     return VEC_OK;
 }
 
+extern "C" {
+
+vec_status vecchia_batch_fit(vec_handle h, int nbatch, const double* locs, const double* y,
+                             const double* X, const int32_t* NNarray, const int64_t* point_offsets,
+                             const int* m, int d, int p, vec_covfun covfun, const double* start,
+                             const vec_fit_opts* opts, void* stream, double* theta_out, double* out,
+                             vec_fit_info* fit_info) {
+    vec_fit_opts o = {1e-4, 40, 10, 1, (int)VEC_FP64};
+    if (opts) o = *opts;
+    vec_status s = check_batch_args("vecchia_batch_fit", h, nbatch, locs, y, X, NNarray,
+                                    point_offsets, m, d, p, covfun, o.prec);
+    if (s != VEC_OK) return s;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    auto prep = [&](int prec, BatchPlan* B) {
+        return prepare_batch(h, h->bs, nbatch, point_offsets, m, d, p, covfun, prec, st, B);
+    };
+    return batch_fit_impl(h, nbatch, prep, locs, y, X, NNarray, d, p, covfun, start, o, stream,
+                          theta_out, out, fit_info);
+}
+
 vec_status vecchia_batch_autotune(vec_handle h, int nbatch, const double* locs, const double* y,
                                   const double* X, const int32_t* NNarray,
                                   const int64_t* point_offsets, const int* m, int d, int p,
@@ -1150,6 +1218,131 @@ vec_status vecchia_batch_autotune(vec_handle h, int nbatch, const double* locs, 
     if (lanes_out) *lanes_out = bestL;
     if (threads_out) *threads_out = bestT;
     if (ms_out) *ms_out = best;
+    return VEC_OK;
+}
+
+static vec_status check_fields_args(const char* who, vec_handle h, int nfields, const double* locs,
+                                    const double* X, const int32_t* NNarray, int64_t n, int d,
+                                    int p, int m, const double* Y, vec_covfun covfun, int prec) {
+    if (!h) return fail(VEC_ERR_ARG, "%s: NULL handle", who);
+    if (!locs || !X || !NNarray || !Y) return fail(VEC_ERR_ARG, "%s: a required pointer is NULL", who);
+    if (nfields < 1) return fail(VEC_ERR_ARG, "%s: nfields = %d", who, nfields);
+    if (n < 1 || n > (int64_t)INT_MAX) return fail(VEC_ERR_ARG, "%s: n = %lld", who, (long long)n);
+    if (m < 0 || m > vg::KMAX - 1) return fail(VEC_ERR_UNSUPPORTED, "%s: m = %d out of range", who, m);
+    if (vecchia_nparms(covfun) < 0) return fail(VEC_ERR_ARG, "%s: unknown covariance function", who);
+    if (d < 1 || d > vg::DMAX || (covfun == VEC_EXP_SPACETIME && d != 3))
+        return fail(VEC_ERR_ARG, "%s: bad d = %d", who, d);
+    if (p < 1 || p > vg::PMAX) return fail(VEC_ERR_ARG, "%s: p = %d out of range", who, p);
+    if (prec != VEC_FP64 && prec != VEC_MIXED) return fail(VEC_ERR_ARG, "%s: unknown precision", who);
+    return VEC_OK;
+}
+
+vec_status vecchia_fields_loglik_grad_info(vec_handle h, int nfields, const double* locs,
+                                           const double* X, const int32_t* NNarray, int64_t n,
+                                           int d, int p, int m, const double* Y,
+                                           const double* covparms, vec_covfun covfun,
+                                           vec_precision prec, void* stream, double* out,
+                                           int64_t* dev_status) {
+    vec_status s = check_fields_args("vecchia_fields_loglik_grad_info", h, nfields, locs, X, NNarray,
+                                     n, d, p, m, Y, covfun, (int)prec);
+    if (s != VEC_OK) return s;
+    if (!covparms || !out || !dev_status) return fail(VEC_ERR_ARG, "a required pointer is NULL");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(VEC_ERR_CUDA, "cannot select device %d", h->device);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    BatchPlan B;
+    s = prepare_fields(h, h->bs, nfields, n, m, d, p, covfun, (int)prec, st, &B);
+    if (s != VEC_OK) return s;
+    return enqueue_batch(h->bs, B, locs, Y, X, NNarray, d, p, covparms, covfun, (int)prec, st, out,
+                         reinterpret_cast<long long*>(dev_status), nullptr);
+}
+
+vec_status vecchia_fields_fit(vec_handle h, int nfields, const double* locs, const double* X,
+                              const int32_t* NNarray, int64_t n, int d, int p, int m,
+                              const double* Y, vec_covfun covfun, const double* start,
+                              const vec_fit_opts* opts, void* stream, double* theta_out,
+                              double* out, vec_fit_info* fit_info) {
+    vec_fit_opts o = {1e-4, 40, 10, 1, (int)VEC_FP64};
+    if (opts) o = *opts;
+    vec_status s = check_fields_args("vecchia_fields_fit", h, nfields, locs, X, NNarray, n, d, p, m,
+                                     Y, covfun, o.prec);
+    if (s != VEC_OK) return s;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    auto prep = [&](int prec, BatchPlan* B) {
+        return prepare_fields(h, h->bs, nfields, n, m, d, p, covfun, prec, st, B);
+    };
+    return batch_fit_impl(h, nfields, prep, locs, Y, X, NNarray, d, p, covfun, start, o, stream,
+                          theta_out, out, fit_info);
+}
+
+vec_status vecchia_fields_simulate(vec_handle h, int nfields, const double* locs,
+                                   const int32_t* NNarray, int64_t n, int d, int m,
+                                   const double* covparms, vec_covfun covfun, const double* z,
+                                   void* stream, double* y, int64_t* dev_status) {
+    // X is not read in factor mode beyond a gather of one column: locs serves as that column
+    vec_status s = check_fields_args("vecchia_fields_simulate", h, nfields, locs, locs, NNarray, n,
+                                     d, 1, m, z, covfun, 0);
+    if (s != VEC_OK) return s;
+    if (!covparms || !y || !dev_status) return fail(VEC_ERR_ARG, "a required pointer is NULL");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(VEC_ERR_CUDA, "cannot select device %d", h->device);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int q = vecchia_nparms(covfun);
+    const size_t row = (size_t)n * (m + 1);
+    // factor rows of a chunk of fields at a time, at most ~1 GiB of scratch
+    const size_t chunk = std::max<size_t>(1, std::min<size_t>((size_t)nfields, ((size_t)1 << 27) / row));
+    cudaError_t e = grow(&h->sim_factor, &h->c_sim_factor, chunk * row);
+    if (e != cudaSuccess) return cuda_fail(e, "vecchia_fields_simulate: allocating factor rows");
+    for (size_t f0 = 0; f0 < (size_t)nfields; f0 += chunk) {
+        const int nf = (int)std::min(chunk, (size_t)nfields - f0);
+        BatchPlan B;
+        s = prepare_fields(h, h->bs, nf, n, m, d, 1, covfun, 0, st, &B);
+        if (s != VEC_OK) return s;
+        s = enqueue_batch(h->bs, B, locs, z + f0 * n, locs, NNarray, d, 1, covparms + f0 * q, covfun,
+                          0, st, nullptr, reinterpret_cast<long long*>(dev_status) + 2 * f0, nullptr,
+                          h->sim_factor);
+        if (s != VEC_OK) return s;
+        e = vg::launch_sim_recur(h->sim_factor, NNarray, (int)n, m, nf, z + f0 * n, y + f0 * n, st);
+        if (e != cudaSuccess) return cuda_fail(e, "vecchia_fields_simulate: launching the recurrence");
+    }
+    return VEC_OK;
+}
+
+vec_status vecchia_fields_variogram(vec_handle h, int nfields, const double* locs,
+                                    const int32_t* NNarray, int64_t n, int d, int m,
+                                    const double* Y, const uint32_t* rand_pairs, int64_t npairs,
+                                    const double* edges2, int nbins, void* stream, float* features,
+                                    double* bin_sum, int64_t* bin_count) {
+    if (!h) return fail(VEC_ERR_ARG, "vecchia_fields_variogram: NULL handle");
+    if (!locs || !NNarray || !Y || !edges2 || !features || (npairs > 0 && !rand_pairs))
+        return fail(VEC_ERR_ARG, "vecchia_fields_variogram: a required pointer is NULL");
+    if (nfields < 1 || n < 2 || n > (int64_t)INT_MAX || d < 1 || d > vg::DMAX || m < 0 ||
+        m > vg::KMAX - 1 || npairs < 0 || nbins < 1 || nbins > vg::VG_MAX_BINS)
+        return fail(VEC_ERR_ARG, "vecchia_fields_variogram: bad sizes (nfields %d, n %lld, d %d, m %d, "
+                    "npairs %lld, nbins %d)", nfields, (long long)n, d, m, (long long)npairs, nbins);
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(VEC_ERR_CUDA, "cannot select device %d", h->device);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    // slices per field: enough blocks to fill the GPU, at least 8192 pairs per block
+    const long long W = n * (long long)m + npairs;
+    long long slices = (4LL * h->nsm * 4 + nfields - 1) / nfields;
+    const long long cap = W / 8192 > 1 ? W / 8192 : 1;
+    if (slices > cap) slices = cap;
+    if (slices < 1) slices = 1;
+    const size_t np = (size_t)nfields * slices * nbins;
+    cudaError_t e = grow(&h->vg_mean, &h->c_vg_mean, (size_t)nfields);
+    if (e == cudaSuccess) e = grow(&h->vg_var, &h->c_vg_var, (size_t)nfields);
+    if (e == cudaSuccess) e = grow(&h->vg_psum, &h->c_vg_psum, np);
+    if (e == cudaSuccess) e = grow(&h->vg_pcnt, &h->c_vg_pcnt, np);
+    if (e != cudaSuccess) return cuda_fail(e, "vecchia_fields_variogram: allocating scratch");
+    e = vg::launch_field_moments(Y, (int)n, nfields, h->vg_mean, h->vg_var, st);
+    if (e == cudaSuccess)
+        e = vg::launch_vario(locs, d, NNarray, (int)n, m, Y, nfields, rand_pairs, (long long)npairs,
+                             edges2, nbins, (int)slices, h->vg_psum, h->vg_pcnt, st);
+    if (e == cudaSuccess)
+        e = vg::launch_vario_finish(h->vg_psum, h->vg_pcnt, (int)slices, nbins, h->vg_var, nfields,
+                                    features, bin_sum, reinterpret_cast<long long*>(bin_count), st);
+    if (e != cudaSuccess) return cuda_fail(e, "vecchia_fields_variogram: launching");
     return VEC_OK;
 }
 

@@ -106,11 +106,17 @@ struct PassArgs {
 // Arguments of the batched pass kernel: many datasets (common d, p, covariance family),
 // concatenated; each has its own n, m and theta.  Work is a list of tiles, each a range of
 // observations of one dataset; each tile's sums become one record.
+// Where dataset b of a batch lives: offsets (in rows of locs and X, entries of y and of
+// the flat NNarray) and its n and m.  Datasets may share rows (fields observed at the
+// same locations share locs, X and NNarray).
+struct DatasetDesc {
+    long long loc, x, y, nn;
+    int n, m;
+};
+
 struct BatchArgs {
-    PassArgs base;                      // concatenated locs/y/X/NN; m = largest m; sizes
-    const long long* __restrict__ pt_off;   // nbatch + 1 observation offsets
-    const long long* __restrict__ nn_off;   // nbatch + 1 NNarray element offsets
-    const int* __restrict__ m_b;            // nbatch
+    PassArgs base;                      // locs/y/X/NN base pointers; m = largest m; sizes
+    const DatasetDesc* __restrict__ desc;   // nbatch
     const double* __restrict__ covparms_b;  // nbatch x q
     const double* __restrict__ tabs;        // nbatch x MT_DOUBLES (Matern)
     const float* __restrict__ tabsf;        // nbatch x MT_FLOATS (Matern, mixed)
@@ -120,6 +126,7 @@ struct BatchArgs {
     int* status_b;                      // nbatch
     long long* bad_b;                   // nbatch
     const int* active_b;                // nbatch flags (datasets to evaluate), or nullptr = all
+    double* factor;                     // nullptr, or the factor rows (see vecchia_point)
 };
 
 // Device-side error reporting: the first error code wins; the smallest failing

@@ -36,10 +36,24 @@ const void* pass_batch_kernel_f32(int cov, int L);
 cudaError_t launch_pass_batch(int cov, const PassPlan& plan, const BatchArgs& args, cudaStream_t st);
 cudaError_t launch_mtab_build_batch(const double* covparms_b, int nbatch, int q, double* tabs,
                                     float* tabsf, const int* active, cudaStream_t st);
+constexpr int VG_MAX_BINS = 64;  // largest number of semivariogram bins
+size_t vario_smem_bytes(int nbins);
+cudaError_t launch_field_moments(const double* Y, int n, int nfields, double* mean, double* var,
+                                 cudaStream_t st);
+cudaError_t launch_vario(const double* locs, int d, const int32_t* NN, int n, int m, const double* Y,
+                         int nfields, const uint32_t* R, long long P, const double* edges2,
+                         int nbins, int slices, double* psum, long long* pcnt, cudaStream_t st);
+cudaError_t launch_vario_finish(const double* psum, const long long* pcnt, int slices, int nbins,
+                                const double* var, int nfields, float* feat, double* bin_sum,
+                                long long* bin_count, cudaStream_t st);
+cudaError_t launch_sim_recur(const double* factor, const int32_t* NN, int n, int m, int nfields,
+                            const double* z, double* y, cudaStream_t st);
+cudaError_t launch_batch_status(const int* status_b, const long long* bad_b, int nbatch,
+                               long long* dev_status, cudaStream_t st);
 cudaError_t launch_init_batch(int* status_b, long long* bad_b, int nbatch, int* tile_counter,
                               cudaStream_t st);
 cudaError_t launch_profile_batch(const double* partials, const int* tile_off, int nbatch, int nstat,
-                                 int p, int cov, const long long* pt_off, const double* covparms_b,
+                                 int p, int cov, const DatasetDesc* desc, const double* covparms_b,
                                  const int* status_b, const long long* bad_b, double* out,
                                  long long* dev_status, cudaStream_t st);
 

@@ -212,7 +212,7 @@ __global__ void k_profile(const double* __restrict__ partials, int nblk, int nst
 // Batch: block b sums the records of dataset b's tiles [tile_off[b], tile_off[b+1]) in
 // order and profiles them with the dataset's parameters.
 __global__ void k_profile_batch(const double* __restrict__ partials, const int* __restrict__ tile_off,
-                                int nstat, int p, int cov, const long long* __restrict__ pt_off,
+                                int nstat, int p, int cov, const DatasetDesc* __restrict__ desc,
                                 const double* __restrict__ covparms_b, const int* status_b,
                                 const long long* bad_b, double* out, long long* dev_status) {
     __shared__ double tot[256];
@@ -226,8 +226,42 @@ __global__ void k_profile_batch(const double* __restrict__ partials, const int* 
     }
     __syncthreads();
     if (tid == 0)
-        profile_from_totals(tot, p, cov, pt_off[b + 1] - pt_off[b], covparms_b + (size_t)b * q,
+        profile_from_totals(tot, p, cov, desc[b].n, covparms_b + (size_t)b * q,
                             status_b[b], bad_b[b], out + (size_t)b * nout, dev_status + 2 * (size_t)b);
+}
+
+// Sequential Vecchia draw of nfields fields from their factor rows (one warp per field):
+// row i holds b = the last row of L^-1 for i's block, in NNarray order, so that
+// b . (y_i, y_N(i)) = z_i, i.e. y_i = (z_i - sum_c b_c y_NN[i][c]) / b_0, in the
+// ordering (each y_i needs only earlier values).
+__global__ void k_sim_recur(const double* __restrict__ factor, const int32_t* __restrict__ NN,
+                            int n, int m, int nfields, const double* __restrict__ z, double* y) {
+    const int w = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (w >= nfields) return;
+    const int W = m + 1;
+    const double* F = factor + (size_t)w * n * W;
+    const double* zz = z + (size_t)w * n;
+    double* yy = y + (size_t)w * n;
+    for (int i = 0; i < n; ++i) {
+        double sum = 0.0;
+        for (int c = 1 + lane; c < W; c += 32) {
+            const int j = NN[(size_t)i * W + c];
+            if (j >= 0) sum = fma(F[(size_t)i * W + c], yy[j], sum);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (lane == 0) yy[i] = (zz[i] - sum) / F[(size_t)i * W];
+        __syncwarp();
+    }
+}
+
+__global__ void k_batch_status(const int* status_b, const long long* bad_b, int nbatch,
+                               long long* dev_status) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbatch) return;
+    dev_status[2 * (size_t)b] = status_b[b];
+    dev_status[2 * (size_t)b + 1] = bad_b[b] == LLONG_MAX ? -1 : bad_b[b];
 }
 
 __global__ void k_init_batch(int* status_b, long long* bad_b, int nbatch, int* tile_counter) {
@@ -402,6 +436,20 @@ cudaError_t launch_mtab_build_batch(const double* covparms_b, int nbatch, int q,
     return cudaGetLastError();
 }
 
+cudaError_t launch_sim_recur(const double* factor, const int32_t* NN, int n, int m, int nfields,
+                            const double* z, double* y, cudaStream_t st) {
+    const int threads = 128;
+    const long long blocks = ((long long)nfields * 32 + threads - 1) / threads;
+    k_sim_recur<<<(unsigned)blocks, threads, 0, st>>>(factor, NN, n, m, nfields, z, y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_status(const int* status_b, const long long* bad_b, int nbatch,
+                               long long* dev_status, cudaStream_t st) {
+    k_batch_status<<<(nbatch + 255) / 256, 256, 0, st>>>(status_b, bad_b, nbatch, dev_status);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_init_batch(int* status_b, long long* bad_b, int nbatch, int* tile_counter,
                               cudaStream_t st) {
     k_init_batch<<<(nbatch + 255) / 256, 256, 0, st>>>(status_b, bad_b, nbatch, tile_counter);
@@ -409,10 +457,10 @@ cudaError_t launch_init_batch(int* status_b, long long* bad_b, int nbatch, int* 
 }
 
 cudaError_t launch_profile_batch(const double* partials, const int* tile_off, int nbatch, int nstat,
-                                 int p, int cov, const long long* pt_off, const double* covparms_b,
+                                 int p, int cov, const DatasetDesc* desc, const double* covparms_b,
                                  const int* status_b, const long long* bad_b, double* out,
                                  long long* dev_status, cudaStream_t st) {
-    k_profile_batch<<<nbatch, 256, 0, st>>>(partials, tile_off, nstat, p, cov, pt_off, covparms_b,
+    k_profile_batch<<<nbatch, 256, 0, st>>>(partials, tile_off, nstat, p, cov, desc, covparms_b,
                                            status_b, bad_b, out, dev_status);
     return cudaGetLastError();
 }

@@ -7,16 +7,18 @@
 //
 //   gather      NNarray row -> block indices (neighbours reversed, observation last),
 //               coordinates relative to the observation and divided by their range,
-//               y and X rows                                         (Algorithm 1, l. 4-5)
-//   assembly    lower triangle of the covariance, nugget on the diagonal       (l. 6)
+//               y and X rows                                        (Algorithm 1: the
+//               substitution of the neighbours, covariance, factor, solves, sums)
+//   assembly    lower triangle of the covariance, nugget on the diagonal
 //   factor      left-looking Cholesky; y and X ride along as extra rows, so the same
-//               column sweep produces Liy = L^-1 y and LiX = L^-1 X            (l. 7-9)
-//   terms       logdet_i, Liy[last], LiX[last, :]                              (l. 10-13)
+//               column sweep produces Liy = L^-1 y and LiX = L^-1 X
+//   terms       logdet_i, Liy[last], LiX[last, :]
 //   derivative  b = last row of L^-1 (back substitution), g_j = dSigma_j b^T with each
 //               pair (a, c) evaluated once (a conflict-free round-robin pair schedule lets
 //               the lanes scatter into g without atomics), m_j = L^-1 g_j, then the dot
-//               products that give dlogdet, dySy, dySX, dXSX and the information (l. 14-15,
-//               written out from dL = L Phi(L^-1 dSigma L^-T))
+//               products that give dlogdet, dySy, dySX, dXSX and the information (the
+//               derivative terms Algorithm 1 leaves out, written out from
+//               dL = L Phi(L^-1 dSigma L^-T))
 //   accumulate  per-observation values into per-lane FP64 running sums (shared memory),
 //               then a fixed-order block reduction into one partial record per block.
 //
@@ -168,6 +170,10 @@ struct PassEnv {
     const uint32_t* sidx;
     double* acc;
     int nstat, vb0, vstep, vmm;
+    // factor mode: when set, the body stops after b and writes it here (row i at
+    // factor + i (m+1), in NNarray order: entry 0 for the observation, entry c for
+    // neighbour NNarray[i][c], 0 for padding)
+    double* factor;
 };
 
 // Algorithm 1 for observation i of the dataset in E (all L lanes of the group call it).
@@ -308,6 +314,12 @@ __device__ __forceinline__ void vecchia_point(const PassEnv<T, Tab>& E, long lon
         const T* Lr = A + c * (c + 1) / 2;
         for (int a = gl; a < c; a += L) bacc[a] = N::fma_(-Lr[a], bc, bacc[a]);
         gsync<L>(gmask);
+    }
+    if (E.factor) {
+        double* fr = E.factor + i * (long long)(m + 1);
+        for (int c = gl; c <= m; c += L) fr[c] = (c < Kp) ? (double)bv[Kp - 1 - c] : 0.0;
+        gsync<L>(gmask);
+        return;
     }
 
     // ---------------- g_j = dSigma_j b^T ----------------
@@ -564,7 +576,7 @@ __global__ void __launch_bounds__(256) k_pass(PassArgs args) {
     E.inv_r1 = inv_r1; E.inv_r2 = inv_r2;
     E.sig2T = sig2T; E.diagC = diagC; E.inv_r1T = inv_r1T; E.inv_r2T = inv_r2T;
     E.tab = tab; E.sidx = sidx; E.acc = acc; E.nstat = args.nstat;
-    E.vb0 = vb0; E.vstep = vstep; E.vmm = vmm;
+    E.vb0 = vb0; E.vstep = vstep; E.vmm = vmm; E.factor = nullptr;
     for (long long i = (long long)blockIdx.x * ngrp + grp; ok && i < n; i += gstride)
         vecchia_point<COV, L, T, Tab>(E, i);
 
@@ -678,12 +690,13 @@ __global__ void __launch_bounds__(256) k_pass_batch(BatchArgs bargs) {
             E.nu = (COV == COV_MATERN) ? th[2] : 0.0;
             E.m_psi = (COV == COV_MATERN && ok) ? dev_digamma(th[2]) : 0.0;
             E.m_lg = (COV == COV_MATERN && ok) ? lgamma(th[2]) : 0.0;
-            const long long po = bargs.pt_off[b];
-            E.locs = args.locs + po * d;
-            E.y = args.y + po;
-            E.X = args.X + po * p;
-            E.NN = args.NN + bargs.nn_off[b];
-            E.m = bargs.m_b[b];
+            const DatasetDesc D = bargs.desc[b];
+            E.locs = args.locs + D.loc * d;
+            E.y = args.y + D.y;
+            E.X = args.X + D.x * p;
+            E.NN = args.NN + D.nn;
+            E.m = D.m;
+            E.factor = bargs.factor ? bargs.factor + D.y * (long long)(D.m + 1) : nullptr;
             E.status = bargs.status_b + b;
             E.bad = bargs.bad_b + b;
             if (COV == COV_MATERN) {
