@@ -387,6 +387,66 @@ VECCHIA_API vec_status vecchia_fields_variogram(vec_handle h, int nfields, const
                                                 int64_t* bin_count);
 
 /*
+ * Learned starting point for Fisher scoring (the paper has no counterpart; its fits start
+ * from fixed rules).  A multilayer perceptron maps the 32 semivariogram features of a field
+ * (vecchia_fields_variogram, 32 log-spaced lag bins) to the isotropic Matern parameters,
+ * as the standardised targets (log(sigma2 / var y), log rho, log nu, log tau2):
+ *   32 -> 128 (ReLU) -> 128 (ReLU) -> 4, FP32.
+ * params: DEVICE, VEC_MLP_NPARAMS floats, row-major (out x in):
+ *   W1[128][32], b1[128], W2[128][128], b2[128], W3[4][128], b3[4].
+ * norm: DEVICE, VEC_MLP_NNORM floats: x_mean[32], x_std[32], t_mean[4], t_std[4]; the
+ * network sees (x - x_mean) / x_std and its outputs are (t - t_mean) / t_std.
+ *
+ * vecchia_mlp_forward: out (nsamples x 4) = predictions o * t_std + t_mean for X
+ *   (nsamples x 32).
+ * vecchia_mlp_grad: loss = mean over samples and outputs of the squared error on the
+ *   standardised targets T, and its gradient (VEC_MLP_NPARAMS floats).  The samples are
+ *   rows index[0..nsamples) of X (rows x 32) and T (rows x 4), or rows 0..nsamples-1
+ *   when index is NULL (a minibatch is a slice of a random permutation).
+ * vecchia_mlp_adam_step: the same gradient, then one Adam step (beta1 0.9, beta2 0.999,
+ *   eps 1e-8, bias corrections for step = 1, 2, ...) on params with the moment buffers
+ *   adam_m, adam_v (VEC_MLP_NPARAMS floats each, zero before step 1); *loss (DEVICE, may be
+ *   NULL) = the loss before the step.  Sums are in a fixed order: runs are reproducible.
+ * vecchia_mlp_column_moments: column means and population standard deviations (1 where
+ *   a column is constant) of X (rows x cols), for x_mean / x_std and t_mean / t_std.
+ * vecchia_fields_warm_start: for fields at shared locations (as vecchia_fields_fit,
+ *   MATERN_ISO), features (32 bins, squared edges edges2, random pairs as in
+ *   vecchia_fields_variogram) -> network -> theta0 = (var(y) e^t0, e^t1, e^t2 clamped to
+ *   [0.05, 20], e^t3); then one pass at theta0 and one at default_start (nfields x 4) in
+ *   precision prec, and start (nfields x 4) = theta0 where it is finite, its pass
+ *   succeeded and its loglik is not below the default's, else the default start.
+ *   used_learned (nfields int) = 1 where theta0 was kept.  features (nfields x 32 FP32,
+ *   may be NULL) receives the features.  Waits for the pass's work-list upload only.
+ * All pointers DEVICE memory; asynchronous on `stream`.
+ */
+#define VEC_MLP_NPARAMS 21252
+#define VEC_MLP_NNORM 72
+VECCHIA_API vec_status vecchia_mlp_forward(vec_handle h, const float* params, const float* norm,
+                                           const float* X, int nsamples, void* stream,
+                                           float* out);
+VECCHIA_API vec_status vecchia_mlp_grad(vec_handle h, const float* params, const float* norm,
+                                        const float* X, const float* T, const int32_t* index,
+                                        int nsamples, void* stream, float* grad, float* loss);
+VECCHIA_API vec_status vecchia_mlp_adam_step(vec_handle h, float* params, float* adam_m,
+                                             float* adam_v, int step, float lr,
+                                             const float* norm, const float* X, const float* T,
+                                             const int32_t* index, int nsamples, void* stream,
+                                             float* loss);
+VECCHIA_API vec_status vecchia_mlp_column_moments(vec_handle h, const float* X, int rows,
+                                                  int cols, void* stream, float* mean,
+                                                  float* sd);
+VECCHIA_API vec_status vecchia_fields_warm_start(vec_handle h, const float* params,
+                                                 const float* norm, int nfields,
+                                                 const double* locs, const double* X,
+                                                 const int32_t* NNarray, int64_t n, int d, int p,
+                                                 int m, const double* Y,
+                                                 const uint32_t* rand_pairs, int64_t npairs,
+                                                 const double* edges2,
+                                                 const double* default_start,
+                                                 vec_precision prec, void* stream, double* start,
+                                                 int* used_learned, float* features);
+
+/*
  * vecchia_covariance_pairs -- the library's device covariance functions on explicit pairs.
  *
  * For each pair k: C[k] = C(la[k], lb[k]; covparms) including the nugget sigma2 tau2 when

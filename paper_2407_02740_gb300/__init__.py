@@ -15,7 +15,9 @@ Entry points (same names as the C ABI):
   * ``vecchia_batch_fit``              -- Fisher scoring for many datasets at once
   * ``vecchia_autotune`` / ``vecchia_batch_autotune`` -- kernel-mapping autotuner
   * ``vecchia_fields_*``               -- many fields at shared locations: pass, fit,
-                                          simulation
+                                          simulation, semivariogram features, learned start
+  * ``vecchia_mlp_*``                  -- the learned start's network (forward, gradient,
+                                          Adam step); training pipeline in ``warmstart``
 Covariance functions (parameter order): EXP_ISO (sigma2, rho, tau2), MATERN_ISO (sigma2,
 rho, nu, tau2), EXP_SPACETIME (sigma2, rho_s, rho_t, tau2); nugget = sigma2 * tau2.
 """
@@ -121,6 +123,13 @@ def lib():
         L.vecchia_fields_simulate.argtypes = [P, ci, P, P, i64, ci, ci, P, ci, P, P, P, P]
         L.vecchia_fields_variogram.argtypes = [P, ci, P, P, i64, ci, ci, P, P, i64, P, ci, P, P, P,
                                                P]
+        cf = ctypes.c_float
+        L.vecchia_mlp_forward.argtypes = [P, P, P, P, ci, P, P]
+        L.vecchia_mlp_grad.argtypes = [P, P, P, P, P, P, ci, P, P, P]
+        L.vecchia_mlp_adam_step.argtypes = [P, P, P, P, ci, cf, P, P, P, P, ci, P, P]
+        L.vecchia_mlp_column_moments.argtypes = [P, P, ci, ci, P, P, P]
+        L.vecchia_fields_warm_start.argtypes = [P, P, P, ci, P, P, P, i64, ci, ci, ci, P, P, i64,
+                                                P, P, ci, P, P, P, P]
         for f in (L.vecchia_create, L.vecchia_destroy, L.vecchia_set_lanes, L.vecchia_set_block_threads,
                   L.vecchia_loglik_grad_info, L.vecchia_loglik_grad_info_host,
                   L.vecchia_covariance_pairs, L.vecchia_nparms, L.vecchia_max_m,
@@ -132,7 +141,9 @@ def lib():
                   L.vecchia_batch_plan_run, L.vecchia_batch_plan_mapping,
                   L.vecchia_batch_plan_destroy, L.vecchia_fields_loglik_grad_info,
                   L.vecchia_fields_fit, L.vecchia_fields_simulate,
-                  L.vecchia_fields_variogram):
+                  L.vecchia_fields_variogram, L.vecchia_mlp_forward, L.vecchia_mlp_grad,
+                  L.vecchia_mlp_adam_step, L.vecchia_mlp_column_moments,
+                  L.vecchia_fields_warm_start):
             f.restype = ci
         _lib = L
     return _lib
@@ -524,6 +535,103 @@ def vecchia_fields_variogram(locs, NNarray, Y, rand_pairs, edges2, stream=None, 
                                           _dptr(feats), _dptr(bs) if raw else None,
                                           _dptr(bc) if raw else None))
     return (feats, bs, bc) if raw else feats
+
+
+MLP_NPARAMS, MLP_NNORM = 21252, 72
+
+
+def _stream(t, stream):
+    import torch
+    return torch.cuda.current_stream(t.device) if stream is None else stream
+
+
+def vecchia_mlp_forward(params, norm, X, stream=None, handle: Handle | None = None):
+    """Predictions (nsamples, 4) of the learned-start network (see include/vecchia.h)."""
+    import torch
+    for t, nm in ((params, "params"), (norm, "norm"), (X, "X")):
+        _dev_tensor_check(t, torch.float32, nm)
+    handle = handle or default_handle(X.device.index or 0)
+    out = torch.empty(X.shape[0], 4, dtype=torch.float32, device=X.device)
+    _check(lib().vecchia_mlp_forward(handle.ptr, _dptr(params), _dptr(norm), _dptr(X), X.shape[0],
+                                     ctypes.c_void_p(_stream(X, stream).cuda_stream), _dptr(out)))
+    return out
+
+
+def _index_arg(index, X):
+    import torch
+    if index is None:
+        return None, X.shape[0]
+    _dev_tensor_check(index, torch.int32, "index")
+    return _dptr(index), index.shape[0]
+
+
+def vecchia_mlp_grad(params, norm, X, T, index=None, stream=None, handle: Handle | None = None):
+    """(gradient, loss) of the mean squared error on standardised targets over the rows
+    `index` (int32 CUDA tensor) of X and T, or all rows."""
+    import torch
+    for t, nm in ((params, "params"), (norm, "norm"), (X, "X"), (T, "T")):
+        _dev_tensor_check(t, torch.float32, nm)
+    handle = handle or default_handle(X.device.index or 0)
+    ip, ns = _index_arg(index, X)
+    g = torch.empty(MLP_NPARAMS, dtype=torch.float32, device=X.device)
+    loss = torch.empty(1, dtype=torch.float32, device=X.device)
+    _check(lib().vecchia_mlp_grad(handle.ptr, _dptr(params), _dptr(norm), _dptr(X), _dptr(T), ip,
+                                  ns, ctypes.c_void_p(_stream(X, stream).cuda_stream), _dptr(g),
+                                  _dptr(loss)))
+    return g, loss
+
+
+def vecchia_mlp_adam_step(params, adam_m, adam_v, step: int, lr: float, norm, X, T, index=None,
+                          loss=None, stream=None, handle: Handle | None = None):
+    """One Adam step in place on params (moment buffers adam_m, adam_v) over the rows
+    `index` of X and T (a minibatch), or all rows."""
+    import torch
+    for t, nm in ((params, "params"), (adam_m, "adam_m"), (adam_v, "adam_v"), (norm, "norm"),
+                  (X, "X"), (T, "T")):
+        _dev_tensor_check(t, torch.float32, nm)
+    handle = handle or default_handle(X.device.index or 0)
+    ip, ns = _index_arg(index, X)
+    _check(lib().vecchia_mlp_adam_step(handle.ptr, _dptr(params), _dptr(adam_m), _dptr(adam_v),
+                                       int(step), float(lr), _dptr(norm), _dptr(X), _dptr(T), ip,
+                                       ns, ctypes.c_void_p(_stream(X, stream).cuda_stream),
+                                       _dptr(loss) if loss is not None else None))
+
+
+def vecchia_mlp_column_moments(X, stream=None, handle: Handle | None = None):
+    """Column means and standard deviations of a float32 CUDA matrix."""
+    import torch
+    _dev_tensor_check(X, torch.float32, "X")
+    handle = handle or default_handle(X.device.index or 0)
+    mean = torch.empty(X.shape[1], dtype=torch.float32, device=X.device)
+    sd = torch.empty_like(mean)
+    _check(lib().vecchia_mlp_column_moments(handle.ptr, _dptr(X), X.shape[0], X.shape[1],
+                                            ctypes.c_void_p(_stream(X, stream).cuda_stream),
+                                            _dptr(mean), _dptr(sd)))
+    return mean, sd
+
+
+def vecchia_fields_warm_start(params, norm, locs, X, NNarray, Y, rand_pairs, edges2,
+                              default_start, prec="fp64", stream=None,
+                              handle: Handle | None = None):
+    """Learned starting points with the default-start fallback (see include/vecchia.h).
+    Returns (start (nfields, 4) float64, used_learned (nfields) int32, features)."""
+    import torch
+    n, d, p, m, nf = _fields_common(locs, X, NNarray, Y, ((default_start, torch.float64, "default_start"),
+                                                          (edges2, torch.float64, "edges2"),
+                                                          (rand_pairs, torch.int32, "rand_pairs")))
+    for t, nm in ((params, "params"), (norm, "norm")):
+        _dev_tensor_check(t, torch.float32, nm)
+    handle = handle or default_handle(locs.device.index or 0)
+    start = torch.empty(nf, 4, dtype=torch.float64, device=locs.device)
+    used = torch.empty(nf, dtype=torch.int32, device=locs.device)
+    feats = torch.empty(nf, 32, dtype=torch.float32, device=locs.device)
+    _check(lib().vecchia_fields_warm_start(handle.ptr, _dptr(params), _dptr(norm), nf, _dptr(locs),
+                                           _dptr(X), _dptr(NNarray), n, d, p, m, _dptr(Y),
+                                           _dptr(rand_pairs), rand_pairs.shape[0], _dptr(edges2),
+                                           _dptr(default_start), _PREC[prec],
+                                           ctypes.c_void_p(_stream(locs, stream).cuda_stream),
+                                           _dptr(start), _dptr(used), _dptr(feats)))
+    return start, used, feats
 
 
 def vecchia_autotune(locs, y, X, NNarray, covparms, covfun: int, prec="fp64", reps: int = 3,

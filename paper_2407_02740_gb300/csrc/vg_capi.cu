@@ -130,6 +130,14 @@ struct vec_handle_s {
     double* vg_var = nullptr; size_t c_vg_var = 0;
     double* vg_psum = nullptr; size_t c_vg_psum = 0;
     long long* vg_pcnt = nullptr; size_t c_vg_pcnt = 0;
+    // MLP and learned start scratch
+    float* mlp_gpart = nullptr; size_t c_mlp_gpart = 0;
+    float* mlp_lpart = nullptr; size_t c_mlp_lpart = 0;
+    float* ws_feat = nullptr; size_t c_ws_feat = 0;
+    float* ws_pred = nullptr; size_t c_ws_pred = 0;
+    double* ws_theta0 = nullptr; size_t c_ws_theta0 = 0;
+    double* ws_out = nullptr; size_t c_ws_out = 0;
+    long long* ws_st = nullptr; size_t c_ws_st = 0;
     // pass scratch
     double* partials = nullptr;
     size_t partials_cap = 0;
@@ -270,6 +278,8 @@ vec_status vecchia_destroy(vec_handle h) {
     cudaFree(h->bf_fs); cudaFree(h->bf_theta); cudaFree(h->bf_active); cudaFree(h->bf_any);
     cudaFree(h->bf_out); cudaFree(h->bf_st); cudaFree(h->sim_factor);
     cudaFree(h->vg_mean); cudaFree(h->vg_var); cudaFree(h->vg_psum); cudaFree(h->vg_pcnt);
+    cudaFree(h->mlp_gpart); cudaFree(h->mlp_lpart); cudaFree(h->ws_feat); cudaFree(h->ws_pred);
+    cudaFree(h->ws_theta0); cudaFree(h->ws_out); cudaFree(h->ws_st);
     if (h->stream) cudaStreamDestroy(h->stream);
     delete h;
     return VEC_OK;
@@ -1343,6 +1353,120 @@ vec_status vecchia_fields_variogram(vec_handle h, int nfields, const double* loc
         e = vg::launch_vario_finish(h->vg_psum, h->vg_pcnt, (int)slices, nbins, h->vg_var, nfields,
                                     features, bin_sum, reinterpret_cast<long long*>(bin_count), st);
     if (e != cudaSuccess) return cuda_fail(e, "vecchia_fields_variogram: launching");
+    return VEC_OK;
+}
+
+vec_status vecchia_mlp_forward(vec_handle h, const float* params, const float* norm,
+                               const float* X, int nsamples, void* stream, float* out) {
+    if (!h || !params || !norm || !X || !out) return fail(VEC_ERR_ARG, "vecchia_mlp_forward: NULL argument");
+    if (nsamples < 1) return fail(VEC_ERR_ARG, "vecchia_mlp_forward: nsamples = %d", nsamples);
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(VEC_ERR_CUDA, "cannot select device %d", h->device);
+    cudaError_t e = vg::launch_mlp_fwdbwd(params, norm, X, nullptr, nullptr, nsamples, 0, out,
+                                          nullptr, nullptr, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "vecchia_mlp_forward");
+    return VEC_OK;
+}
+
+// Loss and gradient (grad != nullptr) or one Adam step.
+static vec_status mlp_train(vec_handle h, float* params, float* adam_m, float* adam_v, int step,
+                            float lr, const float* norm, const float* X, const float* T,
+                            const int32_t* index, int nsamples, void* stream, float* grad,
+                            float* loss) {
+    if (nsamples < 1) return fail(VEC_ERR_ARG, "MLP: nsamples = %d", nsamples);
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(VEC_ERR_CUDA, "cannot select device %d", h->device);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int nblk = (nsamples + vg::mlp_block_samples() - 1) / vg::mlp_block_samples();
+    cudaError_t e = grow(&h->mlp_gpart, &h->c_mlp_gpart, (size_t)nblk * vg::mlp_nparams());
+    if (e == cudaSuccess) e = grow(&h->mlp_lpart, &h->c_mlp_lpart, (size_t)nblk);
+    if (e != cudaSuccess) return cuda_fail(e, "MLP: allocating gradient partials");
+    e = vg::launch_mlp_fwdbwd(params, norm, X, T, index, nsamples, 1, nullptr, h->mlp_gpart,
+                              h->mlp_lpart, st);
+    if (e == cudaSuccess)
+        e = vg::launch_mlp_update(h->mlp_gpart, h->mlp_lpart, nblk, params, adam_m, adam_v, step, lr,
+                                  0.9f, 0.999f, 1e-8f, grad, loss, st);
+    if (e != cudaSuccess) return cuda_fail(e, "MLP: launching");
+    return VEC_OK;
+}
+
+vec_status vecchia_mlp_grad(vec_handle h, const float* params, const float* norm, const float* X,
+                            const float* T, const int32_t* index, int nsamples, void* stream,
+                            float* grad, float* loss) {
+    if (!h || !params || !norm || !X || !T || !grad || !loss)
+        return fail(VEC_ERR_ARG, "vecchia_mlp_grad: NULL argument");
+    return mlp_train(h, const_cast<float*>(params), nullptr, nullptr, 0, 0.0f, norm, X, T, index,
+                     nsamples, stream, grad, loss);
+}
+
+vec_status vecchia_mlp_adam_step(vec_handle h, float* params, float* adam_m, float* adam_v,
+                                 int step, float lr, const float* norm, const float* X,
+                                 const float* T, const int32_t* index, int nsamples, void* stream,
+                                 float* loss) {
+    if (!h || !params || !adam_m || !adam_v || !norm || !X || !T)
+        return fail(VEC_ERR_ARG, "vecchia_mlp_adam_step: NULL argument");
+    if (step < 1 || !(lr > 0.0f)) return fail(VEC_ERR_ARG, "vecchia_mlp_adam_step: step %d, lr %g", step, lr);
+    return mlp_train(h, params, adam_m, adam_v, step, lr, norm, X, T, index, nsamples, stream,
+                     nullptr, loss);
+}
+
+vec_status vecchia_mlp_column_moments(vec_handle h, const float* X, int rows, int cols,
+                                      void* stream, float* mean, float* sd) {
+    if (!h || !X || !mean || !sd || rows < 1 || cols < 1)
+        return fail(VEC_ERR_ARG, "vecchia_mlp_column_moments: bad argument");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(VEC_ERR_CUDA, "cannot select device %d", h->device);
+    cudaError_t e = vg::launch_col_moments(X, rows, cols, mean, sd, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "vecchia_mlp_column_moments");
+    return VEC_OK;
+}
+
+vec_status vecchia_fields_warm_start(vec_handle h, const float* params, const float* norm,
+                                     int nfields, const double* locs, const double* X,
+                                     const int32_t* NNarray, int64_t n, int d, int p, int m,
+                                     const double* Y, const uint32_t* rand_pairs, int64_t npairs,
+                                     const double* edges2, const double* default_start,
+                                     vec_precision prec, void* stream, double* start,
+                                     int* used_learned, float* features) {
+    if (!h || !params || !norm || !default_start || !start || !used_learned)
+        return fail(VEC_ERR_ARG, "vecchia_fields_warm_start: NULL argument");
+    vec_status s = check_fields_args("vecchia_fields_warm_start", h, nfields, locs, X, NNarray, n, d,
+                                     p, m, Y, VEC_MATERN_ISO, (int)prec);
+    if (s != VEC_OK) return s;
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(VEC_ERR_CUDA, "cannot select device %d", h->device);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int q = 4, nout = 1 + q + q * q + p, nbins = 32;
+    cudaError_t e = grow(&h->ws_feat, &h->c_ws_feat, (size_t)nfields * nbins);
+    if (e == cudaSuccess) e = grow(&h->ws_pred, &h->c_ws_pred, (size_t)nfields * 4);
+    if (e == cudaSuccess) e = grow(&h->ws_theta0, &h->c_ws_theta0, (size_t)nfields * q);
+    if (e == cudaSuccess) e = grow(&h->ws_out, &h->c_ws_out, (size_t)2 * nfields * nout);
+    if (e == cudaSuccess) e = grow(&h->ws_st, &h->c_ws_st, (size_t)4 * nfields);
+    if (e != cudaSuccess) return cuda_fail(e, "vecchia_fields_warm_start: allocating scratch");
+    float* feat = features ? features : h->ws_feat;
+    s = vecchia_fields_variogram(h, nfields, locs, NNarray, n, d, m, Y, rand_pairs, npairs, edges2,
+                                 nbins, stream, feat, nullptr, nullptr);
+    if (s != VEC_OK) return s;
+    s = vecchia_mlp_forward(h, params, norm, feat, nfields, stream, h->ws_pred);
+    if (s != VEC_OK) return s;
+    e = vg::launch_theta_from_pred(h->ws_pred, h->vg_var, nfields, h->ws_theta0, st);
+    if (e != cudaSuccess) return cuda_fail(e, "vecchia_fields_warm_start: predicted parameters");
+    BatchPlan B;
+    s = prepare_fields(h, h->bs, nfields, n, m, d, p, VEC_MATERN_ISO, (int)prec, st, &B);
+    if (s != VEC_OK) return s;
+    double* out0 = h->ws_out;
+    double* out1 = h->ws_out + (size_t)nfields * nout;
+    long long* st0 = h->ws_st;
+    long long* st1 = h->ws_st + 2 * (size_t)nfields;
+    s = enqueue_batch(h->bs, B, locs, Y, X, NNarray, d, p, h->ws_theta0, VEC_MATERN_ISO, (int)prec,
+                      st, out0, st0, nullptr);
+    if (s == VEC_OK)
+        s = enqueue_batch(h->bs, B, locs, Y, X, NNarray, d, p, default_start, VEC_MATERN_ISO,
+                          (int)prec, st, out1, st1, nullptr);
+    if (s != VEC_OK) return s;
+    e = vg::launch_choose_start(h->ws_theta0, default_start, out0, st0, out1, st1, nfields, q, nout,
+                                start, used_learned, st);
+    if (e != cudaSuccess) return cuda_fail(e, "vecchia_fields_warm_start: choosing starts");
     return VEC_OK;
 }
 

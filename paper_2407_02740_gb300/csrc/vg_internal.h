@@ -46,6 +46,23 @@ cudaError_t launch_vario(const double* locs, int d, const int32_t* NN, int n, in
 cudaError_t launch_vario_finish(const double* psum, const long long* pcnt, int slices, int nbins,
                                 const double* var, int nfields, float* feat, double* bin_sum,
                                 long long* bin_count, cudaStream_t st);
+size_t mlp_smem_bytes();
+int mlp_nparams();
+int mlp_block_samples();
+cudaError_t launch_mlp_fwdbwd(const float* P, const float* norm, const float* X, const float* T,
+                              const int* index, int B, int mode, float* out, float* gpart,
+                              float* lpart, cudaStream_t st);
+cudaError_t launch_mlp_update(const float* gpart, const float* lpart, int nblk, float* P, float* m,
+                              float* v, int step, float lr, float beta1, float beta2, float eps,
+                              float* grad, float* loss, cudaStream_t st);
+cudaError_t launch_col_moments(const float* X, int rows, int cols, float* mean, float* sd,
+                               cudaStream_t st);
+cudaError_t launch_theta_from_pred(const float* pred, const double* var, int nfields, double* theta,
+                                   cudaStream_t st);
+cudaError_t launch_choose_start(const double* theta0, const double* dflt, const double* out0,
+                                const long long* st0, const double* out1, const long long* st1,
+                                int nfields, int q, int nout, double* start, int* used,
+                                cudaStream_t st);
 cudaError_t launch_sim_recur(const double* factor, const int32_t* NN, int n, int m, int nfields,
                             const double* z, double* y, cudaStream_t st);
 cudaError_t launch_batch_status(const int* status_b, const long long* bad_b, int nbatch,

@@ -1,0 +1,71 @@
+"""What the learned start gains: a network trained (by the library's kernels) on fields
+that the plain method simulated and fitted starts Fisher scoring closer to the optimum on
+held-out fields, so the fits take fewer passes and reach the same optimum as the fits from
+the default start; the fallback keeps the default where the prediction is worse."""
+import numpy as np
+import pytest
+
+import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2407_02740_gb300 as vg  # noqa: E402
+from paper_2407_02740_gb300 import warmstart as ws  # noqa: E402
+
+
+def _geometry(n, m, seed):
+    L = np.random.default_rng(seed).uniform(size=(n, 2))
+    L = L[workloads.maxmin_order(L)]
+    return ws.make_geometry(L, workloads.ordered_nn(L, m), seed=seed)
+
+
+@pytest.fixture(scope="module")
+def trained():
+    g = _geometry(1024, 20, 11)
+    X, T, stats = ws.build_training_set(g, 3000, seed=12, chunk=1500, log=None)
+    assert stats["converged"] >= 0.8 * stats["fields"]
+    P, norm, losses = ws.train(X, T, epochs=40, batch=128, lr=2e-3, log=None)
+    return P, norm, losses, X, T
+
+
+def test_training_reduces_the_loss(trained):
+    P, norm, losses, X, T = trained
+    assert losses[-1] < 0.5 * losses[0]
+    # the fit of the training targets: predictions explain most of their variance
+    pred = vg.vecchia_mlp_forward(P, norm, X)
+    resid = ((pred - T) ** 2).mean(dim=0)
+    assert torch.all(resid < 0.6 * T.var(dim=0, unbiased=False))
+
+
+def test_learned_start_takes_fewer_passes_to_the_same_optimum(trained):
+    P, norm, _, _, _ = trained
+    g = _geometry(4096, 20, 13)
+    res = ws.evaluate(g, P, norm, nfields=48, seed=14, log=print)
+    assert res["both_converged"] >= 0.7 * 48
+    assert res["max_loglik_diff"] <= 1e-6
+    assert res["learned"]["mean_passes"] < res["default"]["mean_passes"]
+    assert res["learned"]["fallback_rate"] < 0.5
+
+
+def test_fallback_keeps_the_default_where_the_prediction_is_worse(trained):
+    P, norm, _, _, _ = trained
+    g = _geometry(1500, 20, 15)
+    Y, _ = ws.simulate_fields(g, ws.sample_priors(np.random.default_rng(16), 6), 17)
+    d0 = ws.default_start(Y)
+    # a network whose output layer predicts an absurd range (rho = e^30) loses to the default
+    bad = P.clone()
+    bad[-4:] = 0.0
+    bad[-4 - 512:-4] = 0.0
+    badnorm = norm.clone()
+    badnorm[64:68] = torch.tensor([0.0, 30.0, 0.0, 0.0], device=norm.device)
+    start, used, feats = vg.vecchia_fields_warm_start(bad, badnorm, g.locs, g.X, g.NN, Y,
+                                                      g.rand_pairs, g.edges2, d0)
+    assert torch.all(used == 0) and torch.equal(start, d0)
+    start, used, feats = vg.vecchia_fields_warm_start(P, norm, g.locs, g.X, g.NN, Y, g.rand_pairs,
+                                                      g.edges2, d0)
+    ref = vg.vecchia_fields_variogram(g.locs, g.NN, Y, g.rand_pairs, g.edges2)
+    assert torch.equal(feats, ref)
+    th = ws.predict_theta(P, norm, feats, Y)
+    keep = used.bool()
+    assert torch.allclose(start[keep], th[keep], rtol=1e-6)
