@@ -17,7 +17,9 @@ Reported beside the device-timed value:
   * cpu_baseline -- the FP64 CPU oracle on the host cores, on a bounded prefix sample.
   * batched    -- 256 independent fields (n from 1000 to 50000, m in {10, 20, 40}): the
                   batched pass as one CUDA-graph replay vs 256 per-dataset calls, and
-                  batched Fisher-scoring fits vs 256 sequential device fits.
+                  batched Fisher-scoring fits vs 256 sequential device fits;
+  * warm_start -- fits of held-out fields (n = 200000) from the default start and from
+                  the learned start.
 ``--impl reference`` times the CPU oracle itself as the reference arm.
 Multi-GPU runs (torchrun) are independent replicas: each rank evaluates its own copy.
 """
@@ -156,6 +158,21 @@ def cpu_oracle_rate(w, target_s: float = 12.0, nthreads: int = 0):
     return ns / dt, ns, dt, cores
 
 
+def tuned_table_placement(handle, m: int, prec: int, batched: bool = False):
+    """The Matern table placement ("shared" / "global") the handle's autotuning record chose
+    for (m, precision), read from its saved records."""
+    import tempfile
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "tune.json")
+        handle.autotune_save(path)
+        recs = json.load(open(path))
+    want = prec + (2 if batched else 0)
+    for r in recs:
+        if r["m"] == m and r["prec"] == want:
+            return {1: "shared", 0: "global"}.get(r.get("tab", -1), "planner")
+    return None
+
+
 def run_batched(vg, torch, dev, stream, steps: int, warmup: int, flush, local: int) -> dict:
     """The 256-dataset batch (Matern fields, n log-uniform in [1000, 50000], m in
     {10, 20, 40}, per-dataset parameters, X = 1): the batched pass as one CUDA-graph
@@ -176,6 +193,7 @@ def run_batched(vg, torch, dev, stream, steps: int, warmup: int, flush, local: i
     hb = vg.Handle(local)
     tune = vg.vecchia_batch_autotune(locs, y, X, NN, bw.offsets, bw.m, th, bw.covfun, reps=2,
                                      stream=stream, handle=hb)
+    btab = tuned_table_placement(hb, int(max(bw.m)), 0, batched=True)
 
     def graph_of(plan, cp, out, st):
         side = torch.cuda.Stream(dev)
@@ -285,6 +303,7 @@ def run_batched(vg, torch, dev, stream, steps: int, warmup: int, flush, local: i
         "ms_per_step": b_ms, "launch": "one CUDA-graph replay of a batch plan (4 kernels)",
         "gpu_launches_per_step": 4,
         "mapping": {"lanes_per_observation": tune["lanes"], "threads_per_block": tune["threads"],
+                    "matern_table": btab,
                     "source": "vecchia_batch_autotune"},
         "roofline": {"bound": "alu", "unit": "GFLOP/s", "peak": FP64_PEAK_GFLOPS,
                      "achieved": flop / (b_ms * 1e-3) / 1e9,
@@ -313,6 +332,23 @@ def run_batched(vg, torch, dev, stream, steps: int, warmup: int, flush, local: i
                                     "max(|loglik|, n) (a field's loglik can be near 0)",
                 "sequential_iters_equal": bool(np.array_equal(seq_iters, bfit["iters"]))},
     }
+
+
+def run_warm_start(torch, dev, local: int, nfields: int = 64) -> dict:
+    """The learned start (the network shipped with the package, trained by its own kernels on
+    50 000 simulated-and-fitted fields of n = 4096) on held-out fields of n = 200 000,
+    m = 30: Fisher-scoring passes and wall time from the default start and from the
+    learned start with its fallback rule, and the agreement of the optima."""
+    import workloads
+    from paper_2407_02740_gb300 import warmstart as ws
+    L = np.random.default_rng(1006).uniform(size=(200000, 2))
+    L = L[workloads.maxmin_order(L)]
+    geom = ws.make_geometry(L, workloads.ordered_nn(L, 30), device=dev, seed=1006)
+    params, norm = ws.load(device=dev)
+    res = ws.evaluate(geom, params, norm, nfields=nfields, seed=1007, log=None)
+    res["workload"] = ("%d held-out Matern fields at one set of n = 200000 uniform locations, "
+                       "m = 30, parameters from the training priors" % nfields)
+    return res
 
 
 def run_reference(args):
@@ -479,6 +515,7 @@ def run_ours(args):
         mfit_times.append(time.perf_counter() - t0)
 
     batched = run_batched(vg, torch, dev, stream, args.steps, args.warmup, flush, local)
+    warm = run_warm_start(torch, dev, local)
 
     if rank != 0:
         if ws > 1:
@@ -517,6 +554,7 @@ def run_ours(args):
         "gpu_launches": args.steps * int(vg.lib().vecchia_kernels_per_pass(w.covfun)),
         "clocks": clocks,
         "mapping": {"lanes_per_observation": tune["lanes"], "threads_per_block": tune["threads"],
+                    "matern_table": tuned_table_placement(h, w.m, 0),
                     "source": "vecchia_autotune"},
         "fit": {"precision": "f64", "tol": 1e-4, "start": [float(v) for v in w.theta_start],
                 "seconds_first_call": fit_times[0], "seconds": fit_times[1],
@@ -528,7 +566,8 @@ def run_ours(args):
                   "ms_per_step": sum(mixed_ms) / args.steps,
                   "kernel_ms": statistics.mean(mixed_pass_ms),
                   "mapping": {"lanes_per_observation": tune_m["lanes"],
-                              "threads_per_block": tune_m["threads"]},
+                              "threads_per_block": tune_m["threads"],
+                              "matern_table": tuned_table_placement(hm, w.m, 1)},
                   "vs_fp64_pass": {
                       "loglik_rel": abs(mixed_res["loglik"] - res["loglik"]) / abs(res["loglik"]),
                       "grad_rel": float(np.linalg.norm(mixed_res["grad"] - res["grad"])) / gscale,
@@ -541,6 +580,7 @@ def run_ours(args):
                           "loglik_rel_to_f64_fit": abs(mfit["loglik"] - fit["loglik"]) / abs(fit["loglik"]),
                           "theta": [float(v) for v in mfit["theta"]]}},
         "batched": batched,
+        "warm_start": warm,
     }
     print(json.dumps(line))
     if ws > 1:

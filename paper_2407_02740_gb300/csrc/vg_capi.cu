@@ -71,6 +71,7 @@ constexpr int kFitKey = 24;  // words of the single-fit graph cache key
 struct TuneEntry {
     int cov, m, d, p, prec, log2n, lanes, threads;
     float ms;
+    int tab;  // Matern table placement of the mapping: 1 shared memory, 0 global, -1 planner's
 };
 
 // Device buffers of a batched pass: the work list (tiles of observations), per-dataset
@@ -98,6 +99,7 @@ struct vec_handle_s {
     int nsm = 0;
     int lanes = 0;    // 0 = automatic
     int threads = 0;  // 0 = automatic
+    int tab_mode = -1;  // Matern table placement while autotuning (-1 = planner's choice)
     cudaStream_t stream = nullptr;
     // tracing
     int timing = 0;
@@ -316,16 +318,18 @@ int ilog2(int64_t n) {
 
 vec_status prepare_pass(vec_handle h, int cov, int m, int d, int p, vg::PassPlan* plan,
                         int64_t n = 0, int prec = 0) {
-    int L = h->lanes, thr = h->threads;
+    int L = h->lanes, thr = h->threads, tab = -1;
     if (L == 0 && thr == 0 && n > 0) {
         const int lg = ilog2(n);
         for (const TuneEntry& t : h->tune)
             if (t.cov == cov && t.m == m && t.d == d && t.p == p && t.prec == prec && t.log2n == lg) {
                 L = t.lanes;
                 thr = t.threads;
+                tab = t.tab;
             }
     }
-    int pr = vg::plan_pass(cov, m, d, p, h->nsm, L, thr, plan, prec);
+    if (h->tab_mode >= 0) tab = h->tab_mode;
+    int pr = vg::plan_pass(cov, m, d, p, h->nsm, L, thr, plan, prec, false, tab);
     if (pr == -1 && (L != h->lanes || thr != h->threads))  // a stale record: plan afresh
         pr = vg::plan_pass(cov, m, d, p, h->nsm, h->lanes, h->threads, plan, prec);
     if (pr == -1) return fail(VEC_ERR_UNSUPPORTED, "no kernel mapping fits m = %d, p = %d", m, p);
@@ -633,14 +637,20 @@ vec_status vecchia_autotune(vec_handle h, const double* locs, const double* y, c
     int bestL = 0, bestT = 0;
     float best = 1e30f;
     static const int thr_list[] = {256, 128, 64};
+    int bestTab = -1;
+    const int ntab = (cov == vg::COV_MATERN) ? 2 : 1;
     for (int ti = 0; ti < 3 && e == cudaSuccess; ++ti) {
-        for (int L = 1; L <= 32 && e == cudaSuccess; L *= 2) {
+        for (int L = 1; L <= 32 && e == cudaSuccess; L *= 2)
+        for (int tb = 0; tb < ntab && e == cudaSuccess; ++tb) {
+            const int tab = (cov == vg::COV_MATERN) ? 1 - tb : -1;  // shared memory first
             if (L > thr_list[ti]) continue;
             vg::PassPlan plan;
-            if (vg::plan_pass(cov, m, d, p, h->nsm, L, thr_list[ti], &plan, (int)prec) != 0) continue;
+            if (vg::plan_pass(cov, m, d, p, h->nsm, L, thr_list[ti], &plan, (int)prec, false, tab) != 0)
+                continue;
             if (plan.L != L || plan.threads != thr_list[ti]) continue;
             h->lanes = L;
             h->threads = thr_list[ti];
+            h->tab_mode = tab;
             s = enqueue_pass(h, locs, y, X, NNarray, n, d, p, m, covparms, covfun, st, out, dst,
                              (int)prec);
             if (s != VEC_OK) break;
@@ -657,12 +667,13 @@ vec_status vecchia_autotune(vec_handle h, const double* locs, const double* y, c
                 if (ms < tmin) tmin = ms;
             }
             if (s != VEC_OK) break;
-            if (tmin < best) { best = tmin; bestL = L; bestT = thr_list[ti]; }
+            if (tmin < best) { best = tmin; bestL = L; bestT = thr_list[ti]; bestTab = tab; }
         }
         if (s != VEC_OK) break;
     }
     h->lanes = saved_L;
     h->threads = saved_T;
+    h->tab_mode = -1;
     h->timing = saved_timing;
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
@@ -671,7 +682,7 @@ vec_status vecchia_autotune(vec_handle h, const double* locs, const double* y, c
     if (s != VEC_OK) return s;
     if (e != cudaSuccess) return cuda_fail(e, "vecchia_autotune");
     if (bestL == 0) return fail(VEC_ERR_UNSUPPORTED, "vecchia_autotune: no mapping fits");
-    TuneEntry t = {cov, m, d, p, (int)prec, ilog2(n), bestL, bestT, best};
+    TuneEntry t = {cov, m, d, p, (int)prec, ilog2(n), bestL, bestT, best, bestTab};
     bool replaced = false;
     for (TuneEntry& u : h->tune)
         if (u.cov == t.cov && u.m == t.m && u.d == t.d && u.p == t.p && u.prec == t.prec &&
@@ -691,8 +702,9 @@ vec_status vecchia_autotune_save(vec_handle h, const char* path) {
     for (size_t i = 0; i < h->tune.size(); ++i) {
         const TuneEntry& t = h->tune[i];
         std::fprintf(f, "  {\"covfun\": %d, \"m\": %d, \"d\": %d, \"p\": %d, \"prec\": %d, "
-                        "\"log2n\": %d, \"lanes\": %d, \"threads\": %d, \"ms\": %.6f}%s\n",
-                     t.cov, t.m, t.d, t.p, t.prec, t.log2n, t.lanes, t.threads, t.ms,
+                        "\"log2n\": %d, \"lanes\": %d, \"threads\": %d, \"ms\": %.6f, "
+                        "\"tab\": %d}%s\n",
+                     t.cov, t.m, t.d, t.p, t.prec, t.log2n, t.lanes, t.threads, t.ms, t.tab,
                      i + 1 < h->tune.size() ? "," : "");
     }
     std::fprintf(f, "]\n");
@@ -729,8 +741,10 @@ vec_status vecchia_autotune_load(vec_handle h, const char* path) {
         bool ok = true;
         for (int i = 0; i < 9 && ok; ++i) ok = get(keys[i], &v[i]);
         if (!ok) return fail(VEC_ERR_ARG, "vecchia_autotune_load: malformed record in %s", path);
+        double tabv = -1.0;  // optional key
+        if (!get("tab", &tabv)) tabv = -1.0;
         TuneEntry t = {(int)v[0], (int)v[1], (int)v[2], (int)v[3], (int)v[4], (int)v[5], (int)v[6],
-                       (int)v[7], (float)v[8]};
+                       (int)v[7], (float)v[8], (int)tabv};
         bool replaced = false;
         for (TuneEntry& u : h->tune)
             if (u.cov == t.cov && u.m == t.m && u.d == t.d && u.p == t.p && u.prec == t.prec &&
@@ -775,14 +789,15 @@ vec_status prepare_batch_desc(vec_handle h, BatchScratch& S, int d, int p, vec_c
     }
     const int cov = (int)covfun;
     // mapping: forced, else autotuned for (cov, mmax, d, p, prec, total n), else planned
-    int L = h->lanes, thr = h->threads;
+    int L = h->lanes, thr = h->threads, tab = -1;
     if (L == 0 && thr == 0) {
         const int lg = ilog2(B->ntot);
         for (const TuneEntry& t : h->tune)
             if (t.cov == cov && t.m == B->mmax && t.d == d && t.p == p && t.prec == prec + 2 &&
-                t.log2n == lg) { L = t.lanes; thr = t.threads; }
+                t.log2n == lg) { L = t.lanes; thr = t.threads; tab = t.tab; }
     }
-    int pr = vg::plan_pass(cov, B->mmax, d, p, h->nsm, L, thr, &B->plan, prec, true);
+    if (h->tab_mode >= 0) tab = h->tab_mode;
+    int pr = vg::plan_pass(cov, B->mmax, d, p, h->nsm, L, thr, &B->plan, prec, true, tab);
     if (pr == -1) pr = vg::plan_pass(cov, B->mmax, d, p, h->nsm, h->lanes, h->threads, &B->plan, prec, true);
     if (pr == -1) return fail(VEC_ERR_UNSUPPORTED, "no kernel mapping fits m = %d, p = %d", B->mmax, p);
     if (pr != 0) return cuda_fail(cudaGetLastError(), "planning the batched pass");
@@ -1179,14 +1194,20 @@ vec_status vecchia_batch_autotune(vec_handle h, int nbatch, const double* locs, 
     float best = 1e30f;
     for (int b = 0; b < nbatch; ++b) mmax = m[b] > mmax ? m[b] : mmax;
     static const int thr_list[] = {256, 128, 64};
+    int bestTab = -1;
+    const int ntab = (cov == vg::COV_MATERN) ? 2 : 1;
     for (int ti = 0; ti < 3 && e == cudaSuccess && s == VEC_OK; ++ti) {
-        for (int L = 1; L <= 32 && e == cudaSuccess; L *= 2) {
+        for (int L = 1; L <= 32 && e == cudaSuccess; L *= 2)
+        for (int tb = 0; tb < ntab && e == cudaSuccess; ++tb) {
+            const int tab = (cov == vg::COV_MATERN) ? 1 - tb : -1;
             if (L > thr_list[ti]) continue;
             vg::PassPlan plan;
-            if (vg::plan_pass(cov, mmax, d, p, h->nsm, L, thr_list[ti], &plan, (int)prec, true) != 0) continue;
+            if (vg::plan_pass(cov, mmax, d, p, h->nsm, L, thr_list[ti], &plan, (int)prec, true, tab) != 0)
+                continue;
             if (plan.L != L || plan.threads != thr_list[ti]) continue;
             h->lanes = L;
             h->threads = thr_list[ti];
+            h->tab_mode = tab;
             BatchPlan B;
             s = prepare_batch(h, h->bs, nbatch, point_offsets, m, d, p, covfun, (int)prec, st, &B);
             if (s != VEC_OK) break;
@@ -1206,11 +1227,12 @@ vec_status vecchia_batch_autotune(vec_handle h, int nbatch, const double* locs, 
                 if (ms < tmin) tmin = ms;
             }
             if (s != VEC_OK) break;
-            if (tmin < best) { best = tmin; bestL = L; bestT = thr_list[ti]; }
+            if (tmin < best) { best = tmin; bestL = L; bestT = thr_list[ti]; bestTab = tab; }
         }
     }
     h->lanes = saved_L;
     h->threads = saved_T;
+    h->tab_mode = -1;
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     cudaFree(out);
@@ -1219,7 +1241,8 @@ vec_status vecchia_batch_autotune(vec_handle h, int nbatch, const double* locs, 
     if (e != cudaSuccess) return cuda_fail(e, "vecchia_batch_autotune");
     if (bestL == 0) return fail(VEC_ERR_UNSUPPORTED, "vecchia_batch_autotune: no mapping fits");
     // batched records are kept apart from single-dataset ones: prec + 2
-    TuneEntry t = {cov, mmax, d, p, (int)prec + 2, ilog2(point_offsets[nbatch]), bestL, bestT, best};
+    TuneEntry t = {cov, mmax, d, p, (int)prec + 2, ilog2(point_offsets[nbatch]), bestL, bestT, best,
+                   bestTab};
     bool replaced = false;
     for (TuneEntry& u : h->tune)
         if (u.cov == t.cov && u.m == t.m && u.d == t.d && u.p == t.p && u.prec == t.prec &&

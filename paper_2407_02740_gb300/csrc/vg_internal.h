@@ -25,8 +25,10 @@ struct PassPlan {
 
 // Chooses the lanes-per-observation mapping that fits shared memory (or the forced one).
 // Returns 0 on success, -1 if no mapping fits, -2 on a CUDA error.
+// force_tab: -1 = Matern table in shared memory when it fits, 1 = shared memory only,
+// 0 = global memory (read through L1).  Returns 0, -1 (no mapping fits) or -2 (CUDA error).
 int plan_pass(int cov, int m, int d, int p, int nsm, int force_L, int force_threads,
-              PassPlan* plan, int prec = 0, bool batched = false);
+              PassPlan* plan, int prec = 0, bool batched = false, int force_tab = -1);
 size_t pass_smem_bytes(int cov, int m, int d, int p, int L, int threads, bool tab_smem,
                        int prec = 0);
 const void* pass_kernel_f64(int cov, int L);

@@ -70,9 +70,11 @@ __global__ void __launch_bounds__(MT_NC * 32) k_mtab_build(const double* __restr
         }
         // u = w / hw: coefficient of w^k is mono_k / hw^k (exact power-of-two scaling);
         // w^0..w^7 stored in FP64, w^8..w^12 in FP32 (see horner_split)
+        // the covariance scales are folded in: F0 x sigma2, F1 x sigma2 / rho, F2 x sigma2
+        const double fsc = (i == 1) ? covparms[0] / covparms[1] : covparms[0];
         double* out = tab + (size_t)it * MT_PER_INT + i * MT_FSTRIDE;
         float* tail = reinterpret_cast<float*>(out + MT_NHEAD);
-        double sc = 1.0;
+        double sc = fsc;
         for (int k = 0; k < MT_NC; ++k) {
             if (k < MT_NHEAD) out[k] = mono[k] * sc;
             else tail[k - MT_NHEAD] = (float)(mono[k] * sc);
@@ -81,7 +83,7 @@ __global__ void __launch_bounds__(MT_NC * 32) k_mtab_build(const double* __restr
         tail[MT_NC - MT_NHEAD] = 0.0f;
         if (tabf) {  // FP32 copy for the mixed path
             float* of = tabf + (size_t)it * MT_PER_INT_F + i * MT_NC;
-            double sc2 = 1.0;
+            double sc2 = fsc;
             for (int k = 0; k < MT_NC; ++k) { of[k] = (float)(mono[k] * sc2); sc2 *= (2.0 * MT_J); }
         }
     }
@@ -299,13 +301,15 @@ __global__ void k_cov_pairs(const double* __restrict__ covparms, const double* _
         double s = 0.0;
         for (int k = 0; k < d; ++k) { double t = a[k] - b[k]; s = fma(t, t, s); }
         s /= th[1] * th[1];
-        const double nu = th[2], psi = dev_digamma(nu), lg = lgamma(nu);
-        double F0 = matern_F0(tab, s, nu, psi, lg), F1, F2;  // FP64 table
-        matern_F12(tab, s, nu, psi, lg, F1, F2);
-        c = s2 * F0;
-        out[0] = F0;
-        out[1] = s2 * F1 / th[1];
-        out[2] = s2 * F2;
+        const double nu = th[2], psi = dev_digamma(nu);
+        // the table holds sigma2 M, dC/drho and dC/dnu
+        const double C0 = matern_F0(tab, s, nu, psi, s2);
+        double F1, F2;
+        matern_F12(tab, s, nu, psi, s2 / th[1], s2, F1, F2);
+        c = C0;
+        out[0] = C0 / s2;
+        out[1] = F1;
+        out[2] = F2;
     } else {
         double t0 = a[0] - b[0], t1 = a[1] - b[1], t2 = a[2] - b[2];
         double us = fma(t0, t0, t1 * t1), ut = t2 * t2;
@@ -355,7 +359,7 @@ size_t pass_smem_bytes(int cov, int m, int d, int p, int L, int threads, bool ta
 }
 
 int plan_pass(int cov, int m, int d, int p, int nsm, int force_L, int force_threads,
-              PassPlan* plan, int prec, bool batched) {
+              PassPlan* plan, int prec, bool batched, int force_tab) {
     // Preference: 256 threads (two warps per SM sub-partition, so that one warp's FP64
     // dependency waits are covered by the other), then 128 (one warp per sub-partition,
     // the minimum that occupies all FP64 units), then fewer when the largest blocks do
@@ -369,9 +373,14 @@ int plan_pass(int cov, int m, int d, int p, int nsm, int force_L, int force_thre
             if (force_L > 0 && L != force_L) continue;
             if (L > thr) continue;
             if (thr == 256 && force_L <= 0 && L > 16) continue;
-            bool t = (cov == COV_MATERN);
+            // Matern table in shared memory when it fits (or as forced: force_tab 1 = shared
+            // memory only, 0 = global memory, read through L1)
+            bool t = (cov == COV_MATERN) && force_tab != 0;
             size_t b = pass_smem_bytes(cov, m, d, p, L, thr, t, prec);
-            if (b > budget && t) { t = false; b = pass_smem_bytes(cov, m, d, p, L, thr, t, prec); }
+            if (b > budget && t && force_tab < 0) {
+                t = false;
+                b = pass_smem_bytes(cov, m, d, p, L, thr, t, prec);
+            }
             if (b <= budget) { chosen = L; tab = t; threads = thr; break; }
         }
     }

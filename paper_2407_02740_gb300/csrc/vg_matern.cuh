@@ -11,10 +11,11 @@
 //     the nodes shared by the 32 lanes of a warp.  The integrands are even and entire in t
 //     and decay double-exponentially, so the trapezoid sum converges geometrically in 1/h.
 //     Scales are kept in log space.
-//  2. A per-pass coefficient table.  Within one pass nu is fixed, so the three functions
-//        F0(s) = M_nu(sqrt s),
-//        F1(s) = -x dM/dx = 2^(1-nu)/Gamma(nu) x^(nu+1) K_(nu-1)(x),  (rho dM/drho)
-//        F2(s) = dM/dnu,
+//  2. A per-pass coefficient table.  Within one pass theta is fixed, so the three functions
+//        F0(s) = sigma2 M_nu(sqrt s),
+//        F1(s) = (sigma2 / rho) (-x dM/dx),  -x dM/dx = 2^(1-nu)/Gamma(nu) x^(nu+1) K_(nu-1)(x)
+//                = rho dM/drho, so F1 = dC/drho,
+//        F2(s) = sigma2 dM/dnu = dC/dnu,
 //     of s = x^2 = |h|^2 / rho^2 are tabulated once per pass as polynomials of degree D on
 //     dyadic sub-intervals: octave [2^e, 2^(e+1)) split into J equal parts.  The octave and
 //     part come from the exponent and leading mantissa bits of s (integer work), the local
@@ -101,7 +102,7 @@ static __device__ __noinline__ void matern_small(double nu, double s, double psi
 // -1 when s < 2^E0 (direct formula, includes s == 0), or -2 when s >= 2^E1 (zero).
 // The interval centre 1 + (2j+1)/(2J) is built from bits, so w = mantissa - centre is
 // one exact FP64 subtraction (Sterbenz).
-__device__ __forceinline__ int mtab_locate(double s, double& w) {
+__device__ __forceinline__ int mtab_locate(double s, double& w, float& wf) {
     const unsigned long long bits = (unsigned long long)__double_as_longlong(s);
     const int e = (int)((bits >> 52) & 0x7ffull) - 1023;
     if (e < MT_E0) return -1;
@@ -112,14 +113,18 @@ __device__ __forceinline__ int mtab_locate(double s, double& w) {
     const double cen = __longlong_as_double(
         (long long)(0x3ff0000000000000ull | ((2ull * j + 1ull) << (52 - MT_LOGJ - 1))));
     w = mant - cen;
+    // the same difference in FP32 for the polynomial tail, without an FP64 conversion:
+    // the mantissa truncated to 23 bits (relative error < 2^-23, harmless in the tail)
+    const float mantf = __uint_as_float(0x3f800000u | (unsigned)((bits >> 29) & 0x7fffffull));
+    const float cenf = __uint_as_float(0x3f800000u | (unsigned)((2ull * j + 1ull) << (23 - MT_LOGJ - 1)));
+    wf = mantf - cenf;
     return (e - MT_E0) * MT_J + (int)j;
 }
 
-// Degree-12 polynomial in w: the tail w^8..w^12 (coefficients <= 1e-8 in size on every
-// interval, so FP32 rounding there is below 1e-15 absolute) in FP32, the head in FP64.
-__device__ __forceinline__ double horner_split(const double* c, double w) {
+// Degree-12 polynomial in w: the tail w^8..w^12 (summing to below ~1e-9 on every interval,
+// so FP32 rounding there is below 1e-15 absolute) in FP32, the head in FP64.
+__device__ __forceinline__ double horner_split(const double* c, double w, float wf) {
     const float* t = reinterpret_cast<const float*>(c + MT_NHEAD);
-    const float wf = (float)w;
     float pt = t[4];
     pt = fmaf(pt, wf, t[3]);
     pt = fmaf(pt, wf, t[2]);
@@ -131,33 +136,39 @@ __device__ __forceinline__ double horner_split(const double* c, double w) {
     return p;
 }
 
-// F0 (and optionally F1, F2) at s = x^2 from the table, with the direct formula below the
-// table and zero above it.
+// The table holds the covariance and its derivatives, not M itself: F0 = sigma2 M,
+// F1 = sigma2 dM/drho = sigma2 (rho dM/drho) / rho, F2 = sigma2 dM/dnu (the builder folds
+// the scales in).  Below the table the expansion's values are scaled here (sc0 = sigma2,
+// sc1 = sigma2 / rho, sc2 = sigma2); above it all three are 0.
 __device__ __forceinline__ double matern_F0(const double* tab, double s, double nu, double psi,
-                                            double lg) {
+                                            double sc0) {
     double w;
-    int it = mtab_locate(s, w);
-    if (it >= 0) return horner_split(tab + it * MT_PER_INT, w);
+    float wf;
+    int it = mtab_locate(s, w, wf);
+    if (it >= 0) return horner_split(tab + it * MT_PER_INT, w, wf);
     if (it == -2) return 0.0;
-    if (!(s > 0.0)) return 1.0;
+    if (!(s > 0.0)) return sc0;
     double f0, f1, f2;
     matern_small(nu, s, psi, f0, f1, f2);
-    return f0;
+    return sc0 * f0;
 }
 __device__ __forceinline__ void matern_F12(const double* tab, double s, double nu, double psi,
-                                           double lg, double& F1, double& F2) {
+                                           double sc1, double sc2, double& F1, double& F2) {
     double w;
-    int it = mtab_locate(s, w);
+    float wf;
+    int it = mtab_locate(s, w, wf);
     if (it >= 0) {
         const double* cf = tab + it * MT_PER_INT;
-        F1 = horner_split(cf + MT_FSTRIDE, w);
-        F2 = horner_split(cf + 2 * MT_FSTRIDE, w);
+        F1 = horner_split(cf + MT_FSTRIDE, w, wf);
+        F2 = horner_split(cf + 2 * MT_FSTRIDE, w, wf);
     } else if (it == -2 || !(s > 0.0)) {
         F1 = 0.0;
         F2 = 0.0;
     } else {
         double f0;
         matern_small(nu, s, psi, f0, F1, F2);
+        F1 *= sc1;
+        F2 *= sc2;
     }
 }
 
@@ -221,18 +232,18 @@ __device__ __forceinline__ float horner13f(const float* c, float w) {
     return p;
 }
 __device__ __forceinline__ float matern_F0f(const float* tab, float s, double nu, double psi,
-                                            double lg) {
+                                            double sc0) {
     float w;
     int it = mtab_locate_f(s, w);
     if (it >= 0) return horner13f(tab + it * MT_PER_INT_F, w);
     if (it == -2) return 0.0f;
-    if (!(s > 0.0f)) return 1.0f;
+    if (!(s > 0.0f)) return (float)sc0;
     double f0, f1, f2;
     matern_small(nu, (double)s, psi, f0, f1, f2);
-    return (float)f0;
+    return (float)(sc0 * f0);
 }
 __device__ __forceinline__ void matern_F12f(const float* tab, float s, double nu, double psi,
-                                            double lg, float& F1, float& F2) {
+                                            double sc1, double sc2, float& F1, float& F2) {
     float w;
     int it = mtab_locate_f(s, w);
     if (it >= 0) {
@@ -245,8 +256,8 @@ __device__ __forceinline__ void matern_F12f(const float* tab, float s, double nu
     } else {
         double f0, f1, f2;
         matern_small(nu, (double)s, psi, f0, f1, f2);
-        F1 = (float)f1;
-        F2 = (float)f2;
+        F1 = (float)(sc1 * f1);
+        F2 = (float)(sc2 * f2);
     }
 }
 

@@ -69,23 +69,25 @@ struct MaternT;
 template <>
 struct MaternT<double> {
     using Tab = double;
-    static __device__ __forceinline__ double F0(const double* tab, double s, double nu, double psi, double lg) {
-        return matern_F0(tab, s, nu, psi, lg);
+    static __device__ __forceinline__ double F0(const double* tab, double s, double nu, double psi,
+                                                double sc0) {
+        return matern_F0(tab, s, nu, psi, sc0);
     }
     static __device__ __forceinline__ void F12(const double* tab, double s, double nu, double psi,
-                                               double lg, double& F1, double& F2) {
-        matern_F12(tab, s, nu, psi, lg, F1, F2);
+                                               double sc1, double sc2, double& F1, double& F2) {
+        matern_F12(tab, s, nu, psi, sc1, sc2, F1, F2);
     }
 };
 template <>
 struct MaternT<float> {
     using Tab = float;
-    static __device__ __forceinline__ float F0(const float* tab, float s, double nu, double psi, double lg) {
-        return matern_F0f(tab, s, nu, psi, lg);
+    static __device__ __forceinline__ float F0(const float* tab, float s, double nu, double psi,
+                                               double sc0) {
+        return matern_F0f(tab, s, nu, psi, sc0);
     }
     static __device__ __forceinline__ void F12(const float* tab, float s, double nu, double psi,
-                                               double lg, float& F1, float& F2) {
-        matern_F12f(tab, s, nu, psi, lg, F1, F2);
+                                               double sc1, double sc2, float& F1, float& F2) {
+        matern_F12f(tab, s, nu, psi, sc1, sc2, F1, F2);
     }
 };
 
@@ -163,7 +165,7 @@ struct PassEnv {
     int* status;
     long long* bad;
     // theta-derived
-    double nu, m_psi, m_lg, inv_r1, inv_r2;
+    double nu, m_psi, sig2, inv_r1, inv_r2;
     T sig2T, diagC, inv_r1T, inv_r2T;
     const Tab* tab;
     // record formulas and per-lane sums
@@ -191,7 +193,7 @@ __device__ __forceinline__ void vecchia_point(const PassEnv<T, Tab>& E, long lon
     double* V = E.V;
     int* idx = E.idx;
     const T sig2T = E.sig2T, diagC = E.diagC, inv_r1T = E.inv_r1T, inv_r2T = E.inv_r2T;
-    const double inv_r1 = E.inv_r1, inv_r2 = E.inv_r2, m_psi = E.m_psi, m_lg = E.m_lg;
+    const double inv_r1 = E.inv_r1, inv_r2 = E.inv_r2, m_psi = E.m_psi;
     const Tab* tab = E.tab;
     const uint32_t* sidx = E.sidx;
     double* acc = E.acc;
@@ -263,7 +265,7 @@ __device__ __forceinline__ void vecchia_point(const PassEnv<T, Tab>& E, long lon
                 T t = loc[k * Kmax + a] - loc[k * Kmax + c];
                 s = N::fma_(t, t, s);
             }
-            C = sig2T * MT::F0(tab, s, E.nu, m_psi, m_lg);
+            C = MT::F0(tab, s, E.nu, m_psi, E.sig2);   // the table holds sigma2 M
         }
         A[e] = C;
     }
@@ -354,9 +356,9 @@ __device__ __forceinline__ void vecchia_point(const PassEnv<T, Tab>& E, long lon
                         s = N::fma_(t, t, s);
                     }
                     T F1, F2;
-                    MT::F12(tab, s, E.nu, m_psi, m_lg, F1, F2);
-                    dv[0] = sig2T * F1 * inv_r1T;
-                    if (NG > 1) dv[NG - 1] = sig2T * F2;
+                    MT::F12(tab, s, E.nu, m_psi, E.sig2 * inv_r1, E.sig2, F1, F2);
+                    dv[0] = F1;                      // dC/drho and dC/dnu from the table
+                    if (NG > 1) dv[NG - 1] = F2;
                 }
                 const T ba = bv[a], bc = bv[c];
 #pragma unroll
@@ -560,8 +562,8 @@ __global__ void __launch_bounds__(256) k_pass(PassArgs args) {
     const double inv_r1 = 1.0 / th[1];
     const double inv_r2 = (COV == COV_ST) ? 1.0 / th[2] : 1.0;
     const T inv_r1T = (T)inv_r1, inv_r2T = (T)inv_r2;
-    double m_psi = 0.0, m_lg = 0.0;
-    if (COV == COV_MATERN && ok) { m_psi = dev_digamma(th[2]); m_lg = lgamma(th[2]); }
+    double m_psi = 0.0;
+    if (COV == COV_MATERN && ok) m_psi = dev_digamma(th[2]);
     __syncthreads();
 
     const long long n = args.n;
@@ -572,7 +574,7 @@ __global__ void __launch_bounds__(256) k_pass(PassArgs args) {
     E.V = V; E.idx = idx; E.Kmax = Kmax;
     E.locs = args.locs; E.y = args.y; E.X = args.X; E.NN = args.NN;
     E.d = d; E.p = p; E.m = m; E.status = args.status; E.bad = args.bad;
-    E.nu = (COV == COV_MATERN) ? th[2] : 0.0; E.m_psi = m_psi; E.m_lg = m_lg;
+    E.nu = (COV == COV_MATERN) ? th[2] : 0.0; E.m_psi = m_psi; E.sig2 = sig2;
     E.inv_r1 = inv_r1; E.inv_r2 = inv_r2;
     E.sig2T = sig2T; E.diagC = diagC; E.inv_r1T = inv_r1T; E.inv_r2T = inv_r2T;
     E.tab = tab; E.sidx = sidx; E.acc = acc; E.nstat = args.nstat;
@@ -689,7 +691,7 @@ __global__ void __launch_bounds__(256) k_pass_batch(BatchArgs bargs) {
             E.inv_r2T = (T)E.inv_r2;
             E.nu = (COV == COV_MATERN) ? th[2] : 0.0;
             E.m_psi = (COV == COV_MATERN && ok) ? dev_digamma(th[2]) : 0.0;
-            E.m_lg = (COV == COV_MATERN && ok) ? lgamma(th[2]) : 0.0;
+            E.sig2 = sig2;
             const DatasetDesc D = bargs.desc[b];
             E.locs = args.locs + D.loc * d;
             E.y = args.y + D.y;

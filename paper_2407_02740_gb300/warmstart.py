@@ -15,7 +15,8 @@ ordered-neighbour array supplied by the caller), X = 1 (beta = 0):
   * simulation: the sequential Vecchia draw of the NNarray (vecchia_fields_simulate);
   * targets: the plain method's optimum, a Fisher-scoring fit from the default start
     (var y, 0.1, 1, 0.1) (vecchia_fields_fit), as (log(sigma2 / var y), log rho, log nu,
-    log tau2); fields whose fit does not converge are left out of the training set;
+    log tau2) clamped to TARGET_RANGE; fields whose fit does not converge are left out of
+    the training set;
   * features: 32 log-spaced lag bins on [0.005, 0.5] of the empirical semivariogram over
     the NNarray pairs and 2^20 random pairs (vecchia_fields_variogram);
   * network and training: 32 -> 128 -> 128 -> 4 (vecchia_mlp_*), Adam on the mean squared
@@ -25,6 +26,7 @@ ordered-neighbour array supplied by the caller), X = 1 (beta = 0):
 """
 from __future__ import annotations
 
+import os
 import time
 from dataclasses import dataclass
 
@@ -98,12 +100,20 @@ def simulate_fields(geom: Geometry, theta: np.ndarray, seed: int):
     return Y, st
 
 
+# Training targets are clamped to these ranges of (sigma2 / var y, rho, nu, tau2): a fit can
+# converge with the nugget driven towards 0 (the likelihood is flat there), and such targets
+# (log tau2 of -50 and below) would dominate the squared-error loss.
+TARGET_RANGE = ((1e-2, 1e2), (1e-4, 1e1), (0.05, 20.0), (1e-6, 1e1))
+
+
 def targets_from_fit(theta_hat, Y):
-    """(log(sigma2 / var y), log rho, log nu, log tau2), float32."""
+    """(log(sigma2 / var y), log rho, log nu, log tau2), clamped to TARGET_RANGE, float32."""
     import torch
     var = Y.var(dim=1, unbiased=False)
     t = torch.log(theta_hat.clone())
     t[:, 0] -= torch.log(var)
+    for j, (lo, hi) in enumerate(TARGET_RANGE):
+        t[:, j] = t[:, j].clamp(float(np.log(lo)), float(np.log(hi)))
     return t.to(torch.float32)
 
 
@@ -193,7 +203,14 @@ def save(path: str, params, norm, meta: dict | None = None):
              meta=np.array(repr(meta or {})))
 
 
-def load(path: str, device="cuda:0"):
+DATA = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data")
+TRAINED = "warmstart_n4096_m30.npz"   # 50 000 fields of n = 4096, m = 30 (see its .json)
+
+
+def load(path: str = None, device="cuda:0"):
+    """Loads a saved network (default: the one trained by this module's command line on
+    50 000 fields of n = 4096, m = 30, shipped in data/)."""
+    path = path or os.path.join(DATA, TRAINED)
     import torch
     z = np.load(path)
     return (torch.as_tensor(z["params"], dtype=torch.float32, device=device),
@@ -213,10 +230,11 @@ def predict_theta(params, norm, feats, Y):
 
 
 def evaluate(geom: Geometry, params, norm, nfields: int, seed: int = 3, prec: str = "fp64",
-             log=print) -> dict:
-    """Held-out fields: fits from the default start and from the learned start (with its
-    fallback rule), each timed as one call (the learned start's call includes features,
-    network and its two passes); both must reach the same optimum."""
+             decide_prec: str = "mixed", log=print) -> dict:
+    """Held-out fields: fits (precision prec) from the default start and from the learned
+    start with its fallback rule, each timed as a whole (the learned start's time includes
+    the features, the network and its two decision passes, run in decide_prec: they only
+    compare two logliks); both must reach the same optimum."""
     import torch
     rng = np.random.default_rng(seed)
     theta = sample_priors(rng, nfields)
@@ -226,22 +244,24 @@ def evaluate(geom: Geometry, params, norm, nfields: int, seed: int = 3, prec: st
     vecchia_fields_fit(geom.locs, geom.X, geom.NN, Y[:1].contiguous(), MATERN_ISO, d0[:1].contiguous(),
                        prec=prec)
     vecchia_fields_warm_start(params, norm, geom.locs, geom.X, geom.NN, Y[:1].contiguous(),
-                              geom.rand_pairs, geom.edges2, d0[:1].contiguous(), prec=prec)
+                              geom.rand_pairs, geom.edges2, d0[:1].contiguous(), prec=decide_prec)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     f_def = vecchia_fields_fit(geom.locs, geom.X, geom.NN, Y, MATERN_ISO, d0, prec=prec)
     t1 = time.perf_counter()
     start, used, _ = vecchia_fields_warm_start(params, norm, geom.locs, geom.X, geom.NN, Y,
-                                               geom.rand_pairs, geom.edges2, d0, prec=prec)
+                                               geom.rand_pairs, geom.edges2, d0, prec=decide_prec)
     f_ws = vecchia_fields_fit(geom.locs, geom.X, geom.NN, Y, MATERN_ISO, start, prec=prec)
     t2 = time.perf_counter()
     ll_d = f_def["out"][:, 0].cpu().numpy()
     ll_w = f_ws["out"][:, 0].cpu().numpy()
     conv = (f_def["status"] == 0) & (f_ws["status"] == 0)
     rel = np.abs(ll_w - ll_d) / np.maximum(np.abs(ll_d), geom.n)
+    same = conv & (rel <= 1e-6)
     used = used.cpu().numpy()
     res = {
         "fields": nfields, "n": geom.n, "m": geom.m, "precision": prec,
+        "decision_precision": decide_prec,
         "default": {"seconds": t1 - t0, "mean_iters": float(f_def["iters"].mean()),
                     "mean_passes": float(f_def["evals"].mean()),
                     "max_passes": int(f_def["evals"].max()),
@@ -252,8 +272,14 @@ def evaluate(geom: Geometry, params, norm, nfields: int, seed: int = 3, prec: st
                     "converged": int((f_ws["status"] == 0).sum()),
                     "fallback_rate": float(1.0 - used.mean())},
         "both_converged": int(conv.sum()),
+        "same_optimum": int(same.sum()),
+        "different_optimum_learned_higher": int((conv & ~same & (ll_w > ll_d)).sum()),
+        "different_optimum_default_higher": int((conv & ~same & (ll_w < ll_d)).sum()),
+        "max_loglik_diff_same": float(rel[same].max()) if same.any() else None,
         "max_loglik_diff": float(rel[conv].max()) if conv.any() else None,
-        "loglik_diff_note": "|loglik(learned) - loglik(default)| / max(|loglik|, n)",
+        "loglik_diff_note": "|loglik(learned) - loglik(default)| / max(|loglik|, n); the same "
+                            "optimum means a difference <= 1e-6 (the likelihoods can be "
+                            "multimodal, and the start decides which maximum is reached)",
         "speedup": (t1 - t0) / (t2 - t1),
     }
     if log:
@@ -268,7 +294,6 @@ def main(argv=None):
     """
     import argparse
     import json
-    import os
     import sys
     ap = argparse.ArgumentParser(description=main.__doc__)
     ap.add_argument("--fields", type=int, default=50000)

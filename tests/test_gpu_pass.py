@@ -230,3 +230,29 @@ def test_full_size_matern_100k_matches_oracle():
     for th in (w.theta_true, w.theta_start):
         o = oracle.loglik_grad_info(w.locs, w.y, w.X, w.NN, th, w.covfun)
         compare(gpu_pass(w, th), o)
+
+
+@pytest.mark.slow
+def test_full_size_swath_matches_oracle():
+    """The 1.2 M-point space-time swath workload at full size (m = 30): the FP64 pass at the
+    true and the starting parameters against the oracle (1e-10), the mixed pass within the
+    stated bounds (tau2 = 0.1), and the FP64 and mixed fits against the oracle's fit."""
+    w = workloads.cfg_swath_1m2()
+    for th in (w.theta_true, w.theta_start):
+        o = oracle.loglik_grad_info(w.locs, w.y, w.X, w.NN, th, w.covfun)
+        compare(gpu_pass(w, th), o)
+        gm = gpu_pass(w, th, prec="mixed")
+        assert abs(gm["loglik"] - o["loglik"]) <= 1e-6 * abs(o["loglik"])
+        scale = max(np.linalg.norm(o["grad"]), np.sqrt(np.trace(o["info"])))
+        assert np.linalg.norm(gm["grad"] - o["grad"]) <= 2e-4 * scale
+    dev = torch.device("cuda:0")
+    t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)  # noqa
+    args = (t(w.locs, torch.float64), t(w.y, torch.float64), t(w.X, torch.float64),
+            t(w.NN, torch.int32), w.covfun, w.theta_start)
+    of = oracle.fisher_fit(w.locs, w.y, w.X, w.NN, w.covfun, w.theta_start)
+    g64 = vg.vecchia_fit(*args)
+    gmx = vg.vecchia_fit(*args, prec="mixed")
+    assert g64["status"] == of["status"] == 0 and gmx["status"] == 0
+    assert g64["iters"] == of["iters"]
+    assert abs(g64["loglik"] - of["loglik"]) <= 1e-8 * abs(of["loglik"])
+    assert abs(gmx["loglik"] - of["loglik"]) <= 1e-8 * abs(of["loglik"])
