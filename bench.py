@@ -49,6 +49,11 @@ WORKLOAD = ("isotropic Matern n=100000 in [0,1]^2, m=30 maxmin-ordered nearest e
 # retires one 32-lane FP64 FMA warp-instruction per 64 cycles (2 FMA/clk/SM, measured by
 # a microbenchmark: 596 GFMA/s at ~1.96 GHz), 152 SMs, 2070 MHz maximum SM clock.
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
+# DRAM bytes (read + write) of one launch of the FP64 pass kernel on this workload, from an
+# ncu capture of the current kernel (the summary under profiles/ names the command); set to
+# None whenever the kernel changes until it is captured again.
+TRAFFIC_BYTES = 17338368 + 500736
+TRAFFIC_NOTE = "dram__bytes_read.sum + dram__bytes_write.sum, profiles/k_pass_matern_n100000_m30.md"
 
 
 def algorithmic_fma_per_point(K: int, p: int, q: int) -> float:
@@ -540,7 +545,8 @@ def run_ours(args):
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "roofline": {"bound": "alu", "unit": "GFLOP/s", "achieved": achieved,
                      "peak": FP64_PEAK_GFLOPS, "frac": achieved / FP64_PEAK_GFLOPS,
-                     "traffic": None, "kernel": "k_pass_fp64 (per-observation pass)",
+                     "traffic": TRAFFIC_BYTES, "traffic_note": TRAFFIC_NOTE,
+                     "kernel": "k_pass<MATERN, L, double> (per-observation pass)",
                      "kernel_ms": kern_ms, "flop_per_point": 2 * fma_pt,
                      "achieved_incl_covariance": achieved_cov,
                      "frac_incl_covariance": achieved_cov / FP64_PEAK_GFLOPS,

@@ -96,6 +96,13 @@ VECCHIA_API vec_status vecchia_set_lanes(vec_handle h, int lanes);
  * choose (the default).  Same rules as vecchia_set_lanes. */
 VECCHIA_API vec_status vecchia_set_block_threads(vec_handle h, int threads);
 
+/* Where the pass kernels read the per-pass Matern coefficient table: 1 = staged in shared
+ * memory by every block, 0 = global memory (read through L1, which leaves more shared
+ * memory for observation slots), -1 = the library's choice (the default: the autotuned
+ * placement when a record matches, else shared memory when it fits).  Same rules as
+ * vecchia_set_lanes; a placement that leaves no mapping fitting is ignored. */
+VECCHIA_API vec_status vecchia_set_matern_table(vec_handle h, int placement);
+
 /*
  * Autotuning of the kernel mapping.  vecchia_autotune runs the pass on the given inputs
  * (DEVICE pointers, as for vecchia_loglik_grad_info) once per candidate mapping -- lanes

@@ -92,6 +92,7 @@ def lib():
         L.vecchia_nparms.argtypes = [ci]
         L.vecchia_set_lanes.argtypes = [P, ci]
         L.vecchia_set_block_threads.argtypes = [P, ci]
+        L.vecchia_set_matern_table.argtypes = [P, ci]
         L.vecchia_autotune.argtypes = [P, P, P, P, P, i64, ci, ci, ci, P, ci, ci, P, ci, P, P, P]
         L.vecchia_autotune_save.argtypes = [P, ctypes.c_char_p]
         L.vecchia_autotune_load.argtypes = [P, ctypes.c_char_p]
@@ -131,6 +132,7 @@ def lib():
         L.vecchia_fields_warm_start.argtypes = [P, P, P, ci, P, P, P, i64, ci, ci, ci, P, P, i64,
                                                 P, P, ci, P, P, P, P]
         for f in (L.vecchia_create, L.vecchia_destroy, L.vecchia_set_lanes, L.vecchia_set_block_threads,
+                  L.vecchia_set_matern_table,
                   L.vecchia_loglik_grad_info, L.vecchia_loglik_grad_info_host,
                   L.vecchia_covariance_pairs, L.vecchia_nparms, L.vecchia_max_m,
                   L.vecchia_set_timing, L.vecchia_last_timing, L.vecchia_kernels_per_pass,
@@ -171,6 +173,11 @@ class Handle:
 
     def set_block_threads(self, threads: int):
         _check(lib().vecchia_set_block_threads(self._h, threads))
+
+    def set_matern_table(self, placement):
+        """"shared", "global" or "auto" (see vecchia_set_matern_table)."""
+        code = {"shared": 1, "global": 0, "auto": -1}.get(placement, placement)
+        _check(lib().vecchia_set_matern_table(self._h, int(code)))
 
     def set_timing(self, enable: bool = True):
         _check(lib().vecchia_set_timing(self._h, 1 if enable else 0))

@@ -99,7 +99,7 @@ struct vec_handle_s {
     int nsm = 0;
     int lanes = 0;    // 0 = automatic
     int threads = 0;  // 0 = automatic
-    int tab_mode = -1;  // Matern table placement while autotuning (-1 = planner's choice)
+    int tab_mode = -1;  // forced Matern table placement (-1 = planner's or autotuned choice)
     cudaStream_t stream = nullptr;
     // tracing
     int timing = 0;
@@ -221,6 +221,14 @@ vec_status vecchia_set_block_threads(vec_handle h, int threads) {
     return VEC_OK;
 }
 
+vec_status vecchia_set_matern_table(vec_handle h, int placement) {
+    if (!h) return fail(VEC_ERR_ARG, "vecchia_set_matern_table: NULL handle");
+    if (placement < -1 || placement > 1)
+        return fail(VEC_ERR_ARG, "placement must be -1, 0 or 1 (got %d)", placement);
+    h->tab_mode = placement;
+    return VEC_OK;
+}
+
 vec_status vecchia_create(vec_handle* out, int device) {
     if (!out) return fail(VEC_ERR_ARG, "vecchia_create: out is NULL");
     *out = nullptr;
@@ -330,7 +338,7 @@ vec_status prepare_pass(vec_handle h, int cov, int m, int d, int p, vg::PassPlan
     }
     if (h->tab_mode >= 0) tab = h->tab_mode;
     int pr = vg::plan_pass(cov, m, d, p, h->nsm, L, thr, plan, prec, false, tab);
-    if (pr == -1 && (L != h->lanes || thr != h->threads))  // a stale record: plan afresh
+    if (pr == -1)  // a stale record or a placement that does not fit: plan afresh
         pr = vg::plan_pass(cov, m, d, p, h->nsm, h->lanes, h->threads, plan, prec);
     if (pr == -1) return fail(VEC_ERR_UNSUPPORTED, "no kernel mapping fits m = %d, p = %d", m, p);
     if (pr != 0) return cuda_fail(cudaGetLastError(), "planning the pass kernel");
@@ -633,6 +641,7 @@ vec_status vecchia_autotune(vec_handle h, const double* locs, const double* y, c
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     const int saved_L = h->lanes, saved_T = h->threads, saved_timing = h->timing;
+    const int saved_tab = h->tab_mode;
     h->timing = 0;
     int bestL = 0, bestT = 0;
     float best = 1e30f;
@@ -673,7 +682,7 @@ vec_status vecchia_autotune(vec_handle h, const double* locs, const double* y, c
     }
     h->lanes = saved_L;
     h->threads = saved_T;
-    h->tab_mode = -1;
+    h->tab_mode = saved_tab;
     h->timing = saved_timing;
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
@@ -1189,7 +1198,7 @@ vec_status vecchia_batch_autotune(vec_handle h, int nbatch, const double* locs, 
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&dst), sizeof(long long) * 2 * nbatch);
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
-    const int saved_L = h->lanes, saved_T = h->threads;
+    const int saved_L = h->lanes, saved_T = h->threads, saved_tab = h->tab_mode;
     int bestL = 0, bestT = 0, mmax = 0;
     float best = 1e30f;
     for (int b = 0; b < nbatch; ++b) mmax = m[b] > mmax ? m[b] : mmax;
@@ -1232,7 +1241,7 @@ vec_status vecchia_batch_autotune(vec_handle h, int nbatch, const double* locs, 
     }
     h->lanes = saved_L;
     h->threads = saved_T;
-    h->tab_mode = -1;
+    h->tab_mode = saved_tab;
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     cudaFree(out);

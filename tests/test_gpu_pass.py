@@ -233,6 +233,35 @@ def test_full_size_matern_100k_matches_oracle():
 
 
 @pytest.mark.slow
+@pytest.mark.parametrize("placement", ["global", "shared"])
+def test_full_size_matern_100k_each_table_placement(placement):
+    """The full-size pass with the mapping the autotuner picks on GB300 for FP64 (8 lanes,
+    64 threads) and for mixed precision (16 lanes, 256 threads), with the Matern table in
+    global and in shared memory; the FP64 pass against the oracle, the mixed one within its
+    bounds."""
+    w = workloads.cfg_matern_100k()
+    o = oracle.loglik_grad_info(w.locs, w.y, w.X, w.NN, w.theta_true, w.covfun)
+    dev = torch.device("cuda:0")
+    t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)  # noqa
+    args = (t(w.locs, torch.float64), t(w.y, torch.float64), t(w.X, torch.float64),
+            t(w.NN, torch.int32), t(w.theta_true, torch.float64), w.covfun)
+    for prec, lanes, threads in (("fp64", 8, 64), ("mixed", 16, 256)):
+        h = vg.Handle(0)
+        h.set_lanes(lanes)
+        h.set_block_threads(threads)
+        h.set_matern_table(placement)
+        out, st = vg.vecchia_loglik_grad_info(*args, prec=prec, handle=h)
+        torch.cuda.synchronize()
+        h.close()
+        assert int(st[0]) == 0
+        g = vg.unpack(out, 4, w.p)
+        if prec == "fp64":
+            compare(g, o)
+        else:
+            assert abs(g["loglik"] - o["loglik"]) <= 1e-6 * abs(o["loglik"])
+
+
+@pytest.mark.slow
 def test_full_size_swath_matches_oracle():
     """The 1.2 M-point space-time swath workload at full size (m = 30): the FP64 pass at the
     true and the starting parameters against the oracle (1e-10), the mixed pass within the
