@@ -16,8 +16,25 @@
 
 namespace vg {
 
+// Coefficients of the Chebyshev polynomials T_0..T_(MT_NC-1) in powers of u (integers),
+// from T_(k+1) = 2u T_k - T_(k-1); computed at compile time.
+struct ChebMono {
+    double c[MT_NC][MT_NC];  // c[deg][k]: coefficient of u^k in T_deg
+    constexpr ChebMono() : c{} {
+        c[0][0] = 1.0;
+        c[1][1] = 1.0;
+        for (int d = 2; d < MT_NC; ++d)
+            for (int k = 0; k < MT_NC; ++k)
+                c[d][k] = (k > 0 ? 2.0 * c[d - 1][k - 1] : 0.0) - c[d - 2][k];
+    }
+};
+__constant__ ChebMono c_cheb = ChebMono();
+
 // Table builder: one block of MT_NC warps per interval; warp i evaluates interpolation
-// node i, then three threads turn node values into monomial coefficients in w.
+// node i (the Chebyshev nodes of the interval); then 3 x MT_NC threads form the Chebyshev
+// coefficients a_k = (2 / MT_NC) sum_q f(u_q) T_k(u_q) (halved for k = 0), one each, and
+// 3 x MT_NC threads the monomial coefficients sum_deg a_deg c_cheb[deg][k], one each.
+// The covariance scales are folded in: F0 x sigma2, F1 x sigma2 / rho, F2 x sigma2.
 // nu is read from covparms[2]; invalid nu leaves the table untouched (the pass reports
 // the parameter error).
 __global__ void __launch_bounds__(MT_NC * 32) k_mtab_build(const double* __restrict__ covparms,
@@ -25,6 +42,7 @@ __global__ void __launch_bounds__(MT_NC * 32) k_mtab_build(const double* __restr
                                                            float* __restrict__ tabf, int q,
                                                            const int* __restrict__ active) {
     __shared__ double vals[3][MT_NC];
+    __shared__ double cheb[3][MT_NC];
     // blockIdx.y selects the dataset of a batch: its parameters and its tables; datasets
     // whose active flag is 0 are skipped
     if (active && !active[blockIdx.y]) return;
@@ -37,55 +55,39 @@ __global__ void __launch_bounds__(MT_NC * 32) k_mtab_build(const double* __restr
     const int e = MT_E0 + it / MT_J, j = it % MT_J;
     const double hw = 1.0 / (2.0 * MT_J);
     const double cen = 1.0 + (double)(2 * j + 1) / (double)(2 * MT_J);
-    const double PI = 3.14159265358979323846;
     const int node = threadIdx.x >> 5;
     {
-        double u = cos(PI * (node + 0.5) / MT_NC);
-        double s = ldexp(cen + hw * u, e);
-        double psi = dev_digamma(nu), lg = lgamma(nu);
+        const double u = cospi((node + 0.5) / MT_NC);
+        const double s = ldexp(cen + hw * u, e);
+        const double psi = dev_digamma(nu), lg = lgamma(nu);
         double f0, f1, f2;
         matern_direct_warp(nu, sqrt(s), psi, lg, f0, f1, f2);
         if ((threadIdx.x & 31) == 0) { vals[0][node] = f0; vals[1][node] = f1; vals[2][node] = f2; }
     }
     __syncthreads();
-    const int i = threadIdx.x;
-    if (i < 3) {
-        double a[MT_NC];
-        for (int k = 0; k < MT_NC; ++k) {
-            double acc = 0.0;
-            for (int q = 0; q < MT_NC; ++q) acc += vals[i][q] * cos(PI * k * (q + 0.5) / MT_NC);
-            a[k] = acc * (2.0 / MT_NC);
-        }
-        a[0] *= 0.5;
-        // sum_k a_k T_k(u) -> monomials in u, via T_{k+1} = 2u T_k - T_{k-1}
-        double mono[MT_NC], Tm[MT_NC], Tc[MT_NC], Tn[MT_NC];
-        for (int k = 0; k < MT_NC; ++k) { mono[k] = 0.0; Tm[k] = 0.0; Tc[k] = 0.0; }
-        Tm[0] = 1.0;            // T_0
-        Tc[1] = 1.0;            // T_1
-        mono[0] = a[0];
-        for (int k = 0; k < MT_NC; ++k) mono[k] += a[1] * Tc[k];
-        for (int deg = 2; deg < MT_NC; ++deg) {
-            for (int k = 0; k < MT_NC; ++k) Tn[k] = -Tm[k] + (k > 0 ? 2.0 * Tc[k - 1] : 0.0);
-            for (int k = 0; k < MT_NC; ++k) { mono[k] += a[deg] * Tn[k]; Tm[k] = Tc[k]; Tc[k] = Tn[k]; }
-        }
-        // u = w / hw: coefficient of w^k is mono_k / hw^k (exact power-of-two scaling);
-        // w^0..w^7 stored in FP64, w^8..w^12 in FP32 (see horner_split)
-        // the covariance scales are folded in: F0 x sigma2, F1 x sigma2 / rho, F2 x sigma2
-        const double fsc = (i == 1) ? covparms[0] / covparms[1] : covparms[0];
-        double* out = tab + (size_t)it * MT_PER_INT + i * MT_FSTRIDE;
+    const int t = threadIdx.x;
+    if (t < 3 * MT_NC) {
+        const int f = t / MT_NC, k = t % MT_NC;
+        double acc = 0.0;
+        for (int qn = 0; qn < MT_NC; ++qn)
+            acc = fma(vals[f][qn], cospi((double)(k * (2 * qn + 1)) / (2.0 * MT_NC)), acc);
+        cheb[f][k] = acc * (k == 0 ? 1.0 / MT_NC : 2.0 / MT_NC);
+    }
+    __syncthreads();
+    if (t < 3 * MT_NC) {
+        const int f = t / MT_NC, k = t % MT_NC;
+        double mono = 0.0;
+        for (int deg = k; deg < MT_NC; ++deg) mono = fma(cheb[f][deg], c_cheb.c[deg][k], mono);
+        // u = w / hw: the coefficient of w^k is mono / hw^k (an exact power-of-two scaling);
+        // w^0..w^7 in FP64, w^8..w^12 in FP32 (see horner_split)
+        const double fsc = (f == 1) ? covparms[0] / covparms[1] : covparms[0];
+        const double v = mono * fsc * ldexp(1.0, k * (MT_LOGJ + 1));
+        double* out = tab + (size_t)it * MT_PER_INT + f * MT_FSTRIDE;
         float* tail = reinterpret_cast<float*>(out + MT_NHEAD);
-        double sc = fsc;
-        for (int k = 0; k < MT_NC; ++k) {
-            if (k < MT_NHEAD) out[k] = mono[k] * sc;
-            else tail[k - MT_NHEAD] = (float)(mono[k] * sc);
-            sc *= (2.0 * MT_J);
-        }
-        tail[MT_NC - MT_NHEAD] = 0.0f;
-        if (tabf) {  // FP32 copy for the mixed path
-            float* of = tabf + (size_t)it * MT_PER_INT_F + i * MT_NC;
-            double sc2 = fsc;
-            for (int k = 0; k < MT_NC; ++k) { of[k] = (float)(mono[k] * sc2); sc2 *= (2.0 * MT_J); }
-        }
+        if (k < MT_NHEAD) out[k] = v;
+        else tail[k - MT_NHEAD] = (float)v;
+        if (k == MT_NC - 1) tail[MT_NC - MT_NHEAD] = 0.0f;
+        if (tabf) tabf[(size_t)it * MT_PER_INT_F + f * MT_NC + k] = (float)v;  // mixed path
     }
 }
 

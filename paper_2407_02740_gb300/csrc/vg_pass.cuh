@@ -461,8 +461,14 @@ __device__ __forceinline__ void vecchia_point(const PassEnv<T, Tab>& E, long lon
     gsync<L>(gmask);
 }
 
+// The FP32 (mixed) instantiations are latency-bound: ask for three resident blocks of 256
+// threads (at most 85 registers a thread; they need 80, with no meaningful spill) so that
+// registers no longer cap the resident warps at 16 per SM.  The FP64 ones are bound by the
+// FP64 pipe and keep the default.
+constexpr int pass_min_blocks(int tsize) { return tsize == 4 ? 3 : 1; }
+
 template <int COV, int L, typename T>
-__global__ void __launch_bounds__(256) k_pass(PassArgs args) {
+__global__ void __launch_bounds__(256, pass_min_blocks(sizeof(T))) k_pass(PassArgs args) {
     extern __shared__ __align__(16) double smem[];
     using N = Num<T>;
     using MT = MaternT<T>;
@@ -597,7 +603,7 @@ __global__ void __launch_bounds__(256) k_pass(PassArgs args) {
 // observations and reduce the tile's sums into its own record (so the result does not
 // depend on which CTA ran which tile).
 template <int COV, int L, typename T>
-__global__ void __launch_bounds__(256) k_pass_batch(BatchArgs bargs) {
+__global__ void __launch_bounds__(256, pass_min_blocks(sizeof(T))) k_pass_batch(BatchArgs bargs) {
     extern __shared__ __align__(16) double smem[];
     using MT = MaternT<T>;
     using Tab = typename MT::Tab;

@@ -34,7 +34,7 @@ import numpy as np
 
 from . import (MATERN_ISO, MLP_NPARAMS, vecchia_fields_fit, vecchia_fields_simulate,
                vecchia_fields_variogram, vecchia_fields_warm_start, vecchia_mlp_adam_step,
-               vecchia_mlp_column_moments, vecchia_mlp_forward)
+               vecchia_mlp_column_moments, vecchia_mlp_forward, vecchia_mlp_grad)
 
 PRIORS = {"sigma2": (0.5, 2.0), "rho": (0.02, 0.3), "nu": (0.5, 2.5), "tau2": (0.001, 0.2)}
 NBINS, LAG_LO, LAG_HI = 32, 0.005, 0.5
@@ -172,7 +172,9 @@ def init_params(seed: int):
 def train(X, T, epochs: int = 60, batch: int = 256, lr: float = 1e-3, seed: int = 2,
           log=print):
     """Adam on the standardised targets, minibatches from a fresh random permutation each
-    epoch.  Returns (params, norm, losses: the last minibatch loss of each epoch)."""
+    epoch.  Returns (params, norm, losses): losses["epochs"] holds the last minibatch loss
+    of each epoch, losses["initial"] / losses["final"] the loss over the whole training set
+    before and after training."""
     import torch
     dev = X.device
     xm, xs = vecchia_mlp_column_moments(X)
@@ -185,16 +187,17 @@ def train(X, T, epochs: int = 60, batch: int = 256, lr: float = 1e-3, seed: int 
     g = torch.Generator(device="cpu").manual_seed(seed + 1)
     N = X.shape[0]
     step = 0
-    losses = []
+    losses = {"epochs": [], "initial": float(vecchia_mlp_grad(P, norm, X, T)[1].item())}
     for ep in range(epochs):
         perm = torch.randperm(N, generator=g).to(torch.int32).to(dev)
         for b0 in range(0, N - batch + 1, batch):
             step += 1
             vecchia_mlp_adam_step(P, m, v, step, lr, norm, X, T, index=perm[b0:b0 + batch],
                                   loss=loss)
-        losses.append(float(loss.item()))
+        losses["epochs"].append(float(loss.item()))
         if log and (ep % 10 == 0 or ep == epochs - 1):
-            log("epoch %d: minibatch loss %.4f" % (ep, losses[-1]))
+            log("epoch %d: minibatch loss %.4f" % (ep, losses["epochs"][-1]))
+    losses["final"] = float(vecchia_mlp_grad(P, norm, X, T)[1].item())
     return P, norm, losses
 
 
@@ -326,7 +329,8 @@ def main(argv=None):
     gev = geometry(a.eval_n, a.m, 1006)
     ev = evaluate(gev, P, norm, a.eval_fields)
     report = {"training_set": stats, "training_set_s": t1 - t0, "train_s": t2 - t1,
-              "final_loss": losses[-1], "losses": losses, "evaluation": ev, "meta": meta}
+              "initial_loss": losses["initial"], "final_loss": losses["final"],
+              "epoch_losses": losses["epochs"], "evaluation": ev, "meta": meta}
     if a.report:
         with open(a.report, "w") as f:
             json.dump(report, f, indent=1)

@@ -32,7 +32,7 @@ def trained():
 
 def test_training_reduces_the_loss(trained):
     P, norm, losses, X, T = trained
-    assert losses[-1] < 0.5 * losses[0]
+    assert losses["final"] < 0.5 * losses["initial"]
     # the fit of the training targets: predictions explain part of each target's variance
     pred = vg.vecchia_mlp_forward(P, norm, X)
     resid = ((pred - T) ** 2).mean(dim=0)
