@@ -19,7 +19,8 @@ Reported beside the device-timed value:
                   batched pass as one CUDA-graph replay vs 256 per-dataset calls, and
                   batched Fisher-scoring fits vs 256 sequential device fits;
   * warm_start -- fits of held-out fields (n = 200000) from the default start and from
-                  the learned start.
+                  the learned start;
+  * nn_search  -- the ordered nearest-neighbour search on the device vs the CPU search.
 ``--impl reference`` times the CPU oracle itself as the reference arm.
 Multi-GPU runs (torchrun) are independent replicas: each rank evaluates its own copy.
 """
@@ -356,6 +357,38 @@ def run_warm_start(torch, dev, local: int, nfields: int = 64) -> dict:
     return res
 
 
+def run_nn_search(vg, torch, dev, stream) -> dict:
+    """Ordered nearest-neighbour search (the NNarray) on the device against the CPU search
+    of the same definition on the host cores: the 100000 maxmin-ordered locations of the
+    headline workload (m = 30) and 1000000 uniform locations in random order (m = 30);
+    the arrays must be identical."""
+    import workloads
+    res = {}
+    for name, n, ordered in (("n100000_maxmin", 100000, True), ("n1000000_random_order", 1000000, False)):
+        rng = np.random.default_rng(1002 if ordered else 1008)
+        L = rng.uniform(size=(n, 2))
+        if ordered:
+            L = L[workloads.maxmin_order(L)]
+        t0 = time.perf_counter()
+        ref = workloads.ordered_nn(L, 30)
+        cpu_s = time.perf_counter() - t0
+        Ld = torch.as_tensor(L, dtype=torch.float64, device=dev)
+        NN = vg.vecchia_ordered_nn(Ld, 30, stream=stream)      # warm-up (scratch allocation)
+        ms = []
+        for _ in range(3):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            NN = vg.vecchia_ordered_nn(Ld, 30, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        res[name] = {"n": n, "m": 30, "gpu_ms": statistics.median(ms), "cpu_ms": cpu_s * 1e3,
+                     "cpu_threads": os.cpu_count() or 1,
+                     "identical": bool(np.array_equal(NN.cpu().numpy(), ref))}
+    return res
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -521,6 +554,7 @@ def run_ours(args):
 
     batched = run_batched(vg, torch, dev, stream, args.steps, args.warmup, flush, local)
     warm = run_warm_start(torch, dev, local)
+    nn = run_nn_search(vg, torch, dev, stream)
 
     if rank != 0:
         if ws > 1:
@@ -587,6 +621,7 @@ def run_ours(args):
                           "theta": [float(v) for v in mfit["theta"]]}},
         "batched": batched,
         "warm_start": warm,
+        "nn_search": nn,
     }
     print(json.dumps(line))
     if ws > 1:

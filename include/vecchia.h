@@ -454,6 +454,25 @@ VECCHIA_API vec_status vecchia_fields_warm_start(vec_handle h, const float* para
                                                  int* used_learned, float* features);
 
 /*
+ * vecchia_ordered_nn -- the NNarray on the device.
+ *
+ * For an ordering of n locations (locs: DEVICE, n x d row-major FP64, already in the order
+ * the likelihood will use, e.g. maxmin), row i of NNarray (DEVICE, n x (m+1) int32) is i
+ * followed by its m nearest among locations 0..i-1, nearest first, -1 padded for i < m
+ * (the input of vecchia_loglik_grad_info; the paper computes it on the CPU and names a GPU
+ * version as future work).  Exact: the neighbours are the m smallest keys (d2, j) over
+ * j < i in lexicographic order, d2 = the sum over coordinates, in order, of (x_ik -
+ * x_jk)^2 with each product and sum rounded separately in FP64 (no fused multiply-add),
+ * so ties go to the lower index and any FP64 implementation of the definition gives the
+ * same array.  A uniform grid over the first two coordinates (built on the device) limits
+ * the search; early observations, which have few earlier points, are searched by brute
+ * force.  1 <= d <= 3, 0 <= m <= vecchia_max_m(), n < 2^31.  Handle scratch ~ 14 bytes
+ * per location.  Asynchronous on `stream`.
+ */
+VECCHIA_API vec_status vecchia_ordered_nn(vec_handle h, const double* locs, int64_t n, int d,
+                                          int m, void* stream, int32_t* NNarray);
+
+/*
  * vecchia_covariance_pairs -- the library's device covariance functions on explicit pairs.
  *
  * For each pair k: C[k] = C(la[k], lb[k]; covparms) including the nugget sigma2 tau2 when

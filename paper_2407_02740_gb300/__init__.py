@@ -125,6 +125,7 @@ def lib():
         L.vecchia_fields_variogram.argtypes = [P, ci, P, P, i64, ci, ci, P, P, i64, P, ci, P, P, P,
                                                P]
         cf = ctypes.c_float
+        L.vecchia_ordered_nn.argtypes = [P, P, i64, ci, ci, P, P]
         L.vecchia_mlp_forward.argtypes = [P, P, P, P, ci, P, P]
         L.vecchia_mlp_grad.argtypes = [P, P, P, P, P, P, ci, P, P, P]
         L.vecchia_mlp_adam_step.argtypes = [P, P, P, P, ci, cf, P, P, P, P, ci, P, P]
@@ -145,7 +146,7 @@ def lib():
                   L.vecchia_fields_fit, L.vecchia_fields_simulate,
                   L.vecchia_fields_variogram, L.vecchia_mlp_forward, L.vecchia_mlp_grad,
                   L.vecchia_mlp_adam_step, L.vecchia_mlp_column_moments,
-                  L.vecchia_fields_warm_start):
+                  L.vecchia_fields_warm_start, L.vecchia_ordered_nn):
             f.restype = ci
         _lib = L
     return _lib
@@ -542,6 +543,19 @@ def vecchia_fields_variogram(locs, NNarray, Y, rand_pairs, edges2, stream=None, 
                                           _dptr(feats), _dptr(bs) if raw else None,
                                           _dptr(bc) if raw else None))
     return (feats, bs, bc) if raw else feats
+
+
+def vecchia_ordered_nn(locs, m: int, stream=None, handle: Handle | None = None):
+    """NNarray (n, m+1) int32 on the device for locations already in their ordering (see
+    vecchia_ordered_nn in include/vecchia.h)."""
+    import torch
+    _dev_tensor_check(locs, torch.float64, "locs")
+    n, d = locs.shape
+    handle = handle or default_handle(locs.device.index or 0)
+    NN = torch.empty(n, m + 1, dtype=torch.int32, device=locs.device)
+    _check(lib().vecchia_ordered_nn(handle.ptr, _dptr(locs), n, d, m,
+                                    ctypes.c_void_p(_stream(locs, stream).cuda_stream), _dptr(NN)))
+    return NN
 
 
 MLP_NPARAMS, MLP_NNORM = 21252, 72

@@ -140,6 +140,8 @@ struct vec_handle_s {
     double* ws_theta0 = nullptr; size_t c_ws_theta0 = 0;
     double* ws_out = nullptr; size_t c_ws_out = 0;
     long long* ws_st = nullptr; size_t c_ws_st = 0;
+    // ordered-neighbour search scratch
+    char* nn_scratch = nullptr; size_t c_nn_scratch = 0;
     // pass scratch
     double* partials = nullptr;
     size_t partials_cap = 0;
@@ -289,7 +291,7 @@ vec_status vecchia_destroy(vec_handle h) {
     cudaFree(h->bf_out); cudaFree(h->bf_st); cudaFree(h->sim_factor);
     cudaFree(h->vg_mean); cudaFree(h->vg_var); cudaFree(h->vg_psum); cudaFree(h->vg_pcnt);
     cudaFree(h->mlp_gpart); cudaFree(h->mlp_lpart); cudaFree(h->ws_feat); cudaFree(h->ws_pred);
-    cudaFree(h->ws_theta0); cudaFree(h->ws_out); cudaFree(h->ws_st);
+    cudaFree(h->ws_theta0); cudaFree(h->ws_out); cudaFree(h->ws_st); cudaFree(h->nn_scratch);
     if (h->stream) cudaStreamDestroy(h->stream);
     delete h;
     return VEC_OK;
@@ -1499,6 +1501,24 @@ vec_status vecchia_fields_warm_start(vec_handle h, const float* params, const fl
     e = vg::launch_choose_start(h->ws_theta0, default_start, out0, st0, out1, st1, nfields, q, nout,
                                 start, used_learned, st);
     if (e != cudaSuccess) return cuda_fail(e, "vecchia_fields_warm_start: choosing starts");
+    return VEC_OK;
+}
+
+vec_status vecchia_ordered_nn(vec_handle h, const double* locs, int64_t n, int d, int m,
+                              void* stream, int32_t* NNarray) {
+    if (!h || !locs || !NNarray) return fail(VEC_ERR_ARG, "vecchia_ordered_nn: NULL argument");
+    if (n < 1 || n > (int64_t)INT_MAX || d < 1 || d > vg::DMAX || m < 0 || m > vg::KMAX - 1)
+        return fail(VEC_ERR_ARG, "vecchia_ordered_nn: bad sizes (n %lld, d %d, m %d)", (long long)n, d, m);
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(VEC_ERR_CUDA, "cannot select device %d", h->device);
+    // about two observations per cell of a G x G grid over the first two coordinates
+    const double cells = std::max(1.0, (double)n / 2.0);
+    const int G = d > 1 ? std::max(1, (int)std::sqrt(cells)) : (int)std::min<double>(cells, 1 << 30);
+    cudaError_t e = grow(&h->nn_scratch, &h->c_nn_scratch, vg::ordered_nn_scratch_bytes(n, d, G));
+    if (e != cudaSuccess) return cuda_fail(e, "vecchia_ordered_nn: allocating scratch");
+    e = vg::launch_ordered_nn(locs, n, d, m, G, h->nn_scratch, NNarray,
+                              reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "vecchia_ordered_nn: launching");
     return VEC_OK;
 }
 

@@ -22,6 +22,7 @@
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
+#include <omp.h>
 #include <string.h>
 
 #define PREP_OK 0
@@ -302,11 +303,16 @@ int prep_ordered_nn(const double* x, int64_t n, int d, int m, int32_t* NN)
     }
     grid_t g;
     if (grid_build(&g, x, n, d, 2.0)) return PREP_ERR_NOMEM;
-    double* cd = (double*)malloc(sizeof(double) * (size_t)m);
-    int64_t* ci = (int64_t*)malloc(sizeof(int64_t) * (size_t)m);
-    if (!cd || !ci) { free(cd); free(ci); grid_free(&g); return PREP_ERR_NOMEM; }
+    /* rows are independent: OpenMP over i, one candidate buffer per thread */
+    const int nthr = omp_get_max_threads();
+    double* cd_all = (double*)malloc(sizeof(double) * (size_t)m * (size_t)nthr);
+    int64_t* ci_all = (int64_t*)malloc(sizeof(int64_t) * (size_t)m * (size_t)nthr);
+    if (!cd_all || !ci_all) { free(cd_all); free(ci_all); grid_free(&g); return PREP_ERR_NOMEM; }
     const int64_t brute_upto = 4 * (int64_t)m + 64;
+#pragma omp parallel for schedule(dynamic, 256)
     for (int64_t i = 0; i < n; i++) {
+        double* cd = cd_all + (size_t)m * (size_t)omp_get_thread_num();
+        int64_t* ci = ci_all + (size_t)m * (size_t)omp_get_thread_num();
         int cnt = 0;
         NN[i * W] = (int32_t)i;
         if (i <= brute_upto) {
@@ -358,8 +364,8 @@ int prep_ordered_nn(const double* x, int64_t n, int d, int m, int32_t* NN)
         }
         for (int t = 0; t < cnt; t++) NN[i * W + 1 + t] = (int32_t)ci[t];
     }
-    free(cd);
-    free(ci);
+    free(cd_all);
+    free(ci_all);
     grid_free(&g);
     return PREP_OK;
 }
