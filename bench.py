@@ -132,6 +132,22 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def max_over_ranks(x: float, ws: int) -> float:
+    """The largest value of x over the ranks (the slowest replica's time); x itself at N = 1."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    tt = torch.tensor([float(x)], dtype=torch.float64)
+    torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_throughput(ws: int, units_per_rank: int, steps: int, total_s: float) -> float:
+    """Whole-job units per second: every rank processes units_per_rank units per step, and
+    the job takes the slowest rank's time."""
+    return ws * units_per_rank * steps / total_s
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -480,13 +496,9 @@ def run_ours(args):
         pass_ms.append(h.last_timing()["pass"])
     torch.cuda.synchronize()
     clocks = sampler.stop()
-    total_ms = float(sum(step_ms))
-    if ws > 1:
-        tt = torch.tensor([total_ms], dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(sum(step_ms), ws)
     ms_per_step = total_ms / args.steps
-    value = ws * w.n * args.steps / (total_ms / 1e3)
+    value = job_throughput(ws, w.n, args.steps, total_ms / 1e3)
 
     # end to end through the host-memory entry point, pinned host buffers
     pin = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt).pin_memory().numpy()  # noqa
@@ -502,11 +514,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         r = vg.vecchia_loglik_grad_info_host(hl, hy, hX, hNN, hth, w.covfun, handle=he)
         e2e_s.append(time.perf_counter() - t0)
-    e2e_total = sum(e2e_s)
-    if ws > 1:
-        tt = torch.tensor([e2e_total], dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e_total = float(tt.item())
+    e2e_total = max_over_ranks(sum(e2e_s), ws)
     h2d = hl.nbytes + hy.nbytes + hX.nbytes + hNN.nbytes + hth.nbytes
     d2h = 8 * (1 + q + q * q + w.p) + 16
 
@@ -589,7 +597,7 @@ def run_ours(args):
                      "hbm_frac_of_measured": bytes_pt * w.n / (kern_ms * 1e-3) / 1e9 / 6785.9},
         "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": cpu_cores, "kind": "oracle",
                          "sample": "first %d of %d observations, %.1f s" % (cpu_n, w.n, cpu_s)},
-        "e2e": {"value": ws * w.n * args.steps / e2e_total, "unit": UNIT,
+        "e2e": {"value": job_throughput(ws, w.n, args.steps, e2e_total), "unit": UNIT,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": args.steps * int(vg.lib().vecchia_kernels_per_pass(w.covfun)),
         "clocks": clocks,
