@@ -473,6 +473,38 @@ VECCHIA_API vec_status vecchia_ordered_nn(vec_handle h, const double* locs, int6
                                           int m, void* stream, int32_t* NNarray);
 
 /*
+ * vecchia_nearest -- the m nearest reference locations of each query location (for
+ * prediction).  locs_ref: DEVICE nref x d, locs_query: DEVICE nquery x d (FP64, row-major);
+ * NNarray: DEVICE nquery x m int32, row q = the indices of the m smallest keys (d2, j) over
+ * all j < nref (d2 as in vecchia_ordered_nn), nearest first, -1 padded when nref < m.  Same
+ * grid search as vecchia_ordered_nn.  1 <= m <= vecchia_max_m().  Asynchronous.
+ *
+ * vecchia_predict -- Vecchia prediction (kriging from a neighbour set).  For target q with
+ * covariates X_pred[q] and neighbours NN_pred[q] (nquery x m rows of observation indices,
+ * a valid prefix then -1, e.g. from vecchia_nearest):
+ *   mean[q] = X_pred[q]' beta + k' Sigma_NN^-1 (y_N - X_N beta),
+ *   var[q]  = c - k' Sigma_NN^-1 k,
+ * Sigma_NN the covariance of the neighbours' observations (nugget sigma2 tau2 on its
+ * diagonal), k their covariances with the target, and c = sigma2 when latent != 0 (the
+ * latent field) or sigma2 (1 + tau2) (a new observation).  Computed per target from the
+ * Cholesky factor of the (neighbours, target) block with one extra row of residuals, in
+ * FP64.  All arrays DEVICE memory: locs (n x d), y (n), X (n x p), beta (p), locs_pred
+ * (npred x d), X_pred (npred x p), NN_pred (npred x m), covparms (q); outputs mean, var
+ * (npred) and dev_status (2: code, first failing target; VEC_ERR_NOT_PD if a block is not
+ * positive definite, VEC_ERR_ARG for bad parameters or neighbour rows).  Asynchronous.
+ */
+VECCHIA_API vec_status vecchia_nearest(vec_handle h, const double* locs_ref, int64_t nref,
+                                       const double* locs_query, int64_t nquery, int d, int m,
+                                       void* stream, int32_t* NNarray);
+VECCHIA_API vec_status vecchia_predict(vec_handle h, const double* locs, const double* y,
+                                       const double* X, int64_t n, const double* beta,
+                                       const double* locs_pred, const double* X_pred,
+                                       const int32_t* NN_pred, int64_t npred, int d, int p,
+                                       int m, const double* covparms, vec_covfun covfun,
+                                       int latent, void* stream, double* mean, double* var,
+                                       int64_t* dev_status);
+
+/*
  * vecchia_covariance_pairs -- the library's device covariance functions on explicit pairs.
  *
  * For each pair k: C[k] = C(la[k], lb[k]; covparms) including the nugget sigma2 tau2 when

@@ -126,6 +126,9 @@ def lib():
                                                P]
         cf = ctypes.c_float
         L.vecchia_ordered_nn.argtypes = [P, P, i64, ci, ci, P, P]
+        L.vecchia_nearest.argtypes = [P, P, i64, P, i64, ci, ci, P, P]
+        L.vecchia_predict.argtypes = [P, P, P, P, i64, P, P, P, P, i64, ci, ci, ci, P, ci, ci, P,
+                                      P, P, P]
         L.vecchia_mlp_forward.argtypes = [P, P, P, P, ci, P, P]
         L.vecchia_mlp_grad.argtypes = [P, P, P, P, P, P, ci, P, P, P]
         L.vecchia_mlp_adam_step.argtypes = [P, P, P, P, ci, cf, P, P, P, P, ci, P, P]
@@ -146,7 +149,8 @@ def lib():
                   L.vecchia_fields_fit, L.vecchia_fields_simulate,
                   L.vecchia_fields_variogram, L.vecchia_mlp_forward, L.vecchia_mlp_grad,
                   L.vecchia_mlp_adam_step, L.vecchia_mlp_column_moments,
-                  L.vecchia_fields_warm_start, L.vecchia_ordered_nn):
+                  L.vecchia_fields_warm_start, L.vecchia_ordered_nn, L.vecchia_nearest,
+                  L.vecchia_predict):
             f.restype = ci
         _lib = L
     return _lib
@@ -556,6 +560,43 @@ def vecchia_ordered_nn(locs, m: int, stream=None, handle: Handle | None = None):
     _check(lib().vecchia_ordered_nn(handle.ptr, _dptr(locs), n, d, m,
                                     ctypes.c_void_p(_stream(locs, stream).cuda_stream), _dptr(NN)))
     return NN
+
+
+def vecchia_nearest(locs_ref, locs_query, m: int, stream=None, handle: Handle | None = None):
+    """(nquery, m) int32 indices of the m nearest reference locations of each query."""
+    import torch
+    _dev_tensor_check(locs_ref, torch.float64, "locs_ref")
+    _dev_tensor_check(locs_query, torch.float64, "locs_query")
+    handle = handle or default_handle(locs_ref.device.index or 0)
+    NN = torch.empty(locs_query.shape[0], m, dtype=torch.int32, device=locs_ref.device)
+    _check(lib().vecchia_nearest(handle.ptr, _dptr(locs_ref), locs_ref.shape[0], _dptr(locs_query),
+                                 locs_query.shape[0], locs_ref.shape[1], m,
+                                 ctypes.c_void_p(_stream(locs_ref, stream).cuda_stream), _dptr(NN)))
+    return NN
+
+
+def vecchia_predict(locs, y, X, beta, locs_pred, X_pred, NN_pred, covparms, covfun: int,
+                    latent: bool = True, stream=None, handle: Handle | None = None):
+    """Vecchia prediction (see vecchia_predict in include/vecchia.h).  Returns (mean, var,
+    status) as CUDA tensors."""
+    import torch
+    for t, dt, nm in ((locs, torch.float64, "locs"), (y, torch.float64, "y"),
+                      (X, torch.float64, "X"), (beta, torch.float64, "beta"),
+                      (locs_pred, torch.float64, "locs_pred"), (X_pred, torch.float64, "X_pred"),
+                      (NN_pred, torch.int32, "NN_pred"), (covparms, torch.float64, "covparms")):
+        _dev_tensor_check(t, dt, nm)
+    n, d = locs.shape
+    npred, m = NN_pred.shape
+    handle = handle or default_handle(locs.device.index or 0)
+    mean = torch.empty(npred, dtype=torch.float64, device=locs.device)
+    var = torch.empty_like(mean)
+    status = torch.empty(2, dtype=torch.int64, device=locs.device)
+    _check(lib().vecchia_predict(handle.ptr, _dptr(locs), _dptr(y), _dptr(X), n, _dptr(beta),
+                                 _dptr(locs_pred), _dptr(X_pred), _dptr(NN_pred), npred, d,
+                                 X.shape[1], m, _dptr(covparms), covfun, 1 if latent else 0,
+                                 ctypes.c_void_p(_stream(locs, stream).cuda_stream), _dptr(mean),
+                                 _dptr(var), _dptr(status)))
+    return mean, var, status
 
 
 MLP_NPARAMS, MLP_NNORM = 21252, 72

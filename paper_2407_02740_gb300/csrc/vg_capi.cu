@@ -1522,6 +1522,55 @@ vec_status vecchia_ordered_nn(vec_handle h, const double* locs, int64_t n, int d
     return VEC_OK;
 }
 
+vec_status vecchia_nearest(vec_handle h, const double* locs_ref, int64_t nref,
+                           const double* locs_query, int64_t nquery, int d, int m, void* stream,
+                           int32_t* NNarray) {
+    if (!h || !locs_ref || !locs_query || !NNarray)
+        return fail(VEC_ERR_ARG, "vecchia_nearest: NULL argument");
+    if (nref < 1 || nref > (int64_t)INT_MAX || nquery < 1 || d < 1 || d > vg::DMAX || m < 1 ||
+        m > vg::KMAX - 1)
+        return fail(VEC_ERR_ARG, "vecchia_nearest: bad sizes (nref %lld, nquery %lld, d %d, m %d)",
+                    (long long)nref, (long long)nquery, d, m);
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(VEC_ERR_CUDA, "cannot select device %d", h->device);
+    const double cells = std::max(1.0, (double)nref / 2.0);
+    const int G = d > 1 ? std::max(1, (int)std::sqrt(cells)) : (int)std::min<double>(cells, 1 << 30);
+    cudaError_t e = grow(&h->nn_scratch, &h->c_nn_scratch, vg::ordered_nn_scratch_bytes(nref, d, G));
+    if (e != cudaSuccess) return cuda_fail(e, "vecchia_nearest: allocating scratch");
+    e = vg::launch_ordered_nn(locs_ref, nref, d, m, G, h->nn_scratch, NNarray,
+                              reinterpret_cast<cudaStream_t>(stream), locs_query, nquery);
+    if (e != cudaSuccess) return cuda_fail(e, "vecchia_nearest: launching");
+    return VEC_OK;
+}
+
+vec_status vecchia_predict(vec_handle h, const double* locs, const double* y, const double* X,
+                           int64_t n, const double* beta, const double* locs_pred,
+                           const double* X_pred, const int32_t* NN_pred, int64_t npred, int d,
+                           int p, int m, const double* covparms, vec_covfun covfun, int latent,
+                           void* stream, double* mean, double* var, int64_t* dev_status) {
+    if (!h || !locs || !y || !X || !beta || !locs_pred || !X_pred || !covparms || !mean || !var ||
+        !dev_status || (m > 0 && !NN_pred))
+        return fail(VEC_ERR_ARG, "vecchia_predict: NULL argument");
+    if (vecchia_nparms(covfun) < 0) return fail(VEC_ERR_ARG, "unknown covariance function");
+    if (n < 1 || npred < 1 || d < 1 || d > vg::DMAX || (covfun == VEC_EXP_SPACETIME && d != 3) ||
+        p < 1 || p > vg::PMAX || m < 0 || m > vg::KMAX - 1 || npred > (int64_t)INT_MAX * 16)
+        return fail(VEC_ERR_ARG, "vecchia_predict: bad sizes (n %lld, npred %lld, d %d, p %d, m %d)",
+                    (long long)n, (long long)npred, d, p, m);
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(VEC_ERR_CUDA, "cannot select device %d", h->device);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = vg::launch_init_status(h->status, h->bad, st);
+    if (e == cudaSuccess && covfun == VEC_MATERN_ISO) e = vg::launch_mtab_build(covparms, h->mtab, nullptr, st);
+    if (e == cudaSuccess)
+        e = vg::launch_predict((int)covfun, locs, y, X, beta, n, locs_pred, X_pred, NN_pred, npred,
+                               d, p, m, covparms, h->mtab, latent ? 1 : 0, h->nsm, mean, var,
+                               h->status, h->bad, st);
+    if (e == cudaSuccess)
+        e = vg::launch_batch_status(h->status, h->bad, 1, reinterpret_cast<long long*>(dev_status), st);
+    if (e != cudaSuccess) return cuda_fail(e, "vecchia_predict: launching");
+    return VEC_OK;
+}
+
 vec_status vecchia_covariance_pairs(vec_handle h, vec_covfun covfun, const double* covparms,
                                     int d, int64_t npairs, const double* la, const double* lb,
                                     const int32_t* same, double* C, double* dC, void* stream) {

@@ -65,9 +65,18 @@ cudaError_t launch_choose_start(const double* theta0, const double* dflt, const 
                                 const long long* st0, const double* out1, const long long* st1,
                                 int nfields, int q, int nout, double* start, int* used,
                                 cudaStream_t st);
+// qx == nullptr: ordered search (candidates j < i, rows [i, neighbours]); else the m
+// nearest of the nq query locations qx among all n reference locations (rows of m).
 cudaError_t launch_ordered_nn(const double* x, long long n, int d, int m, int G, void* scratch,
-                              int32_t* NN, cudaStream_t st);
+                              int32_t* NN, cudaStream_t st, const double* qx = nullptr,
+                              long long nq = 0);
 size_t ordered_nn_scratch_bytes(long long n, int d, int G);
+cudaError_t launch_predict(int cov, const double* locs, const double* y, const double* X,
+                           const double* beta, long long n, const double* qlocs,
+                           const double* qX, const int32_t* NN, long long nq, int d, int p,
+                           int m, const double* covparms, const double* tab, int latent,
+                           int nsm, double* mean, double* var, int* status, long long* bad,
+                           cudaStream_t st);
 cudaError_t launch_sim_recur(const double* factor, const int32_t* NN, int n, int m, int nfields,
                             const double* z, double* y, cudaStream_t st);
 cudaError_t launch_batch_status(const int* status_b, const long long* bad_b, int nbatch,

@@ -1,7 +1,7 @@
-// vg_nn.cu -- ordered nearest-neighbour search on the device: for each observation i of an
+// vg_nn.cu -- nearest-neighbour search on the device: for each observation i of an
 // ordering, its m nearest among the observations 0..i-1 (the NNarray of Sec. 2.1 and
 // Algorithm 1's input; the paper computes it on the CPU and names a GPU version as future
-// work).
+// work); and, for prediction, the m nearest observations of each query location.
 //
 // Definition (exact): neighbours of i = the m smallest keys (d2(i, j), j) over j < i in
 // lexicographic order, d2 = sum over coordinates, in order, of (x_ik - x_jk)^2 in FP64 with
@@ -163,21 +163,26 @@ __device__ void nn_sort_cut(double* bd, int* bj, int& cnt, int m, int lane) {
     if (cnt > m) cnt = m;
 }
 
+// ordered = 1: queries are the reference points themselves, candidates j < i, rows
+// [i, neighbours] (m + 1 columns).  ordered = 0: queries qx (nq of them) against all n
+// reference points, rows [neighbours] (m columns).
 __global__ void __launch_bounds__(NN_WARPS * 32) k_nn_search(
     const double* __restrict__ x, long long n, int d, int m, const NNGrid* __restrict__ grid,
     const int* __restrict__ start, const int* __restrict__ items, long long brute_upto,
-    int32_t* __restrict__ NN) {
+    int32_t* __restrict__ NN, const double* __restrict__ qx, long long nq, int ordered) {
     __shared__ double s_d[NN_WARPS][NN_CAP];
     __shared__ int s_j[NN_WARPS][NN_CAP];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     double* bd = s_d[w];
     int* bj = s_j[w];
     const NNGrid g = *grid;
-    const int W = m + 1;
+    const int W = ordered ? m + 1 : m;
     const double hmin = fmin(g.hx, g.hy);
     const long long nw = (long long)gridDim.x * NN_WARPS;
-    for (long long i = blockIdx.x * (long long)NN_WARPS + w; i < n; i += nw) {
-        const double* xi = x + i * d;
+    const long long nquery = ordered ? n : nq;
+    for (long long i = blockIdx.x * (long long)NN_WARPS + w; i < nquery; i += nw) {
+        const double* xi = ordered ? x + i * d : qx + i * d;
+        const long long lim = ordered ? i : n;   // candidates j < lim
         int cnt = 0;
         double thr_d = INFINITY;   // key of the current m-th best (when cnt == m after a cut)
         int thr_j = INT_MAX;
@@ -198,11 +203,11 @@ __global__ void __launch_bounds__(NN_WARPS * 32) k_nn_search(
             cnt += __popc(mask);
             __syncwarp();
         };
-        if (m > 0 && i > 0) {
-            if (i <= brute_upto) {
-                for (long long j0 = 0; j0 < i; j0 += 32) {
+        if (m > 0 && lim > 0) {
+            if (lim <= brute_upto) {
+                for (long long j0 = 0; j0 < lim; j0 += 32) {
                     const long long j = j0 + lane;
-                    const bool valid = j < i;
+                    const bool valid = j < lim;
                     offer(valid, valid ? nn_d2(xi, x + j * d, d) : 0.0, (int)j);
                 }
             } else {
@@ -236,7 +241,7 @@ __global__ void __launch_bounds__(NN_WARPS * 32) k_nn_search(
                             bool valid = false;
                             if (more) {
                                 j = items[beg++];
-                                valid = j < i;
+                                valid = j < lim;
                                 if (valid) d2 = nn_d2(xi, x + (long long)j * d, d);
                             }
                             offer(valid, d2, j);
@@ -256,14 +261,18 @@ __global__ void __launch_bounds__(NN_WARPS * 32) k_nn_search(
             nn_sort_cut(bd, bj, cnt, m, lane);
         }
         int32_t* row = NN + i * W;
-        for (int k = lane; k < W; k += 32)
-            row[k] = k == 0 ? (int32_t)i : (k - 1 < cnt ? (int32_t)bj[k - 1] : -1);
+        if (ordered) {
+            for (int k = lane; k < W; k += 32)
+                row[k] = k == 0 ? (int32_t)i : (k - 1 < cnt ? (int32_t)bj[k - 1] : -1);
+        } else {
+            for (int k = lane; k < W; k += 32) row[k] = k < cnt ? (int32_t)bj[k] : -1;
+        }
         __syncwarp();
     }
 }
 
 cudaError_t launch_ordered_nn(const double* x, long long n, int d, int m, int G, void* scratch,
-                              int32_t* NN, cudaStream_t st) {
+                              int32_t* NN, cudaStream_t st, const double* qx, long long nq) {
     // scratch layout: NNGrid | cell[n] | count[G*G] | start[G*G+1] | cursor[G*G] | items[n]
     char* p = static_cast<char*>(scratch);
     NNGrid* grid = reinterpret_cast<NNGrid*>(p);
@@ -281,11 +290,13 @@ cudaError_t launch_ordered_nn(const double* x, long long n, int d, int m, int G,
     k_nn_cells<<<blocks, 256, 0, st>>>(x, n, d, grid, cell, count);
     k_nn_scan<<<1, 1024, 0, st>>>(count, (int)nc, start, cursor);
     k_nn_scatter<<<blocks, 256, 0, st>>>(cell, n, cursor, items);
-    // brute force while the earlier points are few: below sqrt(m n) it is cheaper than rings
+    // brute force while the candidates are few: below sqrt(m n) it is cheaper than rings
     const long long brute = (long long)std::max(2.0 * m, std::sqrt((double)m * (double)n));
-    const long long sblocks = (n + NN_WARPS - 1) / NN_WARPS;
+    const int ordered = qx ? 0 : 1;
+    const long long nquery = ordered ? n : nq;
+    const long long sblocks = (nquery + NN_WARPS - 1) / NN_WARPS;
     k_nn_search<<<(unsigned)(sblocks < 65535LL * 8 ? sblocks : 65535LL * 8), NN_WARPS * 32, 0, st>>>(
-        x, n, d, m, grid, start, items, brute, NN);
+        x, n, d, m, grid, start, items, brute, NN, qx, nq, ordered);
     return cudaGetLastError();
 }
 
