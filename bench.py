@@ -20,7 +20,8 @@ Reported beside the device-timed value:
                   batched Fisher-scoring fits vs 256 sequential device fits;
   * warm_start -- fits of held-out fields (n = 200000) from the default start and from
                   the learned start;
-  * nn_search  -- the ordered nearest-neighbour search on the device vs the CPU search.
+  * nn_search  -- the ordered nearest-neighbour search on the device vs the CPU search;
+  * prediction -- Vecchia prediction at 100000 new sites of the headline field.
 ``--impl reference`` times the CPU oracle itself as the reference arm.
 Multi-GPU runs (torchrun) are independent replicas: each rank evaluates its own copy.
 """
@@ -405,6 +406,51 @@ def run_nn_search(vg, torch, dev, stream) -> dict:
     return res
 
 
+def run_prediction(vg, torch, dev, stream, w) -> dict:
+    """Vecchia prediction on the headline field (n = 1e5, m = 30, Matern) at 100 000 new
+    uniform sites: the neighbour search for the queries and the prediction, each timed with
+    CUDA events (median of 3), against the CPU oracle on a sample of targets."""
+    import oracle
+    from oracle import predict as op
+    rng = np.random.default_rng(1009)
+    npred = 100000
+    Lp = rng.uniform(size=(npred, 2))
+    Xp = np.column_stack([np.ones(npred), Lp])
+    beta = np.array([1.0, 0.5, -0.5])
+    t = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)  # noqa
+    locs, y, X, th = t(w.locs), t(w.y), t(w.X), t(w.theta_true)
+    dLp, dXp, dbeta = t(Lp), t(Xp), t(beta)
+    NN = vg.vecchia_nearest(locs, dLp, 30, stream=stream)
+    vg.vecchia_predict(locs, y, X, dbeta, dLp, dXp, NN, th, w.covfun, stream=stream)
+    nn_ms, pr_ms = [], []
+    for _ in range(3):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        NN = vg.vecchia_nearest(locs, dLp, 30, stream=stream)
+        e1.record(stream)
+        mean, var, st = vg.vecchia_predict(locs, y, X, dbeta, dLp, dXp, NN, th, w.covfun,
+                                           stream=stream)
+        e2.record(stream)
+        e2.synchronize()
+        nn_ms.append(e0.elapsed_time(e1))
+        pr_ms.append(e1.elapsed_time(e2))
+    oracle.build()
+    sel = np.arange(0, npred, 100)
+    t0 = time.perf_counter()
+    mo, vo = op.predict(w.locs, w.y, w.X, beta, Lp[sel], Xp[sel], NN.cpu().numpy()[sel],
+                        w.theta_true, w.covfun)
+    cpu_s = time.perf_counter() - t0
+    mg, vgv = mean.cpu().numpy()[sel], var.cpu().numpy()[sel]
+    return {"targets": npred, "m": 30, "status": int(st[0]),
+            "nearest_ms": statistics.median(nn_ms), "predict_ms": statistics.median(pr_ms),
+            "value": npred / (statistics.median(pr_ms) * 1e-3), "unit": "targets/s",
+            "cpu_oracle": {"value": len(sel) / cpu_s, "unit": "targets/s",
+                           "sample": "%d targets (every 100th)" % len(sel),
+                           "kind": "oracle (numpy dense solve per target)"},
+            "max_rel_diff_vs_oracle": {"mean": float(np.max(np.abs(mg - mo) / np.maximum(np.abs(mo), 1e-300))),
+                                       "var": float(np.max(np.abs(vgv - vo) / vo))}}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -563,6 +609,7 @@ def run_ours(args):
     batched = run_batched(vg, torch, dev, stream, args.steps, args.warmup, flush, local)
     warm = run_warm_start(torch, dev, local)
     nn = run_nn_search(vg, torch, dev, stream)
+    pred = run_prediction(vg, torch, dev, stream, w)
 
     if rank != 0:
         if ws > 1:
@@ -630,6 +677,7 @@ def run_ours(args):
         "batched": batched,
         "warm_start": warm,
         "nn_search": nn,
+        "prediction": pred,
     }
     print(json.dumps(line))
     if ws > 1:
