@@ -12,7 +12,8 @@ Every function follows the paper (James & Guinness, arXiv 2407.02740):
     loglikelihood, gradient and Fisher information.
   * ``loglik_grad_info``     -- both of the above.
   * ``fisher_fit``           -- Fisher scoring, Eq. 4, on log-parameters.
-  * ``cov_pairs``            -- the covariance functions of Sec. 4.3 (Eq. 6) and Matern.
+  * ``cov_pairs``            -- the covariance functions of Sec. 4.3 (Eq. 6: isotropic, and
+    with one range per coordinate) and Matern.
 """
 from __future__ import annotations
 
@@ -26,8 +27,19 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "vecchia_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
-EXP_ISO, MATERN_ISO, EXP_SPACETIME = 0, 1, 2
-NPARMS = {EXP_ISO: 3, MATERN_ISO: 4, EXP_SPACETIME: 4}
+EXP_ISO, MATERN_ISO, EXP_SPACETIME, EXP_ANISO = 0, 1, 2, 3
+NPARMS = {EXP_ISO: 3, MATERN_ISO: 4, EXP_SPACETIME: 4}   # families with a fixed count
+DMAX_ANISO = 20
+
+
+def nparms(covfun: int, d: int) -> int:
+    """Number of covariance parameters of a family in d dimensions: the anisotropic
+    exponential has one range per coordinate, theta = (sigma2, rho_1..rho_d, tau2)."""
+    if covfun == EXP_ANISO:
+        if not 1 <= d <= DMAX_ANISO:
+            raise ValueError("anisotropic exponential: d must be in [1, %d]" % DMAX_ANISO)
+        return d + 2
+    return NPARMS[covfun]
 STATUS = {0: "ok", 1: "bad argument", 2: "not positive definite", 3: "non-finite",
           4: "out of memory"}
 
@@ -57,6 +69,7 @@ def _load():
         lib = ctypes.CDLL(build())
         P, i64, ci, cd = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
         lib.orc_nparms.argtypes = [ci]
+        lib.orc_nparms_d.argtypes = [ci, ci]
         lib.orc_stats_len.argtypes = [ci, ci]
         lib.orc_cov_pairs.argtypes = [ci, ci, P, i64, P, P, P, P, P]
         lib.orc_psi.argtypes = [cd]
@@ -68,7 +81,7 @@ def _load():
                                              P, ci]
         lib.orc_fisher_fit.argtypes = [P, P, P, P, i64, ci, ci, ci, ci, P, cd, ci, P, P, P, P,
                                        P, P, P, ci]
-        for f in (lib.orc_nparms, lib.orc_stats_len, lib.orc_cov_pairs, lib.orc_vecchia_stats,
+        for f in (lib.orc_nparms, lib.orc_nparms_d, lib.orc_stats_len, lib.orc_cov_pairs, lib.orc_vecchia_stats,
                   lib.orc_vecchia_records, lib.orc_profile, lib.orc_loglik_grad_info,
                   lib.orc_fisher_fit):
             f.restype = ci
@@ -121,7 +134,7 @@ def cov_pairs(covfun, theta, la, lb, same):
     same = np.ascontiguousarray(same, dtype=np.int32)
     theta = np.ascontiguousarray(theta, dtype=np.float64)
     npairs, d = la.shape
-    q = NPARMS[covfun]
+    q = nparms(covfun, d)
     C = np.empty(npairs)
     dC = np.empty((npairs, q))
     rc = _load().orc_cov_pairs(covfun, d, _p(theta), npairs, _p(la), _p(lb), _p(same), _p(C),
@@ -139,7 +152,7 @@ def stats(locs, y, X, NN, theta, covfun, nthreads: int = 0):
     """Summed Algorithm 1 record.  Returns (record, bad_index)."""
     locs, y, X, NN, n, d, p, m = _inputs(locs, y, X, NN)
     theta = np.ascontiguousarray(theta, dtype=np.float64)
-    q = NPARMS[covfun]
+    q = nparms(covfun, d)
     out = np.empty(stats_len(p, q))
     bad = ctypes.c_int64(-1)
     rc = _load().orc_vecchia_stats(_p(locs), _p(y), _p(X), _p(NN), n, d, p, m, _p(theta),
@@ -155,7 +168,7 @@ def records(locs, y, X, NN, theta, covfun):
     """Per-observation Algorithm 1 records (n x S), for tiny inputs."""
     locs, y, X, NN, n, d, p, m = _inputs(locs, y, X, NN)
     theta = np.ascontiguousarray(theta, dtype=np.float64)
-    q = NPARMS[covfun]
+    q = nparms(covfun, d)
     out = np.empty((n, stats_len(p, q)))
     rc = _load().orc_vecchia_records(_p(locs), _p(y), _p(X), _p(NN), n, d, p, m, _p(theta),
                                      covfun, _p(out))
@@ -180,7 +193,7 @@ def loglik_grad_info(locs, y, X, NN, theta, covfun, nthreads: int = 0):
     """Profiled-beta Vecchia loglikelihood, gradient, Fisher information and betahat."""
     locs, y, X, NN, n, d, p, m = _inputs(locs, y, X, NN)
     theta = np.ascontiguousarray(theta, dtype=np.float64)
-    q = NPARMS[covfun]
+    q = nparms(covfun, d)
     ll = ctypes.c_double()
     grad = np.empty(q)
     info = np.empty((q, q))
@@ -202,7 +215,7 @@ def fisher_fit(locs, y, X, NN, covfun, start, tol: float = 1e-4, maxit: int = 40
     """Fisher scoring on log theta (Eq. 4) with step halving; see the C file for rules."""
     locs, y, X, NN, n, d, p, m = _inputs(locs, y, X, NN)
     start = np.ascontiguousarray(start, dtype=np.float64)
-    q = NPARMS[covfun]
+    q = nparms(covfun, d)
     theta = np.empty(q)
     beta = np.empty(p)
     ll = ctypes.c_double()

@@ -18,7 +18,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import NPARMS, cov_pairs
+from . import cov_pairs, nparms
 
 
 def _cov_matrix(covfun, theta, pts):
@@ -39,7 +39,7 @@ def factor_rows(locs, NN, theta, covfun):
     NN = np.asarray(NN)
     n, W = NN.shape
     theta = np.asarray(theta, dtype=np.float64)
-    assert len(theta) == NPARMS[covfun]
+    assert len(theta) == nparms(covfun, locs.shape[1] if locs.ndim == 2 else 1)
     B = np.zeros((n, W))
     for i in range(n):
         nb = [int(j) for j in NN[i, 1:] if j >= 0]

@@ -19,7 +19,9 @@
  *     loglikelihood, gradient and Fisher information.
  *   - Eq. 4: Fisher scoring, run on log-parameters with step halving.
  *   - Sec. 4.3, Eq. 5-6: the exponential covariance with a relative nugget
- *     sigma^2 tau^2, plus the isotropic Matern family and a space-time exponential.
+ *     sigma^2 tau^2 -- isotropic, and with one range per coordinate (the form fitted to
+ *     the Elevators attributes, q = d + 2) -- plus the isotropic Matern family and a
+ *     space-time exponential.
  *
  * Derivation of the elided terms (per observation, block of size K = k+1 with the
  * observation itself last, L = chol(Sigma_block)):
@@ -54,6 +56,10 @@
 #define ORC_EXP_ISO 0       /* theta = (sigma2, rho, tau2)          Eq. 6, isotropic      */
 #define ORC_MATERN_ISO 1    /* theta = (sigma2, rho, nu, tau2)      Matern, x = r/rho     */
 #define ORC_EXP_SPACETIME 2 /* theta = (sigma2, rho_s, rho_t, tau2) d = 3: (lon, lat, t)  */
+#define ORC_EXP_ANISO 3     /* theta = (sigma2, rho_1..rho_d, tau2), Eq. 6 with one range
+                               per coordinate; 1 <= d <= ORC_DMAX_ANISO                   */
+#define ORC_DMAX_ANISO 20
+#define ORC_QMAX (ORC_DMAX_ANISO + 2)
 
 #define ORC_OK 0
 #define ORC_ERR_ARG 1
@@ -63,15 +69,21 @@
 
 #define ORC_CHUNK 256
 
-int orc_nparms(int covfun)
+/* Number of covariance parameters of a family in d dimensions (-1: unknown family, or a
+ * dimension the family does not take). */
+int orc_nparms_d(int covfun, int d)
 {
     switch (covfun) {
     case ORC_EXP_ISO: return 3;
     case ORC_MATERN_ISO: return 4;
     case ORC_EXP_SPACETIME: return 4;
+    case ORC_EXP_ANISO: return (d >= 1 && d <= ORC_DMAX_ANISO) ? d + 2 : -1;
     default: return -1;
     }
 }
+
+/* The same for the families whose parameter count does not depend on d. */
+int orc_nparms(int covfun) { return covfun == ORC_EXP_ANISO ? -1 : orc_nparms_d(covfun, 1); }
 
 /* Number of doubles in one Algorithm 1 record:
  * logdet, ySy, XSX[p][p], ySX[p], dlogdet[q], dySy[q], dXSX[q][p][p], dySX[q][p], ainfo[q][q] */
@@ -147,16 +159,18 @@ static void matern_eval(double nu, double x, double lg_nu, double psi_nu,
  * dC must hold nparms(covfun) values. */
 typedef struct {
     int covfun, d;
-    double th[4];
+    int q;
+    double th[ORC_QMAX];
     double lg_nu, psi_nu; /* Matern only: log Gamma(nu), digamma(nu) */
 } orc_cov;
 
 static int orc_cov_init(orc_cov* cv, int covfun, int d, const double* theta)
 {
-    int q = orc_nparms(covfun);
+    int q = orc_nparms_d(covfun, d);
     if (q < 0) return ORC_ERR_ARG;
     cv->covfun = covfun;
     cv->d = d;
+    cv->q = q;
     for (int j = 0; j < q; j++) {
         if (!(theta[j] > 0.0) || !isfinite(theta[j])) return ORC_ERR_ARG;
         cv->th[j] = theta[j];
@@ -237,6 +251,29 @@ static double orc_cov_eval(const orc_cov* cv, const double* la, const double* lb
         }
         break;
     }
+    case ORC_EXP_ANISO: { /* sigma2 exp(-sqrt(sum_k (dz_k / rho_k)^2)) + [same] sigma2 tau2 */
+        double D2 = 0.0;
+        for (int k = 0; k < d; k++) {
+            double u = (la[k] - lb[k]) / t[1 + k];
+            D2 += u * u;
+        }
+        double D = sqrt(D2);
+        double e = exp(-D);
+        C = t[0] * e;
+        dC[0] = e;
+        /* dD/drho_k = -(dz_k / rho_k)^2 / (rho_k D), so dC/drho_k = sigma2 e u_k^2 / (rho_k D) */
+        for (int k = 0; k < d; k++) {
+            double u = (la[k] - lb[k]) / t[1 + k];
+            dC[1 + k] = (D > 0.0) ? t[0] * e * u * u / (t[1 + k] * D) : 0.0;
+        }
+        dC[d + 1] = 0.0;
+        if (same) {
+            C += t[0] * t[d + 1];
+            dC[0] += t[d + 1];
+            dC[d + 1] = t[0];
+        }
+        break;
+    }
     }
     return C;
 }
@@ -249,7 +286,7 @@ int orc_cov_pairs(int covfun, int d, const double* theta, int64_t npairs, const 
     orc_cov cv;
     int st = orc_cov_init(&cv, covfun, d, theta);
     if (st) return st;
-    int q = orc_nparms(covfun);
+    int q = cv.q;
     for (int64_t i = 0; i < npairs; i++)
         C[i] = orc_cov_eval(&cv, la + i * d, lb + i * d, same[i], dC + i * q);
     return ORC_OK;
@@ -341,7 +378,7 @@ static int one_point(const orc_cov* cv, const double* locs, const double* y, con
     }
 
     /* covariance matrix and its derivatives (full symmetric storage) */
-    double dC[4];
+    double dC[ORC_QMAX];
     for (int a = 0; a < K; a++) {
         for (int b = 0; b <= a; b++) {
             double C = orc_cov_eval(cv, w->locsub + a * d, w->locsub + b * d, a == b, dC);
@@ -464,7 +501,7 @@ int orc_vecchia_stats(const double* locs, const double* y, const double* X, cons
     orc_cov cv;
     int st = orc_cov_init(&cv, covfun, d, theta);
     if (st) return st;
-    const int q = orc_nparms(covfun);
+    const int q = cv.q;
     const int S = orc_stats_len(p, q);
     const int64_t nchunk = (n + ORC_CHUNK - 1) / ORC_CHUNK;
     double* csum = (double*)calloc((size_t)nchunk * S * 2, sizeof(double));
@@ -534,7 +571,7 @@ int orc_vecchia_records(const double* locs, const double* y, const double* X, co
     orc_cov cv;
     int st = orc_cov_init(&cv, covfun, d, theta);
     if (st) return st;
-    const int q = orc_nparms(covfun);
+    const int q = cv.q;
     const int S = orc_stats_len(p, q);
     orc_work w;
     if (work_alloc(&w, m + 1, d, p, q)) return ORC_ERR_NOMEM;
@@ -620,7 +657,7 @@ int orc_loglik_grad_info(const double* locs, const double* y, const double* X,
                          int covfun, double* loglik, double* grad, double* info,
                          double* betahat, int64_t* bad_index, int nthreads)
 {
-    int q = orc_nparms(covfun);
+    int q = orc_nparms_d(covfun, d);
     if (q < 0 || p < 1 || p > 64) return ORC_ERR_ARG;
     double* stats = (double*)malloc(sizeof(double) * orc_stats_len(p, q));
     if (!stats) return ORC_ERR_NOMEM;
@@ -651,9 +688,9 @@ int orc_fisher_fit(const double* locs, const double* y, const double* X, const i
                    int maxit, double* theta_out, double* betahat, double* loglik, double* grad,
                    double* info, int* iters, int* status, int nthreads)
 {
-    int q = orc_nparms(covfun);
+    int q = orc_nparms_d(covfun, d);
     if (q < 0) return ORC_ERR_ARG;
-    double th[4], ll, g[4], I[16], bh[64];
+    double th[ORC_QMAX], ll, g[ORC_QMAX], I[ORC_QMAX * ORC_QMAX], bh[64];
     for (int j = 0; j < q; j++) th[j] = start[j];
     int64_t bad;
     int st = orc_loglik_grad_info(locs, y, X, NN, n, d, p, m, th, covfun, &ll, g, I, bh, &bad,
@@ -662,7 +699,7 @@ int orc_fisher_fit(const double* locs, const double* y, const double* X, const i
     int it = 0;
     *status = 1;
     for (;;) {
-        double gt[4], It[16], delta[4];
+        double gt[ORC_QMAX], It[ORC_QMAX * ORC_QMAX], delta[ORC_QMAX];
         for (int j = 0; j < q; j++) gt[j] = th[j] * g[j];
         for (int j = 0; j < q; j++)
             for (int l = 0; l < q; l++) It[j * q + l] = th[j] * I[j * q + l] * th[l];
@@ -670,7 +707,7 @@ int orc_fisher_fit(const double* locs, const double* y, const double* X, const i
         for (int j = 0; j < q; j++) maxd = fmax(maxd, It[j * q + j]);
         int ok = -1;
         for (int r = 0; r < 9 && ok; r++) {
-            double A[16];
+            double A[ORC_QMAX * ORC_QMAX];
             for (int t = 0; t < q * q; t++) A[t] = It[t];
             for (int j = 0; j < q; j++) A[j * q + j] += r * 1e-4 * maxd;
             ok = small_chol_solve(q, A, gt, delta);
@@ -682,7 +719,7 @@ int orc_fisher_fit(const double* locs, const double* y, const double* X, const i
         if (it >= maxit) { *status = 1; break; }
         int accepted = 0;
         for (int h = 0; h <= 10 && !accepted; h++) {
-            double tn[4], lln, gn[4], In[16], bhn[64];
+            double tn[ORC_QMAX], lln, gn[ORC_QMAX], In[ORC_QMAX * ORC_QMAX], bhn[64];
             double scale = ldexp(1.0, -h);
             for (int j = 0; j < q; j++) tn[j] = th[j] * exp(delta[j] * scale);
             if (covfun == ORC_MATERN_ISO) tn[2] = fmin(20.0, fmax(0.05, tn[2]));

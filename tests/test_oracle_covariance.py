@@ -131,6 +131,67 @@ def test_spacetime_values_and_fd_derivatives():
     assert dC[0, 1] == 0.0 and dC[0, 2] == 0.0
 
 
+ANI = oracle.EXP_ANISO
+
+
+def test_anisotropic_values_and_fd_derivatives():
+    d = 5
+    theta = np.array([1.4, 0.3, 0.7, 1.1, 2.5, 0.45, 0.08])
+    rng = np.random.default_rng(11)
+    la = rng.uniform(0, 2, size=(15, d))
+    lb = la + rng.normal(0, 0.5, size=(15, d))
+    lb[0] = la[0]                                      # coincident pair (off-diagonal)
+    same = np.zeros(15, np.int32)
+    C, dC = oracle.cov_pairs(ANI, theta, la, lb, same)
+    D = np.sqrt((((la - lb) / theta[1:-1]) ** 2).sum(1))
+    assert np.allclose(C, 1.4 * np.exp(-D), rtol=1e-14)
+    assert np.allclose(dC[:, 0], np.exp(-D), rtol=1e-14)
+    for j in range(1, d + 1):
+        h = 1e-6 * theta[j]
+        tp, tm = theta.copy(), theta.copy()
+        tp[j] += h
+        tm[j] -= h
+        fd = (oracle.cov_pairs(ANI, tp, la, lb, same)[0]
+              - oracle.cov_pairs(ANI, tm, la, lb, same)[0]) / (2 * h)
+        # central-difference rounding: ~1e-16 C / h absolute
+        assert np.allclose(dC[:, j], fd, rtol=1e-7, atol=1e-9)
+    assert np.all(dC[0, 1:] == 0.0) and np.all(dC[:, d + 1] == 0.0)
+    # the diagonal: nugget sigma2 tau2, d/dsigma2 = 1 + tau2, d/dtau2 = sigma2
+    C, dC = oracle.cov_pairs(ANI, theta, la[:1], la[:1], np.ones(1, np.int32))
+    assert C[0] == pytest.approx(1.4 * 1.08, rel=1e-15)
+    assert dC[0, 0] == pytest.approx(1.08, rel=1e-15) and dC[0, d + 1] == pytest.approx(1.4)
+
+
+def test_anisotropic_reduces_to_isotropic_and_spacetime():
+    rng = np.random.default_rng(12)
+    la, lb = rng.uniform(size=(20, 3)), rng.uniform(size=(20, 3))
+    same = np.zeros(20, np.int32)
+    # equal ranges: the isotropic exponential; the range derivatives sum to d C/d rho
+    Ca, dCa = oracle.cov_pairs(ANI, np.array([1.2, 0.3, 0.3, 0.3, 0.05]), la, lb, same)
+    Ci, dCi = oracle.cov_pairs(EXP, np.array([1.2, 0.3, 0.05]), la, lb, same)
+    assert np.allclose(Ca, Ci, rtol=1e-14)
+    assert np.allclose(dCa[:, 1:4].sum(1), dCi[:, 1], rtol=1e-13)
+    # rho_1 = rho_2: the space-time exponential (space = first two coordinates)
+    Ca, dCa = oracle.cov_pairs(ANI, np.array([0.9, 0.4, 0.4, 0.7, 0.1]), la, lb, same)
+    Cs, dCs = oracle.cov_pairs(ST, np.array([0.9, 0.4, 0.7, 0.1]), la, lb, same)
+    assert np.allclose(Ca, Cs, rtol=1e-14)
+    assert np.allclose(dCa[:, 1] + dCa[:, 2], dCs[:, 1], rtol=1e-13)
+    assert np.allclose(dCa[:, 3], dCs[:, 2], rtol=1e-13)
+
+
+def test_anisotropic_parameter_count():
+    assert oracle.nparms(ANI, 18) == 20
+    assert oracle._load().orc_nparms_d(ANI, 18) == 20       # noqa: SLF001
+    assert oracle._load().orc_nparms_d(ANI, 21) == -1       # noqa: SLF001
+    assert oracle._load().orc_nparms(ANI) == -1             # noqa: SLF001
+    with pytest.raises(ValueError):
+        oracle.nparms(ANI, 21)
+    la = np.zeros((1, 4))
+    with pytest.raises(oracle.OracleError):
+        oracle.cov_pairs(ANI, np.array([1.0, 0.1, -0.2, 0.1, 0.3, 0.01]), la, la,
+                         np.ones(1, np.int32))
+
+
 def test_invalid_parameters_rejected():
     la = np.zeros((1, 2))
     with pytest.raises(oracle.OracleError):

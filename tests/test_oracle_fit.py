@@ -9,12 +9,13 @@ import scipy.optimize as so
 import oracle
 import workloads
 
-EXP, MAT = oracle.EXP_ISO, oracle.MATERN_ISO
+EXP, MAT, ANI = oracle.EXP_ISO, oracle.MATERN_ISO, oracle.EXP_ANISO
 
 
 @pytest.mark.parametrize("covfun,theta,start", [
     (EXP, [1.0, 0.1, 0.05], [0.5, 0.3, 0.2]),
     (MAT, [1.5, 0.08, 1.2, 0.05], [1.0, 0.15, 1.0, 0.1]),
+    (ANI, [1.0, 0.1, 0.3, 0.8, 0.05], [0.6, 0.2, 0.2, 0.2, 0.2]),
 ])
 def test_fisher_scoring_reaches_the_optimum(covfun, theta, start):
     w = workloads.make_field(500, covfun, theta, 10, p=2, seed=17, sim="dense",

@@ -20,6 +20,7 @@ import oracle
 import workloads
 
 EXP, MAT, ST = oracle.EXP_ISO, oracle.MATERN_ISO, oracle.EXP_SPACETIME
+ANI = oracle.EXP_ANISO
 
 
 def dense_cov(covfun, theta, locs):
@@ -84,6 +85,8 @@ CASES = [
     (MAT, [2.0, 0.05, 1.5, 0.05], 3),
     (MAT, [1.0, 0.2, 2.7, 0.01], 1),
     (ST, [1.0, 0.3, 0.5, 0.1], 2),
+    (ANI, [1.2, 0.3, 0.6, 1.0, 0.05], 1),
+    (ANI, [1.0, 0.2, 0.4, 0.6, 0.8, 1.0, 1.5, 0.1], 2),
 ]
 
 
@@ -134,7 +137,7 @@ def test_gradient_matches_finite_differences_of_implied_density(covfun, theta, p
     assert np.linalg.norm(o["grad"] - fd) <= 1e-6 * scale
 
 
-@pytest.mark.parametrize("covfun,theta,p", CASES[:4])
+@pytest.mark.parametrize("covfun,theta,p", CASES[:4] + CASES[-2:])
 def test_per_point_info_is_block_minus_neighbour_information(covfun, theta, p):
     n, m = 25, 6
     w = small_case(covfun, n, m, p, seed=3, theta=theta)

@@ -22,6 +22,9 @@ Workloads (the recipes stand in for the paper's datasets, which are not availabl
 * ``cfg_swath_1m2``  -- 16 time slices x 8 swath bands x 9375 points = 1.2M points
   (lon, lat, time); space-time exponential (1, 5 deg, 2 slices, 0.1); X = [1, lat];
   sequential draw with m = 40; fit with m = 30.  Stands in for "Jason-3 + Time" (Table 2).
+* ``cfg_elevators_like`` -- n = 15000 points with 18 N(0,1) attributes as locations,
+  exponential with one range per attribute (log-spaced 1..30), X = 1; sequential draw
+  with m = 30; fit with m = 10 or 30.  Stands in for Elevators (Table 2).
 """
 from __future__ import annotations
 
@@ -39,6 +42,7 @@ _LIB = os.path.join(_HERE, "libprep.so")
 EXP_ISO = 0
 MATERN_ISO = 1
 EXP_SPACETIME = 2
+EXP_ANISO = 3          # one range per coordinate: theta = (sigma2, rho_1..rho_d, tau2)
 NPARMS = {EXP_ISO: 3, MATERN_ISO: 4, EXP_SPACETIME: 4}
 
 
@@ -81,11 +85,12 @@ def _ptr(a: np.ndarray):
 
 
 def maxmin_order(x: np.ndarray, brute: bool = False) -> np.ndarray:
-    """Exact maxmin ordering of the rows of x (n x d, d <= 3); returns original indices."""
+    """Exact maxmin ordering of the rows of x (n x d); returns original indices.  More
+    than 3 coordinates always take the O(n^2 d) search."""
     x = np.ascontiguousarray(x, dtype=np.float64)
     n, d = x.shape
     out = np.empty(n, dtype=np.int64)
-    f = _load().prep_maxmin_brute if brute else _load().prep_maxmin
+    f = _load().prep_maxmin_brute if (brute or d > 3) else _load().prep_maxmin
     rc = f(_ptr(x), n, d, _ptr(out))
     if rc != 0:
         raise RuntimeError("maxmin ordering failed (code %d)" % rc)
@@ -97,7 +102,7 @@ def ordered_nn(x: np.ndarray, m: int, brute: bool = False) -> np.ndarray:
     x = np.ascontiguousarray(x, dtype=np.float64)
     n, d = x.shape
     out = np.empty((n, m + 1), dtype=np.int32)
-    f = _load().prep_ordered_nn_brute if brute else _load().prep_ordered_nn
+    f = _load().prep_ordered_nn_brute if (brute or d > 3) else _load().prep_ordered_nn
     rc = f(_ptr(x), n, d, m, _ptr(out))
     if rc != 0:
         raise RuntimeError("ordered NN failed (code %d)" % rc)
@@ -110,6 +115,9 @@ def ordered_nn(x: np.ndarray, m: int, brute: bool = False) -> np.ndarray:
 def _gen_corr(covfun: int, theta, la: np.ndarray, lb: np.ndarray) -> np.ndarray:
     """Correlation (without sigma2 and nugget) between location arrays la, lb (..., d)."""
     diff = la - lb
+    if covfun == EXP_ANISO:
+        rho = np.asarray(theta[1:-1], dtype=np.float64)
+        return np.exp(-np.sqrt(np.sum((diff / rho) ** 2, axis=-1)))
     if covfun == EXP_SPACETIME:
         D = np.sqrt((diff[..., 0] ** 2 + diff[..., 1] ** 2) / theta[1] ** 2
                     + diff[..., 2] ** 2 / theta[2] ** 2)
@@ -161,6 +169,10 @@ def simulate_sequential(covfun, theta, locs, NN, rng, chunk: int = 2048) -> np.n
     th = np.asarray(theta, dtype=np.float64)
     if covfun == EXP_ISO:
         kind, thc = 0, th[[0, 1, 2]]
+    elif covfun == EXP_ANISO:
+        # the exponential on coordinates divided by their ranges
+        locs = np.asarray(locs, dtype=np.float64) / th[1:-1]
+        kind, thc = 0, np.array([th[0], 1.0, th[-1]])
     elif covfun == EXP_SPACETIME:
         kind, thc = 3, th
     elif covfun == MATERN_ISO and float(th[2]) in (0.5, 1.5, 2.5):
@@ -249,14 +261,19 @@ def _finish(name, covfun, locs, y, X, m, theta_true, theta_start, NN=None, **met
 def make_field(n: int, covfun: int, theta, m: int, p: int = 1, seed: int = 0,
                sim: str = "dense", m_sim: int | None = None, d: int = 2,
                beta=None, ordering: str = "maxmin", name: str = "field") -> Workload:
-    """Generic seeded field in [0,1]^d (d=3 for the space-time covariance), used by tests.
+    """Generic seeded field in [0,1]^d (d=3 for the space-time covariance, d = len(theta)-2
+    for the anisotropic exponential, whose ordering and neighbours are taken on the
+    coordinates divided by the ranges), used by tests.
     X columns: 1, then the first p-1 coordinates.  sim = 'dense' or 'sequential'."""
     rng = np.random.default_rng(seed)
     if covfun == EXP_SPACETIME:
         d = 3
+    if covfun == EXP_ANISO:
+        d = len(theta) - 2
+    scale = (1.0 / np.asarray(theta[1:-1], dtype=np.float64)) if covfun == EXP_ANISO else 1.0
     locs = rng.uniform(0.0, 1.0, size=(n, d))
     if ordering == "maxmin":
-        locs = locs[maxmin_order(locs)]
+        locs = locs[maxmin_order(locs * scale)]
     X = np.ones((n, p))
     for c in range(1, p):
         X[:, c] = locs[:, (c - 1) % d]
@@ -266,10 +283,10 @@ def make_field(n: int, covfun: int, theta, m: int, p: int = 1, seed: int = 0,
         e = simulate_dense(covfun, theta, locs, rng)
     else:
         ms = m if m_sim is None else m_sim
-        e = simulate_sequential(covfun, theta, locs, ordered_nn(locs, ms), rng)
+        e = simulate_sequential(covfun, theta, locs, ordered_nn(locs * scale, ms), rng)
     y = X @ beta + e
     start = theta.copy()
-    return _finish(name, covfun, locs, y, X, m, theta, start, seed=seed)
+    return _finish(name, covfun, locs, y, X, m, theta, start, seed=seed, nn_coords=locs * scale)
 
 
 def cfg_small_exp(seed: int = 1001) -> Workload:
@@ -339,6 +356,37 @@ def cfg_swath_1m2(seed: int = 1003, slices: int = 16, bands: int = 8, per: int =
     NN = np.ascontiguousarray(NNs[:, : m + 1]) if m <= m_sim else ordered_nn(scaled, m)
     start = np.array([np.var(y), 10.0, 4.0, 0.1])
     return _finish("swath_n%d_m%d" % (locs.shape[0], m), EXP_SPACETIME, locs, y, X, m, theta,
+                   start, NN=NN, seed=seed, m_sim=m_sim)
+
+
+def elevators_ranges(d: int = 18) -> np.ndarray:
+    """Ranges of the Elevators-like field: log-spaced from 1 to 30, so that a few
+    attributes carry most of the dependence and the rest are nearly irrelevant."""
+    return np.exp(np.linspace(np.log(1.0), np.log(30.0), d))
+
+
+def cfg_elevators_like(seed: int = 1005, n: int = 15000, d: int = 18, m: int = 30,
+                       m_sim: int = 30) -> Workload:
+    """Stands in for the Elevators runs (n = 15k training points, 18 attributes used as
+    locations, exponential covariance with one range per attribute, X = 1): attributes
+    i.i.d. N(0, 1) (standardised), theta = (1, ranges, 0.1), sequential draw with
+    m_sim = 30, beta = 0.5.  Ordering and neighbours are taken on the attributes divided
+    by the true ranges.  The fit starts from (var y, 2, ..., 2, 0.2)."""
+    rng = np.random.default_rng(seed)
+    rho = elevators_ranges(d)
+    theta = np.concatenate([[1.0], rho, [0.1]])
+    locs = rng.standard_normal((n, d))
+    scaled = locs / rho
+    order = maxmin_order(scaled)
+    locs = locs[order]
+    scaled = scaled[order]
+    NNs = ordered_nn(scaled, max(m, m_sim))
+    e = simulate_sequential(EXP_ANISO, theta, locs, NNs[:, : m_sim + 1], rng)
+    X = np.ones((n, 1))
+    y = 0.5 + e
+    NN = np.ascontiguousarray(NNs[:, : m + 1])
+    start = np.concatenate([[np.var(y)], np.full(d, 2.0), [0.2]])
+    return _finish("elevators_like_n%d_d%d_m%d" % (n, d, m), EXP_ANISO, locs, y, X, m, theta,
                    start, NN=NN, seed=seed, m_sim=m_sim)
 
 

@@ -237,11 +237,12 @@ int prep_maxmin(const double* x, int64_t n, int d, int64_t* order)
     return rc;
 }
 
-/* Exact maxmin by brute force, O(n^2); used to pin prep_maxmin on small inputs. */
+/* Exact maxmin by brute force, O(n^2 d); pins prep_maxmin on small inputs and orders
+ * points of more than 3 coordinates (1 <= d <= 64), where the grid is not used. */
 int prep_maxmin_brute(const double* x, int64_t n, int d, int64_t* order)
 {
-    if (n < 1 || d < 1 || d > 3) return PREP_ERR_ARG;
-    double cen[3] = {0, 0, 0};
+    if (n < 1 || d < 1 || d > 64) return PREP_ERR_ARG;
+    double cen[64] = {0};
     for (int64_t i = 0; i < n; i++)
         for (int k = 0; k < d; k++) cen[k] += x[i * d + k];
     for (int k = 0; k < d; k++) cen[k] /= (double)n;
@@ -370,26 +371,38 @@ int prep_ordered_nn(const double* x, int64_t n, int d, int m, int32_t* NN)
     return PREP_OK;
 }
 
-/* Brute-force ordered NN, O(n^2 m); pins prep_ordered_nn on small inputs. */
+/* Brute-force ordered NN, O(n^2 d); pins prep_ordered_nn on small inputs and searches
+ * points of more than 3 coordinates.  Rows are independent (OpenMP over rows). */
 int prep_ordered_nn_brute(const double* x, int64_t n, int d, int m, int32_t* NN)
 {
-    if (n < 1 || d < 1 || m < 0) return PREP_ERR_ARG;
+    if (n < 1 || d < 1 || m < 0 || n > 2147483647LL) return PREP_ERR_ARG;
     const int64_t W = (int64_t)m + 1;
     for (int64_t i = 0; i < n * W; i++) NN[i] = -1;
-    double* cd = (double*)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
-    int64_t* ci = (int64_t*)malloc(sizeof(int64_t) * (size_t)(m > 0 ? m : 1));
-    if (!cd || !ci) { free(cd); free(ci); return PREP_ERR_NOMEM; }
-    for (int64_t i = 0; i < n; i++) {
-        int cnt = 0;
-        NN[i * W] = (int32_t)i;
-        if (m > 0)
-            for (int64_t j = 0; j < i; j++)
-                cand_insert(cd, ci, &cnt, m, sqdist(x + i * d, x + j * d, d), j);
-        for (int t = 0; t < cnt; t++) NN[i * W + 1 + t] = (int32_t)ci[t];
+    int fail = 0;
+#pragma omp parallel
+    {
+        double* cd = (double*)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
+        int64_t* ci = (int64_t*)malloc(sizeof(int64_t) * (size_t)(m > 0 ? m : 1));
+        const int have = cd && ci;
+        if (!have) {
+#pragma omp atomic write
+            fail = 1;
+        }
+        /* every thread reaches the work-sharing loop; one without buffers skips its rows */
+#pragma omp for schedule(dynamic, 64)
+        for (int64_t i = 0; i < n; i++) {
+            if (!have) continue;
+            int cnt = 0;
+            NN[i * W] = (int32_t)i;
+            if (m > 0)
+                for (int64_t j = 0; j < i; j++)
+                    cand_insert(cd, ci, &cnt, m, sqdist(x + i * d, x + j * d, d), j);
+            for (int t = 0; t < cnt; t++) NN[i * W + 1 + t] = (int32_t)ci[t];
+        }
+        free(cd);
+        free(ci);
     }
-    free(cd);
-    free(ci);
-    return PREP_OK;
+    return fail ? PREP_ERR_NOMEM : PREP_OK;
 }
 
 /* Sequential simulation recurrence: for i = 0..n-1 in order,
