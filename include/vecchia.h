@@ -26,8 +26,12 @@
  *                                                    x = |h| / rho, 0.05 <= nu <= 20
  *       VEC_EXP_SPACETIME  (sigma2, rho_s, rho_t, tau2), d = 3 (lon, lat, time):
  *                          C = sigma2 exp(-sqrt((dlon^2 + dlat^2)/rho_s^2 + dt^2/rho_t^2))
+ *       VEC_EXP_ANISO      (sigma2, rho_1, ..., rho_d, tau2), 1 <= d <= 20: one range per
+ *                          coordinate, C = sigma2 exp(-sqrt(sum_k (h_k / rho_k)^2))
+ *                          (Sec. 4.3, the form fitted to the Elevators attributes)
+ *     The isotropic families take 1 <= d <= 3.
  *   - Results: loglik (scalar), grad (q), info (q x q, row-major, symmetric), betahat (p),
- *     where q = vecchia_nparms(covfun).  The loglikelihood includes -n/2 log(2 pi).
+ *     where q = vecchia_nparms_d(covfun, d).  The loglikelihood includes -n/2 log(2 pi).
  *   - Errors are returned as vec_status codes; nothing is printed, no exception crosses
  *     the ABI, and the library never aborts the process.  vecchia_last_error() returns a
  *     thread-local message for the last failing call on the calling thread.
@@ -58,7 +62,12 @@ typedef enum {
     VEC_ERR_UNSUPPORTED = 7  /* size or option outside what this build supports          */
 } vec_status;
 
-typedef enum { VEC_EXP_ISO = 0, VEC_MATERN_ISO = 1, VEC_EXP_SPACETIME = 2 } vec_covfun;
+typedef enum {
+    VEC_EXP_ISO = 0,
+    VEC_MATERN_ISO = 1,
+    VEC_EXP_SPACETIME = 2,
+    VEC_EXP_ANISO = 3
+} vec_covfun;
 
 /* VEC_FP64: every step in FP64.  VEC_MIXED: covariance assembly, Cholesky trailing
  * updates and solves in FP32; pivots, per-observation last-row terms, the sums over
@@ -81,8 +90,13 @@ VECCHIA_API vec_status vecchia_destroy(vec_handle h);
 /* Message for the last error raised on the calling thread ("" if none). */
 VECCHIA_API const char* vecchia_last_error(void);
 
-/* Number of covariance parameters q of a covariance function, or -1 if unknown. */
+/* Number of covariance parameters q of a covariance function whose count does not depend
+ * on the dimension, or -1 (unknown, or VEC_EXP_ANISO: use vecchia_nparms_d). */
 VECCHIA_API int vecchia_nparms(vec_covfun covfun);
+
+/* Number of covariance parameters q of a covariance function on d-dimensional locations
+ * (VEC_EXP_ANISO: d + 2), or -1 if the family is unknown or does not take d. */
+VECCHIA_API int vecchia_nparms_d(vec_covfun covfun, int d);
 
 /* Largest m supported by this build (the conditioning block is (m+1) x (m+1)). */
 VECCHIA_API int vecchia_max_m(void);
@@ -160,7 +174,7 @@ VECCHIA_API int vecchia_kernels_per_pass(vec_covfun covfun);
  * (bad NNarray row, covariance parameter out of range, block not positive definite,
  * non-finite sums) are reported in dev_status once the stream reaches that point, and
  * then out holds NaNs.  Requires 1 <= n < 2^31, 1 <= d <= 3 (d = 3 for the space-time
- * covariance), 1 <= p <= 8, 0 <= m <= vecchia_max_m().
+ * covariance, 1 <= d <= 20 for VEC_EXP_ANISO), 1 <= p <= 8, 0 <= m <= vecchia_max_m().
  */
 VECCHIA_API vec_status vecchia_loglik_grad_info(vec_handle h, const double* locs, const double* y,
                                     const double* X, const int32_t* NNarray, int64_t n,

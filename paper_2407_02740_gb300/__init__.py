@@ -32,9 +32,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libvecchia_gb300.so")
 
-EXP_ISO, MATERN_ISO, EXP_SPACETIME = 0, 1, 2
+EXP_ISO, MATERN_ISO, EXP_SPACETIME, EXP_ANISO = 0, 1, 2, 3
 FP64, MIXED = 0, 1
-NPARMS = {EXP_ISO: 3, MATERN_ISO: 4, EXP_SPACETIME: 4}
+NPARMS = {EXP_ISO: 3, MATERN_ISO: 4, EXP_SPACETIME: 4}   # EXP_ANISO: d + 2, see nparms()
 STATUS = {0: "VEC_OK", 1: "VEC_ERR_ARG", 2: "VEC_ERR_NOT_PD", 3: "VEC_ERR_NONFINITE",
           4: "VEC_ERR_NOMEM", 5: "VEC_ERR_CUDA", 6: "VEC_ERR_TIMEOUT", 7: "VEC_ERR_UNSUPPORTED"}
 _PREC = {"fp64": FP64, "mixed": MIXED, FP64: FP64, MIXED: MIXED}
@@ -90,6 +90,7 @@ def lib():
         L.vecchia_destroy.argtypes = [P]
         L.vecchia_last_error.restype = ctypes.c_char_p
         L.vecchia_nparms.argtypes = [ci]
+        L.vecchia_nparms_d.argtypes = [ci, ci]
         L.vecchia_set_lanes.argtypes = [P, ci]
         L.vecchia_set_block_threads.argtypes = [P, ci]
         L.vecchia_set_matern_table.argtypes = [P, ci]
@@ -138,7 +139,7 @@ def lib():
         for f in (L.vecchia_create, L.vecchia_destroy, L.vecchia_set_lanes, L.vecchia_set_block_threads,
                   L.vecchia_set_matern_table,
                   L.vecchia_loglik_grad_info, L.vecchia_loglik_grad_info_host,
-                  L.vecchia_covariance_pairs, L.vecchia_nparms, L.vecchia_max_m,
+                  L.vecchia_covariance_pairs, L.vecchia_nparms, L.vecchia_nparms_d, L.vecchia_max_m,
                   L.vecchia_set_timing, L.vecchia_last_timing, L.vecchia_kernels_per_pass,
                   L.vecchia_loglik_grad_info_noalloc, L.vecchia_fit, L.vecchia_autotune,
                   L.vecchia_autotune_save, L.vecchia_autotune_load,
@@ -154,6 +155,15 @@ def lib():
             f.restype = ci
         _lib = L
     return _lib
+
+
+def nparms(covfun: int, d: int) -> int:
+    """Number of covariance parameters of a family on d-dimensional locations (the
+    library's vecchia_nparms_d); raises ValueError if the family does not take d."""
+    q = lib().vecchia_nparms_d(int(covfun), int(d))
+    if q < 0:
+        raise ValueError("covariance function %d does not take d = %d" % (covfun, d))
+    return q
 
 
 def _check(code: int, bad_index: int = -1):
@@ -248,7 +258,7 @@ def vecchia_loglik_grad_info(locs, y, X, NNarray, covparms, covfun: int, prec="f
     n, d = locs.shape
     p = X.shape[1]
     m = NNarray.shape[1] - 1
-    q = NPARMS[covfun]
+    q = nparms(covfun, d)
     dev = locs.device
     if handle is None:
         handle = default_handle(dev.index if dev.index is not None else 0)
@@ -282,7 +292,7 @@ def vecchia_batch_loglik_grad_info(locs, y, X, NNarray, point_offsets, m, covpar
     nb = len(mm)
     d = locs.shape[1]
     p = X.shape[1]
-    q = NPARMS[covfun]
+    q = nparms(covfun, d)
     dev = locs.device
     if handle is None:
         handle = default_handle(dev.index if dev.index is not None else 0)
@@ -374,7 +384,7 @@ def vecchia_batch_fit(locs, y, X, NNarray, point_offsets, m, covfun: int, start,
     nb = len(mm)
     d = locs.shape[1]
     p = X.shape[1]
-    q = NPARMS[covfun]
+    q = nparms(covfun, d)
     dev = locs.device
     if tuple(start.shape) != (nb, q):
         raise ValueError("start must be (nbatch, q)")
@@ -440,7 +450,7 @@ def vecchia_fields_loglik_grad_info(locs, X, NNarray, Y, covparms, covfun: int, 
     (nfields, n), covparms (nfields, q).  Returns (out, status) on the device."""
     import torch
     n, d, p, m, nf = _fields_common(locs, X, NNarray, Y, ((covparms, torch.float64, "covparms"),))
-    q = NPARMS[covfun]
+    q = nparms(covfun, d)
     dev = locs.device
     if handle is None:
         handle = default_handle(dev.index if dev.index is not None else 0)
@@ -465,7 +475,7 @@ def vecchia_fields_fit(locs, X, NNarray, Y, covfun: int, start, tol: float = 1e-
     start is a CUDA tensor (nfields, q).  Same result dictionary as vecchia_batch_fit."""
     import torch
     n, d, p, m, nf = _fields_common(locs, X, NNarray, Y, ((start, torch.float64, "start"),))
-    q = NPARMS[covfun]
+    q = nparms(covfun, d)
     dev = locs.device
     if tuple(start.shape) != (nf, q):
         raise ValueError("start must be (nfields, q)")
@@ -734,7 +744,7 @@ def vecchia_fit(locs, y, X, NNarray, covfun: int, start, tol: float = 1e-4, maxi
     n, d = locs.shape
     p = X.shape[1]
     m = NNarray.shape[1] - 1
-    q = NPARMS[covfun]
+    q = nparms(covfun, d)
     dev = locs.device
     if handle is None:
         handle = default_handle(dev.index if dev.index is not None else 0)
@@ -773,7 +783,7 @@ def vecchia_loglik_grad_info_noalloc(locs, y, X, NNarray, covparms, covfun: int,
     n, d = locs.shape
     p = X.shape[1]
     m = NNarray.shape[1] - 1
-    q = NPARMS[covfun]
+    q = nparms(covfun, d)
     dev = locs.device
     if out is None:
         out = torch.empty(1 + q + q * q + p, dtype=torch.float64, device=dev)
@@ -816,7 +826,7 @@ def vecchia_loglik_grad_info_host(locs, y, X, NNarray, covparms, covfun: int, pr
     n, d = locs.shape
     p = X.shape[1]
     m = NN.shape[1] - 1
-    q = NPARMS[covfun]
+    q = nparms(covfun, d)
     if handle is None:
         handle = default_handle(device)
     ll = ctypes.c_double()
@@ -842,7 +852,7 @@ def vecchia_covariance_pairs(covfun: int, covparms, la, lb, same, stream=None,
     _dev_tensor_check(lb, torch.float64, "lb")
     _dev_tensor_check(same, torch.int32, "same")
     npairs, d = la.shape
-    q = NPARMS[covfun]
+    q = nparms(covfun, d)
     dev = la.device
     if handle is None:
         handle = default_handle(dev.index if dev.index is not None else 0)

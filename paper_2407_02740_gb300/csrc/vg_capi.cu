@@ -163,12 +163,22 @@ extern "C" {
 
 const char* vecchia_last_error(void) { return g_last_error.c_str(); }
 
+int vecchia_nparms_d(vec_covfun covfun, int d) {
+    switch (covfun) {
+    case VEC_EXP_ISO: return (d >= 1 && d <= vg::DMAX) ? 3 : -1;
+    case VEC_MATERN_ISO: return (d >= 1 && d <= vg::DMAX) ? 4 : -1;
+    case VEC_EXP_SPACETIME: return d == 3 ? 4 : -1;
+    case VEC_EXP_ANISO: return (d >= 1 && d <= vg::DMAX_ANISO) ? d + 2 : -1;
+    default: return -1;
+    }
+}
+
 int vecchia_nparms(vec_covfun covfun) {
     switch (covfun) {
     case VEC_EXP_ISO: return 3;
     case VEC_MATERN_ISO: return 4;
     case VEC_EXP_SPACETIME: return 4;
-    default: return -1;
+    default: return -1;   // unknown, or a count that depends on d (VEC_EXP_ANISO)
     }
 }
 
@@ -202,7 +212,7 @@ vec_status vecchia_last_timing(vec_handle h, float* ms_setup, float* ms_pass, fl
 }
 
 int vecchia_kernels_per_pass(vec_covfun covfun) {
-    if (vecchia_nparms(covfun) < 0) return -1;
+    if (vecchia_nparms_d(covfun, covfun == VEC_EXP_SPACETIME ? 3 : 1) < 0) return -1;
     return covfun == VEC_MATERN_ISO ? 4 : 3;
 }
 
@@ -307,10 +317,9 @@ vec_status check_args(const void* locs, const void* y, const void* X, const void
     if (!locs || !y || !X || !NN || !covparms)
         return fail(VEC_ERR_ARG, "a required pointer is NULL");
     if (n < 1 || n > (int64_t)INT_MAX) return fail(VEC_ERR_ARG, "n = %lld out of range", (long long)n);
-    if (vecchia_nparms(covfun) < 0) return fail(VEC_ERR_ARG, "unknown covariance function %d", (int)covfun);
-    if (d < 1 || d > vg::DMAX) return fail(VEC_ERR_ARG, "d = %d out of range [1, 3]", d);
-    if (covfun == VEC_EXP_SPACETIME && d != 3)
-        return fail(VEC_ERR_ARG, "the space-time covariance needs d = 3 (lon, lat, time)");
+    if (vecchia_nparms_d(covfun, d) < 0)
+        return fail(VEC_ERR_ARG, "covariance function %d does not take d = %d (isotropic: 1..3, "
+                    "space-time: 3, one range per coordinate: 1..%d)", (int)covfun, d, vg::DMAX_ANISO);
     if (p < 1 || p > vg::PMAX) return fail(VEC_ERR_ARG, "p = %d out of range [1, %d]", p, vg::PMAX);
     if (m < 0 || m > vg::KMAX - 1)
         return fail(VEC_ERR_UNSUPPORTED, "m = %d out of range [0, %d]", m, vg::KMAX - 1);
@@ -376,7 +385,7 @@ vec_status enqueue_pass(vec_handle h, const double* locs, const double* y, const
     e = vg::launch_pass(cov, plan, a, st);
     if (e != cudaSuccess) return cuda_fail(e, "launching the pass kernel");
     if (tr) cudaEventRecord(h->ev[2], st);
-    e = vg::launch_profile(h->partials, plan.grid, plan.nstat, p, cov, n, covparms, h->status,
+    e = vg::launch_profile(h->partials, plan.grid, plan.nstat, p, vg::nparms(cov, d), n, covparms, h->status,
                            h->bad, out, dev_status, st);
     if (e != cudaSuccess) return cuda_fail(e, "launching the profile kernel");
     if (tr) {
@@ -418,7 +427,7 @@ vec_status vecchia_loglik_grad_info_host(vec_handle h, const double* locs, const
     if (!loglik || !grad || !info || !betahat) return fail(VEC_ERR_ARG, "an output pointer is NULL");
     DeviceGuard g(h->device);
     if (!g.ok) return fail(VEC_ERR_CUDA, "cannot select device %d", h->device);
-    const int q = vecchia_nparms(covfun);
+    const int q = vecchia_nparms_d(covfun, d);
     const size_t nout = 1 + q + (size_t)q * q + p;
     cudaError_t e = grow(&h->h_locs, &h->c_locs, (size_t)n * d);
     if (e == cudaSuccess) e = grow(&h->h_y, &h->c_y, (size_t)n);
@@ -439,7 +448,7 @@ vec_status vecchia_loglik_grad_info_host(vec_handle h, const double* locs, const
     s = enqueue_pass(h, h->h_locs, h->h_y, h->h_X, h->h_NN, n, d, p, m, h->h_cov, covfun, st,
                      h->h_out, h->h_st, (int)prec);
     if (s != VEC_OK) return s;
-    double res[1 + 4 + 16 + vg::PMAX];
+    double res[1 + vg::QMAX + vg::QMAX * vg::QMAX + vg::PMAX];
     long long dst[2];
     e = cudaMemcpyAsync(res, h->h_out, sizeof(double) * nout, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dst, h->h_st, sizeof(long long) * 2, cudaMemcpyDeviceToHost, st);
@@ -475,7 +484,7 @@ vec_status vecchia_fit(vec_handle h, const double* locs, const double* y, const 
     if (!(o.tol >= 0.0) || o.maxit < 0 || o.maxit > 100000 || o.max_halvings < 0 || o.max_halvings > 60)
         return fail(VEC_ERR_ARG, "vecchia_fit: bad options (tol %g, maxit %d, max_halvings %d)", o.tol,
                     o.maxit, o.max_halvings);
-    const int q = vecchia_nparms(covfun);
+    const int q = vecchia_nparms_d(covfun, d);
     for (int j = 0; j < q; ++j)
         if (!(start[j] > 0.0) || !std::isfinite(start[j]))
             return fail(VEC_ERR_ARG, "vecchia_fit: start[%d] = %g is not a positive number", j, start[j]);
@@ -487,9 +496,11 @@ vec_status vecchia_fit(vec_handle h, const double* locs, const double* y, const 
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = cudaSuccess;
     if (!h->fs) e = cudaMalloc(reinterpret_cast<void**>(&h->fs), sizeof(vg::FitState));
-    if (e == cudaSuccess && !h->fit_out) e = cudaMalloc(reinterpret_cast<void**>(&h->fit_out), sizeof(double) * 32);
+    if (e == cudaSuccess && !h->fit_out)
+        e = cudaMalloc(reinterpret_cast<void**>(&h->fit_out),
+                       sizeof(double) * (1 + vg::QMAX + vg::QMAX * vg::QMAX + vg::PMAX));
     if (e == cudaSuccess && !h->fit_st) e = cudaMalloc(reinterpret_cast<void**>(&h->fit_st), sizeof(long long) * 2);
-    if (e == cudaSuccess && !h->fit_start) e = cudaMalloc(reinterpret_cast<void**>(&h->fit_start), sizeof(double) * 4);
+    if (e == cudaSuccess && !h->fit_start) e = cudaMalloc(reinterpret_cast<void**>(&h->fit_start), sizeof(double) * vg::QMAX);
     if (e != cudaSuccess) return cuda_fail(e, "vecchia_fit: allocating the fit state");
     const double* theta_trial = h->fs->theta_trial;  // device address of the member
     // a hard bound on the number of passes, so the device loop always ends
@@ -634,7 +645,7 @@ vec_status vecchia_autotune(vec_handle h, const double* locs, const double* y, c
     if (!g.ok) return fail(VEC_ERR_CUDA, "cannot select device %d", h->device);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const int cov = (int)covfun;
-    const int q = vecchia_nparms(covfun);
+    const int q = vecchia_nparms_d(covfun, d);
     double* out = nullptr;
     long long* dst = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -899,7 +910,7 @@ vec_status enqueue_batch(const BatchScratch& S, const BatchPlan& B, const double
                          double* out, long long* dev_status, const int* active,
                          double* factor = nullptr) {
     const int cov = (int)covfun;
-    const int q = vecchia_nparms(covfun);
+    const int q = vecchia_nparms_d(covfun, d);
     cudaError_t e = vg::launch_init_batch(S.status, S.bad, B.nbatch, S.counter, st);
     if (e == cudaSuccess && cov == vg::COV_MATERN)
         e = vg::launch_mtab_build_batch(covparms, B.nbatch, q, S.tabs, prec ? S.tabsf : nullptr,
@@ -919,7 +930,7 @@ vec_status enqueue_batch(const BatchScratch& S, const BatchPlan& B, const double
     if (e == cudaSuccess && factor)  // factor rows only: report the per-dataset status
         e = vg::launch_batch_status(S.status, S.bad, B.nbatch, dev_status, st);
     else if (e == cudaSuccess)
-        e = vg::launch_profile_batch(S.partials, S.tile_off, B.nbatch, B.plan.nstat, p, cov,
+        e = vg::launch_profile_batch(S.partials, S.tile_off, B.nbatch, B.plan.nstat, p, q,
                                      S.desc, covparms, S.status, S.bad, out, dev_status, st);
     if (e != cudaSuccess) return cuda_fail(e, "launching the batched pass");
     return VEC_OK;
@@ -937,9 +948,8 @@ static vec_status check_batch_args(const char* who, vec_handle h, int nbatch, co
     if (!locs || !y || !X || !NNarray || !point_offsets || !m)
         return fail(VEC_ERR_ARG, "%s: a required pointer is NULL", who);
     if (nbatch < 1) return fail(VEC_ERR_ARG, "%s: nbatch = %d", who, nbatch);
-    if (vecchia_nparms(covfun) < 0) return fail(VEC_ERR_ARG, "%s: unknown covariance function", who);
-    if (d < 1 || d > vg::DMAX || (covfun == VEC_EXP_SPACETIME && d != 3))
-        return fail(VEC_ERR_ARG, "%s: bad d = %d", who, d);
+    if (vecchia_nparms_d(covfun, d) < 0)
+        return fail(VEC_ERR_ARG, "%s: covariance function %d does not take d = %d", who, (int)covfun, d);
     if (p < 1 || p > vg::PMAX) return fail(VEC_ERR_ARG, "%s: p = %d out of range", who, p);
     if (prec != VEC_FP64 && prec != VEC_MIXED) return fail(VEC_ERR_ARG, "%s: unknown precision", who);
     return VEC_OK;
@@ -984,8 +994,8 @@ vec_status vecchia_batch_plan_create(vec_handle h, int nbatch, const int64_t* po
     *plan_out = nullptr;
     if (!h) return fail(VEC_ERR_ARG, "vecchia_batch_plan_create: NULL handle");
     if (!point_offsets || !m) return fail(VEC_ERR_ARG, "vecchia_batch_plan_create: point_offsets and m are required");
-    if (vecchia_nparms(covfun) < 0) return fail(VEC_ERR_ARG, "unknown covariance function");
-    if (d < 1 || d > vg::DMAX || (covfun == VEC_EXP_SPACETIME && d != 3)) return fail(VEC_ERR_ARG, "bad d = %d", d);
+    if (vecchia_nparms_d(covfun, d) < 0)
+        return fail(VEC_ERR_ARG, "covariance function %d does not take d = %d", (int)covfun, d);
     if (p < 1 || p > vg::PMAX) return fail(VEC_ERR_ARG, "p = %d out of range", p);
     if (prec != VEC_FP64 && prec != VEC_MIXED) return fail(VEC_ERR_ARG, "unknown precision");
     DeviceGuard g(h->device);
@@ -1056,7 +1066,7 @@ static vec_status batch_fit_impl(vec_handle h, int nbatch,
     DeviceGuard g(h->device);
     if (!g.ok) return fail(VEC_ERR_CUDA, "cannot select device %d", h->device);
     const int cov = (int)covfun;
-    const int q = vecchia_nparms(covfun);
+    const int q = vecchia_nparms_d(covfun, d);
     const int nout = 1 + q + q * q + p;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = grow(&h->bf_fs, &h->c_bf_fs, (size_t)nbatch);
@@ -1192,7 +1202,7 @@ vec_status vecchia_batch_autotune(vec_handle h, int nbatch, const double* locs, 
     if (!g.ok) return fail(VEC_ERR_CUDA, "cannot select device %d", h->device);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const int cov = (int)covfun;
-    const int q = vecchia_nparms(covfun);
+    const int q = vecchia_nparms_d(covfun, d);
     double* out = nullptr;
     long long* dst = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1273,9 +1283,8 @@ static vec_status check_fields_args(const char* who, vec_handle h, int nfields, 
     if (nfields < 1) return fail(VEC_ERR_ARG, "%s: nfields = %d", who, nfields);
     if (n < 1 || n > (int64_t)INT_MAX) return fail(VEC_ERR_ARG, "%s: n = %lld", who, (long long)n);
     if (m < 0 || m > vg::KMAX - 1) return fail(VEC_ERR_UNSUPPORTED, "%s: m = %d out of range", who, m);
-    if (vecchia_nparms(covfun) < 0) return fail(VEC_ERR_ARG, "%s: unknown covariance function", who);
-    if (d < 1 || d > vg::DMAX || (covfun == VEC_EXP_SPACETIME && d != 3))
-        return fail(VEC_ERR_ARG, "%s: bad d = %d", who, d);
+    if (vecchia_nparms_d(covfun, d) < 0)
+        return fail(VEC_ERR_ARG, "%s: covariance function %d does not take d = %d", who, (int)covfun, d);
     if (p < 1 || p > vg::PMAX) return fail(VEC_ERR_ARG, "%s: p = %d out of range", who, p);
     if (prec != VEC_FP64 && prec != VEC_MIXED) return fail(VEC_ERR_ARG, "%s: unknown precision", who);
     return VEC_OK;
@@ -1331,7 +1340,7 @@ vec_status vecchia_fields_simulate(vec_handle h, int nfields, const double* locs
     DeviceGuard g(h->device);
     if (!g.ok) return fail(VEC_ERR_CUDA, "cannot select device %d", h->device);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    const int q = vecchia_nparms(covfun);
+    const int q = vecchia_nparms_d(covfun, d);
     const size_t row = (size_t)n * (m + 1);
     // factor rows of a chunk of fields at a time, at most ~1 GiB of scratch
     const size_t chunk = std::max<size_t>(1, std::min<size_t>((size_t)nfields, ((size_t)1 << 27) / row));
@@ -1551,8 +1560,9 @@ vec_status vecchia_predict(vec_handle h, const double* locs, const double* y, co
     if (!h || !locs || !y || !X || !beta || !locs_pred || !X_pred || !covparms || !mean || !var ||
         !dev_status || (m > 0 && !NN_pred))
         return fail(VEC_ERR_ARG, "vecchia_predict: NULL argument");
-    if (vecchia_nparms(covfun) < 0) return fail(VEC_ERR_ARG, "unknown covariance function");
-    if (n < 1 || npred < 1 || d < 1 || d > vg::DMAX || (covfun == VEC_EXP_SPACETIME && d != 3) ||
+    if (vecchia_nparms_d(covfun, d) < 0)
+        return fail(VEC_ERR_ARG, "covariance function %d does not take d = %d", (int)covfun, d);
+    if (n < 1 || npred < 1 ||
         p < 1 || p > vg::PMAX || m < 0 || m > vg::KMAX - 1 || npred > (int64_t)INT_MAX * 16)
         return fail(VEC_ERR_ARG, "vecchia_predict: bad sizes (n %lld, npred %lld, d %d, p %d, m %d)",
                     (long long)n, (long long)npred, d, p, m);
@@ -1575,9 +1585,8 @@ vec_status vecchia_covariance_pairs(vec_handle h, vec_covfun covfun, const doubl
                                     int d, int64_t npairs, const double* la, const double* lb,
                                     const int32_t* same, double* C, double* dC, void* stream) {
     if (!h) return fail(VEC_ERR_ARG, "vecchia_covariance_pairs: NULL handle");
-    if (vecchia_nparms(covfun) < 0) return fail(VEC_ERR_ARG, "unknown covariance function");
-    if (d < 1 || d > vg::DMAX || (covfun == VEC_EXP_SPACETIME && d != 3))
-        return fail(VEC_ERR_ARG, "bad d = %d", d);
+    if (vecchia_nparms_d(covfun, d) < 0)
+        return fail(VEC_ERR_ARG, "covariance function %d does not take d = %d", (int)covfun, d);
     if (npairs < 0) return fail(VEC_ERR_ARG, "npairs < 0");
     if (npairs > 0 && (!covparms || !la || !lb || !same || !C || !dC))
         return fail(VEC_ERR_ARG, "a required pointer is NULL");

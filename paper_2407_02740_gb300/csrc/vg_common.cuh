@@ -8,11 +8,15 @@ namespace vg {
 // status codes written by kernels (same numbering as vec_status in include/vecchia.h)
 enum : int { ST_OK = 0, ST_ARG = 1, ST_NOT_PD = 2, ST_NONFINITE = 3 };
 
-enum : int { COV_EXP = 0, COV_MATERN = 1, COV_ST = 2 };
+// COV_ANISO: the exponential with one range per coordinate (Sec. 4.3, Eq. 6 with
+// rho_1..rho_d), theta = (sigma2, rho_1, ..., rho_d, tau2).
+enum : int { COV_EXP = 0, COV_MATERN = 1, COV_ST = 2, COV_ANISO = 3 };
 
 constexpr int KMAX = 81;   // largest conditioning block (m <= 80)
 constexpr int PMAX = 8;    // largest number of regression columns
-constexpr int DMAX = 3;    // largest location dimension
+constexpr int DMAX = 3;    // largest location dimension of the isotropic families
+constexpr int DMAX_ANISO = 20;          // largest dimension with one range per coordinate
+constexpr int QMAX = DMAX_ANISO + 2;    // largest number of covariance parameters
 
 // Geometry of the per-pass Matern coefficient table (see vg_matern.cuh).  Each function
 // on each interval is a degree-12 polynomial in w stored as 8 FP64 coefficients (w^0..w^7)
@@ -32,10 +36,25 @@ constexpr int MT_DOUBLES = MT_NINT * MT_PER_INT;
 constexpr int MT_PER_INT_F = 3 * MT_NC;
 constexpr int MT_FLOATS = MT_NINT * MT_PER_INT_F;
 
-__host__ __device__ constexpr int nparms(int cov) { return cov == COV_EXP ? 3 : 4; }
+// number of covariance parameters (d: location dimension, used by COV_ANISO only)
+__host__ __device__ constexpr int nparms(int cov, int d = 0) {
+    return cov == COV_EXP ? 3 : (cov == COV_ANISO ? d + 2 : 4);
+}
 // number of covariance parameters whose derivative matrix needs a per-pair evaluation
 // (sigma2 and tau2 are handled in closed form)
-__host__ __device__ constexpr int npair_derivs(int cov) { return cov == COV_EXP ? 1 : 2; }
+__host__ __device__ constexpr int npair_derivs(int cov, int d = 0) {
+    return cov == COV_EXP ? 1 : (cov == COV_ANISO ? d : 2);
+}
+
+// theta inside the family's domain: every parameter positive and finite, the Matern
+// smoothness in [0.05, 20].
+__host__ __device__ inline bool theta_ok(int cov, int d, const double* th) {
+    const int q = nparms(cov, d);
+    for (int j = 0; j < q; ++j)
+        if (!(th[j] > 0.0 && th[j] <= 1.7976931348623157e308)) return false;   // finite
+    if (cov == COV_MATERN && !(th[2] >= 0.05 && th[2] <= 20.0)) return false;
+    return true;
+}
 
 // Per-observation record (the Algorithm 1 sums) in packed symmetric storage.
 //   [logdet, ySy, XSX (p(p+1)/2), ySX (p),
@@ -47,13 +66,17 @@ __host__ __device__ constexpr int npair_derivs(int cov) { return cov == COV_EXP 
 struct RecLayout {
     int p, Q, P2, per_j, base_j, base_info, nstat;
     __host__ __device__ void init(int p_, int Q_) {
-        p = p_; Q = Q_; P2 = p * (p + 1) / 2;
+        p = p_; Q = Q_; P2 = p * (p + 1) / 2;   // Q <= QMAX - 1, p <= PMAX
         per_j = 2 + p + P2;
         base_j = 2 + P2 + p;
         base_info = base_j + Q * per_j;
         nstat = base_info + Q * (Q + 1) / 2;
     }
 };
+
+// largest record (p = PMAX, Q = QMAX - 1)
+constexpr int REC_MAX = 2 + PMAX * (PMAX + 1) / 2 + PMAX +
+                        (QMAX - 1) * (2 + PMAX + PMAX * (PMAX + 1) / 2) + (QMAX - 1) * QMAX / 2;
 
 // 1/sqrt(v) from an FP32 seed and two Newton steps.  Each step forms the residual
 // r = 1 - v y^2 in FP64 and applies the small correction y r / 2 in FP32; the result

@@ -29,13 +29,13 @@
 namespace vg {
 
 __device__ static void fit_init_one(FitState* fs, const double* start, int q) {
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < QMAX; ++j) {
         fs->theta_trial[j] = (j < q) ? start[j] : 0.0;
         fs->theta_cur[j] = fs->theta_trial[j];
         fs->delta[j] = 0.0;
         fs->grad[j] = 0.0;
     }
-    for (int t = 0; t < 16; ++t) fs->info[t] = 0.0;
+    for (int t = 0; t < QMAX * QMAX; ++t) fs->info[t] = 0.0;
     for (int t = 0; t < PMAX; ++t) fs->beta[t] = 0.0;
     fs->loglik = -INFINITY;
     fs->iters = 0;
@@ -59,16 +59,16 @@ __global__ void k_fit_init_batch(FitState* fs, const double* start, int from_cur
                                  double* theta_b, int* active) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nbatch) return;
-    double s0[4];
+    double s0[QMAX];
     for (int j = 0; j < q; ++j) s0[j] = from_cur ? fs[b].theta_cur[j] : start[(size_t)b * q + j];
     fit_init_one(fs + b, s0, q);
     for (int j = 0; j < q; ++j) theta_b[(size_t)b * q + j] = fs[b].theta_trial[j];
     active[b] = 1;
 }
 
-// Solves A x = b for a small SPD matrix (n <= 4) by Cholesky; false if not PD.
+// Solves A x = b for a small SPD matrix (n <= QMAX) by Cholesky; false if not PD.
 __device__ static bool small_spd_solve(int n, const double* A, const double* b, double* x) {
-    double L[16], z[4];
+    double L[QMAX * QMAX], z[QMAX];
     for (int i = 0; i < n * n; ++i) L[i] = A[i];
     for (int c = 0; c < n; ++c) {
         double v = L[c * n + c];
@@ -148,7 +148,7 @@ __device__ static void fit_step_one(FitState* fs, const double* out, const long 
     for (int t = 0; t < q * q; ++t) fs->info[t] = out[1 + q + t];
     for (int a = 0; a < p; ++a) fs->beta[a] = out[1 + q + q * q + a];
     // Fisher step on the log scale
-    double gt[4], It[16], A[16], dl[4];
+    double gt[QMAX], It[QMAX * QMAX], A[QMAX * QMAX], dl[QMAX];
     double maxd = 0.0;
     for (int j = 0; j < q; ++j) gt[j] = fs->theta_cur[j] * fs->grad[j];
     for (int j = 0; j < q; ++j)

@@ -11,12 +11,12 @@ enum : int { FIT_CONVERGED = 0, FIT_MAXIT = 1, FIT_NO_ASCENT = 2, FIT_START_FAIL
 
 // Lives in device memory owned by the handle; copied back to the host after a fit.
 struct FitState {
-    double theta_cur[4];     // accepted parameters
-    double theta_trial[4];   // parameters of the next pass
-    double delta[4];         // current log-scale step
-    double loglik;           // at theta_cur
-    double grad[4];
-    double info[16];
+    double theta_cur[QMAX];     // accepted parameters
+    double theta_trial[QMAX];   // parameters of the next pass
+    double delta[QMAX];         // current log-scale step
+    double loglik;              // at theta_cur
+    double grad[QMAX];
+    double info[QMAX * QMAX];
     double beta[PMAX];
     int iters;               // accepted Fisher steps
     int halvings;            // halvings of the current step

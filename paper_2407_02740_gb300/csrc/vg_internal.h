@@ -84,14 +84,14 @@ cudaError_t launch_batch_status(const int* status_b, const long long* bad_b, int
 cudaError_t launch_init_batch(int* status_b, long long* bad_b, int nbatch, int* tile_counter,
                               cudaStream_t st);
 cudaError_t launch_profile_batch(const double* partials, const int* tile_off, int nbatch, int nstat,
-                                 int p, int cov, const DatasetDesc* desc, const double* covparms_b,
+                                 int p, int q, const DatasetDesc* desc, const double* covparms_b,
                                  const int* status_b, const long long* bad_b, double* out,
                                  long long* dev_status, cudaStream_t st);
 
 cudaError_t launch_pass(int cov, const PassPlan& plan, const PassArgs& args, cudaStream_t st);
 cudaError_t launch_init_status(int* status, long long* bad, cudaStream_t st);
 cudaError_t launch_mtab_build(const double* covparms, double* tab, float* tabf, cudaStream_t st);
-cudaError_t launch_profile(const double* partials, int nblk, int nstat, int p, int cov,
+cudaError_t launch_profile(const double* partials, int nblk, int nstat, int p, int q,
                            long long n, const double* covparms, const int* status,
                            const long long* bad, double* out, long long* dev_status,
                            cudaStream_t st);

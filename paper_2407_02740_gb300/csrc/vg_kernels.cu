@@ -97,20 +97,20 @@ __global__ void k_init_status(int* status, long long* bad) {
     bad[0] = LLONG_MAX;
 }
 
-// Profile step from the summed record tot (nstat entries).  The sigma2 entries are
-// formed here from the totals (dSigma/dsigma2 = Sigma/sigma2 with the relative nugget):
+// Profile step from the summed record tot (nstat entries), q covariance parameters.
+// The sigma2 entries are formed here from the totals (dSigma/dsigma2 = Sigma/sigma2 with
+// the relative nugget):
 //   dlogdet_0 = n/sigma2, dySy_0 = -ySy/sigma2, dySX_0 = -ySX/sigma2, dXSX_0 = -XSX/sigma2,
 //   info_00 = n/(2 sigma2^2), info_0l = dlogdet_l/(2 sigma2).
-__device__ void profile_from_totals(const double* tot, int p, int cov, long long n,
+__device__ void profile_from_totals(const double* tot, int p, int q, long long n,
                                     const double* covparms, int st0, long long bad0, double* out,
                                     long long* dev_status) {
-    const int q = nparms(cov), Q = q - 1;
+    const int Q = q - 1;
     RecLayout RL;
     RL.init(p, Q);
     int st = st0;
     const int nout = 1 + q + q * q + p;
-    double XSX[PMAX * PMAX], ySX[PMAX], dySX[4][PMAX], dXSX[4][PMAX * PMAX];
-    double dlogdet[4], dySy[4], info[16];
+    double XSX[PMAX * PMAX], ySX[PMAX];
     const double logdet = tot[0], ySy = tot[1];
     {
         int u = 2;
@@ -118,33 +118,8 @@ __device__ void profile_from_totals(const double* tot, int p, int cov, long long
             for (int b = a; b < p; ++b) { XSX[a * p + b] = XSX[b * p + a] = tot[u]; ++u; }
         for (int a = 0; a < p; ++a) ySX[a] = tot[u++];
     }
-    for (int j = 0; j < Q; ++j) {
-        int u = RL.base_j + j * RL.per_j;
-        dlogdet[j + 1] = tot[u++];
-        dySy[j + 1] = tot[u++];
-        for (int a = 0; a < p; ++a) dySX[j + 1][a] = tot[u++];
-        for (int a = 0; a < p; ++a)
-            for (int b = a; b < p; ++b) {
-                dXSX[j + 1][a * p + b] = dXSX[j + 1][b * p + a] = tot[u];
-                ++u;
-            }
-    }
-    {
-        int u = RL.base_info;
-        for (int j = 0; j < Q; ++j)
-            for (int l = j; l < Q; ++l) {
-                info[(j + 1) * q + (l + 1)] = info[(l + 1) * q + (j + 1)] = tot[u];
-                ++u;
-            }
-    }
     const double s2 = covparms[0];
     const double nd = (double)n;
-    dlogdet[0] = nd / s2;
-    dySy[0] = -ySy / s2;
-    for (int a = 0; a < p; ++a) dySX[0][a] = -ySX[a] / s2;
-    for (int a = 0; a < p * p; ++a) dXSX[0][a] = -XSX[a] / s2;
-    info[0] = nd / (2.0 * s2 * s2);
-    for (int l = 1; l < q; ++l) info[l] = info[l * q] = dlogdet[l] / (2.0 * s2);
 
     // betahat = XSX^-1 ySX by Cholesky
     double Lc[PMAX * PMAX], z[PMAX], beta[PMAX];
@@ -177,14 +152,41 @@ __device__ void profile_from_totals(const double* tot, int p, int cov, long long
     for (int a = 0; a < p; ++a) quad -= ySX[a] * beta[a];
     const double LOG2PI = 1.8378770664093454836;
     out[0] = -0.5 * nd * LOG2PI - 0.5 * logdet - 0.5 * quad;
+    // gradient, one parameter at a time
     for (int J = 0; J < q; ++J) {
-        double t = dlogdet[J] + dySy[J];
-        for (int a = 0; a < p; ++a) t -= 2.0 * beta[a] * dySX[J][a];
+        double dld, dyy, dySX[PMAX], dXSX[PMAX * PMAX];
+        if (J == 0) {
+            dld = nd / s2;
+            dyy = -ySy / s2;
+            for (int a = 0; a < p; ++a) dySX[a] = -ySX[a] / s2;
+            for (int a = 0; a < p * p; ++a) dXSX[a] = -XSX[a] / s2;
+        } else {
+            int u = RL.base_j + (J - 1) * RL.per_j;
+            dld = tot[u++];
+            dyy = tot[u++];
+            for (int a = 0; a < p; ++a) dySX[a] = tot[u++];
+            for (int a = 0; a < p; ++a)
+                for (int b = a; b < p; ++b) { dXSX[a * p + b] = dXSX[b * p + a] = tot[u]; ++u; }
+        }
+        double t = dld + dyy;
+        for (int a = 0; a < p; ++a) t -= 2.0 * beta[a] * dySX[a];
         for (int a = 0; a < p; ++a)
-            for (int b = 0; b < p; ++b) t += beta[a] * dXSX[J][a * p + b] * beta[b];
+            for (int b = 0; b < p; ++b) t += beta[a] * dXSX[a * p + b] * beta[b];
         out[1 + J] = -0.5 * t;
     }
-    for (int t = 0; t < q * q; ++t) out[1 + q + t] = info[t];
+    // Fisher information
+    double* info = out + 1 + q;
+    info[0] = nd / (2.0 * s2 * s2);
+    for (int l = 1; l < q; ++l)
+        info[l] = info[l * q] = tot[RL.base_j + (l - 1) * RL.per_j] / (2.0 * s2);
+    {
+        int u = RL.base_info;
+        for (int j = 0; j < Q; ++j)
+            for (int l = j; l < Q; ++l) {
+                info[(j + 1) * q + (l + 1)] = info[(l + 1) * q + (j + 1)] = tot[u];
+                ++u;
+            }
+    }
     for (int a = 0; a < p; ++a) out[1 + q + q * q + a] = beta[a];
     if (st == 0) {
         if (!pd) st = ST_NONFINITE;
@@ -199,10 +201,10 @@ __device__ void profile_from_totals(const double* tot, int p, int cov, long long
 
 // Single dataset: sum the per-block partial records in a fixed order, then profile.
 __global__ void k_profile(const double* __restrict__ partials, int nblk, int nstat, int p,
-                          int cov, long long n, const double* __restrict__ covparms,
+                          int q, long long n, const double* __restrict__ covparms,
                           const int* status, const long long* bad, double* out,
                           long long* dev_status) {
-    __shared__ double tot[256];
+    __shared__ double tot[REC_MAX];
     const int tid = threadIdx.x;
     for (int t = tid; t < nstat; t += blockDim.x) {
         double s = 0.0;
@@ -210,18 +212,17 @@ __global__ void k_profile(const double* __restrict__ partials, int nblk, int nst
         tot[t] = s;
     }
     __syncthreads();
-    if (tid == 0) profile_from_totals(tot, p, cov, n, covparms, status[0], bad[0], out, dev_status);
+    if (tid == 0) profile_from_totals(tot, p, q, n, covparms, status[0], bad[0], out, dev_status);
 }
 
 // Batch: block b sums the records of dataset b's tiles [tile_off[b], tile_off[b+1]) in
 // order and profiles them with the dataset's parameters.
 __global__ void k_profile_batch(const double* __restrict__ partials, const int* __restrict__ tile_off,
-                                int nstat, int p, int cov, const DatasetDesc* __restrict__ desc,
+                                int nstat, int p, int q, const DatasetDesc* __restrict__ desc,
                                 const double* __restrict__ covparms_b, const int* status_b,
                                 const long long* bad_b, double* out, long long* dev_status) {
-    __shared__ double tot[256];
+    __shared__ double tot[REC_MAX];
     const int b = blockIdx.x, tid = threadIdx.x;
-    const int q = nparms(cov);
     const int nout = 1 + q + q * q + p;
     for (int t = tid; t < nstat; t += blockDim.x) {
         double s = 0.0;
@@ -230,7 +231,7 @@ __global__ void k_profile_batch(const double* __restrict__ partials, const int* 
     }
     __syncthreads();
     if (tid == 0)
-        profile_from_totals(tot, p, cov, desc[b].n, covparms_b + (size_t)b * q,
+        profile_from_totals(tot, p, q, desc[b].n, covparms_b + (size_t)b * q,
                             status_b[b], bad_b[b], out + (size_t)b * nout, dev_status + 2 * (size_t)b);
 }
 
@@ -284,14 +285,27 @@ __global__ void k_cov_pairs(const double* __restrict__ covparms, const double* _
                             double* __restrict__ C, double* __restrict__ dC) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= npairs) return;
-    const int q = nparms(COV);
+    const int q = nparms(COV, d);
     const double* th = covparms;
     const double s2 = th[0], tau2 = th[q - 1];
     const double* a = la + i * d;
     const double* b = lb + i * d;
-    double out[4] = {0.0, 0.0, 0.0, 0.0};
+    double out[QMAX];
+    for (int j = 0; j < q; ++j) out[j] = 0.0;
     double c = 0.0;
-    if (COV == COV_EXP) {
+    if (COV == COV_ANISO) {
+        double s = 0.0;
+        for (int k = 0; k < d; ++k) { double u = (a[k] - b[k]) / th[1 + k]; s = fma(u, u, s); }
+        const double D = sqrt(s);
+        const double e = exp(-D);
+        c = s2 * e;
+        out[0] = e;
+        if (D > 0.0)
+            for (int k = 0; k < d; ++k) {
+                const double u = (a[k] - b[k]) / th[1 + k];
+                out[1 + k] = s2 * e / D * u * u / th[1 + k];
+            }
+    } else if (COV == COV_EXP) {
         double s = 0.0;
         for (int k = 0; k < d; ++k) { double t = a[k] - b[k]; s = fma(t, t, s); }
         double x = sqrt(s) / th[1];
@@ -345,7 +359,7 @@ static const void* pass_kernel(int cov, int L, int prec, bool batched = false) {
 
 size_t pass_smem_bytes(int cov, int m, int d, int p, int L, int threads, bool tab_smem,
                        int prec) {
-    const int Q = npair_derivs(cov) + 1;
+    const int Q = npair_derivs(cov, d) + 1;
     RecLayout RL;
     RL.init(p, Q);
     const int nv = nv_of(p, Q);
@@ -354,7 +368,9 @@ size_t pass_smem_bytes(int cov, int m, int d, int p, int L, int threads, bool ta
     const int ngrp = threads / L;
     const int acc_per_lane = (RL.nstat + L - 1) / L;
     const size_t tab_words = tab_smem ? (prec == 0 ? MT_DOUBLES : (MT_FLOATS + 1) / 2) : 0;
-    size_t bytes = (tab_words + (RL.nstat + 1) / 2 + (size_t)threads * acc_per_lane) * sizeof(double) +
+    const size_t inv_words = (cov == COV_ANISO) ? 2 * DMAX_ANISO : 0;
+    // record formulas: one 64-bit word per record entry
+    size_t bytes = (tab_words + inv_words + RL.nstat + (size_t)threads * acc_per_lane) * sizeof(double) +
                    (size_t)ngrp * SL.bytes;
     size_t ints = (size_t)ngrp * (m + 1);
     return bytes + ints * sizeof(int);
@@ -374,6 +390,7 @@ int plan_pass(int cov, int m, int d, int p, int nsm, int force_L, int force_thre
         for (int L = 1; L <= 32; L *= 2) {
             if (force_L > 0 && L != force_L) continue;
             if (L > thr) continue;
+            if (cov == COV_ANISO && L < 4) continue;   // no instantiation below 4 lanes
             if (thr == 256 && force_L <= 0 && L > 16) continue;
             // Matern table in shared memory when it fits (or as forced: force_tab 1 = shared
             // memory only, 0 = global memory, read through L1)
@@ -387,7 +404,7 @@ int plan_pass(int cov, int m, int d, int p, int nsm, int force_L, int force_thre
         }
     }
     if (chosen < 0) return -1;
-    const int Q = npair_derivs(cov) + 1;
+    const int Q = npair_derivs(cov, d) + 1;
     RecLayout RL;
     RL.init(p, Q);
     plan->L = chosen;
@@ -468,10 +485,11 @@ cudaError_t launch_init_batch(int* status_b, long long* bad_b, int nbatch, int* 
 }
 
 cudaError_t launch_profile_batch(const double* partials, const int* tile_off, int nbatch, int nstat,
-                                 int p, int cov, const DatasetDesc* desc, const double* covparms_b,
+                                 int p, int q, const DatasetDesc* desc, const double* covparms_b,
                                  const int* status_b, const long long* bad_b, double* out,
                                  long long* dev_status, cudaStream_t st) {
-    k_profile_batch<<<nbatch, 256, 0, st>>>(partials, tile_off, nstat, p, cov, desc, covparms_b,
+    if (nstat > REC_MAX) return cudaErrorInvalidValue;
+    k_profile_batch<<<nbatch, 256, 0, st>>>(partials, tile_off, nstat, p, q, desc, covparms_b,
                                            status_b, bad_b, out, dev_status);
     return cudaGetLastError();
 }
@@ -486,11 +504,12 @@ cudaError_t launch_mtab_build(const double* covparms, double* tab, float* tabf, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_profile(const double* partials, int nblk, int nstat, int p, int cov,
+cudaError_t launch_profile(const double* partials, int nblk, int nstat, int p, int q,
                            long long n, const double* covparms, const int* status,
                            const long long* bad, double* out, long long* dev_status,
                            cudaStream_t st) {
-    k_profile<<<1, 256, 0, st>>>(partials, nblk, nstat, p, cov, n, covparms, status, bad, out,
+    if (nstat > REC_MAX) return cudaErrorInvalidValue;
+    k_profile<<<1, 256, 0, st>>>(partials, nblk, nstat, p, q, n, covparms, status, bad, out,
                                  dev_status);
     return cudaGetLastError();
 }
@@ -508,9 +527,14 @@ cudaError_t launch_cov_pairs(int cov, const double* covparms, const double* tab,
     case COV_MATERN:
         k_cov_pairs<COV_MATERN><<<blocks, tpb, 0, st>>>(covparms, tab, d, npairs, la, lb, same, C, dC);
         break;
-    default:
+    case COV_ST:
         k_cov_pairs<COV_ST><<<blocks, tpb, 0, st>>>(covparms, tab, d, npairs, la, lb, same, C, dC);
         break;
+    case COV_ANISO:
+        k_cov_pairs<COV_ANISO><<<blocks, tpb, 0, st>>>(covparms, tab, d, npairs, la, lb, same, C, dC);
+        break;
+    default:
+        return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }

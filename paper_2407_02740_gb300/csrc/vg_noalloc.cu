@@ -65,10 +65,8 @@ VECCHIA_API vec_status vecchia_loglik_grad_info_noalloc(
     if (!locs || !y || !X || !NNarray || !covparms || !out || !dev_status)
         return nfail(VEC_ERR_ARG, "a required pointer is NULL");
     if (n < 1 || n > (int64_t)INT_MAX) return nfail(VEC_ERR_ARG, "n = %lld out of range", (long long)n);
-    if (covfun != VEC_EXP_ISO && covfun != VEC_MATERN_ISO && covfun != VEC_EXP_SPACETIME)
-        return nfail(VEC_ERR_ARG, "unknown covariance function %d", (int)covfun);
-    if (d < 1 || d > vg::DMAX || (covfun == VEC_EXP_SPACETIME && d != 3))
-        return nfail(VEC_ERR_ARG, "d = %d not allowed for this covariance function", d);
+    if (vecchia_nparms_d(covfun, d) < 0)
+        return nfail(VEC_ERR_ARG, "covariance function %d does not take d = %d", (int)covfun, d);
     if (p < 1 || p > vg::PMAX) return nfail(VEC_ERR_ARG, "p = %d out of range [1, %d]", p, vg::PMAX);
     if (m < 0 || m > vg::KMAX - 1)
         return nfail(VEC_ERR_UNSUPPORTED, "m = %d out of range [0, %d]", m, vg::KMAX - 1);
@@ -130,7 +128,7 @@ VECCHIA_API vec_status vecchia_loglik_grad_info_noalloc(
     a.acc_per_lane = plan.acc_per_lane; a.tab_in_smem = plan.tab_smem;
     e = vg::launch_pass(cov, plan, a, st);
     if (e != cudaSuccess) return nfail(VEC_ERR_CUDA, "launching the pass kernel: %s", cudaGetErrorString(e));
-    e = vg::launch_profile(partials, plan.grid, plan.nstat, p, cov, n, covparms, status, bad, out,
+    e = vg::launch_profile(partials, plan.grid, plan.nstat, p, vg::nparms(cov, d), n, covparms, status, bad, out,
                            reinterpret_cast<long long*>(dev_status), st);
     if (e != cudaSuccess) return nfail(VEC_ERR_CUDA, "launching the profile kernel: %s", cudaGetErrorString(e));
     return VEC_OK;

@@ -97,7 +97,7 @@ struct SlotLayout {
     int K, A, Y, inv, loc, bacc, b, G, D1, nT, Vbyte, bytes;
     __host__ __device__ void init(int m, int d, int p, int cov, int nv, int tsize) {
         K = m + 1;
-        int Q = npair_derivs(cov) + 1;
+        int Q = npair_derivs(cov, d) + 1;
         A = 0;
         Y = A + K * (K + 1) / 2;
         inv = Y + (1 + p) * K;
@@ -167,9 +167,11 @@ struct PassEnv {
     // theta-derived
     double nu, m_psi, sig2, inv_r1, inv_r2;
     T sig2T, diagC, inv_r1T, inv_r2T;
+    const double* inv_rk;  // COV_ANISO: 1 / rho_k, k < d (shared memory)
+    const T* inv_rkT;
     const Tab* tab;
     // record formulas and per-lane sums
-    const uint32_t* sidx;
+    const uint64_t* sidx;
     double* acc;
     int nstat, vb0, vstep, vmm;
     // factor mode: when set, the body stops after b and writes it here (row i at
@@ -177,6 +179,105 @@ struct PassEnv {
     // neighbour NNarray[i][c], 0 for padding)
     double* factor;
 };
+
+// Record formulas: entry t of the per-observation record is V[u1] V[v1] + V[u2] V[v2],
+// the four indices packed as 16-bit fields.
+__host__ __device__ constexpr uint64_t rec_pack(int a, int b, int c, int e) {
+    return (uint64_t)a | ((uint64_t)b << 16) | ((uint64_t)c << 32) | ((uint64_t)e << 48);
+}
+
+// Writes the record formulas for p regression columns and Q derivative parameters.
+//   V[0] = 1, V[1] = 0, V[2] = logdet_i, V[3] = ell, V[4..4+p) = x,
+//   V[vb_j + 0] = md_j, +1 = dell_j, +2.. = dx_j (p), +2+p = -md_j/2,
+//   then mm_jl = m_j . m_l for j <= l (from vmm on).
+__device__ inline void build_record_index(uint64_t* sidx, int p, int Q, int vb0, int vstep,
+                                          int vmm) {
+    int t = 0;
+    sidx[t++] = rec_pack(2, 0, 1, 1);                                   // logdet
+    sidx[t++] = rec_pack(3, 3, 1, 1);                                   // ySy
+    for (int a = 0; a < p; ++a)
+        for (int b = a; b < p; ++b) sidx[t++] = rec_pack(4 + a, 4 + b, 1, 1);   // XSX
+    for (int a = 0; a < p; ++a) sidx[t++] = rec_pack(3, 4 + a, 1, 1);           // ySX
+    for (int j = 0; j < Q; ++j) {
+        const int vb = vb0 + j * vstep;
+        sidx[t++] = rec_pack(vb, 0, 1, 1);                              // dlogdet_j
+        sidx[t++] = rec_pack(3, vb + 1, vb + 1, 3);                     // dySy_j = 2 ell dell_j
+        for (int a = 0; a < p; ++a) sidx[t++] = rec_pack(vb + 1, 4 + a, 3, vb + 2 + a);  // dySX
+        for (int a = 0; a < p; ++a)
+            for (int b = a; b < p; ++b)
+                sidx[t++] = rec_pack(vb + 2 + a, 4 + b, 4 + a, vb + 2 + b);          // dXSX
+    }
+    int mm = vmm;
+    for (int j = 0; j < Q; ++j)
+        for (int l = j; l < Q; ++l)
+            sidx[t++] = rec_pack(mm++, 0, vb0 + j * vstep, vb0 + l * vstep + 2 + p);  // info
+}
+
+// Left-looking Cholesky of the packed block A (Kp x Kp) with the rows of Yg (R - Kp
+// augmented rows, stride Kmax) riding along, so the same sweep leaves L^-1 y and L^-1 X in
+// Yg; invd[c] = 1 / L_cc.  Returns false when a pivot is not positive and finite.
+template <int L, typename T>
+__device__ __forceinline__ bool chol_augmented(T* A, T* Yg, T* invd, int Kp, int R, int Kmax,
+                                               int gl, unsigned gmask) {
+    using N = Num<T>;
+    for (int c = 0; c < Kp; ++c) {
+        const T* Lc = A + c * (c + 1) / 2;
+        const int r0 = c + ((gl - c) & (L - 1));
+        for (int r = r0; r < R; r += L) {
+            T* Rr = r < Kp ? A + r * (r + 1) / 2 : Yg + (r - Kp) * Kmax;
+            T v0 = Rr[c], v1 = (T)0;
+            int s = 0;
+            for (; s + 1 < c; s += 2) {
+                v0 = N::fma_(-Rr[s], Lc[s], v0);
+                v1 = N::fma_(-Rr[s + 1], Lc[s + 1], v1);
+            }
+            if (s < c) v0 = N::fma_(-Rr[s], Lc[s], v0);
+            Rr[c] = v0 + v1;
+        }
+        gsync<L>(gmask);
+        const T vc = Lc[c];
+        if (!(vc > (T)0) || !N::finite_(vc)) return false;
+        const T ic = N::rsqrt_pivot(vc);
+        if (r0 == c) invd[c] = ic;
+        for (int r = (r0 == c ? r0 + L : r0); r < R; r += L) {
+            T* Rr = r < Kp ? A + r * (r + 1) / 2 : Yg + (r - Kp) * Kmax;
+            Rr[c] *= ic;
+        }
+        gsync<L>(gmask);
+    }
+    return true;
+}
+
+// b = last row of L^-1 (L^T b^T = e_last), into bv; bacc is scratch.
+template <int L, typename T>
+__device__ __forceinline__ void last_row_of_inverse(const T* A, const T* invd, T* bacc, T* bv,
+                                                    int Kp, int gl, unsigned gmask) {
+    using N = Num<T>;
+    const int last = Kp - 1;
+    for (int a = gl; a < Kp; a += L) bacc[a] = (a == last) ? (T)1 : (T)0;
+    gsync<L>(gmask);
+    for (int c = last; c >= 0; --c) {
+        const T bc = bacc[c] * invd[c];
+        if (((c - gl) & (L - 1)) == 0) bv[c] = bc;
+        const T* Lr = A + c * (c + 1) / 2;
+        for (int a = gl; a < c; a += L) bacc[a] = N::fma_(-Lr[a], bc, bacc[a]);
+        gsync<L>(gmask);
+    }
+}
+
+// Adds the per-observation record (formulas in sidx over the value vector V) to the
+// lane's FP64 running sums: lane gl owns entries gl, gl + L, ...
+template <int L>
+__device__ __forceinline__ void accumulate_record(const uint64_t* sidx, const double* V,
+                                                  double* acc, int nstat, int gl,
+                                                  unsigned gmask) {
+    for (int t = gl, k = 0; t < nstat; t += L, ++k) {
+        const uint64_t w = sidx[t];
+        const double v1 = V[w & 0xffffu] * V[(w >> 16) & 0xffffu];
+        acc[k] += fma(V[(w >> 32) & 0xffffu], V[w >> 48], v1);
+    }
+    gsync<L>(gmask);
+}
 
 // Algorithm 1 for observation i of the dataset in E (all L lanes of the group call it).
 template <int COV, int L, typename T, typename Tab>
@@ -195,7 +296,7 @@ __device__ __forceinline__ void vecchia_point(const PassEnv<T, Tab>& E, long lon
     const T sig2T = E.sig2T, diagC = E.diagC, inv_r1T = E.inv_r1T, inv_r2T = E.inv_r2T;
     const double inv_r1 = E.inv_r1, inv_r2 = E.inv_r2, m_psi = E.m_psi;
     const Tab* tab = E.tab;
-    const uint32_t* sidx = E.sidx;
+    const uint64_t* sidx = E.sidx;
     double* acc = E.acc;
     const int vb0 = E.vb0, vstep = E.vstep, vmm = E.vmm;
     // ---------------- gather ----------------
@@ -273,34 +374,7 @@ __device__ __forceinline__ void vecchia_point(const PassEnv<T, Tab>& E, long lon
 
     // ---------------- Cholesky + forward solves of y and X ----------------
     // combined rows: r < Kp -> matrix row r (packed), r >= Kp -> augmented row r - Kp
-    const int R = Kp + 1 + p;
-    bool pd = true;
-    for (int c = 0; c < Kp; ++c) {
-        const T* Lc = A + c * (c + 1) / 2;
-        const int r0 = c + ((gl - c) & (L - 1));
-        for (int r = r0; r < R; r += L) {
-            T* Rr = r < Kp ? A + r * (r + 1) / 2 : Yg + (r - Kp) * Kmax;
-            T v0 = Rr[c], v1 = (T)0;
-            int s = 0;
-            for (; s + 1 < c; s += 2) {
-                v0 = N::fma_(-Rr[s], Lc[s], v0);
-                v1 = N::fma_(-Rr[s + 1], Lc[s + 1], v1);
-            }
-            if (s < c) v0 = N::fma_(-Rr[s], Lc[s], v0);
-            Rr[c] = v0 + v1;
-        }
-        gsync<L>(gmask);
-        const T vc = Lc[c];
-        if (!(vc > (T)0) || !N::finite_(vc)) { pd = false; break; }
-        const T ic = N::rsqrt_pivot(vc);
-        if (r0 == c) invd[c] = ic;
-        for (int r = (r0 == c ? r0 + L : r0); r < R; r += L) {
-            T* Rr = r < Kp ? A + r * (r + 1) / 2 : Yg + (r - Kp) * Kmax;
-            Rr[c] *= ic;
-        }
-        gsync<L>(gmask);
-    }
-    if (!pd) {
+    if (!chol_augmented<L, T>(A, Yg, invd, Kp, Kp + 1 + p, Kmax, gl, gmask)) {
         if (gl == 0) report(E.status, E.bad, ST_NOT_PD, i);
         gsync<L>(gmask);
         return;
@@ -308,15 +382,7 @@ __device__ __forceinline__ void vecchia_point(const PassEnv<T, Tab>& E, long lon
     const int last = Kp - 1;
 
     // ---------------- b = last row of L^-1 (L^T b^T = e_last) ----------------
-    for (int a = gl; a < Kp; a += L) bacc[a] = (a == last) ? (T)1 : (T)0;
-    gsync<L>(gmask);
-    for (int c = last; c >= 0; --c) {
-        const T bc = bacc[c] * invd[c];
-        if (((c - gl) & (L - 1)) == 0) bv[c] = bc;
-        const T* Lr = A + c * (c + 1) / 2;
-        for (int a = gl; a < c; a += L) bacc[a] = N::fma_(-Lr[a], bc, bacc[a]);
-        gsync<L>(gmask);
-    }
+    last_row_of_inverse<L, T>(A, invd, bacc, bv, Kp, gl, gmask);
     if (E.factor) {
         double* fr = E.factor + i * (long long)(m + 1);
         for (int c = gl; c <= m; c += L) fr[c] = (c < Kp) ? (double)bv[Kp - 1 - c] : 0.0;
@@ -453,12 +519,207 @@ __device__ __forceinline__ void vecchia_point(const PassEnv<T, Tab>& E, long lon
     }
 
     // ---------------- accumulate the record (FP64) ----------------
-    for (int t = gl, k = 0; t < E.nstat; t += L, ++k) {
-        const uint32_t w = sidx[t];
-        const double v1 = V[w & 255u] * V[(w >> 8) & 255u];
-        acc[k] += fma(V[(w >> 16) & 255u], V[w >> 24], v1);
+    accumulate_record<L>(sidx, V, acc, E.nstat, gl, gmask);
+}
+
+// Algorithm 1 for the exponential with one range per coordinate (COV_ANISO): Q = d + 1
+// derivative vectors (d ranges, then the nugget), too many for per-lane registers, so
+// every per-parameter quantity lives in the slot and the work on it is split into items
+// spread over the group's lanes:
+//   covariance  C = sigma2 e^-D, D = |h / rho| (coordinates stored divided by their
+//               ranges), and w = C / D kept per pair
+//   g_k         = dSigma_k b^T with dC/drho_k = w u_k^2 / rho_k (u = scaled difference),
+//               pairs once in the round-robin schedule, the 1/rho_k applied afterwards
+//   m_j         = L^-1 g_j column by column, items (j, row) over the lanes
+//   values      one dot product per item: dell_j, dx_jt (with hat()), m_j . m_l
+template <int L, typename T, typename Tab>
+__device__ __forceinline__ void vecchia_point_aniso(const PassEnv<T, Tab>& E, long long i) {
+    using N = Num<T>;
+    const int gl = E.gl;
+    const unsigned gmask = E.gmask;
+    const int d = E.d, p = E.p, m = E.m, Kmax = E.Kmax;
+    const int NG = d, Q = d + 1;
+    T* A = E.A; T* Yg = E.Yg; T* invd = E.invd; T* loc = E.loc; T* bacc = E.bacc;
+    T* bv = E.bv; T* G = E.G; T* D1 = E.D1;
+    double* V = E.V;
+    // ---------------- gather ----------------
+    const int32_t* row = E.NN + i * (long long)(m + 1);
+    int cnt = 0, badrow = 0;
+    for (int c = gl; c <= m; c += L) {
+        const int v = row[c];
+        if (c == 0) badrow |= (v != (int)i);
+        else if (v >= 0) {
+            cnt++;
+            badrow |= (v >= i) | (c >= 2 && row[c - 1] < 0);
+        } else if (v != -1) badrow = 1;
+    }
+    cnt = gsum<L>(cnt, gmask);
+    badrow = gsum<L>(badrow, gmask);
+    if (badrow) {
+        if (gl == 0) report(E.status, E.bad, ST_ARG, i);
+        return;
+    }
+    const int Kp = cnt + 1;
+    const double* li = E.locs + i * (long long)d;
+    for (int a = gl; a < Kp; a += L) {
+        const int j = row[Kp - 1 - a];
+        E.idx[a] = j;
+        for (int k = 0; k < d; ++k)
+            loc[k * Kmax + a] = (T)((E.locs[(long long)j * d + k] - li[k]) * E.inv_rk[k]);
+        Yg[a] = (T)E.y[j];
+        for (int t = 0; t < p; ++t) Yg[(1 + t) * Kmax + a] = (T)E.X[(long long)j * p + t];
     }
     gsync<L>(gmask);
+
+    // ---------------- covariance assembly ----------------
+    const int ntri = Kp * (Kp + 1) / 2;
+    for (int e = gl; e < ntri; e += L) {
+        int a = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+        while (a * (a + 1) / 2 > e) --a;
+        while ((a + 1) * (a + 2) / 2 <= e) ++a;
+        const int c = e - a * (a + 1) / 2;
+        T C;
+        if (a == c) {
+            C = E.diagC;
+        } else {
+            T s0 = (T)0, s1 = (T)0;
+            int k = 0;
+            for (; k + 1 < d; k += 2) {
+                const T t0 = loc[k * Kmax + a] - loc[k * Kmax + c];
+                const T t1 = loc[(k + 1) * Kmax + a] - loc[(k + 1) * Kmax + c];
+                s0 = N::fma_(t0, t0, s0);
+                s1 = N::fma_(t1, t1, s1);
+            }
+            if (k < d) {
+                const T t0 = loc[k * Kmax + a] - loc[k * Kmax + c];
+                s0 = N::fma_(t0, t0, s0);
+            }
+            const T Dd = N::sqrt_(s0 + s1);
+            C = E.sig2T * N::exp_(-Dd);
+            D1[a * (a - 1) / 2 + c] = Dd > (T)0 ? C / Dd : (T)0;
+        }
+        A[e] = C;
+    }
+    gsync<L>(gmask);
+
+    // ---------------- Cholesky + forward solves, b ----------------
+    if (!chol_augmented<L, T>(A, Yg, invd, Kp, Kp + 1 + p, Kmax, gl, gmask)) {
+        if (gl == 0) report(E.status, E.bad, ST_NOT_PD, i);
+        gsync<L>(gmask);
+        return;
+    }
+    const int last = Kp - 1;
+    last_row_of_inverse<L, T>(A, invd, bacc, bv, Kp, gl, gmask);
+    if (E.factor) {
+        double* fr = E.factor + i * (long long)(m + 1);
+        for (int c = gl; c <= m; c += L) fr[c] = (c < Kp) ? (double)bv[Kp - 1 - c] : 0.0;
+        gsync<L>(gmask);
+        return;
+    }
+
+    // ---------------- g_j = dSigma_j b^T ----------------
+    for (int a = gl; a < Kp; a += L) {
+        for (int k = 0; k < NG; ++k) G[k * Kmax + a] = (T)0;
+        G[NG * Kmax + a] = E.sig2T * bv[a];
+    }
+    gsync<L>(gmask);
+    {
+        const int Nv = (Kp & 1) ? Kp + 1 : Kp;
+        const int npr = Nv / 2;
+        for (int r = 0; r < Nv - 1; ++r) {
+            for (int k2 = gl; k2 < npr; k2 += L) {
+                int a, c;
+                if (!circle_pair(Kp, Nv, r, k2, a, c)) continue;
+                const T w = D1[a * (a - 1) / 2 + c];
+                const T ba = bv[a], bc = bv[c];
+                for (int k = 0; k < NG; ++k) {
+                    const T t = loc[k * Kmax + a] - loc[k * Kmax + c];
+                    const T v = (w * t) * t;
+                    G[k * Kmax + a] = N::fma_(v, bc, G[k * Kmax + a]);
+                    G[k * Kmax + c] = N::fma_(v, ba, G[k * Kmax + c]);
+                }
+            }
+            gsync<L>(gmask);
+        }
+    }
+    // dC/drho_k = w u_k^2 / rho_k
+    for (int a = gl; a < Kp; a += L)
+        for (int k = 0; k < NG; ++k) G[k * Kmax + a] *= E.inv_rkT[k];
+    gsync<L>(gmask);
+
+    // ---------------- m_j = L^-1 g_j (column sweep, items (j, row a > c)) ----------------
+    for (int c = 0; c < Kp; ++c) {
+        const T ic = invd[c];
+        for (int j = gl; j < Q; j += L) G[j * Kmax + c] *= ic;
+        gsync<L>(gmask);
+        const int nr = Kp - 1 - c;
+        if (nr > 0) {
+            const T* Lcol = A;   // entry (a, c) at a (a + 1) / 2 + c
+            int j = gl / nr, off = gl - (gl / nr) * nr;
+            const int jstep = L / nr, ostep = L - (L / nr) * nr;
+            for (; j < Q;) {
+                const int a = c + 1 + off;
+                G[j * Kmax + a] = N::fma_(-Lcol[a * (a + 1) / 2 + c], G[j * Kmax + c], G[j * Kmax + a]);
+                j += jstep;
+                off += ostep;
+                if (off >= nr) { off -= nr; ++j; }
+            }
+        }
+        gsync<L>(gmask);
+    }
+
+    // ---------------- per-observation values ----------------
+    const int vb0 = E.vb0, vstep = E.vstep, vmm = E.vmm;
+    if (gl == 0) {
+        V[0] = 1.0;
+        V[1] = 0.0;
+        V[2] = -2.0 * log((double)invd[last]);
+        V[3] = (double)Yg[last];
+        for (int t = 0; t < p; ++t) V[4 + t] = (double)Yg[(1 + t) * Kmax + last];
+    }
+    for (int j = gl; j < Q; j += L) {
+        const double md = (double)G[j * Kmax + last];
+        V[vb0 + j * vstep] = md;
+        V[vb0 + j * vstep + 2 + p] = -0.5 * md;
+    }
+    // items: (j, t) for the y / X dot products (t = 0: y, t >= 1: column t - 1), then the
+    // pairs j <= l of m_j . m_l in the order of the record
+    const int P1 = 1 + p;
+    const int nyx = Q * P1, nitems = nyx + Q * (Q + 1) / 2;
+    for (int u = gl; u < nitems; u += L) {
+        if (u < nyx) {
+            const int j = u / P1, t = u - j * P1;
+            const T* g = G + j * Kmax;
+            const T* z = Yg + t * Kmax;
+            T s0 = (T)0, s1 = (T)0;
+            int a = 0;
+            for (; a + 1 < last; a += 2) {
+                s0 = N::fma_(g[a], z[a], s0);
+                s1 = N::fma_(g[a + 1], z[a + 1], s1);
+            }
+            if (a < last) s0 = N::fma_(g[a], z[a], s0);
+            s0 = N::fma_(g[last] * (T)0.5, z[last], s0 + s1);   // hat(): last entry halved
+            V[vb0 + j * vstep + 1 + t] = -(double)s0;
+        } else {
+            int r = u - nyx, j = 0;
+            while (r >= Q - j) { r -= Q - j; ++j; }
+            const int l = j + r;
+            const T* g = G + j * Kmax;
+            const T* h = G + l * Kmax;
+            T s0 = (T)0, s1 = (T)0;
+            int a = 0;
+            for (; a + 1 < Kp; a += 2) {
+                s0 = N::fma_(g[a], h[a], s0);
+                s1 = N::fma_(g[a + 1], h[a + 1], s1);
+            }
+            if (a < Kp) s0 = N::fma_(g[a], h[a], s0);
+            V[vmm + (u - nyx)] = (double)(s0 + s1);
+        }
+    }
+    gsync<L>(gmask);
+
+    // ---------------- accumulate the record (FP64) ----------------
+    accumulate_record<L>(E.sidx, V, E.acc, E.nstat, gl, gmask);
 }
 
 // The FP32 (mixed) instantiations are latency-bound: ask for three resident blocks of 256
@@ -470,11 +731,8 @@ constexpr int pass_min_blocks(int tsize) { return tsize == 4 ? 3 : 1; }
 template <int COV, int L, typename T>
 __global__ void __launch_bounds__(256, pass_min_blocks(sizeof(T))) k_pass(PassArgs args) {
     extern __shared__ __align__(16) double smem[];
-    using N = Num<T>;
     using MT = MaternT<T>;
     using Tab = typename MT::Tab;
-    constexpr int NG = npair_derivs(COV);
-    constexpr int Q = NG + 1;
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int gl = lane & (L - 1);
@@ -483,8 +741,10 @@ __global__ void __launch_bounds__(256, pass_min_blocks(sizeof(T))) k_pass(PassAr
     const unsigned gmask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << (lane & ~(L - 1)));
     const int d = args.d, p = args.p, m = args.m;
     const int Kmax = m + 1;
+    const int Q = npair_derivs(COV, d) + 1;
 
-    // ---- shared-memory carve-up: [Matern table][stat index table][acc][slots][int slots]
+    // ---- shared-memory carve-up: [Matern table | inverse ranges][stat index table][acc]
+    //      [slots][int slots]
     double* sp = smem;
     const Tab* tab = sizeof(T) == 8 ? reinterpret_cast<const Tab*>(args.mtab)
                                     : reinterpret_cast<const Tab*>(args.mtabf);
@@ -495,8 +755,11 @@ __global__ void __launch_bounds__(256, pass_min_blocks(sizeof(T))) k_pass(PassAr
         tab = reinterpret_cast<const Tab*>(sp);
         sp += nwords;
     }
-    uint32_t* sidx = reinterpret_cast<uint32_t*>(sp);
-    sp += (args.nstat + 1) / 2;
+    double* inv_rk = sp;                                   // COV_ANISO: 1 / rho_k, then in T
+    T* inv_rkT = reinterpret_cast<T*>(sp + DMAX_ANISO);
+    if (COV == COV_ANISO) sp += 2 * DMAX_ANISO;
+    uint64_t* sidx = reinterpret_cast<uint64_t*>(sp);
+    sp += args.nstat;
     double* acc = sp + (size_t)tid * args.acc_per_lane;
     double* accbase = sp;
     sp += (size_t)blockDim.x * args.acc_per_lane;
@@ -516,52 +779,24 @@ __global__ void __launch_bounds__(256, pass_min_blocks(sizeof(T))) k_pass(PassAr
     T* D1 = slot + SL.D1;
     double* V = reinterpret_cast<double*>(slotc + SL.Vbyte);
 
-    // ---- per-observation value vector V and the record formulas (see RecLayout)
-    //   V[0] = 1, V[1] = 0, V[2] = logdet_i, V[3] = ell, V[4..4+p) = x,
-    //   V[vb_j + 0] = md_j, +1 = dell_j, +2.. = dx_j (p), +2+p = -md_j/2,
-    //   then mm_jl = m_j . m_l for j <= l.
-    // Record entry t = V[u1] V[v1] + V[u2] V[v2], indices packed in sidx[t].
-    RecLayout RL;
-    RL.init(p, Q);
+    // ---- per-observation value vector V (see build_record_index)
     const int vb0 = 4 + p, vstep = 3 + p, vmm = vb0 + Q * vstep;
-    if (tid == 0) {
-        auto pk = [](int a, int b, int c, int e) {
-            return (uint32_t)a | ((uint32_t)b << 8) | ((uint32_t)c << 16) | ((uint32_t)e << 24);
-        };
-        int t = 0;
-        sidx[t++] = pk(2, 0, 1, 1);                       // logdet
-        sidx[t++] = pk(3, 3, 1, 1);                       // ySy
-        for (int a = 0; a < p; ++a)
-            for (int b = a; b < p; ++b) sidx[t++] = pk(4 + a, 4 + b, 1, 1);  // XSX
-        for (int a = 0; a < p; ++a) sidx[t++] = pk(3, 4 + a, 1, 1);          // ySX
-        for (int j = 0; j < Q; ++j) {
-            int vb = vb0 + j * vstep;
-            sidx[t++] = pk(vb, 0, 1, 1);                  // dlogdet_j
-            sidx[t++] = pk(3, vb + 1, vb + 1, 3);         // dySy_j = 2 ell dell_j
-            for (int a = 0; a < p; ++a) sidx[t++] = pk(vb + 1, 4 + a, 3, vb + 2 + a);  // dySX
-            for (int a = 0; a < p; ++a)
-                for (int b = a; b < p; ++b)
-                    sidx[t++] = pk(vb + 2 + a, 4 + b, 4 + a, vb + 2 + b);           // dXSX
-        }
-        int mm = vmm;
-        for (int j = 0; j < Q; ++j)
-            for (int l = j; l < Q; ++l) {
-                sidx[t++] = pk(mm++, 0, vb0 + j * vstep, vb0 + l * vstep + 2 + p);  // info
-            }
-    }
+    if (tid == 0) build_record_index(sidx, p, Q, vb0, vstep, vmm);
     for (int k = 0; k < args.acc_per_lane; ++k) acc[k] = 0.0;
 
     // ---- covariance parameters
     const double* th = args.covparms;
     const double sig2 = th[0];
-    const double tau2 = th[nparms(COV) - 1];
-    bool ok = sig2 > 0.0 && tau2 > 0.0 && th[1] > 0.0 && th[2] > 0.0 &&
-              isfinite(sig2) && isfinite(tau2) && isfinite(th[1]) && isfinite(th[2]);
-    if (COV != COV_EXP) ok = ok && th[3] > 0.0 && isfinite(th[3]);
-    if (COV == COV_MATERN) ok = ok && th[2] >= 0.05 && th[2] <= 20.0;
+    const double tau2 = th[nparms(COV, d) - 1];
+    const bool ok = theta_ok(COV, d, th);
     if (!ok) {
         if (blockIdx.x == 0 && tid == 0) report(args.status, args.bad, ST_ARG, -1);
     }
+    if (COV == COV_ANISO && ok)
+        for (int k = tid; k < d; k += blockDim.x) {
+            inv_rk[k] = 1.0 / th[1 + k];
+            inv_rkT[k] = (T)inv_rk[k];
+        }
     const T sig2T = (T)sig2;
     const T diagC = (T)(sig2 * (1.0 + tau2));
     // EXP: rho = th[1]; MATERN: rho = th[1], nu = th[2]; ST: rho_s = th[1], rho_t = th[2]
@@ -583,10 +818,13 @@ __global__ void __launch_bounds__(256, pass_min_blocks(sizeof(T))) k_pass(PassAr
     E.nu = (COV == COV_MATERN) ? th[2] : 0.0; E.m_psi = m_psi; E.sig2 = sig2;
     E.inv_r1 = inv_r1; E.inv_r2 = inv_r2;
     E.sig2T = sig2T; E.diagC = diagC; E.inv_r1T = inv_r1T; E.inv_r2T = inv_r2T;
+    E.inv_rk = inv_rk; E.inv_rkT = inv_rkT;
     E.tab = tab; E.sidx = sidx; E.acc = acc; E.nstat = args.nstat;
     E.vb0 = vb0; E.vstep = vstep; E.vmm = vmm; E.factor = nullptr;
-    for (long long i = (long long)blockIdx.x * ngrp + grp; ok && i < n; i += gstride)
-        vecchia_point<COV, L, T, Tab>(E, i);
+    for (long long i = (long long)blockIdx.x * ngrp + grp; ok && i < n; i += gstride) {
+        if constexpr (COV == COV_ANISO) vecchia_point_aniso<L, T, Tab>(E, i);
+        else vecchia_point<COV, L, T, Tab>(E, i);
+    }
 
     // ---------------- block reduction (fixed order) ----------------
     __syncthreads();
@@ -607,8 +845,6 @@ __global__ void __launch_bounds__(256, pass_min_blocks(sizeof(T))) k_pass_batch(
     extern __shared__ __align__(16) double smem[];
     using MT = MaternT<T>;
     using Tab = typename MT::Tab;
-    constexpr int NG = npair_derivs(COV);
-    constexpr int Q = NG + 1;
     const PassArgs& args = bargs.base;
     __shared__ int s_tile;
     const int tid = threadIdx.x;
@@ -619,15 +855,19 @@ __global__ void __launch_bounds__(256, pass_min_blocks(sizeof(T))) k_pass_batch(
     const unsigned gmask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << (lane & ~(L - 1)));
     const int d = args.d, p = args.p;
     const int Kmax = args.m + 1;
-    const int q = nparms(COV);
+    const int q = nparms(COV, d);
+    const int Q = npair_derivs(COV, d) + 1;
 
     double* sp = smem;
     Tab* stab = reinterpret_cast<Tab*>(sp);
     const int tab_words = (COV == COV_MATERN && args.tab_in_smem)
                               ? (sizeof(T) == 8 ? MT_DOUBLES : (MT_FLOATS + 1) / 2) : 0;
     sp += tab_words;
-    uint32_t* sidx = reinterpret_cast<uint32_t*>(sp);
-    sp += (args.nstat + 1) / 2;
+    double* inv_rk = sp;                                   // COV_ANISO: 1 / rho_k, then in T
+    T* inv_rkT = reinterpret_cast<T*>(sp + DMAX_ANISO);
+    if (COV == COV_ANISO) sp += 2 * DMAX_ANISO;
+    uint64_t* sidx = reinterpret_cast<uint64_t*>(sp);
+    sp += args.nstat;
     double* acc = sp + (size_t)tid * args.acc_per_lane;
     double* accbase = sp;
     sp += (size_t)blockDim.x * args.acc_per_lane;
@@ -638,31 +878,8 @@ __global__ void __launch_bounds__(256, pass_min_blocks(sizeof(T))) k_pass_batch(
                grp * Kmax;
     T* slot = reinterpret_cast<T*>(slotc);
 
-    RecLayout RL;
-    RL.init(p, Q);
     const int vb0 = 4 + p, vstep = 3 + p, vmm = vb0 + Q * vstep;
-    if (tid == 0) {
-        auto pk = [](int a, int b, int c, int e) {
-            return (uint32_t)a | ((uint32_t)b << 8) | ((uint32_t)c << 16) | ((uint32_t)e << 24);
-        };
-        int t = 0;
-        sidx[t++] = pk(2, 0, 1, 1);
-        sidx[t++] = pk(3, 3, 1, 1);
-        for (int a = 0; a < p; ++a)
-            for (int b = a; b < p; ++b) sidx[t++] = pk(4 + a, 4 + b, 1, 1);
-        for (int a = 0; a < p; ++a) sidx[t++] = pk(3, 4 + a, 1, 1);
-        for (int j = 0; j < Q; ++j) {
-            int vb = vb0 + j * vstep;
-            sidx[t++] = pk(vb, 0, 1, 1);
-            sidx[t++] = pk(3, vb + 1, vb + 1, 3);
-            for (int a = 0; a < p; ++a) sidx[t++] = pk(vb + 1, 4 + a, 3, vb + 2 + a);
-            for (int a = 0; a < p; ++a)
-                for (int b = a; b < p; ++b) sidx[t++] = pk(vb + 2 + a, 4 + b, 4 + a, vb + 2 + b);
-        }
-        int mm = vmm;
-        for (int j = 0; j < Q; ++j)
-            for (int l = j; l < Q; ++l) sidx[t++] = pk(mm++, 0, vb0 + j * vstep, vb0 + l * vstep + 2 + p);
-    }
+    if (tid == 0) build_record_index(sidx, p, Q, vb0, vstep, vmm);
 
     PassEnv<T, Tab> E;
     E.gl = gl; E.gmask = gmask;
@@ -671,6 +888,7 @@ __global__ void __launch_bounds__(256, pass_min_blocks(sizeof(T))) k_pass_batch(
     E.V = reinterpret_cast<double*>(slotc + SL.Vbyte); E.idx = idx; E.Kmax = Kmax;
     E.d = d; E.p = p; E.sidx = sidx; E.acc = acc; E.nstat = args.nstat;
     E.vb0 = vb0; E.vstep = vstep; E.vmm = vmm;
+    E.inv_rk = inv_rk; E.inv_rkT = inv_rkT;
 
     int cur_b = -1;
     bool ok = false;
@@ -685,10 +903,13 @@ __global__ void __launch_bounds__(256, pass_min_blocks(sizeof(T))) k_pass_batch(
             cur_b = b;
             const double* th = bargs.covparms_b + (size_t)b * q;
             const double sig2 = th[0], tau2 = th[q - 1];
-            ok = sig2 > 0.0 && tau2 > 0.0 && th[1] > 0.0 && th[2] > 0.0 && isfinite(sig2) &&
-                 isfinite(tau2) && isfinite(th[1]) && isfinite(th[2]);
-            if (COV != COV_EXP) ok = ok && th[3] > 0.0 && isfinite(th[3]);
-            if (COV == COV_MATERN) ok = ok && th[2] >= 0.05 && th[2] <= 20.0;
+            ok = theta_ok(COV, d, th);
+            // the previous tile's lanes are past the barrier at the top of the loop
+            if (COV == COV_ANISO && ok)
+                for (int k = tid; k < d; k += blockDim.x) {
+                    inv_rk[k] = 1.0 / th[1 + k];
+                    inv_rkT[k] = (T)inv_rk[k];
+                }
             E.inv_r1 = 1.0 / th[1];
             E.inv_r2 = (COV == COV_ST) ? 1.0 / th[2] : 1.0;
             E.sig2T = (T)sig2;
@@ -728,7 +949,10 @@ __global__ void __launch_bounds__(256, pass_min_blocks(sizeof(T))) k_pass_batch(
         __syncthreads();
         const bool active = bargs.active_b == nullptr || bargs.active_b[b] != 0;
         if (ok && active)
-            for (long long i = tile.y + grp; i < tile.z; i += ngrp) vecchia_point<COV, L, T, Tab>(E, i);
+            for (long long i = tile.y + grp; i < tile.z; i += ngrp) {
+                if constexpr (COV == COV_ANISO) vecchia_point_aniso<L, T, Tab>(E, i);
+                else vecchia_point<COV, L, T, Tab>(E, i);
+            }
         __syncthreads();
         for (int u = tid; u < args.nstat; u += blockDim.x) {
             const int lr = u % L, k = u / L;

@@ -52,15 +52,16 @@ __global__ void __launch_bounds__(128) k_predict(PredArgs a) {
     double* invd = R + Kmax;
     double* loc = invd + Kmax;
     const double* th = a.covparms;
-    const int q = nparms(COV);
+    const int q = nparms(COV, d);
     const double sig2 = th[0], tau2 = th[q - 1];
-    bool ok = sig2 > 0.0 && tau2 > 0.0 && th[1] > 0.0 && th[2] > 0.0 && isfinite(sig2) &&
-              isfinite(tau2) && isfinite(th[1]) && isfinite(th[2]);
-    if (COV != COV_EXP) ok = ok && th[3] > 0.0 && isfinite(th[3]);
-    if (COV == COV_MATERN) ok = ok && th[2] >= 0.05 && th[2] <= 20.0;
-    if (!ok) {
+    if (!theta_ok(COV, d, th)) {   // the same for every thread of the grid
         if (blockIdx.x == 0 && tid == 0) report(a.status, a.bad, ST_ARG, -1);
         return;
+    }
+    __shared__ double s_invr[DMAX_ANISO];   // COV_ANISO: 1 / rho_k
+    if (COV == COV_ANISO) {
+        for (int k = tid; k < d; k += blockDim.x) s_invr[k] = 1.0 / th[1 + k];
+        __syncthreads();
     }
     const double inv_r1 = 1.0 / th[1];
     const double inv_r2 = (COV == COV_ST) ? 1.0 / th[2] : 1.0;
@@ -95,7 +96,8 @@ __global__ void __launch_bounds__(128) k_predict(PredArgs a) {
                 const int j = row[cnt - 1 - b];
                 for (int k = 0; k < d; ++k)
                     loc[k * Kmax + b] = (a.locs[(long long)j * d + k] - qi[k]) *
-                                        ((COV == COV_ST && k == 2) ? inv_r2 : inv_r1);
+                                        (COV == COV_ANISO ? s_invr[k]
+                                                          : ((COV == COV_ST && k == 2) ? inv_r2 : inv_r1));
                 double r = a.y[j];
                 for (int t = 0; t < p; ++t) r = fma(-a.X[(long long)j * p + t], a.beta[t], r);
                 R[b] = r;
@@ -115,7 +117,7 @@ __global__ void __launch_bounds__(128) k_predict(PredArgs a) {
             double C;
             if (r == c) {
                 C = (r == last) ? diag_tgt : diag_obs;
-            } else if (COV == COV_EXP) {
+            } else if (COV == COV_EXP || COV == COV_ANISO) {
                 double s = 0.0;
                 for (int k = 0; k < d; ++k) {
                     const double t = loc[k * Kmax + r] - loc[k * Kmax + c];
@@ -187,6 +189,7 @@ static const void* predict_kernel(int cov, int L) {
     VG_PRED(COV_EXP, 4) VG_PRED(COV_EXP, 8) VG_PRED(COV_EXP, 16) VG_PRED(COV_EXP, 32)
     VG_PRED(COV_MATERN, 4) VG_PRED(COV_MATERN, 8) VG_PRED(COV_MATERN, 16) VG_PRED(COV_MATERN, 32)
     VG_PRED(COV_ST, 4) VG_PRED(COV_ST, 8) VG_PRED(COV_ST, 16) VG_PRED(COV_ST, 32)
+    VG_PRED(COV_ANISO, 4) VG_PRED(COV_ANISO, 8) VG_PRED(COV_ANISO, 16) VG_PRED(COV_ANISO, 32)
 #undef VG_PRED
     return nullptr;
 }
@@ -212,11 +215,15 @@ cudaError_t launch_predict(int cov, const double* locs, const double* y, const d
     const void* fn = predict_kernel(cov, L);
     if (!fn) return cudaErrorInvalidValue;
     int dev = 0, optin = 0;
+    cudaFuncAttributes fa;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, fn);
     if (e != cudaSuccess) return e;
-    if ((int)smem > optin) return cudaErrorInvalidValue;
-    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    // the dynamic limit leaves room for the kernel's static shared memory
+    const int dyn_max = optin - (int)fa.sharedSizeBytes;
+    if ((int)smem > dyn_max) return cudaErrorInvalidValue;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem);

@@ -41,6 +41,12 @@ def test_host_only_queries_and_argument_errors():
     assert lib.vecchia_nparms(vg.MATERN_ISO) == 4
     assert lib.vecchia_nparms(vg.EXP_SPACETIME) == 4
     assert lib.vecchia_nparms(99) == -1
+    assert lib.vecchia_nparms(vg.EXP_ANISO) == -1          # depends on d
+    assert lib.vecchia_nparms_d(vg.EXP_ANISO, 18) == 20
+    assert lib.vecchia_nparms_d(vg.EXP_ANISO, 21) == -1
+    assert lib.vecchia_nparms_d(vg.EXP_ISO, 4) == -1
+    assert lib.vecchia_nparms_d(vg.EXP_SPACETIME, 2) == -1
+    assert lib.vecchia_nparms_d(vg.MATERN_ISO, 2) == 4
     assert lib.vecchia_max_m() >= 60
     # a NULL handle is rejected before any CUDA call
     assert lib.vecchia_set_lanes(None, 4) == 1
