@@ -22,6 +22,8 @@ Reported beside the device-timed value:
                   the learned start;
   * nn_search  -- the ordered nearest-neighbour search on the device vs the CPU search;
   * prediction -- Vecchia prediction at 100000 new sites of the headline field.
+  * elevators_like -- the exponential with one range per attribute on an Elevators-like
+                  workload (n = 15000, d = 18): passes, fits, the oracle beside them.
 ``--impl reference`` times the CPU oracle itself as the reference arm.
 Multi-GPU runs (torchrun) are independent replicas: each rank evaluates its own copy.
 """
@@ -54,8 +56,8 @@ FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
 # DRAM bytes (read + write) of one launch of the FP64 pass kernel on this workload, from an
 # ncu capture of the current kernel (the summary under profiles/ names the command); set to
 # None whenever the kernel changes until it is captured again.
-TRAFFIC_BYTES = 17338368 + 500736
-TRAFFIC_NOTE = "dram__bytes_read.sum + dram__bytes_write.sum, profiles/k_pass_matern_n100000_m30.md"
+TRAFFIC_BYTES = None
+TRAFFIC_NOTE = "not yet captured for the current kernel"
 
 
 def algorithmic_fma_per_point(K: int, p: int, q: int) -> float:
@@ -451,6 +453,76 @@ def run_prediction(vg, torch, dev, stream, w) -> dict:
                                        "var": float(np.max(np.abs(vgv - vo) / vo))}}
 
 
+def run_elevators(vg, torch, dev, stream) -> dict:
+    """The Elevators-like workload (n = 15000, 18 attributes as locations, exponential with
+    one range per attribute, q = 20, X = 1) at m = 10 and m = 30: the FP64 and mixed passes
+    in their autotuned mappings (CUDA events, median of 5, inputs resident), the FP64 pass
+    against the FP64 peak (algorithmic FMAs as for the headline, q = 20), Fisher-scoring
+    fits from the start values (FP64, and mixed then FP64; tol 1e-4, wall time of the
+    device fit), and the oracle's pass on the host cores.  The paper's fit times for
+    Elevators on its A40 (3.469 s at m = 10, 6.905 s at m = 30) are context."""
+    import oracle
+    import workloads
+    oracle.build()
+    t = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)  # noqa
+    res = {}
+    for m, paper_s in ((10, 3.469), (30, 6.905)):
+        w = workloads.cfg_elevators_like(m=m)
+        q = w.theta_true.size
+        locs, y, X, NN, th = t(w.locs), t(w.y), t(w.X), t(w.NN, torch.int32), t(w.theta_true)
+        r = {"n": w.n, "d": w.d, "m": m, "q": q}
+        for prec in ("fp64", "mixed"):
+            h = vg.Handle(0)
+            tune = vg.vecchia_autotune(locs, y, X, NN, th, w.covfun, prec=prec, stream=stream, handle=h)
+            out, st = vg.vecchia_loglik_grad_info(locs, y, X, NN, th, w.covfun, prec=prec,
+                                                  stream=stream, handle=h)
+            ms = []
+            for _ in range(5):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                vg.vecchia_loglik_grad_info(locs, y, X, NN, th, w.covfun, prec=prec, stream=stream,
+                                            out=out, status=st, handle=h)
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            r[prec] = {"pass_ms": statistics.median(ms), "points_per_s": w.n / (statistics.median(ms) * 1e-3),
+                       "lanes": tune["lanes"], "threads": tune["threads"], "status": int(st[0].item())}
+            if prec == "fp64":
+                g = vg.unpack(out, q, w.p)
+            h.close()
+        Kp = (w.NN >= 0).sum(axis=1)
+        flop = float(sum(2 * algorithmic_fma_per_point(int(k), w.p, q) for k in Kp))
+        r["roofline_fp64_pass"] = {"bound": "alu", "achieved": flop / (r["fp64"]["pass_ms"] * 1e-3) / 1e9,
+                                   "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                                   "frac": flop / (r["fp64"]["pass_ms"] * 1e-3) / 1e9 / FP64_PEAK_GFLOPS,
+                                   "note": "pass call (setup, pass kernel, profile) duration; "
+                                           "covariance evaluations not counted"}
+        for prec in ("fp64", "mixed"):
+            h = vg.Handle(0)
+            vg.vecchia_fit(locs, y, X, NN, w.covfun, w.theta_start, tol=1e-4, prec=prec,
+                           stream=stream, handle=h)                 # graph capture, tuning
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            f = vg.vecchia_fit(locs, y, X, NN, w.covfun, w.theta_start, tol=1e-4, prec=prec,
+                               stream=stream, handle=h)
+            torch.cuda.synchronize()
+            r["fit_" + prec] = {"s": time.perf_counter() - t0, "iters": int(f["iters"]),
+                                "evals": int(f["evals"]), "status": vg.FIT_STATUS.get(int(f["status"])),
+                                "loglik": float(f["loglik"])}
+            h.close()
+        r["fit_paper_a40_s"] = paper_s
+        t0 = time.perf_counter()
+        o = oracle.loglik_grad_info(w.locs, w.y, w.X, w.NN, w.theta_true, w.covfun)
+        cpu_s = time.perf_counter() - t0
+        r["cpu_oracle"] = {"points_per_s": w.n / cpu_s, "cores": os.cpu_count() or 1,
+                           "kind": "oracle", "sample": "one full pass (n = %d)" % w.n}
+        r["rel_diff_vs_oracle"] = {"loglik": abs(g["loglik"] - o["loglik"]) / abs(o["loglik"]),
+                                   "grad": float(np.linalg.norm(g["grad"] - o["grad"]) /
+                                                 max(np.linalg.norm(o["grad"]), np.sqrt(np.trace(o["info"]))))}
+        res["m%d" % m] = r
+    return res
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -610,6 +682,7 @@ def run_ours(args):
     warm = run_warm_start(torch, dev, local)
     nn = run_nn_search(vg, torch, dev, stream)
     pred = run_prediction(vg, torch, dev, stream, w)
+    elev = run_elevators(vg, torch, dev, stream)
 
     if rank != 0:
         if ws > 1:
@@ -678,6 +751,7 @@ def run_ours(args):
         "warm_start": warm,
         "nn_search": nn,
         "prediction": pred,
+        "elevators_like": elev,
     }
     print(json.dumps(line))
     if ws > 1:
