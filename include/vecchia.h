@@ -519,6 +519,17 @@ VECCHIA_API vec_status vecchia_predict(vec_handle h, const double* locs, const d
                                        int64_t* dev_status);
 
 /*
+ * vecchia_measure_peaks -- throughputs of this GPU that bound the pass kernels, measured
+ * on the handle's device and stream (synchronous, ~0.5 s): out[0] FP64 FMA-chain GFLOP/s,
+ * out[1] FP32 FMA-chain GFLOP/s (8 independent chains per thread, 16 warps per SM),
+ * out[2] exponential covariance evaluations per second (square root, exponential and
+ * division per pair, as the pass does them), out[3] Matern evaluations per second (the
+ * per-pass table's value and two derivatives).  out: HOST memory, 4 doubles.  Temporary
+ * device buffers are allocated and freed by the call.
+ */
+VECCHIA_API vec_status vecchia_measure_peaks(vec_handle h, double* out);
+
+/*
  * vecchia_covariance_pairs -- the library's device covariance functions on explicit pairs.
  *
  * For each pair k: C[k] = C(la[k], lb[k]; covparms) including the nugget sigma2 tau2 when

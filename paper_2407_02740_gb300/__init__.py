@@ -91,6 +91,7 @@ def lib():
         L.vecchia_last_error.restype = ctypes.c_char_p
         L.vecchia_nparms.argtypes = [ci]
         L.vecchia_nparms_d.argtypes = [ci, ci]
+        L.vecchia_measure_peaks.argtypes = [P, P]
         L.vecchia_set_lanes.argtypes = [P, ci]
         L.vecchia_set_block_threads.argtypes = [P, ci]
         L.vecchia_set_matern_table.argtypes = [P, ci]
@@ -151,7 +152,7 @@ def lib():
                   L.vecchia_fields_variogram, L.vecchia_mlp_forward, L.vecchia_mlp_grad,
                   L.vecchia_mlp_adam_step, L.vecchia_mlp_column_moments,
                   L.vecchia_fields_warm_start, L.vecchia_ordered_nn, L.vecchia_nearest,
-                  L.vecchia_predict):
+                  L.vecchia_predict, L.vecchia_measure_peaks):
             f.restype = ci
         _lib = L
     return _lib
@@ -841,6 +842,17 @@ def vecchia_loglik_grad_info_host(locs, y, X, NNarray, covparms, covfun: int, pr
     _check(code, bad.value)
     return {"loglik": ll.value, "grad": grad, "info": info, "betahat": beta,
             "bad_index": bad.value}
+
+
+def vecchia_measure_peaks(handle: Handle | None = None, device: int = 0) -> dict:
+    """Measured FP64 / FP32 FMA-chain GFLOP/s and covariance evaluations per second on the
+    device (see vecchia_measure_peaks in include/vecchia.h)."""
+    if handle is None:
+        handle = default_handle(device)
+    out = (ctypes.c_double * 4)()
+    _check(lib().vecchia_measure_peaks(handle.ptr, ctypes.cast(out, ctypes.c_void_p)))
+    return {"fp64_gflops": out[0], "fp32_gflops": out[1], "exp_pairs_per_s": out[2],
+            "matern_pairs_per_s": out[3]}
 
 
 def vecchia_covariance_pairs(covfun: int, covparms, la, lb, same, stream=None,

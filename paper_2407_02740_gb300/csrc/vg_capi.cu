@@ -1581,6 +1581,15 @@ vec_status vecchia_predict(vec_handle h, const double* locs, const double* y, co
     return VEC_OK;
 }
 
+vec_status vecchia_measure_peaks(vec_handle h, double* out) {
+    if (!h || !out) return fail(VEC_ERR_ARG, "vecchia_measure_peaks: NULL argument");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(VEC_ERR_CUDA, "cannot select device %d", h->device);
+    cudaError_t e = vg::measure_peaks(h->nsm, h->stream, out);
+    if (e != cudaSuccess) return cuda_fail(e, "vecchia_measure_peaks");
+    return VEC_OK;
+}
+
 vec_status vecchia_covariance_pairs(vec_handle h, vec_covfun covfun, const double* covparms,
                                     int d, int64_t npairs, const double* la, const double* lb,
                                     const int32_t* same, double* C, double* dC, void* stream) {

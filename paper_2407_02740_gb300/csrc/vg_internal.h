@@ -95,6 +95,9 @@ cudaError_t launch_profile(const double* partials, int nblk, int nstat, int p, i
                            long long n, const double* covparms, const int* status,
                            const long long* bad, double* out, long long* dev_status,
                            cudaStream_t st);
+// Measured throughputs (see vg_peaks.cu): out = {FP64 GFLOP/s, FP32 GFLOP/s, exponential
+// covariance pairs/s, Matern covariance pairs/s}.  Synchronous on st.
+cudaError_t measure_peaks(int nsm, cudaStream_t st, double* out);
 cudaError_t launch_cov_pairs(int cov, const double* covparms, const double* tab, int d,
                              long long npairs, const double* la, const double* lb,
                              const int32_t* same, double* C, double* dC, cudaStream_t st);

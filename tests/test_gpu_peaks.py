@@ -1,0 +1,20 @@
+"""The measured-throughput entry point (the denominators of the pass kernels' roofline):
+positive, FP32 well above FP64 (this GPU's FP64 rate is a small fraction of its FP32
+rate), and a Matern evaluation (three table polynomials) slower than an exponential one."""
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2407_02740_gb300 as vg  # noqa: E402
+
+
+def test_measure_peaks():
+    h = vg.Handle(0)
+    try:
+        p = vg.vecchia_measure_peaks(h)
+    finally:
+        h.close()
+    assert 100.0 < p["fp64_gflops"] < 1e4
+    assert p["fp32_gflops"] > 10.0 * p["fp64_gflops"]
+    assert 0.0 < p["matern_pairs_per_s"] < p["exp_pairs_per_s"]

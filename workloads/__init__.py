@@ -366,7 +366,7 @@ def elevators_ranges(d: int = 18) -> np.ndarray:
     return np.exp(np.linspace(np.log(1.0), np.log(8.0), d))
 
 
-def cfg_elevators_like(seed: int = 1005, n: int = 15000, d: int = 18, m: int = 30,
+def cfg_elevators_like(seed: int = 1010, n: int = 15000, d: int = 18, m: int = 30,
                        m_sim: int = 30) -> Workload:
     """Stands in for the Elevators runs (n = 15k training points, 18 attributes used as
     locations, exponential covariance with one range per attribute, X = 1): attributes
