@@ -19,15 +19,15 @@ constexpr int DMAX_ANISO = 20;          // largest dimension with one range per 
 constexpr int QMAX = DMAX_ANISO + 2;    // largest number of covariance parameters
 
 // Geometry of the per-pass Matern coefficient table (see vg_matern.cuh).  Each function
-// on each interval is a degree-12 polynomial in w stored as 8 FP64 coefficients (w^0..w^7)
-// followed by 5 FP32 coefficients (w^8..w^12, padded to 6 floats): 11 double slots.
+// on each interval is a degree-12 polynomial in w stored in 11 double slots: w^0, w^1 in
+// FP64, w^2..w^7 as (hi, lo) FP32 pairs, then w^8..w^12 in FP32 (padded to 6 floats).
 constexpr int MT_E0 = -30;   // table covers s in [2^-30, 2^13)
 constexpr int MT_E1 = 13;
 constexpr int MT_LOGJ = 2;
 constexpr int MT_J = 1 << MT_LOGJ;
 constexpr int MT_D = 12;     // polynomial degree
 constexpr int MT_NC = MT_D + 1;
-constexpr int MT_NHEAD = 8;  // FP64 coefficients per function
+constexpr int MT_NHEAD = 8;  // slots before the FP32 tail: 2 FP64 + 6 FP32 pairs
 constexpr int MT_FSTRIDE = MT_NHEAD + 3;       // double slots per function
 constexpr int MT_NINT = (MT_E1 - MT_E0) * MT_J;
 constexpr int MT_PER_INT = 3 * MT_FSTRIDE;     // F0, F1, F2 per interval

@@ -101,8 +101,10 @@ static __device__ __noinline__ void matern_small(double nu, double s, double psi
 // Locates s in the table.  Returns the interval index and the local variable w, or
 // -1 when s < 2^E0 (direct formula, includes s == 0), or -2 when s >= 2^E1 (zero).
 // The interval centre 1 + (2j+1)/(2J) is built from bits, so w = mantissa - centre is
-// one exact FP64 subtraction (Sterbenz).
-__device__ __forceinline__ int mtab_locate(double s, double& w, float& wf) {
+// one exact FP64 subtraction (Sterbenz).  w is also returned as an unevaluated sum of two
+// FP32 numbers, wf + wl = w exactly up to 2^-24 of wl: wf the difference of the mantissa
+// truncated to 23 bits (exact in FP32), wl the remaining 29 mantissa bits (>= 0).
+__device__ __forceinline__ int mtab_locate(double s, double& w, float& wf, float& wl) {
     const unsigned long long bits = (unsigned long long)__double_as_longlong(s);
     const int e = (int)((bits >> 52) & 0x7ffull) - 1023;
     if (e < MT_E0) return -1;
@@ -118,22 +120,60 @@ __device__ __forceinline__ int mtab_locate(double s, double& w, float& wf) {
     const float mantf = __uint_as_float(0x3f800000u | (unsigned)((bits >> 29) & 0x7fffffull));
     const float cenf = __uint_as_float(0x3f800000u | (unsigned)((2ull * j + 1ull) << (23 - MT_LOGJ - 1)));
     wf = mantf - cenf;
+    wl = __uint2float_rn((unsigned)(bits & 0x1fffffffull)) * 0x1p-52f;
     return (e - MT_E0) * MT_J + (int)j;
 }
 
-// Degree-12 polynomial in w: the tail w^8..w^12 (summing to below ~1e-9 on every interval,
-// so FP32 rounding there is below 1e-15 absolute) in FP32, the head in FP64.
-__device__ __forceinline__ double horner_split(const double* c, double w, float wf) {
+// FP32 -> FP64 from the bits (integer work only): exact for normal numbers; zero and
+// subnormals (below 1.2e-38, far below every scale the pass uses) give 0.
+__device__ __forceinline__ double f32_to_f64_bits(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned ex = (u >> 23) & 0xffu;
+    if (ex == 0u) return 0.0;
+    const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
+                                 ((unsigned long long)(ex + 896u) << 52) |
+                                 ((unsigned long long)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)b);
+}
+
+// Degree-12 polynomial in w, |w| <= 1/8, evaluated in three precisions (the table layout
+// per function: c0, c1 in FP64; c2..c7 as (hi, lo) FP32 pairs; c8..c12 in FP32):
+//   * the tail w^8..w^12 (summing to below ~1e-9 on every interval) in FP32;
+//   * w^2..w^7 in double-float arithmetic (a value is an unevaluated FP32 pair, ~48
+//     significant bits; the two-product uses the FMA's exact remainder, the sum Knuth's
+//     two-sum);
+//   * the last two Horner steps, c1 and c0, in FP64.
+// The double-float part r(w) enters the result as w^2 r(w), so its rounding (~2^-47
+// relative) lands below 2^-53 of the result: FP64 accuracy (checked against an FP64
+// Horner chain in extended precision on every interval of the table).  FP32 runs at 64x
+// the FP64 rate on this GPU, so the chain costs 3 FP64 FMAs instead of 9 FP64 operations.
+// The error-free steps use explicitly rounded intrinsics so that no multiply-add is fused.
+__device__ __forceinline__ double horner_split(const double* c, double w, float wh, float wl) {
     const float* t = reinterpret_cast<const float*>(c + MT_NHEAD);
-    float pt = t[4];
-    pt = fmaf(pt, wf, t[3]);
-    pt = fmaf(pt, wf, t[2]);
-    pt = fmaf(pt, wf, t[1]);
-    pt = fmaf(pt, wf, t[0]);
-    double p = (double)pt;
+    float ph = t[4];
+    ph = fmaf(ph, wh, t[3]);
+    ph = fmaf(ph, wh, t[2]);
+    ph = fmaf(ph, wh, t[1]);
+    ph = fmaf(ph, wh, t[0]);
+    float pl = 0.0f;
+    const float2* mid = reinterpret_cast<const float2*>(c + 2);
 #pragma unroll
-    for (int k = MT_NHEAD - 1; k >= 0; --k) p = fma(p, w, c[k]);
-    return p;
+    for (int k = MT_NHEAD - 3; k >= 0; --k) {      // c7 .. c2
+        const float2 ck = mid[k];
+        const float hi = __fmul_rn(ph, wh);
+        float lo = fmaf(ph, wh, -hi);               // exact remainder of ph wh
+        lo = fmaf(ph, wl, lo);
+        lo = fmaf(pl, wh, lo);
+        const float sm = __fadd_rn(hi, ck.x);
+        const float z = __fsub_rn(sm, hi);
+        float er = __fadd_rn(__fsub_rn(hi, __fsub_rn(sm, z)), __fsub_rn(ck.x, z));
+        er = __fadd_rn(er, __fadd_rn(lo, ck.y));
+        ph = __fadd_rn(sm, er);
+        pl = __fsub_rn(er, __fsub_rn(ph, sm));
+    }
+    double p = fma(w, f32_to_f64_bits(pl), c[1]);
+    p = fma(w, f32_to_f64_bits(ph), p);
+    return fma(p, w, c[0]);
 }
 
 // The table holds the covariance and its derivatives, not M itself: F0 = sigma2 M,
@@ -143,9 +183,9 @@ __device__ __forceinline__ double horner_split(const double* c, double w, float 
 __device__ __forceinline__ double matern_F0(const double* tab, double s, double nu, double psi,
                                             double sc0) {
     double w;
-    float wf;
-    int it = mtab_locate(s, w, wf);
-    if (it >= 0) return horner_split(tab + it * MT_PER_INT, w, wf);
+    float wf, wl;
+    int it = mtab_locate(s, w, wf, wl);
+    if (it >= 0) return horner_split(tab + it * MT_PER_INT, w, wf, wl);
     if (it == -2) return 0.0;
     if (!(s > 0.0)) return sc0;
     double f0, f1, f2;
@@ -155,12 +195,12 @@ __device__ __forceinline__ double matern_F0(const double* tab, double s, double 
 __device__ __forceinline__ void matern_F12(const double* tab, double s, double nu, double psi,
                                            double sc1, double sc2, double& F1, double& F2) {
     double w;
-    float wf;
-    int it = mtab_locate(s, w, wf);
+    float wf, wl;
+    int it = mtab_locate(s, w, wf, wl);
     if (it >= 0) {
         const double* cf = tab + it * MT_PER_INT;
-        F1 = horner_split(cf + MT_FSTRIDE, w, wf);
-        F2 = horner_split(cf + 2 * MT_FSTRIDE, w, wf);
+        F1 = horner_split(cf + MT_FSTRIDE, w, wf, wl);
+        F2 = horner_split(cf + 2 * MT_FSTRIDE, w, wf, wl);
     } else if (it == -2 || !(s > 0.0)) {
         F1 = 0.0;
         F2 = 0.0;
