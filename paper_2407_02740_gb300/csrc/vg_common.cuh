@@ -78,21 +78,34 @@ struct RecLayout {
 constexpr int REC_MAX = 2 + PMAX * (PMAX + 1) / 2 + PMAX +
                         (QMAX - 1) * (2 + PMAX + PMAX * (PMAX + 1) / 2) + (QMAX - 1) * QMAX / 2;
 
-// 1/sqrt(v) from an FP32 seed and two Newton steps.  Each step forms the residual
-// r = 1 - v y^2 in FP64 and applies the small correction y r / 2 in FP32; the result
-// carries FP64 accuracy (the seed error ~1e-7 is squared twice).  Values outside the
-// FP32 normal range fall back to the FP64 library routine.
+// FP32 -> FP64 from the bits (integer work only): exact for normal numbers; zero and
+// subnormals (below 1.2e-38, far below every scale the kernels use) give 0.
+__device__ __forceinline__ double f32_to_f64_bits(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned ex = (u >> 23) & 0xffu;
+    if (ex == 0u) return 0.0;
+    const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
+                                 ((unsigned long long)(ex + 896u) << 52) |
+                                 ((unsigned long long)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)b);
+}
+
+// 1/sqrt(v), v > 0, for the Cholesky pivots.  The FP32 seed rsqrtf(v) (v's mantissa
+// truncated to 23 bits, built from the bits like the conversions, so no FP64 <-> FP32
+// conversion instruction is issued) has a relative error e < 2^-21; one third-order step
+//   r = 1 - v y^2,  y <- y (1 + r/2 + 3 r^2 / 8)
+// (the series of (1 - r)^(-1/2) to second order) leaves 5/16 |r|^3 ~ 2.5 e^3 < 2^-61, so the
+// result carries FP64 accuracy: r is formed by one FMA from the rounded v y, and the
+// correction is a small multiple of y.  Five FP64 operations.  v outside the FP32 normal
+// range takes the FP64 library routine.
 __device__ __forceinline__ double rsqrt_newton(double v) {
-    float vf = (float)v;
-    if (!(vf > 1e-36f && vf < 1e36f)) return rsqrt(v);
-    double y = (double)rsqrtf(vf);
-    double t = v * y;
-    double r = fma(-t, y, 1.0);
-    y = y + (double)(0.5f * (float)y * (float)r);
-    t = v * y;
-    r = fma(-t, y, 1.0);
-    y = y + (double)(0.5f * (float)y * (float)r);
-    return y;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int ex = (int)((b >> 52) & 0x7ffull) - 1023;
+    if (ex < -126 || ex > 127) return rsqrt(v);
+    const float vf = __uint_as_float(((unsigned)(ex + 127) << 23) | (unsigned)((b >> 29) & 0x7fffffull));
+    const double y = f32_to_f64_bits(rsqrtf(vf));
+    const double r = fma(-v * y, y, 1.0);
+    return fma(y * r, fma(r, 0.375, 0.5), y);
 }
 
 // digamma(x), x > 0: shift upward with psi(x) = psi(x+1) - 1/x until x >= 12, then the

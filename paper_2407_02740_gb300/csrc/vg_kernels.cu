@@ -130,14 +130,16 @@ __device__ void profile_from_totals(const double* tot, int p, int q, long long n
     const double s2 = covparms[0];
     const double nd = (double)n;
 
-    // betahat = XSX^-1 ySX by Cholesky
+    // betahat = XSX^-1 ySX by Cholesky.  A pivot below 1e-14 of its diagonal entry (about
+    // 50 units of rounding) means X' Sigma^-1 X is singular to working precision: betahat
+    // is not identified and the pass reports a non-finite result.
     double Lc[PMAX * PMAX], z[PMAX], beta[PMAX];
     for (int a = 0; a < PMAX; ++a) beta[a] = 0.0;
     bool pd = true;
     for (int c = 0; c < p && pd; ++c) {
         double v = XSX[c * p + c];
         for (int s = 0; s < c; ++s) v -= Lc[c * p + s] * Lc[c * p + s];
-        if (!(v > 0.0)) { pd = false; break; }
+        if (!(v > 1e-14 * XSX[c * p + c])) { pd = false; break; }
         Lc[c * p + c] = sqrt(v);
         for (int r = c + 1; r < p; ++r) {
             double w = XSX[r * p + c];

@@ -124,18 +124,6 @@ __device__ __forceinline__ int mtab_locate(double s, double& w, float& wf, float
     return (e - MT_E0) * MT_J + (int)j;
 }
 
-// FP32 -> FP64 from the bits (integer work only): exact for normal numbers; zero and
-// subnormals (below 1.2e-38, far below every scale the pass uses) give 0.
-__device__ __forceinline__ double f32_to_f64_bits(float f) {
-    const unsigned u = __float_as_uint(f);
-    const unsigned ex = (u >> 23) & 0xffu;
-    if (ex == 0u) return 0.0;
-    const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
-                                 ((unsigned long long)(ex + 896u) << 52) |
-                                 ((unsigned long long)(u & 0x7fffffu) << 29);
-    return __longlong_as_double((long long)b);
-}
-
 // Degree-12 polynomial in w, |w| <= 1/8, evaluated in three precisions (the table layout
 // per function: c0, c1 in FP64; c2..c7 as (hi, lo) FP32 pairs; c8..c12 in FP32):
 //   * the tail w^8..w^12 (summing to below ~1e-9 on every interval) in FP32;
