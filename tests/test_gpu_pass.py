@@ -235,17 +235,17 @@ def test_full_size_matern_100k_matches_oracle():
 @pytest.mark.slow
 @pytest.mark.parametrize("placement", ["global", "shared"])
 def test_full_size_matern_100k_each_table_placement(placement):
-    """The full-size pass with the mapping the autotuner picks on GB300 for FP64 (8 lanes,
-    64 threads) and for mixed precision (16 lanes, 256 threads), with the Matern table in
-    global and in shared memory; the FP64 pass against the oracle, the mixed one within its
-    bounds."""
+    """The full-size pass with the mappings the autotuner picks on GB300 for FP64 (16 lanes,
+    128 threads) and for mixed precision (16 lanes, 256 threads), then FP64 with 8 lanes and
+    64 threads, with the Matern table in global and in shared memory; the FP64 passes
+    against the oracle, the mixed one within its bounds."""
     w = workloads.cfg_matern_100k()
     o = oracle.loglik_grad_info(w.locs, w.y, w.X, w.NN, w.theta_true, w.covfun)
     dev = torch.device("cuda:0")
     t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)  # noqa
     args = (t(w.locs, torch.float64), t(w.y, torch.float64), t(w.X, torch.float64),
             t(w.NN, torch.int32), t(w.theta_true, torch.float64), w.covfun)
-    for prec, lanes, threads in (("fp64", 8, 64), ("mixed", 16, 256)):
+    for prec, lanes, threads in (("fp64", 16, 128), ("mixed", 16, 256), ("fp64", 8, 64)):
         h = vg.Handle(0)
         h.set_lanes(lanes)
         h.set_block_threads(threads)
