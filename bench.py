@@ -56,8 +56,8 @@ FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
 # DRAM bytes (read + write) of one launch of the FP64 pass kernel on this workload, from an
 # ncu capture of the current kernel (the summary under profiles/ names the command); set to
 # None whenever the kernel changes until it is captured again.
-TRAFFIC_BYTES = None
-TRAFFIC_NOTE = "not yet captured for the current kernel"
+TRAFFIC_BYTES = 17344000 + 511232
+TRAFFIC_NOTE = "dram__bytes_read.sum + dram__bytes_write.sum, profiles/k_pass_matern_n100000_m30.md"
 
 
 def algorithmic_fma_per_point(K: int, p: int, q: int) -> float:
@@ -69,11 +69,13 @@ def algorithmic_fma_per_point(K: int, p: int, q: int) -> float:
 
 def covariance_fma_per_point(K: int, covfun: int, d: int) -> float:
     """FP64 work of the covariance and derivative entries as implemented: per off-diagonal
-    pair, the squared distance (2d + 1 ops) twice, plus three degree-12 Horner chains
-    (Matern value, rho- and nu-derivatives) and the table lookup subtraction."""
+    pair, the squared distance (2d + 1 ops) twice; for the Matern table the two table-
+    variable subtractions and the FP64 part of three polynomials (3 FMAs each; the rest of
+    each polynomial runs in FP32); for the exponential the square root, exponential and
+    division (~35 ops)."""
     pairs = K * (K - 1) / 2
     if covfun == 1:
-        return pairs * (2 * (2 * d + 1) + 3 * 13 + 2 + 6)
+        return pairs * (2 * (2 * d + 1) + 2 + 3 * 3)
     return pairs * (2 * d + 1 + 35)
 
 
