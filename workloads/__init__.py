@@ -359,6 +359,57 @@ def cfg_swath_1m2(seed: int = 1003, slices: int = 16, bands: int = 8, per: int =
                    start, NN=NN, seed=seed, m_sim=m_sim)
 
 
+def grouped_order(locs: np.ndarray, g: int, gmax: int | None = None):
+    """An ordering for grouped conditioning: spatially compact groups of about g points
+    (the cells of a square grid over the first two coordinates, cells of more than gmax
+    points split into runs of gmax), the groups in the maxmin order of their centroids,
+    each group's points by index.  Returns (order, group_off): group b is order[group_off[b]
+    : group_off[b + 1]], a contiguous range of the ordering."""
+    locs = np.asarray(locs, dtype=np.float64)
+    n = locs.shape[0]
+    gmax = 2 * g if gmax is None else gmax
+    xy = locs[:, :2] if locs.shape[1] >= 2 else np.column_stack([locs[:, 0], np.zeros(n)])
+    lo, hi = xy.min(axis=0), xy.max(axis=0)
+    ncell = max(1, int(round(np.sqrt(n / g))))
+    cid = np.minimum(((xy - lo) / np.maximum(hi - lo, 1e-300) * ncell).astype(np.int64), ncell - 1)
+    key = cid[:, 0] * ncell + cid[:, 1]
+    by_cell = np.argsort(key, kind="stable")
+    bounds = np.flatnonzero(np.diff(key[by_cell])) + 1
+    groups = []
+    for cell in np.split(by_cell, bounds):
+        for s in range(0, len(cell), gmax):
+            groups.append(np.sort(cell[s:s + gmax]))
+    cent = np.array([xy[gr].mean(axis=0) for gr in groups])
+    gorder = maxmin_order(cent)
+    order = np.concatenate([groups[k] for k in gorder])
+    off = np.zeros(len(groups) + 1, dtype=np.int64)
+    off[1:] = np.cumsum([len(groups[k]) for k in gorder])
+    return order, off
+
+
+def grouped_field(n: int, covfun: int, theta, m: int, g: int, p: int = 1, seed: int = 0,
+                  m_sim: int = 30, beta=None):
+    """A field in [0,1]^2 (d = 3 for the space-time covariance) in a grouped ordering
+    (grouped_order, groups of about g), y from a sequential draw with m_sim neighbours in
+    that ordering, NNarray with m.  Returns (Workload, group_off)."""
+    rng = np.random.default_rng(seed)
+    d = 3 if covfun == EXP_SPACETIME else 2
+    locs = rng.uniform(0.0, 1.0, size=(n, d))
+    order, goff = grouped_order(locs, g)
+    locs = locs[order]
+    X = np.ones((n, p))
+    for c in range(1, p):
+        X[:, c] = locs[:, (c - 1) % d]
+    beta = np.zeros(p) if beta is None else np.asarray(beta, dtype=np.float64)
+    theta = np.asarray(theta, dtype=np.float64)
+    NNs = ordered_nn(locs, max(m, m_sim))
+    e = simulate_sequential(covfun, theta, locs, NNs[:, :m_sim + 1], rng)
+    y = X @ beta + e
+    w = _finish("grouped_n%d_g%d_m%d" % (n, g, m), covfun, locs, y, X, m, theta, theta.copy(),
+                NN=np.ascontiguousarray(NNs[:, :m + 1]), seed=seed, g=g)
+    return w, goff
+
+
 def elevators_ranges(d: int = 18) -> np.ndarray:
     """Ranges of the Elevators-like field: log-spaced from 1 to 8 (standardised attributes),
     so the attributes differ in relevance by a factor of 8 and every range stays
