@@ -24,6 +24,8 @@ Reported beside the device-timed value:
   * prediction -- Vecchia prediction at 100000 new sites of the headline field.
   * elevators_like -- the exponential with one range per attribute on an Elevators-like
                   workload (n = 15000, d = 18): passes, fits, the oracle beside them.
+  * grouped    -- grouped conditioning (one Cholesky per group of ~8 observations) against
+                  the plain pass on the same n = 1e5 ordering.
 ``--impl reference`` times the CPU oracle itself as the reference arm.
 Multi-GPU runs (torchrun) are independent replicas: each rank evaluates its own copy.
 """
@@ -525,6 +527,52 @@ def run_elevators(vg, torch, dev, stream) -> dict:
     return res
 
 
+def run_grouped(vg, torch, dev, stream) -> dict:
+    """Grouped conditioning on an n = 1e5 Matern field (the headline's parameters) in a
+    grouped ordering (spatially compact groups of about 8 points, at most 12, ordered by the
+    maxmin order of their centroids), m = 30: the grouped pass (one Cholesky per group, FP64 and
+    mixed) against the plain pass on the same ordering and NNarray, CUDA events, median of
+    5, inputs resident."""
+    import workloads
+    th = np.array([2.0, 0.05, 1.5, 0.05])
+    w, goff = workloads.grouped_field(100000, 1, th, 30, 8, p=3, seed=1011, m_sim=30,
+                                      beta=[1.0, 0.5, -0.5], gmax=12)
+    off, idx, nm, kmax = vg.vecchia_group_blocks(w.NN, goff)
+    t = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)  # noqa
+    locs, y, X, NN, dth = t(w.locs), t(w.y), t(w.X), t(w.NN, torch.int32), t(th)
+    doff, didx, dnm = t(off, torch.int64), t(idx, torch.int32), t(nm, torch.int32)
+
+    def timed(fn):
+        fn()
+        ms = []
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out, st = fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms), out, st
+
+    res = {"n": w.n, "m": 30, "groups": len(goff) - 1, "mean_group": float(np.mean(nm)),
+           "mean_block": float(np.mean(np.diff(off))), "largest_block": int(kmax)}
+    for prec in ("fp64", "mixed"):
+        hg = vg.Handle(0)
+        ms_g, out_g, st_g = timed(lambda: vg.vecchia_grouped_loglik_grad_info(
+            locs, y, X, doff, didx, dnm, kmax, dth, w.covfun, prec=prec, stream=stream, handle=hg))
+        hg.close()
+        hp = vg.Handle(0)
+        vg.vecchia_autotune(locs, y, X, NN, dth, w.covfun, prec=prec, stream=stream, handle=hp)
+        ms_p, out_p, st_p = timed(lambda: vg.vecchia_loglik_grad_info(
+            locs, y, X, NN, dth, w.covfun, prec=prec, stream=stream, handle=hp))
+        hp.close()
+        res[prec] = {"grouped_ms": ms_g, "grouped_points_per_s": w.n / (ms_g * 1e-3),
+                     "plain_ms": ms_p, "plain_points_per_s": w.n / (ms_p * 1e-3),
+                     "status": [int(st_g[0].item()), int(st_p[0].item())],
+                     "loglik_grouped": float(out_g[0].item()), "loglik_plain": float(out_p[0].item())}
+    return res
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -685,6 +733,7 @@ def run_ours(args):
     nn = run_nn_search(vg, torch, dev, stream)
     pred = run_prediction(vg, torch, dev, stream, w)
     elev = run_elevators(vg, torch, dev, stream)
+    grouped = run_grouped(vg, torch, dev, stream)
 
     if rank != 0:
         if ws > 1:
@@ -762,6 +811,7 @@ def run_ours(args):
         "nn_search": nn,
         "prediction": pred,
         "elevators_like": elev,
+        "grouped": grouped,
     }
     print(json.dumps(line))
     if ws > 1:

@@ -519,6 +519,45 @@ VECCHIA_API vec_status vecchia_predict(vec_handle h, const double* locs, const d
                                        int64_t* dev_status);
 
 /*
+ * Grouped conditioning (Sec. 2.2: conditioning on joint distributions).  Observations are
+ * partitioned into groups that are contiguous ranges of the ordering; group b (members
+ * B = s .. e-1) conditions jointly on U = (the members' NNarray neighbours) minus B, which
+ * lies before s, so the product of the group conditionals p(y_B | y_U) is a valid density.
+ * It equals the Vecchia density in which member i conditions on U and the earlier members
+ * of its group, and it needs one Cholesky per group.
+ *
+ * vecchia_group_blocks -- HOST helper: the block lists from an NNarray (HOST, n x (m+1))
+ * and group boundaries group_off (HOST, ngroups + 1, group_off[0] = 0, ascending,
+ * group_off[ngroups] = n).  Block b is U (ascending) then the members s .. e-1:
+ * block_idx[block_off[b] .. block_off[b+1]), nmemb[b] = e - s; *kmax = the largest block.
+ * Call it first with block_idx = nmemb = NULL to get block_off and kmax (block_off[ngroups]
+ * is the length block_idx needs), then with the arrays.  VEC_ERR_ARG on a bad NNarray row or
+ * bad group boundaries.  No device work.
+ *
+ * vecchia_grouped_loglik_grad_info -- the grouped pass: the same outputs as
+ * vecchia_loglik_grad_info (loglik, gradient, Fisher information, betahat; n = the number
+ * of observations, every one of them a member of exactly one group) from one group per
+ * unit of work: the block's covariance and one Cholesky, then for each member row the
+ * single-observation terms on the leading block that ends at that row.  DEVICE pointers:
+ * locs, y, X as for the plain pass; block_off (ngroups + 1, int64), block_idx (int32),
+ * nmemb (ngroups, int32) as vecchia_group_blocks writes them; kmax = the largest block,
+ * 1 <= kmax <= vecchia_max_m() + 1.  Isotropic and space-time families (VEC_ERR_UNSUPPORTED
+ * otherwise).  A block whose conditioning set is not ascending and before its members, or
+ * whose members are not consecutive, is reported in dev_status as VEC_ERR_ARG with the group
+ * index.  Asynchronous on `stream`.
+ */
+VECCHIA_API vec_status vecchia_group_blocks(const int32_t* NNarray, int64_t n, int m,
+                                            const int64_t* group_off, int64_t ngroups,
+                                            int64_t* block_off, int32_t* block_idx,
+                                            int32_t* nmemb, int* kmax);
+VECCHIA_API vec_status vecchia_grouped_loglik_grad_info(vec_handle h, const double* locs,
+                                    const double* y, const double* X, int64_t n, int d, int p,
+                                    int64_t ngroups, const int64_t* block_off,
+                                    const int32_t* block_idx, const int32_t* nmemb, int kmax,
+                                    const double* covparms, vec_covfun covfun, vec_precision prec,
+                                    void* stream, double* out, int64_t* dev_status);
+
+/*
  * vecchia_measure_peaks -- throughputs of this GPU that bound the pass kernels, measured
  * on the handle's device and stream (synchronous, ~0.5 s): out[0] FP64 FMA-chain GFLOP/s,
  * out[1] FP32 FMA-chain GFLOP/s (8 independent chains per thread, 16 warps per SM),

@@ -92,6 +92,9 @@ def lib():
         L.vecchia_nparms.argtypes = [ci]
         L.vecchia_nparms_d.argtypes = [ci, ci]
         L.vecchia_measure_peaks.argtypes = [P, P]
+        L.vecchia_group_blocks.argtypes = [P, i64, ci, P, i64, P, P, P, P]
+        L.vecchia_grouped_loglik_grad_info.argtypes = [P, P, P, P, i64, ci, ci, i64, P, P, P, ci,
+                                                       P, ci, ci, P, P, P]
         L.vecchia_set_lanes.argtypes = [P, ci]
         L.vecchia_set_block_threads.argtypes = [P, ci]
         L.vecchia_set_matern_table.argtypes = [P, ci]
@@ -152,7 +155,8 @@ def lib():
                   L.vecchia_fields_variogram, L.vecchia_mlp_forward, L.vecchia_mlp_grad,
                   L.vecchia_mlp_adam_step, L.vecchia_mlp_column_moments,
                   L.vecchia_fields_warm_start, L.vecchia_ordered_nn, L.vecchia_nearest,
-                  L.vecchia_predict, L.vecchia_measure_peaks):
+                  L.vecchia_predict, L.vecchia_measure_peaks, L.vecchia_group_blocks,
+                  L.vecchia_grouped_loglik_grad_info):
             f.restype = ci
         _lib = L
     return _lib
@@ -842,6 +846,58 @@ def vecchia_loglik_grad_info_host(locs, y, X, NNarray, covparms, covfun: int, pr
     _check(code, bad.value)
     return {"loglik": ll.value, "grad": grad, "info": info, "betahat": beta,
             "bad_index": bad.value}
+
+
+def vecchia_group_blocks(NNarray, group_off):
+    """Block lists for grouped conditioning from a HOST NNarray (n, m+1) and contiguous group
+    boundaries (see vecchia_group_blocks in include/vecchia.h).  Returns numpy arrays
+    (block_off int64, block_idx int32, nmemb int32) and kmax."""
+    NN = np.ascontiguousarray(NNarray, dtype=np.int32)
+    goff = np.ascontiguousarray(group_off, dtype=np.int64)
+    n, W = NN.shape
+    ng = len(goff) - 1
+    off = np.empty(ng + 1, dtype=np.int64)
+    kmax = ctypes.c_int()
+    P = ctypes.c_void_p
+    _check(lib().vecchia_group_blocks(NN.ctypes.data_as(P), n, W - 1, goff.ctypes.data_as(P), ng,
+                                      off.ctypes.data_as(P), None, None, ctypes.byref(kmax)))
+    idx = np.empty(int(off[-1]), dtype=np.int32)
+    nm = np.empty(ng, dtype=np.int32)
+    _check(lib().vecchia_group_blocks(NN.ctypes.data_as(P), n, W - 1, goff.ctypes.data_as(P), ng,
+                                      off.ctypes.data_as(P), idx.ctypes.data_as(P),
+                                      nm.ctypes.data_as(P), ctypes.byref(kmax)))
+    return off, idx, nm, kmax.value
+
+
+def vecchia_grouped_loglik_grad_info(locs, y, X, block_off, block_idx, nmemb, kmax: int,
+                                     covparms, covfun: int, prec="fp64", stream=None, out=None,
+                                     status=None, handle: Handle | None = None):
+    """Grouped-conditioning pass (see include/vecchia.h).  CUDA tensors: locs (n, d), y (n,),
+    X (n, p) float64, block_off int64, block_idx int32, nmemb int32, covparms float64.
+    Returns (out, status) on the device, as vecchia_loglik_grad_info."""
+    import torch
+    for t, dt, nm_ in ((locs, torch.float64, "locs"), (y, torch.float64, "y"),
+                       (X, torch.float64, "X"), (block_off, torch.int64, "block_off"),
+                       (block_idx, torch.int32, "block_idx"), (nmemb, torch.int32, "nmemb"),
+                       (covparms, torch.float64, "covparms")):
+        _dev_tensor_check(t, dt, nm_)
+    n, d = locs.shape
+    p = X.shape[1]
+    q = nparms(covfun, d)
+    dev = locs.device
+    if handle is None:
+        handle = default_handle(dev.index if dev.index is not None else 0)
+    if out is None:
+        out = torch.empty(1 + q + q * q + p, dtype=torch.float64, device=dev)
+    if status is None:
+        status = torch.empty(2, dtype=torch.int64, device=dev)
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    _check(lib().vecchia_grouped_loglik_grad_info(
+        handle.ptr, _dptr(locs), _dptr(y), _dptr(X), n, d, p, nmemb.shape[0], _dptr(block_off),
+        _dptr(block_idx), _dptr(nmemb), int(kmax), _dptr(covparms), covfun, _PREC[prec],
+        ctypes.c_void_p(stream.cuda_stream), _dptr(out), _dptr(status)))
+    return out, status
 
 
 def vecchia_measure_peaks(handle: Handle | None = None, device: int = 0) -> dict:

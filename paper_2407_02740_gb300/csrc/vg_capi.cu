@@ -1581,6 +1581,105 @@ vec_status vecchia_predict(vec_handle h, const double* locs, const double* y, co
     return VEC_OK;
 }
 
+vec_status vecchia_group_blocks(const int32_t* NNarray, int64_t n, int m, const int64_t* group_off,
+                                int64_t ngroups, int64_t* block_off, int32_t* block_idx,
+                                int32_t* nmemb, int* kmax) {
+    if (!NNarray || !group_off || !block_off || !kmax || (block_idx && !nmemb) ||
+        (!block_idx && nmemb))
+        return fail(VEC_ERR_ARG, "vecchia_group_blocks: NULL argument");
+    if (n < 1 || n > (int64_t)INT_MAX || m < 0 || ngroups < 1 || ngroups > n)
+        return fail(VEC_ERR_ARG, "vecchia_group_blocks: bad sizes (n %lld, m %d, ngroups %lld)",
+                    (long long)n, m, (long long)ngroups);
+    if (group_off[0] != 0 || group_off[ngroups] != n)
+        return fail(VEC_ERR_ARG, "vecchia_group_blocks: groups must cover 0 .. n-1");
+    const int64_t W = (int64_t)m + 1;
+    std::vector<int32_t> u;
+    int64_t off = 0;
+    int kx = 0;
+    block_off[0] = 0;
+    for (int64_t b = 0; b < ngroups; ++b) {
+        const int64_t s = group_off[b], e = group_off[b + 1];
+        if (e <= s) return fail(VEC_ERR_ARG, "vecchia_group_blocks: group %lld is empty", (long long)b);
+        u.clear();
+        for (int64_t i = s; i < e; ++i) {
+            const int32_t* row = NNarray + i * W;
+            if (row[0] != (int32_t)i)
+                return fail(VEC_ERR_ARG, "vecchia_group_blocks: NNarray row %lld does not start with %lld",
+                            (long long)i, (long long)i);
+            for (int c = 1; c <= m; ++c) {
+                const int32_t v = row[c];
+                if (v < 0) break;
+                if ((int64_t)v >= i)
+                    return fail(VEC_ERR_ARG, "vecchia_group_blocks: NNarray row %lld lists %d", (long long)i, v);
+                if ((int64_t)v < s) u.push_back(v);   // neighbours from s on are members
+            }
+        }
+        std::sort(u.begin(), u.end());
+        u.erase(std::unique(u.begin(), u.end()), u.end());
+        const int64_t len = (int64_t)u.size() + (e - s);
+        if (block_idx) {
+            for (size_t k = 0; k < u.size(); ++k) block_idx[off + (int64_t)k] = u[k];
+            for (int64_t i = s; i < e; ++i) block_idx[off + (int64_t)u.size() + (i - s)] = (int32_t)i;
+            nmemb[b] = (int32_t)(e - s);
+        }
+        off += len;
+        block_off[b + 1] = off;
+        if (len > kx) kx = (int)std::min<int64_t>(len, INT_MAX);
+    }
+    *kmax = kx;
+    return VEC_OK;
+}
+
+vec_status vecchia_grouped_loglik_grad_info(vec_handle h, const double* locs, const double* y,
+                                            const double* X, int64_t n, int d, int p, int64_t ngroups,
+                                            const int64_t* block_off, const int32_t* block_idx,
+                                            const int32_t* nmemb, int kmax, const double* covparms,
+                                            vec_covfun covfun, vec_precision prec, void* stream,
+                                            double* out, int64_t* dev_status) {
+    if (!h) return fail(VEC_ERR_ARG, "vecchia_grouped_loglik_grad_info: NULL handle");
+    if (!locs || !y || !X || !block_off || !block_idx || !nmemb || !covparms || !out || !dev_status)
+        return fail(VEC_ERR_ARG, "vecchia_grouped_loglik_grad_info: a required pointer is NULL");
+    if (n < 1 || n > (int64_t)INT_MAX || ngroups < 1 || ngroups > n)
+        return fail(VEC_ERR_ARG, "n = %lld, ngroups = %lld out of range", (long long)n, (long long)ngroups);
+    if (covfun != VEC_EXP_ISO && covfun != VEC_MATERN_ISO && covfun != VEC_EXP_SPACETIME)
+        return fail(VEC_ERR_UNSUPPORTED, "grouped conditioning: isotropic and space-time families only");
+    const int q = vecchia_nparms_d(covfun, d);
+    if (q < 0) return fail(VEC_ERR_ARG, "covariance function %d does not take d = %d", (int)covfun, d);
+    if (p < 1 || p > vg::PMAX) return fail(VEC_ERR_ARG, "p = %d out of range [1, %d]", p, vg::PMAX);
+    if (kmax < 1 || kmax > vg::KMAX)
+        return fail(VEC_ERR_UNSUPPORTED, "largest block %d outside [1, %d]", kmax, vg::KMAX);
+    if (prec != VEC_FP64 && prec != VEC_MIXED) return fail(VEC_ERR_ARG, "unknown precision %d", (int)prec);
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(VEC_ERR_CUDA, "cannot select device %d", h->device);
+    const int cov = (int)covfun;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    vg::PassPlan plan;
+    int pr = vg::plan_pass(cov, kmax - 1, d, p, h->nsm, h->lanes, h->threads, &plan, (int)prec, false,
+                           h->tab_mode, true);
+    if (pr == -1) return fail(VEC_ERR_UNSUPPORTED, "no kernel mapping fits blocks of %d", kmax);
+    if (pr != 0) return cuda_fail(cudaGetLastError(), "planning the grouped pass kernel");
+    cudaError_t e = grow(&h->partials, &h->partials_cap, (size_t)plan.grid * plan.nstat);
+    if (e == cudaSuccess) e = vg::launch_init_status(h->status, h->bad, st);
+    if (e == cudaSuccess && cov == vg::COV_MATERN)
+        e = vg::launch_mtab_build(covparms, h->mtab, prec ? h->mtabf : nullptr, st);
+    if (e != cudaSuccess) return cuda_fail(e, "grouped pass: set-up");
+    vg::PassArgs a;
+    a.locs = locs; a.y = y; a.X = X; a.NN = nullptr; a.covparms = covparms;
+    a.mtab = h->mtab; a.mtabf = h->mtabf; a.partials = h->partials; a.status = h->status;
+    a.bad = h->bad;
+    a.n = n; a.d = d; a.p = p; a.m = kmax - 1;
+    a.nstat = plan.nstat; a.nv = plan.nv; a.slot_stride = plan.slot_stride;
+    a.acc_per_lane = plan.acc_per_lane; a.tab_in_smem = plan.tab_smem;
+    a.blk_off = reinterpret_cast<const long long*>(block_off); a.blk_idx = block_idx;
+    a.nmemb = nmemb; a.ngroups = ngroups;
+    e = vg::launch_pass(cov, plan, a, st);
+    if (e == cudaSuccess)
+        e = vg::launch_profile(h->partials, plan.grid, plan.nstat, p, q, n, covparms, h->status,
+                               h->bad, out, reinterpret_cast<long long*>(dev_status), st);
+    if (e != cudaSuccess) return cuda_fail(e, "launching the grouped pass");
+    return VEC_OK;
+}
+
 vec_status vecchia_measure_peaks(vec_handle h, double* out) {
     if (!h || !out) return fail(VEC_ERR_ARG, "vecchia_measure_peaks: NULL argument");
     DeviceGuard g(h->device);

@@ -137,6 +137,12 @@ struct PassArgs {
     int slot_stride;                   // doubles per slot
     int acc_per_lane;                  // ceil(nstat / L)
     int tab_in_smem;                   // copy the Matern table into shared memory
+    // grouped conditioning (the grouped kernels only): block b is blk_idx[blk_off[b] ..
+    // blk_off[b + 1]), its conditioning set then its nmemb[b] members
+    const long long* blk_off;
+    const int32_t* blk_idx;
+    const int32_t* nmemb;
+    long long ngroups;
 };
 
 // Arguments of the batched pass kernel: many datasets (common d, p, covariance family),

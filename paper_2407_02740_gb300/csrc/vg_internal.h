@@ -21,6 +21,7 @@ struct PassPlan {
     int acc_per_lane;  // accumulator doubles per thread
     int prec;          // 0 = FP64 kernel, 1 = mixed (FP32 block) kernel
     int batched;       // plan made for the batched kernel
+    int grouped;       // plan made for the grouped-conditioning kernel
 };
 
 // Chooses the lanes-per-observation mapping that fits shared memory (or the forced one).
@@ -28,13 +29,15 @@ struct PassPlan {
 // force_tab: -1 = Matern table in shared memory when it fits, 1 = shared memory only,
 // 0 = global memory (read through L1).  Returns 0, -1 (no mapping fits) or -2 (CUDA error).
 int plan_pass(int cov, int m, int d, int p, int nsm, int force_L, int force_threads,
-              PassPlan* plan, int prec = 0, bool batched = false, int force_tab = -1);
+              PassPlan* plan, int prec = 0, bool batched = false, int force_tab = -1,
+              bool grouped = false);
 size_t pass_smem_bytes(int cov, int m, int d, int p, int L, int threads, bool tab_smem,
                        int prec = 0);
 const void* pass_kernel_f64(int cov, int L);
 const void* pass_kernel_f32(int cov, int L);
 const void* pass_batch_kernel_f64(int cov, int L);
 const void* pass_batch_kernel_f32(int cov, int L);
+const void* pass_group_kernel(int cov, int L, int prec);
 cudaError_t launch_pass_batch(int cov, const PassPlan& plan, const BatchArgs& args, cudaStream_t st);
 cudaError_t launch_mtab_build_batch(const double* covparms_b, int nbatch, int q, double* tabs,
                                     float* tabsf, const int* active, cudaStream_t st);

@@ -363,7 +363,8 @@ __global__ void k_cov_pairs(const double* __restrict__ covparms, const double* _
 // ----------------------------------------------------------------------------------------
 static int nv_of(int p, int Q) { return 4 + p + Q * (3 + p) + Q * (Q + 1) / 2; }
 
-static const void* pass_kernel(int cov, int L, int prec, bool batched = false) {
+static const void* pass_kernel(int cov, int L, int prec, bool batched = false, bool grouped = false) {
+    if (grouped) return pass_group_kernel(cov, L, prec);
     if (batched) return prec == 0 ? pass_batch_kernel_f64(cov, L) : pass_batch_kernel_f32(cov, L);
     return prec == 0 ? pass_kernel_f64(cov, L) : pass_kernel_f32(cov, L);
 }
@@ -388,7 +389,7 @@ size_t pass_smem_bytes(int cov, int m, int d, int p, int L, int threads, bool ta
 }
 
 int plan_pass(int cov, int m, int d, int p, int nsm, int force_L, int force_threads,
-              PassPlan* plan, int prec, bool batched, int force_tab) {
+              PassPlan* plan, int prec, bool batched, int force_tab, bool grouped) {
     // Preference: 256 threads (two warps per SM sub-partition, so that one warp's FP64
     // dependency waits are covered by the other), then 128 (one warp per sub-partition,
     // the minimum that occupies all FP64 units), then fewer when the largest blocks do
@@ -401,7 +402,7 @@ int plan_pass(int cov, int m, int d, int p, int nsm, int force_L, int force_thre
         for (int L = 1; L <= 32; L *= 2) {
             if (force_L > 0 && L != force_L) continue;
             if (L > thr) continue;
-            if (cov == COV_ANISO && L < 4) continue;   // no instantiation below 4 lanes
+            if ((cov == COV_ANISO || grouped) && L < 4) continue;   // no instantiation below 4 lanes
             if (thr == 256 && force_L <= 0 && L > 16) continue;
             // Matern table in shared memory when it fits (or as forced: force_tab 1 = shared
             // memory only, 0 = global memory, read through L1)
@@ -430,7 +431,8 @@ int plan_pass(int cov, int m, int d, int p, int nsm, int force_L, int force_thre
     plan->acc_per_lane = (RL.nstat + chosen - 1) / chosen;
     plan->smem = pass_smem_bytes(cov, m, d, p, chosen, threads, tab, prec);
     plan->batched = batched ? 1 : 0;
-    const void* fn = pass_kernel(cov, chosen, prec, batched);
+    plan->grouped = grouped ? 1 : 0;
+    const void* fn = pass_kernel(cov, chosen, prec, batched, grouped);
     if (!fn) return -1;
     // The attribute is raised to the device's opt-in limit rather than to this launch's
     // size, so that plans and captured graphs made earlier for larger blocks stay
@@ -454,7 +456,7 @@ int plan_pass(int cov, int m, int d, int p, int nsm, int force_L, int force_thre
 }
 
 cudaError_t launch_pass(int cov, const PassPlan& plan, const PassArgs& args, cudaStream_t st) {
-    const void* fn = pass_kernel(cov, plan.L, plan.prec);
+    const void* fn = pass_kernel(cov, plan.L, plan.prec, false, plan.grouped != 0);
     if (!fn) return cudaErrorInvalidValue;
     PassArgs a = args;
     void* params[] = {&a};

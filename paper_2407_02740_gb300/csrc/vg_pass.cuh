@@ -178,6 +178,11 @@ struct PassEnv {
     // factor + i (m+1), in NNarray order: entry 0 for the observation, entry c for
     // neighbour NNarray[i][c], 0 for padding)
     double* factor;
+    // grouped conditioning (see PassArgs)
+    const long long* blk_off;
+    const int32_t* blk_idx;
+    const int32_t* nmemb;
+    long long n;
 };
 
 // Record formulas: entry t of the per-observation record is V[u1] V[v1] + V[u2] V[v2],
@@ -279,58 +284,20 @@ __device__ __forceinline__ void accumulate_record(const uint64_t* sidx, const do
     gsync<L>(gmask);
 }
 
-// Algorithm 1 for observation i of the dataset in E (all L lanes of the group call it).
+// Covariance of the block in the slot (coordinates in loc, relative and scaled): the packed
+// lower triangle of A, nugget on the diagonal; for the exponential families also the pair
+// weights D1 that the derivative step reuses.
 template <int COV, int L, typename T, typename Tab>
-__device__ __forceinline__ void vecchia_point(const PassEnv<T, Tab>& E, long long i) {
+__device__ __forceinline__ void assemble_block(const PassEnv<T, Tab>& E, int Kp) {
     using N = Num<T>;
     using MT = MaternT<T>;
-    constexpr int NG = npair_derivs(COV);
-    constexpr int Q = NG + 1;
     const int gl = E.gl;
     const unsigned gmask = E.gmask;
-    const int d = E.d, p = E.p, m = E.m, Kmax = E.Kmax;
-    T* A = E.A; T* Yg = E.Yg; T* invd = E.invd; T* loc = E.loc; T* bacc = E.bacc;
-    T* bv = E.bv; T* G = E.G; T* D1 = E.D1;
-    double* V = E.V;
-    int* idx = E.idx;
-    const T sig2T = E.sig2T, diagC = E.diagC, inv_r1T = E.inv_r1T, inv_r2T = E.inv_r2T;
-    const double inv_r1 = E.inv_r1, inv_r2 = E.inv_r2, m_psi = E.m_psi;
+    const int d = E.d, Kmax = E.Kmax;
+    T* A = E.A; T* loc = E.loc; T* D1 = E.D1;
+    const T sig2T = E.sig2T, diagC = E.diagC;
+    const double m_psi = E.m_psi;
     const Tab* tab = E.tab;
-    const uint64_t* sidx = E.sidx;
-    double* acc = E.acc;
-    const int vb0 = E.vb0, vstep = E.vstep, vmm = E.vmm;
-    // ---------------- gather ----------------
-    const int32_t* row = E.NN + i * (long long)(m + 1);
-    int cnt = 0, badrow = 0;
-    for (int c = gl; c <= m; c += L) {
-        int v = row[c];
-        if (c == 0) badrow |= (v != (int)i);
-        else if (v >= 0) {
-            cnt++;
-            badrow |= (v >= i) | (c >= 2 && row[c - 1] < 0);
-        } else if (v != -1) badrow = 1;
-    }
-    cnt = gsum<L>(cnt, gmask);
-    badrow = gsum<L>(badrow, gmask);
-    if (badrow) {
-        if (gl == 0) report(E.status, E.bad, ST_ARG, i);
-        return;
-    }
-    const int Kp = cnt + 1;
-    const double* li = E.locs + i * (long long)d;
-    for (int a = gl; a < Kp; a += L) {
-        int j = row[Kp - 1 - a];
-        idx[a] = j;
-        // coordinates relative to the observation, divided by their range parameter
-        // (FP64 difference, then rounded to T): squared distances come out scaled
-        for (int k = 0; k < d; ++k)
-            loc[k * Kmax + a] = (T)((E.locs[(long long)j * d + k] - li[k]) *
-                                    ((COV == COV_ST && k == 2) ? inv_r2 : inv_r1));
-        Yg[a] = (T)E.y[j];
-        for (int t = 0; t < p; ++t) Yg[(1 + t) * Kmax + a] = (T)E.X[(long long)j * p + t];
-    }
-    gsync<L>(gmask);
-
     // ---------------- covariance assembly (packed lower triangle) ----------------
     const int ntri = Kp * (Kp + 1) / 2;
     for (int e = gl; e < ntri; e += L) {
@@ -372,13 +339,31 @@ __device__ __forceinline__ void vecchia_point(const PassEnv<T, Tab>& E, long lon
     }
     gsync<L>(gmask);
 
-    // ---------------- Cholesky + forward solves of y and X ----------------
-    // combined rows: r < Kp -> matrix row r (packed), r >= Kp -> augmented row r - Kp
-    if (!chol_augmented<L, T>(A, Yg, invd, Kp, Kp + 1 + p, Kmax, gl, gmask)) {
-        if (gl == 0) report(E.status, E.bad, ST_NOT_PD, i);
-        gsync<L>(gmask);
-        return;
-    }
+}
+
+// One conditional on the leading Kp x Kp block of the factor in the slot (its last row,
+// Kp - 1, is the observation; the rows above are what it conditions on): b = last row of
+// L^-1, then g_j = dSigma_j b^T, m_j = L^-1 g_j, the per-observation values and their
+// accumulation into the lane's sums.  i is the observation (error reports, factor rows).
+template <int COV, int L, typename T, typename Tab>
+__device__ __forceinline__ void conditional_terms(const PassEnv<T, Tab>& E, int Kp, long long i) {
+    using N = Num<T>;
+    using MT = MaternT<T>;
+    constexpr int NG = npair_derivs(COV);
+    constexpr int Q = NG + 1;
+    const int gl = E.gl;
+    const unsigned gmask = E.gmask;
+    const int d = E.d, p = E.p, m = E.m, Kmax = E.Kmax;
+    T* A = E.A; T* Yg = E.Yg; T* invd = E.invd; T* loc = E.loc; T* bacc = E.bacc;
+    T* bv = E.bv; T* G = E.G; T* D1 = E.D1;
+    double* V = E.V;
+    int* idx = E.idx;
+    const T sig2T = E.sig2T, diagC = E.diagC, inv_r1T = E.inv_r1T, inv_r2T = E.inv_r2T;
+    const double inv_r1 = E.inv_r1, inv_r2 = E.inv_r2, m_psi = E.m_psi;
+    const Tab* tab = E.tab;
+    const uint64_t* sidx = E.sidx;
+    double* acc = E.acc;
+    const int vb0 = E.vb0, vstep = E.vstep, vmm = E.vmm;
     const int last = Kp - 1;
 
     // ---------------- b = last row of L^-1 (L^T b^T = e_last) ----------------
@@ -520,6 +505,116 @@ __device__ __forceinline__ void vecchia_point(const PassEnv<T, Tab>& E, long lon
 
     // ---------------- accumulate the record (FP64) ----------------
     accumulate_record<L>(sidx, V, acc, E.nstat, gl, gmask);
+}
+
+// Algorithm 1 for observation i of the dataset in E (all L lanes of the group call it).
+template <int COV, int L, typename T, typename Tab>
+__device__ __forceinline__ void vecchia_point(const PassEnv<T, Tab>& E, long long i) {
+    const int gl = E.gl;
+    const unsigned gmask = E.gmask;
+    const int d = E.d, p = E.p, m = E.m, Kmax = E.Kmax;
+    T* A = E.A; T* Yg = E.Yg; T* invd = E.invd; T* loc = E.loc;
+    int* idx = E.idx;
+    const double inv_r1 = E.inv_r1, inv_r2 = E.inv_r2;
+    // ---------------- gather ----------------
+    const int32_t* row = E.NN + i * (long long)(m + 1);
+    int cnt = 0, badrow = 0;
+    for (int c = gl; c <= m; c += L) {
+        int v = row[c];
+        if (c == 0) badrow |= (v != (int)i);
+        else if (v >= 0) {
+            cnt++;
+            badrow |= (v >= i) | (c >= 2 && row[c - 1] < 0);
+        } else if (v != -1) badrow = 1;
+    }
+    cnt = gsum<L>(cnt, gmask);
+    badrow = gsum<L>(badrow, gmask);
+    if (badrow) {
+        if (gl == 0) report(E.status, E.bad, ST_ARG, i);
+        return;
+    }
+    const int Kp = cnt + 1;
+    const double* li = E.locs + i * (long long)d;
+    for (int a = gl; a < Kp; a += L) {
+        int j = row[Kp - 1 - a];
+        idx[a] = j;
+        // coordinates relative to the observation, divided by their range parameter
+        // (FP64 difference, then rounded to T): squared distances come out scaled
+        for (int k = 0; k < d; ++k)
+            loc[k * Kmax + a] = (T)((E.locs[(long long)j * d + k] - li[k]) *
+                                    ((COV == COV_ST && k == 2) ? inv_r2 : inv_r1));
+        Yg[a] = (T)E.y[j];
+        for (int t = 0; t < p; ++t) Yg[(1 + t) * Kmax + a] = (T)E.X[(long long)j * p + t];
+    }
+    gsync<L>(gmask);
+
+    assemble_block<COV, L, T, Tab>(E, Kp);
+
+    // ---------------- Cholesky + forward solves of y and X ----------------
+    // combined rows: r < Kp -> matrix row r (packed), r >= Kp -> augmented row r - Kp
+    if (!chol_augmented<L, T>(A, Yg, invd, Kp, Kp + 1 + p, Kmax, gl, gmask)) {
+        if (gl == 0) report(E.status, E.bad, ST_NOT_PD, i);
+        gsync<L>(gmask);
+        return;
+    }
+
+    conditional_terms<COV, L, T, Tab>(E, Kp, i);
+}
+
+// Grouped conditioning: block g holds a conditioning set U (ascending observation indices)
+// followed by its members, consecutive observations s .. e - 1 that all come after U.  The
+// group's contribution is that of the joint conditional p(y_B | y_U), which factors into
+// one conditional per member on U and the earlier members: after one Cholesky of the whole
+// block, member row r is the last row of the leading (r + 1) x (r + 1) block, so each
+// member's terms are the single-observation terms on that leading block.
+template <int COV, int L, typename T, typename Tab>
+__device__ __forceinline__ void vecchia_group(const PassEnv<T, Tab>& E, long long g) {
+    const int gl = E.gl;
+    const unsigned gmask = E.gmask;
+    const int d = E.d, p = E.p, Kmax = E.Kmax;
+    T* A = E.A; T* Yg = E.Yg; T* invd = E.invd; T* loc = E.loc;
+    const long long o0 = E.blk_off[g], len = E.blk_off[g + 1] - o0;
+    const int32_t* blk = E.blk_idx + o0;
+    const int nm = E.nmemb[g];
+    // a valid block: 1 <= members <= length <= Kmax, indices in [0, n), the conditioning
+    // set ascending and before the first member, the members consecutive
+    int bad = !(len >= 1 && len <= Kmax && nm >= 1 && nm <= len);
+    if (!bad) {
+        const int nu = (int)len - nm;
+        for (int a = gl; a < (int)len; a += L) {
+            const int v = blk[a];
+            bad |= (v < 0) | ((long long)v >= E.n);
+            if (a >= 1) {
+                const int u = blk[a - 1];
+                bad |= (a > nu) ? (v != u + 1) : (u >= v);
+            }
+        }
+    }
+    bad = gsum<L>(bad, gmask);
+    if (bad) {
+        if (gl == 0) report(E.status, E.bad, ST_ARG, g);
+        return;
+    }
+    const int Kp = (int)len;
+    // coordinates relative to the last member, divided by their range parameter
+    const double* ref = E.locs + (long long)blk[Kp - 1] * d;
+    for (int a = gl; a < Kp; a += L) {
+        const int j = blk[a];
+        E.idx[a] = j;
+        for (int k = 0; k < d; ++k)
+            loc[k * Kmax + a] = (T)((E.locs[(long long)j * d + k] - ref[k]) *
+                                    ((COV == COV_ST && k == 2) ? E.inv_r2 : E.inv_r1));
+        Yg[a] = (T)E.y[j];
+        for (int t = 0; t < p; ++t) Yg[(1 + t) * Kmax + a] = (T)E.X[(long long)j * p + t];
+    }
+    gsync<L>(gmask);
+    assemble_block<COV, L, T, Tab>(E, Kp);
+    if (!chol_augmented<L, T>(A, Yg, invd, Kp, Kp + 1 + p, Kmax, gl, gmask)) {
+        if (gl == 0) report(E.status, E.bad, ST_NOT_PD, blk[Kp - nm]);
+        gsync<L>(gmask);
+        return;
+    }
+    for (int r = Kp - nm; r < Kp; ++r) conditional_terms<COV, L, T, Tab>(E, r + 1, blk[r]);
 }
 
 // Algorithm 1 for the exponential with one range per coordinate (COV_ANISO): Q = d + 1
@@ -728,7 +823,9 @@ __device__ __forceinline__ void vecchia_point_aniso(const PassEnv<T, Tab>& E, lo
 // FP64 pipe and keep the default.
 constexpr int pass_min_blocks(int tsize) { return tsize == 4 ? 3 : 1; }
 
-template <int COV, int L, typename T>
+// GROUPED: the units are the blocks of grouped conditioning (PassArgs.blk_*), not single
+// observations; m + 1 is then the largest block.
+template <int COV, int L, typename T, bool GROUPED = false>
 __global__ void __launch_bounds__(256, pass_min_blocks(sizeof(T))) k_pass(PassArgs args) {
     extern __shared__ __align__(16) double smem[];
     using MT = MaternT<T>;
@@ -821,9 +918,15 @@ __global__ void __launch_bounds__(256, pass_min_blocks(sizeof(T))) k_pass(PassAr
     E.inv_rk = inv_rk; E.inv_rkT = inv_rkT;
     E.tab = tab; E.sidx = sidx; E.acc = acc; E.nstat = args.nstat;
     E.vb0 = vb0; E.vstep = vstep; E.vmm = vmm; E.factor = nullptr;
-    for (long long i = (long long)blockIdx.x * ngrp + grp; ok && i < n; i += gstride) {
-        if constexpr (COV == COV_ANISO) vecchia_point_aniso<L, T, Tab>(E, i);
-        else vecchia_point<COV, L, T, Tab>(E, i);
+    E.blk_off = args.blk_off; E.blk_idx = args.blk_idx; E.nmemb = args.nmemb; E.n = n;
+    if constexpr (GROUPED) {
+        for (long long g = (long long)blockIdx.x * ngrp + grp; ok && g < args.ngroups; g += gstride)
+            vecchia_group<COV, L, T, Tab>(E, g);
+    } else {
+        for (long long i = (long long)blockIdx.x * ngrp + grp; ok && i < n; i += gstride) {
+            if constexpr (COV == COV_ANISO) vecchia_point_aniso<L, T, Tab>(E, i);
+            else vecchia_point<COV, L, T, Tab>(E, i);
+        }
     }
 
     // ---------------- block reduction (fixed order) ----------------

@@ -1,0 +1,40 @@
+"""The library's host builder of grouped-conditioning blocks (vecchia_group_blocks, no GPU
+needed) against the oracle's, bit for bit, and its argument errors."""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import grouped as og
+
+vg = pytest.importorskip("paper_2407_02740_gb300")
+
+
+@pytest.mark.parametrize("n,m,g,seed", [(3000, 30, 8, 1), (500, 10, 3, 2), (200, 5, 40, 3)])
+def test_blocks_match_oracle(n, m, g, seed):
+    w, goff = workloads.grouped_field(n, 1, [1.0, 0.1, 1.0, 0.05], m, g, seed=seed, m_sim=10)
+    off, idx, nm, kmax = vg.vecchia_group_blocks(w.NN, goff)
+    o_off, o_idx, o_nm = og.group_blocks(w.NN, goff)
+    assert np.array_equal(off, o_off) and np.array_equal(idx, o_idx) and np.array_equal(nm, o_nm)
+    assert kmax == int(np.diff(off).max())
+
+
+def test_singletons_and_one_group():
+    w, _ = workloads.grouped_field(300, 1, [1.0, 0.1, 1.0, 0.05], 8, 4, seed=4, m_sim=8)
+    off, idx, nm, kmax = vg.vecchia_group_blocks(w.NN, np.arange(w.n + 1))
+    assert np.all(nm == 1) and kmax == 9
+    for i in (0, 5, 299):      # block i = i's neighbours ascending, then i
+        nb = sorted(int(j) for j in w.NN[i, 1:] if j >= 0)
+        assert list(idx[off[i]:off[i + 1]]) == nb + [i]
+    off, idx, nm, kmax = vg.vecchia_group_blocks(w.NN, [0, w.n])
+    assert list(idx) == list(range(w.n)) and nm[0] == w.n and kmax == w.n
+
+
+def test_bad_arguments():
+    w, goff = workloads.grouped_field(200, 1, [1.0, 0.1, 1.0, 0.05], 8, 4, seed=5, m_sim=8)
+    for bad in ([0, 50, 50, 200], [0, 100], [1, 200], [0, 120, 100, 200]):
+        with pytest.raises(vg.VecchiaError):
+            vg.vecchia_group_blocks(w.NN, bad)
+    NN = w.NN.copy()
+    NN[40, 2] = 41                          # a neighbour that does not precede its row
+    with pytest.raises(vg.VecchiaError):
+        vg.vecchia_group_blocks(NN, goff)

@@ -361,18 +361,20 @@ def cfg_swath_1m2(seed: int = 1003, slices: int = 16, bands: int = 8, per: int =
 
 def grouped_order(locs: np.ndarray, g: int, gmax: int | None = None):
     """An ordering for grouped conditioning: spatially compact groups of about g points
-    (the cells of a square grid over the first two coordinates, cells of more than gmax
-    points split into runs of gmax), the groups in the maxmin order of their centroids,
-    each group's points by index.  Returns (order, group_off): group b is order[group_off[b]
-    : group_off[b + 1]], a contiguous range of the ordering."""
+    (the cells of a cubic grid over the coordinates, cells of more than gmax points split
+    into runs of gmax), the groups in the maxmin order of their centroids, each group's
+    points by index.  Returns (order, group_off): group b is order[group_off[b] :
+    group_off[b + 1]], a contiguous range of the ordering."""
     locs = np.asarray(locs, dtype=np.float64)
-    n = locs.shape[0]
+    n, d = locs.shape
     gmax = 2 * g if gmax is None else gmax
-    xy = locs[:, :2] if locs.shape[1] >= 2 else np.column_stack([locs[:, 0], np.zeros(n)])
+    xy = locs
     lo, hi = xy.min(axis=0), xy.max(axis=0)
-    ncell = max(1, int(round(np.sqrt(n / g))))
+    ncell = max(1, int(round((n / g) ** (1.0 / d))))
     cid = np.minimum(((xy - lo) / np.maximum(hi - lo, 1e-300) * ncell).astype(np.int64), ncell - 1)
-    key = cid[:, 0] * ncell + cid[:, 1]
+    key = np.zeros(n, dtype=np.int64)
+    for k in range(d):
+        key = key * ncell + cid[:, k]
     by_cell = np.argsort(key, kind="stable")
     bounds = np.flatnonzero(np.diff(key[by_cell])) + 1
     groups = []
@@ -388,14 +390,14 @@ def grouped_order(locs: np.ndarray, g: int, gmax: int | None = None):
 
 
 def grouped_field(n: int, covfun: int, theta, m: int, g: int, p: int = 1, seed: int = 0,
-                  m_sim: int = 30, beta=None):
+                  m_sim: int = 30, beta=None, gmax: int | None = None):
     """A field in [0,1]^2 (d = 3 for the space-time covariance) in a grouped ordering
-    (grouped_order, groups of about g), y from a sequential draw with m_sim neighbours in
-    that ordering, NNarray with m.  Returns (Workload, group_off)."""
+    (grouped_order, groups of about g, at most gmax), y from a sequential draw with m_sim
+    neighbours in that ordering, NNarray with m.  Returns (Workload, group_off)."""
     rng = np.random.default_rng(seed)
     d = 3 if covfun == EXP_SPACETIME else 2
     locs = rng.uniform(0.0, 1.0, size=(n, d))
-    order, goff = grouped_order(locs, g)
+    order, goff = grouped_order(locs, g, gmax)
     locs = locs[order]
     X = np.ones((n, p))
     for c in range(1, p):
