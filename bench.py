@@ -531,8 +531,8 @@ def run_grouped(vg, torch, dev, stream) -> dict:
     """Grouped conditioning on an n = 1e5 Matern field (the headline's parameters) in a
     grouped ordering (spatially compact groups of about 8 points, at most 12, ordered by the
     maxmin order of their centroids), m = 30: the grouped pass (one Cholesky per group, FP64 and
-    mixed) against the plain pass on the same ordering and NNarray, CUDA events, median of
-    5, inputs resident."""
+    mixed; the fastest of six lane/thread mappings) against the plain pass (autotuned) on the
+    same ordering and NNarray, CUDA events, median of 5, inputs resident."""
     import workloads
     th = np.array([2.0, 0.05, 1.5, 0.05])
     w, goff = workloads.grouped_field(100000, 1, th, 30, 8, p=3, seed=1011, m_sim=30,
@@ -557,16 +557,30 @@ def run_grouped(vg, torch, dev, stream) -> dict:
     res = {"n": w.n, "m": 30, "groups": len(goff) - 1, "mean_group": float(np.mean(nm)),
            "mean_block": float(np.mean(np.diff(off))), "largest_block": int(kmax)}
     for prec in ("fp64", "mixed"):
-        hg = vg.Handle(0)
-        ms_g, out_g, st_g = timed(lambda: vg.vecchia_grouped_loglik_grad_info(
-            locs, y, X, doff, didx, dnm, kmax, dth, w.covfun, prec=prec, stream=stream, handle=hg))
-        hg.close()
+        # the grouped pass in each mapping (lanes per group x threads); the fastest is kept
+        best = None
+        for lanes, threads in ((8, 64), (8, 128), (16, 128), (16, 256), (32, 128), (32, 256)):
+            hg = vg.Handle(0)
+            hg.set_lanes(lanes)
+            hg.set_block_threads(threads)
+            try:
+                ms_g, out_g, st_g = timed(lambda: vg.vecchia_grouped_loglik_grad_info(
+                    locs, y, X, doff, didx, dnm, kmax, dth, w.covfun, prec=prec, stream=stream,
+                    handle=hg))
+            except vg.VecchiaError:
+                hg.close()
+                continue
+            hg.close()
+            if best is None or ms_g < best[0]:
+                best = (ms_g, out_g, st_g, lanes, threads)
+        ms_g, out_g, st_g, lanes_g, threads_g = best
         hp = vg.Handle(0)
         vg.vecchia_autotune(locs, y, X, NN, dth, w.covfun, prec=prec, stream=stream, handle=hp)
         ms_p, out_p, st_p = timed(lambda: vg.vecchia_loglik_grad_info(
             locs, y, X, NN, dth, w.covfun, prec=prec, stream=stream, handle=hp))
         hp.close()
         res[prec] = {"grouped_ms": ms_g, "grouped_points_per_s": w.n / (ms_g * 1e-3),
+                     "grouped_mapping": {"lanes": lanes_g, "threads": threads_g},
                      "plain_ms": ms_p, "plain_points_per_s": w.n / (ms_p * 1e-3),
                      "status": [int(st_g[0].item()), int(st_p[0].item())],
                      "loglik_grouped": float(out_g[0].item()), "loglik_plain": float(out_p[0].item())}
