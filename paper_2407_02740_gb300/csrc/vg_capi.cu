@@ -1606,10 +1606,17 @@ vec_status vecchia_group_blocks(const int32_t* NNarray, int64_t n, int m, const 
             if (row[0] != (int32_t)i)
                 return fail(VEC_ERR_ARG, "vecchia_group_blocks: NNarray row %lld does not start with %lld",
                             (long long)i, (long long)i);
+            bool pad = false;   // a valid row: neighbours, then only -1 padding
             for (int c = 1; c <= m; ++c) {
                 const int32_t v = row[c];
-                if (v < 0) break;
-                if ((int64_t)v >= i)
+                if (v < 0) {
+                    if (v != -1)
+                        return fail(VEC_ERR_ARG, "vecchia_group_blocks: NNarray row %lld lists %d",
+                                    (long long)i, v);
+                    pad = true;
+                    continue;
+                }
+                if (pad || (int64_t)v >= i)
                     return fail(VEC_ERR_ARG, "vecchia_group_blocks: NNarray row %lld lists %d", (long long)i, v);
                 if ((int64_t)v < s) u.push_back(v);   // neighbours from s on are members
             }

@@ -31,8 +31,8 @@
 // FP64 on this GPU issues one warp instruction per 64 cycles per SM sub-partition whatever
 // the number of active lanes, so the mapping keeps all 32 lanes busy: rows, pairs and
 // vector entries are spread round-robin over the L lanes of a group, and each FP64 pivot
-// costs an FP32 seed plus two short FP64 Newton steps instead of a square root and a
-// division.
+// costs an FP32 seed and one third-order FP64 correction (rsqrt_newton) instead of a
+// square root and a division.
 #pragma once
 #include "vg_common.cuh"
 #include "vg_matern.cuh"

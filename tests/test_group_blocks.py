@@ -38,3 +38,8 @@ def test_bad_arguments():
     NN[40, 2] = 41                          # a neighbour that does not precede its row
     with pytest.raises(vg.VecchiaError):
         vg.vecchia_group_blocks(NN, goff)
+    NN = w.NN.copy()
+    NN[3, 4:] = -1                          # row 3 has 3 neighbours: pad, then a neighbour
+    NN[3, 5] = 0
+    with pytest.raises(vg.VecchiaError):
+        vg.vecchia_group_blocks(NN, goff)
