@@ -531,16 +531,23 @@ def run_grouped(vg, torch, dev, stream) -> dict:
     """Grouped conditioning on an n = 1e5 Matern field (the headline's parameters) in a
     grouped ordering (spatially compact groups of about 8 points, at most 12, ordered by the
     maxmin order of their centroids), m = 30: the grouped pass (one Cholesky per group, FP64 and
-    mixed; the fastest of six lane/thread mappings) against the plain pass (autotuned) on the
+    mixed; three launch classes by block size; the fastest of six lane/thread mappings)
+    against the plain pass (autotuned) with m = 30 and with m = 45 (about the grouped
+    conditioning size) on the
     same ordering and NNarray, CUDA events, median of 5, inputs resident."""
     import workloads
     th = np.array([2.0, 0.05, 1.5, 0.05])
     w, goff = workloads.grouped_field(100000, 1, th, 30, 8, p=3, seed=1011, m_sim=30,
                                       beta=[1.0, 0.5, -0.5], gmax=12)
     off, idx, nm, kmax = vg.vecchia_group_blocks(w.NN, goff)
+    gorder, coff, ckmax = vg.vecchia_group_classes(off, 3)
     t = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)  # noqa
     locs, y, X, NN, dth = t(w.locs), t(w.y), t(w.X), t(w.NN, torch.int32), t(th)
     doff, didx, dnm = t(off, torch.int64), t(idx, torch.int32), t(nm, torch.int32)
+    classes = (t(gorder, torch.int32), coff, ckmax)
+    # the plain pass at a conditioning size like the grouped one's (each member conditions
+    # on about 45 earlier observations: its group's U and the earlier members)
+    NN45 = t(workloads.ordered_nn(w.locs, 45), torch.int32)
 
     def timed(fn):
         fn()
@@ -555,7 +562,8 @@ def run_grouped(vg, torch, dev, stream) -> dict:
         return statistics.median(ms), out, st
 
     res = {"n": w.n, "m": 30, "groups": len(goff) - 1, "mean_group": float(np.mean(nm)),
-           "mean_block": float(np.mean(np.diff(off))), "largest_block": int(kmax)}
+           "mean_block": float(np.mean(np.diff(off))), "largest_block": int(kmax),
+           "launch_classes": {"groups": np.diff(coff).tolist(), "largest_block": ckmax.tolist()}}
     for prec in ("fp64", "mixed"):
         # the grouped pass in each mapping (lanes per group x threads); the fastest is kept
         best = None
@@ -566,7 +574,7 @@ def run_grouped(vg, torch, dev, stream) -> dict:
             try:
                 ms_g, out_g, st_g = timed(lambda: vg.vecchia_grouped_loglik_grad_info(
                     locs, y, X, doff, didx, dnm, kmax, dth, w.covfun, prec=prec, stream=stream,
-                    handle=hg))
+                    handle=hg, classes=classes))
             except vg.VecchiaError:
                 hg.close()
                 continue
@@ -579,7 +587,13 @@ def run_grouped(vg, torch, dev, stream) -> dict:
         ms_p, out_p, st_p = timed(lambda: vg.vecchia_loglik_grad_info(
             locs, y, X, NN, dth, w.covfun, prec=prec, stream=stream, handle=hp))
         hp.close()
+        h45 = vg.Handle(0)
+        vg.vecchia_autotune(locs, y, X, NN45, dth, w.covfun, prec=prec, stream=stream, handle=h45)
+        ms_45, out_45, _ = timed(lambda: vg.vecchia_loglik_grad_info(
+            locs, y, X, NN45, dth, w.covfun, prec=prec, stream=stream, handle=h45))
+        h45.close()
         res[prec] = {"grouped_ms": ms_g, "grouped_points_per_s": w.n / (ms_g * 1e-3),
+                     "plain_m45_ms": ms_45, "loglik_plain_m45": float(out_45[0].item()),
                      "grouped_mapping": {"lanes": lanes_g, "threads": threads_g},
                      "plain_ms": ms_p, "plain_points_per_s": w.n / (ms_p * 1e-3),
                      "status": [int(st_g[0].item()), int(st_p[0].item())],

@@ -534,28 +534,45 @@ VECCHIA_API vec_status vecchia_predict(vec_handle h, const double* locs, const d
  * is the length block_idx needs), then with the arrays.  VEC_ERR_ARG on a bad NNarray row or
  * bad group boundaries.  No device work.
  *
+ * vecchia_group_classes -- HOST helper: launch classes by block size.  Every slot of a
+ * launch is sized for the launch's largest block, so blocks of very different sizes are
+ * best run in separate launches.  From block_off (HOST, ngroups + 1) it picks at most nclass
+ * (1..16) classes of block sizes minimising sum over classes of (groups x largest size^2)
+ * (the slot size, hence the inverse occupancy) and writes gorder (HOST, ngroups: the group
+ * indices, class by class, ascending within a class), class_off (HOST, nclass + 1: class c
+ * is gorder[class_off[c] .. class_off[c+1])) and class_kmax (HOST, nclass: the class's
+ * largest block; unused trailing classes are empty with kmax 0).
+ *
  * vecchia_grouped_loglik_grad_info -- the grouped pass: the same outputs as
  * vecchia_loglik_grad_info (loglik, gradient, Fisher information, betahat; n = the number
  * of observations, every one of them a member of exactly one group) from one group per
  * unit of work: the block's covariance and one Cholesky, then for each member row the
  * single-observation terms on the leading block that ends at that row.  DEVICE pointers:
  * locs, y, X as for the plain pass; block_off (ngroups + 1, int64), block_idx (int32),
- * nmemb (ngroups, int32) as vecchia_group_blocks writes them; kmax = the largest block,
- * 1 <= kmax <= vecchia_max_m() + 1.  Isotropic and space-time families (VEC_ERR_UNSUPPORTED
- * otherwise).  A block whose conditioning set is not ascending and before its members, or
- * whose members are not consecutive, is reported in dev_status as VEC_ERR_ARG with the group
- * index.  Asynchronous on `stream`.
+ * nmemb (ngroups, int32) as vecchia_group_blocks writes them; gorder (ngroups, int32) as
+ * vecchia_group_classes writes it, or NULL with nclass = 1 (groups in their own order).
+ * HOST: class_off (nclass + 1), class_kmax (nclass), each class_kmax[c] in
+ * [1, vecchia_max_m() + 1] for a non-empty class.  One kernel launch per non-empty class,
+ * all on `stream`, then one profile step.  Isotropic and space-time families
+ * (VEC_ERR_UNSUPPORTED otherwise).  A block whose conditioning set is not ascending and
+ * before its members, whose members are not consecutive, or longer than its class's
+ * class_kmax, is reported in dev_status as VEC_ERR_ARG with the group index.  Asynchronous.
  */
 VECCHIA_API vec_status vecchia_group_blocks(const int32_t* NNarray, int64_t n, int m,
                                             const int64_t* group_off, int64_t ngroups,
                                             int64_t* block_off, int32_t* block_idx,
                                             int32_t* nmemb, int* kmax);
+VECCHIA_API vec_status vecchia_group_classes(const int64_t* block_off, int64_t ngroups,
+                                             int nclass, int32_t* gorder, int64_t* class_off,
+                                             int* class_kmax);
 VECCHIA_API vec_status vecchia_grouped_loglik_grad_info(vec_handle h, const double* locs,
                                     const double* y, const double* X, int64_t n, int d, int p,
                                     int64_t ngroups, const int64_t* block_off,
-                                    const int32_t* block_idx, const int32_t* nmemb, int kmax,
-                                    const double* covparms, vec_covfun covfun, vec_precision prec,
-                                    void* stream, double* out, int64_t* dev_status);
+                                    const int32_t* block_idx, const int32_t* nmemb,
+                                    const int32_t* gorder, int nclass, const int64_t* class_off,
+                                    const int* class_kmax, const double* covparms,
+                                    vec_covfun covfun, vec_precision prec, void* stream,
+                                    double* out, int64_t* dev_status);
 
 /*
  * vecchia_measure_peaks -- throughputs of this GPU that bound the pass kernels, measured

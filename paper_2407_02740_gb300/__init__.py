@@ -93,8 +93,9 @@ def lib():
         L.vecchia_nparms_d.argtypes = [ci, ci]
         L.vecchia_measure_peaks.argtypes = [P, P]
         L.vecchia_group_blocks.argtypes = [P, i64, ci, P, i64, P, P, P, P]
-        L.vecchia_grouped_loglik_grad_info.argtypes = [P, P, P, P, i64, ci, ci, i64, P, P, P, ci,
-                                                       P, ci, ci, P, P, P]
+        L.vecchia_group_classes.argtypes = [P, i64, ci, P, P, P]
+        L.vecchia_grouped_loglik_grad_info.argtypes = [P, P, P, P, i64, ci, ci, i64, P, P, P, P,
+                                                       ci, P, P, P, ci, ci, P, P, P]
         L.vecchia_set_lanes.argtypes = [P, ci]
         L.vecchia_set_block_threads.argtypes = [P, ci]
         L.vecchia_set_matern_table.argtypes = [P, ci]
@@ -156,7 +157,7 @@ def lib():
                   L.vecchia_mlp_adam_step, L.vecchia_mlp_column_moments,
                   L.vecchia_fields_warm_start, L.vecchia_ordered_nn, L.vecchia_nearest,
                   L.vecchia_predict, L.vecchia_measure_peaks, L.vecchia_group_blocks,
-                  L.vecchia_grouped_loglik_grad_info):
+                  L.vecchia_group_classes, L.vecchia_grouped_loglik_grad_info):
             f.restype = ci
         _lib = L
     return _lib
@@ -869,12 +870,28 @@ def vecchia_group_blocks(NNarray, group_off):
     return off, idx, nm, kmax.value
 
 
-def vecchia_grouped_loglik_grad_info(locs, y, X, block_off, block_idx, nmemb, kmax: int,
-                                     covparms, covfun: int, prec="fp64", stream=None, out=None,
-                                     status=None, handle: Handle | None = None):
+def vecchia_group_classes(block_off, nclass: int = 3):
+    """Launch classes of the groups by block size (see vecchia_group_classes in
+    include/vecchia.h).  Returns numpy (gorder int32, class_off int64, class_kmax int32)."""
+    off = np.ascontiguousarray(block_off, dtype=np.int64)
+    ng = len(off) - 1
+    gorder = np.empty(ng, dtype=np.int32)
+    class_off = np.empty(nclass + 1, dtype=np.int64)
+    class_kmax = np.empty(nclass, dtype=np.int32)
+    P = ctypes.c_void_p
+    _check(lib().vecchia_group_classes(off.ctypes.data_as(P), ng, nclass, gorder.ctypes.data_as(P),
+                                       class_off.ctypes.data_as(P), class_kmax.ctypes.data_as(P)))
+    return gorder, class_off, class_kmax
+
+
+def vecchia_grouped_loglik_grad_info(locs, y, X, block_off, block_idx, nmemb, kmax, covparms,
+                                     covfun: int, prec="fp64", stream=None, out=None,
+                                     status=None, handle: Handle | None = None, classes=None):
     """Grouped-conditioning pass (see include/vecchia.h).  CUDA tensors: locs (n, d), y (n,),
-    X (n, p) float64, block_off int64, block_idx int32, nmemb int32, covparms float64.
-    Returns (out, status) on the device, as vecchia_loglik_grad_info."""
+    X (n, p) float64, block_off int64, block_idx int32, nmemb int32, covparms float64.  kmax
+    is the largest block (one launch), unless classes = (gorder CUDA int32, class_off,
+    class_kmax) from vecchia_group_classes (one launch per class).  Returns (out, status) on
+    the device, as vecchia_loglik_grad_info."""
     import torch
     for t, dt, nm_ in ((locs, torch.float64, "locs"), (y, torch.float64, "y"),
                        (X, torch.float64, "X"), (block_off, torch.int64, "block_off"),
@@ -884,6 +901,17 @@ def vecchia_grouped_loglik_grad_info(locs, y, X, block_off, block_idx, nmemb, km
     n, d = locs.shape
     p = X.shape[1]
     q = nparms(covfun, d)
+    ng = nmemb.shape[0]
+    if classes is None:
+        gptr, nclass = None, 1
+        class_off = np.array([0, ng], dtype=np.int64)
+        class_kmax = np.array([int(kmax)], dtype=np.int32)
+    else:
+        gorder, class_off, class_kmax = classes
+        _dev_tensor_check(gorder, torch.int32, "gorder")
+        gptr, nclass = _dptr(gorder), len(class_kmax)
+        class_off = np.ascontiguousarray(class_off, dtype=np.int64)
+        class_kmax = np.ascontiguousarray(class_kmax, dtype=np.int32)
     dev = locs.device
     if handle is None:
         handle = default_handle(dev.index if dev.index is not None else 0)
@@ -893,9 +921,11 @@ def vecchia_grouped_loglik_grad_info(locs, y, X, block_off, block_idx, nmemb, km
         status = torch.empty(2, dtype=torch.int64, device=dev)
     if stream is None:
         stream = torch.cuda.current_stream(dev)
+    P = ctypes.c_void_p
     _check(lib().vecchia_grouped_loglik_grad_info(
-        handle.ptr, _dptr(locs), _dptr(y), _dptr(X), n, d, p, nmemb.shape[0], _dptr(block_off),
-        _dptr(block_idx), _dptr(nmemb), int(kmax), _dptr(covparms), covfun, _PREC[prec],
+        handle.ptr, _dptr(locs), _dptr(y), _dptr(X), n, d, p, ng, _dptr(block_off),
+        _dptr(block_idx), _dptr(nmemb), gptr, nclass, class_off.ctypes.data_as(P),
+        class_kmax.ctypes.data_as(P), _dptr(covparms), covfun, _PREC[prec],
         ctypes.c_void_p(stream.cuda_stream), _dptr(out), _dptr(status)))
     return out, status
 

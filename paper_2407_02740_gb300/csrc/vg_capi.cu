@@ -1637,52 +1637,143 @@ vec_status vecchia_group_blocks(const int32_t* NNarray, int64_t n, int m, const 
     return VEC_OK;
 }
 
+vec_status vecchia_group_classes(const int64_t* block_off, int64_t ngroups, int nclass,
+                                 int32_t* gorder, int64_t* class_off, int* class_kmax) {
+    if (!block_off || !gorder || !class_off || !class_kmax)
+        return fail(VEC_ERR_ARG, "vecchia_group_classes: NULL argument");
+    if (ngroups < 1 || ngroups > (int64_t)INT_MAX || nclass < 1 || nclass > 16)
+        return fail(VEC_ERR_ARG, "vecchia_group_classes: ngroups %lld, nclass %d", (long long)ngroups, nclass);
+    // histogram of block sizes (1 .. KMAX; larger blocks share the top bin)
+    const int V = vg::KMAX + 1;
+    std::vector<int64_t> cnt(V + 1, 0);
+    std::vector<int> len((size_t)ngroups);
+    for (int64_t b = 0; b < ngroups; ++b) {
+        const int64_t l = block_off[b + 1] - block_off[b];
+        if (l < 1) return fail(VEC_ERR_ARG, "vecchia_group_classes: block %lld is empty", (long long)b);
+        len[(size_t)b] = (int)std::min<int64_t>(l, V);
+        cnt[(size_t)len[(size_t)b]]++;
+    }
+    // classes = ranges of sizes; cost of a class = its groups x (its largest size)^2 (the
+    // slot size, so the inverse occupancy); minimise the total over at most nclass classes
+    std::vector<int> sizes;
+    for (int v = 1; v <= V; ++v)
+        if (cnt[(size_t)v]) sizes.push_back(v);
+    const int S = (int)sizes.size();
+    std::vector<int64_t> pre(S + 1, 0);
+    for (int k = 0; k < S; ++k) pre[k + 1] = pre[k] + cnt[(size_t)sizes[k]];
+    const int C = std::min(nclass, S);
+    const double INF = 1e300;
+    std::vector<double> best((size_t)(C + 1) * (S + 1), INF);
+    std::vector<int> from((size_t)(C + 1) * (S + 1), -1);
+    auto at = [&](int c, int k) -> size_t { return (size_t)c * (S + 1) + k; };
+    best[at(0, 0)] = 0.0;
+    for (int c = 1; c <= C; ++c)
+        for (int k = 1; k <= S; ++k)
+            for (int j = c - 1; j < k; ++j) {
+                if (best[at(c - 1, j)] >= INF) continue;
+                const double kk = (double)sizes[k - 1];
+                const double v = best[at(c - 1, j)] + (double)(pre[k] - pre[j]) * kk * kk;
+                if (v < best[at(c, k)]) { best[at(c, k)] = v; from[at(c, k)] = j; }
+            }
+    int cb = 1;
+    for (int c = 1; c <= C; ++c)
+        if (best[at(c, S)] < best[at(cb, S)]) cb = c;
+    std::vector<int> upper;   // largest size of each class, ascending
+    for (int c = cb, k = S; c > 0; --c) {
+        upper.push_back(sizes[k - 1]);
+        k = from[at(c, k)];
+    }
+    std::reverse(upper.begin(), upper.end());
+    // groups ordered by class, then by index
+    class_off[0] = 0;
+    int64_t pos = 0;
+    for (size_t c = 0; c < upper.size(); ++c) {
+        const int lo = c == 0 ? 0 : upper[c - 1];
+        for (int64_t b = 0; b < ngroups; ++b)
+            if (len[(size_t)b] > lo && len[(size_t)b] <= upper[c]) gorder[pos++] = (int32_t)b;
+        class_off[c + 1] = pos;
+        class_kmax[c] = upper[c];
+    }
+    for (int c = (int)upper.size(); c < nclass; ++c) {
+        class_off[c + 1] = pos;
+        class_kmax[c] = 0;
+    }
+    return VEC_OK;
+}
+
 vec_status vecchia_grouped_loglik_grad_info(vec_handle h, const double* locs, const double* y,
                                             const double* X, int64_t n, int d, int p, int64_t ngroups,
                                             const int64_t* block_off, const int32_t* block_idx,
-                                            const int32_t* nmemb, int kmax, const double* covparms,
-                                            vec_covfun covfun, vec_precision prec, void* stream,
-                                            double* out, int64_t* dev_status) {
+                                            const int32_t* nmemb, const int32_t* gorder, int nclass,
+                                            const int64_t* class_off, const int* class_kmax,
+                                            const double* covparms, vec_covfun covfun,
+                                            vec_precision prec, void* stream, double* out,
+                                            int64_t* dev_status) {
     if (!h) return fail(VEC_ERR_ARG, "vecchia_grouped_loglik_grad_info: NULL handle");
-    if (!locs || !y || !X || !block_off || !block_idx || !nmemb || !covparms || !out || !dev_status)
+    if (!locs || !y || !X || !block_off || !block_idx || !nmemb || !covparms || !out ||
+        !dev_status || !class_off || !class_kmax)
         return fail(VEC_ERR_ARG, "vecchia_grouped_loglik_grad_info: a required pointer is NULL");
     if (n < 1 || n > (int64_t)INT_MAX || ngroups < 1 || ngroups > n)
         return fail(VEC_ERR_ARG, "n = %lld, ngroups = %lld out of range", (long long)n, (long long)ngroups);
+    if (nclass < 1 || nclass > 16 || (!gorder && nclass != 1) || class_off[0] != 0 ||
+        class_off[nclass] != ngroups)
+        return fail(VEC_ERR_ARG, "bad group classes (nclass %d)", nclass);
+    for (int c = 0; c < nclass; ++c) {
+        if (class_off[c + 1] < class_off[c]) return fail(VEC_ERR_ARG, "class_off is not ascending");
+        if (class_off[c + 1] > class_off[c] && (class_kmax[c] < 1 || class_kmax[c] > vg::KMAX))
+            return fail(VEC_ERR_UNSUPPORTED, "largest block %d of class %d outside [1, %d]",
+                        class_kmax[c], c, vg::KMAX);
+    }
     if (covfun != VEC_EXP_ISO && covfun != VEC_MATERN_ISO && covfun != VEC_EXP_SPACETIME)
         return fail(VEC_ERR_UNSUPPORTED, "grouped conditioning: isotropic and space-time families only");
     const int q = vecchia_nparms_d(covfun, d);
     if (q < 0) return fail(VEC_ERR_ARG, "covariance function %d does not take d = %d", (int)covfun, d);
     if (p < 1 || p > vg::PMAX) return fail(VEC_ERR_ARG, "p = %d out of range [1, %d]", p, vg::PMAX);
-    if (kmax < 1 || kmax > vg::KMAX)
-        return fail(VEC_ERR_UNSUPPORTED, "largest block %d outside [1, %d]", kmax, vg::KMAX);
     if (prec != VEC_FP64 && prec != VEC_MIXED) return fail(VEC_ERR_ARG, "unknown precision %d", (int)prec);
     DeviceGuard g(h->device);
     if (!g.ok) return fail(VEC_ERR_CUDA, "cannot select device %d", h->device);
     const int cov = (int)covfun;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    vg::PassPlan plan;
-    int pr = vg::plan_pass(cov, kmax - 1, d, p, h->nsm, h->lanes, h->threads, &plan, (int)prec, false,
-                           h->tab_mode, true);
-    if (pr == -1) return fail(VEC_ERR_UNSUPPORTED, "no kernel mapping fits blocks of %d", kmax);
-    if (pr != 0) return cuda_fail(cudaGetLastError(), "planning the grouped pass kernel");
-    cudaError_t e = grow(&h->partials, &h->partials_cap, (size_t)plan.grid * plan.nstat);
+    // one launch per class, each sized by the class's largest block, writing its own range
+    // of partial records; one profile step over all of them
+    vg::PassPlan plans[16];
+    size_t total = 0;
+    int nstat = 0;
+    for (int c = 0; c < nclass; ++c) {
+        if (class_off[c + 1] == class_off[c]) continue;
+        int pr = vg::plan_pass(cov, class_kmax[c] - 1, d, p, h->nsm, h->lanes, h->threads, &plans[c],
+                               (int)prec, false, h->tab_mode, true);
+        if (pr == -1) return fail(VEC_ERR_UNSUPPORTED, "no kernel mapping fits blocks of %d", class_kmax[c]);
+        if (pr != 0) return cuda_fail(cudaGetLastError(), "planning the grouped pass kernel");
+        total += (size_t)plans[c].grid;
+        nstat = plans[c].nstat;
+    }
+    cudaError_t e = grow(&h->partials, &h->partials_cap, total * nstat);
     if (e == cudaSuccess) e = vg::launch_init_status(h->status, h->bad, st);
     if (e == cudaSuccess && cov == vg::COV_MATERN)
         e = vg::launch_mtab_build(covparms, h->mtab, prec ? h->mtabf : nullptr, st);
     if (e != cudaSuccess) return cuda_fail(e, "grouped pass: set-up");
-    vg::PassArgs a;
-    a.locs = locs; a.y = y; a.X = X; a.NN = nullptr; a.covparms = covparms;
-    a.mtab = h->mtab; a.mtabf = h->mtabf; a.partials = h->partials; a.status = h->status;
-    a.bad = h->bad;
-    a.n = n; a.d = d; a.p = p; a.m = kmax - 1;
-    a.nstat = plan.nstat; a.nv = plan.nv; a.slot_stride = plan.slot_stride;
-    a.acc_per_lane = plan.acc_per_lane; a.tab_in_smem = plan.tab_smem;
-    a.blk_off = reinterpret_cast<const long long*>(block_off); a.blk_idx = block_idx;
-    a.nmemb = nmemb; a.ngroups = ngroups;
-    e = vg::launch_pass(cov, plan, a, st);
+    size_t rec0 = 0;
+    for (int c = 0; c < nclass && e == cudaSuccess; ++c) {
+        if (class_off[c + 1] == class_off[c]) continue;
+        const vg::PassPlan& plan = plans[c];
+        vg::PassArgs a;
+        a.locs = locs; a.y = y; a.X = X; a.NN = nullptr; a.covparms = covparms;
+        a.mtab = h->mtab; a.mtabf = h->mtabf; a.partials = h->partials + rec0 * nstat;
+        a.status = h->status; a.bad = h->bad;
+        a.n = n; a.d = d; a.p = p; a.m = class_kmax[c] - 1;
+        a.nstat = plan.nstat; a.nv = plan.nv; a.slot_stride = plan.slot_stride;
+        a.acc_per_lane = plan.acc_per_lane; a.tab_in_smem = plan.tab_smem;
+        a.blk_off = reinterpret_cast<const long long*>(block_off); a.blk_idx = block_idx;
+        a.nmemb = nmemb; a.gorder = gorder ? gorder + class_off[c] : nullptr;
+        a.ngroups = class_off[c + 1] - class_off[c];
+        a.ngroups_all = ngroups;
+        e = vg::launch_pass(cov, plan, a, st);
+        rec0 += (size_t)plan.grid;
+    }
     if (e == cudaSuccess)
-        e = vg::launch_profile(h->partials, plan.grid, plan.nstat, p, q, n, covparms, h->status,
-                               h->bad, out, reinterpret_cast<long long*>(dev_status), st);
+        e = vg::launch_profile(h->partials, (int)total, nstat, p, q, n, covparms, h->status, h->bad,
+                               out, reinterpret_cast<long long*>(dev_status), st);
     if (e != cudaSuccess) return cuda_fail(e, "launching the grouped pass");
     return VEC_OK;
 }

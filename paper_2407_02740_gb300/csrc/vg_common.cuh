@@ -142,7 +142,9 @@ struct PassArgs {
     const long long* blk_off;
     const int32_t* blk_idx;
     const int32_t* nmemb;
-    long long ngroups;
+    const int32_t* gorder;             // unit u is group gorder[u] (nullptr: group u)
+    long long ngroups;                 // units of this launch
+    long long ngroups_all;             // groups in blk_off / nmemb
 };
 
 // Arguments of the batched pass kernel: many datasets (common d, p, covariance family),

@@ -920,8 +920,14 @@ __global__ void __launch_bounds__(256, pass_min_blocks(sizeof(T))) k_pass(PassAr
     E.vb0 = vb0; E.vstep = vstep; E.vmm = vmm; E.factor = nullptr;
     E.blk_off = args.blk_off; E.blk_idx = args.blk_idx; E.nmemb = args.nmemb; E.n = n;
     if constexpr (GROUPED) {
-        for (long long g = (long long)blockIdx.x * ngrp + grp; ok && g < args.ngroups; g += gstride)
+        for (long long u = (long long)blockIdx.x * ngrp + grp; ok && u < args.ngroups; u += gstride) {
+            const long long g = args.gorder ? (long long)args.gorder[u] : u;
+            if (g < 0 || g >= args.ngroups_all) {
+                if (gl == 0) report(args.status, args.bad, ST_ARG, u);
+                continue;
+            }
             vecchia_group<COV, L, T, Tab>(E, g);
+        }
     } else {
         for (long long i = (long long)blockIdx.x * ngrp + grp; ok && i < n; i += gstride) {
             if constexpr (COV == COV_ANISO) vecchia_point_aniso<L, T, Tab>(E, i);

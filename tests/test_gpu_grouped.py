@@ -65,6 +65,31 @@ def test_fp64_matches_oracle(covfun, theta, p, n, m, g):
         assert max(e.values()) <= 1e-10, (L, e)
 
 
+@pytest.mark.parametrize("nclass", [2, 3])
+def test_launch_classes_give_the_same_result(nclass):
+    th = np.array([1.1, 0.1, 0.8, 0.03])
+    w, goff = workloads.grouped_field(1500, MAT, th, 30, 8, p=2, seed=16, m_sim=30,
+                                      beta=[1.0, -0.5])
+    off, idx, nm, kmax = vg.vecchia_group_blocks(w.NN, goff)
+    one = _grouped(w, goff, th, blocks=(off, idx, nm, kmax))
+    gorder, coff, ckmax = vg.vecchia_group_classes(off, nclass)
+    h = vg.Handle(0)
+    try:
+        out, st = vg.vecchia_grouped_loglik_grad_info(
+            _dev(w.locs), _dev(w.y), _dev(w.X), _dev(off, torch.int64), _dev(idx, torch.int32),
+            _dev(nm, torch.int32), kmax, _dev(th), MAT, handle=h,
+            classes=(_dev(gorder, torch.int32), coff, ckmax))
+        torch.cuda.synchronize()
+    finally:
+        h.close()
+    assert int(st[0]) == 0
+    g = vg.unpack(out, 4, 2)
+    e = _errors(g, one)
+    assert max(e.values()) <= 1e-12, e
+    o = og.loglik_grad_info(w.locs, w.y, w.X, off, idx, nm, th, MAT)
+    assert max(_errors(g, o).values()) <= 1e-10
+
+
 def test_singleton_groups_equal_the_plain_pass():
     th = np.array([1.3, 0.08, 1.2, 0.05])
     w, _ = workloads.grouped_field(3000, MAT, th, 30, 8, p=2, seed=12, m_sim=30)

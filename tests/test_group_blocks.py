@@ -43,3 +43,28 @@ def test_bad_arguments():
     NN[3, 5] = 0
     with pytest.raises(vg.VecchiaError):
         vg.vecchia_group_blocks(NN, goff)
+
+
+@pytest.mark.parametrize("nclass", [1, 2, 3, 5])
+def test_group_classes_partition_the_groups(nclass):
+    w, goff = workloads.grouped_field(3000, 1, [1.0, 0.1, 1.0, 0.05], 30, 8, seed=6, m_sim=10)
+    off, idx, nm, kmax = vg.vecchia_group_blocks(w.NN, goff)
+    gorder, coff, ckmax = vg.vecchia_group_classes(off, nclass)
+    ng = len(off) - 1
+    assert sorted(gorder.tolist()) == list(range(ng)) and coff[0] == 0 and coff[-1] == ng
+    size = np.diff(off)
+    lo = 0
+    for c in range(nclass):
+        grp = gorder[coff[c]:coff[c + 1]]
+        if len(grp) == 0:
+            assert ckmax[c] == 0
+            continue
+        assert np.all(np.diff(grp) > 0)                       # ascending within a class
+        assert size[grp].max() == ckmax[c] and size[grp].min() > lo
+        lo = ckmax[c]
+    assert ckmax.max() == kmax
+    if nclass == 1:
+        assert coff[1] == ng
+    # more classes never cost more (sum of groups x largest size^2)
+    cost = sum((coff[c + 1] - coff[c]) * int(ckmax[c]) ** 2 for c in range(nclass))
+    assert cost <= ng * kmax ** 2
