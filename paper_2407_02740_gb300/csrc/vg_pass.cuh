@@ -22,6 +22,12 @@
 //   accumulate  per-observation values into per-lane FP64 running sums (shared memory),
 //               then a fixed-order block reduction into one partial record per block.
 //
+// The steps are device functions (assemble_block, chol_augmented, conditional_terms, ...)
+// shared by three bodies: vecchia_point (one observation), vecchia_group (grouped
+// conditioning: one Cholesky per group, then conditional_terms for each member on the
+// leading block ending at its row) and vecchia_point_aniso (one range per coordinate: the
+// d + 1 derivative vectors live in the slot and their work is split into lane items).
+//
 // T is the working type of the block.  T = double is the FP64 path.  T = float is the
 // mixed path: the block, the covariance entries, the factorisation, the solves and the
 // derivative work are FP32; the coordinate differences (taken in FP64 relative to the

@@ -68,3 +68,14 @@ def test_group_classes_partition_the_groups(nclass):
     # more classes never cost more (sum of groups x largest size^2)
     cost = sum((coff[c + 1] - coff[c]) * int(ckmax[c]) ** 2 for c in range(nclass))
     assert cost <= ng * kmax ** 2
+
+
+def test_group_classes_errors_and_single_group():
+    off = np.array([0, 12], dtype=np.int64)
+    gorder, coff, ckmax = vg.vecchia_group_classes(off, 4)
+    assert list(gorder) == [0] and list(coff) == [0, 1, 1, 1, 1] and list(ckmax) == [12, 0, 0, 0]
+    for nclass in (0, 17):
+        with pytest.raises(vg.VecchiaError):
+            vg.vecchia_group_classes(off, nclass)
+    with pytest.raises(vg.VecchiaError):
+        vg.vecchia_group_classes(np.array([0, 5, 5, 9], dtype=np.int64), 2)   # an empty block
