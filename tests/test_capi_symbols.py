@@ -51,3 +51,13 @@ def test_host_only_queries_and_argument_errors():
     # a NULL handle is rejected before any CUDA call
     assert lib.vecchia_set_lanes(None, 4) == 1
     assert b"NULL" in lib.vecchia_last_error()
+
+
+def test_no_fallback_without_the_library(monkeypatch, tmp_path):
+    # the product path has no CPU fallback: without the built library every call fails loudly
+    monkeypatch.setattr(vg, "_lib", None)
+    monkeypatch.setattr(vg, "LIB_PATH", str(tmp_path / "libvecchia_gb300.so"))
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        vg.lib()
+    with pytest.raises(RuntimeError):
+        vg.nparms(vg.EXP_ISO, 2)
