@@ -519,7 +519,7 @@ VECCHIA_API vec_status vecchia_predict(vec_handle h, const double* locs, const d
                                        int64_t* dev_status);
 
 /*
- * Grouped conditioning (Sec. 2.2: conditioning on joint distributions).  Observations are
+ * Grouped conditioning (Sec. 2.1, Sec. 5: one joint conditional per group).  Observations are
  * partitioned into groups that are contiguous ranges of the ordering; group b (members
  * B = s .. e-1) conditions jointly on U = (the members' NNarray neighbours) minus B, which
  * lies before s, so the product of the group conditionals p(y_B | y_U) is a valid density.

@@ -1,8 +1,8 @@
 """Oracle for grouped (joint) conditioning -- TEST INFRASTRUCTURE (see ``oracle/__init__``).
 
-Sec. 2.2 notes that Vecchia's conditionals may be taken on joint distributions: a group of
-observations is conditioned on jointly, which lowers the number of likelihood terms and
-sharpens the approximation.  The definitions used here:
+Sec. 2.1 (and Sec. 5, as future work) mentions grouping: several observations share one
+conditional, which means fewer likelihood terms and a sharper approximation.  The
+definitions used here:
 
 * groups are contiguous ranges B_b = [s_b, e_b) of the ordering;
 * group b conditions on U_b = (union over i in B_b of i's NNarray neighbours) minus B_b.
