@@ -59,7 +59,7 @@ typedef enum {
     VEC_ERR_NOMEM = 4,       /* device allocation failed                                 */
     VEC_ERR_CUDA = 5,        /* a CUDA runtime call failed                               */
     VEC_ERR_TIMEOUT = 6,     /* a bounded device wait gave up                            */
-    VEC_ERR_UNSUPPORTED = 7  /* size or option outside what this build supports          */
+    VEC_ERR_UNSUPPORTED = 7  /* size or option outside what this library supports        */
 } vec_status;
 
 typedef enum {
@@ -98,7 +98,7 @@ VECCHIA_API int vecchia_nparms(vec_covfun covfun);
  * (VEC_EXP_ANISO: d + 2), or -1 if the family is unknown or does not take d. */
 VECCHIA_API int vecchia_nparms_d(vec_covfun covfun, int d);
 
-/* Largest m supported by this build (the conditioning block is (m+1) x (m+1)). */
+/* Largest m this library supports (the conditioning block is (m+1) x (m+1)). */
 VECCHIA_API int vecchia_max_m(void);
 
 /* Lanes of a warp that work on one observation in the pass kernel: 1, 2, 4, 8, 16 or 32,
