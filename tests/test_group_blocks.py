@@ -79,3 +79,27 @@ def test_group_classes_errors_and_single_group():
             vg.vecchia_group_classes(off, nclass)
     with pytest.raises(vg.VecchiaError):
         vg.vecchia_group_classes(np.array([0, 5, 5, 9], dtype=np.int64), 2)   # an empty block
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_group_classes_minimise_the_stated_cost(seed):
+    # brute force over every split of the distinct block sizes into at most nclass ranges
+    import itertools
+    rng = np.random.default_rng(seed)
+    sizes = rng.integers(1, 82, size=int(rng.integers(3, 40)))
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    nclass = int(rng.integers(1, 4))
+    gorder, coff, ckmax = vg.vecchia_group_classes(off, nclass)
+    got = sum((coff[c + 1] - coff[c]) * int(ckmax[c]) ** 2 for c in range(nclass))
+    vals = np.unique(sizes)
+    best = None
+    for k in range(1, min(nclass, len(vals)) + 1):
+        for cuts in itertools.combinations(range(1, len(vals)), k - 1):
+            bounds = list(cuts) + [len(vals)]
+            lo, cost = 0, 0
+            for b in bounds:
+                top = vals[b - 1]
+                cost += int(np.sum((sizes > (vals[lo - 1] if lo else 0)) & (sizes <= top))) * int(top) ** 2
+                lo = b
+            best = cost if best is None else min(best, cost)
+    assert got == best
