@@ -174,3 +174,24 @@ def test_argument_errors():
     with pytest.raises(ValueError):                         # more than 20 coordinates
         vg.nparms(ANI, 21)
     assert vg.lib().vecchia_nparms_d(ANI, 21) == -1
+
+
+def test_batched_fit_matches_oracle_fits():
+    fields = [_field(n, 3, m, 1, seed) for n, m, seed in ((900, 12, 51), (1400, 15, 52))]
+    off = np.cumsum([0] + [w.n for w, _ in fields])
+    locs = np.concatenate([w.locs for w, _ in fields])
+    y = np.concatenate([w.y for w, _ in fields])
+    X = np.concatenate([w.X for w, _ in fields])
+    NN = np.concatenate([w.NN.reshape(-1) for w, _ in fields])
+    start = np.tile(np.concatenate([[1.0], np.full(3, 0.5), [0.2]]), (len(fields), 1))
+    h = vg.Handle(0)
+    try:
+        r = vg.vecchia_batch_fit(_dev(locs), _dev(y), _dev(X), _dev(NN, torch.int32), list(off),
+                                 [w.m for w, _ in fields], ANI, _dev(start), tol=1e-6, handle=h)
+    finally:
+        h.close()
+    theta = r["theta"].cpu().numpy() if hasattr(r["theta"], "cpu") else np.asarray(r["theta"])
+    for b, (w, _) in enumerate(fields):
+        o = oracle.fisher_fit(w.locs, w.y, w.X, w.NN, ANI, start[b], tol=1e-6)
+        assert o["status"] == 0 and int(r["status"][b]) == 0
+        assert np.allclose(theta[b], o["theta"], rtol=1e-7, atol=0)
