@@ -456,6 +456,28 @@ VECCHIA_API vec_status vecchia_mlp_adam_step(vec_handle h, float* params, float*
 VECCHIA_API vec_status vecchia_mlp_column_moments(vec_handle h, const float* X, int rows,
                                                   int cols, void* stream, float* mean,
                                                   float* sd);
+/*
+ * Small per-field steps of the learned start, on the device (all pointers DEVICE memory,
+ * asynchronous on `stream`):
+ * vecchia_fields_moments: mean and population variance (FP64, two passes, fixed-order
+ *   sums) of each row of Y (nfields x n), the var(y) of the default start (Sec. 4's fit
+ *   rules scale sigma2 by the data) and of the network's first output.
+ * vecchia_mlp_targets: training targets (nfields x 4, FP32) from fitted parameters theta
+ *   (nfields x 4, MATERN_ISO): (log(sigma2 / var), log rho, log nu, log tau2), component j
+ *   clamped to [log lo[j], log hi[j]]; lo and hi are HOST arrays of 4 with
+ *   0 < lo[j] <= hi[j] < inf.
+ * vecchia_mlp_theta: theta0 (nfields x 4) from network outputs pred (nfields x 4, FP32):
+ *   (var e^t0, e^t1, e^t2 clamped to [0.05, 20], e^t3), the rule vecchia_fields_warm_start
+ *   applies.
+ */
+VECCHIA_API vec_status vecchia_fields_moments(vec_handle h, int nfields, int64_t n,
+                                              const double* Y, void* stream, double* mean,
+                                              double* var);
+VECCHIA_API vec_status vecchia_mlp_targets(vec_handle h, int nfields, const double* theta,
+                                           const double* var, const double* lo, const double* hi,
+                                           void* stream, float* targets);
+VECCHIA_API vec_status vecchia_mlp_theta(vec_handle h, int nfields, const float* pred,
+                                         const double* var, void* stream, double* theta);
 VECCHIA_API vec_status vecchia_fields_warm_start(vec_handle h, const float* params,
                                                  const float* norm, int nfields,
                                                  const double* locs, const double* X,
@@ -593,35 +615,43 @@ VECCHIA_API vec_status vecchia_measure_peaks(vec_handle h, double* out);
  * These are the functions assembled in Algorithm 1 (Sec. 4.3 Eq. 6 and the Matern family);
  * for the Matern family the call first rebuilds the handle's coefficient table for nu.
  * Pointers are DEVICE memory, caller owned: covparms (q), la and lb (npairs x d), same
- * (npairs int32), C (npairs), dC (npairs x q).  Asynchronous on `stream`.
+ * (npairs int32), C (npairs), dC (npairs x q).  Asynchronous on `stream`.  covparms is
+ * read on the device, so it is checked there: parameters outside the family's domain
+ * (not positive and finite, or a Matern smoothness outside [0.05, 20]) give NaN in every
+ * output entry.
  */
 VECCHIA_API vec_status vecchia_covariance_pairs(vec_handle h, vec_covfun covfun, const double* covparms,
                                     int d, int64_t npairs, const double* la, const double* lb,
                                     const int32_t* same, double* C, double* dC, void* stream);
 
 /*
- * vecchia_loglik_grad_info_noalloc -- the device-resident pass without any allocation.
+ * vecchia_loglik_grad_info_noalloc -- the device-resident FP64 pass without any allocation.
  *
- * The paper has no counterpart to this entry point; it exists for callers that cannot
- * allocate device memory at the moment they need a likelihood value: code that runs
- * while its stream is being captured into a CUDA graph (an allocation cannot be part of
- * a capture), programs whose GPU memory is owned entirely by another allocator or held
- * to a fixed budget, and latency-sensitive loops that cannot afford the device-wide
- * synchronisation an allocation may cause.
+ * The paper has no counterpart to this entry point.  It is for callers that cannot
+ * allocate device memory at the moment they need a likelihood value: programs whose GPU
+ * memory is owned entirely by another allocator (a framework's caching pool, an
+ * application that reserves the whole device at start-up) or held to a fixed budget, and
+ * latency-sensitive loops that cannot afford the device-wide synchronisation an
+ * allocation may cause.
  *
- * Same arguments, layouts, results and error reporting as vecchia_loglik_grad_info, but
- * no handle: it runs on the calling thread's current CUDA device, all pointers must be
- * device memory on that device, and the caller still provides `out` and `dev_status`.
+ * Arguments, layouts, results and error reporting are those of vecchia_loglik_grad_info
+ * with prec = VEC_FP64, but there is no handle: it runs on the calling thread's current
+ * CUDA device, all pointers must be device memory on that device, and the caller still
+ * provides `out` and `dev_status`.  Only the FP64 path is offered: prec = VEC_MIXED is
+ * rejected with VEC_ERR_UNSUPPORTED before anything runs.
+ *
  * It calls no cudaMalloc, cudaFree or other allocating routine.  Its scratch (per-block
  * partial sums, status word, Matern table) is one file-scope device array of
  * 1,102,592 bytes that every GPU loading this library holds until the process exits;
  * the partial-sum region holds 131072 doubles, and a pass whose launch plan needs more
  * (blocks x record length) is rejected with VEC_ERR_UNSUPPORTED before anything runs.
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress,
- * with that device current); make that first call before any stream capture.
- * Every call shares the one array and leaves its contents behind: the kernels reset the
- * status word and rewrite the rest in full on each call, but calls whose work overlaps on
- * the GPU (other streams, other host threads) race on it and must be serialised.
+ * The first call on a device does a one-time set-up with that device current: it looks
+ * up the array's device address (cudaGetSymbolAddress) and loads every kernel the entry
+ * point can launch, so that later calls load no code.  Make that first call before any
+ * stream capture.  Every call shares the one array and leaves its contents behind: the
+ * kernels reset the status word and rewrite the rest in full on each call, but calls
+ * whose work overlaps on the GPU (other streams, other host threads) race on it and must
+ * be serialised.
  */
 VECCHIA_API vec_status vecchia_loglik_grad_info_noalloc(const double* locs, const double* y,
                                                         const double* X, const int32_t* NNarray,

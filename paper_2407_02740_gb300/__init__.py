@@ -139,6 +139,9 @@ def lib():
         L.vecchia_mlp_grad.argtypes = [P, P, P, P, P, P, ci, P, P, P]
         L.vecchia_mlp_adam_step.argtypes = [P, P, P, P, ci, cf, P, P, P, P, ci, P, P]
         L.vecchia_mlp_column_moments.argtypes = [P, P, ci, ci, P, P, P]
+        L.vecchia_fields_moments.argtypes = [P, ci, i64, P, P, P, P]
+        L.vecchia_mlp_targets.argtypes = [P, ci, P, P, P, P, P, P]
+        L.vecchia_mlp_theta.argtypes = [P, ci, P, P, P, P]
         L.vecchia_fields_warm_start.argtypes = [P, P, P, ci, P, P, P, i64, ci, ci, ci, P, P, i64,
                                                 P, P, ci, P, P, P, P]
         for f in (L.vecchia_create, L.vecchia_destroy, L.vecchia_set_lanes, L.vecchia_set_block_threads,
@@ -155,6 +158,7 @@ def lib():
                   L.vecchia_fields_fit, L.vecchia_fields_simulate,
                   L.vecchia_fields_variogram, L.vecchia_mlp_forward, L.vecchia_mlp_grad,
                   L.vecchia_mlp_adam_step, L.vecchia_mlp_column_moments,
+                  L.vecchia_fields_moments, L.vecchia_mlp_targets, L.vecchia_mlp_theta,
                   L.vecchia_fields_warm_start, L.vecchia_ordered_nn, L.vecchia_nearest,
                   L.vecchia_predict, L.vecchia_measure_peaks, L.vecchia_group_blocks,
                   L.vecchia_group_classes, L.vecchia_grouped_loglik_grad_info):
@@ -688,6 +692,58 @@ def vecchia_mlp_column_moments(X, stream=None, handle: Handle | None = None):
     return mean, sd
 
 
+def vecchia_fields_moments(Y, stream=None, handle: Handle | None = None):
+    """Mean and population variance (float64) of each row of a float64 CUDA matrix Y
+    (nfields, n)."""
+    import torch
+    _dev_tensor_check(Y, torch.float64, "Y")
+    if Y.dim() != 2:
+        raise ValueError("Y must be (nfields, n)")
+    handle = handle or default_handle(Y.device.index or 0)
+    mean = torch.empty(Y.shape[0], dtype=torch.float64, device=Y.device)
+    var = torch.empty_like(mean)
+    _check(lib().vecchia_fields_moments(handle.ptr, Y.shape[0], Y.shape[1], _dptr(Y),
+                                        ctypes.c_void_p(_stream(Y, stream).cuda_stream),
+                                        _dptr(mean), _dptr(var)))
+    return mean, var
+
+
+def vecchia_mlp_targets(theta, var, lo, hi, stream=None, handle: Handle | None = None):
+    """Training targets (nfields, 4) float32 from fitted MATERN_ISO parameters theta
+    (nfields, 4) float64 and the fields' variances var (nfields): (log(sigma2 / var),
+    log rho, log nu, log tau2), component j clamped to [log lo[j], log hi[j]]."""
+    import torch
+    _dev_tensor_check(theta, torch.float64, "theta")
+    _dev_tensor_check(var, torch.float64, "var")
+    nf = theta.shape[0]
+    if theta.dim() != 2 or theta.shape[1] != 4 or var.shape[0] != nf:
+        raise ValueError("theta (nfields, 4), var (nfields)")
+    handle = handle or default_handle(theta.device.index or 0)
+    T = torch.empty(nf, 4, dtype=torch.float32, device=theta.device)
+    lo_ = (ctypes.c_double * 4)(*[float(v) for v in lo])
+    hi_ = (ctypes.c_double * 4)(*[float(v) for v in hi])
+    _check(lib().vecchia_mlp_targets(handle.ptr, nf, _dptr(theta), _dptr(var), lo_, hi_,
+                                     ctypes.c_void_p(_stream(theta, stream).cuda_stream),
+                                     _dptr(T)))
+    return T
+
+
+def vecchia_mlp_theta(pred, var, stream=None, handle: Handle | None = None):
+    """theta0 (nfields, 4) float64 from network outputs pred (nfields, 4) float32 and the
+    fields' variances: (var e^t0, e^t1, e^t2 clamped to [0.05, 20], e^t3)."""
+    import torch
+    _dev_tensor_check(pred, torch.float32, "pred")
+    _dev_tensor_check(var, torch.float64, "var")
+    nf = pred.shape[0]
+    if pred.dim() != 2 or pred.shape[1] != 4 or var.shape[0] != nf:
+        raise ValueError("pred (nfields, 4), var (nfields)")
+    handle = handle or default_handle(pred.device.index or 0)
+    th = torch.empty(nf, 4, dtype=torch.float64, device=pred.device)
+    _check(lib().vecchia_mlp_theta(handle.ptr, nf, _dptr(pred), _dptr(var),
+                                   ctypes.c_void_p(_stream(pred, stream).cuda_stream), _dptr(th)))
+    return th
+
+
 def vecchia_fields_warm_start(params, norm, locs, X, NNarray, Y, rand_pairs, edges2,
                               default_start, prec="fp64", stream=None,
                               handle: Handle | None = None):
@@ -776,11 +832,12 @@ def vecchia_fit(locs, y, X, NNarray, covfun: int, start, tol: float = 1e-4, maxi
 
 def vecchia_loglik_grad_info_noalloc(locs, y, X, NNarray, covparms, covfun: int,
                                      prec="fp64", stream=None, out=None, status=None):
-    """The device-resident pass without any device allocation by the library: for callers
-    that cannot allocate (inside a stream capture, under another allocator's budget).  It
-    runs on the current CUDA device with the library's static scratch; `out` and `status`
-    are still supplied by the caller (allocated here only when not given).  Calls that
-    overlap on the GPU share that scratch and must be serialised."""
+    """The device-resident FP64 pass without any device allocation by the library: for
+    callers that cannot allocate (GPU memory owned by another allocator or held to a fixed
+    budget, loops that cannot take an allocation's synchronisation).  It runs on the
+    current CUDA device with the library's static scratch; `out` and `status` are still
+    supplied by the caller (allocated here only when not given).  Only prec="fp64" is
+    accepted.  Calls that overlap on the GPU share that scratch and must be serialised."""
     import torch
     for t, dt, nm in ((locs, torch.float64, "locs"), (y, torch.float64, "y"),
                       (X, torch.float64, "X"), (NNarray, torch.int32, "NNarray"),

@@ -1399,6 +1399,45 @@ vec_status vecchia_fields_variogram(vec_handle h, int nfields, const double* loc
     return VEC_OK;
 }
 
+vec_status vecchia_fields_moments(vec_handle h, int nfields, int64_t n, const double* Y,
+                                  void* stream, double* mean, double* var) {
+    if (!h || !Y || !mean || !var || nfields < 1 || n < 1 || n > (int64_t)INT_MAX)
+        return fail(VEC_ERR_ARG, "vecchia_fields_moments: bad argument");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(VEC_ERR_CUDA, "cannot select device %d", h->device);
+    cudaError_t e = vg::launch_field_moments(Y, (int)n, nfields, mean, var,
+                                             reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "vecchia_fields_moments");
+    return VEC_OK;
+}
+
+vec_status vecchia_mlp_targets(vec_handle h, int nfields, const double* theta, const double* var,
+                               const double* lo, const double* hi, void* stream, float* targets) {
+    if (!h || !theta || !var || !lo || !hi || !targets || nfields < 1)
+        return fail(VEC_ERR_ARG, "vecchia_mlp_targets: bad argument");
+    for (int j = 0; j < 4; ++j)
+        if (!(lo[j] > 0.0 && hi[j] >= lo[j] && std::isfinite(hi[j])))
+            return fail(VEC_ERR_ARG, "vecchia_mlp_targets: range %d is not 0 < lo <= hi < inf", j);
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(VEC_ERR_CUDA, "cannot select device %d", h->device);
+    cudaError_t e = vg::launch_targets_from_theta(theta, var, nfields, lo, hi, targets,
+                                                  reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "vecchia_mlp_targets");
+    return VEC_OK;
+}
+
+vec_status vecchia_mlp_theta(vec_handle h, int nfields, const float* pred, const double* var,
+                             void* stream, double* theta) {
+    if (!h || !pred || !var || !theta || nfields < 1)
+        return fail(VEC_ERR_ARG, "vecchia_mlp_theta: bad argument");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(VEC_ERR_CUDA, "cannot select device %d", h->device);
+    cudaError_t e = vg::launch_theta_from_pred(pred, var, nfields, theta,
+                                               reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "vecchia_mlp_theta");
+    return VEC_OK;
+}
+
 vec_status vecchia_mlp_forward(vec_handle h, const float* params, const float* norm,
                                const float* X, int nsamples, void* stream, float* out) {
     if (!h || !params || !norm || !X || !out) return fail(VEC_ERR_ARG, "vecchia_mlp_forward: NULL argument");

@@ -109,8 +109,11 @@ __device__ __forceinline__ double rsqrt_newton(double v) {
 }
 
 // digamma(x), x > 0: shift upward with psi(x) = psi(x+1) - 1/x until x >= 12, then the
-// asymptotic expansion psi(z) = ln z - 1/(2z) - sum_k B_2k / (2k z^2k).
+// asymptotic expansion psi(z) = ln z - 1/(2z) - sum_k B_2k / (2k z^2k).  Outside the
+// domain (x <= 0, NaN or infinite) the result is NaN; the shift loop then never starts,
+// so it runs at most 12 times for every input.
 __device__ inline double dev_digamma(double x) {
+    if (!(x > 0.0) || !(x <= 1.7976931348623157e308)) return __longlong_as_double(0x7ff8000000000000ll);
     double acc = 0.0;
     while (x < 12.0) { acc -= 1.0 / x; x += 1.0; }
     double iz = 1.0 / x, z2 = iz * iz;

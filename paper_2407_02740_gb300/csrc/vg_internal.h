@@ -64,6 +64,8 @@ cudaError_t launch_col_moments(const float* X, int rows, int cols, float* mean, 
                                cudaStream_t st);
 cudaError_t launch_theta_from_pred(const float* pred, const double* var, int nfields, double* theta,
                                    cudaStream_t st);
+cudaError_t launch_targets_from_theta(const double* theta, const double* var, int nfields,
+                                      const double* lo, const double* hi, float* T, cudaStream_t st);
 cudaError_t launch_choose_start(const double* theta0, const double* dflt, const double* out0,
                                 const long long* st0, const double* out1, const long long* st1,
                                 int nfields, int q, int nout, double* start, int* used,
@@ -94,6 +96,8 @@ cudaError_t launch_profile_batch(const double* partials, const int* tile_off, in
 cudaError_t launch_pass(int cov, const PassPlan& plan, const PassArgs& args, cudaStream_t st);
 cudaError_t launch_init_status(int* status, long long* bad, cudaStream_t st);
 cudaError_t launch_mtab_build(const double* covparms, double* tab, float* tabf, cudaStream_t st);
+// Loads (under lazy module loading) every kernel the single-dataset FP64 pass can launch.
+cudaError_t load_pass_kernels_f64();
 cudaError_t launch_profile(const double* partials, int nblk, int nstat, int p, int q,
                            long long n, const double* covparms, const int* status,
                            const long long* bad, double* out, long long* dev_status,

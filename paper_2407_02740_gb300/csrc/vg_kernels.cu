@@ -298,6 +298,13 @@ __global__ void k_cov_pairs(const double* __restrict__ covparms, const double* _
     if (i >= npairs) return;
     const int q = nparms(COV, d);
     const double* th = covparms;
+    // parameters outside the family's domain (the check the pass applies) give NaN
+    if (!theta_ok(COV, d, th)) {
+        const double nan = __longlong_as_double(0x7ff8000000000000ll);
+        C[i] = nan;
+        for (int j = 0; j < q; ++j) dC[i * q + j] = nan;
+        return;
+    }
     const double s2 = th[0], tau2 = th[q - 1];
     const double* a = la + i * d;
     const double* b = lb + i * d;
@@ -550,6 +557,27 @@ cudaError_t launch_cov_pairs(int cov, const double* covparms, const double* tab,
         return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+cudaError_t load_pass_kernels_f64() {
+    // cudaFuncGetAttributes makes the runtime load a kernel that lazy module loading has
+    // not loaded yet; every kernel the single-dataset FP64 pass can launch is touched
+    cudaFuncAttributes fa;
+    const void* fixed[] = {reinterpret_cast<const void*>(&k_init_status),
+                           reinterpret_cast<const void*>(&k_mtab_build),
+                           reinterpret_cast<const void*>(&k_profile)};
+    for (const void* fn : fixed) {
+        cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+        if (e != cudaSuccess) return e;
+    }
+    for (int cov = COV_EXP; cov <= COV_ANISO; ++cov)
+        for (int L = 1; L <= 32; L *= 2) {
+            const void* fn = pass_kernel_f64(cov, L);
+            if (!fn) continue;
+            cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+            if (e != cudaSuccess) return e;
+        }
+    return cudaSuccess;
 }
 
 int mtab_doubles() { return MT_DOUBLES; }

@@ -289,6 +289,32 @@ __global__ void k_choose_start(const double* __restrict__ theta0, const double* 
     used[f] = ok ? 1 : 0;
 }
 
+// Training targets from fitted parameters: t_j = log theta_j (log(sigma2 / var y) for
+// j = 0), clamped to [log lo_j, log hi_j], FP32.
+struct TargetRange {
+    double lo[4], hi[4];
+};
+__global__ void k_targets_from_theta(const double* __restrict__ theta, const double* __restrict__ var,
+                                     int nfields, TargetRange R, float* __restrict__ T) {
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nfields) return;
+    const double* th = theta + (size_t)f * 4;
+    for (int j = 0; j < 4; ++j) {
+        double t = log(th[j]);
+        if (j == 0) t -= log(var[f]);
+        t = fmin(log(R.hi[j]), fmax(log(R.lo[j]), t));
+        T[(size_t)f * MO + j] = (float)t;
+    }
+}
+
+cudaError_t launch_targets_from_theta(const double* theta, const double* var, int nfields,
+                                      const double* lo, const double* hi, float* T, cudaStream_t st) {
+    TargetRange R;
+    for (int j = 0; j < 4; ++j) { R.lo[j] = lo[j]; R.hi[j] = hi[j]; }
+    k_targets_from_theta<<<(nfields + 127) / 128, 128, 0, st>>>(theta, var, nfields, R, T);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_theta_from_pred(const float* pred, const double* var, int nfields, double* theta,
                                    cudaStream_t st) {
     k_theta_from_pred<<<(nfields + 127) / 128, 128, 0, st>>>(pred, var, nfields, theta);

@@ -1,18 +1,19 @@
 // vg_noalloc.cu -- a pass entry point that allocates no device memory.
 //
-// Some callers cannot allocate device memory when they need a likelihood value: code that
-// runs while its stream is being captured into a CUDA graph (cudaMalloc is not an
-// operation that can be captured), host programs whose GPU memory is owned entirely by
-// another allocator or held to a fixed budget, and latency-sensitive loops in which the
-// implicit device synchronisation of an allocation is not acceptable.  For them,
-// vecchia_loglik_grad_info_noalloc runs the same kernels as vecchia_loglik_grad_info but
-// takes its scratch (per-block partial sums, the status word, the Matern table) from the
-// file-scope device array below instead of a handle.  Every GPU that loads this library
-// holds that array (1,102,592 bytes) until the process exits.
+// Some callers cannot allocate device memory when they need a likelihood value: host
+// programs whose GPU memory is owned entirely by another allocator (a framework's caching
+// pool, an application that reserves the whole device at start-up) or held to a fixed
+// budget, and latency-sensitive loops in which the implicit device synchronisation of an
+// allocation is not acceptable.  For them, vecchia_loglik_grad_info_noalloc runs the same
+// FP64 kernels as vecchia_loglik_grad_info but takes its scratch (per-block partial sums,
+// the status word, the Matern table) from the file-scope device array below instead of a
+// handle.  Every GPU that loads this library holds that array (1,102,592 bytes) until the
+// process exits.
 //
 // Host code must not pass the array's name to a kernel: on the host the name is only a
 // stand-in for the symbol.  Its device address is looked up once per device with
-// cudaGetSymbolAddress, with that device current, during the first call on the device.
+// cudaGetSymbolAddress, with that device current, during the first call on the device;
+// the same one-time set-up loads every kernel the entry point can launch.
 #include <climits>
 #include <cstdarg>
 #include <cstdio>
@@ -91,6 +92,9 @@ VECCHIA_API vec_status vecchia_loglik_grad_info_noalloc(
             e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
             if (e != cudaSuccess || sms < 1)
                 return nfail(VEC_ERR_CUDA, "cannot query the SM count: %s", cudaGetErrorString(e));
+            e = vg::load_pass_kernels_f64();
+            if (e != cudaSuccess)
+                return nfail(VEC_ERR_CUDA, "loading the pass kernels failed: %s", cudaGetErrorString(e));
             g_scratch_ptr[dev] = static_cast<double*>(ptr);
             g_nsm[dev] = sms;
         }
@@ -102,7 +106,11 @@ VECCHIA_API vec_status vecchia_loglik_grad_info_noalloc(
     vg::PassPlan plan;
     int pr = vg::plan_pass(cov, m, d, p, nsm, 0, 0, &plan);
     if (pr == -1) return nfail(VEC_ERR_UNSUPPORTED, "no kernel mapping fits m = %d, p = %d", m, p);
-    if (pr != 0) return nfail(VEC_ERR_CUDA, "planning the pass kernel failed");
+    if (pr != 0) {
+        // report the runtime's error and clear it, so that it does not surface in a later call
+        e = cudaGetLastError();
+        return nfail(VEC_ERR_CUDA, "planning the pass kernel failed: %s", cudaGetErrorString(e));
+    }
     const long long need = (long long)plan.grid * plan.nstat;
     if (need > kPartLen)
         return nfail(VEC_ERR_UNSUPPORTED,

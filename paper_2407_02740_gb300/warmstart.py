@@ -2,10 +2,10 @@
 start from fixed rules): training data, training, and use with a fallback.
 
 The simulation, the fits, the features, the network's training and inference and the
-learned start with its fallback run in the library's CUDA kernels through the C ABI.  This
-module orders those calls; PyTorch provides device memory, the seeded random inputs
-(normal variates, random index pairs, sample permutations) and the element-wise
-bookkeeping around them: the default start's var(y) and the training targets' logarithms.
+learned start with its fallback, the fields' variances and the training targets run in
+the library's CUDA kernels through the C ABI.  This module orders those calls; PyTorch
+provides device memory and the seeded random inputs (normal variates, random index pairs,
+sample permutations).
 
 Fields are isotropic Matern fields at one shared set of n locations (maxmin order and
 ordered-neighbour array supplied by the caller), X = 1 (beta = 0):
@@ -32,9 +32,10 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from . import (MATERN_ISO, MLP_NPARAMS, vecchia_fields_fit, vecchia_fields_simulate,
-               vecchia_fields_variogram, vecchia_fields_warm_start, vecchia_mlp_adam_step,
-               vecchia_mlp_column_moments, vecchia_mlp_forward, vecchia_mlp_grad)
+from . import (MATERN_ISO, MLP_NPARAMS, vecchia_fields_fit, vecchia_fields_moments,
+               vecchia_fields_simulate, vecchia_fields_variogram, vecchia_fields_warm_start,
+               vecchia_mlp_adam_step, vecchia_mlp_column_moments, vecchia_mlp_forward,
+               vecchia_mlp_grad, vecchia_mlp_targets, vecchia_mlp_theta)
 
 PRIORS = {"sigma2": (0.5, 2.0), "rho": (0.02, 0.3), "nu": (0.5, 2.5), "tau2": (0.001, 0.2)}
 NBINS, LAG_LO, LAG_HI = 32, 0.005, 0.5
@@ -81,7 +82,7 @@ def sample_priors(rng: np.random.Generator, nfields: int) -> np.ndarray:
 def default_start(Y):
     """(var y, 0.1, 1, 0.1) per field, on the device (FP64 variance of each row)."""
     import torch
-    var = Y.var(dim=1, unbiased=False)
+    _, var = vecchia_fields_moments(Y)
     s = torch.empty(Y.shape[0], 4, dtype=torch.float64, device=Y.device)
     s[:, 0] = var
     s[:, 1] = 0.1
@@ -108,13 +109,9 @@ TARGET_RANGE = ((1e-2, 1e2), (1e-4, 1e1), (0.05, 20.0), (1e-6, 1e1))
 
 def targets_from_fit(theta_hat, Y):
     """(log(sigma2 / var y), log rho, log nu, log tau2), clamped to TARGET_RANGE, float32."""
-    import torch
-    var = Y.var(dim=1, unbiased=False)
-    t = torch.log(theta_hat.clone())
-    t[:, 0] -= torch.log(var)
-    for j, (lo, hi) in enumerate(TARGET_RANGE):
-        t[:, j] = t[:, j].clamp(float(np.log(lo)), float(np.log(hi)))
-    return t.to(torch.float32)
+    _, var = vecchia_fields_moments(Y)
+    return vecchia_mlp_targets(theta_hat.contiguous(), var, [r[0] for r in TARGET_RANGE],
+                               [r[1] for r in TARGET_RANGE])
 
 
 def build_training_set(geom: Geometry, nfields: int, seed: int = 1, chunk: int = 4096,
@@ -223,13 +220,9 @@ def load(path: str = None, device="cuda:0"):
 def predict_theta(params, norm, feats, Y):
     """Predicted parameters (nfields, 4) from features, without the fallback rule (a
     diagnostic; vecchia_fields_warm_start forms its own in a kernel)."""
-    import torch
-    pred = vecchia_mlp_forward(params, norm, feats).to(torch.float64)
-    var = Y.var(dim=1, unbiased=False)
-    th = torch.exp(pred)
-    th[:, 0] *= var
-    th[:, 2] = th[:, 2].clamp(0.05, 20.0)
-    return th
+    pred = vecchia_mlp_forward(params, norm, feats)
+    _, var = vecchia_fields_moments(Y)
+    return vecchia_mlp_theta(pred.contiguous(), var)
 
 
 def evaluate(geom: Geometry, params, norm, nfields: int, seed: int = 3, prec: str = "fp64",

@@ -102,3 +102,29 @@ def test_training_fits_a_smooth_function():
                                      loss=loss)
         losses.append(float(loss.item()))
     assert losses[-1] < 0.1 * losses[0]
+
+
+def test_field_moments_targets_and_theta_from_predictions():
+    # the learned start's per-field steps against their definitions in numpy (FP64)
+    rng = np.random.default_rng(11)
+    nf, n = 37, 1001
+    Y = rng.normal(size=(nf, n)) * rng.uniform(0.2, 3.0, (nf, 1)) + rng.normal(size=(nf, 1))
+    Yd = torch.as_tensor(Y, device="cuda:0")
+    mean, var = vg.vecchia_fields_moments(Yd)
+    assert np.allclose(mean.cpu().numpy(), Y.mean(axis=1), rtol=1e-13, atol=1e-14)
+    assert np.allclose(var.cpu().numpy(), Y.var(axis=1), rtol=1e-13)
+    theta = np.column_stack([rng.uniform(0.1, 5, nf), np.exp(rng.uniform(-12, 3, nf)),
+                             rng.uniform(0.06, 19, nf), np.exp(rng.uniform(-16, 3, nf))])
+    lo, hi = [1e-2, 1e-4, 0.05, 1e-6], [1e2, 1e1, 20.0, 1e1]
+    T = vg.vecchia_mlp_targets(torch.as_tensor(theta, device="cuda:0"), var, lo, hi).cpu().numpy()
+    ref = np.log(theta)
+    ref[:, 0] -= np.log(Y.var(axis=1))
+    ref = np.clip(ref, np.log(lo), np.log(hi)).astype(np.float32)
+    assert np.allclose(T, ref, rtol=1e-6, atol=1e-6)
+    pred = rng.normal(size=(nf, 4)).astype(np.float32) * 2
+    pred[:3, 2] = [-4.0, 4.0, 0.0]            # nu below and above the clamp
+    th0 = vg.vecchia_mlp_theta(_f32(pred), var).cpu().numpy()
+    want = np.exp(pred.astype(np.float64))
+    want[:, 0] *= Y.var(axis=1)
+    want[:, 2] = np.clip(want[:, 2], 0.05, 20.0)
+    assert np.allclose(th0, want, rtol=1e-13)
