@@ -28,7 +28,8 @@ def _errors(g, o, n):
     scale = max(np.linalg.norm(o["grad"]), np.sqrt(np.trace(o["info"])))
     return {"loglik": abs(g["loglik"] - o["loglik"]) / max(abs(o["loglik"]), n),
             "grad": np.linalg.norm(g["grad"] - o["grad"]) / scale,
-            "grad_j": float(np.max(np.abs(g["grad"] - o["grad"]) / np.sqrt(np.diag(o["info"])))),
+            "grad_j": float(np.max(np.abs(g["grad"] - o["grad"]) / np.maximum(
+                np.sqrt(np.abs(np.diag(o["info"]))), 1e-8 * np.sqrt(np.trace(o["info"]))))),
             "info": np.linalg.norm(g["info"] - o["info"]) / np.linalg.norm(o["info"]),
             "beta": np.linalg.norm(g["betahat"] - o["betahat"]) / (np.linalg.norm(o["betahat"]) + 1)}
 

@@ -25,7 +25,8 @@ def compare(g, o, tol=TOL):
     i_err = np.linalg.norm(g["info"] - o["info"]) / np.linalg.norm(o["info"])
     b_err = np.linalg.norm(g["betahat"] - o["betahat"]) / (np.linalg.norm(o["betahat"]) + 1)
     # each component on its own scale too, so that a small one cannot hide under the norm
-    gj_err = float(np.max(np.abs(g["grad"] - o["grad"]) / np.sqrt(np.diag(o["info"]))))
+    gj_scale = np.maximum(np.sqrt(np.abs(np.diag(o["info"]))), 1e-8 * np.sqrt(np.trace(o["info"])))
+    gj_err = float(np.max(np.abs(g["grad"] - o["grad"]) / gj_scale))
     errs = dict(loglik=ll_err, grad=g_err, grad_j=gj_err, info=i_err, beta=b_err)
     assert max(errs.values()) <= tol, errs
     return errs
@@ -90,11 +91,12 @@ def test_covariance_pairs_outside_the_domain_give_nan():
     # NaN outputs (finite invalid values only: they end quickly on every code path)
     dev = torch.device("cuda:0")
     la = torch.zeros((4, 2), dtype=torch.float64, device=dev)
-    lb = torch.tensor([[0.1, 0.0], [0.3, 0.2], [0.0, 0.0], [1.0, 1.0]], device=dev)
+    lb = torch.tensor([[0.1, 0.0], [0.3, 0.2], [0.0, 0.0], [1.0, 1.0]], dtype=torch.float64, device=dev)
     same = torch.tensor([0, 0, 1, 0], dtype=torch.int32, device=dev)
     for covfun, th in ((MAT, [1.0, 0.1, -1.0, 0.1]), (MAT, [1.0, 0.1, 25.0, 0.1]),
                        (MAT, [1.0, -0.1, 1.5, 0.1]), (EXP, [1.0, 0.0, 0.1])):
-        C, dC = vg.vecchia_covariance_pairs(covfun, torch.tensor(th, device=dev), la, lb, same)
+        C, dC = vg.vecchia_covariance_pairs(covfun, torch.tensor(th, dtype=torch.float64, device=dev),
+                                            la, lb, same)
         assert torch.isnan(C).all() and torch.isnan(dC).all(), (covfun, th)
 
 
