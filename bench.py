@@ -24,8 +24,10 @@ Reported beside the device-timed value:
   * prediction -- Vecchia prediction at 100000 new sites of the headline field.
   * elevators_like -- the exponential with one range per attribute on an Elevators-like
                   workload (n = 15000, d = 18): passes, fits, the oracle beside them.
-  * grouped    -- grouped conditioning (one Cholesky per group of ~8 observations) against
-                  the plain pass on the same n = 1e5 ordering.
+  * grouped    -- grouped conditioning (one factorisation per group of ~8 observations)
+                  against the plain pass on the same n = 1e5 ordering.
+  * swath      -- the 1.2 M-point space-time swath: FP64 and mixed passes, FP64, mixed-
+                  then-FP64 and mixed-only fits, the oracle on a prefix beside them.
 ``--impl reference`` times the CPU oracle itself as the reference arm.
 Multi-GPU runs (torchrun) are independent replicas: each rank evaluates its own copy.
 """
@@ -601,6 +603,114 @@ def run_grouped(vg, torch, dev, stream) -> dict:
     return res
 
 
+def mixed_fma_split(K: int, p: int, q: int):
+    """The algorithmic FMAs of one observation (algorithmic_fma_per_point) split by the
+    precision the mixed path does them in: FP64 the pivots' diagonal updates (K(K-1)/2) and
+    the per-observation dot products (q(1+p)K + q(q+1)K/2); FP32 the rest."""
+    total = algorithmic_fma_per_point(K, p, q)
+    f64 = K * (K - 1) / 2 + q * (1 + p) * K + q * (q + 1) * K / 2
+    return total - f64, f64
+
+
+def run_swath(vg, torch, dev, stream, steps: int, warmup: int, flush) -> dict:
+    """The satellite-like space-time swath (stands in for the paper's Jason-3 + time data,
+    Table 2): n = 1 200 000 points in (lon, lat, time), 16 time slices x 8 swath bands x
+    9375, space-time exponential (sigma2 1, spatial range 5 degrees, temporal range 2
+    slices, tau2 0.1), X = [1, lat], y from the sequential Vecchia draw with m = 40, m = 30.
+    The FP64 and the mixed pass at the generating parameters (inputs 207 MB, larger than
+    L2), Fisher-scoring fits from the stated start in FP64, mixed-then-FP64 and mixed only,
+    and the FP64 oracle on a prefix of the observations beside them (throughput and the
+    FP64 pass's error on the same prefix)."""
+    import oracle
+    import workloads
+    t_gen = time.perf_counter()
+    w = workloads.cfg_swath_1m2()
+    t_gen = time.perf_counter() - t_gen
+    t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)  # noqa
+    locs, y, X, NN = (t(w.locs, torch.float64), t(w.y, torch.float64), t(w.X, torch.float64),
+                      t(w.NN, torch.int32))
+    th = t(w.theta_true, torch.float64)
+    q, K = 4, w.m + 1
+    res = {"workload": "space-time swath n=%d (16 slices x 8 bands x 9375), exponential "
+                       "space-time (1, 5, 2, 0.1), X=[1, lat], m=%d, sequential draw m=40"
+                       % (w.n, w.m), "n": w.n, "m": w.m, "p": w.p, "generation_s": t_gen}
+    outs = {}
+    for prec in ("fp64", "mixed"):
+        h = vg.Handle(0)
+        h.set_timing(True)
+        tune = vg.vecchia_autotune(locs, y, X, NN, th, w.covfun, prec=prec, stream=stream, handle=h)
+        out = torch.empty(1 + q + q * q + w.p, dtype=torch.float64, device=dev)
+        st = torch.empty(2, dtype=torch.int64, device=dev)
+        for _ in range(warmup):
+            vg.vecchia_loglik_grad_info(locs, y, X, NN, th, w.covfun, prec=prec, stream=stream,
+                                        out=out, status=st, handle=h)
+        torch.cuda.synchronize()
+        ms, kms = [], []
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            vg.vecchia_loglik_grad_info(locs, y, X, NN, th, w.covfun, prec=prec, stream=stream,
+                                        out=out, status=st, handle=h)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            kms.append(h.last_timing()["pass"])
+        h.close()
+        if int(st[0].item()) != 0:
+            raise RuntimeError("swath %s pass failed: %s" % (prec, st.cpu().numpy()))
+        outs[prec] = vg.unpack(out, q, w.p)
+        step_ms = statistics.median(ms)
+        kern = statistics.median(kms)
+        flop = 2 * algorithmic_fma_per_point(K, w.p, q) * w.n
+        res[prec] = {"value": w.n / (step_ms * 1e-3), "unit": UNIT, "ms_per_step": step_ms,
+                     "kernel_ms": kern, "mapping": {"lanes": tune["lanes"], "threads": tune["threads"]},
+                     "algorithmic_gflops": flop / (kern * 1e-3) / 1e9}
+    r64, rmx = outs["fp64"], outs["mixed"]
+    gs = max(float(np.linalg.norm(r64["grad"])), float(np.sqrt(np.trace(r64["info"]))))
+    res["mixed"]["vs_fp64_pass"] = {
+        "loglik_rel": abs(rmx["loglik"] - r64["loglik"]) / abs(r64["loglik"]),
+        "grad_rel": float(np.linalg.norm(rmx["grad"] - r64["grad"])) / gs,
+        "info_rel": float(np.linalg.norm(rmx["info"] - r64["info"]) / np.linalg.norm(r64["info"]))}
+    # fits from the stated start; the first FP64 call also builds the iteration graph
+    fits = {}
+    h = vg.Handle(0)
+    for name, prec in (("fp64_first_call", "fp64"), ("fp64", "fp64"), ("mixed_then_fp64", "mixed"),
+                       ("mixed_only", "mixed_only")):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        f = vg.vecchia_fit(locs, y, X, NN, w.covfun, w.theta_start, tol=1e-4, prec=prec,
+                           stream=stream, handle=h)
+        fits[name] = {"seconds": time.perf_counter() - t0, "iters": f["iters"],
+                      "passes": f["evals"], "status": f["status"], "loglik": f["loglik"],
+                      "theta": [float(v) for v in f["theta"]]}
+    h.close()
+    ref = np.array(fits["fp64"]["theta"])
+    for name in ("mixed_then_fp64", "mixed_only"):
+        fits[name]["theta_rel_err_vs_fp64_fit"] = [float(v) for v in
+                                                   np.abs(np.array(fits[name]["theta"]) - ref) / ref]
+        fits[name]["loglik_rel_to_fp64_fit"] = abs(fits[name]["loglik"] - fits["fp64"]["loglik"]) / \
+            abs(fits["fp64"]["loglik"])
+    res["fit"] = dict(fits, tol=1e-4, start=[float(v) for v in w.theta_start],
+                      paper_a40_s={"m10": 10.279, "m30": 23.888,
+                                   "note": "Jason-3 + time, n = 960k, Table 2 (context)"})
+    # the FP64 oracle on a prefix: its rate on the host cores and the FP64 pass's error there
+    rate, ns, dt, cores = cpu_oracle_rate(w, target_s=8.0)
+    o = oracle.loglik_grad_info(w.locs[:ns], w.y[:ns], w.X[:ns], w.NN[:ns], w.theta_true, w.covfun)
+    out, st = vg.vecchia_loglik_grad_info(locs[:ns], y[:ns], X[:ns], NN[:ns], th, w.covfun,
+                                          stream=stream)
+    g = vg.unpack(out, q, w.p)
+    sc = max(float(np.linalg.norm(o["grad"])), float(np.sqrt(np.trace(o["info"]))))
+    res["cpu_oracle"] = {"points_per_s": rate, "cores": cores, "kind": "oracle",
+                         "sample": "first %d observations, %.1f s" % (ns, dt),
+                         "fp64_pass_rel_err_on_sample": {
+                             "loglik": abs(g["loglik"] - o["loglik"]) / abs(o["loglik"]),
+                             "grad": float(np.linalg.norm(g["grad"] - o["grad"])) / sc,
+                             "info": float(np.linalg.norm(g["info"] - o["info"]) / np.linalg.norm(o["info"]))}}
+    return res
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -755,6 +865,14 @@ def run_ours(args):
         mfit = vg.vecchia_fit(locs, y, X, NN, w.covfun, w.theta_start, tol=1e-4, prec="mixed",
                               stream=stream, handle=hm)
         mfit_times.append(time.perf_counter() - t0)
+    # a fit that stays in mixed precision to the end: its optimum against the FP64 fit's
+    ofit_times, ofit = [], None
+    for _ in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ofit = vg.vecchia_fit(locs, y, X, NN, w.covfun, w.theta_start, tol=1e-4,
+                              prec="mixed_only", stream=stream, handle=hm)
+        ofit_times.append(time.perf_counter() - t0)
 
     batched = run_batched(vg, torch, dev, stream, args.steps, args.warmup, flush, local)
     warm = run_warm_start(torch, dev, local)
@@ -762,6 +880,7 @@ def run_ours(args):
     pred = run_prediction(vg, torch, dev, stream, w)
     elev = run_elevators(vg, torch, dev, stream)
     grouped = run_grouped(vg, torch, dev, stream)
+    swath = run_swath(vg, torch, dev, stream, max(3, args.steps // 2), args.warmup, flush)
 
     if rank != 0:
         if ws > 1:
@@ -779,6 +898,11 @@ def run_ours(args):
     cpu_rate, cpu_n, cpu_s, cpu_cores = cpu_oracle_rate(w)
     cpu1_rate, cpu1_n, cpu1_s, _ = cpu_oracle_rate(w, target_s=6.0, nthreads=1)
     peaks = vg.vecchia_measure_peaks(h)
+    f32_pt, f64_pt = mixed_fma_split(K, w.p, q)
+    mk_ms = statistics.mean(mixed_pass_ms)
+    m_ach32 = 2 * f32_pt * w.n / (mk_ms * 1e-3) / 1e9
+    m_ach64 = 2 * f64_pt * w.n / (mk_ms * 1e-3) / 1e9
+    th_f64 = np.array(fit["theta"])
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -828,6 +952,25 @@ def run_ours(args):
                       "grad_rel": float(np.linalg.norm(mixed_res["grad"] - res["grad"])) / gscale,
                       "info_rel": float(np.linalg.norm(mixed_res["info"] - res["info"])
                                         / np.linalg.norm(res["info"]))},
+                  "roofline": {"bound": "alu", "unit": "GFLOP/s", "kernel_ms": mk_ms,
+                               "fp32": {"achieved": m_ach32, "peak": peaks["fp32_gflops"],
+                                        "frac": m_ach32 / peaks["fp32_gflops"],
+                                        "flop_per_point": 2 * f32_pt},
+                               "fp64": {"achieved": m_ach64, "peak": FP64_PEAK_GFLOPS,
+                                        "frac": m_ach64 / FP64_PEAK_GFLOPS,
+                                        "flop_per_point": 2 * f64_pt},
+                               "note": "algorithmic FMAs split by the precision the mixed "
+                                       "path does them in (FP64: pivot diagonal updates and "
+                                       "per-observation dot products); FP32 peak measured "
+                                       "by the FMA-chain microbenchmark"},
+                  "fit_mixed_only": {"precision": "mixed throughout", "tol": 1e-4,
+                                     "seconds_first_call": ofit_times[0], "seconds": ofit_times[1],
+                                     "iters": ofit["iters"], "passes": ofit["evals"],
+                                     "status": ofit["status"], "loglik": ofit["loglik"],
+                                     "loglik_rel_to_f64_fit": abs(ofit["loglik"] - fit["loglik"]) / abs(fit["loglik"]),
+                                     "theta": [float(v) for v in ofit["theta"]],
+                                     "theta_rel_err_vs_f64_fit": [float(v) for v in
+                                                                  np.abs(np.array(ofit["theta"]) - th_f64) / th_f64]},
                   "fit": {"precision": "mixed then f64 polish", "tol": 1e-4,
                           "seconds_first_call": mfit_times[0], "seconds": mfit_times[1],
                           "iters": mfit["iters"], "passes": mfit["evals"],
@@ -840,6 +983,7 @@ def run_ours(args):
         "prediction": pred,
         "elevators_like": elev,
         "grouped": grouped,
+        "swath": swath,
     }
     print(json.dumps(line))
     if ws > 1:

@@ -231,8 +231,11 @@ typedef struct {
                            0: one host round trip per iteration                             */
     int prec;           /* VEC_FP64 (default): FP64 passes throughout.  VEC_MIXED: mixed-
                            precision passes until convergence, then FP64 passes from that
-                           point until convergence again (the results are FP64 results)    */
+                           point until convergence again (the results are FP64 results).
+                           VEC_FIT_MIXED_ONLY: mixed-precision passes throughout (the
+                           optimum, loglik, gradient and information are the mixed path's) */
 } vec_fit_opts;
+#define VEC_FIT_MIXED_ONLY 2
 
 /* Outcome of vecchia_fit. */
 typedef struct {

@@ -38,6 +38,7 @@ NPARMS = {EXP_ISO: 3, MATERN_ISO: 4, EXP_SPACETIME: 4}   # EXP_ANISO: d + 2, see
 STATUS = {0: "VEC_OK", 1: "VEC_ERR_ARG", 2: "VEC_ERR_NOT_PD", 3: "VEC_ERR_NONFINITE",
           4: "VEC_ERR_NOMEM", 5: "VEC_ERR_CUDA", 6: "VEC_ERR_TIMEOUT", 7: "VEC_ERR_UNSUPPORTED"}
 _PREC = {"fp64": FP64, "mixed": MIXED, FP64: FP64, MIXED: MIXED}
+FIT_MIXED_ONLY = 2   # vecchia_fit only: mixed-precision passes throughout
 
 
 class FitOpts(ctypes.Structure):
@@ -798,7 +799,9 @@ def vecchia_fit(locs, y, X, NNarray, covfun: int, start, tol: float = 1e-4, maxi
                 handle: Handle | None = None) -> dict:
     """Fisher scoring on the device (see vecchia_fit in include/vecchia.h).  Data tensors
     are CUDA tensors as for vecchia_loglik_grad_info; start is a host sequence of q values.
-    Returns theta, betahat, loglik, grad, info (numpy) and status / iters / evals."""
+    prec: "fp64", "mixed" (mixed phase, then an FP64 phase) or "mixed_only" (mixed passes
+    throughout).  Returns theta, betahat, loglik, grad, info (numpy) and status / iters /
+    evals."""
     import torch
     for t, dt, nm in ((locs, torch.float64, "locs"), (y, torch.float64, "y"),
                       (X, torch.float64, "X"), (NNarray, torch.int32, "NNarray")):
@@ -813,7 +816,8 @@ def vecchia_fit(locs, y, X, NNarray, covfun: int, start, tol: float = 1e-4, maxi
     if stream is None:
         stream = torch.cuda.current_stream(dev)
     st = np.ascontiguousarray(start, dtype=np.float64)
-    opts = FitOpts(tol, maxit, max_halvings, 1 if use_graph else 0, _PREC[prec])
+    opts = FitOpts(tol, maxit, max_halvings, 1 if use_graph else 0,
+                   FIT_MIXED_ONLY if prec == "mixed_only" else _PREC[prec])
     info_ = FitInfo()
     theta = np.empty(q)
     beta = np.empty(p)

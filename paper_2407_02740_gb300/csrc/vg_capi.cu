@@ -477,7 +477,10 @@ vec_status vecchia_fit(vec_handle h, const double* locs, const double* y, const 
     if (!h) return fail(VEC_ERR_ARG, "vecchia_fit: NULL handle");
     vec_fit_opts o = {1e-4, 40, 10, 1, (int)VEC_FP64};
     if (opts) o = *opts;
-    vec_status s = check_args(locs, y, X, NNarray, n, d, p, m, start, covfun, (vec_precision)o.prec);
+    // VEC_FIT_MIXED_ONLY (fit option only): every pass in mixed precision, no FP64 phase
+    const bool mixed_only = (o.prec == VEC_FIT_MIXED_ONLY);
+    vec_status s = check_args(locs, y, X, NNarray, n, d, p, m, start, covfun,
+                              mixed_only ? VEC_MIXED : (vec_precision)o.prec);
     if (s != VEC_OK) return s;
     if (!theta_out || !betahat || !loglik || !grad || !info)
         return fail(VEC_ERR_ARG, "vecchia_fit: an output pointer is NULL");
@@ -513,7 +516,7 @@ vec_status vecchia_fit(vec_handle h, const double* locs, const double* y, const 
     const int nphase = (o.prec == (int)VEC_MIXED) ? 2 : 1;
     int total_iters = 0, total_evals = 0;
     for (int phase = 0; phase < nphase; ++phase) {
-        const int prec = (nphase == 2 && phase == 0) ? 1 : 0;
+        const int prec = (mixed_only || (nphase == 2 && phase == 0)) ? 1 : 0;
         const double* phase_start = (phase == 0) ? h->fit_start : h->fs->theta_cur;
         vg::PassPlan pplan;
         s = prepare_pass(h, cov, m, d, p, &pplan, n, prec);
@@ -1083,7 +1086,7 @@ static vec_status batch_fit_impl(vec_handle h, int nbatch,
     const int saved_timing = h->timing;
     h->timing = 0;
     for (int phase = 0; phase < nphase; ++phase) {
-        const int prec = (nphase == 2 && phase == 0) ? 1 : 0;
+        const int prec = (mixed_only || (nphase == 2 && phase == 0)) ? 1 : 0;
         BatchPlan B;
         s = prep(prec, &B);
         if (s != VEC_OK) break;

@@ -108,6 +108,25 @@ __device__ __forceinline__ double rsqrt_newton(double v) {
     return fma(y * r, fma(r, 0.375, 0.5), y);
 }
 
+// 1/v, v > 0, for the LDL^T pivots.  The FP32 seed is the approximate FP32 reciprocal of
+// v's mantissa truncated to 23 bits (built from the bits, like the conversions, so no
+// FP64 <-> FP32 conversion instruction is issued); its relative error is e < 2^-21.  One
+// third-order step
+//   e = 1 - v y,  y <- y (1 + e + e^2)
+// (the series of 1 / (1 - e) to second order) leaves e^3 < 2^-63 relative: FP64 accuracy
+// in three FP64 operations.  v outside [2^-125, 2^126) takes an FP64 division.
+__device__ __forceinline__ double rcp_newton(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int ex = (int)((b >> 52) & 0x7ffull) - 1023;
+    if (ex < -125 || ex > 125) return 1.0 / v;
+    const float vf = __uint_as_float(((unsigned)(ex + 127) << 23) | (unsigned)((b >> 29) & 0x7fffffull));
+    float rf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(vf));
+    const double y = f32_to_f64_bits(rf);
+    const double e = fma(-v, y, 1.0);
+    return fma(y, fma(e, e, e), y);
+}
+
 // digamma(x), x > 0: shift upward with psi(x) = psi(x+1) - 1/x until x >= 12, then the
 // asymptotic expansion psi(z) = ln z - 1/(2z) - sum_k B_2k / (2k z^2k).  Outside the
 // domain (x <= 0, NaN or infinite) the result is NaN; the shift loop then never starts,

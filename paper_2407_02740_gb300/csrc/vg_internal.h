@@ -32,7 +32,7 @@ int plan_pass(int cov, int m, int d, int p, int nsm, int force_L, int force_thre
               PassPlan* plan, int prec = 0, bool batched = false, int force_tab = -1,
               bool grouped = false);
 size_t pass_smem_bytes(int cov, int m, int d, int p, int L, int threads, bool tab_smem,
-                       int prec = 0);
+                       int prec = 0, bool grouped = false);
 const void* pass_kernel_f64(int cov, int L);
 const void* pass_kernel_f32(int cov, int L);
 const void* pass_batch_kernel_f64(int cov, int L);

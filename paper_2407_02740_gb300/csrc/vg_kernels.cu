@@ -78,14 +78,14 @@ __global__ void __launch_bounds__(MT_NC * 32) k_mtab_build(const double* __restr
         const int f = t / MT_NC, k = t % MT_NC;
         double mono = 0.0;
         for (int deg = k; deg < MT_NC; ++deg) mono = fma(cheb[f][deg], c_cheb.c[deg][k], mono);
-        // u = w / hw: the coefficient of w^k is mono / hw^k (an exact power-of-two scaling);
-        // w^0, w^1 in FP64, w^2..w^7 as (hi, lo) FP32 pairs, w^8..w^12 in FP32 (see
-        // horner_split)
+        // u = w / hw: the coefficient of w^k is mono / hw^k (an exact power-of-two scaling).
+        // F0: w^0, w^1 in FP64, w^2..w^7 as (hi, lo) FP32 pairs, w^8..w^12 in FP32 (see
+        // horner_split); F1, F2: w^0..w^7 as pairs, w^8..w^12 in FP32 (see horner_df)
         const double fsc = (f == 1) ? covparms[0] / covparms[1] : covparms[0];
         const double v = mono * fsc * ldexp(1.0, k * (MT_LOGJ + 1));
         double* out = tab + (size_t)it * MT_PER_INT + f * MT_FSTRIDE;
         float* tail = reinterpret_cast<float*>(out + MT_NHEAD);
-        if (k < 2) {
+        if (k < 2 && f == 0) {
             out[k] = v;
         } else if (k < MT_NHEAD) {
             const float hi = (float)v;
@@ -377,13 +377,13 @@ static const void* pass_kernel(int cov, int L, int prec, bool batched = false, b
 }
 
 size_t pass_smem_bytes(int cov, int m, int d, int p, int L, int threads, bool tab_smem,
-                       int prec) {
+                       int prec, bool grouped) {
     const int Q = npair_derivs(cov, d) + 1;
     RecLayout RL;
     RL.init(p, Q);
     const int nv = nv_of(p, Q);
     SlotLayout SL;
-    SL.init(m, d, p, cov, nv, prec == 0 ? 8 : 4);
+    SL.init(m, d, p, cov, nv, prec == 0 ? 8 : 4, grouped);
     const int ngrp = threads / L;
     const int acc_per_lane = (RL.nstat + L - 1) / L;
     const size_t tab_words = tab_smem ? (prec == 0 ? MT_DOUBLES : (MT_FLOATS + 1) / 2) : 0;
@@ -414,10 +414,10 @@ int plan_pass(int cov, int m, int d, int p, int nsm, int force_L, int force_thre
             // Matern table in shared memory when it fits (or as forced: force_tab 1 = shared
             // memory only, 0 = global memory, read through L1)
             bool t = (cov == COV_MATERN) && force_tab != 0;
-            size_t b = pass_smem_bytes(cov, m, d, p, L, thr, t, prec);
+            size_t b = pass_smem_bytes(cov, m, d, p, L, thr, t, prec, grouped);
             if (b > budget && t && force_tab < 0) {
                 t = false;
-                b = pass_smem_bytes(cov, m, d, p, L, thr, t, prec);
+                b = pass_smem_bytes(cov, m, d, p, L, thr, t, prec, grouped);
             }
             if (b <= budget) { chosen = L; tab = t; threads = thr; break; }
         }
@@ -432,11 +432,11 @@ int plan_pass(int cov, int m, int d, int p, int nsm, int force_L, int force_thre
     plan->nstat = RL.nstat;
     plan->nv = nv_of(p, Q);
     SlotLayout SL;
-    SL.init(m, d, p, cov, plan->nv, prec == 0 ? 8 : 4);
+    SL.init(m, d, p, cov, plan->nv, prec == 0 ? 8 : 4, grouped);
     plan->slot_stride = SL.bytes;
     plan->prec = prec;
     plan->acc_per_lane = (RL.nstat + chosen - 1) / chosen;
-    plan->smem = pass_smem_bytes(cov, m, d, p, chosen, threads, tab, prec);
+    plan->smem = pass_smem_bytes(cov, m, d, p, chosen, threads, tab, prec, grouped);
     plan->batched = batched ? 1 : 0;
     plan->grouped = grouped ? 1 : 0;
     const void* fn = pass_kernel(cov, chosen, prec, batched, grouped);

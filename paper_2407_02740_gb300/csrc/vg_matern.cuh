@@ -164,6 +164,54 @@ __device__ __forceinline__ double horner_split(const double* c, double w, float 
     return fma(p, w, c[0]);
 }
 
+// Locates s in the table like mtab_locate, but returns the local variable only as the
+// FP32 pair (wf, wl): integer and FP32 work, no FP64 instruction.
+__device__ __forceinline__ int mtab_locate_pair(double s, float& wf, float& wl) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(s);
+    const int e = (int)((bits >> 52) & 0x7ffull) - 1023;
+    if (e < MT_E0) return -1;
+    if (e >= MT_E1) return -2;
+    const unsigned long long j = (bits >> (52 - MT_LOGJ)) & (unsigned long long)(MT_J - 1);
+    const float mantf = __uint_as_float(0x3f800000u | (unsigned)((bits >> 29) & 0x7fffffull));
+    const float cenf = __uint_as_float(0x3f800000u | (unsigned)((2ull * j + 1ull) << (23 - MT_LOGJ - 1)));
+    wf = mantf - cenf;
+    wl = __uint2float_rn((unsigned)(bits & 0x1fffffffull)) * 0x1p-52f;
+    return (e - MT_E0) * MT_J + (int)j;
+}
+
+// Degree-12 polynomial entirely in double-float FP32 arithmetic (the derivative tables'
+// layout: c0..c7 as (hi, lo) FP32 pairs, c8..c12 in FP32); the result is the pair's sum in
+// FP64, one FP64 addition.  Relative accuracy about 2^-46: enough for the derivative
+// matrices, which enter the gradient and information linearly (an error of 2^-44 relative
+// in every derivative entry moves the gradient by ~1e-11 of its scale even at a nugget of
+// 0.001), whereas the covariance itself is amplified by the block's conditioning and keeps
+// its FP64 head (horner_split).
+__device__ __forceinline__ double horner_df(const double* c, float wh, float wl) {
+    const float* t = reinterpret_cast<const float*>(c + MT_NHEAD);
+    float ph = t[4];
+    ph = fmaf(ph, wh, t[3]);
+    ph = fmaf(ph, wh, t[2]);
+    ph = fmaf(ph, wh, t[1]);
+    ph = fmaf(ph, wh, t[0]);
+    float pl = 0.0f;
+    const float2* mid = reinterpret_cast<const float2*>(c);
+#pragma unroll
+    for (int k = MT_NHEAD - 1; k >= 0; --k) {      // c7 .. c0
+        const float2 ck = mid[k];
+        const float hi = __fmul_rn(ph, wh);
+        float lo = fmaf(ph, wh, -hi);               // exact remainder of ph wh
+        lo = fmaf(ph, wl, lo);
+        lo = fmaf(pl, wh, lo);
+        const float sm = __fadd_rn(hi, ck.x);
+        const float z = __fsub_rn(sm, hi);
+        float er = __fadd_rn(__fsub_rn(hi, __fsub_rn(sm, z)), __fsub_rn(ck.x, z));
+        er = __fadd_rn(er, __fadd_rn(lo, ck.y));
+        ph = __fadd_rn(sm, er);
+        pl = __fsub_rn(er, __fsub_rn(ph, sm));
+    }
+    return f32_to_f64_bits(ph) + f32_to_f64_bits(pl);
+}
+
 // The table holds the covariance and its derivatives, not M itself: F0 = sigma2 M,
 // F1 = sigma2 dM/drho = sigma2 (rho dM/drho) / rho, F2 = sigma2 dM/dnu (the builder folds
 // the scales in).  Below the table the expansion's values are scaled here (sc0 = sigma2,
@@ -182,13 +230,12 @@ __device__ __forceinline__ double matern_F0(const double* tab, double s, double 
 }
 __device__ __forceinline__ void matern_F12(const double* tab, double s, double nu, double psi,
                                            double sc1, double sc2, double& F1, double& F2) {
-    double w;
     float wf, wl;
-    int it = mtab_locate(s, w, wf, wl);
+    int it = mtab_locate_pair(s, wf, wl);
     if (it >= 0) {
         const double* cf = tab + it * MT_PER_INT;
-        F1 = horner_split(cf + MT_FSTRIDE, w, wf, wl);
-        F2 = horner_split(cf + 2 * MT_FSTRIDE, w, wf, wl);
+        F1 = horner_df(cf + MT_FSTRIDE, wf, wl);
+        F2 = horner_df(cf + 2 * MT_FSTRIDE, wf, wl);
     } else if (it == -2 || !(s > 0.0)) {
         F1 = 0.0;
         F2 = 0.0;

@@ -9,43 +9,51 @@
 //               coordinates relative to the observation and divided by their range,
 //               y and X rows                                        (Algorithm 1: the
 //               substitution of the neighbours, covariance, factor, solves, sums)
-//   assembly    lower triangle of the covariance, nugget on the diagonal
-//   factor      left-looking Cholesky; y and X ride along as extra rows, so the same
-//               column sweep produces Liy = L^-1 y and LiX = L^-1 X
-//   terms       logdet_i, Liy[last], LiX[last, :]
-//   derivative  b = last row of L^-1 (back substitution), g_j = dSigma_j b^T with each
-//               pair (a, c) evaluated once (a conflict-free round-robin pair schedule lets
-//               the lanes scatter into g without atomics), m_j = L^-1 g_j, then the dot
+//   assembly    strict lower triangle of the covariance, FP64 diagonal sigma2 (1 + tau2)
+//   factor      right-looking LDL^T (Sigma = U D U^T, U unit lower); y and X ride along as
+//               extra rows of a bordered matrix, so the same sweep produces
+//               z = D^-1 U^-1 (y, X); every update of a step is one item and the items
+//               are spread evenly over the lanes.  The Cholesky factor of Algorithm 1 is
+//               L = U D^1/2: L^-1 y = D^1/2 z, log det = sum log d_c, and its last row of
+//               the inverse is b = d_K^-1/2 u with u the last row of U^-1
+//   terms       logdet_i = log d_K, ell = d_K^1/2 z_y[K], x = d_K^1/2 z_X[K]
+//   derivative  u (back substitution, no divisions), h_j = dSigma_j u^T with each pair
+//               (a, c) evaluated once (a conflict-free round-robin pair schedule lets the
+//               lanes scatter into h without atomics), f_j = U^-1 h_j, then the dot
 //               products that give dlogdet, dySy, dySX, dXSX and the information (the
 //               derivative terms Algorithm 1 leaves out, written out from
-//               dL = L Phi(L^-1 dSigma L^-T))
+//               dL = L Phi(L^-1 dSigma L^-T) and rescaled from L to U and D)
 //   accumulate  per-observation values into per-lane FP64 running sums (shared memory),
 //               then a fixed-order block reduction into one partial record per block.
 //
-// The steps are device functions (assemble_block, chol_augmented, conditional_terms, ...)
-// shared by three bodies: vecchia_point (one observation), vecchia_group (grouped
-// conditioning: one Cholesky per group, then conditional_terms for each member on the
-// leading block ending at its row) and vecchia_point_aniso (one range per coordinate: the
-// d + 1 derivative vectors live in the slot and their work is split into lane items).
+// The steps are device functions (assemble_block, ldl_augmented, conditional_terms,
+// finish_terms, ...) shared by three bodies: vecchia_point (one observation),
+// vecchia_group (grouped conditioning: one factorisation per group, then
+// conditional_terms for each member on the leading block ending at its row) and
+// vecchia_point_aniso (one range per coordinate: the d + 1 derivative vectors live in the
+// slot and their work is split into lane items).
 //
 // T is the working type of the block.  T = double is the FP64 path.  T = float is the
-// mixed path: the block, the covariance entries, the factorisation, the solves and the
-// derivative work are FP32; the coordinate differences (taken in FP64 relative to the
-// observation before rounding), the per-observation values, every sum over observations,
-// the profile step and the Fisher step stay FP64.
+// mixed path: the covariance entries, the trailing updates of the factorisation, the
+// solves and the derivative vectors are FP32; the pivots (the diagonal of the
+// factorisation, accumulated in FP64 from the exact products of FP32 values), the
+// per-observation dot products and values, every sum over observations, the profile step
+// and the Fisher step are FP64.
 //
 // FP64 on this GPU issues one warp instruction per 64 cycles per SM sub-partition whatever
-// the number of active lanes, so the mapping keeps all 32 lanes busy: rows, pairs and
-// vector entries are spread round-robin over the L lanes of a group, and each FP64 pivot
-// costs an FP32 seed and one third-order FP64 correction (rsqrt_newton) instead of a
-// square root and a division.
+// the number of active lanes, so the mapping keeps all lanes busy: updates, pairs and dot
+// products are items spread evenly over the L lanes of a group, the pivots are FP64
+// reciprocals from an FP32 seed and one third-order correction (rcp_newton, three FP64
+// operations), and the derivative solves need no divisions.
 #pragma once
 #include "vg_common.cuh"
 #include "vg_matern.cuh"
 
 namespace vg {
 
-// Per-type arithmetic used by the pass.
+// Per-type arithmetic used by the pass.  to64 widens a block value to FP64 (exactly; from
+// the bits for FP32, so that no conversion instruction is issued), fromd narrows an FP64
+// value to the working type (round to nearest, from the bits for FP32).
 template <typename T>
 struct Num;
 template <>
@@ -53,20 +61,24 @@ struct Num<double> {
     static __device__ __forceinline__ double fma_(double a, double b, double c) { return fma(a, b, c); }
     static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
     static __device__ __forceinline__ double exp_(double x) { return exp(x); }
-    static __device__ __forceinline__ double rsqrt_pivot(double v) { return rsqrt_newton(v); }
-    static __device__ __forceinline__ bool finite_(double x) { return isfinite(x); }
+    static __device__ __forceinline__ double to64(double x) { return x; }
+    static __device__ __forceinline__ double fromd(double x) { return x; }
 };
 template <>
 struct Num<float> {
     static __device__ __forceinline__ float fma_(float a, float b, float c) { return fmaf(a, b, c); }
     static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
     static __device__ __forceinline__ float exp_(float x) { return expf(x); }
-    // FP32 seed and one FP32 Newton step
-    static __device__ __forceinline__ float rsqrt_pivot(float v) {
-        float y = rsqrtf(v);
-        return y * fmaf(-0.5f * v * y, y, 1.5f);
+    static __device__ __forceinline__ double to64(float x) { return f32_to_f64_bits(x); }
+    static __device__ __forceinline__ float fromd(double x) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+        const int ex = (int)((b >> 52) & 0x7ffull) - 1023;
+        if (ex < -126 || ex > 127) return (float)x;
+        unsigned u = ((unsigned)(b >> 32) & 0x80000000u) | ((unsigned)(ex + 127) << 23) |
+                     (unsigned)((b >> 29) & 0x7fffffull);
+        u += (unsigned)((b >> 28) & 1ull);       // round half up; a carry moves the exponent
+        return __uint_as_float(u);
     }
-    static __device__ __forceinline__ bool finite_(float x) { return isfinite(x); }
 };
 
 // Matern lookups in the working type: FP64 table (split Horner) or FP32 table.
@@ -97,24 +109,43 @@ struct MaternT<float> {
     }
 };
 
-// Layout of one slot: the T arrays first (offsets in T elements), then the FP64 value
-// vector V.  K = m + 1.
+// Layout of one slot.  Working-type arrays first (offsets in T elements), then FP64 arrays
+// (offsets in doubles from Dbyte).  K = m + 1, Q = derivative vectors.
+//   A     packed lower triangle (row r at r (r + 1) / 2; the diagonal lives in dg); after
+//         the derivative solves the same bytes hold Gs (Q x K FP64), except in the grouped
+//         kernels, whose factor serves every member of the group: there Gs has its own
+//         region after V
+//   Y     (1 + p) x K augmented rows: y and the columns of X, then z = D^-1 U^-1 (y, X)
+//   loc   d x K coordinates relative to the observation, divided by their ranges
+//   u     K: the unscaled pivot column during the factorisation, then u = last row of U^-1
+//   G     Q x K: h_j = dSigma_j u^T, then f_j = U^-1 h_j
+//   D1    exponential families (all but the Matern): per-pair weights reused by the
+//         derivative step
+//   dg    K FP64: diagonal of the factorisation, then the pivots d_c
+//   dinv  K FP64: 1 / d_c
+//   V     nv FP64: the per-observation values
 struct SlotLayout {
-    int K, A, Y, inv, loc, bacc, b, G, D1, nT, Vbyte, bytes;
-    __host__ __device__ void init(int m, int d, int p, int cov, int nv, int tsize) {
+    int K, A, Y, loc, u, G, D1, nT, Dbyte, dg, dinv, V, Gs, bytes;
+    __host__ __device__ void init(int m, int d, int p, int cov, int nv, int tsize,
+                                  bool grouped = false) {
         K = m + 1;
-        int Q = npair_derivs(cov, d) + 1;
+        const int Q = npair_derivs(cov, d) + 1;
+        int asz = K * (K + 1) / 2;
+        const int gs = (Q * K * 8 + tsize - 1) / tsize;
+        if (!grouped && gs > asz) asz = gs;
         A = 0;
-        Y = A + K * (K + 1) / 2;
-        inv = Y + (1 + p) * K;
-        loc = inv + K;
-        bacc = loc + d * K;
-        b = bacc + K;
-        G = b + K;
+        Y = A + asz;
+        loc = Y + (1 + p) * K;
+        u = loc + d * K;
+        G = u + K;
         D1 = G + Q * K;
         nT = D1 + (cov == COV_MATERN ? 0 : K * (K - 1) / 2);
-        Vbyte = ((nT * tsize + 7) / 8) * 8;
-        bytes = Vbyte + nv * 8;
+        Dbyte = ((nT * tsize + 7) / 8) * 8;
+        dg = 0;
+        dinv = K;
+        V = 2 * K;
+        Gs = grouped ? 2 * K + nv : -1;        // -1: over A
+        bytes = Dbyte + (2 * K + nv + (grouped ? Q * K : 0)) * 8;
         bytes = ((bytes / 8) | 1) * 8;  // odd number of 8-byte words: slots spread over banks
     }
 };
@@ -158,8 +189,8 @@ struct PassEnv {
     int gl;
     unsigned gmask;
     // slot (shared memory)
-    T *A, *Yg, *invd, *loc, *bacc, *bv, *G, *D1;
-    double* V;
+    T *A, *Yg, *loc, *u, *G, *D1;
+    double *Gs, *dg, *dinv, *V;
     int* idx;
     int Kmax;             // slot stride: largest block size of the launch
     // dataset
@@ -171,8 +202,8 @@ struct PassEnv {
     int* status;
     long long* bad;
     // theta-derived
-    double nu, m_psi, sig2, inv_r1, inv_r2;
-    T sig2T, diagC, inv_r1T, inv_r2T;
+    double nu, m_psi, sig2, inv_r1, inv_r2, diag64;
+    T sig2T, inv_r1T, inv_r2T;
     const double* inv_rk;  // COV_ANISO: 1 / rho_k, k < d (shared memory)
     const T* inv_rkT;
     const Tab* tab;
@@ -180,8 +211,8 @@ struct PassEnv {
     const uint64_t* sidx;
     double* acc;
     int nstat, vb0, vstep, vmm;
-    // factor mode: when set, the body stops after b and writes it here (row i at
-    // factor + i (m+1), in NNarray order: entry 0 for the observation, entry c for
+    // factor mode: when set, the body stops after b = last row of L^-1 and writes it here
+    // (row i at factor + i (m+1), in NNarray order: entry 0 for the observation, entry c for
     // neighbour NNarray[i][c], 0 for padding)
     double* factor;
     // grouped conditioning (see PassArgs)
@@ -224,54 +255,91 @@ __device__ inline void build_record_index(uint64_t* sidx, int p, int Q, int vb0,
             sidx[t++] = rec_pack(mm++, 0, vb0 + j * vstep, vb0 + l * vstep + 2 + p);  // info
 }
 
-// Left-looking Cholesky of the packed block A (Kp x Kp) with the rows of Yg (R - Kp
-// augmented rows, stride Kmax) riding along, so the same sweep leaves L^-1 y and L^-1 X in
-// Yg; invd[c] = 1 / L_cc.  Returns false when a pivot is not positive and finite.
+// LDL^T factorisation of the packed block A (Kp x Kp, diagonal in dg) with the naug rows of
+// Yg (stride Kmax) riding along as extra rows of a bordered matrix, right-looking, one
+// column per step.  Step c: pivot d_c = dg[c] and its reciprocal (every lane, FP64); the
+// column below the pivot is scaled (l_rc = a_rc / d_c, the unscaled a_rc kept in tmp; for
+// the augmented rows the scaled entry is z_c); then every entry of the trailing triangle
+// and of the augmented rows right of c, a_rk -= l_rc a_kc, is one item, and the items are
+// spread evenly over the group's lanes (at most one item per lane of imbalance per step).
+// On return the strict lower triangle of A holds U (unit lower, Sigma = U D U^T), dg the
+// pivots d_c, dinv their reciprocals and Yg rows z = D^-1 U^-1 (y, X).  The pivots and the
+// diagonal updates are FP64 for both working types: with T = float every product of two
+// FP32 values is exact in FP64, so the pivots carry no FP32 rounding of their own.
+// Returns false when a pivot is not positive and finite.
 template <int L, typename T>
-__device__ __forceinline__ bool chol_augmented(T* A, T* Yg, T* invd, int Kp, int R, int Kmax,
-                                               int gl, unsigned gmask) {
+__device__ __forceinline__ bool ldl_augmented(T* A, T* Yg, double* dg, double* dinv, T* tmp, int Kp,
+                                              int naug, int Kmax, int gl, unsigned gmask) {
     using N = Num<T>;
     for (int c = 0; c < Kp; ++c) {
-        const T* Lc = A + c * (c + 1) / 2;
-        const int r0 = c + ((gl - c) & (L - 1));
-        for (int r = r0; r < R; r += L) {
-            T* Rr = r < Kp ? A + r * (r + 1) / 2 : Yg + (r - Kp) * Kmax;
-            T v0 = Rr[c], v1 = (T)0;
-            int s = 0;
-            for (; s + 1 < c; s += 2) {
-                v0 = N::fma_(-Rr[s], Lc[s], v0);
-                v1 = N::fma_(-Rr[s + 1], Lc[s + 1], v1);
+        const double dc = dg[c];
+        if (!(dc > 0.0) || !(dc <= 1.7976931348623157e308)) return false;
+        const double ic = rcp_newton(dc);
+        const T icT = N::fromd(ic);
+        if (((c - gl) & (L - 1)) == 0) dinv[c] = ic;
+        const int nr = Kp - 1 - c;
+        for (int e = gl; e < nr + naug; e += L) {
+            if (e < nr) {
+                const int r = c + 1 + e;
+                T* Ar = A + r * (r + 1) / 2;
+                const T t = Ar[c];
+                tmp[r] = t;
+                Ar[c] = t * icT;
+            } else {
+                T* z = Yg + (e - nr) * Kmax + c;
+                *z = *z * icT;
             }
-            if (s < c) v0 = N::fma_(-Rr[s], Lc[s], v0);
-            Rr[c] = v0 + v1;
         }
         gsync<L>(gmask);
-        const T vc = Lc[c];
-        if (!(vc > (T)0) || !N::finite_(vc)) return false;
-        const T ic = N::rsqrt_pivot(vc);
-        if (r0 == c) invd[c] = ic;
-        for (int r = (r0 == c ? r0 + L : r0); r < R; r += L) {
-            T* Rr = r < Kp ? A + r * (r + 1) / 2 : Yg + (r - Kp) * Kmax;
-            Rr[c] *= ic;
+        const int ntri = nr * (nr + 1) / 2;
+        int e = gl;
+        if (e < ntri) {
+            int rr = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+            while (rr * (rr + 1) / 2 > e) --rr;
+            while ((rr + 1) * (rr + 2) / 2 <= e) ++rr;
+            int kk = e - rr * (rr + 1) / 2;
+            for (; e < ntri; e += L) {
+                const int r = c + 1 + rr;
+                T* Ar = A + r * (r + 1) / 2;
+                const T l = Ar[c];
+                if (kk == rr) {
+                    dg[r] = fma(-N::to64(l), N::to64(tmp[r]), dg[r]);
+                } else {
+                    const int k = c + 1 + kk;
+                    Ar[k] = N::fma_(-l, tmp[k], Ar[k]);
+                }
+                kk += L;
+                while (kk > rr) { kk -= rr + 1; ++rr; }
+            }
+        }
+        if (naug > 0 && nr > 0) {
+            const int e2 = e - ntri;
+            int a = e2 / nr, kk = e2 - a * nr;
+            while (a < naug) {
+                T* z = Yg + a * Kmax;
+                const int k = c + 1 + kk;
+                z[k] = N::fma_(-z[c], tmp[k], z[k]);
+                kk += L;
+                while (kk >= nr) { kk -= nr; ++a; }
+            }
         }
         gsync<L>(gmask);
     }
     return true;
 }
 
-// b = last row of L^-1 (L^T b^T = e_last), into bv; bacc is scratch.
+// u = last row of U^-1 (U^T u^T = e_last, U unit lower in A): u[last] = 1 and, from the
+// bottom row up, u[a] -= U[r][a] u[r] for a < r once u[r] is final.  No divisions.
 template <int L, typename T>
-__device__ __forceinline__ void last_row_of_inverse(const T* A, const T* invd, T* bacc, T* bv,
-                                                    int Kp, int gl, unsigned gmask) {
+__device__ __forceinline__ void last_row_of_Uinv(const T* A, T* u, int Kp, int gl, unsigned gmask) {
     using N = Num<T>;
     const int last = Kp - 1;
-    for (int a = gl; a < Kp; a += L) bacc[a] = (a == last) ? (T)1 : (T)0;
+    for (int a = gl; a < Kp; a += L) u[a] = (a == last) ? (T)1 : (T)0;
     gsync<L>(gmask);
-    for (int c = last; c >= 0; --c) {
-        const T bc = bacc[c] * invd[c];
-        if (((c - gl) & (L - 1)) == 0) bv[c] = bc;
-        const T* Lr = A + c * (c + 1) / 2;
-        for (int a = gl; a < c; a += L) bacc[a] = N::fma_(-Lr[a], bc, bacc[a]);
+    for (int r = last; r >= 1; --r) {
+        const T ur = u[r];
+        const T* Ur = A + r * (r + 1) / 2;
+        for (int a = gl; a < r; a += L) u[a] = N::fma_(-Ur[a], ur, u[a]);
         gsync<L>(gmask);
     }
 }
@@ -291,8 +359,8 @@ __device__ __forceinline__ void accumulate_record(const uint64_t* sidx, const do
 }
 
 // Covariance of the block in the slot (coordinates in loc, relative and scaled): the packed
-// lower triangle of A, nugget on the diagonal; for the exponential families also the pair
-// weights D1 that the derivative step reuses.
+// strict lower triangle of A and the FP64 diagonal dg (sigma2 (1 + tau2)); for the
+// exponential families also the pair weights D1 that the derivative step reuses.
 template <int COV, int L, typename T, typename Tab>
 __device__ __forceinline__ void assemble_block(const PassEnv<T, Tab>& E, int Kp) {
     using N = Num<T>;
@@ -301,20 +369,21 @@ __device__ __forceinline__ void assemble_block(const PassEnv<T, Tab>& E, int Kp)
     const unsigned gmask = E.gmask;
     const int d = E.d, Kmax = E.Kmax;
     T* A = E.A; T* loc = E.loc; T* D1 = E.D1;
-    const T sig2T = E.sig2T, diagC = E.diagC;
+    const T sig2T = E.sig2T;
     const double m_psi = E.m_psi;
     const Tab* tab = E.tab;
-    // ---------------- covariance assembly (packed lower triangle) ----------------
     const int ntri = Kp * (Kp + 1) / 2;
     for (int e = gl; e < ntri; e += L) {
         int a = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
         while (a * (a + 1) / 2 > e) --a;
         while ((a + 1) * (a + 2) / 2 <= e) ++a;
         int c = e - a * (a + 1) / 2;
-        T C;
         if (a == c) {
-            C = diagC;
-        } else if (COV == COV_EXP) {
+            E.dg[a] = E.diag64;
+            continue;
+        }
+        T C;
+        if (COV == COV_EXP) {
             T s = (T)0;
             for (int k = 0; k < d; ++k) {
                 T t = loc[k * Kmax + a] - loc[k * Kmax + c];
@@ -328,8 +397,8 @@ __device__ __forceinline__ void assemble_block(const PassEnv<T, Tab>& E, int Kp)
             T t0 = loc[a] - loc[c];
             T t1 = loc[Kmax + a] - loc[Kmax + c];
             T t2 = loc[2 * Kmax + a] - loc[2 * Kmax + c];
-            T u = N::fma_(t0, t0, N::fma_(t1, t1, t2 * t2));
-            T D = N::sqrt_(u);
+            T uu = N::fma_(t0, t0, N::fma_(t1, t1, t2 * t2));
+            T D = N::sqrt_(uu);
             T ex = sig2T * N::exp_(-D);
             C = ex;
             D1[a * (a - 1) / 2 + c] = D > (T)0 ? ex / D : (T)0;
@@ -344,13 +413,117 @@ __device__ __forceinline__ void assemble_block(const PassEnv<T, Tab>& E, int Kp)
         A[e] = C;
     }
     gsync<L>(gmask);
+}
 
+// The derivative solves and the per-observation values on the leading Kp x Kp block, once
+// G holds h_j = dSigma_j u^T for the Q derivative vectors (u = last row of U^-1):
+//   f_j = U^-1 h_j      unit forward substitution, column by column; the items (j, a > c)
+//                       of a column are spread over the lanes
+//   Gs_j = f_j / d      FP64, in the bytes of A (no longer needed)
+//   values              with b = d_K^-1/2 u the last row of L^-1 (L = U D^1/2) and
+//                       m_j = L^-1 dSigma_j b^T = d_K^-1/2 D^-1/2 f_j:
+//                         logdet_i = log d_K,  ell = d_K^1/2 z_y[K],  x = d_K^1/2 z_X[K],
+//                         md_j = m_j[K] = f_j[K] / d_K,
+//                         dell_j = -m_j . hat(L^-1 y) = -d_K^-1/2 f_j . hat(z_y),
+//                         dx_j = -d_K^-1/2 f_j . hat(z_X),
+//                         m_j . m_l = d_K^-1 f_j . Gs_l,
+//                       each dot product one item (FP64 accumulation for both working
+//                       types), hat() halving the last entry
+// then the record is added to the lane's sums.
+template <int L, typename T, typename Tab>
+__device__ __forceinline__ void finish_terms(const PassEnv<T, Tab>& E, int Kp, int Q) {
+    using N = Num<T>;
+    const int gl = E.gl;
+    const unsigned gmask = E.gmask;
+    const int p = E.p, Kmax = E.Kmax;
+    const T* A = E.A; const T* Yg = E.Yg; T* G = E.G;
+    double* V = E.V;
+    const int last = Kp - 1;
+    // ---------------- f_j = U^-1 h_j (unit lower, in place) ----------------
+    for (int c = 0; c < last; ++c) {
+        const int nr = last - c;
+        int j = gl / nr, off = gl - j * nr;
+        const int jstep = L / nr, ostep = L - jstep * nr;
+        while (j < Q) {
+            const int a = c + 1 + off;
+            G[j * Kmax + a] = N::fma_(-A[a * (a + 1) / 2 + c], G[j * Kmax + c], G[j * Kmax + a]);
+            j += jstep;
+            off += ostep;
+            if (off >= nr) { off -= nr; ++j; }
+        }
+        gsync<L>(gmask);
+    }
+    // ---------------- Gs = f / d (FP64, over A) ----------------
+    double* Gs = E.Gs;
+    {
+        int j = gl / Kp, a = gl - j * Kp;
+        const int jstep = L / Kp, astep = L - jstep * Kp;
+        while (j < Q) {
+            Gs[j * Kmax + a] = N::to64(G[j * Kmax + a]) * E.dinv[a];
+            j += jstep;
+            a += astep;
+            if (a >= Kp) { a -= Kp; ++j; }
+        }
+    }
+    gsync<L>(gmask);
+    // ---------------- per-observation values ----------------
+    const double dK = E.dg[last], idK = E.dinv[last];
+    const double rs = rsqrt_newton(dK);
+    const double sq = dK * rs;
+    const int vb0 = E.vb0, vstep = E.vstep, vmm = E.vmm;
+    if (gl == 0) {
+        V[0] = 1.0;
+        V[1] = 0.0;
+        V[2] = log(dK);
+        V[3] = N::to64(Yg[last]) * sq;
+        for (int t = 0; t < p; ++t) V[4 + t] = N::to64(Yg[(1 + t) * Kmax + last]) * sq;
+    }
+    for (int j = gl; j < Q; j += L) {
+        const double md = N::to64(G[j * Kmax + last]) * idK;
+        V[vb0 + j * vstep] = md;
+        V[vb0 + j * vstep + 2 + p] = -0.5 * md;
+    }
+    const int P1 = 1 + p;
+    const int nz = Q * P1, nitems = nz + Q * (Q + 1) / 2;
+    for (int it = gl; it < nitems; it += L) {
+        if (it < nz) {
+            const int j = it / P1, t = it - j * P1;
+            const T* g = G + j * Kmax;
+            const T* z = Yg + t * Kmax;
+            double s0 = 0.0, s1 = 0.0;
+            int a = 0;
+            for (; a + 1 < last; a += 2) {
+                s0 = fma(N::to64(g[a]), N::to64(z[a]), s0);
+                s1 = fma(N::to64(g[a + 1]), N::to64(z[a + 1]), s1);
+            }
+            if (a < last) s0 = fma(N::to64(g[a]), N::to64(z[a]), s0);
+            s0 = fma(0.5 * N::to64(g[last]), N::to64(z[last]), s0 + s1);  // hat(): last halved
+            V[vb0 + j * vstep + 1 + t] = -s0 * rs;
+        } else {
+            int r = it - nz, j = 0;
+            while (r >= Q - j) { r -= Q - j; ++j; }
+            const int l = j + r;
+            const T* g = G + j * Kmax;
+            const double* h = Gs + l * Kmax;
+            double s0 = 0.0, s1 = 0.0;
+            int a = 0;
+            for (; a + 1 < Kp; a += 2) {
+                s0 = fma(N::to64(g[a]), h[a], s0);
+                s1 = fma(N::to64(g[a + 1]), h[a + 1], s1);
+            }
+            if (a < Kp) s0 = fma(N::to64(g[a]), h[a], s0);
+            V[vmm + (it - nz)] = (s0 + s1) * idK;
+        }
+    }
+    gsync<L>(gmask);
+    accumulate_record<L>(E.sidx, V, E.acc, E.nstat, gl, gmask);
 }
 
 // One conditional on the leading Kp x Kp block of the factor in the slot (its last row,
-// Kp - 1, is the observation; the rows above are what it conditions on): b = last row of
-// L^-1, then g_j = dSigma_j b^T, m_j = L^-1 g_j, the per-observation values and their
-// accumulation into the lane's sums.  i is the observation (error reports, factor rows).
+// Kp - 1, is the observation; the rows above are what it conditions on): u = last row of
+// U^-1, h_j = dSigma_j u^T with each pair (a, c) evaluated once (a conflict-free round-robin
+// pair schedule lets the lanes scatter into h without atomics), then finish_terms.
+// i is the observation (factor rows).
 template <int COV, int L, typename T, typename Tab>
 __device__ __forceinline__ void conditional_terms(const PassEnv<T, Tab>& E, int Kp, long long i) {
     using N = Num<T>;
@@ -359,34 +532,28 @@ __device__ __forceinline__ void conditional_terms(const PassEnv<T, Tab>& E, int 
     constexpr int Q = NG + 1;
     const int gl = E.gl;
     const unsigned gmask = E.gmask;
-    const int d = E.d, p = E.p, m = E.m, Kmax = E.Kmax;
-    T* A = E.A; T* Yg = E.Yg; T* invd = E.invd; T* loc = E.loc; T* bacc = E.bacc;
-    T* bv = E.bv; T* G = E.G; T* D1 = E.D1;
-    double* V = E.V;
-    int* idx = E.idx;
-    const T sig2T = E.sig2T, diagC = E.diagC, inv_r1T = E.inv_r1T, inv_r2T = E.inv_r2T;
-    const double inv_r1 = E.inv_r1, inv_r2 = E.inv_r2, m_psi = E.m_psi;
+    const int d = E.d, m = E.m, Kmax = E.Kmax;
+    T* u = E.u; T* G = E.G; const T* loc = E.loc; const T* D1 = E.D1;
+    const T sig2T = E.sig2T, inv_r1T = E.inv_r1T, inv_r2T = E.inv_r2T;
+    const double inv_r1 = E.inv_r1, m_psi = E.m_psi;
     const Tab* tab = E.tab;
-    const uint64_t* sidx = E.sidx;
-    double* acc = E.acc;
-    const int vb0 = E.vb0, vstep = E.vstep, vmm = E.vmm;
-    const int last = Kp - 1;
 
-    // ---------------- b = last row of L^-1 (L^T b^T = e_last) ----------------
-    last_row_of_inverse<L, T>(A, invd, bacc, bv, Kp, gl, gmask);
+    last_row_of_Uinv<L, T>(E.A, u, Kp, gl, gmask);
     if (E.factor) {
+        // b = last row of L^-1 = d_K^-1/2 u, in NNarray order
+        const double rs = rsqrt_newton(E.dg[Kp - 1]);
         double* fr = E.factor + i * (long long)(m + 1);
-        for (int c = gl; c <= m; c += L) fr[c] = (c < Kp) ? (double)bv[Kp - 1 - c] : 0.0;
+        for (int c = gl; c <= m; c += L) fr[c] = (c < Kp) ? N::to64(u[Kp - 1 - c]) * rs : 0.0;
         gsync<L>(gmask);
         return;
     }
 
-    // ---------------- g_j = dSigma_j b^T ----------------
-    // g for the pair-derivative parameters starts at 0; the nugget one is sigma2 b.
+    // ---------------- h_j = dSigma_j u^T ----------------
+    // h for the pair-derivative parameters starts at 0; the nugget one is sigma2 u.
     for (int a = gl; a < Kp; a += L) {
 #pragma unroll
         for (int j = 0; j < NG; ++j) G[j * Kmax + a] = (T)0;
-        G[NG * Kmax + a] = sig2T * bv[a];
+        G[NG * Kmax + a] = sig2T * u[a];
     }
     gsync<L>(gmask);
     {
@@ -417,100 +584,17 @@ __device__ __forceinline__ void conditional_terms(const PassEnv<T, Tab>& E, int 
                     dv[0] = F1;                      // dC/drho and dC/dnu from the table
                     if (NG > 1) dv[NG - 1] = F2;
                 }
-                const T ba = bv[a], bc = bv[c];
+                const T ua = u[a], uc = u[c];
 #pragma unroll
                 for (int j = 0; j < NG; ++j) {
-                    G[j * Kmax + a] = N::fma_(dv[j], bc, G[j * Kmax + a]);
-                    G[j * Kmax + c] = N::fma_(dv[j], ba, G[j * Kmax + c]);
+                    G[j * Kmax + a] = N::fma_(dv[j], uc, G[j * Kmax + a]);
+                    G[j * Kmax + c] = N::fma_(dv[j], ua, G[j * Kmax + c]);
                 }
             }
             gsync<L>(gmask);
         }
     }
-
-    // ---------------- m_j = L^-1 g_j (in place, column sweep) ----------------
-    // Column c: every lane reads the finished residual g_j[c] and scales it; after a
-    // group barrier the owner of c stores m_j[c] and each lane updates its rows a > c.
-    for (int c = 0; c < Kp; ++c) {
-        const T ic = invd[c];
-        T mc[Q];
-#pragma unroll
-        for (int j = 0; j < Q; ++j) mc[j] = G[j * Kmax + c] * ic;
-        gsync<L>(gmask);
-        if (((c - gl) & (L - 1)) == 0) {
-#pragma unroll
-            for (int j = 0; j < Q; ++j) G[j * Kmax + c] = mc[j];
-        }
-        const int a0 = c + 1 + ((gl - c - 1) & (L - 1));
-        for (int a = a0; a < Kp; a += L) {
-            const T lac = A[a * (a + 1) / 2 + c];
-#pragma unroll
-            for (int j = 0; j < Q; ++j) G[j * Kmax + a] = N::fma_(-lac, mc[j], G[j * Kmax + a]);
-        }
-        gsync<L>(gmask);
-    }
-
-    // ---------------- per-observation values ----------------
-    {
-        // partial dot products over this lane's entries, last entry of hat() halved
-        T dl[Q], dx[Q][PMAX], mm[Q * (Q + 1) / 2];
-#pragma unroll
-        for (int j = 0; j < Q; ++j) {
-            dl[j] = (T)0;
-            for (int t = 0; t < p; ++t) dx[j][t] = (T)0;
-        }
-#pragma unroll
-        for (int t = 0; t < Q * (Q + 1) / 2; ++t) mm[t] = (T)0;
-        for (int a = gl; a < Kp; a += L) {
-            const T hf = (a == last) ? (T)0.5 : (T)1;
-            const T ly = Yg[a] * hf;
-            T mj[Q];
-#pragma unroll
-            for (int j = 0; j < Q; ++j) {
-                mj[j] = G[j * Kmax + a];
-                dl[j] = N::fma_(mj[j], ly, dl[j]);
-            }
-            for (int t = 0; t < p; ++t) {
-                const T lx = Yg[(1 + t) * Kmax + a] * hf;
-#pragma unroll
-                for (int j = 0; j < Q; ++j) dx[j][t] = N::fma_(mj[j], lx, dx[j][t]);
-            }
-            int u = 0;
-#pragma unroll
-            for (int j = 0; j < Q; ++j)
-#pragma unroll
-                for (int l = j; l < Q; ++l) { mm[u] = N::fma_(mj[j], mj[l], mm[u]); ++u; }
-        }
-#pragma unroll
-        for (int j = 0; j < Q; ++j) {
-            dl[j] = gsum<L>(dl[j], gmask);
-            for (int t = 0; t < p; ++t) dx[j][t] = gsum<L>(dx[j][t], gmask);
-        }
-#pragma unroll
-        for (int t = 0; t < Q * (Q + 1) / 2; ++t) mm[t] = gsum<L>(mm[t], gmask);
-        if (gl == 0) {
-            V[0] = 1.0;
-            V[1] = 0.0;
-            V[2] = -2.0 * log((double)invd[last]);
-            V[3] = (double)Yg[last];
-            for (int t = 0; t < p; ++t) V[4 + t] = (double)Yg[(1 + t) * Kmax + last];
-#pragma unroll
-            for (int j = 0; j < Q; ++j) {
-                const int vb = vb0 + j * vstep;
-                const double md = (double)G[j * Kmax + last];
-                V[vb] = md;
-                V[vb + 1] = -(double)dl[j];
-                for (int t = 0; t < p; ++t) V[vb + 2 + t] = -(double)dx[j][t];
-                V[vb + 2 + p] = -0.5 * md;
-            }
-#pragma unroll
-            for (int t = 0; t < Q * (Q + 1) / 2; ++t) V[vmm + t] = (double)mm[t];
-        }
-        gsync<L>(gmask);
-    }
-
-    // ---------------- accumulate the record (FP64) ----------------
-    accumulate_record<L>(sidx, V, acc, E.nstat, gl, gmask);
+    finish_terms<L, T, Tab>(E, Kp, Q);
 }
 
 // Algorithm 1 for observation i of the dataset in E (all L lanes of the group call it).
@@ -519,7 +603,7 @@ __device__ __forceinline__ void vecchia_point(const PassEnv<T, Tab>& E, long lon
     const int gl = E.gl;
     const unsigned gmask = E.gmask;
     const int d = E.d, p = E.p, m = E.m, Kmax = E.Kmax;
-    T* A = E.A; T* Yg = E.Yg; T* invd = E.invd; T* loc = E.loc;
+    T* Yg = E.Yg; T* loc = E.loc;
     int* idx = E.idx;
     const double inv_r1 = E.inv_r1, inv_r2 = E.inv_r2;
     // ---------------- gather ----------------
@@ -556,9 +640,8 @@ __device__ __forceinline__ void vecchia_point(const PassEnv<T, Tab>& E, long lon
 
     assemble_block<COV, L, T, Tab>(E, Kp);
 
-    // ---------------- Cholesky + forward solves of y and X ----------------
-    // combined rows: r < Kp -> matrix row r (packed), r >= Kp -> augmented row r - Kp
-    if (!chol_augmented<L, T>(A, Yg, invd, Kp, Kp + 1 + p, Kmax, gl, gmask)) {
+    // ---------------- LDL^T + forward solves of y and X ----------------
+    if (!ldl_augmented<L, T>(E.A, Yg, E.dg, E.dinv, E.u, Kp, 1 + p, Kmax, gl, gmask)) {
         if (gl == 0) report(E.status, E.bad, ST_NOT_PD, i);
         gsync<L>(gmask);
         return;
@@ -570,15 +653,16 @@ __device__ __forceinline__ void vecchia_point(const PassEnv<T, Tab>& E, long lon
 // Grouped conditioning: block g holds a conditioning set U (ascending observation indices)
 // followed by its members, consecutive observations s .. e - 1 that all come after U.  The
 // group's contribution is that of the joint conditional p(y_B | y_U), which factors into
-// one conditional per member on U and the earlier members: after one Cholesky of the whole
-// block, member row r is the last row of the leading (r + 1) x (r + 1) block, so each
-// member's terms are the single-observation terms on that leading block.
+// one conditional per member on U and the earlier members: after one factorisation of the
+// whole block, member row r is the last row of the leading (r + 1) x (r + 1) block (the
+// leading part of U, D and z is the factorisation of the leading block), so each member's
+// terms are the single-observation terms on that leading block.
 template <int COV, int L, typename T, typename Tab>
 __device__ __forceinline__ void vecchia_group(const PassEnv<T, Tab>& E, long long g) {
     const int gl = E.gl;
     const unsigned gmask = E.gmask;
     const int d = E.d, p = E.p, Kmax = E.Kmax;
-    T* A = E.A; T* Yg = E.Yg; T* invd = E.invd; T* loc = E.loc;
+    T* Yg = E.Yg; T* loc = E.loc;
     const long long o0 = E.blk_off[g], len = E.blk_off[g + 1] - o0;
     const int32_t* blk = E.blk_idx + o0;
     const int nm = E.nmemb[g];
@@ -615,7 +699,7 @@ __device__ __forceinline__ void vecchia_group(const PassEnv<T, Tab>& E, long lon
     }
     gsync<L>(gmask);
     assemble_block<COV, L, T, Tab>(E, Kp);
-    if (!chol_augmented<L, T>(A, Yg, invd, Kp, Kp + 1 + p, Kmax, gl, gmask)) {
+    if (!ldl_augmented<L, T>(E.A, Yg, E.dg, E.dinv, E.u, Kp, 1 + p, Kmax, gl, gmask)) {
         if (gl == 0) report(E.status, E.bad, ST_NOT_PD, blk[Kp - nm]);
         gsync<L>(gmask);
         return;
@@ -629,10 +713,9 @@ __device__ __forceinline__ void vecchia_group(const PassEnv<T, Tab>& E, long lon
 // spread over the group's lanes:
 //   covariance  C = sigma2 e^-D, D = |h / rho| (coordinates stored divided by their
 //               ranges), and w = C / D kept per pair
-//   g_k         = dSigma_k b^T with dC/drho_k = w u_k^2 / rho_k (u = scaled difference),
+//   h_k         = dSigma_k u^T with dC/drho_k = w u_k^2 / rho_k (u = scaled difference),
 //               pairs once in the round-robin schedule, the 1/rho_k applied afterwards
-//   m_j         = L^-1 g_j column by column, items (j, row) over the lanes
-//   values      one dot product per item: dell_j, dx_jt (with hat()), m_j . m_l
+//   then the derivative solves and values of finish_terms.
 template <int L, typename T, typename Tab>
 __device__ __forceinline__ void vecchia_point_aniso(const PassEnv<T, Tab>& E, long long i) {
     using N = Num<T>;
@@ -640,9 +723,7 @@ __device__ __forceinline__ void vecchia_point_aniso(const PassEnv<T, Tab>& E, lo
     const unsigned gmask = E.gmask;
     const int d = E.d, p = E.p, m = E.m, Kmax = E.Kmax;
     const int NG = d, Q = d + 1;
-    T* A = E.A; T* Yg = E.Yg; T* invd = E.invd; T* loc = E.loc; T* bacc = E.bacc;
-    T* bv = E.bv; T* G = E.G; T* D1 = E.D1;
-    double* V = E.V;
+    T* A = E.A; T* Yg = E.Yg; T* loc = E.loc; T* u = E.u; T* G = E.G; T* D1 = E.D1;
     // ---------------- gather ----------------
     const int32_t* row = E.NN + i * (long long)(m + 1);
     int cnt = 0, badrow = 0;
@@ -679,49 +760,48 @@ __device__ __forceinline__ void vecchia_point_aniso(const PassEnv<T, Tab>& E, lo
         while (a * (a + 1) / 2 > e) --a;
         while ((a + 1) * (a + 2) / 2 <= e) ++a;
         const int c = e - a * (a + 1) / 2;
-        T C;
         if (a == c) {
-            C = E.diagC;
-        } else {
-            T s0 = (T)0, s1 = (T)0;
-            int k = 0;
-            for (; k + 1 < d; k += 2) {
-                const T t0 = loc[k * Kmax + a] - loc[k * Kmax + c];
-                const T t1 = loc[(k + 1) * Kmax + a] - loc[(k + 1) * Kmax + c];
-                s0 = N::fma_(t0, t0, s0);
-                s1 = N::fma_(t1, t1, s1);
-            }
-            if (k < d) {
-                const T t0 = loc[k * Kmax + a] - loc[k * Kmax + c];
-                s0 = N::fma_(t0, t0, s0);
-            }
-            const T Dd = N::sqrt_(s0 + s1);
-            C = E.sig2T * N::exp_(-Dd);
-            D1[a * (a - 1) / 2 + c] = Dd > (T)0 ? C / Dd : (T)0;
+            E.dg[a] = E.diag64;
+            continue;
         }
+        T s0 = (T)0, s1 = (T)0;
+        int k = 0;
+        for (; k + 1 < d; k += 2) {
+            const T t0 = loc[k * Kmax + a] - loc[k * Kmax + c];
+            const T t1 = loc[(k + 1) * Kmax + a] - loc[(k + 1) * Kmax + c];
+            s0 = N::fma_(t0, t0, s0);
+            s1 = N::fma_(t1, t1, s1);
+        }
+        if (k < d) {
+            const T t0 = loc[k * Kmax + a] - loc[k * Kmax + c];
+            s0 = N::fma_(t0, t0, s0);
+        }
+        const T Dd = N::sqrt_(s0 + s1);
+        const T C = E.sig2T * N::exp_(-Dd);
+        D1[a * (a - 1) / 2 + c] = Dd > (T)0 ? C / Dd : (T)0;
         A[e] = C;
     }
     gsync<L>(gmask);
 
-    // ---------------- Cholesky + forward solves, b ----------------
-    if (!chol_augmented<L, T>(A, Yg, invd, Kp, Kp + 1 + p, Kmax, gl, gmask)) {
+    // ---------------- LDL^T + forward solves, u ----------------
+    if (!ldl_augmented<L, T>(A, Yg, E.dg, E.dinv, u, Kp, 1 + p, Kmax, gl, gmask)) {
         if (gl == 0) report(E.status, E.bad, ST_NOT_PD, i);
         gsync<L>(gmask);
         return;
     }
-    const int last = Kp - 1;
-    last_row_of_inverse<L, T>(A, invd, bacc, bv, Kp, gl, gmask);
+    last_row_of_Uinv<L, T>(A, u, Kp, gl, gmask);
     if (E.factor) {
+        const double rs = rsqrt_newton(E.dg[Kp - 1]);
         double* fr = E.factor + i * (long long)(m + 1);
-        for (int c = gl; c <= m; c += L) fr[c] = (c < Kp) ? (double)bv[Kp - 1 - c] : 0.0;
+        for (int c = gl; c <= m; c += L) fr[c] = (c < Kp) ? N::to64(u[Kp - 1 - c]) * rs : 0.0;
         gsync<L>(gmask);
         return;
     }
 
-    // ---------------- g_j = dSigma_j b^T ----------------
+    // ---------------- h_k = dSigma_k u^T ----------------
     for (int a = gl; a < Kp; a += L) {
         for (int k = 0; k < NG; ++k) G[k * Kmax + a] = (T)0;
-        G[NG * Kmax + a] = E.sig2T * bv[a];
+        G[NG * Kmax + a] = E.sig2T * u[a];
     }
     gsync<L>(gmask);
     {
@@ -732,12 +812,12 @@ __device__ __forceinline__ void vecchia_point_aniso(const PassEnv<T, Tab>& E, lo
                 int a, c;
                 if (!circle_pair(Kp, Nv, r, k2, a, c)) continue;
                 const T w = D1[a * (a - 1) / 2 + c];
-                const T ba = bv[a], bc = bv[c];
+                const T ua = u[a], uc = u[c];
                 for (int k = 0; k < NG; ++k) {
                     const T t = loc[k * Kmax + a] - loc[k * Kmax + c];
                     const T v = (w * t) * t;
-                    G[k * Kmax + a] = N::fma_(v, bc, G[k * Kmax + a]);
-                    G[k * Kmax + c] = N::fma_(v, ba, G[k * Kmax + c]);
+                    G[k * Kmax + a] = N::fma_(v, uc, G[k * Kmax + a]);
+                    G[k * Kmax + c] = N::fma_(v, ua, G[k * Kmax + c]);
                 }
             }
             gsync<L>(gmask);
@@ -748,79 +828,7 @@ __device__ __forceinline__ void vecchia_point_aniso(const PassEnv<T, Tab>& E, lo
         for (int k = 0; k < NG; ++k) G[k * Kmax + a] *= E.inv_rkT[k];
     gsync<L>(gmask);
 
-    // ---------------- m_j = L^-1 g_j (column sweep, items (j, row a > c)) ----------------
-    for (int c = 0; c < Kp; ++c) {
-        const T ic = invd[c];
-        for (int j = gl; j < Q; j += L) G[j * Kmax + c] *= ic;
-        gsync<L>(gmask);
-        const int nr = Kp - 1 - c;
-        if (nr > 0) {
-            const T* Lcol = A;   // entry (a, c) at a (a + 1) / 2 + c
-            int j = gl / nr, off = gl - (gl / nr) * nr;
-            const int jstep = L / nr, ostep = L - (L / nr) * nr;
-            for (; j < Q;) {
-                const int a = c + 1 + off;
-                G[j * Kmax + a] = N::fma_(-Lcol[a * (a + 1) / 2 + c], G[j * Kmax + c], G[j * Kmax + a]);
-                j += jstep;
-                off += ostep;
-                if (off >= nr) { off -= nr; ++j; }
-            }
-        }
-        gsync<L>(gmask);
-    }
-
-    // ---------------- per-observation values ----------------
-    const int vb0 = E.vb0, vstep = E.vstep, vmm = E.vmm;
-    if (gl == 0) {
-        V[0] = 1.0;
-        V[1] = 0.0;
-        V[2] = -2.0 * log((double)invd[last]);
-        V[3] = (double)Yg[last];
-        for (int t = 0; t < p; ++t) V[4 + t] = (double)Yg[(1 + t) * Kmax + last];
-    }
-    for (int j = gl; j < Q; j += L) {
-        const double md = (double)G[j * Kmax + last];
-        V[vb0 + j * vstep] = md;
-        V[vb0 + j * vstep + 2 + p] = -0.5 * md;
-    }
-    // items: (j, t) for the y / X dot products (t = 0: y, t >= 1: column t - 1), then the
-    // pairs j <= l of m_j . m_l in the order of the record
-    const int P1 = 1 + p;
-    const int nyx = Q * P1, nitems = nyx + Q * (Q + 1) / 2;
-    for (int u = gl; u < nitems; u += L) {
-        if (u < nyx) {
-            const int j = u / P1, t = u - j * P1;
-            const T* g = G + j * Kmax;
-            const T* z = Yg + t * Kmax;
-            T s0 = (T)0, s1 = (T)0;
-            int a = 0;
-            for (; a + 1 < last; a += 2) {
-                s0 = N::fma_(g[a], z[a], s0);
-                s1 = N::fma_(g[a + 1], z[a + 1], s1);
-            }
-            if (a < last) s0 = N::fma_(g[a], z[a], s0);
-            s0 = N::fma_(g[last] * (T)0.5, z[last], s0 + s1);   // hat(): last entry halved
-            V[vb0 + j * vstep + 1 + t] = -(double)s0;
-        } else {
-            int r = u - nyx, j = 0;
-            while (r >= Q - j) { r -= Q - j; ++j; }
-            const int l = j + r;
-            const T* g = G + j * Kmax;
-            const T* h = G + l * Kmax;
-            T s0 = (T)0, s1 = (T)0;
-            int a = 0;
-            for (; a + 1 < Kp; a += 2) {
-                s0 = N::fma_(g[a], h[a], s0);
-                s1 = N::fma_(g[a + 1], h[a + 1], s1);
-            }
-            if (a < Kp) s0 = N::fma_(g[a], h[a], s0);
-            V[vmm + (u - nyx)] = (double)(s0 + s1);
-        }
-    }
-    gsync<L>(gmask);
-
-    // ---------------- accumulate the record (FP64) ----------------
-    accumulate_record<L>(E.sidx, V, E.acc, E.nstat, gl, gmask);
+    finish_terms<L, T, Tab>(E, Kp, Q);
 }
 
 // The FP32 (mixed) instantiations are latency-bound: ask for three resident blocks of 256
@@ -867,20 +875,12 @@ __global__ void __launch_bounds__(256, pass_min_blocks(sizeof(T))) k_pass(PassAr
     double* accbase = sp;
     sp += (size_t)blockDim.x * args.acc_per_lane;
     SlotLayout SL;
-    SL.init(m, d, p, COV, args.nv, (int)sizeof(T));
+    SL.init(m, d, p, COV, args.nv, (int)sizeof(T), GROUPED);
     char* slotc = reinterpret_cast<char*>(sp) + (size_t)grp * args.slot_stride;
     int* idx = reinterpret_cast<int*>(reinterpret_cast<char*>(sp) + (size_t)ngrp * args.slot_stride) +
                grp * Kmax;
     T* slot = reinterpret_cast<T*>(slotc);
-    T* A = slot + SL.A;
-    T* Yg = slot + SL.Y;
-    T* invd = slot + SL.inv;
-    T* loc = slot + SL.loc;
-    T* bacc = slot + SL.bacc;
-    T* bv = slot + SL.b;
-    T* G = slot + SL.G;
-    T* D1 = slot + SL.D1;
-    double* V = reinterpret_cast<double*>(slotc + SL.Vbyte);
+    double* slotd = reinterpret_cast<double*>(slotc + SL.Dbyte);
 
     // ---- per-observation value vector V (see build_record_index)
     const int vb0 = 4 + p, vstep = 3 + p, vmm = vb0 + Q * vstep;
@@ -901,7 +901,6 @@ __global__ void __launch_bounds__(256, pass_min_blocks(sizeof(T))) k_pass(PassAr
             inv_rkT[k] = (T)inv_rk[k];
         }
     const T sig2T = (T)sig2;
-    const T diagC = (T)(sig2 * (1.0 + tau2));
     // EXP: rho = th[1]; MATERN: rho = th[1], nu = th[2]; ST: rho_s = th[1], rho_t = th[2]
     const double inv_r1 = 1.0 / th[1];
     const double inv_r2 = (COV == COV_ST) ? 1.0 / th[2] : 1.0;
@@ -914,13 +913,16 @@ __global__ void __launch_bounds__(256, pass_min_blocks(sizeof(T))) k_pass(PassAr
     const long long gstride = (long long)gridDim.x * ngrp;
     PassEnv<T, Tab> E;
     E.gl = gl; E.gmask = gmask;
-    E.A = A; E.Yg = Yg; E.invd = invd; E.loc = loc; E.bacc = bacc; E.bv = bv; E.G = G; E.D1 = D1;
-    E.V = V; E.idx = idx; E.Kmax = Kmax;
+    E.A = slot + SL.A; E.Yg = slot + SL.Y; E.loc = slot + SL.loc; E.u = slot + SL.u;
+    E.G = slot + SL.G; E.D1 = slot + SL.D1;
+    E.Gs = SL.Gs < 0 ? reinterpret_cast<double*>(slotc) : slotd + SL.Gs;
+    E.dg = slotd + SL.dg; E.dinv = slotd + SL.dinv; E.V = slotd + SL.V;
+    E.idx = idx; E.Kmax = Kmax;
     E.locs = args.locs; E.y = args.y; E.X = args.X; E.NN = args.NN;
     E.d = d; E.p = p; E.m = m; E.status = args.status; E.bad = args.bad;
     E.nu = (COV == COV_MATERN) ? th[2] : 0.0; E.m_psi = m_psi; E.sig2 = sig2;
     E.inv_r1 = inv_r1; E.inv_r2 = inv_r2;
-    E.sig2T = sig2T; E.diagC = diagC; E.inv_r1T = inv_r1T; E.inv_r2T = inv_r2T;
+    E.sig2T = sig2T; E.diag64 = sig2 * (1.0 + tau2); E.inv_r1T = inv_r1T; E.inv_r2T = inv_r2T;
     E.inv_rk = inv_rk; E.inv_rkT = inv_rkT;
     E.tab = tab; E.sidx = sidx; E.acc = acc; E.nstat = args.nstat;
     E.vb0 = vb0; E.vstep = vstep; E.vmm = vmm; E.factor = nullptr;
@@ -998,9 +1000,12 @@ __global__ void __launch_bounds__(256, pass_min_blocks(sizeof(T))) k_pass_batch(
 
     PassEnv<T, Tab> E;
     E.gl = gl; E.gmask = gmask;
-    E.A = slot + SL.A; E.Yg = slot + SL.Y; E.invd = slot + SL.inv; E.loc = slot + SL.loc;
-    E.bacc = slot + SL.bacc; E.bv = slot + SL.b; E.G = slot + SL.G; E.D1 = slot + SL.D1;
-    E.V = reinterpret_cast<double*>(slotc + SL.Vbyte); E.idx = idx; E.Kmax = Kmax;
+    double* slotd = reinterpret_cast<double*>(slotc + SL.Dbyte);
+    E.A = slot + SL.A; E.Yg = slot + SL.Y; E.loc = slot + SL.loc; E.u = slot + SL.u;
+    E.G = slot + SL.G; E.D1 = slot + SL.D1;
+    E.Gs = SL.Gs < 0 ? reinterpret_cast<double*>(slotc) : slotd + SL.Gs;
+    E.dg = slotd + SL.dg; E.dinv = slotd + SL.dinv; E.V = slotd + SL.V;
+    E.idx = idx; E.Kmax = Kmax;
     E.d = d; E.p = p; E.sidx = sidx; E.acc = acc; E.nstat = args.nstat;
     E.vb0 = vb0; E.vstep = vstep; E.vmm = vmm;
     E.inv_rk = inv_rk; E.inv_rkT = inv_rkT;
@@ -1028,7 +1033,7 @@ __global__ void __launch_bounds__(256, pass_min_blocks(sizeof(T))) k_pass_batch(
             E.inv_r1 = 1.0 / th[1];
             E.inv_r2 = (COV == COV_ST) ? 1.0 / th[2] : 1.0;
             E.sig2T = (T)sig2;
-            E.diagC = (T)(sig2 * (1.0 + tau2));
+            E.diag64 = sig2 * (1.0 + tau2);
             E.inv_r1T = (T)E.inv_r1;
             E.inv_r2T = (T)E.inv_r2;
             E.nu = (COV == COV_MATERN) ? th[2] : 0.0;

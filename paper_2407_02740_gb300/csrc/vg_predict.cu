@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(128) k_predict(PredArgs a) {
             gsync<L>(gmask);
             const double vc = Lc[c];
             if (!(vc > 0.0) || !isfinite(vc)) { pd = false; break; }
-            const double ic = N::rsqrt_pivot(vc);
+            const double ic = rsqrt_newton(vc);
             if (r0 == c) invd[c] = ic;
             for (int r = (r0 == c ? r0 + L : r0); r < Rn; r += L) {
                 double* Rr = r < Kp ? A + r * (r + 1) / 2 : R;

@@ -29,7 +29,7 @@ def _errors(g, o, n):
     return {"loglik": abs(g["loglik"] - o["loglik"]) / max(abs(o["loglik"]), n),
             "grad": np.linalg.norm(g["grad"] - o["grad"]) / scale,
             "grad_j": float(np.max(np.abs(g["grad"] - o["grad"]) / np.maximum(
-                np.sqrt(np.abs(np.diag(o["info"]))), 1e-8 * np.sqrt(np.trace(o["info"]))))),
+                np.sqrt(np.abs(np.diag(o["info"]))), 1e-4 * max(np.linalg.norm(o["grad"]), np.sqrt(np.trace(o["info"])))))),
             "info": np.linalg.norm(g["info"] - o["info"]) / np.linalg.norm(o["info"]),
             "beta": np.linalg.norm(g["betahat"] - o["betahat"]) / (np.linalg.norm(o["betahat"]) + 1)}
 

@@ -44,7 +44,7 @@ def _rel_errors(g, o, n):
     return {"loglik": abs(g["loglik"] - o["loglik"]) / max(abs(o["loglik"]), n),
             "grad": np.linalg.norm(g["grad"] - o["grad"]) / scale,
             "grad_j": float(np.max(np.abs(g["grad"] - o["grad"]) / np.maximum(
-                np.sqrt(np.abs(np.diag(o["info"]))), 1e-8 * np.sqrt(np.trace(o["info"]))))),
+                np.sqrt(np.abs(np.diag(o["info"]))), 1e-4 * max(np.linalg.norm(o["grad"]), np.sqrt(np.trace(o["info"])))))),
             "info": np.linalg.norm(g["info"] - o["info"]) / np.linalg.norm(o["info"]),
             "beta": np.linalg.norm(g["betahat"] - o["betahat"]) / (np.linalg.norm(o["betahat"]) + 1)}
 
@@ -90,7 +90,7 @@ def test_batch_fp64_matches_oracle():
             scale = max(np.linalg.norm(o["grad"]), np.sqrt(np.trace(o["info"])))
             assert np.linalg.norm(g["grad"] - o["grad"]) <= 1e-10 * scale
             assert np.all(np.abs(g["grad"] - o["grad"]) <= 1e-10 * np.maximum(
-                np.sqrt(np.abs(np.diag(o["info"]))), 1e-8 * np.sqrt(np.trace(o["info"]))))
+                np.sqrt(np.abs(np.diag(o["info"]))), 1e-4 * max(np.linalg.norm(o["grad"]), np.sqrt(np.trace(o["info"])))))
             assert np.linalg.norm(g["info"] - o["info"]) <= 1e-10 * np.linalg.norm(o["info"])
             assert np.allclose(g["betahat"], o["betahat"], rtol=1e-9, atol=1e-10)
     finally:

@@ -123,4 +123,4 @@ def test_fields_pass_matches_oracle():
         scale = max(np.linalg.norm(o["grad"]), np.sqrt(np.trace(o["info"])))
         assert np.linalg.norm(g["grad"] - o["grad"]) <= 1e-10 * scale
         assert np.all(np.abs(g["grad"] - o["grad"]) <= 1e-10 * np.maximum(
-            np.sqrt(np.abs(np.diag(o["info"]))), 1e-8 * np.sqrt(np.trace(o["info"]))))
+            np.sqrt(np.abs(np.diag(o["info"]))), 1e-4 * max(np.linalg.norm(o["grad"]), np.sqrt(np.trace(o["info"])))))
