@@ -406,7 +406,8 @@ def vecchia_batch_fit(locs, y, X, NNarray, point_offsets, m, covfun: int, start,
     theta = torch.empty(nb, q, dtype=torch.float64, device=dev)
     out = torch.empty(nb, 1 + q + q * q + p, dtype=torch.float64, device=dev)
     infos = (FitInfo * nb)()
-    opts = FitOpts(tol, maxit, max_halvings, 1 if use_graph else 0, _PREC[prec])
+    opts = FitOpts(tol, maxit, max_halvings, 1 if use_graph else 0,
+                   FIT_MIXED_ONLY if prec == "mixed_only" else _PREC[prec])
     P = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
     _check(lib().vecchia_batch_fit(handle.ptr, nb, _dptr(locs), _dptr(y), _dptr(X), _dptr(NNarray),
                                    P(off), P(mm), d, p, covfun, _dptr(start), ctypes.byref(opts),
@@ -497,7 +498,8 @@ def vecchia_fields_fit(locs, X, NNarray, Y, covfun: int, start, tol: float = 1e-
     theta = torch.empty(nf, q, dtype=torch.float64, device=dev)
     out = torch.empty(nf, 1 + q + q * q + p, dtype=torch.float64, device=dev)
     infos = (FitInfo * nf)()
-    opts = FitOpts(tol, maxit, max_halvings, 1 if use_graph else 0, _PREC[prec])
+    opts = FitOpts(tol, maxit, max_halvings, 1 if use_graph else 0,
+                   FIT_MIXED_ONLY if prec == "mixed_only" else _PREC[prec])
     _check(lib().vecchia_fields_fit(handle.ptr, nf, _dptr(locs), _dptr(X), _dptr(NNarray), n, d,
                                     p, m, _dptr(Y), covfun, _dptr(start), ctypes.byref(opts),
                                     ctypes.c_void_p(stream.cuda_stream), _dptr(theta), _dptr(out),

@@ -1080,6 +1080,7 @@ static vec_status batch_fit_impl(vec_handle h, int nbatch,
     if (e == cudaSuccess) e = grow(&h->bf_st, &h->c_bf_st, (size_t)nbatch * 2);
     if (e != cudaSuccess) return cuda_fail(e, "vecchia_batch_fit: allocating the fit state");
     const int max_evals = (o.maxit + 2) * (o.max_halvings + 2);
+    const bool mixed_only = (o.prec == VEC_FIT_MIXED_ONLY);
     const int nphase = (o.prec == (int)VEC_MIXED) ? 2 : 1;
     std::vector<vg::FitState> fsh((size_t)nbatch);
     std::vector<int> iters0((size_t)nbatch, 0), evals0((size_t)nbatch, 0);
@@ -1180,7 +1181,8 @@ vec_status vecchia_batch_fit(vec_handle h, int nbatch, const double* locs, const
     vec_fit_opts o = {1e-4, 40, 10, 1, (int)VEC_FP64};
     if (opts) o = *opts;
     vec_status s = check_batch_args("vecchia_batch_fit", h, nbatch, locs, y, X, NNarray,
-                                    point_offsets, m, d, p, covfun, o.prec);
+                                    point_offsets, m, d, p, covfun,
+                                    o.prec == VEC_FIT_MIXED_ONLY ? (int)VEC_MIXED : o.prec);
     if (s != VEC_OK) return s;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     auto prep = [&](int prec, BatchPlan* B) {
@@ -1321,7 +1323,7 @@ vec_status vecchia_fields_fit(vec_handle h, int nfields, const double* locs, con
     vec_fit_opts o = {1e-4, 40, 10, 1, (int)VEC_FP64};
     if (opts) o = *opts;
     vec_status s = check_fields_args("vecchia_fields_fit", h, nfields, locs, X, NNarray, n, d, p, m,
-                                     Y, covfun, o.prec);
+                                     Y, covfun, o.prec == VEC_FIT_MIXED_ONLY ? (int)VEC_MIXED : o.prec);
     if (s != VEC_OK) return s;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     auto prep = [&](int prec, BatchPlan* B) {
