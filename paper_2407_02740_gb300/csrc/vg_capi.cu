@@ -371,8 +371,8 @@ vec_status enqueue_pass(vec_handle h, const double* locs, const double* y, const
     const bool tr = h->timing != 0;
     if (tr) cudaEventRecord(h->ev[0], st);
     e = vg::launch_init_status(h->status, h->bad, st);
-    if (e == cudaSuccess && cov == vg::COV_MATERN)
-        e = vg::launch_mtab_build(covparms, h->mtab, prec ? h->mtabf : nullptr, st);
+    if (e == cudaSuccess && vg::uses_table(cov, prec))
+        e = vg::launch_mtab_build(cov, covparms, h->mtab, prec ? h->mtabf : nullptr, st);
     if (e != cudaSuccess) return cuda_fail(e, "launching the setup kernels");
     vg::PassArgs a;
     a.locs = locs; a.y = y; a.X = X; a.NN = NN; a.covparms = covparms;
@@ -663,11 +663,11 @@ vec_status vecchia_autotune(vec_handle h, const double* locs, const double* y, c
     float best = 1e30f;
     static const int thr_list[] = {256, 128, 64};
     int bestTab = -1;
-    const int ntab = (cov == vg::COV_MATERN) ? 2 : 1;
+    const int ntab = vg::uses_table(cov, (int)prec) ? 2 : 1;
     for (int ti = 0; ti < 3 && e == cudaSuccess; ++ti) {
         for (int L = 1; L <= 32 && e == cudaSuccess; L *= 2)
         for (int tb = 0; tb < ntab && e == cudaSuccess; ++tb) {
-            const int tab = (cov == vg::COV_MATERN) ? 1 - tb : -1;  // shared memory first
+            const int tab = vg::uses_table(cov, (int)prec) ? 1 - tb : -1;  // shared memory first
             if (L > thr_list[ti]) continue;
             vg::PassPlan plan;
             if (vg::plan_pass(cov, m, d, p, h->nsm, L, thr_list[ti], &plan, (int)prec, false, tab) != 0)
@@ -846,7 +846,7 @@ vec_status prepare_batch_desc(vec_handle h, BatchScratch& S, int d, int p, vec_c
     if (e == cudaSuccess) e = grow(&S.bad, &S.c_bad, (size_t)nbatch);
     if (e == cudaSuccess) e = grow(&S.counter, &S.c_counter, (size_t)1);
     if (e == cudaSuccess) e = grow(&S.partials, &S.c_part, (size_t)B->ntiles * B->plan.nstat);
-    if (e == cudaSuccess && cov == vg::COV_MATERN)
+    if (e == cudaSuccess && vg::uses_table(cov, prec))
         e = grow(&S.tabs, &S.c_tabs, (size_t)nbatch * vg::mtab_doubles());
     if (e == cudaSuccess && cov == vg::COV_MATERN && prec)
         e = grow(&S.tabsf, &S.c_tabsf, (size_t)nbatch * vg::mtab_floats());
@@ -915,8 +915,8 @@ vec_status enqueue_batch(const BatchScratch& S, const BatchPlan& B, const double
     const int cov = (int)covfun;
     const int q = vecchia_nparms_d(covfun, d);
     cudaError_t e = vg::launch_init_batch(S.status, S.bad, B.nbatch, S.counter, st);
-    if (e == cudaSuccess && cov == vg::COV_MATERN)
-        e = vg::launch_mtab_build_batch(covparms, B.nbatch, q, S.tabs, prec ? S.tabsf : nullptr,
+    if (e == cudaSuccess && vg::uses_table(cov, prec))
+        e = vg::launch_mtab_build_batch(cov, covparms, B.nbatch, q, S.tabs, prec ? S.tabsf : nullptr,
                                         active, st);
     if (e != cudaSuccess) return cuda_fail(e, "launching the batch setup kernels");
     vg::BatchArgs a;
@@ -1221,11 +1221,11 @@ vec_status vecchia_batch_autotune(vec_handle h, int nbatch, const double* locs, 
     for (int b = 0; b < nbatch; ++b) mmax = m[b] > mmax ? m[b] : mmax;
     static const int thr_list[] = {256, 128, 64};
     int bestTab = -1;
-    const int ntab = (cov == vg::COV_MATERN) ? 2 : 1;
+    const int ntab = vg::uses_table(cov, (int)prec) ? 2 : 1;
     for (int ti = 0; ti < 3 && e == cudaSuccess && s == VEC_OK; ++ti) {
         for (int L = 1; L <= 32 && e == cudaSuccess; L *= 2)
         for (int tb = 0; tb < ntab && e == cudaSuccess; ++tb) {
-            const int tab = (cov == vg::COV_MATERN) ? 1 - tb : -1;
+            const int tab = vg::uses_table(cov, (int)prec) ? 1 - tb : -1;
             if (L > thr_list[ti]) continue;
             vg::PassPlan plan;
             if (vg::plan_pass(cov, mmax, d, p, h->nsm, L, thr_list[ti], &plan, (int)prec, true, tab) != 0)
@@ -1614,7 +1614,7 @@ vec_status vecchia_predict(vec_handle h, const double* locs, const double* y, co
     if (!g.ok) return fail(VEC_ERR_CUDA, "cannot select device %d", h->device);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = vg::launch_init_status(h->status, h->bad, st);
-    if (e == cudaSuccess && covfun == VEC_MATERN_ISO) e = vg::launch_mtab_build(covparms, h->mtab, nullptr, st);
+    if (e == cudaSuccess && covfun == VEC_MATERN_ISO) e = vg::launch_mtab_build(vg::COV_MATERN, covparms, h->mtab, nullptr, st);
     if (e == cudaSuccess)
         e = vg::launch_predict((int)covfun, locs, y, X, beta, n, locs_pred, X_pred, NN_pred, npred,
                                d, p, m, covparms, h->mtab, latent ? 1 : 0, h->nsm, mean, var,
@@ -1794,8 +1794,8 @@ vec_status vecchia_grouped_loglik_grad_info(vec_handle h, const double* locs, co
     }
     cudaError_t e = grow(&h->partials, &h->partials_cap, total * nstat);
     if (e == cudaSuccess) e = vg::launch_init_status(h->status, h->bad, st);
-    if (e == cudaSuccess && cov == vg::COV_MATERN)
-        e = vg::launch_mtab_build(covparms, h->mtab, prec ? h->mtabf : nullptr, st);
+    if (e == cudaSuccess && vg::uses_table(cov, prec))
+        e = vg::launch_mtab_build(cov, covparms, h->mtab, prec ? h->mtabf : nullptr, st);
     if (e != cudaSuccess) return cuda_fail(e, "grouped pass: set-up");
     size_t rec0 = 0;
     for (int c = 0; c < nclass && e == cudaSuccess; ++c) {
@@ -1844,7 +1844,7 @@ vec_status vecchia_covariance_pairs(vec_handle h, vec_covfun covfun, const doubl
     if (!g.ok) return fail(VEC_ERR_CUDA, "cannot select device %d", h->device);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = cudaSuccess;
-    if (covfun == VEC_MATERN_ISO) e = vg::launch_mtab_build(covparms, h->mtab, nullptr, st);
+    if (covfun == VEC_MATERN_ISO) e = vg::launch_mtab_build(vg::COV_MATERN, covparms, h->mtab, nullptr, st);
     if (e == cudaSuccess)
         e = vg::launch_cov_pairs((int)covfun, covparms, h->mtab, d, npairs, la, lb, same, C, dC, st);
     if (e != cudaSuccess) return cuda_fail(e, "vecchia_covariance_pairs");

@@ -36,6 +36,14 @@ constexpr int MT_DOUBLES = MT_NINT * MT_PER_INT;
 constexpr int MT_PER_INT_F = 3 * MT_NC;
 constexpr int MT_FLOATS = MT_NINT * MT_PER_INT_F;
 
+// Families whose pass reads a per-pass coefficient table: the Matern family always (its
+// FP64 table, and an FP32 copy for the mixed path), the exponential families on the FP64
+// path (prec 0), whose covariance and pair weights come from the same kind of table
+// instead of a square root, an exponential and a division per pair.
+__host__ __device__ constexpr bool uses_table(int cov, int prec) {
+    return cov == COV_MATERN || prec == 0;
+}
+
 // number of covariance parameters (d: location dimension, used by COV_ANISO only)
 __host__ __device__ constexpr int nparms(int cov, int d = 0) {
     return cov == COV_EXP ? 3 : (cov == COV_ANISO ? d + 2 : 4);

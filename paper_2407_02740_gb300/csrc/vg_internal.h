@@ -39,8 +39,10 @@ const void* pass_batch_kernel_f64(int cov, int L);
 const void* pass_batch_kernel_f32(int cov, int L);
 const void* pass_group_kernel(int cov, int L, int prec);
 cudaError_t launch_pass_batch(int cov, const PassPlan& plan, const BatchArgs& args, cudaStream_t st);
-cudaError_t launch_mtab_build_batch(const double* covparms_b, int nbatch, int q, double* tabs,
-                                    float* tabsf, const int* active, cudaStream_t st);
+// Per-pass coefficient tables (the Matern family, or the exponential families' closed
+// forms for any other cov); the FP32 copy only for the Matern family.
+cudaError_t launch_mtab_build_batch(int cov, const double* covparms_b, int nbatch, int q,
+                                    double* tabs, float* tabsf, const int* active, cudaStream_t st);
 constexpr int VG_MAX_BINS = 64;  // largest number of semivariogram bins
 size_t vario_smem_bytes(int nbins);
 cudaError_t launch_field_moments(const double* Y, int n, int nfields, double* mean, double* var,
@@ -95,7 +97,8 @@ cudaError_t launch_profile_batch(const double* partials, const int* tile_off, in
 
 cudaError_t launch_pass(int cov, const PassPlan& plan, const PassArgs& args, cudaStream_t st);
 cudaError_t launch_init_status(int* status, long long* bad, cudaStream_t st);
-cudaError_t launch_mtab_build(const double* covparms, double* tab, float* tabf, cudaStream_t st);
+cudaError_t launch_mtab_build(int cov, const double* covparms, double* tab, float* tabf,
+                              cudaStream_t st);
 // Loads (under lazy module loading) every kernel the single-dataset FP64 pass can launch.
 cudaError_t load_pass_kernels_f64();
 cudaError_t launch_profile(const double* partials, int nblk, int nstat, int p, int q,

@@ -40,7 +40,8 @@ __constant__ ChebMono c_cheb = ChebMono();
 __global__ void __launch_bounds__(MT_NC * 32) k_mtab_build(const double* __restrict__ covparms,
                                                            double* __restrict__ tab,
                                                            float* __restrict__ tabf, int q,
-                                                           const int* __restrict__ active) {
+                                                           const int* __restrict__ active,
+                                                           int expfam) {
     __shared__ double vals[3][MT_NC];
     __shared__ double cheb[3][MT_NC];
     // blockIdx.y selects the dataset of a batch: its parameters and its tables; datasets
@@ -49,7 +50,8 @@ __global__ void __launch_bounds__(MT_NC * 32) k_mtab_build(const double* __restr
     covparms += (size_t)blockIdx.y * q;
     tab += (size_t)blockIdx.y * MT_DOUBLES;
     if (tabf) tabf += (size_t)blockIdx.y * MT_FLOATS;
-    const double nu = covparms[2];
+    // expfam: the exponential families' table (closed forms, scale sigma2 for all three)
+    const double nu = expfam ? 0.5 : covparms[2];
     if (!(nu >= 0.05 && nu <= 20.0)) return;
     const int it = blockIdx.x;
     const int e = MT_E0 + it / MT_J, j = it % MT_J;
@@ -59,9 +61,16 @@ __global__ void __launch_bounds__(MT_NC * 32) k_mtab_build(const double* __restr
     {
         const double u = cospi((node + 0.5) / MT_NC);
         const double s = ldexp(cen + hw * u, e);
-        const double psi = dev_digamma(nu), lg = lgamma(nu);
         double f0, f1, f2;
-        matern_direct_warp(nu, sqrt(s), psi, lg, f0, f1, f2);
+        if (expfam) {
+            const double x = sqrt(s), e = exp(-x);
+            f0 = e;
+            f1 = x * e;
+            f2 = e / x;
+        } else {
+            const double psi = dev_digamma(nu), lg = lgamma(nu);
+            matern_direct_warp(nu, sqrt(s), psi, lg, f0, f1, f2);
+        }
         if ((threadIdx.x & 31) == 0) { vals[0][node] = f0; vals[1][node] = f1; vals[2][node] = f2; }
     }
     __syncthreads();
@@ -81,7 +90,7 @@ __global__ void __launch_bounds__(MT_NC * 32) k_mtab_build(const double* __restr
         // u = w / hw: the coefficient of w^k is mono / hw^k (an exact power-of-two scaling).
         // F0: w^0, w^1 in FP64, w^2..w^7 as (hi, lo) FP32 pairs, w^8..w^12 in FP32 (see
         // horner_split); F1, F2: w^0..w^7 as pairs, w^8..w^12 in FP32 (see horner_df)
-        const double fsc = (f == 1) ? covparms[0] / covparms[1] : covparms[0];
+        const double fsc = (f == 1 && !expfam) ? covparms[0] / covparms[1] : covparms[0];
         const double v = mono * fsc * ldexp(1.0, k * (MT_LOGJ + 1));
         double* out = tab + (size_t)it * MT_PER_INT + f * MT_FSTRIDE;
         float* tail = reinterpret_cast<float*>(out + MT_NHEAD);
@@ -413,7 +422,7 @@ int plan_pass(int cov, int m, int d, int p, int nsm, int force_L, int force_thre
             if (thr == 256 && force_L <= 0 && L > 16) continue;
             // Matern table in shared memory when it fits (or as forced: force_tab 1 = shared
             // memory only, 0 = global memory, read through L1)
-            bool t = (cov == COV_MATERN) && force_tab != 0;
+            bool t = uses_table(cov, prec) && force_tab != 0;
             size_t b = pass_smem_bytes(cov, m, d, p, L, thr, t, prec, grouped);
             if (b > budget && t && force_tab < 0) {
                 t = false;
@@ -478,9 +487,10 @@ cudaError_t launch_pass_batch(int cov, const PassPlan& plan, const BatchArgs& ar
     return cudaLaunchKernel(fn, dim3(plan.grid), dim3(plan.threads), params, plan.smem, st);
 }
 
-cudaError_t launch_mtab_build_batch(const double* covparms_b, int nbatch, int q, double* tabs,
-                                    float* tabsf, const int* active, cudaStream_t st) {
-    k_mtab_build<<<dim3(MT_NINT, nbatch), MT_NC * 32, 0, st>>>(covparms_b, tabs, tabsf, q, active);
+cudaError_t launch_mtab_build_batch(int cov, const double* covparms_b, int nbatch, int q,
+                                    double* tabs, float* tabsf, const int* active, cudaStream_t st) {
+    k_mtab_build<<<dim3(MT_NINT, nbatch), MT_NC * 32, 0, st>>>(
+        covparms_b, tabs, cov == COV_MATERN ? tabsf : nullptr, q, active, cov == COV_MATERN ? 0 : 1);
     return cudaGetLastError();
 }
 
@@ -519,8 +529,10 @@ cudaError_t launch_init_status(int* status, long long* bad, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_mtab_build(const double* covparms, double* tab, float* tabf, cudaStream_t st) {
-    k_mtab_build<<<MT_NINT, MT_NC * 32, 0, st>>>(covparms, tab, tabf, 4, nullptr);
+cudaError_t launch_mtab_build(int cov, const double* covparms, double* tab, float* tabf,
+                              cudaStream_t st) {
+    k_mtab_build<<<MT_NINT, MT_NC * 32, 0, st>>>(covparms, tab, cov == COV_MATERN ? tabf : nullptr,
+                                                 4, nullptr, cov == COV_MATERN ? 0 : 1);
     return cudaGetLastError();
 }
 

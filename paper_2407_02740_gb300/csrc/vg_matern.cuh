@@ -247,6 +247,30 @@ __device__ __forceinline__ void matern_F12(const double* tab, double s, double n
     }
 }
 
+// The exponential families from a table of the same layout, built in closed form by the
+// same builder: F0 = sigma2 e^-x, F1 = sigma2 x e^-x (rho dC/drho of the isotropic
+// exponential), F2 = sigma2 e^-x / x (the pair weight C / D of the space-time and the
+// per-coordinate ranges families), all at s = x^2 in scaled coordinates.  F0 keeps the
+// FP64 head (horner_split); the weights are double-float (horner_df), like the Matern
+// derivatives.  Below the table the functions are evaluated directly (F2 = 0 for
+// coincident points, where every range derivative vanishes); above it they are 0.
+__device__ __forceinline__ double exp_F0(const double* tab, double s, double sig2) {
+    double w;
+    float wf, wl;
+    const int it = mtab_locate(s, w, wf, wl);
+    if (it >= 0) return horner_split(tab + it * MT_PER_INT, w, wf, wl);
+    if (it == -2) return 0.0;
+    return sig2 * exp(-sqrt(s));
+}
+__device__ __forceinline__ double exp_F12(const double* tab, double s, double sig2, int f) {
+    float wf, wl;
+    const int it = mtab_locate_pair(s, wf, wl);
+    if (it >= 0) return horner_df(tab + it * MT_PER_INT + f * MT_FSTRIDE, wf, wl);
+    if (it == -2 || !(s > 0.0)) return 0.0;
+    const double x = sqrt(s), e = sig2 * exp(-x);
+    return f == 1 ? x * e : e / x;
+}
+
 // F0, F1, F2 at x > 0 by the trapezoid rule (h = 0.1; see the header), for the table
 // builder: the envelope exponent mu t - x cosh t with mu = max(nu, |nu-1|) bounds all three
 // integrands and its maximum Phi is factored out; lane l sums the nodes k = l, l+32, ...,

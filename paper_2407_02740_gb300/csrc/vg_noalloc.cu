@@ -126,7 +126,7 @@ VECCHIA_API vec_status vecchia_loglik_grad_info_noalloc(
     // the status word and failing index restart from zero / "none" on every call; the
     // table and every partial record are rewritten in full by the kernels below
     e = vg::launch_init_status(status, bad, st);
-    if (e == cudaSuccess && cov == vg::COV_MATERN) e = vg::launch_mtab_build(covparms, tab, nullptr, st);
+    if (e == cudaSuccess && vg::uses_table(cov, 0)) e = vg::launch_mtab_build(cov, covparms, tab, nullptr, st);
     if (e != cudaSuccess) return nfail(VEC_ERR_CUDA, "launching the setup kernels: %s", cudaGetErrorString(e));
     vg::PassArgs a;
     a.locs = locs; a.y = y; a.X = X; a.NN = NNarray; a.covparms = covparms;

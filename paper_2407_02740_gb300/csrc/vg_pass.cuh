@@ -271,11 +271,24 @@ template <int L, typename T>
 __device__ __forceinline__ bool ldl_augmented(T* A, T* Yg, double* dg, double* dinv, T* tmp, int Kp,
                                               int naug, int Kmax, int gl, unsigned gmask) {
     using N = Num<T>;
+    constexpr bool F64 = sizeof(T) == 8;
     for (int c = 0; c < Kp; ++c) {
         const double dc = dg[c];
         if (!(dc > 0.0) || !(dc <= 1.7976931348623157e308)) return false;
-        const double ic = rcp_newton(dc);
-        const T icT = N::fromd(ic);
+        // the reciprocal scales the FP32 column with FP32 accuracy on the mixed path (an FP32
+        // reciprocal of the FP64 pivot; only the last pivot's reciprocal is taken again in
+        // FP64, where the values need it)
+        double ic;
+        T icT;
+        if constexpr (F64) {
+            ic = rcp_newton(dc);
+            icT = ic;
+        } else {
+            float r;
+            asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(N::fromd(dc)));
+            icT = r;
+            ic = N::to64(r);
+        }
         if (((c - gl) & (L - 1)) == 0) dinv[c] = ic;
         const int nr = Kp - 1 - c;
         for (int e = gl; e < nr + naug; e += L) {
@@ -291,7 +304,15 @@ __device__ __forceinline__ bool ldl_augmented(T* A, T* Yg, double* dg, double* d
             }
         }
         gsync<L>(gmask);
-        const int ntri = nr * (nr + 1) / 2;
+        // FP64 blocks: the diagonal updates are items of the triangle like the rest; FP32
+        // blocks: the FP64 diagonal updates form their own loop (one FP64 instruction per
+        // L rows, instead of one in nearly every round of the FP32 items), and the items
+        // are the strict lower triangle (row r + 1 of the items is row c + 2 + r)
+        if constexpr (!F64)
+            for (int r = c + 1 + gl; r < Kp; r += L)
+                dg[r] = fma(-N::to64(A[r * (r + 1) / 2 + c]), N::to64(tmp[r]), dg[r]);
+        const int nrt = F64 ? nr : nr - 1;              // rows of the item triangle
+        const int ntri = nrt > 0 ? nrt * (nrt + 1) / 2 : 0;
         int e = gl;
         if (e < ntri) {
             int rr = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
@@ -299,13 +320,13 @@ __device__ __forceinline__ bool ldl_augmented(T* A, T* Yg, double* dg, double* d
             while ((rr + 1) * (rr + 2) / 2 <= e) ++rr;
             int kk = e - rr * (rr + 1) / 2;
             for (; e < ntri; e += L) {
-                const int r = c + 1 + rr;
+                const int r = c + (F64 ? 1 : 2) + rr;
                 T* Ar = A + r * (r + 1) / 2;
                 const T l = Ar[c];
-                if (kk == rr) {
+                const int k = c + 1 + kk;
+                if (F64 && k == r) {
                     dg[r] = fma(-N::to64(l), N::to64(tmp[r]), dg[r]);
                 } else {
-                    const int k = c + 1 + kk;
                     Ar[k] = N::fma_(-l, tmp[k], Ar[k]);
                 }
                 kk += L;
@@ -389,19 +410,29 @@ __device__ __forceinline__ void assemble_block(const PassEnv<T, Tab>& E, int Kp)
                 T t = loc[k * Kmax + a] - loc[k * Kmax + c];
                 s = N::fma_(t, t, s);
             }
-            T x = N::sqrt_(s);
-            T ex = sig2T * N::exp_(-x);
-            C = ex;
-            D1[a * (a - 1) / 2 + c] = ex * x;          // rho dC/drho
+            if constexpr (sizeof(T) == 8) {              // the per-pass table
+                C = exp_F0(tab, s, E.sig2);
+                D1[a * (a - 1) / 2 + c] = exp_F12(tab, s, E.sig2, 1);   // rho dC/drho
+            } else {
+                T x = N::sqrt_(s);
+                T ex = sig2T * N::exp_(-x);
+                C = ex;
+                D1[a * (a - 1) / 2 + c] = ex * x;          // rho dC/drho
+            }
         } else if (COV == COV_ST) {
             T t0 = loc[a] - loc[c];
             T t1 = loc[Kmax + a] - loc[Kmax + c];
             T t2 = loc[2 * Kmax + a] - loc[2 * Kmax + c];
             T uu = N::fma_(t0, t0, N::fma_(t1, t1, t2 * t2));
-            T D = N::sqrt_(uu);
-            T ex = sig2T * N::exp_(-D);
-            C = ex;
-            D1[a * (a - 1) / 2 + c] = D > (T)0 ? ex / D : (T)0;
+            if constexpr (sizeof(T) == 8) {              // the per-pass table
+                C = exp_F0(tab, uu, E.sig2);
+                D1[a * (a - 1) / 2 + c] = exp_F12(tab, uu, E.sig2, 2);  // C / D
+            } else {
+                T D = N::sqrt_(uu);
+                T ex = sig2T * N::exp_(-D);
+                C = ex;
+                D1[a * (a - 1) / 2 + c] = D > (T)0 ? ex / D : (T)0;
+            }
         } else {  // Matern
             T s = (T)0;
             for (int k = 0; k < d; ++k) {
@@ -467,7 +498,8 @@ __device__ __forceinline__ void finish_terms(const PassEnv<T, Tab>& E, int Kp, i
     }
     gsync<L>(gmask);
     // ---------------- per-observation values ----------------
-    const double dK = E.dg[last], idK = E.dinv[last];
+    const double dK = E.dg[last];
+    const double idK = sizeof(T) == 8 ? E.dinv[last] : rcp_newton(dK);
     const double rs = rsqrt_newton(dK);
     const double sq = dK * rs;
     const int vb0 = E.vb0, vstep = E.vstep, vmm = E.vmm;
@@ -776,10 +808,15 @@ __device__ __forceinline__ void vecchia_point_aniso(const PassEnv<T, Tab>& E, lo
             const T t0 = loc[k * Kmax + a] - loc[k * Kmax + c];
             s0 = N::fma_(t0, t0, s0);
         }
-        const T Dd = N::sqrt_(s0 + s1);
-        const T C = E.sig2T * N::exp_(-Dd);
-        D1[a * (a - 1) / 2 + c] = Dd > (T)0 ? C / Dd : (T)0;
-        A[e] = C;
+        if constexpr (sizeof(T) == 8) {                  // the per-pass table
+            A[e] = exp_F0(E.tab, s0 + s1, E.sig2);
+            D1[a * (a - 1) / 2 + c] = exp_F12(E.tab, s0 + s1, E.sig2, 2);   // C / D
+        } else {
+            const T Dd = N::sqrt_(s0 + s1);
+            const T C = E.sig2T * N::exp_(-Dd);
+            D1[a * (a - 1) / 2 + c] = Dd > (T)0 ? C / Dd : (T)0;
+            A[e] = C;
+        }
     }
     gsync<L>(gmask);
 
@@ -859,7 +896,7 @@ __global__ void __launch_bounds__(256, pass_min_blocks(sizeof(T))) k_pass(PassAr
     double* sp = smem;
     const Tab* tab = sizeof(T) == 8 ? reinterpret_cast<const Tab*>(args.mtab)
                                     : reinterpret_cast<const Tab*>(args.mtabf);
-    if (COV == COV_MATERN && args.tab_in_smem) {
+    if (uses_table(COV, sizeof(T) == 8 ? 0 : 1) && args.tab_in_smem) {
         const int nwords = sizeof(T) == 8 ? MT_DOUBLES : (MT_FLOATS + 1) / 2;
         const double* src = sizeof(T) == 8 ? args.mtab : reinterpret_cast<const double*>(args.mtabf);
         for (int t = tid; t < nwords; t += blockDim.x) sp[t] = src[t];
@@ -977,7 +1014,7 @@ __global__ void __launch_bounds__(256, pass_min_blocks(sizeof(T))) k_pass_batch(
 
     double* sp = smem;
     Tab* stab = reinterpret_cast<Tab*>(sp);
-    const int tab_words = (COV == COV_MATERN && args.tab_in_smem)
+    const int tab_words = (uses_table(COV, sizeof(T) == 8 ? 0 : 1) && args.tab_in_smem)
                               ? (sizeof(T) == 8 ? MT_DOUBLES : (MT_FLOATS + 1) / 2) : 0;
     sp += tab_words;
     double* inv_rk = sp;                                   // COV_ANISO: 1 / rho_k, then in T
@@ -1048,7 +1085,7 @@ __global__ void __launch_bounds__(256, pass_min_blocks(sizeof(T))) k_pass_batch(
             E.factor = bargs.factor ? bargs.factor + D.y * (long long)(D.m + 1) : nullptr;
             E.status = bargs.status_b + b;
             E.bad = bargs.bad_b + b;
-            if (COV == COV_MATERN) {
+            if (uses_table(COV, sizeof(T) == 8 ? 0 : 1)) {
                 const Tab* gt = sizeof(T) == 8
                     ? reinterpret_cast<const Tab*>(bargs.tabs + (size_t)b * MT_DOUBLES)
                     : reinterpret_cast<const Tab*>(bargs.tabsf + (size_t)b * MT_FLOATS);

@@ -99,7 +99,7 @@ cudaError_t measure_peaks(int nsm, cudaStream_t st, double* out) {
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&theta), sizeof(double) * 4);
     const double th[4] = {1.3, 0.05, 1.5, 0.05};
     if (e == cudaSuccess) e = cudaMemcpyAsync(theta, th, sizeof(th), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = launch_mtab_build(theta, tab, nullptr, st);
+    if (e == cudaSuccess) e = launch_mtab_build(COV_MATERN, theta, tab, nullptr, st);
     // two blocks of 256 threads per SM: 16 warps, 4 per sub-partition
     const dim3 grid(2 * nsm), block(256);
     const double threads = (double)grid.x * block.x;
