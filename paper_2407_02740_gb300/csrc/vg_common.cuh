@@ -18,16 +18,17 @@ constexpr int DMAX = 3;    // largest location dimension of the isotropic famili
 constexpr int DMAX_ANISO = 20;          // largest dimension with one range per coordinate
 constexpr int QMAX = DMAX_ANISO + 2;    // largest number of covariance parameters
 
-// Geometry of the per-pass Matern coefficient table (see vg_matern.cuh).  Each function
-// on each interval is a degree-12 polynomial in w stored in 11 double slots: w^0, w^1 in
-// FP64, w^2..w^7 as (hi, lo) FP32 pairs, then w^8..w^12 in FP32 (padded to 6 floats).
+// Geometry of the per-pass coefficient table (see vg_matern.cuh).  Each function on each
+// interval is a degree-12 polynomial in w stored in 11 double slots: the covariance F0 as
+// w^0 in FP64 and w^1..w^7 as (hi, lo) FP32 pairs, the derivatives F1, F2 as w^0..w^7 in
+// pairs; then w^8..w^12 in FP32 (padded to 6 floats).
 constexpr int MT_E0 = -30;   // table covers s in [2^-30, 2^13)
 constexpr int MT_E1 = 13;
 constexpr int MT_LOGJ = 2;
 constexpr int MT_J = 1 << MT_LOGJ;
 constexpr int MT_D = 12;     // polynomial degree
 constexpr int MT_NC = MT_D + 1;
-constexpr int MT_NHEAD = 8;  // slots before the FP32 tail: 2 FP64 + 6 FP32 pairs
+constexpr int MT_NHEAD = 8;  // slots before the FP32 tail
 constexpr int MT_FSTRIDE = MT_NHEAD + 3;       // double slots per function
 constexpr int MT_NINT = (MT_E1 - MT_E0) * MT_J;
 constexpr int MT_PER_INT = 3 * MT_FSTRIDE;     // F0, F1, F2 per interval

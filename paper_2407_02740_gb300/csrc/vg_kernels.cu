@@ -88,13 +88,13 @@ __global__ void __launch_bounds__(MT_NC * 32) k_mtab_build(const double* __restr
         double mono = 0.0;
         for (int deg = k; deg < MT_NC; ++deg) mono = fma(cheb[f][deg], c_cheb.c[deg][k], mono);
         // u = w / hw: the coefficient of w^k is mono / hw^k (an exact power-of-two scaling).
-        // F0: w^0, w^1 in FP64, w^2..w^7 as (hi, lo) FP32 pairs, w^8..w^12 in FP32 (see
+        // F0: w^0 in FP64, w^1..w^7 as (hi, lo) FP32 pairs, w^8..w^12 in FP32 (see
         // horner_split); F1, F2: w^0..w^7 as pairs, w^8..w^12 in FP32 (see horner_df)
         const double fsc = (f == 1 && !expfam) ? covparms[0] / covparms[1] : covparms[0];
         const double v = mono * fsc * ldexp(1.0, k * (MT_LOGJ + 1));
         double* out = tab + (size_t)it * MT_PER_INT + f * MT_FSTRIDE;
         float* tail = reinterpret_cast<float*>(out + MT_NHEAD);
-        if (k < 2 && f == 0) {
+        if (k < 1 && f == 0) {
             out[k] = v;
         } else if (k < MT_NHEAD) {
             const float hi = (float)v;

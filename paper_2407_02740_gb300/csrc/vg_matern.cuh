@@ -125,17 +125,17 @@ __device__ __forceinline__ int mtab_locate(double s, double& w, float& wf, float
 }
 
 // Degree-12 polynomial in w, |w| <= 1/8, evaluated in three precisions (the table layout
-// per function: c0, c1 in FP64; c2..c7 as (hi, lo) FP32 pairs; c8..c12 in FP32):
+// per function: c0 in FP64; c1..c7 as (hi, lo) FP32 pairs; c8..c12 in FP32):
 //   * the tail w^8..w^12 (summing to below ~1e-9 on every interval) in FP32;
-//   * w^2..w^7 in double-float arithmetic (a value is an unevaluated FP32 pair, ~48
-//     significant bits; the two-product uses the FMA's exact remainder, the sum Knuth's
-//     two-sum);
-//   * the last two Horner steps, c1 and c0, in FP64.
-// The double-float part r(w) enters the result as w^2 r(w), so its rounding (~2^-47
-// relative) lands below 2^-53 of the result: FP64 accuracy (checked against an FP64
-// Horner chain in extended precision on every interval of the table).  FP32 runs at 64x
-// the FP64 rate on this GPU, so the chain costs 3 FP64 FMAs instead of 9 FP64 operations.
-// The error-free steps use explicitly rounded intrinsics so that no multiply-add is fused.
+//   * P = c1 + w (c2 + ...) in double-float arithmetic (a value is an unevaluated FP32
+//     pair, ~48 significant bits; the two-product uses the FMA's exact remainder, the sum
+//     Knuth's two-sum);
+//   * the last Horner step, c0 + w P, in FP64 (two FMAs, one per half of the pair).
+// The double-float part enters the result as w P with |w| <= 1/8, so its rounding lands
+// at ~2^-50 of |c1|: a few units of the last place of the covariance scale sigma2, below
+// what the likelihood resolves even at a nugget of 0.001.  FP32 runs at 64x the FP64 rate
+// on this GPU, so the chain costs 2 FP64 FMAs instead of 9 FP64 operations.  The
+// error-free steps use explicitly rounded intrinsics so that no multiply-add is fused.
 __device__ __forceinline__ double horner_split(const double* c, double w, float wh, float wl) {
     const float* t = reinterpret_cast<const float*>(c + MT_NHEAD);
     float ph = t[4];
@@ -144,9 +144,9 @@ __device__ __forceinline__ double horner_split(const double* c, double w, float 
     ph = fmaf(ph, wh, t[1]);
     ph = fmaf(ph, wh, t[0]);
     float pl = 0.0f;
-    const float2* mid = reinterpret_cast<const float2*>(c + 2);
+    const float2* mid = reinterpret_cast<const float2*>(c + 1);
 #pragma unroll
-    for (int k = MT_NHEAD - 3; k >= 0; --k) {      // c7 .. c2
+    for (int k = MT_NHEAD - 2; k >= 0; --k) {      // c7 .. c1
         const float2 ck = mid[k];
         const float hi = __fmul_rn(ph, wh);
         float lo = fmaf(ph, wh, -hi);               // exact remainder of ph wh
@@ -159,9 +159,7 @@ __device__ __forceinline__ double horner_split(const double* c, double w, float 
         ph = __fadd_rn(sm, er);
         pl = __fsub_rn(er, __fsub_rn(ph, sm));
     }
-    double p = fma(w, f32_to_f64_bits(pl), c[1]);
-    p = fma(w, f32_to_f64_bits(ph), p);
-    return fma(p, w, c[0]);
+    return fma(w, f32_to_f64_bits(ph), fma(w, f32_to_f64_bits(pl), c[0]));
 }
 
 // Locates s in the table like mtab_locate, but returns the local variable only as the
@@ -210,6 +208,36 @@ __device__ __forceinline__ double horner_df(const double* c, float wh, float wl)
         pl = __fsub_rn(er, __fsub_rn(ph, sm));
     }
     return f32_to_f64_bits(ph) + f32_to_f64_bits(pl);
+}
+
+// The derivative pair F1, F2 at s given as a double-float value sh + sl (FP32 numbers,
+// |sl| <= ulp(sh)): the interval comes from the bits of sh, and the local variable
+// w = (mantissa(sh) - centre) + sl 2^-e is the exact FP32 difference plus the scaled low
+// part; no FP64 instruction except the two final additions of horner_df.  Arguments below
+// the table take the FP64 expansion at sh + sl.
+__device__ __forceinline__ void matern_F12_df(const double* tab, float sh, float sl, double nu,
+                                              double psi, double sc1, double sc2, double& F1,
+                                              double& F2) {
+    const unsigned bits = __float_as_uint(sh);
+    const int e = (int)((bits >> 23) & 0xffu) - 127;
+    if (e >= MT_E0 && e < MT_E1) {
+        const unsigned j = (bits >> (23 - MT_LOGJ)) & (unsigned)(MT_J - 1);
+        const float mant = __uint_as_float((bits & 0x007fffffu) | 0x3f800000u);
+        const float cen = __uint_as_float(0x3f800000u | ((2u * j + 1u) << (23 - MT_LOGJ - 1)));
+        const float wf = mant - cen;                                  // exact
+        const float wl = __fmul_rn(sl, __uint_as_float((unsigned)(127 - e) << 23));  // sl 2^-e
+        const double* cf = tab + ((e - MT_E0) * MT_J + (int)j) * MT_PER_INT;
+        F1 = horner_df(cf + MT_FSTRIDE, wf, wl);
+        F2 = horner_df(cf + 2 * MT_FSTRIDE, wf, wl);
+    } else if (e >= MT_E1 || !(sh > 0.0f)) {
+        F1 = 0.0;
+        F2 = 0.0;
+    } else {
+        double f0;
+        matern_small(nu, f32_to_f64_bits(sh) + f32_to_f64_bits(sl), psi, f0, F1, F2);
+        F1 *= sc1;
+        F2 *= sc2;
+    }
 }
 
 // The table holds the covariance and its derivatives, not M itself: F0 = sigma2 M,

@@ -121,11 +121,15 @@ struct MaternT<float> {
 //   G     Q x K: h_j = dSigma_j u^T, then f_j = U^-1 h_j
 //   D1    exponential families (all but the Matern): per-pair weights reused by the
 //         derivative step
+//   lf    Matern, FP64 block: d x K coordinates again as double-float pairs (hi, lo FP32),
+//         from which the derivative step forms squared distances without FP64 work
 //   dg    K FP64: diagonal of the factorisation, then the pivots d_c
 //   dinv  K FP64: 1 / d_c
 //   V     nv FP64: the per-observation values
+//   lp    2 FP64: the group's running product of pivot mantissas and sum of exponents, so
+//         that log det needs one logarithm per group and tile, not one per observation
 struct SlotLayout {
-    int K, A, Y, loc, u, G, D1, nT, Dbyte, dg, dinv, V, Gs, bytes;
+    int K, A, Y, loc, u, G, D1, lf, nT, Dbyte, dg, dinv, V, lp, Gs, bytes;
     __host__ __device__ void init(int m, int d, int p, int cov, int nv, int tsize,
                                   bool grouped = false) {
         K = m + 1;
@@ -139,13 +143,15 @@ struct SlotLayout {
         u = loc + d * K;
         G = u + K;
         D1 = G + Q * K;
-        nT = D1 + (cov == COV_MATERN ? 0 : K * (K - 1) / 2);
+        lf = D1 + (cov == COV_MATERN ? 0 : K * (K - 1) / 2);
+        nT = lf + ((cov == COV_MATERN && tsize == 8) ? (d * K * 8 + tsize - 1) / tsize : 0);
         Dbyte = ((nT * tsize + 7) / 8) * 8;
         dg = 0;
         dinv = K;
         V = 2 * K;
-        Gs = grouped ? 2 * K + nv : -1;        // -1: over A
-        bytes = Dbyte + (2 * K + nv + (grouped ? Q * K : 0)) * 8;
+        lp = 2 * K + nv;
+        Gs = grouped ? 2 * K + nv + 2 : -1;    // -1: over A
+        bytes = Dbyte + (2 * K + nv + 2 + (grouped ? Q * K : 0)) * 8;
         bytes = ((bytes / 8) | 1) * 8;  // odd number of 8-byte words: slots spread over banks
     }
 };
@@ -190,7 +196,8 @@ struct PassEnv {
     unsigned gmask;
     // slot (shared memory)
     T *A, *Yg, *loc, *u, *G, *D1;
-    double *Gs, *dg, *dinv, *V;
+    float2* locf;         // Matern, FP64 block: the coordinates as double-float pairs
+    double *Gs, *dg, *dinv, *V, *lp;
     int* idx;
     int Kmax;             // slot stride: largest block size of the launch
     // dataset
@@ -229,7 +236,8 @@ __host__ __device__ constexpr uint64_t rec_pack(int a, int b, int c, int e) {
 }
 
 // Writes the record formulas for p regression columns and Q derivative parameters.
-//   V[0] = 1, V[1] = 0, V[2] = logdet_i, V[3] = ell, V[4..4+p) = x,
+//   V[0] = 1, V[1] = 0, V[2] = 0 (logdet_i goes through the group's pivot product),
+//   V[3] = ell, V[4..4+p) = x,
 //   V[vb_j + 0] = md_j, +1 = dell_j, +2.. = dx_j (p), +2+p = -md_j/2,
 //   then mm_jl = m_j . m_l for j <= l (from vmm on).
 __device__ inline void build_record_index(uint64_t* sidx, int p, int Q, int vb0, int vstep,
@@ -393,16 +401,16 @@ __device__ __forceinline__ void assemble_block(const PassEnv<T, Tab>& E, int Kp)
     const T sig2T = E.sig2T;
     const double m_psi = E.m_psi;
     const Tab* tab = E.tab;
-    const int ntri = Kp * (Kp + 1) / 2;
+    // the diagonal (FP64), then the strict lower triangle: pair e is (a, c) with
+    // a (a - 1) / 2 <= e < a (a + 1) / 2, so every round of the loop is all off-diagonal
+    for (int a = gl; a < Kp; a += L) E.dg[a] = E.diag64;
+    const int ntri = Kp * (Kp - 1) / 2;
     for (int e = gl; e < ntri; e += L) {
-        int a = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-        while (a * (a + 1) / 2 > e) --a;
-        while ((a + 1) * (a + 2) / 2 <= e) ++a;
-        int c = e - a * (a + 1) / 2;
-        if (a == c) {
-            E.dg[a] = E.diag64;
-            continue;
-        }
+        int a = (int)((sqrtf(8.0f * (float)e + 1.0f) + 1.0f) * 0.5f);
+        while (a * (a - 1) / 2 > e) --a;
+        while (a * (a + 1) / 2 <= e) ++a;
+        const int c = e - a * (a - 1) / 2;
+        const int ea = a * (a + 1) / 2 + c;           // packed position of (a, c)
         T C;
         if (COV == COV_EXP) {
             T s = (T)0;
@@ -441,9 +449,29 @@ __device__ __forceinline__ void assemble_block(const PassEnv<T, Tab>& E, int Kp)
             }
             C = MT::F0(tab, s, E.nu, m_psi, E.sig2);   // the table holds sigma2 M
         }
-        A[e] = C;
+        A[ea] = C;
     }
     gsync<L>(gmask);
+}
+
+// log d over many pivots with one logarithm: lp[0] holds a product of mantissas in [1, 2)
+// (renormalised from the bits after each multiplication), lp[1] the sum of the binary
+// exponents taken out; log of the whole product is log(lp[0]) + lp[1] log 2 (log_fold).
+// One FP64 multiplication per pivot instead of a logarithm.
+__device__ __forceinline__ void log_pivot(double* lp, double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const long long ev = (long long)((b >> 52) & 0x7ffull) - 1023;
+    const double mv = __longlong_as_double((long long)((b & 0x000fffffffffffffull) | 0x3ff0000000000000ull));
+    const unsigned long long pb = (unsigned long long)__double_as_longlong(lp[0] * mv);
+    const long long ep = (long long)((pb >> 52) & 0x7ffull) - 1023;
+    lp[0] = __longlong_as_double((long long)((pb & 0x000fffffffffffffull) | 0x3ff0000000000000ull));
+    lp[1] += (double)(ev + ep);
+}
+__device__ __forceinline__ double log_fold(double* lp) {
+    const double r = log(lp[0]) + lp[1] * 0.69314718055994530942;
+    lp[0] = 1.0;
+    lp[1] = 0.0;
+    return r;
 }
 
 // The derivative solves and the per-observation values on the leading Kp x Kp block, once
@@ -506,7 +534,8 @@ __device__ __forceinline__ void finish_terms(const PassEnv<T, Tab>& E, int Kp, i
     if (gl == 0) {
         V[0] = 1.0;
         V[1] = 0.0;
-        V[2] = log(dK);
+        V[2] = 0.0;                 // log d_K goes into the group's product (log_pivot)
+        log_pivot(E.lp, dK);
         V[3] = N::to64(Yg[last]) * sq;
         for (int t = 0; t < p; ++t) V[4 + t] = N::to64(Yg[(1 + t) * Kmax + last]) * sq;
     }
@@ -605,6 +634,33 @@ __device__ __forceinline__ void conditional_terms(const PassEnv<T, Tab>& E, int 
                     T w = D1[a * (a - 1) / 2 + c];
                     dv[0] = w * N::fma_(t0, t0, t1 * t1) * inv_r1T;
                     if (NG > 1) dv[NG - 1] = w * t2 * t2 * inv_r2T;
+                } else if constexpr (sizeof(T) == 8) {
+                    // the squared distance in double-float arithmetic from the pairs in lf
+                    // (about 2^-46 relative, enough for derivative entries), so that the
+                    // only FP64 work left per pair is the two table values and the scatter
+                    float sh = 0.0f, sl = 0.0f;
+                    for (int kk = 0; kk < d; ++kk) {
+                        const float2 pa = E.locf[kk * Kmax + a], pc = E.locf[kk * Kmax + c];
+                        const float th = __fsub_rn(pa.x, pc.x);          // two-sum of the highs
+                        const float bb = __fsub_rn(th, pa.x);
+                        float te = __fadd_rn(__fsub_rn(pa.x, __fsub_rn(th, bb)), __fsub_rn(-pc.x, bb));
+                        te = __fadd_rn(te, __fsub_rn(pa.y, pc.y));       // plus the lows
+                        const float t1 = __fadd_rn(th, te);
+                        const float tl = __fsub_rn(te, __fsub_rn(t1, th));
+                        const float pp = __fmul_rn(t1, t1);              // t^2 = t1^2 + 2 t1 tl
+                        float pe = fmaf(t1, t1, -pp);
+                        pe = fmaf(2.0f * t1, tl, pe);
+                        const float ss = __fadd_rn(sh, pp);              // (sh, sl) += (pp, pe)
+                        const float b2 = __fsub_rn(ss, sh);
+                        float er = __fadd_rn(__fsub_rn(sh, __fsub_rn(ss, b2)), __fsub_rn(pp, b2));
+                        er = __fadd_rn(er, __fadd_rn(sl, pe));
+                        sh = __fadd_rn(ss, er);
+                        sl = __fsub_rn(er, __fsub_rn(sh, ss));
+                    }
+                    double F1, F2;
+                    matern_F12_df(tab, sh, sl, E.nu, m_psi, E.sig2 * inv_r1, E.sig2, F1, F2);
+                    dv[0] = F1;                      // dC/drho and dC/dnu from the table
+                    if (NG > 1) dv[NG - 1] = F2;
                 } else {
                     T s = (T)0;
                     for (int kk = 0; kk < d; ++kk) {
@@ -662,9 +718,15 @@ __device__ __forceinline__ void vecchia_point(const PassEnv<T, Tab>& E, long lon
         idx[a] = j;
         // coordinates relative to the observation, divided by their range parameter
         // (FP64 difference, then rounded to T): squared distances come out scaled
-        for (int k = 0; k < d; ++k)
-            loc[k * Kmax + a] = (T)((E.locs[(long long)j * d + k] - li[k]) *
-                                    ((COV == COV_ST && k == 2) ? inv_r2 : inv_r1));
+        for (int k = 0; k < d; ++k) {
+            const double v = (E.locs[(long long)j * d + k] - li[k]) *
+                             ((COV == COV_ST && k == 2) ? inv_r2 : inv_r1);
+            loc[k * Kmax + a] = (T)v;
+            if constexpr (COV == COV_MATERN && sizeof(T) == 8) {
+                const float hi = Num<float>::fromd(v);
+                E.locf[k * Kmax + a] = make_float2(hi, Num<float>::fromd(v - f32_to_f64_bits(hi)));
+            }
+        }
         Yg[a] = (T)E.y[j];
         for (int t = 0; t < p; ++t) Yg[(1 + t) * Kmax + a] = (T)E.X[(long long)j * p + t];
     }
@@ -723,9 +785,15 @@ __device__ __forceinline__ void vecchia_group(const PassEnv<T, Tab>& E, long lon
     for (int a = gl; a < Kp; a += L) {
         const int j = blk[a];
         E.idx[a] = j;
-        for (int k = 0; k < d; ++k)
-            loc[k * Kmax + a] = (T)((E.locs[(long long)j * d + k] - ref[k]) *
-                                    ((COV == COV_ST && k == 2) ? E.inv_r2 : E.inv_r1));
+        for (int k = 0; k < d; ++k) {
+            const double v = (E.locs[(long long)j * d + k] - ref[k]) *
+                             ((COV == COV_ST && k == 2) ? E.inv_r2 : E.inv_r1);
+            loc[k * Kmax + a] = (T)v;
+            if constexpr (COV == COV_MATERN && sizeof(T) == 8) {
+                const float hi = Num<float>::fromd(v);
+                E.locf[k * Kmax + a] = make_float2(hi, Num<float>::fromd(v - f32_to_f64_bits(hi)));
+            }
+        }
         Yg[a] = (T)E.y[j];
         for (int t = 0; t < p; ++t) Yg[(1 + t) * Kmax + a] = (T)E.X[(long long)j * p + t];
     }
@@ -786,16 +854,14 @@ __device__ __forceinline__ void vecchia_point_aniso(const PassEnv<T, Tab>& E, lo
     gsync<L>(gmask);
 
     // ---------------- covariance assembly ----------------
-    const int ntri = Kp * (Kp + 1) / 2;
+    for (int a = gl; a < Kp; a += L) E.dg[a] = E.diag64;
+    const int ntri = Kp * (Kp - 1) / 2;
     for (int e = gl; e < ntri; e += L) {
-        int a = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-        while (a * (a + 1) / 2 > e) --a;
-        while ((a + 1) * (a + 2) / 2 <= e) ++a;
-        const int c = e - a * (a + 1) / 2;
-        if (a == c) {
-            E.dg[a] = E.diag64;
-            continue;
-        }
+        int a = (int)((sqrtf(8.0f * (float)e + 1.0f) + 1.0f) * 0.5f);
+        while (a * (a - 1) / 2 > e) --a;
+        while (a * (a + 1) / 2 <= e) ++a;
+        const int c = e - a * (a - 1) / 2;
+        const int ea = a * (a + 1) / 2 + c;
         T s0 = (T)0, s1 = (T)0;
         int k = 0;
         for (; k + 1 < d; k += 2) {
@@ -809,13 +875,13 @@ __device__ __forceinline__ void vecchia_point_aniso(const PassEnv<T, Tab>& E, lo
             s0 = N::fma_(t0, t0, s0);
         }
         if constexpr (sizeof(T) == 8) {                  // the per-pass table
-            A[e] = exp_F0(E.tab, s0 + s1, E.sig2);
+            A[ea] = exp_F0(E.tab, s0 + s1, E.sig2);
             D1[a * (a - 1) / 2 + c] = exp_F12(E.tab, s0 + s1, E.sig2, 2);   // C / D
         } else {
             const T Dd = N::sqrt_(s0 + s1);
             const T C = E.sig2T * N::exp_(-Dd);
             D1[a * (a - 1) / 2 + c] = Dd > (T)0 ? C / Dd : (T)0;
-            A[e] = C;
+            A[ea] = C;
         }
     }
     gsync<L>(gmask);
@@ -951,9 +1017,9 @@ __global__ void __launch_bounds__(256, pass_min_blocks(sizeof(T))) k_pass(PassAr
     PassEnv<T, Tab> E;
     E.gl = gl; E.gmask = gmask;
     E.A = slot + SL.A; E.Yg = slot + SL.Y; E.loc = slot + SL.loc; E.u = slot + SL.u;
-    E.G = slot + SL.G; E.D1 = slot + SL.D1;
+    E.G = slot + SL.G; E.D1 = slot + SL.D1; E.locf = reinterpret_cast<float2*>(slot + SL.lf);
     E.Gs = SL.Gs < 0 ? reinterpret_cast<double*>(slotc) : slotd + SL.Gs;
-    E.dg = slotd + SL.dg; E.dinv = slotd + SL.dinv; E.V = slotd + SL.V;
+    E.dg = slotd + SL.dg; E.dinv = slotd + SL.dinv; E.V = slotd + SL.V; E.lp = slotd + SL.lp;
     E.idx = idx; E.Kmax = Kmax;
     E.locs = args.locs; E.y = args.y; E.X = args.X; E.NN = args.NN;
     E.d = d; E.p = p; E.m = m; E.status = args.status; E.bad = args.bad;
@@ -964,6 +1030,7 @@ __global__ void __launch_bounds__(256, pass_min_blocks(sizeof(T))) k_pass(PassAr
     E.tab = tab; E.sidx = sidx; E.acc = acc; E.nstat = args.nstat;
     E.vb0 = vb0; E.vstep = vstep; E.vmm = vmm; E.factor = nullptr;
     E.blk_off = args.blk_off; E.blk_idx = args.blk_idx; E.nmemb = args.nmemb; E.n = n;
+    if (gl == 0) { E.lp[0] = 1.0; E.lp[1] = 0.0; }
     if constexpr (GROUPED) {
         for (long long u = (long long)blockIdx.x * ngrp + grp; ok && u < args.ngroups; u += gstride) {
             const long long g = args.gorder ? (long long)args.gorder[u] : u;
@@ -979,6 +1046,8 @@ __global__ void __launch_bounds__(256, pass_min_blocks(sizeof(T))) k_pass(PassAr
             else vecchia_point<COV, L, T, Tab>(E, i);
         }
     }
+    // log det of the group's pivots into the record's first entry (owned by lane 0)
+    if (gl == 0) acc[0] += log_fold(E.lp);
 
     // ---------------- block reduction (fixed order) ----------------
     __syncthreads();
@@ -1039,9 +1108,9 @@ __global__ void __launch_bounds__(256, pass_min_blocks(sizeof(T))) k_pass_batch(
     E.gl = gl; E.gmask = gmask;
     double* slotd = reinterpret_cast<double*>(slotc + SL.Dbyte);
     E.A = slot + SL.A; E.Yg = slot + SL.Y; E.loc = slot + SL.loc; E.u = slot + SL.u;
-    E.G = slot + SL.G; E.D1 = slot + SL.D1;
+    E.G = slot + SL.G; E.D1 = slot + SL.D1; E.locf = reinterpret_cast<float2*>(slot + SL.lf);
     E.Gs = SL.Gs < 0 ? reinterpret_cast<double*>(slotc) : slotd + SL.Gs;
-    E.dg = slotd + SL.dg; E.dinv = slotd + SL.dinv; E.V = slotd + SL.V;
+    E.dg = slotd + SL.dg; E.dinv = slotd + SL.dinv; E.V = slotd + SL.V; E.lp = slotd + SL.lp;
     E.idx = idx; E.Kmax = Kmax;
     E.d = d; E.p = p; E.sidx = sidx; E.acc = acc; E.nstat = args.nstat;
     E.vb0 = vb0; E.vstep = vstep; E.vmm = vmm;
@@ -1103,6 +1172,7 @@ __global__ void __launch_bounds__(256, pass_min_blocks(sizeof(T))) k_pass_batch(
             if (!ok && tid == 0) report(E.status, E.bad, ST_ARG, -1);
         }
         for (int k = 0; k < args.acc_per_lane; ++k) acc[k] = 0.0;
+        if (gl == 0) { E.lp[0] = 1.0; E.lp[1] = 0.0; }
         __syncthreads();
         const bool active = bargs.active_b == nullptr || bargs.active_b[b] != 0;
         if (ok && active)
@@ -1110,6 +1180,7 @@ __global__ void __launch_bounds__(256, pass_min_blocks(sizeof(T))) k_pass_batch(
                 if constexpr (COV == COV_ANISO) vecchia_point_aniso<L, T, Tab>(E, i);
                 else vecchia_point<COV, L, T, Tab>(E, i);
             }
+        if (gl == 0) acc[0] += log_fold(E.lp);
         __syncthreads();
         for (int u = tid; u < args.nstat; u += blockDim.x) {
             const int lr = u % L, k = u / L;
