@@ -298,8 +298,12 @@ def main(argv=None):
     ap.add_argument("--epochs", type=int, default=60)
     ap.add_argument("--eval-fields", type=int, default=64)
     ap.add_argument("--eval-n", type=int, default=200000)
-    ap.add_argument("--out", required=True)
+    ap.add_argument("--out", default=None, help="where to save the trained network")
     ap.add_argument("--report", default=None)
+    ap.add_argument("--evaluate-only", action="store_true",
+                    help="skip training: evaluate the network in --net (default: the shipped "
+                         "one) and add the result to the report under 'evaluation_<fields>'")
+    ap.add_argument("--net", default=None)
     a = ap.parse_args(argv)
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     if root not in sys.path:
@@ -310,6 +314,25 @@ def main(argv=None):
         L = np.random.default_rng(seed).uniform(size=(n, 2))
         L = L[workloads.maxmin_order(L)]
         return make_geometry(L, workloads.ordered_nn(L, m), seed=seed)
+
+    if a.evaluate_only:
+        P, norm = load(a.net)
+        gev = geometry(a.eval_n, a.m, 1006)
+        t0 = time.perf_counter()
+        ev = evaluate(gev, P, norm, a.eval_fields, seed=1007)
+        ev["wall_s"] = time.perf_counter() - t0
+        report = {}
+        if a.report and os.path.exists(a.report):
+            with open(a.report) as f:
+                report = json.load(f)
+        report["evaluation_%d_fields" % a.eval_fields] = ev
+        if a.report:
+            with open(a.report, "w") as f:
+                json.dump(report, f, indent=1)
+        print(json.dumps(ev))
+        return 0
+    if not a.out:
+        ap.error("--out is required unless --evaluate-only is given")
 
     t0 = time.perf_counter()
     gtr = geometry(a.n, a.m, 1005)
