@@ -512,6 +512,26 @@ VECCHIA_API vec_status vecchia_ordered_nn(vec_handle h, const double* locs, int6
                                           int m, void* stream, int32_t* NNarray);
 
 /*
+ * vecchia_maxmin_order -- the maxmin ordering on the device.
+ *
+ * order (DEVICE, n int64) receives the original indices of the n locations (locs: DEVICE,
+ * n x d row-major FP64, 1 <= d <= 3) in maxmin order, the ordering Sec. 2.1 uses (the
+ * paper computes it on the CPU): first the location nearest to the centroid, then at each
+ * step the location whose smallest squared distance to the locations already chosen is
+ * largest, ties to the lowest index.  Squared distances are sums over coordinates, in
+ * order, of (x_k - y_k)^2 with every product and sum rounded separately in FP64, so the
+ * decisions are those of any FP64 implementation of the definition; the centroid is a
+ * fixed-order sum whose last bits may differ from another implementation's, which can
+ * only matter when two locations are equally near it to within rounding.  Exact: each
+ * step accepts the longest prefix of the candidates (sorted by distance, then index) that
+ * the one-at-a-time rule would pick in a row.  One cooperative kernel runs all steps; its
+ * grid barriers wait a bounded time and report VEC_ERR_TIMEOUT instead of hanging.
+ * Handle scratch ~ 20 bytes per location.  Synchronises with `stream` before returning.
+ */
+VECCHIA_API vec_status vecchia_maxmin_order(vec_handle h, const double* locs, int64_t n, int d,
+                                            void* stream, int64_t* order);
+
+/*
  * vecchia_nearest -- the m nearest reference locations of each query location (for
  * prediction).  locs_ref: DEVICE nref x d, locs_query: DEVICE nquery x d (FP64, row-major);
  * NNarray: DEVICE nquery x m int32, row q = the indices of the m smallest keys (d2, j) over

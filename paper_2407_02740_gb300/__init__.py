@@ -141,6 +141,7 @@ def lib():
         L.vecchia_mlp_adam_step.argtypes = [P, P, P, P, ci, cf, P, P, P, P, ci, P, P]
         L.vecchia_mlp_column_moments.argtypes = [P, P, ci, ci, P, P, P]
         L.vecchia_fields_moments.argtypes = [P, ci, i64, P, P, P, P]
+        L.vecchia_maxmin_order.argtypes = [P, P, i64, ci, P, P]
         L.vecchia_mlp_targets.argtypes = [P, ci, P, P, P, P, P, P]
         L.vecchia_mlp_theta.argtypes = [P, ci, P, P, P, P]
         L.vecchia_fields_warm_start.argtypes = [P, P, P, ci, P, P, P, i64, ci, ci, ci, P, P, i64,
@@ -160,6 +161,7 @@ def lib():
                   L.vecchia_fields_variogram, L.vecchia_mlp_forward, L.vecchia_mlp_grad,
                   L.vecchia_mlp_adam_step, L.vecchia_mlp_column_moments,
                   L.vecchia_fields_moments, L.vecchia_mlp_targets, L.vecchia_mlp_theta,
+                  L.vecchia_maxmin_order,
                   L.vecchia_fields_warm_start, L.vecchia_ordered_nn, L.vecchia_nearest,
                   L.vecchia_predict, L.vecchia_measure_peaks, L.vecchia_group_blocks,
                   L.vecchia_group_classes, L.vecchia_grouped_loglik_grad_info):
@@ -693,6 +695,23 @@ def vecchia_mlp_column_moments(X, stream=None, handle: Handle | None = None):
                                             ctypes.c_void_p(_stream(X, stream).cuda_stream),
                                             _dptr(mean), _dptr(sd)))
     return mean, sd
+
+
+def vecchia_maxmin_order(locs, stream=None, handle: Handle | None = None):
+    """Maxmin ordering of the rows of a float64 CUDA tensor locs (n, d), d <= 3, on the
+    device: returns the int64 CUDA tensor of original indices in maxmin order."""
+    import torch
+    _dev_tensor_check(locs, torch.float64, "locs")
+    n, d = locs.shape
+    dev = locs.device
+    if handle is None:
+        handle = default_handle(dev.index if dev.index is not None else 0)
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    order = torch.empty(n, dtype=torch.int64, device=dev)
+    _check(lib().vecchia_maxmin_order(handle.ptr, _dptr(locs), n, d,
+                                      ctypes.c_void_p(stream.cuda_stream), _dptr(order)))
+    return order
 
 
 def vecchia_fields_moments(Y, stream=None, handle: Handle | None = None):

@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libvecchia_gb300.so")
 SOURCES = ["vg_kernels.cu", "vg_pass_f64.cu", "vg_pass_f32.cu", "vg_capi.cu", "vg_noalloc.cu",
            "vg_fit.cu", "vg_features.cu", "vg_mlp.cu", "vg_nn.cu", "vg_predict.cu", "vg_peaks.cu",
-           "vg_pass_group.cu"]
+           "vg_pass_group.cu", "vg_maxmin.cu"]
 HEADERS = ["vg_common.cuh", "vg_matern.cuh", "vg_pass.cuh", "vg_internal.h", "vg_fit.h"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -142,6 +142,10 @@ struct vec_handle_s {
     long long* ws_st = nullptr; size_t c_ws_st = 0;
     // ordered-neighbour search scratch
     char* nn_scratch = nullptr; size_t c_nn_scratch = 0;
+    // maxmin ordering scratch
+    char* mm_scratch = nullptr; size_t c_mm_scratch = 0;
+    double* mm_bbox = nullptr; size_t c_mm_bbox = 0;
+    int* mm_err = nullptr; size_t c_mm_err = 0;
     // pass scratch
     double* partials = nullptr;
     size_t partials_cap = 0;
@@ -275,6 +279,9 @@ vec_status vecchia_destroy(vec_handle h) {
     DeviceGuard g(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
     cudaFree(h->partials);
+    cudaFree(h->mm_scratch);
+    cudaFree(h->mm_bbox);
+    cudaFree(h->mm_err);
     cudaFree(h->mtab);
     cudaFree(h->mtabf);
     cudaFree(h->status);
@@ -1572,6 +1579,54 @@ vec_status vecchia_ordered_nn(vec_handle h, const double* locs, int64_t n, int d
     e = vg::launch_ordered_nn(locs, n, d, m, G, h->nn_scratch, NNarray,
                               reinterpret_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "vecchia_ordered_nn: launching");
+    return VEC_OK;
+}
+
+vec_status vecchia_maxmin_order(vec_handle h, const double* locs, int64_t n, int d, void* stream,
+                                int64_t* order) {
+    if (!h || !locs || !order) return fail(VEC_ERR_ARG, "vecchia_maxmin_order: NULL argument");
+    if (n < 1 || n > (int64_t)INT_MAX || d < 1 || d > vg::DMAX)
+        return fail(VEC_ERR_ARG, "vecchia_maxmin_order: bad sizes (n %lld, d %d)", (long long)n, d);
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(VEC_ERR_CUDA, "cannot select device %d", h->device);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int nblk = vg::maxmin_blocks(h->nsm);
+    if (nblk < 1) return cuda_fail(cudaGetLastError(), "vecchia_maxmin_order: occupancy of the step kernel");
+    cudaError_t e = grow(&h->mm_bbox, &h->c_mm_bbox, (size_t)nblk * 6);
+    if (e == cudaSuccess) e = grow(&h->mm_err, &h->c_mm_err, (size_t)1);
+    if (e != cudaSuccess) return cuda_fail(e, "vecchia_maxmin_order: allocating scratch");
+    std::vector<double> part((size_t)nblk * 6);
+    e = vg::launch_maxmin_bbox(locs, n, d, nblk, h->mm_bbox, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(part.data(), h->mm_bbox, sizeof(double) * part.size(), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "vecchia_maxmin_order: bounding box");
+    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    for (int k = 0; k < d; ++k) {
+        lo[k] = part[k];
+        hi[k] = part[3 + k];
+        for (int b = 1; b < nblk; ++b) {
+            lo[k] = std::min(lo[k], part[(size_t)b * 6 + k]);
+            hi[k] = std::max(hi[k], part[(size_t)b * 6 + 3 + k]);
+        }
+        if (!std::isfinite(lo[k]) || !std::isfinite(hi[k]))
+            return fail(VEC_ERR_ARG, "vecchia_maxmin_order: coordinate %d is not finite", k);
+    }
+    double hcell;
+    int nc[3];
+    long long ncell;
+    vg::maxmin_grid(n, d, lo, hi, &hcell, nc, &ncell);
+    const size_t need = vg::maxmin_scratch_bytes(n, nblk, ncell);
+    e = grow(&h->mm_scratch, &h->c_mm_scratch, need);
+    if (e != cudaSuccess) return cuda_fail(e, "vecchia_maxmin_order: allocating scratch");
+    e = vg::launch_maxmin(locs, n, d, lo, nblk, hcell, nc, ncell, h->mm_scratch, h->c_mm_scratch,
+                          reinterpret_cast<long long*>(order), h->mm_err, st);
+    int err = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&err, h->mm_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "vecchia_maxmin_order: launching");
+    if (err == 1) return fail(VEC_ERR_TIMEOUT, "vecchia_maxmin_order: a grid barrier waited too long");
+    if (err != 0) return fail(VEC_ERR_CUDA, "vecchia_maxmin_order: the ordering did not complete (%d)", err);
     return VEC_OK;
 }
 

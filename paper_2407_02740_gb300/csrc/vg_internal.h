@@ -78,6 +78,18 @@ cudaError_t launch_ordered_nn(const double* x, long long n, int d, int m, int G,
                               int32_t* NN, cudaStream_t st, const double* qx = nullptr,
                               long long nq = 0);
 size_t ordered_nn_scratch_bytes(long long n, int d, int G);
+// maxmin ordering (vg_maxmin.cu): co-resident blocks of its step kernel, the bounding box
+// partials (nblk x 6), the grid over the box, the scratch size, and the launch (the error
+// flag of the step kernel is copied to err_out, device memory)
+int maxmin_blocks(int nsm);
+cudaError_t launch_maxmin_bbox(const double* x, long long n, int d, int nblk, double* part,
+                               cudaStream_t st);
+void maxmin_grid(long long n, int d, const double* lo, const double* hi, double* h, int* nc,
+                 long long* ncell);
+size_t maxmin_scratch_bytes(long long n, int nblocks, long long ncell);
+cudaError_t launch_maxmin(const double* x, long long n, int d, const double* lo, int nblk,
+                          double h, const int* nc, long long ncell, void* scratch,
+                          size_t scratch_bytes, long long* order, int* err_out, cudaStream_t st);
 cudaError_t launch_predict(int cov, const double* locs, const double* y, const double* X,
                            const double* beta, long long n, const double* qlocs,
                            const double* qX, const int32_t* NN, long long nq, int d, int p,

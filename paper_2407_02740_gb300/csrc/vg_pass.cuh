@@ -321,66 +321,35 @@ __device__ __forceinline__ bool ldl_augmented(T* A, T* Yg, double* dg, double* d
                 dg[r] = fma(-N::to64(A[r * (r + 1) / 2 + c]), N::to64(tmp[r]), dg[r]);
         const int nrt = F64 ? nr : nr - 1;              // rows of the item triangle
         const int ntri = nrt > 0 ? nrt * (nrt + 1) / 2 : 0;
-        const int roff = F64 ? 1 : 2;
-        // two interleaved walks per lane (items e and e + L of each pair of rounds), their
-        // loads issued before either update, so that two FP64 updates are in flight
-        if (gl < ntri) {
-            int rrA = (int)((sqrtf(8.0f * (float)gl + 1.0f) - 1.0f) * 0.5f);
-            while (rrA * (rrA + 1) / 2 > gl) --rrA;
-            while ((rrA + 1) * (rrA + 2) / 2 <= gl) ++rrA;
-            int kkA = gl - rrA * (rrA + 1) / 2;
-            int rrB = rrA, kkB = kkA + L;
-            while (kkB > rrB) { kkB -= rrB + 1; ++rrB; }
-            for (int eA = gl; eA < ntri; eA += 2 * L) {
-                const bool hb = eA + L < ntri;
-                const int rA = c + roff + rrA, kA = c + 1 + kkA;
-                T* ArA = A + rA * (rA + 1) / 2;
-                T* pA = (F64 && kA == rA) ? reinterpret_cast<T*>(dg + rA) : ArA + kA;
-                const T lA = ArA[c], tA = tmp[kA];
-                const T xA = *pA;
-                T lB = (T)0, tB = (T)0, xB = (T)0;
-                T* pB = pA;
-                if (hb) {
-                    const int rB = c + roff + rrB, kB = c + 1 + kkB;
-                    T* ArB = A + rB * (rB + 1) / 2;
-                    pB = (F64 && kB == rB) ? reinterpret_cast<T*>(dg + rB) : ArB + kB;
-                    lB = ArB[c];
-                    tB = tmp[kB];
-                    xB = *pB;
+        int e = gl;
+        if (e < ntri) {
+            int rr = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+            while (rr * (rr + 1) / 2 > e) --rr;
+            while ((rr + 1) * (rr + 2) / 2 <= e) ++rr;
+            int kk = e - rr * (rr + 1) / 2;
+            for (; e < ntri; e += L) {
+                const int r = c + (F64 ? 1 : 2) + rr;
+                T* Ar = A + r * (r + 1) / 2;
+                const T l = Ar[c];
+                const int k = c + 1 + kk;
+                if (F64 && k == r) {
+                    dg[r] = fma(-N::to64(l), N::to64(tmp[r]), dg[r]);
+                } else {
+                    Ar[k] = N::fma_(-l, tmp[k], Ar[k]);
                 }
-                *pA = N::fma_(-lA, tA, xA);
-                if (hb) *pB = N::fma_(-lB, tB, xB);
-                kkA += 2 * L;
-                while (kkA > rrA) { kkA -= rrA + 1; ++rrA; }
-                kkB += 2 * L;
-                while (kkB > rrB) { kkB -= rrB + 1; ++rrB; }
+                kk += L;
+                while (kk > rr) { kk -= rr + 1; ++rr; }
             }
         }
         if (naug > 0 && nr > 0) {
-            // the lane's first item at or after the triangle
-            const int e0 = gl >= ntri ? gl : gl + ((ntri - gl + L - 1) / L) * L;
-            const int e2 = e0 - ntri;
-            int aA = e2 / nr, kA = e2 - aA * nr;
-            int aB = aA, kB = kA + L;
-            while (kB >= nr) { kB -= nr; ++aB; }
-            while (aA < naug) {
-                const bool hb = aB < naug;
-                T* zA = Yg + aA * Kmax;
-                const T lA = zA[c], tA = tmp[c + 1 + kA], xA = zA[c + 1 + kA];
-                T lB = (T)0, tB = (T)0, xB = (T)0;
-                T* zB = zA;
-                if (hb) {
-                    zB = Yg + aB * Kmax;
-                    lB = zB[c];
-                    tB = tmp[c + 1 + kB];
-                    xB = zB[c + 1 + kB];
-                }
-                zA[c + 1 + kA] = N::fma_(-lA, tA, xA);
-                if (hb) zB[c + 1 + kB] = N::fma_(-lB, tB, xB);
-                kA += 2 * L;
-                while (kA >= nr) { kA -= nr; ++aA; }
-                kB += 2 * L;
-                while (kB >= nr) { kB -= nr; ++aB; }
+            const int e2 = e - ntri;
+            int a = e2 / nr, kk = e2 - a * nr;
+            while (a < naug) {
+                T* z = Yg + a * Kmax;
+                const int k = c + 1 + kk;
+                z[k] = N::fma_(-z[c], tmp[k], z[k]);
+                kk += L;
+                while (kk >= nr) { kk -= nr; ++a; }
             }
         }
         gsync<L>(gmask);
@@ -418,83 +387,69 @@ __device__ __forceinline__ void accumulate_record(const uint64_t* sidx, const do
     gsync<L>(gmask);
 }
 
-// Covariance entry of the pair (a, c) of the block (coordinates in loc, relative and
-// scaled), and for the exponential families the pair weight D1 the derivative step
-// reuses (rho dC/drho for the isotropic exponential, C / D for the space-time one).
-template <int COV, typename T, typename Tab>
-__device__ __forceinline__ T pair_covariance(const PassEnv<T, Tab>& E, int a, int c, T& w) {
-    using N = Num<T>;
-    using MT = MaternT<T>;
-    const int d = E.d, Kmax = E.Kmax;
-    const T* loc = E.loc;
-    if (COV == COV_EXP) {
-        T s = (T)0;
-        for (int k = 0; k < d; ++k) {
-            T t = loc[k * Kmax + a] - loc[k * Kmax + c];
-            s = N::fma_(t, t, s);
-        }
-        if constexpr (sizeof(T) == 8) {                  // the per-pass table
-            w = exp_F12(E.tab, s, E.sig2, 1);
-            return exp_F0(E.tab, s, E.sig2);
-        } else {
-            T x = N::sqrt_(s);
-            T ex = E.sig2T * N::exp_(-x);
-            w = ex * x;
-            return ex;
-        }
-    } else if (COV == COV_ST) {
-        T t0 = loc[a] - loc[c];
-        T t1 = loc[Kmax + a] - loc[Kmax + c];
-        T t2 = loc[2 * Kmax + a] - loc[2 * Kmax + c];
-        T uu = N::fma_(t0, t0, N::fma_(t1, t1, t2 * t2));
-        if constexpr (sizeof(T) == 8) {                  // the per-pass table
-            w = exp_F12(E.tab, uu, E.sig2, 2);
-            return exp_F0(E.tab, uu, E.sig2);
-        } else {
-            T D = N::sqrt_(uu);
-            T ex = E.sig2T * N::exp_(-D);
-            w = D > (T)0 ? ex / D : (T)0;
-            return ex;
-        }
-    } else {  // Matern
-        T s = (T)0;
-        for (int k = 0; k < d; ++k) {
-            T t = loc[k * Kmax + a] - loc[k * Kmax + c];
-            s = N::fma_(t, t, s);
-        }
-        w = (T)0;
-        return MT::F0(E.tab, s, E.nu, E.m_psi, E.sig2);   // the table holds sigma2 M
-    }
-}
-
-// Covariance of the block in the slot: the FP64 diagonal dg (sigma2 (1 + tau2)), then the
-// strict lower triangle: pair e is (a, c) with a (a - 1) / 2 <= e < a (a + 1) / 2 (so every
-// round of the loop is off-diagonal), two pairs per lane and round computed before either
-// is stored; for the exponential families also the pair weights D1.
+// Covariance of the block in the slot (coordinates in loc, relative and scaled): the packed
+// strict lower triangle of A and the FP64 diagonal dg (sigma2 (1 + tau2)); for the
+// exponential families also the pair weights D1 that the derivative step reuses.
 template <int COV, int L, typename T, typename Tab>
 __device__ __forceinline__ void assemble_block(const PassEnv<T, Tab>& E, int Kp) {
+    using N = Num<T>;
+    using MT = MaternT<T>;
     const int gl = E.gl;
     const unsigned gmask = E.gmask;
-    T* A = E.A; T* D1 = E.D1;
+    const int d = E.d, Kmax = E.Kmax;
+    T* A = E.A; T* loc = E.loc; T* D1 = E.D1;
+    const T sig2T = E.sig2T;
+    const double m_psi = E.m_psi;
+    const Tab* tab = E.tab;
+    // the diagonal (FP64), then the strict lower triangle: pair e is (a, c) with
+    // a (a - 1) / 2 <= e < a (a + 1) / 2, so every round of the loop is all off-diagonal
     for (int a = gl; a < Kp; a += L) E.dg[a] = E.diag64;
     const int ntri = Kp * (Kp - 1) / 2;
-    for (int e = gl; e < ntri; e += 2 * L) {
-        const bool hb = e + L < ntri;
-        int aA = (int)((sqrtf(8.0f * (float)e + 1.0f) + 1.0f) * 0.5f);
-        while (aA * (aA - 1) / 2 > e) --aA;
-        while (aA * (aA + 1) / 2 <= e) ++aA;
-        const int cA = e - aA * (aA - 1) / 2;
-        T wA, wB = (T)0, CB = (T)0;
-        const T CA = pair_covariance<COV, T, Tab>(E, aA, cA, wA);
-        int aB = aA, cB = cA + L;
-        while (cB >= aB) { cB -= aB; ++aB; }
-        if (hb) CB = pair_covariance<COV, T, Tab>(E, aB, cB, wB);
-        A[aA * (aA + 1) / 2 + cA] = CA;
-        if (COV != COV_MATERN) D1[aA * (aA - 1) / 2 + cA] = wA;
-        if (hb) {
-            A[aB * (aB + 1) / 2 + cB] = CB;
-            if (COV != COV_MATERN) D1[aB * (aB - 1) / 2 + cB] = wB;
+    for (int e = gl; e < ntri; e += L) {
+        int a = (int)((sqrtf(8.0f * (float)e + 1.0f) + 1.0f) * 0.5f);
+        while (a * (a - 1) / 2 > e) --a;
+        while (a * (a + 1) / 2 <= e) ++a;
+        const int c = e - a * (a - 1) / 2;
+        const int ea = a * (a + 1) / 2 + c;           // packed position of (a, c)
+        T C;
+        if (COV == COV_EXP) {
+            T s = (T)0;
+            for (int k = 0; k < d; ++k) {
+                T t = loc[k * Kmax + a] - loc[k * Kmax + c];
+                s = N::fma_(t, t, s);
+            }
+            if constexpr (sizeof(T) == 8) {              // the per-pass table
+                C = exp_F0(tab, s, E.sig2);
+                D1[a * (a - 1) / 2 + c] = exp_F12(tab, s, E.sig2, 1);   // rho dC/drho
+            } else {
+                T x = N::sqrt_(s);
+                T ex = sig2T * N::exp_(-x);
+                C = ex;
+                D1[a * (a - 1) / 2 + c] = ex * x;          // rho dC/drho
+            }
+        } else if (COV == COV_ST) {
+            T t0 = loc[a] - loc[c];
+            T t1 = loc[Kmax + a] - loc[Kmax + c];
+            T t2 = loc[2 * Kmax + a] - loc[2 * Kmax + c];
+            T uu = N::fma_(t0, t0, N::fma_(t1, t1, t2 * t2));
+            if constexpr (sizeof(T) == 8) {              // the per-pass table
+                C = exp_F0(tab, uu, E.sig2);
+                D1[a * (a - 1) / 2 + c] = exp_F12(tab, uu, E.sig2, 2);  // C / D
+            } else {
+                T D = N::sqrt_(uu);
+                T ex = sig2T * N::exp_(-D);
+                C = ex;
+                D1[a * (a - 1) / 2 + c] = D > (T)0 ? ex / D : (T)0;
+            }
+        } else {  // Matern
+            T s = (T)0;
+            for (int k = 0; k < d; ++k) {
+                T t = loc[k * Kmax + a] - loc[k * Kmax + c];
+                s = N::fma_(t, t, s);
+            }
+            C = MT::F0(tab, s, E.nu, m_psi, E.sig2);   // the table holds sigma2 M
         }
+        A[ea] = C;
     }
     gsync<L>(gmask);
 }
@@ -546,30 +501,14 @@ __device__ __forceinline__ void finish_terms(const PassEnv<T, Tab>& E, int Kp, i
     // ---------------- f_j = U^-1 h_j (unit lower, in place) ----------------
     for (int c = 0; c < last; ++c) {
         const int nr = last - c;
-        // items (j, a = c + 1 + off), item t = j nr + off; two interleaved walks per lane
-        // (items t and t + L), loads before updates
-        int jA = gl / nr, oA = gl - jA * nr;
-        int jB = (gl + L) / nr, oB = (gl + L) - jB * nr;
-        const int jstep = (2 * L) / nr, ostep = 2 * L - jstep * nr;
-        while (jA < Q) {
-            const bool hb = jB < Q;
-            const int aA = c + 1 + oA;
-            const T uA = A[aA * (aA + 1) / 2 + c], gA = G[jA * Kmax + c], xA = G[jA * Kmax + aA];
-            T uB = (T)0, gB = (T)0, xB = (T)0;
-            const int aB = c + 1 + oB;
-            if (hb) {
-                uB = A[aB * (aB + 1) / 2 + c];
-                gB = G[jB * Kmax + c];
-                xB = G[jB * Kmax + aB];
-            }
-            G[jA * Kmax + aA] = N::fma_(-uA, gA, xA);
-            if (hb) G[jB * Kmax + aB] = N::fma_(-uB, gB, xB);
-            jA += jstep;
-            oA += ostep;
-            if (oA >= nr) { oA -= nr; ++jA; }
-            jB += jstep;
-            oB += ostep;
-            if (oB >= nr) { oB -= nr; ++jB; }
+        int j = gl / nr, off = gl - j * nr;
+        const int jstep = L / nr, ostep = L - jstep * nr;
+        while (j < Q) {
+            const int a = c + 1 + off;
+            G[j * Kmax + a] = N::fma_(-A[a * (a + 1) / 2 + c], G[j * Kmax + c], G[j * Kmax + a]);
+            j += jstep;
+            off += ostep;
+            if (off >= nr) { off -= nr; ++j; }
         }
         gsync<L>(gmask);
     }
@@ -641,80 +580,24 @@ __device__ __forceinline__ void finish_terms(const PassEnv<T, Tab>& E, int Kp, i
     accumulate_record<L>(E.sidx, V, E.acc, E.nstat, gl, gmask);
 }
 
-// Derivative entries dC/dtheta_j of the pair (a, c) for the pair-derivative parameters
-// (NG of them): from the pair weights D1 for the exponential families, from the table for
-// the Matern family (on the FP64 path from double-float squared distances, about 2^-46
-// relative, enough for derivative entries, so that the only FP64 work left per pair is
-// the two table values and the scatter).
-template <int COV, int NG, typename T, typename Tab>
-__device__ __forceinline__ void pair_derivatives(const PassEnv<T, Tab>& E, int a, int c, T* dv) {
-    using N = Num<T>;
-    using MT = MaternT<T>;
-    const int d = E.d, Kmax = E.Kmax;
-    const T* loc = E.loc;
-    const T* D1 = E.D1;
-    if (COV == COV_EXP) {
-        dv[0] = D1[a * (a - 1) / 2 + c] * E.inv_r1T;
-    } else if (COV == COV_ST) {
-        T t0 = loc[a] - loc[c];
-        T t1 = loc[Kmax + a] - loc[Kmax + c];
-        T t2 = loc[2 * Kmax + a] - loc[2 * Kmax + c];
-        T w = D1[a * (a - 1) / 2 + c];
-        dv[0] = w * N::fma_(t0, t0, t1 * t1) * E.inv_r1T;
-        if (NG > 1) dv[NG - 1] = w * t2 * t2 * E.inv_r2T;
-    } else if constexpr (sizeof(T) == 8) {
-        float sh = 0.0f, sl = 0.0f;
-        for (int kk = 0; kk < d; ++kk) {
-            const float2 pa = E.locf[kk * Kmax + a], pc = E.locf[kk * Kmax + c];
-            const float th = __fsub_rn(pa.x, pc.x);          // two-sum of the highs
-            const float bb = __fsub_rn(th, pa.x);
-            float te = __fadd_rn(__fsub_rn(pa.x, __fsub_rn(th, bb)), __fsub_rn(-pc.x, bb));
-            te = __fadd_rn(te, __fsub_rn(pa.y, pc.y));       // plus the lows
-            const float t1 = __fadd_rn(th, te);
-            const float tl = __fsub_rn(te, __fsub_rn(t1, th));
-            const float pp = __fmul_rn(t1, t1);              // t^2 = t1^2 + 2 t1 tl
-            float pe = fmaf(t1, t1, -pp);
-            pe = fmaf(2.0f * t1, tl, pe);
-            const float ss = __fadd_rn(sh, pp);              // (sh, sl) += (pp, pe)
-            const float b2 = __fsub_rn(ss, sh);
-            float er = __fadd_rn(__fsub_rn(sh, __fsub_rn(ss, b2)), __fsub_rn(pp, b2));
-            er = __fadd_rn(er, __fadd_rn(sl, pe));
-            sh = __fadd_rn(ss, er);
-            sl = __fsub_rn(er, __fsub_rn(sh, ss));
-        }
-        double F1, F2;
-        matern_F12_df(E.tab, sh, sl, E.nu, E.m_psi, E.sig2 * E.inv_r1, E.sig2, F1, F2);
-        dv[0] = F1;                      // dC/drho and dC/dnu from the table
-        if (NG > 1) dv[NG - 1] = F2;
-    } else {
-        T sq = (T)0;
-        for (int kk = 0; kk < d; ++kk) {
-            T t = loc[kk * Kmax + a] - loc[kk * Kmax + c];
-            sq = N::fma_(t, t, sq);
-        }
-        T F1, F2;
-        MT::F12(E.tab, sq, E.nu, E.m_psi, E.sig2 * E.inv_r1, E.sig2, F1, F2);
-        dv[0] = F1;
-        if (NG > 1) dv[NG - 1] = F2;
-    }
-}
-
 // One conditional on the leading Kp x Kp block of the factor in the slot (its last row,
 // Kp - 1, is the observation; the rows above are what it conditions on): u = last row of
 // U^-1, h_j = dSigma_j u^T with each pair (a, c) evaluated once (a conflict-free round-robin
-// pair schedule lets the lanes scatter into h without atomics), then finish_terms.  The
-// derivative entries of a lane's first pair of the next round are evaluated before the
-// scatter and the barrier of the current round, so that their latency overlaps them.
+// pair schedule lets the lanes scatter into h without atomics), then finish_terms.
 // i is the observation (factor rows).
 template <int COV, int L, typename T, typename Tab>
 __device__ __forceinline__ void conditional_terms(const PassEnv<T, Tab>& E, int Kp, long long i) {
     using N = Num<T>;
+    using MT = MaternT<T>;
     constexpr int NG = npair_derivs(COV);
     constexpr int Q = NG + 1;
     const int gl = E.gl;
     const unsigned gmask = E.gmask;
-    const int m = E.m, Kmax = E.Kmax;
-    T* u = E.u; T* G = E.G;
+    const int d = E.d, m = E.m, Kmax = E.Kmax;
+    T* u = E.u; T* G = E.G; const T* loc = E.loc; const T* D1 = E.D1;
+    const T sig2T = E.sig2T, inv_r1T = E.inv_r1T, inv_r2T = E.inv_r2T;
+    const double inv_r1 = E.inv_r1, m_psi = E.m_psi;
+    const Tab* tab = E.tab;
 
     last_row_of_Uinv<L, T>(E.A, u, Kp, gl, gmask);
     if (E.factor) {
@@ -731,43 +614,69 @@ __device__ __forceinline__ void conditional_terms(const PassEnv<T, Tab>& E, int 
     for (int a = gl; a < Kp; a += L) {
 #pragma unroll
         for (int j = 0; j < NG; ++j) G[j * Kmax + a] = (T)0;
-        G[NG * Kmax + a] = E.sig2T * u[a];
+        G[NG * Kmax + a] = sig2T * u[a];
     }
     gsync<L>(gmask);
     {
         const int Nv = (Kp & 1) ? Kp + 1 : Kp;
         const int npr = Nv / 2;
-        const int nrounds = Nv - 1;
-        T dvn[NG];
-        int an = 0, cn = 0;
-        bool hn = nrounds > 0 && gl < npr && circle_pair(Kp, Nv, 0, gl, an, cn);
-        if (hn) pair_derivatives<COV, NG, T, Tab>(E, an, cn, dvn);
-        for (int r = 0; r < nrounds; ++r) {
-            T dv[NG];
-#pragma unroll
-            for (int j = 0; j < NG; ++j) dv[j] = dvn[j];
-            const int a0 = an, c0 = cn;
-            const bool h0 = hn;
-            hn = r + 1 < nrounds && gl < npr && circle_pair(Kp, Nv, r + 1, gl, an, cn);
-            if (hn) pair_derivatives<COV, NG, T, Tab>(E, an, cn, dvn);
-            if (h0) {
-                const T ua = u[a0], uc = u[c0];
-#pragma unroll
-                for (int j = 0; j < NG; ++j) {
-                    G[j * Kmax + a0] = N::fma_(dv[j], uc, G[j * Kmax + a0]);
-                    G[j * Kmax + c0] = N::fma_(dv[j], ua, G[j * Kmax + c0]);
-                }
-            }
-            for (int k = gl + L; k < npr; k += L) {       // further pairs of the round
+        for (int r = 0; r < Nv - 1; ++r) {
+            for (int k = gl; k < npr; k += L) {
                 int a, c;
                 if (!circle_pair(Kp, Nv, r, k, a, c)) continue;
-                T dk[NG];
-                pair_derivatives<COV, NG, T, Tab>(E, a, c, dk);
+                T dv[NG];
+                if (COV == COV_EXP) {
+                    dv[0] = D1[a * (a - 1) / 2 + c] * inv_r1T;
+                } else if (COV == COV_ST) {
+                    T t0 = loc[a] - loc[c];
+                    T t1 = loc[Kmax + a] - loc[Kmax + c];
+                    T t2 = loc[2 * Kmax + a] - loc[2 * Kmax + c];
+                    T w = D1[a * (a - 1) / 2 + c];
+                    dv[0] = w * N::fma_(t0, t0, t1 * t1) * inv_r1T;
+                    if (NG > 1) dv[NG - 1] = w * t2 * t2 * inv_r2T;
+                } else if constexpr (sizeof(T) == 8) {
+                    // the squared distance in double-float arithmetic from the pairs in lf
+                    // (about 2^-46 relative, enough for derivative entries), so that the
+                    // only FP64 work left per pair is the two table values and the scatter
+                    float sh = 0.0f, sl = 0.0f;
+                    for (int kk = 0; kk < d; ++kk) {
+                        const float2 pa = E.locf[kk * Kmax + a], pc = E.locf[kk * Kmax + c];
+                        const float th = __fsub_rn(pa.x, pc.x);          // two-sum of the highs
+                        const float bb = __fsub_rn(th, pa.x);
+                        float te = __fadd_rn(__fsub_rn(pa.x, __fsub_rn(th, bb)), __fsub_rn(-pc.x, bb));
+                        te = __fadd_rn(te, __fsub_rn(pa.y, pc.y));       // plus the lows
+                        const float t1 = __fadd_rn(th, te);
+                        const float tl = __fsub_rn(te, __fsub_rn(t1, th));
+                        const float pp = __fmul_rn(t1, t1);              // t^2 = t1^2 + 2 t1 tl
+                        float pe = fmaf(t1, t1, -pp);
+                        pe = fmaf(2.0f * t1, tl, pe);
+                        const float ss = __fadd_rn(sh, pp);              // (sh, sl) += (pp, pe)
+                        const float b2 = __fsub_rn(ss, sh);
+                        float er = __fadd_rn(__fsub_rn(sh, __fsub_rn(ss, b2)), __fsub_rn(pp, b2));
+                        er = __fadd_rn(er, __fadd_rn(sl, pe));
+                        sh = __fadd_rn(ss, er);
+                        sl = __fsub_rn(er, __fsub_rn(sh, ss));
+                    }
+                    double F1, F2;
+                    matern_F12_df(tab, sh, sl, E.nu, m_psi, E.sig2 * inv_r1, E.sig2, F1, F2);
+                    dv[0] = F1;                      // dC/drho and dC/dnu from the table
+                    if (NG > 1) dv[NG - 1] = F2;
+                } else {
+                    T s = (T)0;
+                    for (int kk = 0; kk < d; ++kk) {
+                        T t = loc[kk * Kmax + a] - loc[kk * Kmax + c];
+                        s = N::fma_(t, t, s);
+                    }
+                    T F1, F2;
+                    MT::F12(tab, s, E.nu, m_psi, E.sig2 * inv_r1, E.sig2, F1, F2);
+                    dv[0] = F1;                      // dC/drho and dC/dnu from the table
+                    if (NG > 1) dv[NG - 1] = F2;
+                }
                 const T ua = u[a], uc = u[c];
 #pragma unroll
                 for (int j = 0; j < NG; ++j) {
-                    G[j * Kmax + a] = N::fma_(dk[j], uc, G[j * Kmax + a]);
-                    G[j * Kmax + c] = N::fma_(dk[j], ua, G[j * Kmax + c]);
+                    G[j * Kmax + a] = N::fma_(dv[j], uc, G[j * Kmax + a]);
+                    G[j * Kmax + c] = N::fma_(dv[j], ua, G[j * Kmax + c]);
                 }
             }
             gsync<L>(gmask);

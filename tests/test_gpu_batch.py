@@ -13,15 +13,21 @@ pytestmark = pytest.mark.gpu
 
 import paper_2407_02740_gb300 as vg  # noqa: E402
 
-# error bounds of the mixed path against FP64 at nugget tau2 >= 0.05 (the single-dataset
-# mixed tests); the FP32 covariance entries carry relative errors of ~6e-8, which the
-# block's conditioning (~(1 + tau2) / tau2 for correlated neighbours) amplifies, so below
-# tau2 = 0.05 every bound is scaled by 0.05 / tau2
+# error bounds of the mixed path (FP32 entries and trailing updates, FP64 pivots and
+# per-observation dot products) against FP64, by nugget band: the FP32 covariance entries
+# and the FP32 factor of the neighbours' block carry relative errors of ~1e-7, which the
+# block's conditioning (~(1 + tau2) / tau2 for correlated neighbours) amplifies; the FP64
+# pivots keep that amplification well below 1 / tau2 (measured worst cases at tau2 = 0.001:
+# loglik 2e-6, gradient 3.3e-4, information 2.9e-5, betahat 6.9e-5)
 MIXED_BOUNDS = {"loglik": 1e-6, "grad": 2e-4, "info": 2e-5, "beta": 5e-6}
 
 
-def mixed_scale(tau2):
-    return max(1.0, 0.05 / tau2)
+def mixed_bounds(tau2):
+    if tau2 >= 0.05:
+        return MIXED_BOUNDS
+    if tau2 >= 0.01:
+        return dict(MIXED_BOUNDS, beta=5e-5)
+    return {"loglik": 1e-5, "grad": 1e-3, "info": 1e-4, "beta": 2e-4}
 
 
 def _dev(a, dt):
@@ -108,9 +114,9 @@ def test_batch_mixed_within_bounds_of_fp64():
         for b in range(bw.nbatch):
             err = _rel_errors(vg.unpack(omx[b], 4, 1), vg.unpack(o64[b], 4, 1),
                               bw.offsets[b + 1] - bw.offsets[b])
-            f = mixed_scale(bw.theta_true[b, 3])
-            for k, bound in MIXED_BOUNDS.items():
-                assert err[k] <= bound * f, (b, k, f, err)
+            bounds = mixed_bounds(bw.theta_true[b, 3])
+            for k, bound in bounds.items():
+                assert err[k] <= bound, (b, k, bw.theta_true[b, 3], err)
     finally:
         h.close()
 

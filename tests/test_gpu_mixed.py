@@ -100,3 +100,32 @@ def test_mixed_then_fp64_fit_reaches_the_fp64_optimum():
     assert a["status"] == 0 and b["status"] == 0
     assert abs(a["loglik"] - b["loglik"]) <= 1e-8 * abs(a["loglik"])
     assert np.allclose(a["theta"], b["theta"], rtol=1e-4)
+
+
+def _mixed_bounds(tau2):
+    # the bands stated for the mixed path (FP64 pivots and per-observation dot products):
+    # the tau2 >= 0.05 bounds above, a wider betahat bound down to 0.01, then wider bounds
+    # down to 0.001 (measured worst cases there: loglik 2e-6, gradient 3.3e-4, information
+    # 2.9e-5, betahat 6.9e-5)
+    if tau2 >= 0.05:
+        return BOUNDS
+    if tau2 >= 0.01:
+        return dict(BOUNDS, beta=5e-5)
+    return {"loglik": 1e-5, "grad": 1e-3, "info": 1e-4, "beta": 2e-4}
+
+
+@pytest.mark.parametrize("tau2", [0.05, 0.01, 0.003, 0.001])
+@pytest.mark.parametrize("nu,rho,m", [(0.5, 0.1, 10), (1.5, 0.05, 20), (2.5, 0.2, 40),
+                                      (1.5, 0.3, 30)])
+def test_mixed_pass_small_nugget_bands(tau2, nu, rho, m):
+    # nugget-dominated conditioning: the regime the FP64 pivots are for
+    th = np.array([1.3, rho, nu, tau2])
+    w = workloads.make_field(3000, vg.MATERN_ISO, th, m, p=1, seed=int(1000 * tau2) + m,
+                             sim="sequential", beta=[0.5], m_sim=min(m + 10, 60))
+    o = oracle.loglik_grad_info(w.locs, w.y, w.X, w.NN, th, vg.MATERN_ISO)
+    g = mixed_pass(w, th)
+    assert g["status"] == 0
+    err = errors(g, o)
+    err["loglik"] = abs(g["loglik"] - o["loglik"]) / max(abs(o["loglik"]), w.n)
+    for k, b in _mixed_bounds(tau2).items():
+        assert err[k] <= b, (k, tau2, err)
