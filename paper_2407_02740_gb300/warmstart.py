@@ -226,11 +226,12 @@ def predict_theta(params, norm, feats, Y):
 
 
 def evaluate(geom: Geometry, params, norm, nfields: int, seed: int = 3, prec: str = "fp64",
-             decide_prec: str = "mixed", log=print) -> dict:
+             decide_prec: str = "mixed", log=print, detail: bool = False) -> dict:
     """Held-out fields: fits (precision prec) from the default start and from the learned
     start with its fallback rule, each timed as a whole (the learned start's time includes
     the features, the network and its two decision passes, run in decide_prec: they only
-    compare two logliks); both must reach the same optimum."""
+    compare two logliks); both must reach the same optimum.  detail=True adds the per-field
+    arrays under "fields" (data, optima, logliks, statuses)."""
     import torch
     rng = np.random.default_rng(seed)
     theta = sample_priors(rng, nfields)
@@ -278,6 +279,11 @@ def evaluate(geom: Geometry, params, norm, nfields: int, seed: int = 3, prec: st
                             "multimodal, and the start decides which maximum is reached)",
         "speedup": (t1 - t0) / (t2 - t1),
     }
+    if detail:
+        res["fields_detail"] = {
+            "Y": Y.cpu().numpy(), "theta_true": theta,
+            "theta_default": f_def["theta"].cpu().numpy(), "theta_learned": f_ws["theta"].cpu().numpy(),
+            "loglik_default": ll_d, "loglik_learned": ll_w, "converged_both": conv, "same": same}
     if log:
         log("held-out: %s" % res)
     return res

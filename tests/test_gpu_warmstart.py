@@ -1,11 +1,19 @@
 """What the learned start gains: a network trained (by the library's kernels) on fields
 that the plain method simulated and fitted starts Fisher scoring closer to the optimum on
-held-out fields, so the fits take fewer passes and (where the likelihood has one maximum
-in reach) reach the same optimum as the fits from the default start; the fallback keeps
-the default where the prediction is worse."""
+held-out fields, so the fits take fewer passes and reach the same optimum as the fits from
+the default start; the fallback keeps the default where the prediction is worse.
+
+"The same optimum" is the plain method's converged optimum, loglik within 1e-6 relative
+(the default start's fit is the judge).  A Matern likelihood can have more than one local
+maximum, and then the start decides which one Fisher scoring reaches: a field whose two
+fits converge to different logliks passes only if the FP64 oracle confirms that both end
+points are local maxima (stationary in the Fisher metric, and lower on both sides along
+every parameter, 5% away on the log scale), and the learned start's maximum is not the
+lower one."""
 import numpy as np
 import pytest
 
+import oracle
 import workloads
 
 torch = pytest.importorskip("torch")
@@ -26,7 +34,7 @@ def trained():
     g = _geometry(1024, 20, 11)
     X, T, stats = ws.build_training_set(g, 3000, seed=12, chunk=1500, log=None)
     assert stats["converged"] >= 0.8 * stats["fields"]
-    P, norm, losses = ws.train(X, T, epochs=40, batch=128, lr=2e-3, log=None)
+    P, norm, losses = ws.train(X, T, epochs=80, batch=128, lr=2e-3, log=None)
     return P, norm, losses, X, T
 
 
@@ -36,19 +44,45 @@ def test_training_reduces_the_loss(trained):
     # the fit of the training targets: predictions explain part of each target's variance
     pred = vg.vecchia_mlp_forward(P, norm, X)
     resid = ((pred - T) ** 2).mean(dim=0)
-    assert torch.all(resid < 0.8 * T.var(dim=0, unbiased=False))
+    assert torch.all(resid < 0.6 * T.var(dim=0, unbiased=False))
+
+
+def _stationary(locs, y, X, NN, th):
+    # the fit rule's convergence measure at th, from the FP64 oracle: g~' I~^-1 g~ on the
+    # log scale
+    o = oracle.loglik_grad_info(locs, y, X, NN, th, oracle.MATERN_ISO)
+    gt = th * o["grad"]
+    It = th[:, None] * o["info"] * th[None, :]
+    return float(gt @ np.linalg.solve(It, gt)), o["loglik"]
 
 
 def test_learned_start_takes_fewer_passes_to_the_same_optimum(trained):
     P, norm, _, _, _ = trained
     g = _geometry(4096, 20, 13)
-    res = ws.evaluate(g, P, norm, nfields=48, seed=14, log=print)
-    assert res["both_converged"] >= 0.7 * 48
-    # the likelihoods can be multimodal: nearly all fields reach the same maximum from both
-    # starts, and where they differ the learned start is not the one stuck lower more often
-    assert res["same_optimum"] >= 0.9 * res["both_converged"]
+    res = ws.evaluate(g, P, norm, nfields=48, seed=14, log=print, detail=True)
+    det = res["fields_detail"]
+    assert res["learned"]["converged"] >= res["default"]["converged"]
+    assert res["both_converged"] >= 0.8 * 48
     assert res["max_loglik_diff_same"] <= 1e-6
-    assert res["different_optimum_default_higher"] <= max(1, res["different_optimum_learned_higher"])
+    locs, X, NN = (g.locs.cpu().numpy(), g.X.cpu().numpy(), g.NN.cpu().numpy())
+    differing = np.nonzero(det["converged_both"] & ~det["same"])[0]
+    for f in differing:
+        y = det["Y"][f]
+        ends = []
+        for th in (det["theta_default"][f], det["theta_learned"][f]):
+            crit, ll = _stationary(locs, y, X, NN, th)
+            assert crit < 1e-3, (f, th, crit)          # the fits stop below tol = 1e-4
+            for j in range(4):                         # lower on both sides: a maximum
+                for sg in (-1.0, 1.0):
+                    th2 = th.copy()
+                    th2[j] *= np.exp(0.05 * sg)
+                    th2[2] = min(max(th2[2], 0.05), 20.0)
+                    o2 = oracle.loglik_grad_info(locs, y, X, NN, th2, oracle.MATERN_ISO)
+                    assert o2["loglik"] < ll + 1e-9 * abs(ll), (f, th, j, sg)
+            ends.append(ll)
+        scale = max(abs(ends[0]), len(y))
+        assert abs(ends[0] - ends[1]) > 1e-6 * scale             # two distinct maxima
+        assert ends[1] >= ends[0], f                              # the learned one not lower
     assert res["learned"]["mean_passes"] < res["default"]["mean_passes"]
     assert res["learned"]["fallback_rate"] < 0.5
 
