@@ -20,7 +20,8 @@ Reported beside the device-timed value:
                   batched Fisher-scoring fits vs 256 sequential device fits;
   * warm_start -- fits of held-out fields (n = 200000) from the default start and from
                   the learned start;
-  * nn_search  -- the ordered nearest-neighbour search on the device vs the CPU search;
+  * nn_search  -- the ordered nearest-neighbour search and the maxmin ordering on the
+                  device vs the CPU versions;
   * prediction -- Vecchia prediction at 100000 new sites of the headline field.
   * elevators_like -- the exponential with one range per attribute on an Elevators-like
                   workload (n = 15000, d = 18): passes, fits, the oracle beside them.
@@ -411,6 +412,27 @@ def run_nn_search(vg, torch, dev, stream) -> dict:
         res[name] = {"n": n, "m": 30, "gpu_ms": statistics.median(ms), "cpu_ms": cpu_s * 1e3,
                      "cpu_threads": os.cpu_count() or 1,
                      "identical": bool(np.array_equal(NN.cpu().numpy(), ref))}
+    # the maxmin ordering on the device against the CPU ordering (grid and lazy max-heap,
+    # one host thread) on 100000 uniform points and on the 1.2 M-point swath's scaled
+    # coordinates; the orders must be identical
+    for name, pts in (("maxmin_n100000", np.random.default_rng(1002).uniform(size=(100000, 2))),
+                      ("maxmin_swath_n1200000",
+                       workloads.swath_locations(np.random.default_rng(1003)) / np.array([5.0, 5.0, 2.0]))):
+        t0 = time.perf_counter()
+        ref = workloads.maxmin_order(pts)
+        cpu_s = time.perf_counter() - t0
+        P = torch.as_tensor(pts, dtype=torch.float64, device=dev)
+        vg.vecchia_maxmin_order(P, stream=stream)          # warm-up (scratch allocation)
+        ms = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            order = vg.vecchia_maxmin_order(P, stream=stream)
+            ms.append((time.perf_counter() - t0) * 1e3)
+        res[name] = {"n": int(pts.shape[0]), "d": int(pts.shape[1]), "gpu_ms": statistics.median(ms),
+                     "cpu_ms": cpu_s * 1e3, "cpu_threads": 1,
+                     "identical": bool(np.array_equal(order.cpu().numpy(), ref)),
+                     "timing": "wall time around the call (it synchronises), median of 3"}
     return res
 
 
