@@ -106,8 +106,8 @@ VECCHIA_API int vecchia_max_m(void);
  * shared-memory footprint does not fit makes later passes return VEC_ERR_UNSUPPORTED. */
 VECCHIA_API vec_status vecchia_set_lanes(vec_handle h, int lanes);
 
-/* Threads per block of the pass kernel: 32, 64, 128 or 256, or 0 to let the library
- * choose (the default).  Same rules as vecchia_set_lanes. */
+/* Threads per block of the pass kernel: 32, 64, 96, 128, 192 or 256, or 0 to let the
+ * library choose (the default).  Same rules as vecchia_set_lanes. */
 VECCHIA_API vec_status vecchia_set_block_threads(vec_handle h, int threads);
 
 /* Where the pass kernels read the per-pass Matern coefficient table: 1 = staged in shared
@@ -120,8 +120,8 @@ VECCHIA_API vec_status vecchia_set_matern_table(vec_handle h, int placement);
 /*
  * Autotuning of the kernel mapping.  vecchia_autotune runs the pass on the given inputs
  * (DEVICE pointers, as for vecchia_loglik_grad_info) once per candidate mapping -- lanes
- * per observation 1..32 x threads per block 64..256, every pair whose shared memory fits --
- * times each with CUDA events (one warm-up, best of `reps`), and records the fastest in
+ * per observation 1..32 x threads per block 64, 96, 128, 192, 256, every pair whose shared
+ * memory fits -- times each with CUDA events (one warm-up, best of `reps`), and records the fastest in
  * the handle under the key (covfun, m, d, p, precision, floor(log2 n)).  Later passes and
  * fits on the handle whose key matches use that mapping unless vecchia_set_lanes /
  * vecchia_set_block_threads force one.  Outputs (HOST, may be NULL): the chosen lanes,

@@ -231,8 +231,9 @@ vec_status vecchia_set_lanes(vec_handle h, int lanes) {
 
 vec_status vecchia_set_block_threads(vec_handle h, int threads) {
     if (!h) return fail(VEC_ERR_ARG, "vecchia_set_block_threads: NULL handle");
-    if (!(threads == 0 || threads == 32 || threads == 64 || threads == 128 || threads == 256))
-        return fail(VEC_ERR_ARG, "threads must be 0, 32, 64, 128 or 256 (got %d)", threads);
+    if (!(threads == 0 || threads == 32 || threads == 64 || threads == 96 || threads == 128 ||
+          threads == 192 || threads == 256))
+        return fail(VEC_ERR_ARG, "threads must be 0, 32, 64, 96, 128, 192 or 256 (got %d)", threads);
     h->threads = threads;
     return VEC_OK;
 }
@@ -668,10 +669,10 @@ vec_status vecchia_autotune(vec_handle h, const double* locs, const double* y, c
     h->timing = 0;
     int bestL = 0, bestT = 0;
     float best = 1e30f;
-    static const int thr_list[] = {256, 128, 64};
+    static const int thr_list[] = {256, 192, 128, 96, 64};
     int bestTab = -1;
     const int ntab = vg::uses_table(cov, (int)prec) ? 2 : 1;
-    for (int ti = 0; ti < 3 && e == cudaSuccess; ++ti) {
+    for (int ti = 0; ti < 5 && e == cudaSuccess; ++ti) {
         for (int L = 1; L <= 32 && e == cudaSuccess; L *= 2)
         for (int tb = 0; tb < ntab && e == cudaSuccess; ++tb) {
             const int tab = vg::uses_table(cov, (int)prec) ? 1 - tb : -1;  // shared memory first
@@ -1226,10 +1227,10 @@ vec_status vecchia_batch_autotune(vec_handle h, int nbatch, const double* locs, 
     int bestL = 0, bestT = 0, mmax = 0;
     float best = 1e30f;
     for (int b = 0; b < nbatch; ++b) mmax = m[b] > mmax ? m[b] : mmax;
-    static const int thr_list[] = {256, 128, 64};
+    static const int thr_list[] = {256, 192, 128, 96, 64};
     int bestTab = -1;
     const int ntab = vg::uses_table(cov, (int)prec) ? 2 : 1;
-    for (int ti = 0; ti < 3 && e == cudaSuccess && s == VEC_OK; ++ti) {
+    for (int ti = 0; ti < 5 && e == cudaSuccess && s == VEC_OK; ++ti) {
         for (int L = 1; L <= 32 && e == cudaSuccess; L *= 2)
         for (int tb = 0; tb < ntab && e == cudaSuccess; ++tb) {
             const int tab = vg::uses_table(cov, (int)prec) ? 1 - tb : -1;

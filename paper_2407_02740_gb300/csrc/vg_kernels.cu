@@ -398,10 +398,8 @@ size_t pass_smem_bytes(int cov, int m, int d, int p, int L, int threads, bool ta
     const size_t tab_words = tab_smem ? (prec == 0 ? MT_DOUBLES : (MT_FLOATS + 1) / 2) : 0;
     const size_t inv_words = (cov == COV_ANISO) ? 2 * DMAX_ANISO : 0;
     // record formulas: one 64-bit word per record entry
-    size_t bytes = (tab_words + inv_words + RL.nstat + (size_t)threads * acc_per_lane) * sizeof(double) +
-                   (size_t)ngrp * SL.bytes;
-    size_t ints = (size_t)ngrp * (m + 1);
-    return bytes + ints * sizeof(int);
+    return (tab_words + inv_words + RL.nstat + (size_t)threads * acc_per_lane) * sizeof(double) +
+           (size_t)ngrp * SL.bytes;
 }
 
 int plan_pass(int cov, int m, int d, int p, int nsm, int force_L, int force_threads,
@@ -413,7 +411,9 @@ int plan_pass(int cov, int m, int d, int p, int nsm, int force_L, int force_thre
     const size_t budget = 220 * 1024;
     int chosen = -1, threads = 128;
     bool tab = false;
-    for (int thr = 256; thr >= 32 && chosen < 0; thr /= 2) {
+    static const int thr_list[] = {256, 192, 128, 96, 64, 32};
+    for (int ti = 0; ti < 6 && chosen < 0; ++ti) {
+        const int thr = thr_list[ti];
         if (force_threads > 0 && thr != force_threads) continue;
         for (int L = 1; L <= 32; L *= 2) {
             if (force_L > 0 && L != force_L) continue;

@@ -111,47 +111,50 @@ struct MaternT<float> {
 
 // Layout of one slot.  Working-type arrays first (offsets in T elements), then FP64 arrays
 // (offsets in doubles from Dbyte).  K = m + 1, Q = derivative vectors.
-//   A     packed lower triangle (row r at r (r + 1) / 2; the diagonal lives in dg); after
+//   A     packed strict lower triangle (row r at r (r - 1) / 2, entries c < r; the
+//         diagonal lives in dg); after
 //         the derivative solves the same bytes hold Gs (Q x K FP64), except in the grouped
 //         kernels, whose factor serves every member of the group: there Gs has its own
 //         region after V
 //   Y     (1 + p) x K augmented rows: y and the columns of X, then z = D^-1 U^-1 (y, X)
 //   loc   d x K coordinates relative to the observation, divided by their ranges
-//   u     K: the unscaled pivot column during the factorisation, then u = last row of U^-1
+//   u     K: the unscaled pivot column during the factorisation, then u = last row of U^-1;
+//         then (sized for it) the FP64 per-observation values V
 //   G     Q x K: h_j = dSigma_j u^T, then f_j = U^-1 h_j
 //   D1    exponential families (all but the Matern): per-pair weights reused by the
 //         derivative step
-//   lf    Matern, FP64 block: d x K coordinates again as double-float pairs (hi, lo FP32),
-//         from which the derivative step forms squared distances without FP64 work
+//   (lf)  Matern, FP64 block: once the covariance is assembled, loc is rewritten in place
+//         as double-float pairs (hi, lo FP32), from which the derivative step forms squared
+//         distances without FP64 work
 //   dg    K FP64: diagonal of the factorisation, then the pivots d_c
 //   dinv  K FP64: 1 / d_c
-//   V     nv FP64: the per-observation values
 //   lp    2 FP64: the group's running product of pivot mantissas and sum of exponents, so
 //         that log det needs one logarithm per group and tile, not one per observation
 struct SlotLayout {
-    int K, A, Y, loc, u, G, D1, lf, nT, Dbyte, dg, dinv, V, lp, Gs, bytes;
+    int K, A, Y, loc, u, G, D1, nT, Dbyte, dg, dinv, lp, Gs, bytes;
     __host__ __device__ void init(int m, int d, int p, int cov, int nv, int tsize,
                                   bool grouped = false) {
         K = m + 1;
         const int Q = npair_derivs(cov, d) + 1;
-        int asz = K * (K + 1) / 2;
+        int asz = K * (K - 1) / 2;
         const int gs = (Q * K * 8 + tsize - 1) / tsize;
         if (!grouped && gs > asz) asz = gs;
         A = 0;
         Y = A + asz;
         loc = Y + (1 + p) * K;
         u = loc + d * K;
-        G = u + K;
+        if (tsize == 4) u += (u & 1);          // 8-byte aligned: V is FP64
+        int usz = (nv * 8 + tsize - 1) / tsize;
+        if (usz < K) usz = K;
+        G = u + usz;
         D1 = G + Q * K;
-        lf = D1 + (cov == COV_MATERN ? 0 : K * (K - 1) / 2);
-        nT = lf + ((cov == COV_MATERN && tsize == 8) ? (d * K * 8 + tsize - 1) / tsize : 0);
+        nT = D1 + (cov == COV_MATERN ? 0 : K * (K - 1) / 2);
         Dbyte = ((nT * tsize + 7) / 8) * 8;
         dg = 0;
         dinv = K;
-        V = 2 * K;
-        lp = 2 * K + nv;
-        Gs = grouped ? 2 * K + nv + 2 : -1;    // -1: over A
-        bytes = Dbyte + (2 * K + nv + 2 + (grouped ? Q * K : 0)) * 8;
+        lp = 2 * K;
+        Gs = grouped ? 2 * K + 2 : -1;         // -1: over A
+        bytes = Dbyte + (2 * K + 2 + (grouped ? Q * K : 0)) * 8;
         bytes = ((bytes / 8) | 1) * 8;  // odd number of 8-byte words: slots spread over banks
     }
 };
@@ -198,7 +201,6 @@ struct PassEnv {
     T *A, *Yg, *loc, *u, *G, *D1;
     float2* locf;         // Matern, FP64 block: the coordinates as double-float pairs
     double *Gs, *dg, *dinv, *V, *lp;
-    int* idx;
     int Kmax;             // slot stride: largest block size of the launch
     // dataset
     const double* locs;
@@ -302,7 +304,7 @@ __device__ __forceinline__ bool ldl_augmented(T* A, T* Yg, double* dg, double* d
         for (int e = gl; e < nr + naug; e += L) {
             if (e < nr) {
                 const int r = c + 1 + e;
-                T* Ar = A + r * (r + 1) / 2;
+                T* Ar = A + r * (r - 1) / 2;
                 const T t = Ar[c];
                 tmp[r] = t;
                 Ar[c] = t * icT;
@@ -318,7 +320,7 @@ __device__ __forceinline__ bool ldl_augmented(T* A, T* Yg, double* dg, double* d
         // are the strict lower triangle (row r + 1 of the items is row c + 2 + r)
         if constexpr (!F64)
             for (int r = c + 1 + gl; r < Kp; r += L)
-                dg[r] = fma(-N::to64(A[r * (r + 1) / 2 + c]), N::to64(tmp[r]), dg[r]);
+                dg[r] = fma(-N::to64(A[r * (r - 1) / 2 + c]), N::to64(tmp[r]), dg[r]);
         const int nrt = F64 ? nr : nr - 1;              // rows of the item triangle
         const int ntri = nrt > 0 ? nrt * (nrt + 1) / 2 : 0;
         int e = gl;
@@ -329,7 +331,7 @@ __device__ __forceinline__ bool ldl_augmented(T* A, T* Yg, double* dg, double* d
             int kk = e - rr * (rr + 1) / 2;
             for (; e < ntri; e += L) {
                 const int r = c + (F64 ? 1 : 2) + rr;
-                T* Ar = A + r * (r + 1) / 2;
+                T* Ar = A + r * (r - 1) / 2;
                 const T l = Ar[c];
                 const int k = c + 1 + kk;
                 if (F64 && k == r) {
@@ -367,7 +369,7 @@ __device__ __forceinline__ void last_row_of_Uinv(const T* A, T* u, int Kp, int g
     gsync<L>(gmask);
     for (int r = last; r >= 1; --r) {
         const T ur = u[r];
-        const T* Ur = A + r * (r + 1) / 2;
+        const T* Ur = A + r * (r - 1) / 2;
         for (int a = gl; a < r; a += L) u[a] = N::fma_(-Ur[a], ur, u[a]);
         gsync<L>(gmask);
     }
@@ -410,7 +412,7 @@ __device__ __forceinline__ void assemble_block(const PassEnv<T, Tab>& E, int Kp)
         while (a * (a - 1) / 2 > e) --a;
         while (a * (a + 1) / 2 <= e) ++a;
         const int c = e - a * (a - 1) / 2;
-        const int ea = a * (a + 1) / 2 + c;           // packed position of (a, c)
+        const int ea = a * (a - 1) / 2 + c;           // packed position of (a, c)
         T C;
         if (COV == COV_EXP) {
             T s = (T)0;
@@ -452,6 +454,16 @@ __device__ __forceinline__ void assemble_block(const PassEnv<T, Tab>& E, int Kp)
         A[ea] = C;
     }
     gsync<L>(gmask);
+    if constexpr (COV == COV_MATERN && sizeof(T) == 8) {
+        // the coordinates as double-float pairs, in place, for the derivative step
+        for (int a = gl; a < Kp; a += L)
+            for (int k = 0; k < d; ++k) {
+                const double v = loc[k * Kmax + a];
+                const float hi = Num<float>::fromd(v);
+                E.locf[k * Kmax + a] = make_float2(hi, Num<float>::fromd(v - f32_to_f64_bits(hi)));
+            }
+        gsync<L>(gmask);
+    }
 }
 
 // log d over many pivots with one logarithm: lp[0] holds a product of mantissas in [1, 2)
@@ -505,7 +517,7 @@ __device__ __forceinline__ void finish_terms(const PassEnv<T, Tab>& E, int Kp, i
         const int jstep = L / nr, ostep = L - jstep * nr;
         while (j < Q) {
             const int a = c + 1 + off;
-            G[j * Kmax + a] = N::fma_(-A[a * (a + 1) / 2 + c], G[j * Kmax + c], G[j * Kmax + a]);
+            G[j * Kmax + a] = N::fma_(-A[a * (a - 1) / 2 + c], G[j * Kmax + c], G[j * Kmax + a]);
             j += jstep;
             off += ostep;
             if (off >= nr) { off -= nr; ++j; }
@@ -692,7 +704,6 @@ __device__ __forceinline__ void vecchia_point(const PassEnv<T, Tab>& E, long lon
     const unsigned gmask = E.gmask;
     const int d = E.d, p = E.p, m = E.m, Kmax = E.Kmax;
     T* Yg = E.Yg; T* loc = E.loc;
-    int* idx = E.idx;
     const double inv_r1 = E.inv_r1, inv_r2 = E.inv_r2;
     // ---------------- gather ----------------
     const int32_t* row = E.NN + i * (long long)(m + 1);
@@ -715,18 +726,11 @@ __device__ __forceinline__ void vecchia_point(const PassEnv<T, Tab>& E, long lon
     const double* li = E.locs + i * (long long)d;
     for (int a = gl; a < Kp; a += L) {
         int j = row[Kp - 1 - a];
-        idx[a] = j;
         // coordinates relative to the observation, divided by their range parameter
         // (FP64 difference, then rounded to T): squared distances come out scaled
-        for (int k = 0; k < d; ++k) {
-            const double v = (E.locs[(long long)j * d + k] - li[k]) *
-                             ((COV == COV_ST && k == 2) ? inv_r2 : inv_r1);
-            loc[k * Kmax + a] = (T)v;
-            if constexpr (COV == COV_MATERN && sizeof(T) == 8) {
-                const float hi = Num<float>::fromd(v);
-                E.locf[k * Kmax + a] = make_float2(hi, Num<float>::fromd(v - f32_to_f64_bits(hi)));
-            }
-        }
+        for (int k = 0; k < d; ++k)
+            loc[k * Kmax + a] = (T)((E.locs[(long long)j * d + k] - li[k]) *
+                                    ((COV == COV_ST && k == 2) ? inv_r2 : inv_r1));
         Yg[a] = (T)E.y[j];
         for (int t = 0; t < p; ++t) Yg[(1 + t) * Kmax + a] = (T)E.X[(long long)j * p + t];
     }
@@ -784,16 +788,9 @@ __device__ __forceinline__ void vecchia_group(const PassEnv<T, Tab>& E, long lon
     const double* ref = E.locs + (long long)blk[Kp - 1] * d;
     for (int a = gl; a < Kp; a += L) {
         const int j = blk[a];
-        E.idx[a] = j;
-        for (int k = 0; k < d; ++k) {
-            const double v = (E.locs[(long long)j * d + k] - ref[k]) *
-                             ((COV == COV_ST && k == 2) ? E.inv_r2 : E.inv_r1);
-            loc[k * Kmax + a] = (T)v;
-            if constexpr (COV == COV_MATERN && sizeof(T) == 8) {
-                const float hi = Num<float>::fromd(v);
-                E.locf[k * Kmax + a] = make_float2(hi, Num<float>::fromd(v - f32_to_f64_bits(hi)));
-            }
-        }
+        for (int k = 0; k < d; ++k)
+            loc[k * Kmax + a] = (T)((E.locs[(long long)j * d + k] - ref[k]) *
+                                    ((COV == COV_ST && k == 2) ? E.inv_r2 : E.inv_r1));
         Yg[a] = (T)E.y[j];
         for (int t = 0; t < p; ++t) Yg[(1 + t) * Kmax + a] = (T)E.X[(long long)j * p + t];
     }
@@ -845,7 +842,6 @@ __device__ __forceinline__ void vecchia_point_aniso(const PassEnv<T, Tab>& E, lo
     const double* li = E.locs + i * (long long)d;
     for (int a = gl; a < Kp; a += L) {
         const int j = row[Kp - 1 - a];
-        E.idx[a] = j;
         for (int k = 0; k < d; ++k)
             loc[k * Kmax + a] = (T)((E.locs[(long long)j * d + k] - li[k]) * E.inv_rk[k]);
         Yg[a] = (T)E.y[j];
@@ -861,7 +857,7 @@ __device__ __forceinline__ void vecchia_point_aniso(const PassEnv<T, Tab>& E, lo
         while (a * (a - 1) / 2 > e) --a;
         while (a * (a + 1) / 2 <= e) ++a;
         const int c = e - a * (a - 1) / 2;
-        const int ea = a * (a + 1) / 2 + c;
+        const int ea = a * (a - 1) / 2 + c;
         T s0 = (T)0, s1 = (T)0;
         int k = 0;
         for (; k + 1 < d; k += 2) {
@@ -936,9 +932,10 @@ __device__ __forceinline__ void vecchia_point_aniso(const PassEnv<T, Tab>& E, lo
 
 // The FP32 (mixed) instantiations are latency-bound: ask for three resident blocks of 256
 // threads (at most 85 registers a thread; they need 80, with no meaningful spill) so that
-// registers no longer cap the resident warps at 16 per SM.  The FP64 ones are bound by the
-// FP64 pipe and keep the default.
-constexpr int pass_min_blocks(int tsize) { return tsize == 4 ? 3 : 1; }
+// registers no longer cap the resident warps at 16 per SM.  The FP64 ones ask for two
+// blocks of 256 threads (at most 128 registers), which lets four blocks of 128 threads or
+// five of 96 share an SM when their shared memory allows.
+constexpr int pass_min_blocks(int tsize) { return tsize == 4 ? 3 : 2; }
 
 // GROUPED: the units are the blocks of grouped conditioning (PassArgs.blk_*), not single
 // observations; m + 1 is then the largest block.
@@ -980,8 +977,6 @@ __global__ void __launch_bounds__(256, pass_min_blocks(sizeof(T))) k_pass(PassAr
     SlotLayout SL;
     SL.init(m, d, p, COV, args.nv, (int)sizeof(T), GROUPED);
     char* slotc = reinterpret_cast<char*>(sp) + (size_t)grp * args.slot_stride;
-    int* idx = reinterpret_cast<int*>(reinterpret_cast<char*>(sp) + (size_t)ngrp * args.slot_stride) +
-               grp * Kmax;
     T* slot = reinterpret_cast<T*>(slotc);
     double* slotd = reinterpret_cast<double*>(slotc + SL.Dbyte);
 
@@ -1017,10 +1012,11 @@ __global__ void __launch_bounds__(256, pass_min_blocks(sizeof(T))) k_pass(PassAr
     PassEnv<T, Tab> E;
     E.gl = gl; E.gmask = gmask;
     E.A = slot + SL.A; E.Yg = slot + SL.Y; E.loc = slot + SL.loc; E.u = slot + SL.u;
-    E.G = slot + SL.G; E.D1 = slot + SL.D1; E.locf = reinterpret_cast<float2*>(slot + SL.lf);
+    E.G = slot + SL.G; E.D1 = slot + SL.D1; E.locf = reinterpret_cast<float2*>(slot + SL.loc);
     E.Gs = SL.Gs < 0 ? reinterpret_cast<double*>(slotc) : slotd + SL.Gs;
-    E.dg = slotd + SL.dg; E.dinv = slotd + SL.dinv; E.V = slotd + SL.V; E.lp = slotd + SL.lp;
-    E.idx = idx; E.Kmax = Kmax;
+    E.dg = slotd + SL.dg; E.dinv = slotd + SL.dinv; E.lp = slotd + SL.lp;
+    E.V = reinterpret_cast<double*>(slot + SL.u);
+    E.Kmax = Kmax;
     E.locs = args.locs; E.y = args.y; E.X = args.X; E.NN = args.NN;
     E.d = d; E.p = p; E.m = m; E.status = args.status; E.bad = args.bad;
     E.nu = (COV == COV_MATERN) ? th[2] : 0.0; E.m_psi = m_psi; E.sig2 = sig2;
@@ -1097,8 +1093,6 @@ __global__ void __launch_bounds__(256, pass_min_blocks(sizeof(T))) k_pass_batch(
     SlotLayout SL;
     SL.init(args.m, d, p, COV, args.nv, (int)sizeof(T));
     char* slotc = reinterpret_cast<char*>(sp) + (size_t)grp * args.slot_stride;
-    int* idx = reinterpret_cast<int*>(reinterpret_cast<char*>(sp) + (size_t)ngrp * args.slot_stride) +
-               grp * Kmax;
     T* slot = reinterpret_cast<T*>(slotc);
 
     const int vb0 = 4 + p, vstep = 3 + p, vmm = vb0 + Q * vstep;
@@ -1108,10 +1102,11 @@ __global__ void __launch_bounds__(256, pass_min_blocks(sizeof(T))) k_pass_batch(
     E.gl = gl; E.gmask = gmask;
     double* slotd = reinterpret_cast<double*>(slotc + SL.Dbyte);
     E.A = slot + SL.A; E.Yg = slot + SL.Y; E.loc = slot + SL.loc; E.u = slot + SL.u;
-    E.G = slot + SL.G; E.D1 = slot + SL.D1; E.locf = reinterpret_cast<float2*>(slot + SL.lf);
+    E.G = slot + SL.G; E.D1 = slot + SL.D1; E.locf = reinterpret_cast<float2*>(slot + SL.loc);
     E.Gs = SL.Gs < 0 ? reinterpret_cast<double*>(slotc) : slotd + SL.Gs;
-    E.dg = slotd + SL.dg; E.dinv = slotd + SL.dinv; E.V = slotd + SL.V; E.lp = slotd + SL.lp;
-    E.idx = idx; E.Kmax = Kmax;
+    E.dg = slotd + SL.dg; E.dinv = slotd + SL.dinv; E.lp = slotd + SL.lp;
+    E.V = reinterpret_cast<double*>(slot + SL.u);
+    E.Kmax = Kmax;
     E.d = d; E.p = p; E.sidx = sidx; E.acc = acc; E.nstat = args.nstat;
     E.vb0 = vb0; E.vstep = vstep; E.vmm = vmm;
     E.inv_rk = inv_rk; E.inv_rkT = inv_rkT;
