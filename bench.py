@@ -948,7 +948,8 @@ def run_ours(args):
                          "one_core": {"value": cpu1_rate, "unit": UNIT, "cores": 1,
                                       "sample": "first %d observations, %.1f s" % (cpu1_n, cpu1_s)}},
         "measured_peaks": dict(peaks, source="vecchia_measure_peaks (FMA chains, covariance "
-                                             "evaluations as the pass does them)",
+                                             "evaluations as the pass does them, FP64 "
+                                             "m8n8k4 tensor-core chains)",
                                fp64_peak_from_unit_counts_gflops=FP64_PEAK_GFLOPS),
         "e2e": {"value": job_throughput(ws, w.n, args.steps, e2e_total), "unit": UNIT,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},

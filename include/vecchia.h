@@ -625,8 +625,9 @@ VECCHIA_API vec_status vecchia_grouped_loglik_grad_info(vec_handle h, const doub
  * out[1] FP32 FMA-chain GFLOP/s (8 independent chains per thread, 16 warps per SM),
  * out[2] exponential covariance evaluations per second (square root, exponential and
  * division per pair, as the pass does them), out[3] Matern evaluations per second (the
- * per-pass table's value and two derivatives).  out: HOST memory, 4 doubles.  Temporary
- * device buffers are allocated and freed by the call.
+ * per-pass table's value and two derivatives), out[4] FP64 tensor-core GFLOP/s (chains of
+ * the m8n8k4 double-precision matrix multiply-add, 8 per warp).  out: HOST memory,
+ * 5 doubles.  Temporary device buffers are allocated and freed by the call.
  */
 VECCHIA_API vec_status vecchia_measure_peaks(vec_handle h, double* out);
 

@@ -1013,14 +1013,14 @@ def vecchia_grouped_loglik_grad_info(locs, y, X, block_off, block_idx, nmemb, km
 
 
 def vecchia_measure_peaks(handle: Handle | None = None, device: int = 0) -> dict:
-    """Measured FP64 / FP32 FMA-chain GFLOP/s and covariance evaluations per second on the
-    device (see vecchia_measure_peaks in include/vecchia.h)."""
+    """Measured FP64 / FP32 FMA-chain GFLOP/s, covariance evaluations per second and the
+    FP64 tensor-core GFLOP/s on the device (see vecchia_measure_peaks in include/vecchia.h)."""
     if handle is None:
         handle = default_handle(device)
-    out = (ctypes.c_double * 4)()
+    out = (ctypes.c_double * 5)()
     _check(lib().vecchia_measure_peaks(handle.ptr, ctypes.cast(out, ctypes.c_void_p)))
     return {"fp64_gflops": out[0], "fp32_gflops": out[1], "exp_pairs_per_s": out[2],
-            "matern_pairs_per_s": out[3]}
+            "matern_pairs_per_s": out[3], "fp64_tensor_gflops": out[4]}
 
 
 def vecchia_covariance_pairs(covfun: int, covparms, la, lb, same, stream=None,

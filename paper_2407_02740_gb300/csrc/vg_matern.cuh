@@ -100,27 +100,22 @@ static __device__ __noinline__ void matern_small(double nu, double s, double psi
 
 // Locates s in the table.  Returns the interval index and the local variable w, or
 // -1 when s < 2^E0 (direct formula, includes s == 0), or -2 when s >= 2^E1 (zero).
-// The interval centre 1 + (2j+1)/(2J) is built from bits, so w = mantissa - centre is
-// one exact FP64 subtraction (Sterbenz).  w is also returned as an unevaluated sum of two
-// FP32 numbers, wf + wl = w exactly up to 2^-24 of wl: wf the difference of the mantissa
-// truncated to 23 bits (exact in FP32), wl the remaining 29 mantissa bits (>= 0).
-__device__ __forceinline__ int mtab_locate(double s, double& w, float& wf, float& wl) {
+// w = mantissa - centre, the centre 1 + (2j+1)/(2J) of interval j, is a multiple of 2^-52
+// of magnitude at most 1/(2J): an integer W of at most 50 bits in units of 2^-52 (from the
+// bits, no FP64 instruction).  It is returned as an exact unevaluated sum of two FP32
+// numbers, split by rounding at 2^25: wh = round(W / 2^25) 2^-27 and
+// wl = (W - round(W / 2^25) 2^25) 2^-52, each part at most 2^24 in units and so exact.
+__device__ __forceinline__ int mtab_locate(double s, float& wh, float& wl) {
     const unsigned long long bits = (unsigned long long)__double_as_longlong(s);
     const int e = (int)((bits >> 52) & 0x7ffull) - 1023;
     if (e < MT_E0) return -1;
     if (e >= MT_E1) return -2;
     const unsigned long long j = (bits >> (52 - MT_LOGJ)) & (unsigned long long)(MT_J - 1);
-    const double mant = __longlong_as_double((long long)((bits & 0x000fffffffffffffull) |
-                                                         0x3ff0000000000000ull));
-    const double cen = __longlong_as_double(
-        (long long)(0x3ff0000000000000ull | ((2ull * j + 1ull) << (52 - MT_LOGJ - 1))));
-    w = mant - cen;
-    // the same difference in FP32 for the polynomial tail, without an FP64 conversion:
-    // the mantissa truncated to 23 bits (relative error < 2^-23, harmless in the tail)
-    const float mantf = __uint_as_float(0x3f800000u | (unsigned)((bits >> 29) & 0x7fffffull));
-    const float cenf = __uint_as_float(0x3f800000u | (unsigned)((2ull * j + 1ull) << (23 - MT_LOGJ - 1)));
-    wf = mantf - cenf;
-    wl = __uint2float_rn((unsigned)(bits & 0x1fffffffull)) * 0x1p-52f;
+    const long long W = (long long)(bits & 0x000fffffffffffffull) -
+                        (long long)((2ull * j + 1ull) << (52 - MT_LOGJ - 1));
+    const long long Wh = (W + (1ll << 24)) >> 25;
+    wh = __int2float_rn((int)Wh) * 0x1p-27f;
+    wl = __int2float_rn((int)(W - (Wh << 25))) * 0x1p-52f;
     return (e - MT_E0) * MT_J + (int)j;
 }
 
@@ -129,14 +124,17 @@ __device__ __forceinline__ int mtab_locate(double s, double& w, float& wf, float
 //   * the tail w^8..w^12 (summing to below ~1e-9 on every interval) in FP32;
 //   * P = c1 + w (c2 + ...) in double-float arithmetic (a value is an unevaluated FP32
 //     pair, ~48 significant bits; the two-product uses the FMA's exact remainder, the sum
-//     Knuth's two-sum);
-//   * the last Horner step, c0 + w P, in FP64 (two FMAs, one per half of the pair).
-// The double-float part enters the result as w P with |w| <= 1/8, so its rounding lands
-// at ~2^-50 of |c1|: a few units of the last place of the covariance scale sigma2, below
-// what the likelihood resolves even at a nugget of 0.001.  FP32 runs at 64x the FP64 rate
-// on this GPU, so the chain costs 2 FP64 FMAs instead of 9 FP64 operations.  The
-// error-free steps use explicitly rounded intrinsics so that no multiply-add is fused.
-__device__ __forceinline__ double horner_split(const double* c, double w, float wh, float wl) {
+//     Knuth's two-sum), with w = wh + wl exact (mtab_locate);
+//   * q = w P in double-float: wh ph exactly as its rounded product and the FMA's
+//     remainder, plus the cross terms wh pl and wl ph (wl pl is below 2^-52 of |q|);
+//   * c0 + q_hi + q_lo in FP64: two additions.
+// q enters the result with |q| <= |c1|/8 + ..., and its double-float rounding (~2^-48 of
+// |q|) lands at ~2^-50 of |c1|: a few units of the last place of the covariance scale
+// sigma2, below what the likelihood resolves even at a nugget of 0.001.  FP32 runs at 64x
+// the FP64 rate on this GPU, so the chain costs 2 FP64 additions instead of 9 FP64
+// operations.  The error-free steps use explicitly rounded intrinsics so that no
+// multiply-add is fused.
+__device__ __forceinline__ double horner_split(const double* c, float wh, float wl) {
     const float* t = reinterpret_cast<const float*>(c + MT_NHEAD);
     float ph = t[4];
     ph = fmaf(ph, wh, t[3]);
@@ -159,7 +157,11 @@ __device__ __forceinline__ double horner_split(const double* c, double w, float 
         ph = __fadd_rn(sm, er);
         pl = __fsub_rn(er, __fsub_rn(ph, sm));
     }
-    return fma(w, f32_to_f64_bits(ph), fma(w, f32_to_f64_bits(pl), c[0]));
+    const float qh = __fmul_rn(wh, ph);
+    float ql = fmaf(wh, ph, -qh);                   // exact remainder of wh ph
+    ql = fmaf(wh, pl, ql);
+    ql = fmaf(wl, ph, ql);
+    return (c[0] + f32_to_f64_bits(qh)) + f32_to_f64_bits(ql);
 }
 
 // Locates s in the table like mtab_locate, but returns the local variable only as the
@@ -246,10 +248,9 @@ __device__ __forceinline__ void matern_F12_df(const double* tab, float sh, float
 // sc1 = sigma2 / rho, sc2 = sigma2); above it all three are 0.
 __device__ __forceinline__ double matern_F0(const double* tab, double s, double nu, double psi,
                                             double sc0) {
-    double w;
-    float wf, wl;
-    int it = mtab_locate(s, w, wf, wl);
-    if (it >= 0) return horner_split(tab + it * MT_PER_INT, w, wf, wl);
+    float wh, wl;
+    int it = mtab_locate(s, wh, wl);
+    if (it >= 0) return horner_split(tab + it * MT_PER_INT, wh, wl);
     if (it == -2) return 0.0;
     if (!(s > 0.0)) return sc0;
     double f0, f1, f2;
@@ -283,10 +284,9 @@ __device__ __forceinline__ void matern_F12(const double* tab, double s, double n
 // derivatives.  Below the table the functions are evaluated directly (F2 = 0 for
 // coincident points, where every range derivative vanishes); above it they are 0.
 __device__ __forceinline__ double exp_F0(const double* tab, double s, double sig2) {
-    double w;
-    float wf, wl;
-    const int it = mtab_locate(s, w, wf, wl);
-    if (it >= 0) return horner_split(tab + it * MT_PER_INT, w, wf, wl);
+    float wh, wl;
+    const int it = mtab_locate(s, wh, wl);
+    if (it >= 0) return horner_split(tab + it * MT_PER_INT, wh, wl);
     if (it == -2) return 0.0;
     return sig2 * exp(-sqrt(s));
 }

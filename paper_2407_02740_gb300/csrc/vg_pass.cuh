@@ -284,7 +284,11 @@ __device__ __forceinline__ bool ldl_augmented(T* A, T* Yg, double* dg, double* d
     constexpr bool F64 = sizeof(T) == 8;
     for (int c = 0; c < Kp; ++c) {
         const double dc = dg[c];
-        if (!(dc > 0.0) || !(dc <= 1.7976931348623157e308)) return false;
+        // d_c positive and finite, tested on the bits (an FP64 comparison would take the
+        // FP64 unit): as a signed 64-bit integer a positive finite double lies strictly
+        // between 0 and the bits of +infinity; zero, negatives and NaN fall outside
+        const long long dcb = __double_as_longlong(dc);
+        if (dcb <= 0 || dcb >= 0x7ff0000000000000LL) return false;
         // the reciprocal scales the FP32 column with FP32 accuracy on the mixed path (an FP32
         // reciprocal of the FP64 pivot; only the last pivot's reciprocal is taken again in
         // FP64, where the values need it)
@@ -467,9 +471,10 @@ __device__ __forceinline__ void assemble_block(const PassEnv<T, Tab>& E, int Kp)
 }
 
 // log d over many pivots with one logarithm: lp[0] holds a product of mantissas in [1, 2)
-// (renormalised from the bits after each multiplication), lp[1] the sum of the binary
-// exponents taken out; log of the whole product is log(lp[0]) + lp[1] log 2 (log_fold).
-// One FP64 multiplication per pivot instead of a logarithm.
+// (renormalised from the bits after each multiplication), the bytes of lp[1] a 64-bit
+// integer sum of the binary exponents taken out; log of the whole product is
+// log(lp[0]) + lp[1] log 2 (log_fold).  One FP64 multiplication per pivot instead of a
+// logarithm, and the exponent sum is integer work.  A zeroed lp[1] is an exponent sum of 0.
 __device__ __forceinline__ void log_pivot(double* lp, double v) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(v);
     const long long ev = (long long)((b >> 52) & 0x7ffull) - 1023;
@@ -477,12 +482,14 @@ __device__ __forceinline__ void log_pivot(double* lp, double v) {
     const unsigned long long pb = (unsigned long long)__double_as_longlong(lp[0] * mv);
     const long long ep = (long long)((pb >> 52) & 0x7ffull) - 1023;
     lp[0] = __longlong_as_double((long long)((pb & 0x000fffffffffffffull) | 0x3ff0000000000000ull));
-    lp[1] += (double)(ev + ep);
+    long long* es = reinterpret_cast<long long*>(lp + 1);
+    *es += ev + ep;
 }
 __device__ __forceinline__ double log_fold(double* lp) {
-    const double r = log(lp[0]) + lp[1] * 0.69314718055994530942;
+    long long* es = reinterpret_cast<long long*>(lp + 1);
+    const double r = log(lp[0]) + (double)*es * 0.69314718055994530942;
     lp[0] = 1.0;
-    lp[1] = 0.0;
+    *es = 0;
     return r;
 }
 
@@ -558,35 +565,65 @@ __device__ __forceinline__ void finish_terms(const PassEnv<T, Tab>& E, int Kp, i
     }
     const int P1 = 1 + p;
     const int nz = Q * P1, nitems = nz + Q * (Q + 1) / 2;
-    for (int it = gl; it < nitems; it += L) {
+    // Partial sum of item it over the rows a0, a0 + astep, ...: the nz items f_j . z_t over
+    // the rows before the last (the halved last term is added by fin), the others
+    // f_j . Gs_l over all Kp rows.
+    auto part = [&](int it, int a0, int astep) -> double {
+        const T* g;
+        const T* zt = nullptr;
+        const double* h = nullptr;
+        int len;
         if (it < nz) {
             const int j = it / P1, t = it - j * P1;
-            const T* g = G + j * Kmax;
-            const T* z = Yg + t * Kmax;
-            double s0 = 0.0, s1 = 0.0;
-            int a = 0;
-            for (; a + 1 < last; a += 2) {
-                s0 = fma(N::to64(g[a]), N::to64(z[a]), s0);
-                s1 = fma(N::to64(g[a + 1]), N::to64(z[a + 1]), s1);
-            }
-            if (a < last) s0 = fma(N::to64(g[a]), N::to64(z[a]), s0);
-            s0 = fma(0.5 * N::to64(g[last]), N::to64(z[last]), s0 + s1);  // hat(): last halved
-            V[vb0 + j * vstep + 1 + t] = -s0 * rs;
+            g = G + j * Kmax;
+            zt = Yg + t * Kmax;
+            len = last;
         } else {
             int r = it - nz, j = 0;
             while (r >= Q - j) { r -= Q - j; ++j; }
-            const int l = j + r;
-            const T* g = G + j * Kmax;
-            const double* h = Gs + l * Kmax;
-            double s0 = 0.0, s1 = 0.0;
-            int a = 0;
-            for (; a + 1 < Kp; a += 2) {
-                s0 = fma(N::to64(g[a]), h[a], s0);
-                s1 = fma(N::to64(g[a + 1]), h[a + 1], s1);
-            }
-            if (a < Kp) s0 = fma(N::to64(g[a]), h[a], s0);
-            V[vmm + (it - nz)] = (s0 + s1) * idK;
+            g = G + j * Kmax;
+            h = Gs + (j + r) * Kmax;
+            len = Kp;
         }
+        double s0 = 0.0, s1 = 0.0;
+        int a = a0;
+        if (zt) {
+            for (; a + astep < len; a += 2 * astep) {
+                s0 = fma(N::to64(g[a]), N::to64(zt[a]), s0);
+                s1 = fma(N::to64(g[a + astep]), N::to64(zt[a + astep]), s1);
+            }
+            if (a < len) s0 = fma(N::to64(g[a]), N::to64(zt[a]), s0);
+        } else {
+            for (; a + astep < len; a += 2 * astep) {
+                s0 = fma(N::to64(g[a]), h[a], s0);
+                s1 = fma(N::to64(g[a + astep]), h[a + astep], s1);
+            }
+            if (a < len) s0 = fma(N::to64(g[a]), h[a], s0);
+        }
+        return s0 + s1;
+    };
+    auto fin = [&](int it, double sm) {
+        if (it < nz) {
+            const int j = it / P1, t = it - j * P1;
+            sm = fma(0.5 * N::to64(G[j * Kmax + last]), N::to64(Yg[t * Kmax + last]), sm);  // hat()
+            V[vb0 + j * vstep + 1 + t] = -sm * rs;
+        } else {
+            V[vmm + (it - nz)] = sm * idK;
+        }
+    };
+    // Whole rounds of L items take one item per lane.  The rest, fewer than L items, are
+    // split: each gets sub lanes (L / rest rounded down to a power of two) that take every
+    // sub-th row and add their partial sums by shuffles, so that the last round does not
+    // cost a whole item's length for a few busy lanes.
+    const int full = nitems - nitems % L;
+    for (int it = gl; it < full; it += L) fin(it, part(it, 0, 1));
+    if (full < nitems) {
+        const int rest = nitems - full;
+        const int sub = 1 << (31 - __clz(L / rest));
+        const int it = full + gl / sub, a0 = gl & (sub - 1);
+        double sm = it < nitems ? part(it, a0, sub) : 0.0;
+        for (int o = sub / 2; o > 0; o >>= 1) sm += __shfl_xor_sync(gmask, sm, o);
+        if (it < nitems && a0 == 0) fin(it, sm);
     }
     gsync<L>(gmask);
     accumulate_record<L>(E.sidx, V, E.acc, E.nstat, gl, gmask);
@@ -1026,7 +1063,7 @@ __global__ void __launch_bounds__(256, pass_min_blocks(sizeof(T))) k_pass(PassAr
     E.tab = tab; E.sidx = sidx; E.acc = acc; E.nstat = args.nstat;
     E.vb0 = vb0; E.vstep = vstep; E.vmm = vmm; E.factor = nullptr;
     E.blk_off = args.blk_off; E.blk_idx = args.blk_idx; E.nmemb = args.nmemb; E.n = n;
-    if (gl == 0) { E.lp[0] = 1.0; E.lp[1] = 0.0; }
+    if (gl == 0) { E.lp[0] = 1.0; *reinterpret_cast<long long*>(E.lp + 1) = 0; }
     if constexpr (GROUPED) {
         for (long long u = (long long)blockIdx.x * ngrp + grp; ok && u < args.ngroups; u += gstride) {
             const long long g = args.gorder ? (long long)args.gorder[u] : u;
@@ -1167,7 +1204,7 @@ __global__ void __launch_bounds__(256, pass_min_blocks(sizeof(T))) k_pass_batch(
             if (!ok && tid == 0) report(E.status, E.bad, ST_ARG, -1);
         }
         for (int k = 0; k < args.acc_per_lane; ++k) acc[k] = 0.0;
-        if (gl == 0) { E.lp[0] = 1.0; E.lp[1] = 0.0; }
+        if (gl == 0) { E.lp[0] = 1.0; *reinterpret_cast<long long*>(E.lp + 1) = 0; }
         __syncthreads();
         const bool active = bargs.active_b == nullptr || bargs.active_b[b] != 0;
         if (ok && active)

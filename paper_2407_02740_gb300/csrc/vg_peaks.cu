@@ -30,6 +30,33 @@ __global__ void __launch_bounds__(256) k_fma_chain(T* sink, int iters, T a, T b)
     if (s == (T)-12345) sink[0] = s;   // keeps the chains live; never true in practice
 }
 
+// FP64 on the tensor cores: independent chains of the m8n8k4 double-precision matrix
+// multiply-add (an 8 x 4 by 4 x 8 product added into 8 x 8: 512 flops per warp
+// instruction), the FP64 tensor operation this GPU offers.  Measured so that the choice of
+// the FP64 ALU for the pass's contractions rests on a number.
+__global__ void __launch_bounds__(256) k_dmma_chain(double* sink, int iters, double a, double b) {
+    double c0[kChains], c1[kChains];
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) {
+        c0[c] = (double)(threadIdx.x + c);
+        c1[c] = (double)(threadIdx.x - c);
+    }
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+#pragma unroll
+            for (int c = 0; c < kChains; ++c)
+                asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};"
+                             : "+d"(c0[c]), "+d"(c1[c])
+                             : "d"(a), "d"(b));
+        }
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) s += c0[c] + c1[c];
+    if (s == -12345.0) sink[0] = s;
+}
+
 // One pair evaluation per iteration and thread, at squared distances spread over the
 // range the pass meets (s from ~1e-4 to ~40 in units of the range).
 __global__ void __launch_bounds__(256) k_exp_eval(double* sink, int iters) {
@@ -89,7 +116,8 @@ cudaError_t time_launch(cudaStream_t st, F launch, float* ms) {
 
 namespace vg {
 
-// out = {FP64 GFLOP/s, FP32 GFLOP/s, exponential pairs/s, Matern pairs/s}
+// out = {FP64 GFLOP/s, FP32 GFLOP/s, exponential pairs/s, Matern pairs/s,
+//        FP64 tensor-core GFLOP/s}
 cudaError_t measure_peaks(int nsm, cudaStream_t st, double* out) {
     double* sink = nullptr;
     double* tab = nullptr;
@@ -120,6 +148,10 @@ cudaError_t measure_peaks(int nsm, cudaStream_t st, double* out) {
     if (e == cudaSuccess)
         e = time_launch(st, [&] { k_matern_eval<<<grid, block, 0, st>>>(tab, 1.5, psi, sink, itev); }, &ms);
     if (e == cudaSuccess) out[3] = threads * itev / (ms * 1e-3);
+    const int itmm = 500;
+    if (e == cudaSuccess)
+        e = time_launch(st, [&] { k_dmma_chain<<<grid, block, 0, st>>>(sink, itmm, 1e-3, 1e-3); }, &ms);
+    if (e == cudaSuccess) out[4] = 512.0 * (threads / 32.0) * itmm * kUnroll * kChains / (ms * 1e-3) / 1e9;
     cudaError_t e2 = cudaStreamSynchronize(st);
     if (e == cudaSuccess) e = e2;
     cudaFree(sink);
