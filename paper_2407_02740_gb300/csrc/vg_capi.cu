@@ -1868,6 +1868,7 @@ vec_status vecchia_grouped_loglik_grad_info(vec_handle h, const double* locs, co
         a.nmemb = nmemb; a.gorder = gorder ? gorder + class_off[c] : nullptr;
         a.ngroups = class_off[c + 1] - class_off[c];
         a.ngroups_all = ngroups;
+        a.gchunk = plan.gchunk;
         e = vg::launch_pass(cov, plan, a, st);
         rec0 += (size_t)plan.grid;
     }

@@ -176,6 +176,7 @@ struct PassArgs {
     const int32_t* gorder;             // unit u is group gorder[u] (nullptr: group u)
     long long ngroups;                 // units of this launch
     long long ngroups_all;             // groups in blk_off / nmemb
+    int gchunk = 1;                    // members whose terms are formed together
 };
 
 // Arguments of the batched pass kernel: many datasets (common d, p, covariance family),

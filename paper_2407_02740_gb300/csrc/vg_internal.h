@@ -22,6 +22,7 @@ struct PassPlan {
     int prec;          // 0 = FP64 kernel, 1 = mixed (FP32 block) kernel
     int batched;       // plan made for the batched kernel
     int grouped;       // plan made for the grouped-conditioning kernel
+    int gchunk;        // grouped: members whose terms are formed together (slot sized for it)
 };
 
 // Chooses the lanes-per-observation mapping that fits shared memory (or the forced one).
@@ -32,7 +33,7 @@ int plan_pass(int cov, int m, int d, int p, int nsm, int force_L, int force_thre
               PassPlan* plan, int prec = 0, bool batched = false, int force_tab = -1,
               bool grouped = false);
 size_t pass_smem_bytes(int cov, int m, int d, int p, int L, int threads, bool tab_smem,
-                       int prec = 0, bool grouped = false);
+                       int prec = 0, bool grouped = false, int gchunk = 1);
 const void* pass_kernel_f64(int cov, int L);
 const void* pass_kernel_f32(int cov, int L);
 const void* pass_batch_kernel_f64(int cov, int L);

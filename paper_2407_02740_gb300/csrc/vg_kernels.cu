@@ -386,13 +386,13 @@ static const void* pass_kernel(int cov, int L, int prec, bool batched = false, b
 }
 
 size_t pass_smem_bytes(int cov, int m, int d, int p, int L, int threads, bool tab_smem,
-                       int prec, bool grouped) {
+                       int prec, bool grouped, int gchunk) {
     const int Q = npair_derivs(cov, d) + 1;
     RecLayout RL;
     RL.init(p, Q);
     const int nv = nv_of(p, Q);
     SlotLayout SL;
-    SL.init(m, d, p, cov, nv, prec == 0 ? 8 : 4, grouped);
+    SL.init(m, d, p, cov, nv, prec == 0 ? 8 : 4, grouped, gchunk);
     const int ngrp = threads / L;
     const int acc_per_lane = (RL.nstat + L - 1) / L;
     const size_t tab_words = tab_smem ? (prec == 0 ? MT_DOUBLES : (MT_FLOATS + 1) / 2) : 0;
@@ -409,7 +409,7 @@ int plan_pass(int cov, int m, int d, int p, int nsm, int force_L, int force_thre
     // the minimum that occupies all FP64 units), then fewer when the largest blocks do
     // not fit; within a block size, the fewest lanes per observation that fit.
     const size_t budget = 220 * 1024;
-    int chosen = -1, threads = 128;
+    int chosen = -1, threads = 128, gch = 1;
     bool tab = false;
     static const int thr_list[] = {256, 192, 128, 96, 64, 32};
     for (int ti = 0; ti < 6 && chosen < 0; ++ti) {
@@ -422,13 +422,18 @@ int plan_pass(int cov, int m, int d, int p, int nsm, int force_L, int force_thre
             if (thr == 256 && force_L <= 0 && L > 16) continue;
             // Matern table in shared memory when it fits (or as forced: force_tab 1 = shared
             // memory only, 0 = global memory, read through L1)
-            bool t = uses_table(cov, prec) && force_tab != 0;
-            size_t b = pass_smem_bytes(cov, m, d, p, L, thr, t, prec, grouped);
-            if (b > budget && t && force_tab < 0) {
-                t = false;
-                b = pass_smem_bytes(cov, m, d, p, L, thr, t, prec, grouped);
+            // grouped: the most members formed together (GCH, then fewer) that fit
+            bool fit = false;
+            for (int ch = grouped ? GCH : 1; ch >= 1 && !fit; ch /= 2) {
+                bool t = uses_table(cov, prec) && force_tab != 0;
+                size_t b = pass_smem_bytes(cov, m, d, p, L, thr, t, prec, grouped, ch);
+                if (b > budget && t && force_tab < 0) {
+                    t = false;
+                    b = pass_smem_bytes(cov, m, d, p, L, thr, t, prec, grouped, ch);
+                }
+                if (b <= budget) { fit = true; chosen = L; tab = t; threads = thr; gch = ch; }
             }
-            if (b <= budget) { chosen = L; tab = t; threads = thr; break; }
+            if (fit) break;
         }
     }
     if (chosen < 0) return -1;
@@ -441,11 +446,12 @@ int plan_pass(int cov, int m, int d, int p, int nsm, int force_L, int force_thre
     plan->nstat = RL.nstat;
     plan->nv = nv_of(p, Q);
     SlotLayout SL;
-    SL.init(m, d, p, cov, plan->nv, prec == 0 ? 8 : 4, grouped);
+    SL.init(m, d, p, cov, plan->nv, prec == 0 ? 8 : 4, grouped, gch);
     plan->slot_stride = SL.bytes;
+    plan->gchunk = gch;
     plan->prec = prec;
     plan->acc_per_lane = (RL.nstat + chosen - 1) / chosen;
-    plan->smem = pass_smem_bytes(cov, m, d, p, chosen, threads, tab, prec, grouped);
+    plan->smem = pass_smem_bytes(cov, m, d, p, chosen, threads, tab, prec, grouped, gch);
     plan->batched = batched ? 1 : 0;
     plan->grouped = grouped ? 1 : 0;
     const void* fn = pass_kernel(cov, chosen, prec, batched, grouped);

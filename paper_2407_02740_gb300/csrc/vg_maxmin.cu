@@ -43,6 +43,7 @@ namespace {
 constexpr int MM_THREADS = 512;
 constexpr int MM_PMAX = 2048;      // pool capacity (one block sorts it in shared memory)
 constexpr int MM_TACC = 256;       // candidates examined per step
+constexpr int MM_TCHUNK = 64;      // candidates checked together (the prefix ends at the first conflict)
 constexpr long long MM_SPIN_LIMIT = 1ll << 26;   // ~seconds of waiting per barrier
 
 enum : int { MODE_UPDATE = 0, MODE_REBUILD = 1, MODE_DONE = 2 };
@@ -95,8 +96,11 @@ __device__ __forceinline__ int cell_coord(double v, double lo, double h, int nc)
     return c;
 }
 
-// (dist desc, index asc): true when key a ranks before key b
-__device__ __forceinline__ bool ranks_before(double da, int ia, double db, int ib) {
+// (dist desc, index asc): true when key a ranks before key b.  Distances are compared as
+// their FP64 bit patterns, which order like the values for non-negative numbers (selected
+// points hold -1 and padding LLONG_MIN: negative patterns, after every valid key); an
+// integer comparison keeps the one-block sort off the GPU's narrow FP64 unit.
+__device__ __forceinline__ bool ranks_before(long long da, int ia, long long db, int ib) {
     return da > db || (da == db && ia < ib);
 }
 
@@ -265,7 +269,7 @@ __global__ void k_mm_fill(long long n, const int* __restrict__ cell_of, int* __r
 // Phase A (block 0): sort the pool by (dist desc, index asc), accept the exact prefix,
 // record the accepted points and their update boxes.
 __device__ void mm_phase_a(const MMArgs& a) {
-    __shared__ double sk[MM_PMAX];
+    __shared__ long long sk[MM_PMAX];   // dist as its bit pattern
     __shared__ int si[MM_PMAX];
     __shared__ int s_first_conflict;
     __shared__ int s_nvalid;
@@ -277,10 +281,10 @@ __device__ void mm_phase_a(const MMArgs& a) {
     for (int t = tid; t < P2; t += blockDim.x) {
         if (t < np) {
             const int i = __ldcg(a.pool + t);
-            sk[t] = __ldcg(a.dist + i);  // selected entries hold -1 and sort last
+            sk[t] = __ldcg(reinterpret_cast<const long long*>(a.dist) + i);  // selected: -1, last
             si[t] = i;
         } else {
-            sk[t] = -2.0;
+            sk[t] = LLONG_MIN;
             si[t] = INT_MAX;
         }
     }
@@ -294,7 +298,7 @@ __device__ void mm_phase_a(const MMArgs& a) {
                     const bool up = (t & kk) == 0;
                     const bool before = ranks_before(sk[u], si[u], sk[t], si[t]);
                     if (before == up) {
-                        const double td = sk[t]; sk[t] = sk[u]; sk[u] = td;
+                        const long long td = sk[t]; sk[t] = sk[u]; sk[u] = td;
                         const int ti = si[t]; si[t] = si[u]; si[u] = ti;
                     }
                 }
@@ -304,7 +308,7 @@ __device__ void mm_phase_a(const MMArgs& a) {
     // entries still at or above the threshold key form the valid head of the sorted pool
     if (tid == 0) { s_nvalid = 0; s_first_conflict = INT_MAX; }
     __syncthreads();
-    const double thr_d = *(volatile double*)&ctl->thr_d;
+    const long long thr_d = __double_as_longlong(*(volatile double*)&ctl->thr_d);   // >= 0
     const long long thr_i = *(volatile long long*)&ctl->thr_i;
     for (int t = tid; t < np; t += blockDim.x) {
         const bool ok = sk[t] > thr_d || (sk[t] == thr_d && (long long)si[t] <= thr_i);
@@ -319,24 +323,32 @@ __device__ void mm_phase_a(const MMArgs& a) {
         return;
     }
     const int T = nvalid < MM_TACC ? nvalid : MM_TACC;
-    // c_t conflicts when an earlier candidate is closer to it than its dist
-    for (int w = tid; w < T * T; w += blockDim.x) {
-        const int t = w / T, s = w - t * T;
-        if (s < t) {
-            const double s2 = sqdist_rn(a.x + (long long)si[t] * a.d, a.x + (long long)si[s] * a.d, a.d);
-            if (s2 < sk[t]) atomicMin(&s_first_conflict, t);
+    // c_t conflicts when an earlier candidate is closer to it than its dist.  The prefix
+    // ends at the first conflict, so the candidates are checked MM_TCHUNK at a time, each
+    // against every earlier one, and the check stops after the first chunk with a conflict
+    // (squared distances and dists are non-negative: compared as bit patterns).
+    for (int t0 = 0; t0 < T; t0 += MM_TCHUNK) {
+        const int t1 = t0 + MM_TCHUNK < T ? t0 + MM_TCHUNK : T;
+        for (int w = tid; w < (t1 - t0) * t1; w += blockDim.x) {
+            const int t = t0 + w / t1, s = w - (w / t1) * t1;
+            if (s < t) {
+                const double s2 = sqdist_rn(a.x + (long long)si[t] * a.d, a.x + (long long)si[s] * a.d, a.d);
+                if (__double_as_longlong(s2) < sk[t]) atomicMin(&s_first_conflict, t);
+            }
         }
+        __syncthreads();
+        if (s_first_conflict < t1) break;
     }
-    __syncthreads();
     const int p = s_first_conflict < T ? s_first_conflict : T;
     for (int t = tid; t < p; t += blockDim.x) {
         const int i = si[t];
         a.order[k + t] = i;
         a.acc_idx[t] = i;
-        a.acc_r2[t] = sk[t];
+        const double r2 = __longlong_as_double(sk[t]);
+        a.acc_r2[t] = r2;
         a.dist[i] = -1.0;
         // cells within sqrt(dist) of the point, one cell of margin on each side
-        const double R = sqrt(sk[t]);
+        const double R = sqrt(r2);
         long long cnt = 1;
         for (int q = 0; q < 3; ++q) {
             int c0 = 0, c1 = 0;
@@ -393,11 +405,11 @@ __device__ void mm_phase_b(const MMArgs& a) {
         const double* xs = a.x + (long long)__ldcg(a.acc_idx + s) * a.d;
         for (int t = a.cell_start[cell]; t < a.cell_start[cell + 1]; ++t) {
             const int u = a.cell_items[t];
-            const double du = __ldcg(a.dist + u);
-            if (!(du > 0.0)) continue;           // selected, or already at 0
-            const double s2 = sqdist_rn(a.x + (long long)u * a.d, xs, a.d);
-            if (s2 < du)
-                atomicMin(reinterpret_cast<long long*>(a.dist + u), __double_as_longlong(s2));
+            // compared as bit patterns (non-negative values order like their patterns)
+            const long long du = __ldcg(reinterpret_cast<const long long*>(a.dist) + u);
+            if (du <= 0) continue;               // selected (-1), or already at 0
+            const long long s2 = __double_as_longlong(sqdist_rn(a.x + (long long)u * a.d, xs, a.d));
+            if (s2 < du) atomicMin(reinterpret_cast<long long*>(a.dist + u), s2);
         }
     }
 }

@@ -119,8 +119,9 @@ struct MaternT<float> {
 //   Y     (1 + p) x K augmented rows: y and the columns of X, then z = D^-1 U^-1 (y, X)
 //   loc   d x K coordinates relative to the observation, divided by their ranges
 //   u     K: the unscaled pivot column during the factorisation, then u = last row of U^-1;
-//         then (sized for it) the FP64 per-observation values V
-//   G     Q x K: h_j = dSigma_j u^T, then f_j = U^-1 h_j
+//         then (sized for it) the FP64 per-observation values V.  Grouped kernels: gchunk
+//         rows of U^-1, one per member whose terms are formed together
+//   G     Q x K: h_j = dSigma_j u^T, then f_j = U^-1 h_j (grouped: gchunk such blocks)
 //   D1    exponential families (all but the Matern): per-pair weights reused by the
 //         derivative step
 //   (lf)  Matern, FP64 block: once the covariance is assembled, loc is rewritten in place
@@ -130,24 +131,30 @@ struct MaternT<float> {
 //   dinv  K FP64: 1 / d_c
 //   lp    2 FP64: the group's running product of pivot mantissas and sum of exponents, so
 //         that log det needs one logarithm per group and tile, not one per observation
+// Grouped conditioning forms the terms of up to GCH members of a group together (each
+// pair of the block evaluated once for all of them, that many times the items between
+// barriers); the planner takes fewer (gchunk) where the larger slot does not fit.
+constexpr int GCH = 4;
+
 struct SlotLayout {
     int K, A, Y, loc, u, G, D1, nT, Dbyte, dg, dinv, lp, Gs, bytes;
     __host__ __device__ void init(int m, int d, int p, int cov, int nv, int tsize,
-                                  bool grouped = false) {
+                                  bool grouped = false, int gchunk = 1) {
         K = m + 1;
         const int Q = npair_derivs(cov, d) + 1;
         int asz = K * (K - 1) / 2;
         const int gs = (Q * K * 8 + tsize - 1) / tsize;
         if (!grouped && gs > asz) asz = gs;
+        const int ch = grouped ? gchunk : 1;   // members whose terms are formed together
         A = 0;
         Y = A + asz;
         loc = Y + (1 + p) * K;
         u = loc + d * K;
         if (tsize == 4) u += (u & 1);          // 8-byte aligned: V is FP64
         int usz = (nv * 8 + tsize - 1) / tsize;
-        if (usz < K) usz = K;
+        if (usz < ch * K) usz = ch * K;
         G = u + usz;
-        D1 = G + Q * K;
+        D1 = G + ch * Q * K;
         nT = D1 + (cov == COV_MATERN ? 0 : K * (K - 1) / 2);
         Dbyte = ((nT * tsize + 7) / 8) * 8;
         dg = 0;
@@ -229,6 +236,7 @@ struct PassEnv {
     const int32_t* blk_idx;
     const int32_t* nmemb;
     long long n;
+    int gchunk;           // members whose terms are formed together
 };
 
 // Record formulas: entry t of the per-observation record is V[u1] V[v1] + V[u2] V[v2],
@@ -508,29 +516,17 @@ __device__ __forceinline__ double log_fold(double* lp) {
 //                       each dot product one item (FP64 accumulation for both working
 //                       types), hat() halving the last entry
 // then the record is added to the lane's sums.
+// finish_values: the steps after the solves, for the derivative vectors f_j at G + j Kmax
+// (f_j = U^-1 h_j already formed).
 template <int L, typename T, typename Tab>
-__device__ __forceinline__ void finish_terms(const PassEnv<T, Tab>& E, int Kp, int Q) {
+__device__ __forceinline__ void finish_values(const PassEnv<T, Tab>& E, const T* G, int Kp, int Q) {
     using N = Num<T>;
     const int gl = E.gl;
     const unsigned gmask = E.gmask;
     const int p = E.p, Kmax = E.Kmax;
-    const T* A = E.A; const T* Yg = E.Yg; T* G = E.G;
+    const T* Yg = E.Yg;
     double* V = E.V;
     const int last = Kp - 1;
-    // ---------------- f_j = U^-1 h_j (unit lower, in place) ----------------
-    for (int c = 0; c < last; ++c) {
-        const int nr = last - c;
-        int j = gl / nr, off = gl - j * nr;
-        const int jstep = L / nr, ostep = L - jstep * nr;
-        while (j < Q) {
-            const int a = c + 1 + off;
-            G[j * Kmax + a] = N::fma_(-A[a * (a - 1) / 2 + c], G[j * Kmax + c], G[j * Kmax + a]);
-            j += jstep;
-            off += ostep;
-            if (off >= nr) { off -= nr; ++j; }
-        }
-        gsync<L>(gmask);
-    }
     // ---------------- Gs = f / d (FP64, over A) ----------------
     double* Gs = E.Gs;
     {
@@ -629,6 +625,92 @@ __device__ __forceinline__ void finish_terms(const PassEnv<T, Tab>& E, int Kp, i
     accumulate_record<L>(E.sidx, V, E.acc, E.nstat, gl, gmask);
 }
 
+template <int L, typename T, typename Tab>
+__device__ __forceinline__ void finish_terms(const PassEnv<T, Tab>& E, int Kp, int Q) {
+    using N = Num<T>;
+    const int gl = E.gl;
+    const unsigned gmask = E.gmask;
+    const int Kmax = E.Kmax;
+    const T* A = E.A; T* G = E.G;
+    const int last = Kp - 1;
+    // ---------------- f_j = U^-1 h_j (unit lower, in place) ----------------
+    for (int c = 0; c < last; ++c) {
+        const int nr = last - c;
+        int j = gl / nr, off = gl - j * nr;
+        const int jstep = L / nr, ostep = L - jstep * nr;
+        while (j < Q) {
+            const int a = c + 1 + off;
+            G[j * Kmax + a] = N::fma_(-A[a * (a - 1) / 2 + c], G[j * Kmax + c], G[j * Kmax + a]);
+            j += jstep;
+            off += ostep;
+            if (off >= nr) { off -= nr; ++j; }
+        }
+        gsync<L>(gmask);
+    }
+    finish_values<L, T, Tab>(E, G, Kp, Q);
+}
+
+// The pair-derivative entries dSigma_j[a][c], j < NG, of the block in the slot (a > c):
+// from the pair weights D1 kept by the assembly (exponential families), or from the
+// coordinates and the per-pass table (Matern; on the FP64 path the squared distance in
+// double-float arithmetic from the pairs in locf, about 2^-46 relative, enough for
+// derivative entries, so that the only FP64 work left per pair is the two table values).
+template <int COV, typename T, typename Tab>
+__device__ __forceinline__ void pair_derivs(const PassEnv<T, Tab>& E, int a, int c, T* dv) {
+    using N = Num<T>;
+    using MT = MaternT<T>;
+    constexpr int NG = npair_derivs(COV);
+    const int d = E.d, Kmax = E.Kmax;
+    const T* loc = E.loc; const T* D1 = E.D1;
+    const T inv_r1T = E.inv_r1T, inv_r2T = E.inv_r2T;
+    const double inv_r1 = E.inv_r1, m_psi = E.m_psi;
+    const Tab* tab = E.tab;
+    if (COV == COV_EXP) {
+        dv[0] = D1[a * (a - 1) / 2 + c] * inv_r1T;
+    } else if (COV == COV_ST) {
+        T t0 = loc[a] - loc[c];
+        T t1 = loc[Kmax + a] - loc[Kmax + c];
+        T t2 = loc[2 * Kmax + a] - loc[2 * Kmax + c];
+        T w = D1[a * (a - 1) / 2 + c];
+        dv[0] = w * N::fma_(t0, t0, t1 * t1) * inv_r1T;
+        if (NG > 1) dv[NG - 1] = w * t2 * t2 * inv_r2T;
+    } else if constexpr (sizeof(T) == 8) {
+        float sh = 0.0f, sl = 0.0f;
+        for (int kk = 0; kk < d; ++kk) {
+            const float2 pa = E.locf[kk * Kmax + a], pc = E.locf[kk * Kmax + c];
+            const float th = __fsub_rn(pa.x, pc.x);          // two-sum of the highs
+            const float bb = __fsub_rn(th, pa.x);
+            float te = __fadd_rn(__fsub_rn(pa.x, __fsub_rn(th, bb)), __fsub_rn(-pc.x, bb));
+            te = __fadd_rn(te, __fsub_rn(pa.y, pc.y));       // plus the lows
+            const float t1 = __fadd_rn(th, te);
+            const float tl = __fsub_rn(te, __fsub_rn(t1, th));
+            const float pp = __fmul_rn(t1, t1);              // t^2 = t1^2 + 2 t1 tl
+            float pe = fmaf(t1, t1, -pp);
+            pe = fmaf(2.0f * t1, tl, pe);
+            const float ss = __fadd_rn(sh, pp);              // (sh, sl) += (pp, pe)
+            const float b2 = __fsub_rn(ss, sh);
+            float er = __fadd_rn(__fsub_rn(sh, __fsub_rn(ss, b2)), __fsub_rn(pp, b2));
+            er = __fadd_rn(er, __fadd_rn(sl, pe));
+            sh = __fadd_rn(ss, er);
+            sl = __fsub_rn(er, __fsub_rn(sh, ss));
+        }
+        double F1, F2;
+        matern_F12_df(tab, sh, sl, E.nu, m_psi, E.sig2 * inv_r1, E.sig2, F1, F2);
+        dv[0] = F1;                      // dC/drho and dC/dnu from the table
+        if (NG > 1) dv[NG - 1] = F2;
+    } else {
+        T s = (T)0;
+        for (int kk = 0; kk < d; ++kk) {
+            T t = loc[kk * Kmax + a] - loc[kk * Kmax + c];
+            s = N::fma_(t, t, s);
+        }
+        T F1, F2;
+        MT::F12(tab, s, E.nu, m_psi, E.sig2 * inv_r1, E.sig2, F1, F2);
+        dv[0] = F1;                      // dC/drho and dC/dnu from the table
+        if (NG > 1) dv[NG - 1] = F2;
+    }
+}
+
 // One conditional on the leading Kp x Kp block of the factor in the slot (its last row,
 // Kp - 1, is the observation; the rows above are what it conditions on): u = last row of
 // U^-1, h_j = dSigma_j u^T with each pair (a, c) evaluated once (a conflict-free round-robin
@@ -637,16 +719,13 @@ __device__ __forceinline__ void finish_terms(const PassEnv<T, Tab>& E, int Kp, i
 template <int COV, int L, typename T, typename Tab>
 __device__ __forceinline__ void conditional_terms(const PassEnv<T, Tab>& E, int Kp, long long i) {
     using N = Num<T>;
-    using MT = MaternT<T>;
     constexpr int NG = npair_derivs(COV);
     constexpr int Q = NG + 1;
     const int gl = E.gl;
     const unsigned gmask = E.gmask;
-    const int d = E.d, m = E.m, Kmax = E.Kmax;
-    T* u = E.u; T* G = E.G; const T* loc = E.loc; const T* D1 = E.D1;
-    const T sig2T = E.sig2T, inv_r1T = E.inv_r1T, inv_r2T = E.inv_r2T;
-    const double inv_r1 = E.inv_r1, m_psi = E.m_psi;
-    const Tab* tab = E.tab;
+    const int m = E.m, Kmax = E.Kmax;
+    T* u = E.u; T* G = E.G;
+    const T sig2T = E.sig2T;
 
     last_row_of_Uinv<L, T>(E.A, u, Kp, gl, gmask);
     if (E.factor) {
@@ -674,53 +753,7 @@ __device__ __forceinline__ void conditional_terms(const PassEnv<T, Tab>& E, int 
                 int a, c;
                 if (!circle_pair(Kp, Nv, r, k, a, c)) continue;
                 T dv[NG];
-                if (COV == COV_EXP) {
-                    dv[0] = D1[a * (a - 1) / 2 + c] * inv_r1T;
-                } else if (COV == COV_ST) {
-                    T t0 = loc[a] - loc[c];
-                    T t1 = loc[Kmax + a] - loc[Kmax + c];
-                    T t2 = loc[2 * Kmax + a] - loc[2 * Kmax + c];
-                    T w = D1[a * (a - 1) / 2 + c];
-                    dv[0] = w * N::fma_(t0, t0, t1 * t1) * inv_r1T;
-                    if (NG > 1) dv[NG - 1] = w * t2 * t2 * inv_r2T;
-                } else if constexpr (sizeof(T) == 8) {
-                    // the squared distance in double-float arithmetic from the pairs in lf
-                    // (about 2^-46 relative, enough for derivative entries), so that the
-                    // only FP64 work left per pair is the two table values and the scatter
-                    float sh = 0.0f, sl = 0.0f;
-                    for (int kk = 0; kk < d; ++kk) {
-                        const float2 pa = E.locf[kk * Kmax + a], pc = E.locf[kk * Kmax + c];
-                        const float th = __fsub_rn(pa.x, pc.x);          // two-sum of the highs
-                        const float bb = __fsub_rn(th, pa.x);
-                        float te = __fadd_rn(__fsub_rn(pa.x, __fsub_rn(th, bb)), __fsub_rn(-pc.x, bb));
-                        te = __fadd_rn(te, __fsub_rn(pa.y, pc.y));       // plus the lows
-                        const float t1 = __fadd_rn(th, te);
-                        const float tl = __fsub_rn(te, __fsub_rn(t1, th));
-                        const float pp = __fmul_rn(t1, t1);              // t^2 = t1^2 + 2 t1 tl
-                        float pe = fmaf(t1, t1, -pp);
-                        pe = fmaf(2.0f * t1, tl, pe);
-                        const float ss = __fadd_rn(sh, pp);              // (sh, sl) += (pp, pe)
-                        const float b2 = __fsub_rn(ss, sh);
-                        float er = __fadd_rn(__fsub_rn(sh, __fsub_rn(ss, b2)), __fsub_rn(pp, b2));
-                        er = __fadd_rn(er, __fadd_rn(sl, pe));
-                        sh = __fadd_rn(ss, er);
-                        sl = __fsub_rn(er, __fsub_rn(sh, ss));
-                    }
-                    double F1, F2;
-                    matern_F12_df(tab, sh, sl, E.nu, m_psi, E.sig2 * inv_r1, E.sig2, F1, F2);
-                    dv[0] = F1;                      // dC/drho and dC/dnu from the table
-                    if (NG > 1) dv[NG - 1] = F2;
-                } else {
-                    T s = (T)0;
-                    for (int kk = 0; kk < d; ++kk) {
-                        T t = loc[kk * Kmax + a] - loc[kk * Kmax + c];
-                        s = N::fma_(t, t, s);
-                    }
-                    T F1, F2;
-                    MT::F12(tab, s, E.nu, m_psi, E.sig2 * inv_r1, E.sig2, F1, F2);
-                    dv[0] = F1;                      // dC/drho and dC/dnu from the table
-                    if (NG > 1) dv[NG - 1] = F2;
-                }
+                pair_derivs<COV, T, Tab>(E, a, c, dv);
                 const T ua = u[a], uc = u[c];
 #pragma unroll
                 for (int j = 0; j < NG; ++j) {
@@ -732,6 +765,116 @@ __device__ __forceinline__ void conditional_terms(const PassEnv<T, Tab>& E, int 
         }
     }
     finish_terms<L, T, Tab>(E, Kp, Q);
+}
+
+// Grouped conditioning: the terms of members r0 .. r0 + cnt - 1 (cnt <= gchunk) of the
+// factored block in the slot.  Member r's terms are the single-observation terms on the
+// leading (r + 1) block: u_r = row r of U^-1 (the leading block's U^-1 is the leading block
+// of U^-1), h_j = dSigma_j u_r^T on rows <= r, f_j = U^-1 h_j, then the values.  Formed
+// together, each pair (a, c) of the chunk's block (Kc = r0 + cnt rows) is evaluated once
+// for all its members, and every step carries up to cnt members' items between the same
+// barriers:
+//   W   row k = u_{r0+k} (zero past its own row), by back substitution from row Kc - 1 up:
+//       row t updates the members whose row t is final (r0 + k >= t)
+//   H   G + k Q Kmax holds member k's h_j; pair (a, c) adds to the members with
+//       r0 + k >= a (both rows inside the member's block)
+//   F   unit forward substitution of all members' vectors, column by column (rows past a
+//       member's own are carried along and never read)
+// then Gs, the values and the record of each member in turn (finish_values; V reuses W).
+template <int COV, int L, typename T, typename Tab>
+__device__ __forceinline__ void group_chunk_terms(const PassEnv<T, Tab>& E, int r0, int cnt) {
+    using N = Num<T>;
+    constexpr int NG = npair_derivs(COV);
+    constexpr int Q = NG + 1;
+    const int gl = E.gl;
+    const unsigned gmask = E.gmask;
+    const int Kmax = E.Kmax;
+    const T* A = E.A;
+    T* W = E.u;
+    T* G = E.G;
+    const int Kc = r0 + cnt;
+    // ---------------- W: rows r0 .. Kc - 1 of U^-1 ----------------
+    {
+        int k = gl / Kc, a = gl - k * Kc;
+        const int ks = L / Kc, as = L - ks * Kc;
+        while (k < cnt) {
+            W[k * Kmax + a] = (a == r0 + k) ? (T)1 : (T)0;
+            k += ks;
+            a += as;
+            if (a >= Kc) { a -= Kc; ++k; }
+        }
+    }
+    gsync<L>(gmask);
+    for (int t = Kc - 1; t >= 1; --t) {
+        const int k0 = t > r0 ? t - r0 : 0;
+        const T* Ut = A + t * (t - 1) / 2;
+        int k = gl / t, a = gl - k * t;
+        k += k0;
+        const int ks = L / t, as = L - ks * t;
+        while (k < cnt) {
+            W[k * Kmax + a] = N::fma_(-Ut[a], W[k * Kmax + t], W[k * Kmax + a]);
+            k += ks;
+            a += as;
+            if (a >= t) { a -= t; ++k; }
+        }
+        gsync<L>(gmask);
+    }
+    // ---------------- H: h_j = dSigma_j u^T per member ----------------
+    {
+        int k = gl / Kc, a = gl - k * Kc;
+        const int ks = L / Kc, as = L - ks * Kc;
+        while (k < cnt) {
+            T* Gk = G + k * Q * Kmax;
+#pragma unroll
+            for (int j = 0; j < NG; ++j) Gk[j * Kmax + a] = (T)0;
+            Gk[NG * Kmax + a] = E.sig2T * W[k * Kmax + a];
+            k += ks;
+            a += as;
+            if (a >= Kc) { a -= Kc; ++k; }
+        }
+    }
+    gsync<L>(gmask);
+    {
+        const int Nv = (Kc & 1) ? Kc + 1 : Kc;
+        const int npr = Nv / 2;
+        for (int r = 0; r < Nv - 1; ++r) {
+            for (int q = gl; q < npr; q += L) {
+                int a, c;
+                if (!circle_pair(Kc, Nv, r, q, a, c)) continue;
+                T dv[NG];
+                pair_derivs<COV, T, Tab>(E, a, c, dv);
+                for (int k = a > r0 ? a - r0 : 0; k < cnt; ++k) {
+                    T* Gk = G + k * Q * Kmax;
+                    const T wa = W[k * Kmax + a], wc = W[k * Kmax + c];
+#pragma unroll
+                    for (int j = 0; j < NG; ++j) {
+                        Gk[j * Kmax + a] = N::fma_(dv[j], wc, Gk[j * Kmax + a]);
+                        Gk[j * Kmax + c] = N::fma_(dv[j], wa, Gk[j * Kmax + c]);
+                    }
+                }
+            }
+            gsync<L>(gmask);
+        }
+    }
+    // ---------------- F: f_j = U^-1 h_j per member (unit lower, in place) ----------------
+    for (int c = 0; c < Kc - 1; ++c) {
+        const int k0 = c >= r0 ? c - r0 + 1 : 0;      // members with rows past c
+        const int nr = Kc - 1 - c;
+        const int nkj = (cnt - k0) * Q;
+        T* Gc = G + k0 * Q * Kmax;
+        int kj = gl / nr, off = gl - kj * nr;
+        const int ks = L / nr, os = L - ks * nr;
+        while (kj < nkj) {
+            T* g = Gc + kj * Kmax;
+            const int a = c + 1 + off;
+            g[a] = N::fma_(-A[a * (a - 1) / 2 + c], g[c], g[a]);
+            kj += ks;
+            off += os;
+            if (off >= nr) { off -= nr; ++kj; }
+        }
+        gsync<L>(gmask);
+    }
+    for (int k = 0; k < cnt; ++k) finish_values<L, T, Tab>(E, G + k * Q * Kmax, r0 + k + 1, Q);
 }
 
 // Algorithm 1 for observation i of the dataset in E (all L lanes of the group call it).
@@ -838,7 +981,9 @@ __device__ __forceinline__ void vecchia_group(const PassEnv<T, Tab>& E, long lon
         gsync<L>(gmask);
         return;
     }
-    for (int r = Kp - nm; r < Kp; ++r) conditional_terms<COV, L, T, Tab>(E, r + 1, blk[r]);
+    const int ch = E.gchunk;
+    for (int r0 = Kp - nm; r0 < Kp; r0 += ch)
+        group_chunk_terms<COV, L, T, Tab>(E, r0, Kp - r0 < ch ? Kp - r0 : ch);
 }
 
 // Algorithm 1 for the exponential with one range per coordinate (COV_ANISO): Q = d + 1
@@ -1012,7 +1157,7 @@ __global__ void __launch_bounds__(256, pass_min_blocks(sizeof(T))) k_pass(PassAr
     double* accbase = sp;
     sp += (size_t)blockDim.x * args.acc_per_lane;
     SlotLayout SL;
-    SL.init(m, d, p, COV, args.nv, (int)sizeof(T), GROUPED);
+    SL.init(m, d, p, COV, args.nv, (int)sizeof(T), GROUPED, args.gchunk);
     char* slotc = reinterpret_cast<char*>(sp) + (size_t)grp * args.slot_stride;
     T* slot = reinterpret_cast<T*>(slotc);
     double* slotd = reinterpret_cast<double*>(slotc + SL.Dbyte);
@@ -1063,6 +1208,7 @@ __global__ void __launch_bounds__(256, pass_min_blocks(sizeof(T))) k_pass(PassAr
     E.tab = tab; E.sidx = sidx; E.acc = acc; E.nstat = args.nstat;
     E.vb0 = vb0; E.vstep = vstep; E.vmm = vmm; E.factor = nullptr;
     E.blk_off = args.blk_off; E.blk_idx = args.blk_idx; E.nmemb = args.nmemb; E.n = n;
+    E.gchunk = args.gchunk;
     if (gl == 0) { E.lp[0] = 1.0; *reinterpret_cast<long long*>(E.lp + 1) = 0; }
     if constexpr (GROUPED) {
         for (long long u = (long long)blockIdx.x * ngrp + grp; ok && u < args.ngroups; u += gstride) {
