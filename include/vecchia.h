@@ -273,10 +273,12 @@ VECCHIA_API vec_status vecchia_fit(vec_handle h, const double* locs, const doubl
  * Batch plans: the batched pass split into a host-side preparation and a device-only run.
  *
  * vecchia_batch_plan_create does everything of vecchia_batch_loglik_grad_info that needs
- * the host: it checks the batch description (point_offsets and m, HOST, as there), picks
- * the kernel mapping (forced on the handle, else the handle's batched autotuning record,
- * else planned), builds the work list, allocates the plan's own device buffers and
- * uploads the work list (waiting for the copy).  The plan is bound to the handle's
+ * the host: it checks the batch description (point_offsets and m, HOST, as there), splits
+ * the datasets into up to three classes by block size (m + 1 <= 16, <= 32, larger; each
+ * class is one launch whose shared-memory slots are sized for its own largest m), picks
+ * each class's kernel mapping (forced on the handle, else the handle's batched autotuning
+ * record for the class, else planned), builds the work list, allocates the plan's own
+ * device buffers and uploads the work list (waiting for the copy).  The plan is bound to the handle's
  * device, independent of the handle afterwards, and must be released with
  * vecchia_batch_plan_destroy.
  *
@@ -286,8 +288,11 @@ VECCHIA_API vec_status vecchia_fit(vec_handle h, const double* locs, const doubl
  * no synchronisation), so it can be captured into a CUDA graph and replayed.  Runs of one
  * plan share its buffers: two runs of the same plan must not overlap on the GPU.
  *
- * vecchia_batch_plan_mapping reports the plan's lanes per observation, threads per block
- * and number of tiles (HOST pointers, each may be NULL).
+ * vecchia_batch_plan_mapping reports the lanes per observation and threads per block of the
+ * class with the most observations, and the number of tiles of all classes (HOST pointers,
+ * each may be NULL).  vecchia_batch_plan_class reports class c (0, 1, 2: m + 1 <= 16,
+ * <= 32, larger): its largest m (-1 for a class without datasets), lanes, threads and
+ * tiles; VEC_ERR_ARG for c outside 0..2.
  */
 typedef struct vec_batch_plan_s* vec_batch_plan;
 VECCHIA_API vec_status vecchia_batch_plan_create(vec_handle h, int nbatch,
@@ -300,6 +305,8 @@ VECCHIA_API vec_status vecchia_batch_plan_run(vec_batch_plan plan, const double*
                                               void* stream, double* out, int64_t* dev_status);
 VECCHIA_API vec_status vecchia_batch_plan_mapping(vec_batch_plan plan, int* lanes, int* threads,
                                                   int* ntiles);
+VECCHIA_API vec_status vecchia_batch_plan_class(vec_batch_plan plan, int c, int* mmax, int* lanes,
+                                                int* threads, int* ntiles);
 VECCHIA_API vec_status vecchia_batch_plan_destroy(vec_batch_plan plan);
 
 /*
@@ -329,11 +336,14 @@ VECCHIA_API vec_status vecchia_batch_fit(vec_handle h, int nbatch, const double*
 /*
  * vecchia_batch_autotune -- vecchia_autotune for the batched pass.
  *
- * Times the batched pass (vecchia_batch_loglik_grad_info, same arguments) under every
- * (lanes per observation, threads per block) mapping that fits the largest m of the batch
- * and records the fastest in the handle, keyed by (covfun, largest m, d, p, prec,
- * floor(log2(total n))) apart from the single-dataset records; later batched calls with
- * a matching key use it unless a mapping is forced.  Synchronises `stream`.
+ * For each class of datasets (by block size, as the batched pass splits them; see batch
+ * plans) times the batched pass of that class's datasets (vecchia_batch_loglik_grad_info,
+ * same arguments) under every (lanes per observation, threads per block) mapping that
+ * fits the class's largest m, and records the fastest in the handle, keyed by (covfun,
+ * the class's largest m, d, p, prec, floor(log2(the class's observations))) apart from the
+ * single-dataset records; later batched calls whose classes match a key use it unless a
+ * mapping is forced.  lanes_out and threads_out: the mapping of the class with the most
+ * observations; ms_out: the sum of the classes' best times.  Synchronises `stream`.
  */
 VECCHIA_API vec_status vecchia_batch_autotune(vec_handle h, int nbatch, const double* locs,
                                               const double* y, const double* X,

@@ -123,6 +123,7 @@ def lib():
         L.vecchia_batch_plan_create.argtypes = [P, ci, P, P, ci, ci, ci, ci, ctypes.POINTER(P)]
         L.vecchia_batch_plan_run.argtypes = [P, P, P, P, P, P, P, P, P]
         L.vecchia_batch_plan_mapping.argtypes = [P, P, P, P]
+        L.vecchia_batch_plan_class.argtypes = [P, ci, P, P, P, P]
         L.vecchia_batch_plan_destroy.argtypes = [P]
         L.vecchia_fields_loglik_grad_info.argtypes = [P, ci, P, P, P, i64, ci, ci, ci, P, P, ci,
                                                       ci, P, P, P]
@@ -156,6 +157,7 @@ def lib():
                   L.vecchia_batch_loglik_grad_info, L.vecchia_batch_fit,
                   L.vecchia_batch_autotune, L.vecchia_batch_plan_create,
                   L.vecchia_batch_plan_run, L.vecchia_batch_plan_mapping,
+                  L.vecchia_batch_plan_class,
                   L.vecchia_batch_plan_destroy, L.vecchia_fields_loglik_grad_info,
                   L.vecchia_fields_fit, L.vecchia_fields_simulate,
                   L.vecchia_fields_variogram, L.vecchia_mlp_forward, L.vecchia_mlp_grad,
@@ -355,10 +357,20 @@ class BatchPlan:
         self.nbatch, self.d, self.p, self.covfun = len(mm), d, p, covfun
 
     def mapping(self) -> dict:
+        """Lanes and threads of the class with the most observations, all tiles, and per
+        class of datasets (by block size) its largest m, mapping and tiles."""
         a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         _check(lib().vecchia_batch_plan_mapping(self._p, ctypes.byref(a), ctypes.byref(b),
                                                 ctypes.byref(c)))
-        return {"lanes": a.value, "threads": b.value, "ntiles": c.value}
+        classes = []
+        for k in range(3):
+            mm, la, th, nt = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+            _check(lib().vecchia_batch_plan_class(self._p, k, ctypes.byref(mm), ctypes.byref(la),
+                                                  ctypes.byref(th), ctypes.byref(nt)))
+            if mm.value >= 0:
+                classes.append({"mmax": mm.value, "lanes": la.value, "threads": th.value,
+                                "ntiles": nt.value})
+        return {"lanes": a.value, "threads": b.value, "ntiles": c.value, "classes": classes}
 
     def run(self, locs, y, X, NNarray, covparms, out, status, stream=None):
         """Enqueues the batched pass; out (nbatch, 1+q+q*q+p) and status (nbatch, 2) are

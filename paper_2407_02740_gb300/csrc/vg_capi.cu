@@ -83,13 +83,14 @@ struct BatchScratch {
     int* status = nullptr; size_t c_status = 0;
     long long* bad = nullptr; size_t c_bad = 0;
     int* counter = nullptr; size_t c_counter = 0;
+    int* tile_ids = nullptr; size_t c_tile_ids = 0;
     double* partials = nullptr; size_t c_part = 0;
     double* tabs = nullptr; size_t c_tabs = 0;
     float* tabsf = nullptr; size_t c_tabsf = 0;
     void release() {
         cudaFree(tiles); cudaFree(tile_off); cudaFree(desc);
-        cudaFree(status); cudaFree(bad); cudaFree(counter); cudaFree(partials); cudaFree(tabs);
-        cudaFree(tabsf);
+        cudaFree(status); cudaFree(bad); cudaFree(counter); cudaFree(tile_ids); cudaFree(partials);
+        cudaFree(tabs); cudaFree(tabsf);
         *this = BatchScratch();
     }
 };
@@ -795,14 +796,47 @@ vec_status vecchia_autotune_load(vec_handle h, const char* path) {
 namespace {
 
 // Host-side description of a batch and the uploads shared by the batched pass and fit.
+// Datasets are split into up to three classes by block size K = m + 1 (K <= 16, K <= 32,
+// larger), each launched with its own kernel mapping and slots sized for its largest m: a
+// K = 11 block on the lanes chosen for K = 41 leaves most of them idle.  Tiles stay in
+// dataset order (records per tile, reduced per dataset); each class launch takes its
+// tiles from its own index list and counter.
+constexpr int kBatchClasses = 3;
+
+static int batch_class_of(int m) { return m + 1 <= 16 ? 0 : (m + 1 <= 32 ? 1 : 2); }
+
 struct BatchPlan {
     int nbatch, mmax, ntiles;
     long long ntot;
-    vg::PassPlan plan;
+    vg::PassPlan plan;                   // the class with the most observations (reported)
+    int nclass;                          // classes with datasets
+    vg::PassPlan cplan[kBatchClasses];
+    int cmmax[kBatchClasses];
+    int cbeg[kBatchClasses + 1];         // class c's tiles: tile_ids[cbeg[c] .. cbeg[c + 1])
     std::vector<int4> tiles;
     std::vector<int> tile_off;
+    std::vector<int> tile_ids;
     std::vector<vg::DatasetDesc> desc;
 };
+
+// Mapping of one class: forced, else autotuned for (cov, class mmax, d, p, prec, class
+// observations), else planned.  Returns a vec_status.
+static vec_status plan_batch_class(vec_handle h, int cov, int mmax, long long ntot, int d, int p,
+                                   int prec, vg::PassPlan* plan) {
+    int L = h->lanes, thr = h->threads, tab = -1;
+    if (L == 0 && thr == 0) {
+        const int lg = ilog2(ntot);
+        for (const TuneEntry& t : h->tune)
+            if (t.cov == cov && t.m == mmax && t.d == d && t.p == p && t.prec == prec + 2 &&
+                t.log2n == lg) { L = t.lanes; thr = t.threads; tab = t.tab; }
+    }
+    if (h->tab_mode >= 0) tab = h->tab_mode;
+    int pr = vg::plan_pass(cov, mmax, d, p, h->nsm, L, thr, plan, prec, true, tab);
+    if (pr == -1) pr = vg::plan_pass(cov, mmax, d, p, h->nsm, h->lanes, h->threads, plan, prec, true);
+    if (pr == -1) return fail(VEC_ERR_UNSUPPORTED, "no kernel mapping fits m = %d, p = %d", mmax, p);
+    if (pr != 0) return cuda_fail(cudaGetLastError(), "planning the batched pass");
+    return VEC_OK;
+}
 
 // Plans and uploads a batch described dataset by dataset (B->desc filled by the caller).
 vec_status prepare_batch_desc(vec_handle h, BatchScratch& S, int d, int p, vec_covfun covfun,
@@ -812,6 +846,8 @@ vec_status prepare_batch_desc(vec_handle h, BatchScratch& S, int d, int p, vec_c
     B->nbatch = nbatch;
     B->mmax = 0;
     B->ntot = 0;
+    long long cn[kBatchClasses] = {0, 0, 0};
+    for (int c = 0; c < kBatchClasses; ++c) B->cmmax[c] = -1;
     for (int b = 0; b < nbatch; ++b) {
         const vg::DatasetDesc& D = B->desc[b];
         if (D.n < 1) return fail(VEC_ERR_ARG, "dataset %d has n = %d", b, D.n);
@@ -819,26 +855,38 @@ vec_status prepare_batch_desc(vec_handle h, BatchScratch& S, int d, int p, vec_c
             return fail(VEC_ERR_UNSUPPORTED, "dataset %d: m = %d out of range", b, D.m);
         if (D.m > B->mmax) B->mmax = D.m;
         B->ntot += D.n;
+        const int c = batch_class_of(D.m);
+        cn[c] += D.n;
+        if (D.m > B->cmmax[c]) B->cmmax[c] = D.m;
     }
     const int cov = (int)covfun;
-    // mapping: forced, else autotuned for (cov, mmax, d, p, prec, total n), else planned
-    int L = h->lanes, thr = h->threads, tab = -1;
-    if (L == 0 && thr == 0) {
-        const int lg = ilog2(B->ntot);
-        for (const TuneEntry& t : h->tune)
-            if (t.cov == cov && t.m == B->mmax && t.d == d && t.p == p && t.prec == prec + 2 &&
-                t.log2n == lg) { L = t.lanes; thr = t.threads; tab = t.tab; }
+    B->nclass = 0;
+    int main_c = -1;
+    for (int c = 0; c < kBatchClasses; ++c) {
+        if (cn[c] == 0) continue;
+        ++B->nclass;
+        vec_status s = plan_batch_class(h, cov, B->cmmax[c], cn[c], d, p, prec, &B->cplan[c]);
+        if (s != VEC_OK) return s;
+        if (main_c < 0 || cn[c] > cn[main_c]) main_c = c;
     }
-    if (h->tab_mode >= 0) tab = h->tab_mode;
-    int pr = vg::plan_pass(cov, B->mmax, d, p, h->nsm, L, thr, &B->plan, prec, true, tab);
-    if (pr == -1) pr = vg::plan_pass(cov, B->mmax, d, p, h->nsm, h->lanes, h->threads, &B->plan, prec, true);
-    if (pr == -1) return fail(VEC_ERR_UNSUPPORTED, "no kernel mapping fits m = %d, p = %d", B->mmax, p);
-    if (pr != 0) return cuda_fail(cudaGetLastError(), "planning the batched pass");
-    const int ngrp = B->plan.threads / B->plan.L;
-    const long long tsize = ngrp * 32 > 256 ? ngrp * 32 : 256;
+    B->plan = B->cplan[main_c];
+    // tiles in dataset order; a class's tiles hold up to 32 observations per group of its
+    // mapping, fewer where that would leave fewer than about four tiles per block of its
+    // launch (the last tiles of a launch set its tail); then the index lists
+    long long csize[kBatchClasses];
+    for (int c = 0; c < kBatchClasses; ++c) {
+        if (cn[c] == 0) continue;
+        const vg::PassPlan& P = B->cplan[c];
+        const long long ngrp = P.threads / P.L;
+        const long long per = (cn[c] + 4LL * P.grid - 1) / (4LL * P.grid);
+        long long t = per > ngrp ? per : ngrp;
+        t = t > 64 ? t : 64;
+        csize[c] = t < ngrp * 32 ? t : ngrp * 32;
+    }
     B->tiles.clear();
     B->tile_off.assign(nbatch + 1, 0);
     for (int b = 0; b < nbatch; ++b) {
+        const long long tsize = csize[batch_class_of(B->desc[b].m)];
         const long long nb = B->desc[b].n;
         for (long long s0 = 0; s0 < nb; s0 += tsize) {
             long long e0 = s0 + tsize < nb ? s0 + tsize : nb;
@@ -847,12 +895,23 @@ vec_status prepare_batch_desc(vec_handle h, BatchScratch& S, int d, int p, vec_c
         B->tile_off[b + 1] = (int)B->tiles.size();
     }
     B->ntiles = (int)B->tiles.size();
+    B->tile_ids.clear();
+    for (int c = 0; c < kBatchClasses; ++c) {
+        B->cbeg[c] = (int)B->tile_ids.size();
+        if (B->nclass > 1)
+            for (int b = 0; b < nbatch; ++b)
+                if (batch_class_of(B->desc[b].m) == c)
+                    for (int t = B->tile_off[b]; t < B->tile_off[b + 1]; ++t) B->tile_ids.push_back(t);
+    }
+    B->cbeg[kBatchClasses] = (int)B->tile_ids.size();
     cudaError_t e = grow(&S.tiles, &S.c_tiles, (size_t)B->ntiles);
     if (e == cudaSuccess) e = grow(&S.tile_off, &S.c_tile_off, (size_t)nbatch + 1);
     if (e == cudaSuccess) e = grow(&S.desc, &S.c_desc, (size_t)nbatch);
     if (e == cudaSuccess) e = grow(&S.status, &S.c_status, (size_t)nbatch);
     if (e == cudaSuccess) e = grow(&S.bad, &S.c_bad, (size_t)nbatch);
-    if (e == cudaSuccess) e = grow(&S.counter, &S.c_counter, (size_t)1);
+    if (e == cudaSuccess) e = grow(&S.counter, &S.c_counter, (size_t)kBatchClasses);
+    if (e == cudaSuccess && !B->tile_ids.empty())
+        e = grow(&S.tile_ids, &S.c_tile_ids, B->tile_ids.size());
     if (e == cudaSuccess) e = grow(&S.partials, &S.c_part, (size_t)B->ntiles * B->plan.nstat);
     if (e == cudaSuccess && vg::uses_table(cov, prec))
         e = grow(&S.tabs, &S.c_tabs, (size_t)nbatch * vg::mtab_doubles());
@@ -864,14 +923,35 @@ vec_status prepare_batch_desc(vec_handle h, BatchScratch& S, int d, int p, vec_c
         e = cudaMemcpyAsync(S.tile_off, B->tile_off.data(), sizeof(int) * (nbatch + 1), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(S.desc, B->desc.data(), sizeof(vg::DatasetDesc) * nbatch, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !B->tile_ids.empty())
+        e = cudaMemcpyAsync(S.tile_ids, B->tile_ids.data(), sizeof(int) * B->tile_ids.size(),
+                            cudaMemcpyHostToDevice, st);
     // the host vectors are released when B goes out of scope: make the copies complete
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "uploading the batch description");
     return VEC_OK;
 }
 
-// Concatenated datasets: dataset b owns rows [off[b], off[b+1]) and the next n_b (m_b+1)
-// NNarray entries.
+// Dataset descriptions of concatenated datasets: dataset b owns rows [off[b], off[b+1])
+// and the next n_b (m_b+1) NNarray entries.
+vec_status batch_descs(int nbatch, const int64_t* point_offsets, const int* m,
+                       std::vector<vg::DatasetDesc>* desc) {
+    desc->assign(nbatch, vg::DatasetDesc());
+    long long nn = 0;
+    for (int b = 0; b < nbatch; ++b) {
+        const long long nb = point_offsets[b + 1] - point_offsets[b];
+        if (nb < 1) return fail(VEC_ERR_ARG, "dataset %d has n = %lld", b, nb);
+        vg::DatasetDesc& D = (*desc)[b];
+        D.loc = D.x = D.y = point_offsets[b];
+        D.nn = nn;
+        D.n = (int)nb;
+        D.m = m[b];
+        nn += nb * (long long)(m[b] + 1);
+    }
+    return VEC_OK;
+}
+
+// Concatenated datasets (batch_descs), planned and uploaded.
 vec_status prepare_batch(vec_handle h, BatchScratch& S, int nbatch, const int64_t* point_offsets,
                          const int* m, int d, int p, vec_covfun covfun, int prec, cudaStream_t st,
                          BatchPlan* B) {
@@ -879,18 +959,8 @@ vec_status prepare_batch(vec_handle h, BatchScratch& S, int nbatch, const int64_
     if (!point_offsets || !m) return fail(VEC_ERR_ARG, "point_offsets and m are required");
     if (point_offsets[0] != 0) return fail(VEC_ERR_ARG, "point_offsets[0] must be 0");
     if (point_offsets[nbatch] > (int64_t)INT_MAX) return fail(VEC_ERR_ARG, "too many observations");
-    B->desc.assign(nbatch, vg::DatasetDesc());
-    long long nn = 0;
-    for (int b = 0; b < nbatch; ++b) {
-        const long long nb = point_offsets[b + 1] - point_offsets[b];
-        if (nb < 1) return fail(VEC_ERR_ARG, "dataset %d has n = %lld", b, nb);
-        vg::DatasetDesc& D = B->desc[b];
-        D.loc = D.x = D.y = point_offsets[b];
-        D.nn = nn;
-        D.n = (int)nb;
-        D.m = m[b];
-        nn += nb * (long long)(m[b] + 1);
-    }
+    vec_status s = batch_descs(nbatch, point_offsets, m, &B->desc);
+    if (s != VEC_OK) return s;
     return prepare_batch_desc(h, S, d, p, covfun, prec, st, B);
 }
 
@@ -922,22 +992,29 @@ vec_status enqueue_batch(const BatchScratch& S, const BatchPlan& B, const double
                          double* factor = nullptr) {
     const int cov = (int)covfun;
     const int q = vecchia_nparms_d(covfun, d);
-    cudaError_t e = vg::launch_init_batch(S.status, S.bad, B.nbatch, S.counter, st);
+    cudaError_t e = vg::launch_init_batch(S.status, S.bad, B.nbatch, S.counter, kBatchClasses, st);
     if (e == cudaSuccess && vg::uses_table(cov, prec))
         e = vg::launch_mtab_build_batch(cov, covparms, B.nbatch, q, S.tabs, prec ? S.tabsf : nullptr,
                                         active, st);
     if (e != cudaSuccess) return cuda_fail(e, "launching the batch setup kernels");
-    vg::BatchArgs a;
-    a.base.locs = locs; a.base.y = y; a.base.X = X; a.base.NN = NN; a.base.covparms = nullptr;
-    a.base.mtab = nullptr; a.base.mtabf = nullptr; a.base.partials = S.partials;
-    a.base.status = nullptr; a.base.bad = nullptr;
-    a.base.n = B.ntot; a.base.d = d; a.base.p = p; a.base.m = B.mmax;
-    a.base.nstat = B.plan.nstat; a.base.nv = B.plan.nv; a.base.slot_stride = B.plan.slot_stride;
-    a.base.acc_per_lane = B.plan.acc_per_lane; a.base.tab_in_smem = B.plan.tab_smem;
-    a.desc = S.desc; a.covparms_b = covparms; a.factor = factor;
-    a.tabs = S.tabs; a.tabsf = S.tabsf; a.tiles = S.tiles; a.ntiles = B.ntiles;
-    a.tile_counter = S.counter; a.status_b = S.status; a.bad_b = S.bad; a.active_b = active;
-    e = vg::launch_pass_batch(cov, B.plan, a, st);
+    for (int c = 0; c < kBatchClasses && e == cudaSuccess; ++c) {
+        const int one = B.nclass == 1;
+        if (B.cmmax[c] < 0) continue;
+        const vg::PassPlan& P = B.cplan[c];
+        vg::BatchArgs a;
+        a.base.locs = locs; a.base.y = y; a.base.X = X; a.base.NN = NN; a.base.covparms = nullptr;
+        a.base.mtab = nullptr; a.base.mtabf = nullptr; a.base.partials = S.partials;
+        a.base.status = nullptr; a.base.bad = nullptr;
+        a.base.n = B.ntot; a.base.d = d; a.base.p = p; a.base.m = B.cmmax[c];
+        a.base.nstat = P.nstat; a.base.nv = P.nv; a.base.slot_stride = P.slot_stride;
+        a.base.acc_per_lane = P.acc_per_lane; a.base.tab_in_smem = P.tab_smem;
+        a.desc = S.desc; a.covparms_b = covparms; a.factor = factor;
+        a.tabs = S.tabs; a.tabsf = S.tabsf; a.tiles = S.tiles;
+        a.tile_ids = one ? nullptr : S.tile_ids + B.cbeg[c];
+        a.ntiles = one ? B.ntiles : B.cbeg[c + 1] - B.cbeg[c];
+        a.tile_counter = S.counter + c; a.status_b = S.status; a.bad_b = S.bad; a.active_b = active;
+        e = vg::launch_pass_batch(cov, P, a, st);
+    }
     if (e == cudaSuccess && factor)  // factor rows only: report the per-dataset status
         e = vg::launch_batch_status(S.status, S.bad, B.nbatch, dev_status, st);
     else if (e == cudaSuccess)
@@ -1048,6 +1125,19 @@ vec_status vecchia_batch_plan_mapping(vec_batch_plan plan, int* lanes, int* thre
     if (lanes) *lanes = plan->B.plan.L;
     if (threads) *threads = plan->B.plan.threads;
     if (ntiles) *ntiles = plan->B.ntiles;
+    return VEC_OK;
+}
+
+vec_status vecchia_batch_plan_class(vec_batch_plan plan, int c, int* mmax, int* lanes, int* threads,
+                                    int* ntiles) {
+    if (!plan) return fail(VEC_ERR_ARG, "vecchia_batch_plan_class: NULL plan");
+    if (c < 0 || c >= kBatchClasses) return fail(VEC_ERR_ARG, "vecchia_batch_plan_class: class %d", c);
+    const BatchPlan& B = plan->B;
+    const bool has = B.cmmax[c] >= 0;
+    if (mmax) *mmax = has ? B.cmmax[c] : -1;
+    if (lanes) *lanes = has ? B.cplan[c].L : 0;
+    if (threads) *threads = has ? B.cplan[c].threads : 0;
+    if (ntiles) *ntiles = !has ? 0 : (B.nclass == 1 ? B.ntiles : B.cbeg[c + 1] - B.cbeg[c]);
     return VEC_OK;
 }
 
@@ -1224,45 +1314,74 @@ vec_status vecchia_batch_autotune(vec_handle h, int nbatch, const double* locs, 
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     const int saved_L = h->lanes, saved_T = h->threads, saved_tab = h->tab_mode;
-    int bestL = 0, bestT = 0, mmax = 0;
-    float best = 1e30f;
-    for (int b = 0; b < nbatch; ++b) mmax = m[b] > mmax ? m[b] : mmax;
+    // each class of datasets (by block size, as the batch plan splits them) is tuned on its
+    // own datasets, and recorded under its largest m and its observation count
+    std::vector<vg::DatasetDesc> all;
+    if (e == cudaSuccess) s = batch_descs(nbatch, point_offsets, m, &all);
+    int repL = 0, repT = 0;
+    long long repN = -1;
+    float total = 0.f;
     static const int thr_list[] = {256, 192, 128, 96, 64};
-    int bestTab = -1;
     const int ntab = vg::uses_table(cov, (int)prec) ? 2 : 1;
-    for (int ti = 0; ti < 5 && e == cudaSuccess && s == VEC_OK; ++ti) {
-        for (int L = 1; L <= 32 && e == cudaSuccess; L *= 2)
-        for (int tb = 0; tb < ntab && e == cudaSuccess; ++tb) {
-            const int tab = vg::uses_table(cov, (int)prec) ? 1 - tb : -1;
-            if (L > thr_list[ti]) continue;
-            vg::PassPlan plan;
-            if (vg::plan_pass(cov, mmax, d, p, h->nsm, L, thr_list[ti], &plan, (int)prec, true, tab) != 0)
-                continue;
-            if (plan.L != L || plan.threads != thr_list[ti]) continue;
-            h->lanes = L;
-            h->threads = thr_list[ti];
-            h->tab_mode = tab;
-            BatchPlan B;
-            s = prepare_batch(h, h->bs, nbatch, point_offsets, m, d, p, covfun, (int)prec, st, &B);
-            if (s != VEC_OK) break;
-            s = enqueue_batch(h->bs, B, locs, y, X, NNarray, d, p, covparms, covfun, (int)prec, st, out,
-                              dst, nullptr);
-            if (s != VEC_OK) break;
-            float tmin = 1e30f;
-            for (int r = 0; r < reps && e == cudaSuccess; ++r) {
-                e = cudaEventRecord(e0, st);
+    for (int c = 0; c < kBatchClasses && e == cudaSuccess && s == VEC_OK; ++c) {
+        std::vector<vg::DatasetDesc> sub;
+        int mmax = 0;
+        long long ntot = 0;
+        for (const vg::DatasetDesc& D : all)
+            if (batch_class_of(D.m) == c) {
+                sub.push_back(D);
+                mmax = D.m > mmax ? D.m : mmax;
+                ntot += D.n;
+            }
+        if (sub.empty()) continue;
+        int bestL = 0, bestT = 0, bestTab = -1;
+        float best = 1e30f;
+        for (int ti = 0; ti < 5 && e == cudaSuccess && s == VEC_OK; ++ti) {
+            for (int L = 1; L <= 32 && e == cudaSuccess && s == VEC_OK; L *= 2)
+            for (int tb = 0; tb < ntab && e == cudaSuccess; ++tb) {
+                const int tab = vg::uses_table(cov, (int)prec) ? 1 - tb : -1;
+                if (L > thr_list[ti]) continue;
+                vg::PassPlan plan;
+                if (vg::plan_pass(cov, mmax, d, p, h->nsm, L, thr_list[ti], &plan, (int)prec, true, tab) != 0)
+                    continue;
+                if (plan.L != L || plan.threads != thr_list[ti]) continue;
+                h->lanes = L;
+                h->threads = thr_list[ti];
+                h->tab_mode = tab;
+                BatchPlan B;
+                B.desc = sub;
+                s = prepare_batch_desc(h, h->bs, d, p, covfun, (int)prec, st, &B);
+                if (s != VEC_OK) break;
                 s = enqueue_batch(h->bs, B, locs, y, X, NNarray, d, p, covparms, covfun, (int)prec, st,
                                   out, dst, nullptr);
                 if (s != VEC_OK) break;
-                if (e == cudaSuccess) e = cudaEventRecord(e1, st);
-                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-                float ms = 0.f;
-                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-                if (ms < tmin) tmin = ms;
+                float tmin = 1e30f;
+                for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+                    e = cudaEventRecord(e0, st);
+                    s = enqueue_batch(h->bs, B, locs, y, X, NNarray, d, p, covparms, covfun, (int)prec,
+                                      st, out, dst, nullptr);
+                    if (s != VEC_OK) break;
+                    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+                    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                    float ms = 0.f;
+                    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                    if (ms < tmin) tmin = ms;
+                }
+                if (s != VEC_OK) break;
+                if (tmin < best) { best = tmin; bestL = L; bestT = thr_list[ti]; bestTab = tab; }
             }
-            if (s != VEC_OK) break;
-            if (tmin < best) { best = tmin; bestL = L; bestT = thr_list[ti]; bestTab = tab; }
         }
+        if (s != VEC_OK || e != cudaSuccess) break;
+        if (bestL == 0) { s = fail(VEC_ERR_UNSUPPORTED, "vecchia_batch_autotune: no mapping fits"); break; }
+        // batched records are kept apart from single-dataset ones: prec + 2
+        TuneEntry t = {cov, mmax, d, p, (int)prec + 2, ilog2(ntot), bestL, bestT, best, bestTab};
+        bool replaced = false;
+        for (TuneEntry& u : h->tune)
+            if (u.cov == t.cov && u.m == t.m && u.d == t.d && u.p == t.p && u.prec == t.prec &&
+                u.log2n == t.log2n) { u = t; replaced = true; }
+        if (!replaced) h->tune.push_back(t);
+        total += best;
+        if (ntot > repN) { repN = ntot; repL = bestL; repT = bestT; }
     }
     h->lanes = saved_L;
     h->threads = saved_T;
@@ -1273,18 +1392,9 @@ vec_status vecchia_batch_autotune(vec_handle h, int nbatch, const double* locs, 
     cudaFree(dst);
     if (s != VEC_OK) return s;
     if (e != cudaSuccess) return cuda_fail(e, "vecchia_batch_autotune");
-    if (bestL == 0) return fail(VEC_ERR_UNSUPPORTED, "vecchia_batch_autotune: no mapping fits");
-    // batched records are kept apart from single-dataset ones: prec + 2
-    TuneEntry t = {cov, mmax, d, p, (int)prec + 2, ilog2(point_offsets[nbatch]), bestL, bestT, best,
-                   bestTab};
-    bool replaced = false;
-    for (TuneEntry& u : h->tune)
-        if (u.cov == t.cov && u.m == t.m && u.d == t.d && u.p == t.p && u.prec == t.prec &&
-            u.log2n == t.log2n) { u = t; replaced = true; }
-    if (!replaced) h->tune.push_back(t);
-    if (lanes_out) *lanes_out = bestL;
-    if (threads_out) *threads_out = bestT;
-    if (ms_out) *ms_out = best;
+    if (lanes_out) *lanes_out = repL;
+    if (threads_out) *threads_out = repT;
+    if (ms_out) *ms_out = total;
     return VEC_OK;
 }
 

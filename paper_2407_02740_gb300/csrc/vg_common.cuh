@@ -197,7 +197,9 @@ struct BatchArgs {
     const double* __restrict__ tabs;        // nbatch x MT_DOUBLES (Matern)
     const float* __restrict__ tabsf;        // nbatch x MT_FLOATS (Matern, mixed)
     const int4* __restrict__ tiles;         // (dataset, first, end, unused)
-    int ntiles;
+    const int* __restrict__ tile_ids;       // this launch's tiles (indices into tiles), or
+                                            // nullptr for tiles 0 .. ntiles - 1
+    int ntiles;                             // tiles of this launch
     int* tile_counter;
     int* status_b;                      // nbatch
     long long* bad_b;                   // nbatch

@@ -102,7 +102,7 @@ cudaError_t launch_sim_recur(const double* factor, const int32_t* NN, int n, int
 cudaError_t launch_batch_status(const int* status_b, const long long* bad_b, int nbatch,
                                long long* dev_status, cudaStream_t st);
 cudaError_t launch_init_batch(int* status_b, long long* bad_b, int nbatch, int* tile_counter,
-                              cudaStream_t st);
+                              int ncounter, cudaStream_t st);
 cudaError_t launch_profile_batch(const double* partials, const int* tile_off, int nbatch, int nstat,
                                  int p, int q, const DatasetDesc* desc, const double* covparms_b,
                                  const int* status_b, const long long* bad_b, double* out,

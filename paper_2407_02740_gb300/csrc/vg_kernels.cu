@@ -289,12 +289,13 @@ __global__ void k_batch_status(const int* status_b, const long long* bad_b, int 
     dev_status[2 * (size_t)b + 1] = bad_b[b] == LLONG_MAX ? -1 : bad_b[b];
 }
 
-__global__ void k_init_batch(int* status_b, long long* bad_b, int nbatch, int* tile_counter) {
+__global__ void k_init_batch(int* status_b, long long* bad_b, int nbatch, int* tile_counter,
+                             int ncounter) {
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbatch; b += gridDim.x * blockDim.x) {
         status_b[b] = 0;
         bad_b[b] = LLONG_MAX;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) *tile_counter = 0;
+    if (blockIdx.x == 0 && (int)threadIdx.x < ncounter) tile_counter[threadIdx.x] = 0;
 }
 
 // Covariance C and its q theta-derivatives for npairs location pairs (AoS, d each).
@@ -515,8 +516,10 @@ cudaError_t launch_batch_status(const int* status_b, const long long* bad_b, int
 }
 
 cudaError_t launch_init_batch(int* status_b, long long* bad_b, int nbatch, int* tile_counter,
-                              cudaStream_t st) {
-    k_init_batch<<<(nbatch + 255) / 256, 256, 0, st>>>(status_b, bad_b, nbatch, tile_counter);
+                              int ncounter, cudaStream_t st) {
+    if (ncounter < 1 || ncounter > 256) return cudaErrorInvalidValue;
+    k_init_batch<<<(nbatch + 255) / 256, 256, 0, st>>>(status_b, bad_b, nbatch, tile_counter,
+                                                       ncounter);
     return cudaGetLastError();
 }
 

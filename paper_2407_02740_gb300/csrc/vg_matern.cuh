@@ -186,7 +186,7 @@ __device__ __forceinline__ int mtab_locate_pair(double s, float& wf, float& wl) 
 // in every derivative entry moves the gradient by ~1e-11 of its scale even at a nugget of
 // 0.001), whereas the covariance itself is amplified by the block's conditioning and keeps
 // its FP64 head (horner_split).
-__device__ __forceinline__ double horner_df(const double* c, float wh, float wl) {
+__device__ __forceinline__ float2 horner_df_pair(const double* c, float wh, float wl) {
     const float* t = reinterpret_cast<const float*>(c + MT_NHEAD);
     float ph = t[4];
     ph = fmaf(ph, wh, t[3]);
@@ -209,7 +209,11 @@ __device__ __forceinline__ double horner_df(const double* c, float wh, float wl)
         ph = __fadd_rn(sm, er);
         pl = __fsub_rn(er, __fsub_rn(ph, sm));
     }
-    return f32_to_f64_bits(ph) + f32_to_f64_bits(pl);
+    return make_float2(ph, pl);
+}
+__device__ __forceinline__ double horner_df(const double* c, float wh, float wl) {
+    const float2 r = horner_df_pair(c, wh, wl);
+    return f32_to_f64_bits(r.x) + f32_to_f64_bits(r.y);
 }
 
 // The derivative pair F1, F2 at s given as a double-float value sh + sl (FP32 numbers,
@@ -297,6 +301,17 @@ __device__ __forceinline__ double exp_F12(const double* tab, double s, double si
     if (it == -2 || !(s > 0.0)) return 0.0;
     const double x = sqrt(s), e = sig2 * exp(-x);
     return f == 1 ? x * e : e / x;
+}
+// exp_F12 as an unevaluated double-float pair (hi + lo is the value, about 2^-46
+// relative), for callers that go on in double-float arithmetic: no FP64 instruction inside
+// the table; outside it the FP64 value, split.
+__device__ __forceinline__ float2 exp_F12_pair(const double* tab, double s, double sig2, int f) {
+    float wf, wl;
+    const int it = mtab_locate_pair(s, wf, wl);
+    if (it >= 0) return horner_df_pair(tab + it * MT_PER_INT + f * MT_FSTRIDE, wf, wl);
+    const double v = exp_F12(tab, s, sig2, f);
+    const float hi = __double2float_rn(v);
+    return make_float2(hi, __double2float_rn(v - (double)hi));
 }
 
 // F0, F1, F2 at x > 0 by the trapezoid rule (h = 0.1; see the header), for the table

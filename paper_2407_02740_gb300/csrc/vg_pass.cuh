@@ -1054,7 +1054,8 @@ __device__ __forceinline__ void vecchia_point_aniso(const PassEnv<T, Tab>& E, lo
         }
         if constexpr (sizeof(T) == 8) {                  // the per-pass table
             A[ea] = exp_F0(E.tab, s0 + s1, E.sig2);
-            D1[a * (a - 1) / 2 + c] = exp_F12(E.tab, s0 + s1, E.sig2, 2);   // C / D
+            // C / D as a double-float pair (the derivative step works in double-float)
+            reinterpret_cast<float2*>(D1)[ea] = exp_F12_pair(E.tab, s0 + s1, E.sig2, 2);
         } else {
             const T Dd = N::sqrt_(s0 + s1);
             const T C = E.sig2T * N::exp_(-Dd);
@@ -1083,23 +1084,57 @@ __device__ __forceinline__ void vecchia_point_aniso(const PassEnv<T, Tab>& E, lo
     for (int a = gl; a < Kp; a += L) {
         for (int k = 0; k < NG; ++k) G[k * Kmax + a] = (T)0;
         G[NG * Kmax + a] = E.sig2T * u[a];
+        if constexpr (sizeof(T) == 8)     // the coordinates as double-float pairs, in place
+            for (int k = 0; k < d; ++k) {
+                const double v = loc[k * Kmax + a];
+                const float hi = Num<float>::fromd(v);
+                E.locf[k * Kmax + a] = make_float2(hi, Num<float>::fromd(v - f32_to_f64_bits(hi)));
+            }
     }
     gsync<L>(gmask);
     {
+        // Each round's items are (pair, coordinate): d per pair, spread over all the lanes
+        // (the pairs of a round are vertex-disjoint, so no two items write one entry).  On
+        // the FP64 path the entry w t_k^2 is formed in double-float arithmetic (t_k from the
+        // coordinate pairs, w from the assembly's pair weights; about 2^-46 relative, enough
+        // for derivative entries) and enters the FP64 scatter through one addition.
         const int Nv = (Kp & 1) ? Kp + 1 : Kp;
         const int npr = Nv / 2;
         for (int r = 0; r < Nv - 1; ++r) {
-            for (int k2 = gl; k2 < npr; k2 += L) {
+            int k2 = gl / NG, k = gl - k2 * NG;
+            const int k2s = L / NG, ks = L - k2s * NG;
+            for (; k2 < npr; ) {
                 int a, c;
-                if (!circle_pair(Kp, Nv, r, k2, a, c)) continue;
-                const T w = D1[a * (a - 1) / 2 + c];
-                const T ua = u[a], uc = u[c];
-                for (int k = 0; k < NG; ++k) {
-                    const T t = loc[k * Kmax + a] - loc[k * Kmax + c];
-                    const T v = (w * t) * t;
-                    G[k * Kmax + a] = N::fma_(v, uc, G[k * Kmax + a]);
-                    G[k * Kmax + c] = N::fma_(v, ua, G[k * Kmax + c]);
+                if (circle_pair(Kp, Nv, r, k2, a, c)) {
+                    T v;
+                    if constexpr (sizeof(T) == 8) {
+                        const float2 w = reinterpret_cast<const float2*>(D1)[a * (a - 1) / 2 + c];
+                        const float2 pa = E.locf[k * Kmax + a], pc = E.locf[k * Kmax + c];
+                        const float th = __fsub_rn(pa.x, pc.x);          // two-sum of the highs
+                        const float bb = __fsub_rn(th, pa.x);
+                        float te = __fadd_rn(__fsub_rn(pa.x, __fsub_rn(th, bb)), __fsub_rn(-pc.x, bb));
+                        te = __fadd_rn(te, __fsub_rn(pa.y, pc.y));       // plus the lows
+                        const float t1 = __fadd_rn(th, te);
+                        const float tl = __fsub_rn(te, __fsub_rn(t1, th));
+                        const float pp = __fmul_rn(t1, t1);              // t^2 = t1^2 + 2 t1 tl
+                        float pe = fmaf(t1, t1, -pp);
+                        pe = fmaf(2.0f * t1, tl, pe);
+                        const float vh = __fmul_rn(w.x, pp);             // w t^2
+                        float vl = fmaf(w.x, pp, -vh);
+                        vl = fmaf(w.x, pe, vl);
+                        vl = fmaf(w.y, pp, vl);
+                        v = f32_to_f64_bits(vh) + f32_to_f64_bits(vl);
+                    } else {
+                        const T w = D1[a * (a - 1) / 2 + c];
+                        const T t = loc[k * Kmax + a] - loc[k * Kmax + c];
+                        v = (w * t) * t;
+                    }
+                    G[k * Kmax + a] = N::fma_(v, u[c], G[k * Kmax + a]);
+                    G[k * Kmax + c] = N::fma_(v, u[a], G[k * Kmax + c]);
                 }
+                k2 += k2s;
+                k += ks;
+                if (k >= NG) { k -= NG; ++k2; }
             }
             gsync<L>(gmask);
         }
@@ -1299,8 +1334,8 @@ __global__ void __launch_bounds__(256, pass_min_blocks(sizeof(T))) k_pass_batch(
     for (;;) {
         if (tid == 0) s_tile = atomicAdd(bargs.tile_counter, 1);
         __syncthreads();
-        const int t = s_tile;
-        if (t >= bargs.ntiles) break;
+        if (s_tile >= bargs.ntiles) break;
+        const int t = bargs.tile_ids ? bargs.tile_ids[s_tile] : s_tile;   // record index
         const int4 tile = bargs.tiles[t];
         const int b = tile.x;
         if (b != cur_b) {

@@ -203,3 +203,36 @@ def test_batch_plan_run_and_graph_replay():
     finally:
         plan.close()
         h.close()
+
+
+@pytest.mark.slow
+def test_full_size_batch_matches_oracle_and_single_passes():
+    # the 256-dataset workload at full size (3.35 M observations, n in [1000, 50000],
+    # m in {10, 20, 40}) in the default batch plan: the smallest dataset of each m against
+    # the FP64 oracle, and the largest datasets against their own single-dataset passes
+    bw = workloads.cfg_batch()
+    h = vg.Handle(0)
+    try:
+        out, st = _batch(bw, bw.theta_true, "fp64", h)
+        assert np.all(st[:, 0] == 0)
+        sizes = np.diff(bw.offsets)
+        for m in sorted(set(int(v) for v in bw.m)):
+            b = int(min((i for i in range(bw.nbatch) if bw.m[i] == m), key=lambda i: sizes[i]))
+            w = bw.dataset(b)
+            o = oracle.loglik_grad_info(w.locs, w.y, w.X, w.NN, w.theta_true, w.covfun)
+            e = _rel_errors(vg.unpack(out[b], 4, 1), o, w.n)
+            assert max(e.values()) <= 1e-10, (b, m, e)
+        for b in np.argsort(sizes)[-3:]:
+            w = bw.dataset(int(b))
+            r, s = vg.vecchia_loglik_grad_info(
+                _dev(w.locs, torch.float64), _dev(w.y, torch.float64), _dev(w.X, torch.float64),
+                _dev(w.NN, torch.int32), _dev(w.theta_true, torch.float64), w.covfun, handle=h)
+            torch.cuda.synchronize()
+            assert int(s[0]) == 0
+            g, o = vg.unpack(out[int(b)], 4, 1), vg.unpack(r, 4, 1)
+            assert abs(g["loglik"] - o["loglik"]) <= 1e-12 * max(abs(o["loglik"]), w.n)
+            assert np.linalg.norm(g["grad"] - o["grad"]) <= 1e-10 * max(
+                np.linalg.norm(o["grad"]), np.sqrt(np.trace(o["info"])))
+            assert np.linalg.norm(g["info"] - o["info"]) <= 1e-10 * np.linalg.norm(o["info"])
+    finally:
+        h.close()

@@ -2,6 +2,8 @@
 own single-dataset device fit under the same kernel mapping (same statuses and step
 counts, loglik to 1e-10 relative), reaches the oracle's optimum, and the CUDA-graph loop
 equals the host-driven loop bit for bit; plus the batched autotuner."""
+import json
+
 import numpy as np
 import pytest
 
@@ -119,7 +121,9 @@ def test_batch_fit_maxit_zero_returns_start_values(small_batch):
 
 
 def test_batch_autotune_records_and_uses_mapping(tmp_path):
-    bw = workloads.cfg_batch(seed=32, nbatch=5, n_range=(500, 3000), m_choices=(10, 20),
+    # one block-size class (m + 1 <= 16): the tuned mapping is the plan's, and forcing it
+    # gives the same kernels and tiles, hence bitwise equal results
+    bw = workloads.cfg_batch(seed=32, nbatch=5, n_range=(500, 3000), m_choices=(8, 12),
                              m_sim=20)
     h = vg.Handle(0)
     try:
@@ -140,7 +144,40 @@ def test_batch_autotune_records_and_uses_mapping(tmp_path):
                                                       bw.covfun, handle=h2)
         torch.cuda.synchronize()
         h2.close()
-        # same mapping: the same kernels and the same tiles, hence bitwise equal
         assert torch.equal(auto, forced)
+    finally:
+        h.close()
+
+
+def test_batch_autotune_per_class(tmp_path):
+    # datasets in two block-size classes (m = 10 and m = 20): one record per class, keyed by
+    # the class's largest m, and a plan made afterwards uses each class's record
+    bw = workloads.cfg_batch(seed=33, nbatch=6, n_range=(500, 3000), m_choices=(10, 20),
+                             m_sim=20)
+    h = vg.Handle(0)
+    try:
+        cp = _dev(bw.theta_true, torch.float64)
+        vg.vecchia_batch_autotune(*_inputs(bw), bw.offsets, bw.m, cp, bw.covfun, reps=1, handle=h)
+        path = str(tmp_path / "tune.json")
+        h.autotune_save(path)
+        recs = {r["m"]: r for r in json.load(open(path)) if r["prec"] == 2}
+        assert set(recs) == {10, 20}
+        plan = vg.BatchPlan(bw.offsets, bw.m, 2, 1, bw.covfun, handle=h)
+        try:
+            cls = plan.mapping()["classes"]
+        finally:
+            plan.close()
+        assert [c["mmax"] for c in cls] == [10, 20]
+        for c in cls:
+            assert (c["lanes"], c["threads"]) == (recs[c["mmax"]]["lanes"], recs[c["mmax"]]["threads"])
+        out, st = vg.vecchia_batch_loglik_grad_info(*_inputs(bw), bw.offsets, bw.m, cp, bw.covfun,
+                                                    handle=h)
+        torch.cuda.synchronize()
+        assert np.all(st.cpu().numpy()[:, 0] == 0)
+        for b in range(bw.nbatch):
+            w = bw.dataset(b)
+            o = oracle.loglik_grad_info(w.locs, w.y, w.X, w.NN, w.theta_true, w.covfun)
+            g = vg.unpack(out[b], 4, 1)
+            assert abs(g["loglik"] - o["loglik"]) <= 1e-10 * max(abs(o["loglik"]), w.n)
     finally:
         h.close()

@@ -2,7 +2,7 @@
 terms as differences of dense Gaussian blocks), FP64 to 1e-10 as for the plain pass, at
 every lane mapping; singleton groups against the plain device pass; the mixed pass within
 its stated bounds; a full-size field against the C oracle's plain pass on the equivalent
-expanded NNarray; errors."""
+expanded NNarray, in one launch and in launch classes by block size; errors."""
 import numpy as np
 import pytest
 
@@ -33,14 +33,18 @@ def _errors(g, o):
             "beta": np.linalg.norm(g["betahat"] - o["betahat"]) / (np.linalg.norm(o["betahat"]) + 1)}
 
 
-def _grouped(w, goff, th, lanes=0, prec="fp64", blocks=None):
+def _grouped(w, goff, th, lanes=0, prec="fp64", blocks=None, nclass=0):
     off, idx, nm, kmax = blocks if blocks is not None else vg.vecchia_group_blocks(w.NN, goff)
+    classes = None
+    if nclass:
+        gorder, coff, ckmax = vg.vecchia_group_classes(off, nclass)
+        classes = (_dev(gorder, torch.int32), coff, ckmax)
     h = vg.Handle(0)
     h.set_lanes(lanes)
     try:
         out, st = vg.vecchia_grouped_loglik_grad_info(
             _dev(w.locs), _dev(w.y), _dev(w.X), _dev(off, torch.int64), _dev(idx, torch.int32),
-            _dev(nm, torch.int32), kmax, _dev(th), w.covfun, prec=prec, handle=h)
+            _dev(nm, torch.int32), kmax, _dev(th), w.covfun, prec=prec, handle=h, classes=classes)
         torch.cuda.synchronize()
         r = vg.unpack(out, len(th), w.p)
         r["status"], r["bad"] = int(st[0]), int(st[1])
@@ -137,6 +141,11 @@ def test_full_size_against_the_expanded_plain_oracle():
     NNx = _expanded_nn(*blocks[:3])
     o = oracle.loglik_grad_info(w.locs, w.y, w.X, NNx, th, MAT)
     r = _grouped(w, goff, th, blocks=blocks)
+    assert r["status"] == 0
+    e = _errors(r, o)
+    assert max(e.values()) <= 1e-10, e
+    # the same groups in three launches by block size (slots sized per class)
+    r = _grouped(w, goff, th, blocks=blocks, nclass=3)
     assert r["status"] == 0
     e = _errors(r, o)
     assert max(e.values()) <= 1e-10, e

@@ -261,7 +261,7 @@ def test_full_size_matern_100k_matches_oracle():
 @pytest.mark.parametrize("placement", ["global", "shared"])
 def test_full_size_matern_100k_each_table_placement(placement):
     """The full-size pass with the mappings the autotuner picks on GB300 for FP64 (16 lanes,
-    128 threads) and for mixed precision (16 lanes, 256 threads), then FP64 with 8 lanes and
+    96 threads) and for mixed precision (16 lanes, 192 threads), then FP64 with 8 lanes and
     64 threads, with the Matern table in global and in shared memory; the FP64 passes
     against the oracle, the mixed one within its bounds."""
     w = workloads.cfg_matern_100k()
@@ -270,7 +270,7 @@ def test_full_size_matern_100k_each_table_placement(placement):
     t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)  # noqa
     args = (t(w.locs, torch.float64), t(w.y, torch.float64), t(w.X, torch.float64),
             t(w.NN, torch.int32), t(w.theta_true, torch.float64), w.covfun)
-    for prec, lanes, threads in (("fp64", 16, 128), ("mixed", 16, 256), ("fp64", 8, 64)):
+    for prec, lanes, threads in (("fp64", 16, 96), ("mixed", 16, 192), ("fp64", 8, 64)):
         h = vg.Handle(0)
         h.set_lanes(lanes)
         h.set_block_threads(threads)
