@@ -594,9 +594,10 @@ VECCHIA_API vec_status vecchia_predict(vec_handle h, const double* locs, const d
  * best run in separate launches.  From block_off (HOST, ngroups + 1) it picks at most nclass
  * (1..16) classes of block sizes minimising sum over classes of (groups x largest size^2)
  * (the slot size, hence the inverse occupancy) and writes gorder (HOST, ngroups: the group
- * indices, class by class, ascending within a class), class_off (HOST, nclass + 1: class c
- * is gorder[class_off[c] .. class_off[c+1])) and class_kmax (HOST, nclass: the class's
- * largest block; unused trailing classes are empty with kmax 0).
+ * indices, class by class; within a class by block size descending, then by index: the
+ * grouped pass hands groups to its slots in this order, the quickest last), class_off
+ * (HOST, nclass + 1: class c is gorder[class_off[c] .. class_off[c+1])) and class_kmax
+ * (HOST, nclass: the class's largest block; unused trailing classes are empty with kmax 0).
  *
  * vecchia_grouped_loglik_grad_info -- the grouped pass: the same outputs as
  * vecchia_loglik_grad_info (loglik, gradient, Fisher information, betahat; n = the number
@@ -607,8 +608,12 @@ VECCHIA_API vec_status vecchia_predict(vec_handle h, const double* locs, const d
  * nmemb (ngroups, int32) as vecchia_group_blocks writes them; gorder (ngroups, int32) as
  * vecchia_group_classes writes it, or NULL with nclass = 1 (groups in their own order).
  * HOST: class_off (nclass + 1), class_kmax (nclass), each class_kmax[c] in
- * [1, vecchia_max_m() + 1] for a non-empty class.  One kernel launch per non-empty class,
- * all on `stream`, then one profile step.  Isotropic and space-time families
+ * [1, vecchia_max_m() + 1] for a non-empty class.  One kernel launch per non-empty class
+ * (the largest blocks first), the launches side by side on `stream` and two side streams
+ * of the handle that wait for `stream` and that `stream` then waits for (so the call is
+ * ordered on `stream` like any other); each launch's slots take groups from a counter and
+ * each group writes its own record, summed in group order (results do not depend on the
+ * schedule); then one profile step.  Isotropic and space-time families
  * (VEC_ERR_UNSUPPORTED otherwise).  A block whose conditioning set is not ascending and
  * before its members, whose members are not consecutive, or longer than its class's
  * class_kmax, is reported in dev_status as VEC_ERR_ARG with the group index.  Asynchronous.

@@ -145,6 +145,11 @@ struct vec_handle_s {
     char* nn_scratch = nullptr; size_t c_nn_scratch = 0;
     // maxmin ordering scratch
     char* mm_scratch = nullptr; size_t c_mm_scratch = 0;
+    // grouped pass: unit counters of the class launches, and the side streams and events
+    // that let the classes share the GPU (created on first use)
+    int* gcount = nullptr; size_t c_gcount = 0;
+    cudaStream_t gside[2] = {nullptr, nullptr};
+    cudaEvent_t gev[3] = {nullptr, nullptr, nullptr};
     double* mm_bbox = nullptr; size_t c_mm_bbox = 0;
     int* mm_err = nullptr; size_t c_mm_err = 0;
     // pass scratch
@@ -281,6 +286,11 @@ vec_status vecchia_destroy(vec_handle h) {
     DeviceGuard g(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
     cudaFree(h->partials);
+    cudaFree(h->gcount);
+    for (int k = 0; k < 2; ++k)
+        if (h->gside[k]) cudaStreamDestroy(h->gside[k]);
+    for (int k = 0; k < 3; ++k)
+        if (h->gev[k]) cudaEventDestroy(h->gev[k]);
     cudaFree(h->mm_scratch);
     cudaFree(h->mm_bbox);
     cudaFree(h->mm_err);
@@ -1894,13 +1904,15 @@ vec_status vecchia_group_classes(const int64_t* block_off, int64_t ngroups, int 
         k = from[at(c, k)];
     }
     std::reverse(upper.begin(), upper.end());
-    // groups ordered by class, then by index
+    // groups ordered by class; within a class the larger blocks first (slots take groups in
+    // this order, so the last groups handed out are the quickest), then by index
     class_off[0] = 0;
     int64_t pos = 0;
     for (size_t c = 0; c < upper.size(); ++c) {
         const int lo = c == 0 ? 0 : upper[c - 1];
-        for (int64_t b = 0; b < ngroups; ++b)
-            if (len[(size_t)b] > lo && len[(size_t)b] <= upper[c]) gorder[pos++] = (int32_t)b;
+        for (int v = upper[c]; v > lo; --v)
+            for (int64_t b = 0; b < ngroups; ++b)
+                if (len[(size_t)b] == v) gorder[pos++] = (int32_t)b;
         class_off[c + 1] = pos;
         class_kmax[c] = upper[c];
     }
@@ -1944,10 +1956,11 @@ vec_status vecchia_grouped_loglik_grad_info(vec_handle h, const double* locs, co
     if (!g.ok) return fail(VEC_ERR_CUDA, "cannot select device %d", h->device);
     const int cov = (int)covfun;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    // one launch per class, each sized by the class's largest block, writing its own range
-    // of partial records; one profile step over all of them
+    // one launch per class, each sized by the class's largest block, taking its groups from
+    // its own counter and writing one record per group; the launches run side by side on
+    // the caller's stream and two side streams (a class's last groups then overlap the
+    // next class's work); one profile step over all the records, in group order
     vg::PassPlan plans[16];
-    size_t total = 0;
     int nstat = 0;
     for (int c = 0; c < nclass; ++c) {
         if (class_off[c + 1] == class_off[c]) continue;
@@ -1955,21 +1968,34 @@ vec_status vecchia_grouped_loglik_grad_info(vec_handle h, const double* locs, co
                                (int)prec, false, h->tab_mode, true);
         if (pr == -1) return fail(VEC_ERR_UNSUPPORTED, "no kernel mapping fits blocks of %d", class_kmax[c]);
         if (pr != 0) return cuda_fail(cudaGetLastError(), "planning the grouped pass kernel");
-        total += (size_t)plans[c].grid;
         nstat = plans[c].nstat;
     }
-    cudaError_t e = grow(&h->partials, &h->partials_cap, total * nstat);
+    // group records, then their sums 64 at a time (the profile step adds those)
+    const int rchunk = 64;
+    const int nsum = (int)((ngroups + rchunk - 1) / rchunk);
+    cudaError_t e = grow(&h->partials, &h->partials_cap, ((size_t)ngroups + nsum) * nstat);
+    if (e == cudaSuccess) e = grow(&h->gcount, &h->c_gcount, (size_t)16);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k)
+        if (!h->gside[k]) e = cudaStreamCreateWithFlags(&h->gside[k], cudaStreamNonBlocking);
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k)
+        if (!h->gev[k]) e = cudaEventCreateWithFlags(&h->gev[k], cudaEventDisableTiming);
     if (e == cudaSuccess) e = vg::launch_init_status(h->status, h->bad, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->gcount, 0, sizeof(int) * 16, st);
     if (e == cudaSuccess && vg::uses_table(cov, prec))
         e = vg::launch_mtab_build(cov, covparms, h->mtab, prec ? h->mtabf : nullptr, st);
+    if (e == cudaSuccess) e = cudaEventRecord(h->gev[0], st);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(h->gside[k], h->gev[0], 0);
     if (e != cudaSuccess) return cuda_fail(e, "grouped pass: set-up");
-    size_t rec0 = 0;
-    for (int c = 0; c < nclass && e == cudaSuccess; ++c) {
+    // classes with the largest blocks first: their groups take longest
+    int used = 0;
+    for (int c = nclass - 1; c >= 0 && e == cudaSuccess; --c) {
         if (class_off[c + 1] == class_off[c]) continue;
         const vg::PassPlan& plan = plans[c];
+        cudaStream_t sc = used % 3 == 0 ? st : h->gside[used % 3 - 1];
+        ++used;
         vg::PassArgs a;
         a.locs = locs; a.y = y; a.X = X; a.NN = nullptr; a.covparms = covparms;
-        a.mtab = h->mtab; a.mtabf = h->mtabf; a.partials = h->partials + rec0 * nstat;
+        a.mtab = h->mtab; a.mtabf = h->mtabf; a.partials = h->partials + (size_t)class_off[c] * nstat;
         a.status = h->status; a.bad = h->bad;
         a.n = n; a.d = d; a.p = p; a.m = class_kmax[c] - 1;
         a.nstat = plan.nstat; a.nv = plan.nv; a.slot_stride = plan.slot_stride;
@@ -1979,12 +2005,19 @@ vec_status vecchia_grouped_loglik_grad_info(vec_handle h, const double* locs, co
         a.ngroups = class_off[c + 1] - class_off[c];
         a.ngroups_all = ngroups;
         a.gchunk = plan.gchunk;
-        e = vg::launch_pass(cov, plan, a, st);
-        rec0 += (size_t)plan.grid;
+        a.unit_counter = h->gcount + c;
+        e = vg::launch_pass(cov, plan, a, sc);
     }
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = cudaEventRecord(h->gev[1 + k], h->gside[k]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, h->gev[1 + k], 0);
+    }
+    double* sums = h->partials + (size_t)ngroups * nstat;
     if (e == cudaSuccess)
-        e = vg::launch_profile(h->partials, (int)total, nstat, p, q, n, covparms, h->status, h->bad,
-                               out, reinterpret_cast<long long*>(dev_status), st);
+        e = vg::launch_reduce_records(h->partials, (int)ngroups, nstat, rchunk, sums, st);
+    if (e == cudaSuccess)
+        e = vg::launch_profile(sums, nsum, nstat, p, q, n, covparms, h->status, h->bad, out,
+                               reinterpret_cast<long long*>(dev_status), st);
     if (e != cudaSuccess) return cuda_fail(e, "launching the grouped pass");
     return VEC_OK;
 }

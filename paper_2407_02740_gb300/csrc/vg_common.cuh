@@ -177,6 +177,8 @@ struct PassArgs {
     long long ngroups;                 // units of this launch
     long long ngroups_all;             // groups in blk_off / nmemb
     int gchunk = 1;                    // members whose terms are formed together
+    int* unit_counter = nullptr;       // grouped: next unit for a slot (zero at launch), or
+                                       // nullptr for a fixed stride; one record per unit
 };
 
 // Arguments of the batched pass kernel: many datasets (common d, p, covariance family),

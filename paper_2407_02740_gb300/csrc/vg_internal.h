@@ -114,6 +114,10 @@ cudaError_t launch_mtab_build(int cov, const double* covparms, double* tab, floa
                               cudaStream_t st);
 // Loads (under lazy module loading) every kernel the single-dataset FP64 pass can launch.
 cudaError_t load_pass_kernels_f64();
+// out[k] = the sum of records k chunk .. (k+1) chunk - 1 of in, in order (nrec records of
+// nstat doubles; ceil(nrec / chunk) outputs)
+cudaError_t launch_reduce_records(const double* in, int nrec, int nstat, int chunk, double* out,
+                                  cudaStream_t st);
 cudaError_t launch_profile(const double* partials, int nblk, int nstat, int p, int q,
                            long long n, const double* covparms, const int* status,
                            const long long* bad, double* out, long long* dev_status,

@@ -30,20 +30,25 @@ struct ChebMono {
 };
 __constant__ ChebMono c_cheb = ChebMono();
 
-// Table builder: one block of MT_NC warps per interval; warp i evaluates interpolation
-// node i (the Chebyshev nodes of the interval); then 3 x MT_NC threads form the Chebyshev
-// coefficients a_k = (2 / MT_NC) sum_q f(u_q) T_k(u_q) (halved for k = 0), one each, and
-// 3 x MT_NC threads the monomial coefficients sum_deg a_deg c_cheb[deg][k], one each.
+// Table builder: one block of MT_NC + 1 warps per interval; warp i < MT_NC evaluates
+// interpolation node i (the Chebyshev nodes of the interval), warp MT_NC the digamma and
+// log-gamma of nu that the nodes' scaling needs (once per block, while the nodes sum
+// their integrals); then 3 x MT_NC threads form the Chebyshev coefficients
+// a_k = (2 / MT_NC) sum_q f(u_q) T_k(u_q) (halved for k = 0), one each, from a table of
+// T_k(u_q) = cos(pi k (2q + 1) / (2 MT_NC)) filled one entry per thread, and 3 x MT_NC
+// threads the monomial coefficients sum_deg a_deg c_cheb[deg][k], one each.
 // The covariance scales are folded in: F0 x sigma2, F1 x sigma2 / rho, F2 x sigma2.
 // nu is read from covparms[2]; invalid nu leaves the table untouched (the pass reports
 // the parameter error).
-__global__ void __launch_bounds__(MT_NC * 32) k_mtab_build(const double* __restrict__ covparms,
-                                                           double* __restrict__ tab,
-                                                           float* __restrict__ tabf, int q,
-                                                           const int* __restrict__ active,
-                                                           int expfam) {
+__global__ void __launch_bounds__((MT_NC + 1) * 32) k_mtab_build(const double* __restrict__ covparms,
+                                                                 double* __restrict__ tab,
+                                                                 float* __restrict__ tabf, int q,
+                                                                 const int* __restrict__ active,
+                                                                 int expfam) {
     __shared__ double vals[3][MT_NC];
     __shared__ double cheb[3][MT_NC];
+    __shared__ double tk[MT_NC][MT_NC];   // tk[k][q] = T_k(u_q)
+    __shared__ double s_psi, s_lg;
     // blockIdx.y selects the dataset of a batch: its parameters and its tables; datasets
     // whose active flag is 0 are skipped
     if (active && !active[blockIdx.y]) return;
@@ -58,19 +63,31 @@ __global__ void __launch_bounds__(MT_NC * 32) k_mtab_build(const double* __restr
     const double hw = 1.0 / (2.0 * MT_J);
     const double cen = 1.0 + (double)(2 * j + 1) / (double)(2 * MT_J);
     const int node = threadIdx.x >> 5;
-    {
-        const double u = cospi((node + 0.5) / MT_NC);
+    for (int i = threadIdx.x; i < MT_NC * MT_NC; i += blockDim.x)
+        tk[i / MT_NC][i % MT_NC] = cospi((double)((i / MT_NC) * (2 * (i % MT_NC) + 1)) / (2.0 * MT_NC));
+    if (node == MT_NC && !expfam) {
+        const int l = threadIdx.x & 31;
+        if (l == 0) s_psi = dev_digamma(nu);
+        if (l == 1) s_lg = lgamma(nu);
+    }
+    __syncthreads();
+    double f0 = 0.0, f1 = 0.0, f2 = 0.0, S0 = 0.0, S1 = 0.0, S2 = 0.0, Phi = 0.0, x = 0.0;
+    if (node < MT_NC) {
+        const double u = tk[1][node];
         const double s = ldexp(cen + hw * u, e);
-        double f0, f1, f2;
+        x = sqrt(s);
         if (expfam) {
-            const double x = sqrt(s), e = exp(-x);
-            f0 = e;
-            f1 = x * e;
-            f2 = e / x;
+            const double ex = exp(-x);
+            f0 = ex;
+            f1 = x * ex;
+            f2 = ex / x;
         } else {
-            const double psi = dev_digamma(nu), lg = lgamma(nu);
-            matern_direct_warp(nu, sqrt(s), psi, lg, f0, f1, f2);
+            matern_sums_warp(nu, x, S0, S1, S2, Phi);
         }
+    }
+    __syncthreads();
+    if (node < MT_NC) {
+        if (!expfam) matern_finish_warp(nu, x, s_psi, s_lg, S0, S1, S2, Phi, f0, f1, f2);
         if ((threadIdx.x & 31) == 0) { vals[0][node] = f0; vals[1][node] = f1; vals[2][node] = f2; }
     }
     __syncthreads();
@@ -78,8 +95,7 @@ __global__ void __launch_bounds__(MT_NC * 32) k_mtab_build(const double* __restr
     if (t < 3 * MT_NC) {
         const int f = t / MT_NC, k = t % MT_NC;
         double acc = 0.0;
-        for (int qn = 0; qn < MT_NC; ++qn)
-            acc = fma(vals[f][qn], cospi((double)(k * (2 * qn + 1)) / (2.0 * MT_NC)), acc);
+        for (int qn = 0; qn < MT_NC; ++qn) acc = fma(vals[f][qn], tk[k][qn], acc);
         cheb[f][k] = acc * (k == 0 ? 1.0 / MT_NC : 2.0 / MT_NC);
     }
     __syncthreads();
@@ -496,7 +512,7 @@ cudaError_t launch_pass_batch(int cov, const PassPlan& plan, const BatchArgs& ar
 
 cudaError_t launch_mtab_build_batch(int cov, const double* covparms_b, int nbatch, int q,
                                     double* tabs, float* tabsf, const int* active, cudaStream_t st) {
-    k_mtab_build<<<dim3(MT_NINT, nbatch), MT_NC * 32, 0, st>>>(
+    k_mtab_build<<<dim3(MT_NINT, nbatch), (MT_NC + 1) * 32, 0, st>>>(
         covparms_b, tabs, cov == COV_MATERN ? tabsf : nullptr, q, active, cov == COV_MATERN ? 0 : 1);
     return cudaGetLastError();
 }
@@ -540,8 +556,29 @@ cudaError_t launch_init_status(int* status, long long* bad, cudaStream_t st) {
 
 cudaError_t launch_mtab_build(int cov, const double* covparms, double* tab, float* tabf,
                               cudaStream_t st) {
-    k_mtab_build<<<MT_NINT, MT_NC * 32, 0, st>>>(covparms, tab, cov == COV_MATERN ? tabf : nullptr,
+    k_mtab_build<<<MT_NINT, (MT_NC + 1) * 32, 0, st>>>(covparms, tab, cov == COV_MATERN ? tabf : nullptr,
                                                  4, nullptr, cov == COV_MATERN ? 0 : 1);
+    return cudaGetLastError();
+}
+
+// Sums of consecutive records, chunk at a time and in order: out[k] = sum of in[k chunk ..
+// (k+1) chunk) (the last chunk shorter), one block per output record, one thread per entry.
+__global__ void k_reduce_records(const double* __restrict__ in, int nrec, int nstat, int chunk,
+                                 double* __restrict__ out) {
+    const int r0 = blockIdx.x * chunk;
+    const int r1 = r0 + chunk < nrec ? r0 + chunk : nrec;
+    for (int t = threadIdx.x; t < nstat; t += blockDim.x) {
+        double s = 0.0;
+        for (int r = r0; r < r1; ++r) s += in[(size_t)r * nstat + t];
+        out[(size_t)blockIdx.x * nstat + t] = s;
+    }
+}
+
+cudaError_t launch_reduce_records(const double* in, int nrec, int nstat, int chunk, double* out,
+                                  cudaStream_t st) {
+    if (nrec < 1 || chunk < 1 || nstat < 1) return cudaErrorInvalidValue;
+    const int nout = (nrec + chunk - 1) / chunk;
+    k_reduce_records<<<nout, 64, 0, st>>>(in, nrec, nstat, chunk, out);
     return cudaGetLastError();
 }
 

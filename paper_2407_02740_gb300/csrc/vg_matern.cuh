@@ -5,7 +5,8 @@
 // Here M_nu(x) = 2^(1-nu)/Gamma(nu) x^nu K_nu(x) and the two derivatives the likelihood
 // needs are evaluated in two layers:
 //
-//  1. matern_direct_warp (table builder): K_nu, K_(nu-1) and dK_nu/dnu from the integral
+//  1. matern_sums_warp / matern_finish_warp (table builder): K_nu, K_(nu-1) and dK_nu/dnu
+//     from the integral
 //        K_nu(x) = int_0^inf exp(-x cosh t) cosh(nu t) dt
 //     (and its nu-derivative int exp(-x cosh t) t sinh(nu t) dt), trapezoid rule in t,
 //     the nodes shared by the 32 lanes of a warp.  The integrands are even and entire in t
@@ -315,29 +316,49 @@ __device__ __forceinline__ float2 exp_F12_pair(const double* tab, double s, doub
 }
 
 // F0, F1, F2 at x > 0 by the trapezoid rule (h = 0.1; see the header), for the table
-// builder: the envelope exponent mu t - x cosh t with mu = max(nu, |nu-1|) bounds all three
-// integrands and its maximum Phi is factored out; lane l sums the nodes k = l, l+32, ...,
-// then the partial sums are combined in a fixed order.  psi = digamma(nu),
-// lgnu = lgamma(nu).
-__device__ inline void matern_direct_warp(double nu, double x, double psi, double lgnu,
-                                          double& F0, double& F1, double& F2) {
+// builder, in two steps.  matern_sums_warp: the three trapezoid sums with the envelope
+// exponent mu t - x cosh t (mu = max(nu, |nu-1|) bounds all three integrands) and its
+// maximum Phi factored out; lane l sums the nodes t = (l + 32 i) h, then the partial sums
+// are combined in a fixed order.  Along a lane's nodes e^t, e^-t and the four exponentials
+// e^(c t) of the cosh(nu t), cosh((nu-1) t) and t sinh(nu t) factors are geometric in i
+// (ratio e^(32 c h)), so they are advanced by one multiplication each and only the
+// envelope's exponential is evaluated per node (a lane takes at most ~7 nodes, so the
+// products add a few units of the last place).  matern_finish_warp: the scaling
+// 2^(1-nu) x^nu / Gamma(nu) and the nu-derivative's digamma term (psi = digamma(nu),
+// lgnu = lgamma(nu)).
+__device__ inline void matern_sums_warp(double nu, double x, double& S0, double& S1,
+                                        double& S2, double& Phi) {
     const double h = 0.1;
     const int lane = threadIdx.x & 31;
-    double mu = fmax(nu, fabs(nu - 1.0));
-    double ts = asinh(mu / x);
-    double Phi = mu * ts - x * cosh(ts);
-    double S0 = 0.0, S1 = 0.0, S2 = 0.0;
+    const double mu = fmax(nu, fabs(nu - 1.0));
+    const double ts = asinh(mu / x);
+    Phi = mu * ts - x * cosh(ts);
     const double nu1 = fabs(nu - 1.0);
+    const double t0 = lane * h, H = 32.0 * h;
+    double ep = exp(t0), em = exp(-t0);
+    double a = exp((nu - mu) * t0), b = exp(-(nu + mu) * t0);
+    double c = exp((nu1 - mu) * t0), dd = exp(-(nu1 + mu) * t0);
+    const double rp = exp(H), rm = exp(-H);
+    const double ra = exp((nu - mu) * H), rb = exp(-(nu + mu) * H);
+    const double rc = exp((nu1 - mu) * H), rd = exp(-(nu1 + mu) * H);
+    S0 = 0.0;
+    S1 = 0.0;
+    S2 = 0.0;
+    double t = t0;
     for (int k = lane; k < 20000; k += 32) {
-        double t = k * h;
-        double ph = mu * t - x * cosh(t) - Phi;
-        double E = exp(ph) * (k == 0 ? 0.5 : 1.0);
-        double a = exp((nu - mu) * t), b = exp(-(nu + mu) * t);
-        double c = exp((nu1 - mu) * t), dd = exp(-(nu1 + mu) * t);
+        const double ph = mu * t - x * (0.5 * (ep + em)) - Phi;
+        const double E = exp(ph) * (k == 0 ? 0.5 : 1.0);
         S0 += E * 0.5 * (a + b);
         S1 += E * 0.5 * (c + dd);
         S2 += E * 0.5 * t * (a - b);
         if (t > ts && ph < -50.0) break;  // the integrand decreases from here on
+        t += H;
+        ep *= rp;
+        em *= rm;
+        a *= ra;
+        b *= rb;
+        c *= rc;
+        dd *= rd;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -345,6 +366,11 @@ __device__ inline void matern_direct_warp(double nu, double x, double psi, doubl
         S1 += __shfl_xor_sync(0xffffffffu, S1, o);
         S2 += __shfl_xor_sync(0xffffffffu, S2, o);
     }
+}
+__device__ inline void matern_finish_warp(double nu, double x, double psi, double lgnu,
+                                          double S0, double S1, double S2, double Phi,
+                                          double& F0, double& F1, double& F2) {
+    const double h = 0.1;
     const double LN2 = 0.6931471805599453;
     double lx = log(x);
     double logA = (1.0 - nu) * LN2 - lgnu + nu * lx + Phi + log(h);

@@ -1246,14 +1246,38 @@ __global__ void __launch_bounds__(256, pass_min_blocks(sizeof(T))) k_pass(PassAr
     E.gchunk = args.gchunk;
     if (gl == 0) { E.lp[0] = 1.0; *reinterpret_cast<long long*>(E.lp + 1) = 0; }
     if constexpr (GROUPED) {
-        for (long long u = (long long)blockIdx.x * ngrp + grp; ok && u < args.ngroups; u += gstride) {
+        // Units (groups) are taken by each slot from a counter (dynamic: the groups' costs
+        // vary with their block sizes, and launches of several classes may share the GPU),
+        // or in a fixed stride without one.  Each unit writes its own record (the lanes'
+        // sums, log det folded in), so the result does not depend on which slot ran it.
+        const int lead = lane & ~(L - 1);
+        long long u = (long long)blockIdx.x * ngrp + grp;
+        if (args.unit_counter) {
+            int v = 0;
+            if (gl == 0) v = atomicAdd(args.unit_counter, 1);
+            u = __shfl_sync(gmask, v, lead);
+        }
+        while (ok && u < args.ngroups) {
             const long long g = args.gorder ? (long long)args.gorder[u] : u;
             if (g < 0 || g >= args.ngroups_all) {
                 if (gl == 0) report(args.status, args.bad, ST_ARG, u);
-                continue;
+            } else {
+                vecchia_group<COV, L, T, Tab>(E, g);
             }
-            vecchia_group<COV, L, T, Tab>(E, g);
+            if (gl == 0) acc[0] += log_fold(E.lp);
+            for (int t = gl, k = 0; t < args.nstat; t += L, ++k) {
+                args.partials[(size_t)u * args.nstat + t] = acc[k];
+                acc[k] = 0.0;
+            }
+            if (args.unit_counter) {
+                int v = 0;
+                if (gl == 0) v = atomicAdd(args.unit_counter, 1);
+                u = __shfl_sync(gmask, v, lead);
+            } else {
+                u += gstride;
+            }
         }
+        return;
     } else {
         for (long long i = (long long)blockIdx.x * ngrp + grp; ok && i < n; i += gstride) {
             if constexpr (COV == COV_ANISO) vecchia_point_aniso<L, T, Tab>(E, i);

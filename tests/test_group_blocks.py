@@ -59,7 +59,9 @@ def test_group_classes_partition_the_groups(nclass):
         if len(grp) == 0:
             assert ckmax[c] == 0
             continue
-        assert np.all(np.diff(grp) > 0)                       # ascending within a class
+        sz = size[grp]                                        # larger blocks first,
+        assert np.all(np.diff(sz) <= 0)                       # then ascending index
+        assert np.all((np.diff(sz) < 0) | (np.diff(grp) > 0))
         assert size[grp].max() == ckmax[c] and size[grp].min() > lo
         lo = ckmax[c]
     assert ckmax.max() == kmax
