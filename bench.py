@@ -593,23 +593,26 @@ def run_grouped(vg, torch, dev, stream) -> dict:
            "mean_block": float(np.mean(np.diff(off))), "largest_block": int(kmax),
            "launch_classes": {"groups": np.diff(coff).tolist(), "largest_block": ckmax.tolist()}}
     for prec in ("fp64", "mixed"):
-        # the grouped pass in each mapping (lanes per group x threads); the fastest is kept
+        # the grouped pass in each mapping (lanes per group x threads x members formed
+        # together, 0 = the planner's choice); the fastest is kept
         best = None
         for lanes, threads in ((8, 64), (8, 128), (16, 128), (16, 256), (32, 128), (32, 256)):
-            hg = vg.Handle(0)
-            hg.set_lanes(lanes)
-            hg.set_block_threads(threads)
-            try:
-                ms_g, out_g, st_g = timed(lambda: vg.vecchia_grouped_loglik_grad_info(
-                    locs, y, X, doff, didx, dnm, kmax, dth, w.covfun, prec=prec, stream=stream,
-                    handle=hg, classes=classes))
-            except vg.VecchiaError:
+            for chunk in (0, 2, 8):
+                hg = vg.Handle(0)
+                hg.set_lanes(lanes)
+                hg.set_block_threads(threads)
+                hg.set_group_chunk(chunk)
+                try:
+                    ms_g, out_g, st_g = timed(lambda: vg.vecchia_grouped_loglik_grad_info(
+                        locs, y, X, doff, didx, dnm, kmax, dth, w.covfun, prec=prec, stream=stream,
+                        handle=hg, classes=classes))
+                except vg.VecchiaError:
+                    hg.close()
+                    continue
                 hg.close()
-                continue
-            hg.close()
-            if best is None or ms_g < best[0]:
-                best = (ms_g, out_g, st_g, lanes, threads)
-        ms_g, out_g, st_g, lanes_g, threads_g = best
+                if best is None or ms_g < best[0]:
+                    best = (ms_g, out_g, st_g, lanes, threads, chunk)
+        ms_g, out_g, st_g, lanes_g, threads_g, chunk_g = best
         hp = vg.Handle(0)
         vg.vecchia_autotune(locs, y, X, NN, dth, w.covfun, prec=prec, stream=stream, handle=hp)
         ms_p, out_p, st_p = timed(lambda: vg.vecchia_loglik_grad_info(
@@ -622,7 +625,8 @@ def run_grouped(vg, torch, dev, stream) -> dict:
         h45.close()
         res[prec] = {"grouped_ms": ms_g, "grouped_points_per_s": w.n / (ms_g * 1e-3),
                      "plain_m45_ms": ms_45, "loglik_plain_m45": float(out_45[0].item()),
-                     "grouped_mapping": {"lanes": lanes_g, "threads": threads_g},
+                     "grouped_mapping": {"lanes": lanes_g, "threads": threads_g,
+                                         "members_together": chunk_g or "planner (up to 4)"},
                      "plain_ms": ms_p, "plain_points_per_s": w.n / (ms_p * 1e-3),
                      "status": [int(st_g[0].item()), int(st_p[0].item())],
                      "loglik_grouped": float(out_g[0].item()), "loglik_plain": float(out_p[0].item())}

@@ -110,6 +110,13 @@ VECCHIA_API vec_status vecchia_set_lanes(vec_handle h, int lanes);
  * library choose (the default).  Same rules as vecchia_set_lanes. */
 VECCHIA_API vec_status vecchia_set_block_threads(vec_handle h, int threads);
 
+/* Grouped conditioning only (vecchia_grouped_loglik_grad_info): how many members of a
+ * group have their derivative terms formed together, 1..8, or 0 for the library's choice
+ * (the default: the most, up to 4, whose slots fit).  More members per step give each
+ * barrier more work but larger slots, hence fewer resident groups.  A choice whose slots
+ * do not fit makes later grouped passes return VEC_ERR_UNSUPPORTED. */
+VECCHIA_API vec_status vecchia_set_group_chunk(vec_handle h, int chunk);
+
 /* Where the pass kernels read the per-pass Matern coefficient table: 1 = staged in shared
  * memory by every block, 0 = global memory (read through L1, which leaves more shared
  * memory for observation slots), -1 = the library's choice (the default: the autotuned

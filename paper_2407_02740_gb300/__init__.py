@@ -99,6 +99,7 @@ def lib():
                                                        ci, P, P, P, ci, ci, P, P, P]
         L.vecchia_set_lanes.argtypes = [P, ci]
         L.vecchia_set_block_threads.argtypes = [P, ci]
+        L.vecchia_set_group_chunk.argtypes = [P, ci]
         L.vecchia_set_matern_table.argtypes = [P, ci]
         L.vecchia_autotune.argtypes = [P, P, P, P, P, i64, ci, ci, ci, P, ci, ci, P, ci, P, P, P]
         L.vecchia_autotune_save.argtypes = [P, ctypes.c_char_p]
@@ -148,7 +149,7 @@ def lib():
         L.vecchia_fields_warm_start.argtypes = [P, P, P, ci, P, P, P, i64, ci, ci, ci, P, P, i64,
                                                 P, P, ci, P, P, P, P]
         for f in (L.vecchia_create, L.vecchia_destroy, L.vecchia_set_lanes, L.vecchia_set_block_threads,
-                  L.vecchia_set_matern_table,
+                  L.vecchia_set_group_chunk, L.vecchia_set_matern_table,
                   L.vecchia_loglik_grad_info, L.vecchia_loglik_grad_info_host,
                   L.vecchia_covariance_pairs, L.vecchia_nparms, L.vecchia_nparms_d, L.vecchia_max_m,
                   L.vecchia_set_timing, L.vecchia_last_timing, L.vecchia_kernels_per_pass,
@@ -203,6 +204,10 @@ class Handle:
 
     def set_block_threads(self, threads: int):
         _check(lib().vecchia_set_block_threads(self._h, threads))
+
+    def set_group_chunk(self, chunk: int):
+        """Grouped pass: members whose terms are formed together (0 = library's choice)."""
+        _check(lib().vecchia_set_group_chunk(self._h, chunk))
 
     def set_matern_table(self, placement):
         """"shared", "global" or "auto" (see vecchia_set_matern_table)."""

@@ -101,6 +101,7 @@ struct vec_handle_s {
     int lanes = 0;    // 0 = automatic
     int threads = 0;  // 0 = automatic
     int tab_mode = -1;  // forced Matern table placement (-1 = planner's or autotuned choice)
+    int gchunk = 0;     // grouped: members formed together (0 = planner's choice)
     cudaStream_t stream = nullptr;
     // tracing
     int timing = 0;
@@ -241,6 +242,14 @@ vec_status vecchia_set_block_threads(vec_handle h, int threads) {
           threads == 192 || threads == 256))
         return fail(VEC_ERR_ARG, "threads must be 0, 32, 64, 96, 128, 192 or 256 (got %d)", threads);
     h->threads = threads;
+    return VEC_OK;
+}
+
+vec_status vecchia_set_group_chunk(vec_handle h, int chunk) {
+    if (!h) return fail(VEC_ERR_ARG, "vecchia_set_group_chunk: NULL handle");
+    if (chunk < 0 || chunk > vg::GCH_MAX)
+        return fail(VEC_ERR_ARG, "chunk must be 0..%d (got %d)", vg::GCH_MAX, chunk);
+    h->gchunk = chunk;
     return VEC_OK;
 }
 
@@ -1965,7 +1974,7 @@ vec_status vecchia_grouped_loglik_grad_info(vec_handle h, const double* locs, co
     for (int c = 0; c < nclass; ++c) {
         if (class_off[c + 1] == class_off[c]) continue;
         int pr = vg::plan_pass(cov, class_kmax[c] - 1, d, p, h->nsm, h->lanes, h->threads, &plans[c],
-                               (int)prec, false, h->tab_mode, true);
+                               (int)prec, false, h->tab_mode, true, h->gchunk);
         if (pr == -1) return fail(VEC_ERR_UNSUPPORTED, "no kernel mapping fits blocks of %d", class_kmax[c]);
         if (pr != 0) return cuda_fail(cudaGetLastError(), "planning the grouped pass kernel");
         nstat = plans[c].nstat;

@@ -13,6 +13,12 @@ enum : int { ST_OK = 0, ST_ARG = 1, ST_NOT_PD = 2, ST_NONFINITE = 3 };
 enum : int { COV_EXP = 0, COV_MATERN = 1, COV_ST = 2, COV_ANISO = 3 };
 
 constexpr int KMAX = 81;   // largest conditioning block (m <= 80)
+// Grouped conditioning forms the terms of up to GCH members of a group together (each
+// pair of the block evaluated once for all of them, that many times the items between
+// barriers); the planner takes fewer where the larger slot does not fit, and a caller may
+// ask for up to GCH_MAX.
+constexpr int GCH = 4;
+constexpr int GCH_MAX = 8;
 constexpr int PMAX = 8;    // largest number of regression columns
 constexpr int DMAX = 3;    // largest location dimension of the isotropic families
 constexpr int DMAX_ANISO = 20;          // largest dimension with one range per coordinate

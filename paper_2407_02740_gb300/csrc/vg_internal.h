@@ -31,7 +31,7 @@ struct PassPlan {
 // 0 = global memory (read through L1).  Returns 0, -1 (no mapping fits) or -2 (CUDA error).
 int plan_pass(int cov, int m, int d, int p, int nsm, int force_L, int force_threads,
               PassPlan* plan, int prec = 0, bool batched = false, int force_tab = -1,
-              bool grouped = false);
+              bool grouped = false, int force_gchunk = 0);
 size_t pass_smem_bytes(int cov, int m, int d, int p, int L, int threads, bool tab_smem,
                        int prec = 0, bool grouped = false, int gchunk = 1);
 const void* pass_kernel_f64(int cov, int L);

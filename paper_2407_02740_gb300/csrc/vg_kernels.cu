@@ -420,7 +420,8 @@ size_t pass_smem_bytes(int cov, int m, int d, int p, int L, int threads, bool ta
 }
 
 int plan_pass(int cov, int m, int d, int p, int nsm, int force_L, int force_threads,
-              PassPlan* plan, int prec, bool batched, int force_tab, bool grouped) {
+              PassPlan* plan, int prec, bool batched, int force_tab, bool grouped,
+              int force_gchunk) {
     // Preference: 256 threads (two warps per SM sub-partition, so that one warp's FP64
     // dependency waits are covered by the other), then 128 (one warp per sub-partition,
     // the minimum that occupies all FP64 units), then fewer when the largest blocks do
@@ -439,9 +440,11 @@ int plan_pass(int cov, int m, int d, int p, int nsm, int force_L, int force_thre
             if (thr == 256 && force_L <= 0 && L > 16) continue;
             // Matern table in shared memory when it fits (or as forced: force_tab 1 = shared
             // memory only, 0 = global memory, read through L1)
-            // grouped: the most members formed together (GCH, then fewer) that fit
+            // grouped: the most members formed together (GCH, then fewer) that fit, or the
+            // forced number
             bool fit = false;
-            for (int ch = grouped ? GCH : 1; ch >= 1 && !fit; ch /= 2) {
+            const int ch0 = !grouped ? 1 : (force_gchunk > 0 ? force_gchunk : GCH);
+            for (int ch = ch0; ch >= 1 && !fit; ch = (force_gchunk > 0 && grouped) ? 0 : ch / 2) {
                 bool t = uses_table(cov, prec) && force_tab != 0;
                 size_t b = pass_smem_bytes(cov, m, d, p, L, thr, t, prec, grouped, ch);
                 if (b > budget && t && force_tab < 0) {

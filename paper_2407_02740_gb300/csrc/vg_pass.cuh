@@ -131,11 +131,6 @@ struct MaternT<float> {
 //   dinv  K FP64: 1 / d_c
 //   lp    2 FP64: the group's running product of pivot mantissas and sum of exponents, so
 //         that log det needs one logarithm per group and tile, not one per observation
-// Grouped conditioning forms the terms of up to GCH members of a group together (each
-// pair of the block evaluated once for all of them, that many times the items between
-// barriers); the planner takes fewer (gchunk) where the larger slot does not fit.
-constexpr int GCH = 4;
-
 struct SlotLayout {
     int K, A, Y, loc, u, G, D1, nT, Dbyte, dg, dinv, lp, Gs, bytes;
     __host__ __device__ void init(int m, int d, int p, int cov, int nv, int tsize,

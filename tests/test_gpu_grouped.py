@@ -33,7 +33,7 @@ def _errors(g, o):
             "beta": np.linalg.norm(g["betahat"] - o["betahat"]) / (np.linalg.norm(o["betahat"]) + 1)}
 
 
-def _grouped(w, goff, th, lanes=0, prec="fp64", blocks=None, nclass=0):
+def _grouped(w, goff, th, lanes=0, prec="fp64", blocks=None, nclass=0, chunk=0):
     off, idx, nm, kmax = blocks if blocks is not None else vg.vecchia_group_blocks(w.NN, goff)
     classes = None
     if nclass:
@@ -41,6 +41,7 @@ def _grouped(w, goff, th, lanes=0, prec="fp64", blocks=None, nclass=0):
         classes = (_dev(gorder, torch.int32), coff, ckmax)
     h = vg.Handle(0)
     h.set_lanes(lanes)
+    h.set_group_chunk(chunk)
     try:
         out, st = vg.vecchia_grouped_loglik_grad_info(
             _dev(w.locs), _dev(w.y), _dev(w.X), _dev(off, torch.int64), _dev(idx, torch.int32),
@@ -69,6 +70,27 @@ def test_fp64_matches_oracle(covfun, theta, p, n, m, g):
         assert r["status"] == 0
         e = _errors(r, o)
         assert max(e.values()) <= 1e-10, (L, e)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_members_formed_together_in_any_number(prec):
+    # the members' terms formed 1, 2, 3, 5 or 8 at a time (groups of up to 8 members: full
+    # chunks, a shorter last chunk, one chunk for the whole group): FP64 against the oracle,
+    # mixed within its bounds
+    covfun, theta, p, n, m, g = CASES[1]
+    w, goff = workloads.grouped_field(n, covfun, theta, m, g, p=p, seed=11, m_sim=min(m + 5, 40),
+                                      beta=np.linspace(1.0, -0.5, p))
+    th = np.array(theta)
+    off, idx, nm = og.group_blocks(w.NN, goff)
+    o = og.loglik_grad_info(w.locs, w.y, w.X, off, idx, nm, th, covfun)
+    for chunk in (1, 2, 3, 5, 8):
+        r = _grouped(w, goff, th, lanes=32, prec=prec, chunk=chunk)
+        assert r["status"] == 0
+        e = _errors(r, o)
+        if prec == "fp64":
+            assert max(e.values()) <= 1e-10, (chunk, e)
+        else:
+            assert all(e[k] <= MIXED_BOUNDS[k] for k in MIXED_BOUNDS), (chunk, e)
 
 
 @pytest.mark.parametrize("nclass", [2, 3])
