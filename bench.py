@@ -40,6 +40,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import threading
 import time
 
@@ -193,7 +194,6 @@ def cpu_oracle_rate(w, target_s: float = 12.0, nthreads: int = 0):
 def tuned_table_placement(handle, m: int, prec: int, batched: bool = False):
     """The Matern table placement ("shared" / "global") the handle's autotuning record chose
     for (m, precision), read from its saved records."""
-    import tempfile
     with tempfile.TemporaryDirectory() as d:
         path = os.path.join(d, "tune.json")
         handle.autotune_save(path)
@@ -841,6 +841,11 @@ def run_ours(args):
     hl, hy, hX = pin(w.locs, torch.float64), pin(w.y, torch.float64), pin(w.X, torch.float64)
     hNN, hth = pin(w.NN, torch.int32), pin(w.theta_true, torch.float64)
     he = vg.Handle(local)
+    # the autotuned mapping carried over through the saved records, as a caller would
+    with tempfile.TemporaryDirectory() as dtmp:
+        tpath = os.path.join(dtmp, "tune.json")
+        h.autotune_save(tpath)
+        he.autotune_load(tpath)
     for _ in range(2):
         vg.vecchia_loglik_grad_info_host(hl, hy, hX, hNN, hth, w.covfun, handle=he)
     e2e_s = []
