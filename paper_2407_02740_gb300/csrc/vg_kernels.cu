@@ -422,38 +422,57 @@ size_t pass_smem_bytes(int cov, int m, int d, int p, int L, int threads, bool ta
 int plan_pass(int cov, int m, int d, int p, int nsm, int force_L, int force_threads,
               PassPlan* plan, int prec, bool batched, int force_tab, bool grouped,
               int force_gchunk) {
-    // Preference: 256 threads (two warps per SM sub-partition, so that one warp's FP64
-    // dependency waits are covered by the other), then 128 (one warp per sub-partition,
-    // the minimum that occupies all FP64 units), then fewer when the largest blocks do
-    // not fit; within a block size, the fewest lanes per observation that fit.
+    // Candidates: every (threads, lanes, table placement) that fits the shared-memory
+    // budget, or the forced ones.  Unforced lanes are limited to the two powers of two
+    // around half the block size K = m + 1 (fewer lanes leave long triangular loops per
+    // lane, more leave lanes idle in every item round).  The candidate with the most
+    // resident warps per SM (shared memory, registers and threads permitting) is taken;
+    // ties go to fewer lanes, then to more threads (fewer blocks, so fewer partial
+    // records), then to the table in global memory (read through L1).  Grouped: for each
+    // candidate the most members formed together (GCH, then fewer) that fit, or the forced
+    // number.
     const size_t budget = 220 * 1024;
     int chosen = -1, threads = 128, gch = 1;
     bool tab = false;
+    long long best_w = -1;
+    int kp = 1;
+    while (kp < m + 1) kp *= 2;
+    int lmin = kp / 2 < 1 ? 1 : (kp / 2 > 32 ? 32 : kp / 2);
+    if ((cov == COV_ANISO || grouped) && lmin < 4) lmin = 4;   // no instantiation below 4 lanes
     static const int thr_list[] = {256, 192, 128, 96, 64, 32};
-    for (int ti = 0; ti < 6 && chosen < 0; ++ti) {
-        const int thr = thr_list[ti];
-        if (force_threads > 0 && thr != force_threads) continue;
-        for (int L = 1; L <= 32; L *= 2) {
-            if (force_L > 0 && L != force_L) continue;
+    for (int L = 1; L <= 32; L *= 2) {
+        if (force_L > 0 ? L != force_L : (L < lmin || L > 2 * lmin)) continue;
+        if ((cov == COV_ANISO || grouped) && L < 4) continue;
+        const void* fn = pass_kernel(cov, L, prec, batched, grouped);
+        cudaFuncAttributes fa;
+        if (!fn || cudaFuncGetAttributes(&fa, fn) != cudaSuccess) continue;
+        const int regs = fa.numRegs > 0 ? fa.numRegs : 1;
+        for (int ti = 0; ti < 6; ++ti) {
+            const int thr = thr_list[ti];
+            if (force_threads > 0 && thr != force_threads) continue;
             if (L > thr) continue;
-            if ((cov == COV_ANISO || grouped) && L < 4) continue;   // no instantiation below 4 lanes
-            if (thr == 256 && force_L <= 0 && L > 16) continue;
-            // Matern table in shared memory when it fits (or as forced: force_tab 1 = shared
-            // memory only, 0 = global memory, read through L1)
-            // grouped: the most members formed together (GCH, then fewer) that fit, or the
-            // forced number
-            bool fit = false;
-            const int ch0 = !grouped ? 1 : (force_gchunk > 0 ? force_gchunk : GCH);
-            for (int ch = ch0; ch >= 1 && !fit; ch = (force_gchunk > 0 && grouped) ? 0 : ch / 2) {
-                bool t = uses_table(cov, prec) && force_tab != 0;
-                size_t b = pass_smem_bytes(cov, m, d, p, L, thr, t, prec, grouped, ch);
-                if (b > budget && t && force_tab < 0) {
-                    t = false;
-                    b = pass_smem_bytes(cov, m, d, p, L, thr, t, prec, grouped, ch);
+            for (int tb = 0; tb < 2; ++tb) {
+                // tb 0: table in global memory, tb 1: in shared memory (force_tab: 1 = shared
+                // memory only, 0 = global memory only)
+                const bool t = tb == 1;
+                if (t && (!uses_table(cov, prec) || force_tab == 0)) continue;
+                if (!t && uses_table(cov, prec) && force_tab == 1) continue;
+                const int ch0 = !grouped ? 1 : (force_gchunk > 0 ? force_gchunk : GCH);
+                for (int ch = ch0; ch >= 1; ch = (force_gchunk > 0 && grouped) ? 0 : ch / 2) {
+                    const size_t b = pass_smem_bytes(cov, m, d, p, L, thr, t, prec, grouped, ch);
+                    if (b > budget) continue;
+                    long long blk = 2048 / thr;
+                    const long long by_regs = 65536 / ((long long)regs * thr);
+                    const long long by_smem = (233472LL) / (long long)(b + 1024);
+                    blk = blk < by_regs ? blk : by_regs;
+                    blk = blk < by_smem ? blk : by_smem;
+                    blk = blk < 32 ? blk : 32;
+                    if (blk < 1) blk = 1;
+                    const long long w = blk * thr / 32;
+                    if (w > best_w) { best_w = w; chosen = L; tab = t; threads = thr; gch = ch; }
+                    break;   // the most members that fit
                 }
-                if (b <= budget) { fit = true; chosen = L; tab = t; threads = thr; gch = ch; }
             }
-            if (fit) break;
         }
     }
     if (chosen < 0) return -1;
