@@ -321,44 +321,73 @@ __device__ __forceinline__ bool ldl_augmented(T* A, T* Yg, double* dg, double* d
             }
         }
         gsync<L>(gmask);
-        // FP64 blocks: the diagonal updates are items of the triangle like the rest; FP32
-        // blocks: the FP64 diagonal updates form their own loop (one FP64 instruction per
-        // L rows, instead of one in nearly every round of the FP32 items), and the items
-        // are the strict lower triangle (row r + 1 of the items is row c + 2 + r)
+        // FP32 blocks: the FP64 diagonal updates form their own loop (one FP64 instruction
+        // per L rows); FP64 blocks: they are items of the triangle like the rest
         if constexpr (!F64)
             for (int r = c + 1 + gl; r < Kp; r += L)
                 dg[r] = fma(-N::to64(A[r * (r - 1) / 2 + c]), N::to64(tmp[r]), dg[r]);
-        const int nrt = F64 ? nr : nr - 1;              // rows of the item triangle
-        const int ntri = nrt > 0 ? nrt * (nrt + 1) / 2 : 0;
-        int e = gl;
-        if (e < ntri) {
-            int rr = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-            while (rr * (rr + 1) / 2 > e) --rr;
-            while ((rr + 1) * (rr + 2) / 2 <= e) ++rr;
-            int kk = e - rr * (rr + 1) / 2;
-            for (; e < ntri; e += L) {
-                const int r = c + (F64 ? 1 : 2) + rr;
-                T* Ar = A + r * (r - 1) / 2;
-                const T l = Ar[c];
-                const int k = c + 1 + kk;
-                if (F64 && k == r) {
-                    dg[r] = fma(-N::to64(l), N::to64(tmp[r]), dg[r]);
-                } else {
-                    Ar[k] = N::fma_(-l, tmp[k], Ar[k]);
+        if constexpr (!F64) {
+            // FP32 blocks: whole rows of the strict lower triangle per lane (rows c + 2 ..,
+            // in a zigzag over the lanes so that long and short rows pair up), then the
+            // augmented rows entry by entry.  A row costs one load of its pivot-column
+            // entry and, per update, the loads of the entry and of tmp[k] (the same k in
+            // every lane at once); the item bookkeeping of the FP64 blocks (which keeps
+            // every lane's FP64 slots busy) would cost more integer instructions than the
+            // FP32 update itself.
+            const int nrt = nr - 1;
+            for (int b0 = 0; b0 < nrt; b0 += 2 * L) {
+#pragma unroll
+                for (int h2 = 0; h2 < 2; ++h2) {
+                    const int jr = h2 == 0 ? b0 + gl : b0 + 2 * L - 1 - gl;
+                    if (jr >= nrt) continue;
+                    const int r = c + 2 + jr;
+                    T* Ar = A + r * (r - 1) / 2;
+                    const T l = Ar[c];
+                    for (int k = c + 1; k < r; ++k) Ar[k] = N::fma_(-l, tmp[k], Ar[k]);
                 }
-                kk += L;
-                while (kk > rr) { kk -= rr + 1; ++rr; }
             }
-        }
-        if (naug > 0 && nr > 0) {
-            const int e2 = e - ntri;
-            int a = e2 / nr, kk = e2 - a * nr;
-            while (a < naug) {
-                T* z = Yg + a * Kmax;
-                const int k = c + 1 + kk;
-                z[k] = N::fma_(-z[c], tmp[k], z[k]);
-                kk += L;
-                while (kk >= nr) { kk -= nr; ++a; }
+            for (int k = c + 1 + gl; k < Kp; k += L) {
+                const T tk = tmp[k];
+                for (int a = 0; a < naug; ++a) {
+                    T* z = Yg + a * Kmax;
+                    z[k] = N::fma_(-z[c], tk, z[k]);
+                }
+            }
+        } else {
+            // FP64 blocks: every update of the trailing triangle (diagonal included) and of
+            // the augmented rows is one item; the items are spread evenly over the lanes
+            const int nrt = nr;                             // rows of the item triangle
+            const int ntri = nrt > 0 ? nrt * (nrt + 1) / 2 : 0;
+            int e = gl;
+            if (e < ntri) {
+                int rr = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+                while (rr * (rr + 1) / 2 > e) --rr;
+                while ((rr + 1) * (rr + 2) / 2 <= e) ++rr;
+                int kk = e - rr * (rr + 1) / 2;
+                for (; e < ntri; e += L) {
+                    const int r = c + 1 + rr;
+                    T* Ar = A + r * (r - 1) / 2;
+                    const T l = Ar[c];
+                    const int k = c + 1 + kk;
+                    if (k == r) {
+                        dg[r] = fma(-N::to64(l), N::to64(tmp[r]), dg[r]);
+                    } else {
+                        Ar[k] = N::fma_(-l, tmp[k], Ar[k]);
+                    }
+                    kk += L;
+                    while (kk > rr) { kk -= rr + 1; ++rr; }
+                }
+            }
+            if (naug > 0 && nr > 0) {
+                const int e2 = e - ntri;
+                int a = e2 / nr, kk = e2 - a * nr;
+                while (a < naug) {
+                    T* z = Yg + a * Kmax;
+                    const int k = c + 1 + kk;
+                    z[k] = N::fma_(-z[c], tmp[k], z[k]);
+                    kk += L;
+                    while (kk >= nr) { kk -= nr; ++a; }
+                }
             }
         }
         gsync<L>(gmask);
