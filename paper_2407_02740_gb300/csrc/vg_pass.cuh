@@ -12,8 +12,9 @@
 //   assembly    strict lower triangle of the covariance, FP64 diagonal sigma2 (1 + tau2)
 //   factor      right-looking LDL^T (Sigma = U D U^T, U unit lower); y and X ride along as
 //               extra rows of a bordered matrix, so the same sweep produces
-//               z = D^-1 U^-1 (y, X); every update of a step is one item and the items
-//               are spread evenly over the lanes.  The Cholesky factor of Algorithm 1 is
+//               z = D^-1 U^-1 (y, X); FP64 blocks make every update of a step one item
+//               and spread the items evenly over the lanes, FP32 blocks give each lane
+//               whole rows (their cost is instructions, not FP64 slots).  The Cholesky factor of Algorithm 1 is
 //               L = U D^1/2: L^-1 y = D^1/2 z, log det = sum log d_c, and its last row of
 //               the inverse is b = d_K^-1/2 u with u the last row of U^-1
 //   terms       logdet_i = log d_K, ell = d_K^1/2 z_y[K], x = d_K^1/2 z_X[K]
@@ -658,16 +659,27 @@ __device__ __forceinline__ void finish_terms(const PassEnv<T, Tab>& E, int Kp, i
     const T* A = E.A; T* G = E.G;
     const int last = Kp - 1;
     // ---------------- f_j = U^-1 h_j (unit lower, in place) ----------------
+    // FP64 blocks: the items (j, a > c) of a column spread evenly over the lanes; FP32
+    // blocks: rows a per lane, all Q vectors of a row together (one load of U[a][c], no
+    // item bookkeeping)
     for (int c = 0; c < last; ++c) {
-        const int nr = last - c;
-        int j = gl / nr, off = gl - j * nr;
-        const int jstep = L / nr, ostep = L - jstep * nr;
-        while (j < Q) {
-            const int a = c + 1 + off;
-            G[j * Kmax + a] = N::fma_(-A[a * (a - 1) / 2 + c], G[j * Kmax + c], G[j * Kmax + a]);
-            j += jstep;
-            off += ostep;
-            if (off >= nr) { off -= nr; ++j; }
+        if constexpr (sizeof(T) == 4) {
+            for (int a = c + 1 + gl; a < Kp; a += L) {
+                const T l = A[a * (a - 1) / 2 + c];
+                for (int j = 0; j < Q; ++j)
+                    G[j * Kmax + a] = N::fma_(-l, G[j * Kmax + c], G[j * Kmax + a]);
+            }
+        } else {
+            const int nr = last - c;
+            int j = gl / nr, off = gl - j * nr;
+            const int jstep = L / nr, ostep = L - jstep * nr;
+            while (j < Q) {
+                const int a = c + 1 + off;
+                G[j * Kmax + a] = N::fma_(-A[a * (a - 1) / 2 + c], G[j * Kmax + c], G[j * Kmax + a]);
+                j += jstep;
+                off += ostep;
+                if (off >= nr) { off -= nr; ++j; }
+            }
         }
         gsync<L>(gmask);
     }
