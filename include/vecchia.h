@@ -157,8 +157,9 @@ VECCHIA_API vec_status vecchia_set_timing(vec_handle h, int enable);
 VECCHIA_API vec_status vecchia_last_timing(vec_handle h, float* ms_setup, float* ms_pass,
                                            float* ms_profile);
 
-/* Number of kernels one vecchia_loglik_grad_info call launches for this covariance
- * function (used to count launches in benchmarks). */
+/* Number of kernels one FP64 vecchia_loglik_grad_info call launches for this covariance
+ * function (status reset, coefficient table, pass, sums of the block records, profile
+ * step; used to count launches in benchmarks), or -1 for an unknown function. */
 VECCHIA_API int vecchia_kernels_per_pass(vec_covfun covfun);
 
 /*

@@ -224,7 +224,7 @@ vec_status vecchia_last_timing(vec_handle h, float* ms_setup, float* ms_pass, fl
 
 int vecchia_kernels_per_pass(vec_covfun covfun) {
     if (vecchia_nparms_d(covfun, covfun == VEC_EXP_SPACETIME ? 3 : 1) < 0) return -1;
-    return covfun == VEC_MATERN_ISO ? 4 : 3;
+    return 5;   // status reset, table, pass, record sums, profile (FP64: every family's table)
 }
 
 vec_status vecchia_set_lanes(vec_handle h, int lanes) {
@@ -363,6 +363,10 @@ int ilog2(int64_t n) {
     return k;
 }
 
+// Block records are summed this many at a time by k_reduce_records before the profile
+// step (fixed order, so the result does not depend on the grid).
+constexpr int kRecChunk = 64;
+
 vec_status prepare_pass(vec_handle h, int cov, int m, int d, int p, vg::PassPlan* plan,
                         int64_t n = 0, int prec = 0) {
     int L = h->lanes, thr = h->threads, tab = -1;
@@ -381,7 +385,9 @@ vec_status prepare_pass(vec_handle h, int cov, int m, int d, int p, vg::PassPlan
         pr = vg::plan_pass(cov, m, d, p, h->nsm, h->lanes, h->threads, plan, prec);
     if (pr == -1) return fail(VEC_ERR_UNSUPPORTED, "no kernel mapping fits m = %d, p = %d", m, p);
     if (pr != 0) return cuda_fail(cudaGetLastError(), "planning the pass kernel");
-    cudaError_t e = grow(&h->partials, &h->partials_cap, (size_t)plan->grid * plan->nstat);
+    // the blocks' records, then their sums kRecChunk at a time
+    const size_t nsum = ((size_t)plan->grid + kRecChunk - 1) / kRecChunk;
+    cudaError_t e = grow(&h->partials, &h->partials_cap, ((size_t)plan->grid + nsum) * plan->nstat);
     if (e != cudaSuccess) return cuda_fail(e, "allocating partial sums");
     return VEC_OK;
 }
@@ -413,9 +419,15 @@ vec_status enqueue_pass(vec_handle h, const double* locs, const double* y, const
     e = vg::launch_pass(cov, plan, a, st);
     if (e != cudaSuccess) return cuda_fail(e, "launching the pass kernel");
     if (tr) cudaEventRecord(h->ev[2], st);
-    e = vg::launch_profile(h->partials, plan.grid, plan.nstat, p, vg::nparms(cov, d), n, covparms, h->status,
-                           h->bad, out, dev_status, st);
-    if (e != cudaSuccess) return cuda_fail(e, "launching the profile kernel");
+    // the block records summed kRecChunk at a time (in order, by many blocks), then the
+    // profile step over those sums
+    double* sums = h->partials + (size_t)plan.grid * plan.nstat;
+    const int nsum = (plan.grid + kRecChunk - 1) / kRecChunk;
+    e = vg::launch_reduce_records(h->partials, plan.grid, plan.nstat, kRecChunk, sums, st);
+    if (e == cudaSuccess)
+        e = vg::launch_profile(sums, nsum, plan.nstat, p, vg::nparms(cov, d), n, covparms,
+                               h->status, h->bad, out, dev_status, st);
+    if (e != cudaSuccess) return cuda_fail(e, "launching the profile kernels");
     if (tr) {
         cudaEventRecord(h->ev[3], st);
         h->traced = 1;
@@ -1980,7 +1992,7 @@ vec_status vecchia_grouped_loglik_grad_info(vec_handle h, const double* locs, co
         nstat = plans[c].nstat;
     }
     // group records, then their sums 64 at a time (the profile step adds those)
-    const int rchunk = 64;
+    const int rchunk = kRecChunk;
     const int nsum = (int)((ngroups + rchunk - 1) / rchunk);
     cudaError_t e = grow(&h->partials, &h->partials_cap, ((size_t)ngroups + nsum) * nstat);
     if (e == cudaSuccess) e = grow(&h->gcount, &h->c_gcount, (size_t)16);

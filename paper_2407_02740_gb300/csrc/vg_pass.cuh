@@ -898,15 +898,25 @@ __device__ __forceinline__ void group_chunk_terms(const PassEnv<T, Tab>& E, int 
         const int nr = Kc - 1 - c;
         const int nkj = (cnt - k0) * Q;
         T* Gc = G + k0 * Q * Kmax;
-        int kj = gl / nr, off = gl - kj * nr;
-        const int ks = L / nr, os = L - ks * nr;
-        while (kj < nkj) {
-            T* g = Gc + kj * Kmax;
-            const int a = c + 1 + off;
-            g[a] = N::fma_(-A[a * (a - 1) / 2 + c], g[c], g[a]);
-            kj += ks;
-            off += os;
-            if (off >= nr) { off -= nr; ++kj; }
+        if constexpr (sizeof(T) == 4) {          // FP32: rows per lane (see finish_terms)
+            for (int a = c + 1 + gl; a < Kc; a += L) {
+                const T l = A[a * (a - 1) / 2 + c];
+                for (int kj = 0; kj < nkj; ++kj) {
+                    T* g = Gc + kj * Kmax;
+                    g[a] = N::fma_(-l, g[c], g[a]);
+                }
+            }
+        } else {
+            int kj = gl / nr, off = gl - kj * nr;
+            const int ks = L / nr, os = L - ks * nr;
+            while (kj < nkj) {
+                T* g = Gc + kj * Kmax;
+                const int a = c + 1 + off;
+                g[a] = N::fma_(-A[a * (a - 1) / 2 + c], g[c], g[a]);
+                kj += ks;
+                off += os;
+                if (off >= nr) { off -= nr; ++kj; }
+            }
         }
         gsync<L>(gmask);
     }
