@@ -123,23 +123,40 @@ __device__ __forceinline__ double rsqrt_newton(double v) {
     return fma(y * r, fma(r, 0.375, 0.5), y);
 }
 
-// 1/v, v > 0, for the LDL^T pivots.  The FP32 seed is the approximate FP32 reciprocal of
-// v's mantissa truncated to 23 bits (built from the bits, like the conversions, so no
-// FP64 <-> FP32 conversion instruction is issued); its relative error is e < 2^-21.  One
-// third-order step
-//   e = 1 - v y,  y <- y (1 + e + e^2)
-// (the series of 1 / (1 - e) to second order) leaves e^3 < 2^-63 relative: FP64 accuracy
-// in three FP64 operations.  v outside [2^-125, 2^126) takes an FP64 division.
+// 1/v, v > 0, for the LDL^T pivots, in two FP64 operations.  With v = M 2^ex (M in
+// [1, 2)):
+//   * y0 = the approximate FP32 reciprocal of M's first 24 bits (relative error < 2^-21);
+//   * e = 1 - M y0 in FP32, from M split into its first 24 bits and the rest (each
+//     product through an FMA), so y0 (1 + e) is within ~2^-42 of 1/M;
+//   * that value as a fixed-point integer in units of 2^-53 (y0 exactly, plus y0 e
+//     rounded to units of 2^-45), normalised into an FP64 number with 2^-ex folded into
+//     its exponent: integer work only;
+//   * one FP64 Newton step, e2 = 1 - v y1, y = y1 + y1 e2, squares that error (below
+//     2^-80 before the last rounding).
+// v outside [2^-125, 2^126) takes an FP64 division.
 __device__ __forceinline__ double rcp_newton(double v) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(v);
     const int ex = (int)((b >> 52) & 0x7ffull) - 1023;
     if (ex < -125 || ex > 125) return 1.0 / v;
-    const float vf = __uint_as_float(((unsigned)(ex + 127) << 23) | (unsigned)((b >> 29) & 0x7fffffull));
-    float rf;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(vf));
-    const double y = f32_to_f64_bits(rf);
-    const double e = fma(-v, y, 1.0);
-    return fma(y, fma(e, e, e), y);
+    const float mh = __uint_as_float(0x3f800000u | (unsigned)((b >> 29) & 0x7fffffull));
+    const float ml = __uint2float_rn((unsigned)(b & 0x1fffffffull)) * 0x1p-52f;
+    float y0;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(mh));
+    float e = fmaf(-mh, y0, 1.0f);
+    e = fmaf(-ml, y0, e);
+    const float dlt = __fmul_rn(y0, e);
+    const unsigned uy = __float_as_uint(y0);
+    const int sh = (int)((uy >> 23) & 0xffu) - 127 + 30;     // y0 in [1/2, 1]: 29 or 30
+    if (sh < 0 || sh > 40) return 1.0 / v;
+    const long long q0 = (long long)(0x800000u | (uy & 0x7fffffu)) << sh;
+    const long long q1 = q0 + ((long long)__float2int_rn(dlt * 0x1p45f) << 8);
+    const int top = 63 - __clzll(q1);                        // 51 .. 53
+    const unsigned long long mant = top >= 52 ? (unsigned long long)q1 >> (top - 52)
+                                              : (unsigned long long)q1 << (52 - top);
+    const long long bits = ((long long)(1023 + top - 53 - ex) << 52) |
+                           (long long)(mant & 0x000fffffffffffffull);
+    const double y1 = __longlong_as_double(bits);
+    return fma(y1, fma(-v, y1, 1.0), y1);
 }
 
 // digamma(x), x > 0: shift upward with psi(x) = psi(x+1) - 1/x until x >= 12, then the
