@@ -48,9 +48,13 @@ def test_host_only_queries_and_argument_errors():
     assert lib.vecchia_nparms_d(vg.EXP_SPACETIME, 2) == -1
     assert lib.vecchia_nparms_d(vg.MATERN_ISO, 2) == 4
     assert lib.vecchia_max_m() >= 60
-    # a NULL handle is rejected before any CUDA call
+    # a NULL handle or plan is rejected before any CUDA call
     assert lib.vecchia_set_lanes(None, 4) == 1
     assert b"NULL" in lib.vecchia_last_error()
+    assert lib.vecchia_set_group_chunk(None, 4) == 1
+    assert lib.vecchia_batch_plan_class(None, 0, None, None, None, None) == 1
+    assert lib.vecchia_kernels_per_pass(vg.MATERN_ISO) == 5
+    assert lib.vecchia_kernels_per_pass(99) == -1
 
 
 def test_no_fallback_without_the_library(monkeypatch, tmp_path):

@@ -4,7 +4,7 @@ held-out fields, so the fits take fewer passes and reach the same optimum as the
 the default start; the fallback keeps the default where the prediction is worse.
 
 "The same optimum" is the plain method's converged optimum, loglik within 1e-6 relative
-(the default start's fit is the judge).  A Matern likelihood can have more than one local
+(the default start's fit is the reference).  A Matern likelihood can have more than one local
 maximum, and then the start decides which one Fisher scoring reaches: a field whose two
 fits converge to different logliks passes only if the FP64 oracle confirms that both end
 points are local maxima (stationary in the Fisher metric, and lower on both sides along
